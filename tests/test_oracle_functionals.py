@@ -1,0 +1,399 @@
+"""Pins for oracle.binning, oracle.functionals and oracle.selectors.
+
+Every pin compares the oracle with something other than itself: closed
+forms (n = 1, 2), brute-force scalar loops, invariants that hold exactly,
+an independent formulation (tent functions for linear binning, the Parseval
+sum for the binned functional), finite differences for gradients and the
+convergence order of the binning error.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import binning, functionals as F, gauss, rules, selectors as S
+
+
+def _spd(rng, d, scale=1.0):
+    A = rng.standard_normal((d, d))
+    return scale * (A @ A.T / d + 0.3 * np.eye(d))
+
+
+def _mix(rng, n, d):
+    X = rng.standard_normal((n, d))
+    X[: n // 2] += 1.5
+    return X
+
+
+# ---------------------------------------------------------------- binning
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_linear_binning_matches_tent_functions(d):
+    """c_j = sum_i prod_k max(0, 1 - |t_ik - j_k|): the multilinear weights
+    written as hat functions, an independent formulation."""
+    rng = np.random.default_rng(d)
+    M = [5, 4, 6, 3][:d]
+    lo = -np.ones(d)
+    hi = np.array([1.0, 2.0, 1.5, 0.5][:d])
+    X = lo + rng.uniform(0, 1, size=(30, d)) * (hi - lo)
+    X[0] = hi  # upper corner
+    X[1] = lo
+    c = binning.bin_linear(X, lo, hi, M)
+    delta = rules.bin_width(lo, hi, M)
+    want = np.zeros(M)
+    for i in range(X.shape[0]):
+        t = (X[i] - lo) / delta
+        for j in itertools.product(*[range(m) for m in M]):
+            want[j] += math.prod(max(0.0, 1.0 - abs(t[k] - j[k])) for k in range(d))
+    np.testing.assert_allclose(c, want, rtol=1e-13, atol=1e-13)
+
+
+def test_binning_invariants():
+    rng = np.random.default_rng(3)
+    d, M = 2, [17, 23]
+    X = _mix(rng, 500, d)
+    lo, hi = X.min(0) - 0.1, X.max(0) + 0.1
+    c = binning.bin_linear(X, lo, hi, M)
+    assert c.sum() == pytest.approx(500.0, rel=1e-14)
+    g = binning.grid_points(lo, hi, M)
+    # multilinear weights reproduce linear functions: sum c_j g_j = sum X_i
+    assert float(np.sum(c.sum(1) * g[0])) == pytest.approx(X[:, 0].sum(), rel=1e-12)
+    assert float(np.sum(c.sum(0) * g[1])) == pytest.approx(X[:, 1].sum(), rel=1e-12)
+    cs = binning.bin_simple(X, lo, hi, M)
+    assert cs.dtype == np.int64 and int(cs.sum()) == 500
+    # nodes bin onto themselves
+    nodes = np.array([[g[0][3], g[1][7]], [g[0][16], g[1][0]]])
+    cn = binning.bin_linear(nodes, lo, hi, M)
+    assert cn[3, 7] == pytest.approx(1.0, abs=1e-12) and cn[16, 0] == pytest.approx(1.0, abs=1e-12)
+    assert cn.sum() == pytest.approx(2.0, abs=1e-12)
+    # simple binning: ties at half a bin round up
+    half = np.array([[lo[0] + 2.5 * (hi[0] - lo[0]) / 16, g[1][4]]])
+    assert binning.bin_simple(half, lo, hi, M)[3, 4] == 1
+
+
+def test_outside_points():
+    X = np.array([[0.5, 0.5], [1.5, 0.5]])
+    with pytest.raises(binning.OutsideGrid):
+        binning.bin_linear(X, [0, 0], [1, 1], [4, 4])
+    c = binning.bin_linear(X, [0, 0], [1, 1], [4, 4], policy="drop")
+    assert c.sum() == pytest.approx(1.0)
+
+
+# ---------------------------------------------------------------- direct sums
+
+def test_direct_brute_force_scalar_loop():
+    rng = np.random.default_rng(1)
+    d, n = 2, 25
+    X = rng.standard_normal((n, d))
+    H = _spd(rng, d, 0.3)
+    Hi = np.linalg.inv(H)
+    nrm = 1.0 / (2 * math.pi * math.sqrt(np.linalg.det(H)))
+    tot = 0.0
+    for i in range(n):
+        for j in range(n):
+            u = X[i] - X[j]
+            tot += nrm * math.exp(-0.5 * u @ Hi @ u)
+    got = F.direct_sum(X, [(1.0, H, (0, 0))], block=7)
+    assert got == pytest.approx(tot / n ** 2, rel=1e-13)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_psi_closed_forms_n1_n2(d):
+    rng = np.random.default_rng(20 + d)
+    H = _spd(rng, d, 0.5)
+    X1 = rng.standard_normal((1, d))
+    for alpha in gauss.multi_indices(d, 4):
+        got = F.direct_sum(X1, [(1.0, H, alpha)])
+        assert got == pytest.approx(gauss.pairings_value_at_zero(H, alpha), rel=1e-12)
+    X2 = rng.standard_normal((2, d))
+    for alpha in gauss.multi_indices(d, 2):
+        got = F.direct_sum(X2, [(1.0, H, alpha)])
+        want = 0.5 * gauss.pairings_value_at_zero(H, alpha) + \
+            0.5 * float(gauss.gauss_deriv((X2[0] - X2[1])[None], H, alpha)[0])
+        assert got == pytest.approx(want, rel=1e-12)
+
+
+def test_psi_invariants_scaling_rotation():
+    rng = np.random.default_rng(9)
+    d, n = 2, 40
+    X = _mix(rng, n, d)
+    H = _spd(rng, d, 0.4)
+    ev = lambda X_: (lambda terms: F.direct_sum(X_, terms))
+    # scaling: psi_alpha(c^2 H; c X) = c^{-d-|alpha|} psi_alpha(H; X)
+    c = 1.7
+    for r in (0, 2, 4):
+        a = S.psi_vector(ev(X), H, r)
+        b = S.psi_vector(ev(c * X), c * c * H, r)
+        np.testing.assert_allclose(b, c ** (-d - r) * a, rtol=1e-11, atol=1e-15)
+    # rotation: psi_r(R H R^T; X R^T) = R^{(x)r} psi_r(H; X)
+    th = 0.61
+    R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    for r in (2, 4):
+        a = S.psi_vector(ev(X), H, r)
+        b = S.psi_vector(ev(X @ R.T), R @ H @ R.T, r)
+        Rk = R
+        for _ in range(r - 1):
+            Rk = np.kron(Rk, R)
+        np.testing.assert_allclose(b, Rk @ a, rtol=1e-10, atol=1e-12)
+
+
+def test_psi2_is_vec_hessian():
+    """D^{(x)2} f = vec(Hessian f) (Sec. 5)."""
+    rng = np.random.default_rng(4)
+    d, n = 3, 12
+    X = rng.standard_normal((n, d))
+    H = _spd(rng, d, 0.5)
+    v = S.psi_vector(lambda t: F.direct_sum(X, t), H, 2)
+    Hess = np.zeros((d, d))
+    for a in range(d):
+        for b in range(d):
+            al = [0] * d
+            al[a] += 1
+            al[b] += 1
+            Hess[a, b] = F.direct_sum(X, [(1.0, H, tuple(al))])
+    np.testing.assert_allclose(v, Hess.reshape(-1, order="F"), rtol=1e-13)
+
+
+# ---------------------------------------------------------------- binned sums
+
+def _binned_case(d, M, n=300, seed=0):
+    rng = np.random.default_rng(seed)
+    X = _mix(rng, n, d)
+    lo, hi = X.min(0) - 0.2, X.max(0) + 0.2
+    c = binning.bin_linear(X, lo, hi, M)
+    delta = rules.bin_width(lo, hi, M)
+    return X, c, delta
+
+
+@pytest.mark.parametrize("d,M,L", [(1, [40], [9]), (2, [20, 17], [6, 9]), (3, [9, 8, 10], [3, 4, 2])])
+def test_fft_steps_equal_binned_double_sum(d, M, L):
+    X, c, delta = _binned_case(d, M)
+    rng = np.random.default_rng(d)
+    H = _spd(rng, d, 0.2)
+    for terms in (S.lscv_T_terms(H), [(1.0, H, tuple([2] + [0] * (d - 1)))]):
+        ref = F.binned_direct(c, 300, terms, delta, L)
+        for P in (rules.P_paper(M, L), rules.P_minimal(M, L)):
+            got = F.binned_fft(c, 300, terms, delta, L, P)
+            assert got == pytest.approx(ref, rel=1e-11, abs=1e-15)
+
+
+def _parseval(c, n, terms, delta, L, P):
+    """n^-2 P_tot^-1 sum_w |C_w|^2 K_w with k wrapped to j mod P: the
+    frequency-domain form of Eq. 25 (discrete Parseval)."""
+    d = c.ndim
+    czp = np.zeros(P)
+    czp[tuple(slice(0, m) for m in c.shape)] = c
+    k = F.lag_kernel(terms, delta, L)
+    kzp = np.zeros(P)
+    for j in itertools.product(*[range(-l, l + 1) for l in L]):
+        kzp[tuple(jj % p for jj, p in zip(j, P))] += k[tuple(jj + l for jj, l in zip(j, L))]
+    C = np.fft.fftn(czp)
+    K = np.fft.fftn(kzp)
+    return float(np.sum(np.abs(C) ** 2 * K.real)) / np.prod(P) / n ** 2
+
+
+def test_parseval_form_and_aliasing():
+    rng = np.random.default_rng(5)
+    c = rng.uniform(0.0, 3.0, size=(16, 14))     # mass up to the grid edges
+    delta = np.array([0.11, 0.13])
+    H = _spd(np.random.default_rng(8), 2, 0.5)
+    L = [8, 7]
+    terms = S.lscv_T_terms(H)
+    ref = F.binned_direct(c, 300, terms, delta, L)
+    for P in ([24, 21], [25, 24], [32, 32]):
+        assert _parseval(c, 300, terms, delta, L, P) == pytest.approx(ref, rel=1e-11)
+    # one short of M + L aliases
+    bad = _parseval(c, 300, terms, delta, L, [23, 20])
+    assert abs(bad - ref) > 1e-4 * abs(ref)
+
+
+def test_binned_equals_direct_on_nodes():
+    """All points on nodes and L = M - 1: binned sum = direct sum."""
+    rng = np.random.default_rng(2)
+    M = [11, 9]
+    lo, hi = np.array([-1.0, -2.0]), np.array([1.5, 1.0])
+    g = binning.grid_points(lo, hi, M)
+    idx = rng.integers(0, 9, size=(50, 2))
+    X = np.stack([g[0][idx[:, 0]], g[1][idx[:, 1]]], axis=1)
+    c = binning.bin_linear(X, lo, hi, M)
+    H = _spd(rng, 2, 0.3)
+    delta = rules.bin_width(lo, hi, M)
+    for terms in (S.lscv_T_terms(H), [(1.0, H, (2, 2))]):
+        a = F.binned_direct(c, 50, terms, delta, [10, 8])
+        b = F.direct_sum(X, terms)
+        assert a == pytest.approx(b, rel=1e-11)
+
+
+def test_binning_error_is_second_order():
+    """Binned-vs-direct error falls about 4x when the grid spacing halves."""
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((400, 2))
+    H = np.array([[0.3, 0.1], [0.1, 0.4]])
+    terms = S.lscv_T_terms(H)
+    ref = F.direct_sum(X, terms)
+    lo, hi = X.min(0) - 0.5, X.max(0) + 0.5
+    errs = []
+    for m in (21, 41, 81):
+        M = [m, m]
+        c = binning.bin_linear(X, lo, hi, M)
+        delta = rules.bin_width(lo, hi, M)
+        errs.append(abs(F.binned_fft(c, 400, terms, delta, [m - 1, m - 1], [2 * m, 2 * m]) - ref))
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 2.5 < e1 / e2 < 6.0
+
+
+def test_riemann_sum_of_T_is_minus_one():
+    H = np.array([[0.2, 0.07], [0.07, 0.15]])
+    delta = [0.02, 0.02]
+    L = [300, 300]
+    k = F.lag_kernel(S.lscv_T_terms(H), delta, L)
+    assert float(np.prod(delta) * k.sum()) == pytest.approx(-1.0, abs=1e-9)
+
+
+def test_mirrored_lag_layout_fails_for_full_H():
+    """Wand's reshaping uses k_{|j_1|,|j_2|}: exact for diagonal H, wrong for
+    off-diagonal H (Sec. 2, the corrupted estimate)."""
+    X, c, delta = _binned_case(2, [18, 18], seed=3)
+    L = [10, 10]
+
+    def mirrored(terms):
+        k = F.lag_kernel(terms, delta, L)
+        tot = 0.0
+        for j in itertools.product(range(-L[0], L[0] + 1), range(-L[1], L[1] + 1)):
+            tot += k[abs(j[0]) + L[0], abs(j[1]) + L[1]] * F._overlap(c, j)
+        return tot / 300 ** 2
+
+    Hd = np.diag([0.2, 0.3])
+    assert mirrored(S.lscv_T_terms(Hd)) == pytest.approx(F.binned_direct(c, 300, S.lscv_T_terms(Hd), delta, L), rel=1e-12)
+    Hf = np.array([[0.2, 0.15], [0.15, 0.3]])
+    a = mirrored(S.lscv_T_terms(Hf))
+    b = F.binned_direct(c, 300, S.lscv_T_terms(Hf), delta, L)
+    assert abs(a - b) > 1e-3 * abs(b)
+    # the correct functional is invariant under (H_12, x_2) -> (-H_12, -x_2)
+    Hm = Hf * np.array([[1, -1], [-1, 1]])
+    Xm = X * np.array([1.0, -1.0])
+    assert F.direct_sum(Xm, S.lscv_T_terms(Hm)) == pytest.approx(F.direct_sum(X, S.lscv_T_terms(Hf)), rel=1e-12)
+
+
+def test_normal_population_limit():
+    """For X ~ N(0, Sigma): E psi_alpha = n^-1 d^alpha phi_H(0) +
+    (1 - n^-1) d^alpha phi_{H + 2 Sigma}(0); Monte Carlo with a CLT tolerance
+    (5 standard errors, Var ~ 4 Var_i(row mean) / n for a V-statistic)."""
+    rng = np.random.default_rng(31)
+    d, n = 2, 1500
+    Sig = np.array([[1.0, 0.4], [0.4, 0.7]])
+    H = np.array([[0.2, 0.05], [0.05, 0.15]])
+    X = rng.standard_normal((n, d)) @ np.linalg.cholesky(Sig).T
+    diff = X[:, None, :] - X[None, :, :]
+    for alpha in [(0, 0), (2, 0), (1, 1)]:
+        got = F.direct_sum(X, [(1.0, H, alpha)])
+        rows = gauss.gauss_deriv(diff, H, alpha).mean(axis=1)
+        se = math.sqrt(4.0 * rows.var() / n)
+        want = gauss.pairings_value_at_zero(H, alpha) / n + \
+            (1 - 1 / n) * gauss.pairings_value_at_zero(H + 2 * Sig, alpha)
+        assert abs(got - want) < 5.0 * se
+        assert se < 0.2 * abs(want)
+
+
+# ---------------------------------------------------------------- selectors
+
+def _ev_binned(c, n, delta, L):
+    return lambda terms: F.binned_direct(c, n, terms, delta, L)
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_lscv_gradient_by_finite_differences(exact):
+    X, c, delta = _binned_case(2, [20, 20], n=200, seed=4)
+    L = [8, 8]
+    ev = _ev_binned(c, 200, delta, L)
+    H = np.array([[0.35, 0.12], [0.12, 0.25]])
+    _, g = S.lscv(ev, H, 200, exact_loo=exact, grad=True)
+    h = 1e-5
+    for a, b in S.vech_pairs(2):
+        E = np.zeros((2, 2))
+        E[a, b] = E[b, a] = 1.0
+        fd = (S.lscv(ev, H + h * E, 200, exact) - S.lscv(ev, H - h * E, 200, exact)) / (2 * h)
+        assert g[a, b] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_scv_and_pi_gradients_by_finite_differences():
+    X, c, delta = _binned_case(2, [18, 18], n=200, seed=6)
+    ev = _ev_binned(c, 200, delta, [10, 10])
+    H = np.array([[0.3, -0.08], [-0.08, 0.22]])
+    G = np.array([[0.2, 0.03], [0.03, 0.25]])
+    _, g = S.scv(ev, H, G, 200, grad=True)
+    psi4 = S.psi_vector(ev, G, 4)
+    _, gp = S.pi_from_psi4(psi4, H, 200, grad=True)
+    h = 1e-5
+    for a, b in S.vech_pairs(2):
+        E = np.zeros((2, 2))
+        E[a, b] = E[b, a] = 1.0
+        fd = (S.scv(ev, H + h * E, G, 200) - S.scv(ev, H - h * E, G, 200)) / (2 * h)
+        assert g[a, b] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+        fdp = (S.pi_from_psi4(psi4, H + h * E, 200) - S.pi_from_psi4(psi4, H - h * E, 200)) / (2 * h)
+        assert gp[a, b] == pytest.approx(fdp, rel=1e-6, abs=1e-9)
+
+
+def test_pi_eta02_route_equals_psi4_contraction():
+    rng = np.random.default_rng(8)
+    X = _mix(rng, 60, 3)
+    ev = lambda t: F.direct_sum(X, t)
+    H = _spd(rng, 3, 0.2)
+    G = _spd(rng, 3, 0.3)
+    a = S.pi_from_psi4(S.psi_vector(ev, G, 4), H, 60)
+    b = S.pi_eta(ev, H, G, 60)
+    assert a == pytest.approx(b, rel=1e-11)
+
+
+def test_scv_single_point_closed_form():
+    H = np.array([[0.3, 0.1], [0.1, 0.2]])
+    G = np.array([[0.15, 0.0], [0.0, 0.1]])
+    X = np.array([[0.3, -0.2]])
+    got = S.scv(lambda t: F.direct_sum(X, t), H, G, 1)
+    phi0 = lambda Sg: 1.0 / (2 * math.pi * math.sqrt(np.linalg.det(Sg)))
+    want = 1.0 / (4 * math.pi * math.sqrt(np.linalg.det(H))) + \
+        phi0(2 * H + 2 * G) - 2 * phi0(H + 2 * G) + phi0(2 * G)
+    assert got == pytest.approx(want, rel=1e-13)
+
+
+def test_lscv_loo_forms_and_lscv_r0():
+    rng = np.random.default_rng(13)
+    X = _mix(rng, 80, 2)
+    ev = lambda t: F.direct_sum(X, t)
+    H = np.array([[0.25, 0.05], [0.05, 0.3]])
+    n = 80
+    # Eq. 8 evaluated literally with an explicit j != i loop
+    Hi2, Hi = np.linalg.inv(2 * H), np.linalg.inv(H)
+    p2 = 1 / (2 * math.pi * math.sqrt(np.linalg.det(2 * H)))
+    p1 = 1 / (2 * math.pi * math.sqrt(np.linalg.det(H)))
+    a = b = 0.0
+    for i in range(n):
+        for j in range(n):
+            u = X[i] - X[j]
+            a += p2 * math.exp(-0.5 * u @ Hi2 @ u)
+            if i != j:
+                b += p1 * math.exp(-0.5 * u @ Hi @ u)
+    eq8 = a / n ** 2 - 2 * b / (n * (n - 1))
+    assert S.lscv(ev, H, n, exact_loo=True) == pytest.approx(eq8, rel=1e-12)
+    # Eq. 10 form differs from Eq. 8 by O(1/n)
+    assert abs(S.lscv(ev, H, n) - eq8) < 5.0 / n * abs(eq8) + 1e-3
+    # Eqs. 35-36 at r = 0 reduce to Eqs. 8 and 10
+    assert S.lscv_r(ev, H, n, 0, exact_loo=True) == pytest.approx(eq8, rel=1e-12)
+    assert S.lscv_r(ev, H, n, 0) == pytest.approx(S.lscv(ev, H, n), rel=1e-12)
+
+
+def test_eta_r_is_iterated_laplacian():
+    sp = pytest.importorskip("sympy")
+    Sg = np.array([[0.5, 0.2], [0.2, 0.4]])
+    x0, x1 = sp.symbols("x0 x1")
+    Lam = sp.Matrix(np.linalg.inv(Sg).tolist())
+    v = sp.Matrix([x0, x1])
+    phi = 1 / (2 * sp.pi * sp.sqrt(sp.Float(np.linalg.det(Sg), 30))) * sp.exp(-(v.T * Lam * v)[0, 0] / 2)
+    pt = np.array([[0.3, -0.4]])
+    f = phi
+    for r in (1, 2):
+        f = sp.diff(f, x0, 2) + sp.diff(f, x1, 2)
+        want = float(f.subs({x0: pt[0, 0], x1: pt[0, 1]}))
+        got = float(gauss.kernel_eval(pt, S.eta_r_terms(Sg, r))[0])
+        assert got == pytest.approx(want, rel=1e-10)

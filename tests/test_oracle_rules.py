@@ -1,0 +1,86 @@
+"""Pins for oracle.rules against the paper's Tables 2 and 3 (Sec. 6.3)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import rules
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        if line.strip() and not line.startswith("#"):
+            rows.append(tuple(int(v) for v in line.split()))
+    return rows
+
+
+def test_table2_follows_from_table3_by_eq27():
+    P = {(M, n): (p1, p2) for M, n, p1, p2 in _load("table2_P.txt")}
+    L = {(n, M): (l1, l2) for n, M, l1, l2 in _load("table3_L.txt")}
+    checked = 0
+    for (n, M), (l1, l2) in L.items():
+        if (M, n) in P:
+            assert tuple(rules.P_paper([M, M], [l1, l2])) == P[(M, n)]
+            checked += 1
+    assert checked == 20
+
+
+def test_table3_rows_fit_eq26_with_eq16():
+    """Each (row, axis) of Table 3 must be ceil(c (M-1)) for one constant
+    c = tau sqrt(lambda) / range (Eq. 26 with delta = range/(M-1), Eq. 16).
+    The constant is recovered, then support_L must regenerate the row."""
+    rows = {}
+    for n, M, l1, l2 in _load("table3_L.txt"):
+        rows.setdefault(n, []).append((M, l1, l2))
+    for n, r in rows.items():
+        for ax in (0, 1):
+            lo, hi = -1.0, 1e9
+            for M, l1, l2 in r:
+                Lk = (l1, l2)[ax]
+                lo = max(lo, (Lk - 1) / (M - 1))
+                hi = min(hi, Lk / (M - 1))
+            assert lo < hi, (n, ax)
+            c = 0.5 * (lo + hi)
+            rng_width = 10.0
+            tau = 3.7
+            lam = (c * rng_width / tau) ** 2
+            for M, l1, l2 in r:
+                delta = rules.bin_width([0.0], [rng_width], [M])
+                got = rules.support_L(lam, delta, [M], tau)[0]
+                assert got == (l1, l2)[ax], (n, M, ax)
+
+
+def test_table3_rejects_range_over_M():
+    """The same fit with delta = range/M fails on some rows: Table 3 does
+    distinguish Eq. 16 from that plausible slip."""
+    rows = {}
+    for n, M, l1, l2 in _load("table3_L.txt"):
+        rows.setdefault(n, []).append((M, l1, l2))
+    bad = 0
+    for n, r in rows.items():
+        for ax in (0, 1):
+            lo, hi = -1.0, 1e9
+            for M, l1, l2 in r:
+                Lk = (l1, l2)[ax]
+                lo = max(lo, (Lk - 1) / M)
+                hi = min(hi, Lk / M)
+            bad += not (lo < hi)
+    assert bad > 0
+
+
+def test_P_rules_small_values():
+    assert rules.P_paper_full([100]) == [512]          # 3*100-1 = 299
+    assert rules.P_paper([100], [20]) == [256]         # 139
+    assert rules.P_minimal([100], [20]) == [120]
+    assert rules.P_minimal([256], [21]) == [288]
+    assert rules.P_minimal([48], [47]) == [96]
+    assert rules.support_L(1.0, [0.1], [10], 3.7) == [9]   # capped at M-1
+    assert rules.support_L(0.04, [0.1], [100], 3.7) == [8]  # ceil(7.4)
+
+
+def test_bin_width_eq16():
+    np.testing.assert_allclose(rules.bin_width([0.0, -1.0], [1.0, 1.0], [11, 5]), [0.1, 0.5])
