@@ -13,8 +13,11 @@ weight rule; the reading used here is the standard multilinear one:
   the product taken in axis order k = 0..d-1.
 
 Simple binning puts weight 1 on the nearest node, l_k = floor(t_k + 0.5)
-(ties at half a bin round up).  A point with t_k < 0 or t_k > M_k - 1 lies
-outside the grid: policy "error" raises, policy "drop" skips it.
+(ties at half a bin round up).  A point lies inside the grid when
+g_{k1} <= x_k <= g_{kM_k} on every axis (the grid range contains the data,
+Sec. 4); rounding in delta_k can push t_k of a point at the upper end just
+past M_k - 1, so t_k is clamped to M_k - 1.  A point outside: policy "error"
+raises, policy "drop" skips it.
 
 Counts are laid out row-major over (M_0, ..., M_{d-1}), last axis fastest.
 """
@@ -36,12 +39,13 @@ def _coords(X, lo, hi, M):
     lo = np.asarray(lo, dtype=np.float64)
     delta = bin_width(lo, hi, M)
     t = (X - lo) / delta
+    t = np.minimum(t, (np.asarray(M, dtype=np.int64) - 1).astype(np.float64))
     return t, delta
 
 
-def _inside(t, M, policy):
-    M = np.asarray(M, dtype=np.int64)
-    ok = np.all((t >= 0.0) & (t <= (M - 1).astype(np.float64)), axis=1)
+def _inside(X, lo, hi, policy):
+    X = np.asarray(X, dtype=np.float64)
+    ok = np.all((X >= np.asarray(lo, dtype=np.float64)) & (X <= np.asarray(hi, dtype=np.float64)), axis=1)
     if not np.all(ok):
         if policy == "error":
             raise OutsideGrid(f"{int((~ok).sum())} points outside the grid")
@@ -52,7 +56,7 @@ def bin_linear(X, lo, hi, M, policy: str = "error"):
     """Linear binning; returns FP64 counts of shape M."""
     M = [int(m) for m in M]
     t, _ = _coords(X, lo, hi, M)
-    ok = _inside(t, M, policy)
+    ok = _inside(X, lo, hi, policy)
     t = t[ok]
     l = np.floor(t)
     Mm1 = np.asarray(M, dtype=np.float64) - 1.0
@@ -74,7 +78,7 @@ def bin_simple(X, lo, hi, M, policy: str = "error"):
     """Simple (nearest-node) binning; returns int64 counts of shape M."""
     M = [int(m) for m in M]
     t, _ = _coords(X, lo, hi, M)
-    ok = _inside(t, M, policy)
+    ok = _inside(X, lo, hi, policy)
     t = t[ok]
     l = np.floor(t + 0.5).astype(np.int64)
     c = np.zeros(M, dtype=np.int64)

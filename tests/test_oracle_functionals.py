@@ -72,6 +72,18 @@ def test_binning_invariants():
     assert binning.bin_simple(half, lo, hi, M)[3, 4] == 1
 
 
+def test_upper_edge_rounding_stays_inside():
+    """A point exactly at hi is inside even when (hi - lo)/delta rounds to
+    just above M - 1; it lands on the last node with weight 1."""
+    lo, hi, M = -0.920732229392339, 0.11341865083372567, 120
+    assert (hi - lo) / ((hi - lo) / (M - 1)) > M - 1      # the rounding case
+    X = np.array([[hi], [lo]])
+    c = binning.bin_linear(X, [lo], [hi], [M])
+    assert c[-1] == pytest.approx(1.0, abs=1e-12) and c[0] == 1.0 and c.sum() == pytest.approx(2.0)
+    cs = binning.bin_simple(X, [lo], [hi], [M])
+    assert cs[-1] == 1 and cs[0] == 1
+
+
 def test_outside_points():
     X = np.array([[0.5, 0.5], [1.5, 0.5]])
     with pytest.raises(binning.OutsideGrid):
