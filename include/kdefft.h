@@ -1,0 +1,218 @@
+/*
+ * kdefft.h -- C ABI of the GB300 (sm_103a) library for FFT-based bandwidth
+ * selection in multivariate kernel density estimation with unconstrained
+ * (full, symmetric positive definite) d x d bandwidth matrices H.
+ *
+ * Method: Gramacki & Gramacki, "FFT-Based Fast Bandwidth Selector for
+ * Multivariate Kernel Density Estimation" (arXiv 1511.07482).  Sec. 4 gives
+ * the four steps for the LSCV objective: (1) bin the sample onto a grid,
+ * (2) write the binned double sum (Eq. 14) as a convolution of the counts
+ * with a kernel-lag array (Eqs. 17-18, truncated to |j_k| <= L_k by Eq. 25-26),
+ * (3) evaluate the convolution with a zero-padded d-dimensional FFT
+ * (Eqs. 19-23), (4) multiply by the counts and sum (Eq. 24).  Sec. 5 extends
+ * the same steps to the functionals psi_r (Eq. 13) and to the scalar
+ * eta_{r,s} V-statistics (Eqs. 29-32) used by the SCV and plug-in selectors.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: KDEFFT_OK (0) or one of the KDEFFT_ERR_* codes below;
+ *     kdefft_strerror() names a code, kdefft_last_error() gives a one-line
+ *     description of the most recent failure on the calling thread.
+ *   - Pointers: the caller owns every pointer argument.  Array arguments that
+ *     are marked "host or device" may point to host memory or to device
+ *     memory of the context's GPU (detected with cudaPointerGetAttributes);
+ *     all other arrays are host memory.  Calls are ordered on the stream given
+ *     to kdefft_create and return after host outputs have been written;
+ *     device outputs are complete when that stream reaches the call's end.
+ *   - Layouts: the sample X is n x d FP64 row-major; a bandwidth H (and the
+ *     pilot G) is d x d FP64 row-major and must be symmetric to 1e-12
+ *     relative (it is symmetrised as (H + H^T)/2) and positive definite (FP64
+ *     Cholesky, checked before any launch: KDEFFT_ERR_NOT_SPD).  Batches of
+ *     bandwidths are nH consecutive d x d matrices.  Grid counts are laid out
+ *     row-major over (M_0, ..., M_{d-1}), last axis fastest.
+ *   - Gradients: d x d symmetric FP64 matrices g per bandwidth with
+ *     g_aa = dF/dH_aa and, for a != b, g_ab = g_ba = derivative of F along
+ *     E_ab + E_ba (the single free off-diagonal parameter moving both entries).
+ *   - Limits: 1 <= d <= 4, 2 <= M_k, padded sizes P_k <= 4096 and of the form
+ *     2^a 3^b 5^c, derivative order r even and r <= 8 (r <= 6 when d = 4).
+ */
+#ifndef KDEFFT_H
+#define KDEFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define KDEFFT_OK               0
+#define KDEFFT_ERR_ARG          1  /* bad argument: sizes, d, r, null pointer  */
+#define KDEFFT_ERR_NOT_SPD      2  /* H, G or a derived covariance not SPD     */
+#define KDEFFT_ERR_OUTSIDE_GRID 3  /* sample point outside [lo, hi] (policy ERROR) */
+#define KDEFFT_ERR_CUDA         4  /* a CUDA runtime call failed               */
+#define KDEFFT_ERR_ALLOC        5  /* device or host allocation failed         */
+#define KDEFFT_ERR_TIMEOUT      6  /* a bounded device-side wait gave up       */
+#define KDEFFT_ERR_UNSUPPORTED  7  /* size outside the limits above            */
+
+/* ---- options ------------------------------------------------------------ */
+/* Effective-support basis for L_k (Eq. 26): which matrix's largest
+ * eigenvalue sets L_k.  AUTO: the bandwidth argument itself for LSCV and
+ * psi_r (the paper's rule, lambda_max(H)); the widest covariance in the kernel
+ * for SCV (2H + 2G) and for the plug-in functionals (G).  FULL: L_k = M_k - 1
+ * (no truncation, Eq. 17). */
+enum { KDEFFT_L_AUTO = 0, KDEFFT_L_PAPER = 1, KDEFFT_L_WIDEST = 2, KDEFFT_L_FULL = 3 };
+/* Padded FFT length P_k.  MINIMAL: smallest 2^a 3^b 5^c >= M_k + L_k (the
+ * least length for which the circular convolution has no wrapped term at the
+ * needed outputs).  PAPER: Eq. 27, 2^ceil(log2(M_k + 2 L_k - 1)).
+ * PAPER_FULL: Eq. 21, 2^ceil(log2(3 M_k - 1)).  FIXED: opts.P_fixed[k]
+ * (must be >= M_k + L_k). */
+enum { KDEFFT_P_MINIMAL = 0, KDEFFT_P_PAPER = 1, KDEFFT_P_PAPER_FULL = 2, KDEFFT_P_FIXED = 3 };
+enum { KDEFFT_FP32 = 0, KDEFFT_FP64 = 1 };
+/* LINEAR: multilinear weights to the 2^d surrounding nodes (Sec. 4 first
+ * step).  SIMPLE: weight 1 to the nearest node, ties at half a bin upwards;
+ * counts are exact integers. */
+enum { KDEFFT_BIN_LINEAR = 0, KDEFFT_BIN_SIMPLE = 1 };
+enum { KDEFFT_OUTSIDE_ERROR = 0, KDEFFT_OUTSIDE_DROP = 1 };
+enum { KDEFFT_LSCV = 0, KDEFFT_SCV = 1, KDEFFT_PI = 2 };
+enum { KDEFFT_DT_F32 = 0, KDEFFT_DT_F64 = 1, KDEFFT_DT_I32 = 2 };
+
+typedef struct {
+    double tau;          /* Eq. 26 support multiplier; the paper suggests 3.7 */
+    int    L_basis;      /* KDEFFT_L_*                                          */
+    int    P_rule;       /* KDEFFT_P_*                                          */
+    int    P_fixed[4];   /* used with KDEFFT_P_FIXED                            */
+    int    exact_loo;    /* LSCV: 0 = Eq. 10 (n ~ n-1), 1 = Eq. 8 (leave-one-out) */
+    int    precision;    /* KDEFFT_FP32 or KDEFFT_FP64 arithmetic on the GPU    */
+    int    binning;      /* KDEFFT_BIN_*                                        */
+    int    outside_policy; /* KDEFFT_OUTSIDE_*                                  */
+} kdefft_opts;
+
+typedef struct kdefft_ctx_s* kdefft_ctx;
+typedef struct kdefft_ds_s*  kdefft_ds;
+
+/* Fill *opts with the defaults: tau 3.7, L AUTO, P MINIMAL, exact_loo 0,
+ * FP32, LINEAR binning, outside points are an error. */
+int kdefft_opts_default(kdefft_opts* opts);
+
+/* Create a context on CUDA device `device`, ordering all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns its
+ * device buffers (twiddle tables, scratch, work lists) until kdefft_destroy.
+ * Fails with KDEFFT_ERR_CUDA when no usable GPU is present: there is no CPU
+ * fallback. */
+int kdefft_create(kdefft_ctx* ctx, int device, void* stream);
+int kdefft_destroy(kdefft_ctx ctx);
+
+/* Step 1 of Sec. 4: bin the sample X (n x d FP64 row-major; host or device)
+ * onto the grid g_k1 = lo[k] .. g_kM_k = hi[k] with M[k] nodes per axis
+ * (bin width Eq. 16).  Creates a dataset that owns the device counts and the
+ * cached count spectra |F(c_zp)|^2 (one per padded size) until
+ * kdefft_ds_destroy.  opts may be NULL (defaults); the dataset keeps a copy.
+ * Points outside the grid: KDEFFT_ERR_OUTSIDE_GRID under policy ERROR (no
+ * dataset is created), skipped under policy DROP (n keeps its value as the
+ * sample size; kdefft_ds_info reports the dropped count). */
+int kdefft_bin(kdefft_ctx ctx, const double* X, int64_t n, int d,
+               const double* lo, const double* hi, const int64_t* M,
+               const kdefft_opts* opts, kdefft_ds* out);
+int kdefft_ds_destroy(kdefft_ds ds);
+
+/* Replace the dataset's per-call options (tau, L_basis, P_rule, P_fixed,
+ * exact_loo).  Precision, binning and outside policy are fixed at bin time
+ * and are ignored here. */
+int kdefft_ds_set_opts(kdefft_ds ds, const kdefft_opts* opts);
+
+/* n (sample size), d, and the number of dropped points. */
+int kdefft_ds_info(kdefft_ds ds, int64_t* n, int* d, int64_t* dropped);
+
+/* Copy the grid counts (prod M_k values) to dst (host or device) as dtype
+ * KDEFFT_DT_F32, _F64 or _I32 (I32 only for SIMPLE binning, exact). */
+int kdefft_counts(kdefft_ds ds, void* dst, int dtype);
+
+/* The truncation L_k (Eq. 26) and padded sizes P_k that the functional
+ * `method` (KDEFFT_LSCV, _SCV, _PI) or, when method < 0, psi_r would use for
+ * bandwidth H (and pilot G where the method takes one); d ints each. */
+int kdefft_plan(kdefft_ds ds, int method, const double* H, const double* G,
+                int* L_out, int* P_out);
+
+/* psi_r(H) of Eq. 13 with the Gaussian kernel, binned (Eq. 25) and
+ * evaluated by Secs. 4-5's FFT steps, for nH bandwidths: out holds nH
+ * vectors of d^r FP64 values in Kronecker order (Sec. 5: position
+ * (i_1..i_r), i_1 slowest, holds n^-2 sum_ij d^alpha phi_H(X_i - X_j) with
+ * alpha_k = #{m : i_m = k}).  r even, 0 <= r <= 8.  out: host or device. */
+int kdefft_psi(kdefft_ds ds, const double* H, int nH, int r, double* out);
+
+/* LSCV(H) for nH bandwidths: Eq. 10 (psi of Eq. 12 with T_H of Eq. 11, plus
+ * 2 n^-1 K_H(0)) or, with opts.exact_loo, Eq. 8.  val: nH FP64; grad: NULL
+ * or nH d x d gradients (heat-equation kernels through the same FFT, L held
+ * at the value's L).  val/grad: host or device. */
+int kdefft_lscv(kdefft_ds ds, const double* H, int nH, double* val, double* grad);
+
+/* SCV(H) with pilot G (d x d), Gaussian kernels, V-statistic form:
+ * n^-1 (4 pi)^{-d/2} |H|^{-1/2} + n^-2 sum_ij [phi_{2H+2G} - 2 phi_{H+2G}
+ * + phi_{2G}](X_i - X_j).  The paper names SCV (Sec. 3) and defers its
+ * formula (Sec. 5) to Chacon & Duong; this is that source's Gaussian form.
+ * val/grad as kdefft_lscv. */
+int kdefft_scv(kdefft_ds ds, const double* H, int nH, const double* G,
+               double* val, double* grad);
+
+/* Plug-in objective PI(H) = n^-1 (4 pi)^{-d/2} |H|^{-1/2} + 1/4 (vec^T H)^{(x)2}
+ * psi_4(G) with pilot G: the fourth-order functional psi_4(G) is computed
+ * once per call (binned, FFT) and contracted per H; equivalently the
+ * eta_{0,2}(.; H, G) V-statistic of Eqs. 29-30.  val/grad as kdefft_lscv. */
+int kdefft_pi(kdefft_ds ds, const double* H, int nH, const double* G,
+              double* val, double* grad);
+
+/* Per-H plug-in functional V = n^-2 sum_ij eta_{0,2}(X_i - X_j; H, G)
+ * (Eq. 29 with Eq. 30, r = 0, s = 2): one scalar kernel grid per H through
+ * the FFT.  val: nH FP64, host or device. */
+int kdefft_eta02(kdefft_ds ds, const double* H, int nH, const double* G, double* val);
+
+/* Minimise `method` (KDEFFT_LSCV or _SCV or _PI) over H in F, the SPD
+ * matrices (Eq. 9), with a quasi-Newton method on the Cholesky factor of H
+ * (log diagonal) using the exact gradients.  H0: start (NULL: the normal-scale
+ * rule (4/(d+2))^{2/(d+4)} n^{-2/(d+4)} S_hat).  G: pilot for SCV/PI (NULL:
+ * the normal-scale matrix).  n_starts >= 1 independent starts (start 0 is H0,
+ * the others are deterministic dilations/rotations of it) run in lock-step,
+ * one batched evaluation per iteration; the best end point is returned.
+ * H_out: d x d; f_out: objective at H_out; n_evals: total objective+gradient
+ * evaluations (may be NULL). All host. */
+int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G,
+                    int n_starts, int max_iter, double* H_out, double* f_out,
+                    int64_t* n_evals);
+
+/* LSCV(H) and its gradient for many datasets at once: dataset i gets
+ * nH_per_ds[i] consecutive bandwidths from H; every (dataset, H) unit runs
+ * in one batched launch sequence.  val: total nH FP64; grad: NULL or total
+ * nH d x d.  All datasets must belong to ctx and share d and precision.
+ * H, val, grad: host. */
+int kdefft_batch_lscv(kdefft_ctx ctx, int nds, const kdefft_ds* ds,
+                      const int* nH_per_ds, const double* H,
+                      double* val, double* grad);
+
+/* Instrumentation (no paper counterpart).  kdefft_profile(ctx, mode):
+ * mode 1 resets the counters and turns per-kernel timing on, 2 turns it on
+ * without a reset, 0 resets and turns it off.  With timing on, every kernel
+ * launch of the context is bracketed by CUDA events on the context's stream
+ * and its algorithmic bytes (the bytes the pass must move: inputs read once,
+ * outputs written once) and FFT flops (5 P log2 P per transformed line) are
+ * accumulated per kernel name.  Kernel launches and host<->device bytes are
+ * always counted.  kdefft_profile_read copies up to `cap` records. */
+typedef struct {
+    char    name[24];
+    int64_t launches;
+    double  ms;        /* summed CUDA-event duration of the launches */
+    double  bytes;     /* summed algorithmic bytes                   */
+    double  flops;     /* summed algorithmic flops                   */
+} kdefft_kstat;
+
+int kdefft_profile(kdefft_ctx ctx, int mode);
+int kdefft_profile_read(kdefft_ctx ctx, kdefft_kstat* out, int cap, int* count,
+                        int64_t* launches, int64_t* h2d_bytes, int64_t* d2h_bytes);
+
+const char* kdefft_strerror(int code);
+const char* kdefft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDEFFT_H */

@@ -1,0 +1,304 @@
+"""ctypes binding of the C ABI in include/kdefft.h (argument marshalling only).
+
+Every computation runs in libkdefft.so on the GPU; if the library is missing
+or no CUDA device is usable the calls raise: there is no CPU fallback.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); outputs
+are returned as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkdefft.so")
+
+OK, ERR_ARG, ERR_NOT_SPD, ERR_OUTSIDE_GRID, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+L_AUTO, L_PAPER, L_WIDEST, L_FULL = range(4)
+P_MINIMAL, P_PAPER, P_PAPER_FULL, P_FIXED = range(4)
+FP32, FP64 = 0, 1
+BIN_LINEAR, BIN_SIMPLE = 0, 1
+OUTSIDE_ERROR, OUTSIDE_DROP = 0, 1
+LSCV, SCV, PI = 0, 1, 2
+DT_F32, DT_F64, DT_I32 = 0, 1, 2
+
+EXPORTS = [
+    "kdefft_opts_default", "kdefft_create", "kdefft_destroy", "kdefft_bin", "kdefft_ds_destroy",
+    "kdefft_ds_set_opts", "kdefft_ds_info", "kdefft_counts", "kdefft_plan", "kdefft_psi",
+    "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H",
+    "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
+]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tau", C.c_double), ("L_basis", C.c_int), ("P_rule", C.c_int),
+                ("P_fixed", C.c_int * 4), ("exact_loo", C.c_int), ("precision", C.c_int),
+                ("binning", C.c_int), ("outside_policy", C.c_int)]
+
+
+class KStat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+class KdefftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"kdefft error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libkdefft.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with paper_1511_07482_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, D, I, I64 = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int64
+    sig = {
+        "kdefft_opts_default": (I, [C.POINTER(Opts)]),
+        "kdefft_create": (I, [C.POINTER(C.c_void_p), I, P]),
+        "kdefft_destroy": (I, [P]),
+        "kdefft_bin": (I, [P, P, I64, I, P, P, P, C.POINTER(Opts), C.POINTER(C.c_void_p)]),
+        "kdefft_ds_destroy": (I, [P]),
+        "kdefft_ds_set_opts": (I, [P, C.POINTER(Opts)]),
+        "kdefft_ds_info": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+        "kdefft_counts": (I, [P, P, I]),
+        "kdefft_plan": (I, [P, I, P, P, P, P]),
+        "kdefft_psi": (I, [P, P, I, I, P]),
+        "kdefft_lscv": (I, [P, P, I, P, P]),
+        "kdefft_scv": (I, [P, P, I, P, P, P]),
+        "kdefft_pi": (I, [P, P, I, P, P, P]),
+        "kdefft_eta02": (I, [P, P, I, P, P]),
+        "kdefft_select_H": (I, [P, I, P, P, I, I, P, P, P]),
+        "kdefft_batch_lscv": (I, [P, I, P, P, P, P, P]),
+        "kdefft_profile": (I, [P, I]),
+        "kdefft_profile_read": (I, [P, P, I, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)]),
+        "kdefft_strerror": (C.c_char_p, [I]),
+        "kdefft_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != OK:
+        lib = load()
+        raise KdefftError(code, (lib.kdefft_last_error() or b"").decode() or lib.kdefft_strerror(code).decode())
+
+
+def _host_f64(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _ptr_of(x):
+    """(keepalive, pointer) for a numpy array or a torch tensor (host or CUDA)."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64:
+                raise TypeError("expected a float64 tensor")
+            x = x.contiguous()
+            return x, C.c_void_p(x.data_ptr())
+    except ImportError:
+        pass
+    return _host_f64(x)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _check(load().kdefft_opts_default(C.byref(o)))
+    for k, v in kw.items():
+        if k == "P_fixed":
+            for i, p in enumerate(v):
+                o.P_fixed[i] = int(p)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Context:
+    """A kdefft context on one CUDA device and stream (a torch stream or a raw
+    cudaStream_t handle; default: torch's current stream when torch is
+    available, else the legacy default stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except ImportError:
+                stream = None
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        _check(lib.kdefft_create(C.byref(h), int(device), C.c_void_p(stream or 0)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            load().kdefft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, mode: int = 1):
+        """1: reset counters and time every kernel with CUDA events; 2: keep
+        timing without a reset; 0: reset and stop timing."""
+        _check(load().kdefft_profile(self.h, int(mode)))
+
+    def profile_read(self):
+        """Per-kernel stats and counters: (dict name -> dict, launches, h2d, d2h)."""
+        lib = load()
+        arr = (KStat * 64)()
+        cnt = C.c_int()
+        la, hb, db = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.kdefft_profile_read(self.h, C.cast(arr, C.c_void_p), 64, C.byref(cnt), C.byref(la),
+                                       C.byref(hb), C.byref(db)))
+        ks = {}
+        for i in range(min(cnt.value, 64)):
+            k = arr[i]
+            ks[k.name.decode()] = {"launches": k.launches, "ms": k.ms, "bytes": k.bytes, "flops": k.flops}
+        return ks, la.value, hb.value, db.value
+
+    def bin(self, X, lo, hi, M, **opts) -> "Dataset":
+        """Sec. 4 step 1: bin the n x d FP64 sample onto the grid."""
+        keep, px = _ptr_of(X)
+        n, d = int(keep.shape[0]), int(keep.shape[1])
+        lo_a, plo = _host_f64(lo)
+        hi_a, phi = _host_f64(hi)
+        M_a = np.ascontiguousarray(np.asarray(M, dtype=np.int64))
+        o = default_opts(**opts)
+        h = C.c_void_p()
+        _check(load().kdefft_bin(self.h, px, n, d, plo, phi, M_a.ctypes.data_as(C.c_void_p), C.byref(o),
+                                 C.byref(h)))
+        return Dataset(self, h, d, [int(m) for m in M_a])
+
+    def batch_lscv(self, datasets, H_per_ds, grad=True):
+        """LSCV (+ gradient) for many datasets in one batched launch sequence."""
+        lib = load()
+        d = datasets[0].d
+        nh = np.array([len(h) for h in H_per_ds], dtype=np.int32)
+        H = np.ascontiguousarray(np.concatenate([np.asarray(h, dtype=np.float64).reshape(-1, d, d)
+                                                 for h in H_per_ds]))
+        tot = int(nh.sum())
+        val = np.zeros(tot)
+        g = np.zeros((tot, d, d)) if grad else None
+        arr = (C.c_void_p * len(datasets))(*[ds.h for ds in datasets])
+        _check(lib.kdefft_batch_lscv(self.h, len(datasets), arr, nh.ctypes.data_as(C.c_void_p),
+                                     H.ctypes.data_as(C.c_void_p), val.ctypes.data_as(C.c_void_p),
+                                     g.ctypes.data_as(C.c_void_p) if grad else None))
+        return (val, g) if grad else val
+
+
+class Dataset:
+    def __init__(self, ctx, h, d, M):
+        self.ctx, self.h, self.d, self.M = ctx, h, d, M
+
+    def close(self):
+        if self.h:
+            load().kdefft_ds_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_opts(self, **opts):
+        o = default_opts(**opts)
+        _check(load().kdefft_ds_set_opts(self.h, C.byref(o)))
+
+    def info(self):
+        n, d, dr = C.c_int64(), C.c_int(), C.c_int64()
+        _check(load().kdefft_ds_info(self.h, C.byref(n), C.byref(d), C.byref(dr)))
+        return n.value, d.value, dr.value
+
+    def counts(self, dtype=DT_F64):
+        np_t = {DT_F32: np.float32, DT_F64: np.float64, DT_I32: np.int32}[dtype]
+        out = np.zeros(self.M, dtype=np_t)
+        _check(load().kdefft_counts(self.h, out.ctypes.data_as(C.c_void_p), dtype))
+        return out
+
+    def plan(self, method, H, G=None):
+        Ha, pH = _host_f64(H)
+        Ga, pG = _host_f64(G) if G is not None else (None, None)
+        L = np.zeros(self.d, dtype=np.int32)
+        P = np.zeros(self.d, dtype=np.int32)
+        _check(load().kdefft_plan(self.h, method, pH, pG, L.ctypes.data_as(C.c_void_p),
+                                  P.ctypes.data_as(C.c_void_p)))
+        return [int(v) for v in L], [int(v) for v in P]
+
+    def _Hs(self, H):
+        H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, self.d, self.d))
+        return H, H.shape[0]
+
+    def psi(self, H, r):
+        """psi_r(H) (Eq. 13) as nH x d^r, Kronecker order."""
+        H, nH = self._Hs(H)
+        out = np.zeros((nH, self.d ** r))
+        _check(load().kdefft_psi(self.h, H.ctypes.data_as(C.c_void_p), nH, r, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def lscv(self, H, grad=False):
+        H, nH = self._Hs(H)
+        val = np.zeros(nH)
+        g = np.zeros((nH, self.d, self.d)) if grad else None
+        _check(load().kdefft_lscv(self.h, H.ctypes.data_as(C.c_void_p), nH, val.ctypes.data_as(C.c_void_p),
+                                  g.ctypes.data_as(C.c_void_p) if grad else None))
+        return (val, g) if grad else val
+
+    def scv(self, H, G, grad=False):
+        H, nH = self._Hs(H)
+        Ga, pG = _host_f64(G)
+        val = np.zeros(nH)
+        g = np.zeros((nH, self.d, self.d)) if grad else None
+        _check(load().kdefft_scv(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
+                                 g.ctypes.data_as(C.c_void_p) if grad else None))
+        return (val, g) if grad else val
+
+    def pi(self, H, G, grad=False):
+        H, nH = self._Hs(H)
+        Ga, pG = _host_f64(G)
+        val = np.zeros(nH)
+        g = np.zeros((nH, self.d, self.d)) if grad else None
+        _check(load().kdefft_pi(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
+                                g.ctypes.data_as(C.c_void_p) if grad else None))
+        return (val, g) if grad else val
+
+    def eta02(self, H, G):
+        H, nH = self._Hs(H)
+        Ga, pG = _host_f64(G)
+        val = np.zeros(nH)
+        _check(load().kdefft_eta02(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p)))
+        return val
+
+    def select_H(self, method=LSCV, H0=None, G=None, n_starts=1, max_iter=100):
+        Ha, pH = _host_f64(H0) if H0 is not None else (None, None)
+        Ga, pG = _host_f64(G) if G is not None else (None, None)
+        Hout = np.zeros((self.d, self.d))
+        f = C.c_double()
+        ne = C.c_int64()
+        _check(load().kdefft_select_H(self.h, method, pH, pG, int(n_starts), int(max_iter),
+                                      Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
+        return Hout, f.value, ne.value

@@ -1,0 +1,1947 @@
+// Host side of the library and the C ABI declared in include/kdefft.h.
+//
+// Responsibilities (the device does all per-sample and per-grid-point work):
+//   - FP64 bandwidth algebra: symmetrisation, Cholesky (SPD check), inverse,
+//     determinant, largest eigenvalue (Jacobi) -> L_k (Eq. 26), P_k (Eqs. 21,
+//     27 or the minimal no-alias length);
+//   - kernel descriptions: which Gaussian partials, covariances and weights
+//     make each lag kernel (T_H of Eq. 11, heat-equation gradient kernels,
+//     the SCV kernel, psi_r partials, eta_{0,2});
+//   - work lists: pairs of real kernels packed into one complex transform,
+//     tiles of each pass, scratch offsets; one launch sequence per batch;
+//   - objective assembly in FP64 (adding 2 n^-1 K_H(0) etc.);
+//   - the quasi-Newton bandwidth optimiser of kdefft_select_H.
+#include <algorithm>
+#include <functional>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+#include "kdefft.h"
+
+using namespace kdefft;
+
+// ============================================================ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define KCU(call)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(KDEFFT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define KCHK(expr)              \
+    do {                        \
+        int r_ = (expr);        \
+        if (r_ != KDEFFT_OK) return r_; \
+    } while (0)
+
+// ============================================================ buffers
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    int ensure(size_t bytes) {
+        if (bytes <= cap) return KDEFFT_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)4096);
+        want = want + want / 4;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            p = nullptr;
+            return fail(KDEFFT_ERR_ALLOC, "device allocation of " + std::to_string(want) + " bytes failed");
+        }
+        cap = want;
+        return KDEFFT_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct HostBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    HostBuf() = default;
+    HostBuf(const HostBuf&) = delete;
+    HostBuf& operator=(const HostBuf&) = delete;
+    ~HostBuf() { release(); }
+    int ensure(size_t bytes) {
+        if (bytes <= cap) return KDEFFT_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)4096);
+        want = want + want / 4;
+        if (cudaMallocHost(&p, want) != cudaSuccess) {
+            p = nullptr;
+            return fail(KDEFFT_ERR_ALLOC, "pinned host allocation failed");
+        }
+        cap = want;
+        return KDEFFT_OK;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ============================================================ small FP64 matrices (row stride 4)
+struct Mat {
+    int d = 0;
+    double a[16] = {0};
+    double& operator()(int i, int j) { return a[i * 4 + j]; }
+    double operator()(int i, int j) const { return a[i * 4 + j]; }
+};
+
+static Mat mat_from(const double* H, int d) {
+    Mat m;
+    m.d = d;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) m(i, j) = H[i * d + j];
+    return m;
+}
+
+static Mat lin(double a, const Mat& A, double b, const Mat& B) {
+    Mat m;
+    m.d = A.d;
+    for (int i = 0; i < A.d; ++i)
+        for (int j = 0; j < A.d; ++j) m(i, j) = a * A(i, j) + b * B(i, j);
+    return m;
+}
+
+static Mat scaled(double a, const Mat& A) { return lin(a, A, 0.0, A); }
+
+// symmetric check (relative 1e-12) and symmetrisation
+static int sym_check(const double* H, int d, Mat& out, const char* name) {
+    double mx = 0.0;
+    for (int i = 0; i < d * d; ++i) {
+        if (!std::isfinite(H[i])) return fail(KDEFFT_ERR_ARG, std::string(name) + " has a non-finite entry");
+        mx = std::max(mx, std::fabs(H[i]));
+    }
+    out = mat_from(H, d);
+    for (int i = 0; i < d; ++i)
+        for (int j = i + 1; j < d; ++j) {
+            if (std::fabs(out(i, j) - out(j, i)) > 1e-12 * mx)
+                return fail(KDEFFT_ERR_ARG, std::string(name) + " is not symmetric");
+            const double s = 0.5 * (out(i, j) + out(j, i));
+            out(i, j) = out(j, i) = s;
+        }
+    return KDEFFT_OK;
+}
+
+static bool cholesky(const Mat& A, Mat& L) {
+    const int d = A.d;
+    L = Mat();
+    L.d = d;
+    for (int j = 0; j < d; ++j) {
+        double s = A(j, j);
+        for (int k = 0; k < j; ++k) s -= L(j, k) * L(j, k);
+        if (!(s > 0.0) || !std::isfinite(s)) return false;
+        L(j, j) = std::sqrt(s);
+        for (int i = j + 1; i < d; ++i) {
+            double t = A(i, j);
+            for (int k = 0; k < j; ++k) t -= L(i, k) * L(j, k);
+            L(i, j) = t / L(j, j);
+        }
+    }
+    return true;
+}
+
+// inverse and determinant of an SPD matrix from its Cholesky factor
+static bool spd_inv_det(const Mat& A, Mat& inv, double& det) {
+    Mat L;
+    if (!cholesky(A, L)) return false;
+    const int d = A.d;
+    det = 1.0;
+    for (int i = 0; i < d; ++i) det *= L(i, i) * L(i, i);
+    // solve A x = e_c for each column
+    inv = Mat();
+    inv.d = d;
+    for (int c = 0; c < d; ++c) {
+        double y[4], x[4];
+        for (int i = 0; i < d; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L(i, k) * y[k];
+            y[i] = s / L(i, i);
+        }
+        for (int i = d - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int k = i + 1; k < d; ++k) s -= L(k, i) * x[k];
+            x[i] = s / L(i, i);
+        }
+        for (int i = 0; i < d; ++i) inv(i, c) = x[i];
+    }
+    for (int i = 0; i < d; ++i)
+        for (int j = i + 1; j < d; ++j) inv(i, j) = inv(j, i) = 0.5 * (inv(i, j) + inv(j, i));
+    return true;
+}
+
+// largest eigenvalue of a symmetric matrix, cyclic Jacobi rotations
+static double lambda_max(const Mat& S) {
+    const int d = S.d;
+    Mat A = S;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = i + 1; j < d; ++j) off += A(i, j) * A(i, j);
+        if (off < 1e-300) break;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                if (A(p, q) == 0.0) continue;
+                const double theta = (A(q, q) - A(p, p)) / (2.0 * A(p, q));
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < d; ++k) {
+                    const double akp = A(k, p), akq = A(k, q);
+                    A(k, p) = c * akp - s * akq;
+                    A(k, q) = s * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {
+                    const double apk = A(p, k), aqk = A(q, k);
+                    A(p, k) = c * apk - s * aqk;
+                    A(q, k) = s * apk + c * aqk;
+                }
+            }
+    }
+    double m = A(0, 0);
+    for (int i = 1; i < d; ++i) m = std::max(m, A(i, i));
+    return m;
+}
+
+// ============================================================ Hermite recurrence tables
+static const int kRmax[5] = {0, 8, 8, 8, 6};
+
+struct MultiIndex {
+    int a[MAXD];
+};
+
+// graded enumeration: order 0, 1, ..., R; within an order alpha_0 descending,
+// then alpha_1 descending, ...
+static void enumerate(int d, int R, std::vector<MultiIndex>& out) {
+    out.clear();
+    for (int o = 0; o <= R; ++o) {
+        std::vector<MultiIndex> lvl;
+        MultiIndex m{};
+        std::function<void(int, int)> rec = [&](int k, int left) {
+            if (k == d - 1) {
+                m.a[k] = left;
+                lvl.push_back(m);
+                return;
+            }
+            for (int v = left; v >= 0; --v) {
+                m.a[k] = v;
+                rec(k + 1, left - v);
+            }
+        };
+        rec(0, o);
+        out.insert(out.end(), lvl.begin(), lvl.end());
+    }
+}
+
+struct HermiteIndex {
+    std::vector<MultiIndex> list[5];
+    std::map<std::vector<int>, int> index[5];
+    int idx(int d, const int* a) const {
+        std::vector<int> k(a, a + d);
+        auto it = index[d].find(k);
+        return it == index[d].end() ? -1 : it->second;
+    }
+};
+
+static HermiteIndex& hindex() {
+    static HermiteIndex h;
+    static bool init = false;
+    if (!init) {
+        for (int d = 1; d <= 4; ++d) {
+            enumerate(d, kRmax[d], h.list[d]);
+            for (size_t t = 0; t < h.list[d].size(); ++t)
+                h.index[d][std::vector<int>(h.list[d][t].a, h.list[d][t].a + d)] = (int)t;
+        }
+        init = true;
+    }
+    return h;
+}
+
+static int upload_tables() {
+    HermiteIndex& h = hindex();
+    std::vector<HEnt> tab;
+    int offs[5];
+    offs[0] = 0;
+    for (int d = 1; d <= 4; ++d) {
+        for (size_t t = 0; t < h.list[d].size(); ++t) {
+            HEnt e{};
+            if (t > 0) {
+                const MultiIndex& al = h.list[d][t];
+                int piv = 0;
+                while (al.a[piv] == 0) ++piv;
+                int beta[MAXD] = {0};
+                for (int k = 0; k < d; ++k) beta[k] = al.a[k];
+                beta[piv] -= 1;
+                e.piv = (uint8_t)piv;
+                e.par = (uint16_t)h.idx(d, beta);
+                e.nred = 0;
+                for (int j = 0; j < d; ++j)
+                    if (beta[j] > 0) {
+                        int g[MAXD];
+                        for (int k = 0; k < d; ++k) g[k] = beta[k];
+                        g[j] -= 1;
+                        e.rj[e.nred] = (uint8_t)j;
+                        e.rc[e.nred] = (uint8_t)beta[j];
+                        e.ridx[e.nred] = (uint16_t)h.idx(d, g);
+                        e.nred++;
+                    }
+            }
+            tab.push_back(e);
+        }
+        offs[d] = (int)tab.size();
+    }
+    KCU(upload_hermite_tables(tab.data(), offs, (int)tab.size()));
+    return KDEFFT_OK;
+}
+
+// ============================================================ radix plans & twiddles
+static bool radix_plan(int P, AxisPlan& ap) {
+    if (P < 2 || P > MAXP) return false;
+    int x = P;
+    int n = 0;
+    while (x % 8 == 0) {
+        ap.radix[n++] = 8;
+        x /= 8;
+    }
+    if (x % 4 == 0) {
+        ap.radix[n++] = 4;
+        x /= 4;
+    }
+    if (x % 2 == 0) {
+        ap.radix[n++] = 2;
+        x /= 2;
+    }
+    while (x % 5 == 0) {
+        ap.radix[n++] = 5;
+        x /= 5;
+    }
+    while (x % 3 == 0) {
+        ap.radix[n++] = 3;
+        x /= 3;
+    }
+    if (x != 1 || n > MAXST) return false;
+    ap.P = P;
+    ap.nst = n;
+    return true;
+}
+
+static bool is_smooth(long long x) {
+    if (x < 1) return false;
+    for (int p : {2, 3, 5})
+        while (x % p == 0) x /= p;
+    return x == 1;
+}
+
+// ============================================================ context & dataset
+struct kdefft_ds_s;
+
+struct kdefft_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 1;
+    std::map<int, int> tw_off;
+    std::vector<double> tw_host;      // interleaved re, im
+    DevBuf tw32, tw64;
+    size_t tw_dev_n = 0;              // twiddles resident on the device
+    DevBuf scratch, partial, items, tiles, out;
+    HostBuf h_items, h_out;
+    // counters: kernel launches and host<->device bytes (always), per-kernel
+    // CUDA-event times and algorithmic bytes/flops (when profiling is on)
+    struct KStat {
+        int64_t launches = 0;
+        double ms = 0.0, bytes = 0.0, flops = 0.0;
+    };
+    bool prof = false;
+    std::map<std::string, KStat> kstat;
+    struct Pending {
+        std::string name;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> evpool;
+    int64_t launches = 0, h2d = 0, d2h = 0;
+};
+
+static cudaEvent_t ev_get(kdefft_ctx c) {
+    if (!c->evpool.empty()) {
+        cudaEvent_t e = c->evpool.back();
+        c->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket a launch: returns the start event (or null when profiling is off).
+static cudaEvent_t prof_start(kdefft_ctx c) {
+    c->launches++;
+    if (!c->prof) return nullptr;
+    cudaEvent_t a = ev_get(c);
+    cudaEventRecord(a, c->stream);
+    return a;
+}
+
+static void prof_stop(kdefft_ctx c, cudaEvent_t a, const char* name, double bytes, double flops) {
+    if (!c->prof || !a) return;
+    cudaEvent_t b = ev_get(c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({name, a, b, bytes, flops});
+}
+
+// after a stream synchronisation: fold the finished event pairs into the stats
+static void prof_flush(kdefft_ctx c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        auto& k = c->kstat[p.name];
+        k.launches++;
+        k.ms += ms;
+        k.bytes += p.bytes;
+        k.flops += p.flops;
+        c->evpool.push_back(p.a);
+        c->evpool.push_back(p.b);
+    }
+    c->pending.clear();
+}
+
+struct kdefft_ds_s {
+    kdefft_ctx ctx = nullptr;
+    int d = 0;
+    int64_t n = 0;
+    int64_t dropped = 0;
+    double lo[4] = {0}, hi[4] = {0}, delta[4] = {0};
+    int64_t M[4] = {1, 1, 1, 1};
+    int64_t ncells = 0;
+    kdefft_opts opts;
+    DevBuf counts;        // float or double
+    DevBuf counts_i;      // int32 (simple binning)
+    std::map<std::vector<int>, std::shared_ptr<DevBuf>> spectra;
+    double cov[16] = {0}; // sample covariance (d x d, row-major)
+};
+
+static int twiddle_offset(kdefft_ctx c, int P) {
+    auto it = c->tw_off.find(P);
+    if (it != c->tw_off.end()) return it->second;
+    const int off = (int)(c->tw_host.size() / 2);
+    for (int t = 0; t < P; ++t) {
+        const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)P;
+        c->tw_host.push_back((double)cosl(ang));
+        c->tw_host.push_back((double)sinl(ang));
+    }
+    c->tw_off[P] = off;
+    return off;
+}
+
+// make every twiddle on the host resident on the device
+static int sync_twiddles(kdefft_ctx c) {
+    const size_t n = c->tw_host.size() / 2;
+    if (n == c->tw_dev_n) return KDEFFT_OK;
+    KCU(cudaStreamSynchronize(c->stream));
+    KCHK(c->tw64.ensure(n * sizeof(double2)));
+    KCHK(c->tw32.ensure(n * sizeof(float2)));
+    std::vector<float> f(2 * n);
+    for (size_t i = 0; i < 2 * n; ++i) f[i] = (float)c->tw_host[i];
+    KCU(cudaMemcpy(c->tw64.p, c->tw_host.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+    KCU(cudaMemcpy(c->tw32.p, f.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    c->tw_dev_n = n;
+    return KDEFFT_OK;
+}
+
+// ============================================================ kernel descriptions
+struct Term {
+    int sig;
+    int alpha[MAXD];
+    double w;   // weight of d^alpha phi_Sigma (the Hermite sign is applied later)
+};
+
+struct KSpec {
+    int nsig = 0;
+    Mat sig[MAXSIG];
+};
+
+// One real lag kernel to be reduced against a dataset's spectrum.
+struct GridReq {
+    kdefft_ds ds;
+    int spec;              // index into the request set's KSpec list
+    int L[4];
+    int P[4];
+    std::vector<Term> terms;
+    double value = 0.0;    // result: n^-2 sum_w |C|^2 K / prod P  (= Eq. 25)
+};
+
+struct ReqSet {
+    std::vector<KSpec> specs;
+    std::vector<GridReq> grids;
+};
+
+static int support_L(const kdefft_ds ds, double lam, int* L) {
+    for (int k = 0; k < ds->d; ++k) {
+        const double v = ds->opts.tau * std::sqrt(std::fabs(lam)) / ds->delta[k];
+        double c = std::ceil(v);
+        const double cap = (double)(ds->M[k] - 1);
+        if (!(c <= cap)) c = cap;   // also catches NaN/inf
+        if (c < 1.0) c = 1.0;
+        L[k] = (int)c;
+    }
+    return KDEFFT_OK;
+}
+
+static int choose_P(const kdefft_ds ds, const int* L, int* P) {
+    for (int k = 0; k < ds->d; ++k) {
+        const long long M = ds->M[k];
+        long long p = 0;
+        switch (ds->opts.P_rule) {
+            case KDEFFT_P_PAPER: {
+                p = 1;
+                while (p < M + 2 * L[k] - 1) p *= 2;
+                break;
+            }
+            case KDEFFT_P_PAPER_FULL: {
+                p = 1;
+                while (p < 3 * M - 1) p *= 2;
+                break;
+            }
+            case KDEFFT_P_FIXED:
+                p = ds->opts.P_fixed[k];
+                break;
+            default: {
+                p = M + L[k];
+                while (!is_smooth(p)) ++p;
+            }
+        }
+        if (p < M + L[k]) return fail(KDEFFT_ERR_ARG, "padded size P_k below M_k + L_k would alias");
+        if (p > MAXP || !is_smooth(p))
+            return fail(KDEFFT_ERR_UNSUPPORTED, "padded size " + std::to_string(p) + " not 2^a3^b5^c <= 4096");
+        P[k] = (int)p;
+    }
+    return KDEFFT_OK;
+}
+
+// support and padding for a kernel whose basis matrix is B
+static int plan_for(const kdefft_ds ds, const Mat& B, int* L, int* P) {
+    if (ds->opts.L_basis == KDEFFT_L_FULL) {
+        for (int k = 0; k < ds->d; ++k) L[k] = (int)(ds->M[k] - 1);
+    } else {
+        KCHK(support_L(ds, lambda_max(B), L));
+    }
+    return choose_P(ds, L, P);
+}
+
+static int spd_or_fail(const Mat& S, const char* what) {
+    Mat L;
+    if (!cholesky(S, L)) return fail(KDEFFT_ERR_NOT_SPD, std::string(what) + " is not positive definite");
+    return KDEFFT_OK;
+}
+
+static void alpha2(int d, int a, int b, int* out) {
+    for (int k = 0; k < MAXD; ++k) out[k] = 0;
+    out[a] += 1;
+    out[b] += 1;
+    (void)d;
+}
+
+// ---- LSCV (Eqs. 8, 10-11) ------------------------------------------------
+// grids: [value grids..., gradient grids (a <= b)...]
+static int add_lscv(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int& first) {
+    const int d = ds->d;
+    KCHK(spd_or_fail(H, "H"));
+    KSpec sp;
+    sp.nsig = 2;
+    sp.sig[0] = scaled(2.0, H);
+    sp.sig[1] = H;
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    const Mat& basis = (ds->opts.L_basis == KDEFFT_L_WIDEST) ? sp.sig[0] : H;
+    KCHK(plan_for(ds, basis, L, P));
+    first = (int)rs.grids.size();
+    auto push = [&](std::vector<Term> t) {
+        GridReq g;
+        g.ds = ds;
+        g.spec = si;
+        std::memcpy(g.L, L, sizeof(L));
+        std::memcpy(g.P, P, sizeof(P));
+        g.terms = std::move(t);
+        rs.grids.push_back(std::move(g));
+    };
+    const double n = (double)ds->n;
+    if (!ds->opts.exact_loo) {
+        push({Term{0, {0, 0, 0, 0}, 1.0}, Term{1, {0, 0, 0, 0}, -2.0}});
+    } else {
+        push({Term{0, {0, 0, 0, 0}, 1.0}});
+        push({Term{1, {0, 0, 0, 0}, 1.0}});
+    }
+    if (grad) {
+        const double f = ds->opts.exact_loo ? n / (n - 1.0) : 1.0;
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) {
+                const double s = (a == b) ? 1.0 : 2.0;
+                Term t0{0, {0}, s}, t1{1, {0}, -s * f};
+                alpha2(d, a, b, t0.alpha);
+                alpha2(d, a, b, t1.alpha);
+                push({t0, t1});
+            }
+    }
+    return KDEFFT_OK;
+}
+
+// ---- SCV (reading; Gaussian pilot G) --------------------------------------
+static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool grad, int& first) {
+    const int d = ds->d;
+    KCHK(spd_or_fail(H, "H"));
+    KSpec sp;
+    sp.nsig = 3;
+    sp.sig[0] = lin(2.0, H, 2.0, G);
+    sp.sig[1] = lin(1.0, H, 2.0, G);
+    sp.sig[2] = scaled(2.0, G);
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    const Mat& basis = (ds->opts.L_basis == KDEFFT_L_PAPER) ? H : sp.sig[0];
+    KCHK(plan_for(ds, basis, L, P));
+    first = (int)rs.grids.size();
+    auto push = [&](std::vector<Term> t) {
+        GridReq g;
+        g.ds = ds;
+        g.spec = si;
+        std::memcpy(g.L, L, sizeof(L));
+        std::memcpy(g.P, P, sizeof(P));
+        g.terms = std::move(t);
+        rs.grids.push_back(std::move(g));
+    };
+    push({Term{0, {0}, 1.0}, Term{1, {0}, -2.0}, Term{2, {0}, 1.0}});
+    if (grad) {
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) {
+                const double s = (a == b) ? 1.0 : 2.0;
+                Term t0{0, {0}, s}, t1{1, {0}, -s};
+                alpha2(d, a, b, t0.alpha);
+                alpha2(d, a, b, t1.alpha);
+                push({t0, t1});
+            }
+    }
+    return KDEFFT_OK;
+}
+
+// ---- psi_r (Eq. 13): one grid per unique multi-index |alpha| = r ----------
+static int add_psi(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first, std::vector<MultiIndex>& alphas) {
+    const int d = ds->d;
+    KSpec sp;
+    sp.nsig = 1;
+    sp.sig[0] = H;
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    KCHK(plan_for(ds, H, L, P));
+    first = (int)rs.grids.size();
+    alphas.clear();
+    for (const MultiIndex& m : hindex().list[d]) {
+        int o = 0;
+        for (int k = 0; k < d; ++k) o += m.a[k];
+        if (o == r) alphas.push_back(m);
+    }
+    for (const MultiIndex& m : alphas) {
+        GridReq g;
+        g.ds = ds;
+        g.spec = si;
+        std::memcpy(g.L, L, sizeof(L));
+        std::memcpy(g.P, P, sizeof(P));
+        Term t{0, {0}, 1.0};
+        for (int k = 0; k < MAXD; ++k) t.alpha[k] = (k < d) ? m.a[k] : 0;
+        g.terms = {t};
+        rs.grids.push_back(std::move(g));
+    }
+    return KDEFFT_OK;
+}
+
+// ---- eta_{0,2}(x; B, Sigma) = (vec^T B)^{(x)2} D^{(x)4} phi_Sigma (Eq. 30) ----
+static int add_eta02(ReqSet& rs, kdefft_ds ds, const Mat& B, const Mat& Sg, int& first) {
+    const int d = ds->d;
+    KSpec sp;
+    sp.nsig = 1;
+    sp.sig[0] = Sg;
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    KCHK(plan_for(ds, Sg, L, P));
+    first = (int)rs.grids.size();
+    std::map<std::vector<int>, double> w;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b)
+            for (int c = 0; c < d; ++c)
+                for (int e = 0; e < d; ++e) {
+                    std::vector<int> al(MAXD, 0);
+                    al[a]++;
+                    al[b]++;
+                    al[c]++;
+                    al[e]++;
+                    w[al] += B(a, b) * B(c, e);
+                }
+    GridReq g;
+    g.ds = ds;
+    g.spec = si;
+    std::memcpy(g.L, L, sizeof(L));
+    std::memcpy(g.P, P, sizeof(P));
+    for (auto& kv : w) {
+        if (kv.second == 0.0) continue;
+        Term t{0, {0}, kv.second};
+        for (int k = 0; k < MAXD; ++k) t.alpha[k] = kv.first[k];
+        g.terms.push_back(t);
+    }
+    rs.grids.push_back(std::move(g));
+    return KDEFFT_OK;
+}
+
+// ============================================================ execution
+static size_t spec_elems(int d, const int* P) {
+    size_t q = (size_t)(P[d - 1] / 2 + 1);
+    for (int k = 0; k < d - 1; ++k) q *= (size_t)P[k];
+    return q;
+}
+
+template <typename real>
+static int fill_axes(kdefft_ctx c, int d, const int* P, Item<real>& it) {
+    for (int k = 0; k < d; ++k) {
+        if (!radix_plan(P[k], it.ax[k])) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
+        it.ax[k].tw_off = twiddle_offset(c, P[k]);
+    }
+    return KDEFFT_OK;
+}
+
+// Tiles and scratch of one item; appends to the per-pass tile lists.
+struct PassLists {
+    std::vector<Tile> A, mid[MAXD], F;
+    int capA = 0, capM[MAXD] = {0}, capF = 0;
+    int pA = 0, pM[MAXD] = {0}, pF = 0;
+    long long scratch = 0;
+};
+
+// complex scratch elements an item needs (both ping-pong regions)
+template <typename real>
+static long long scratch_need(const Item<real>& it) {
+    const int d = it.d;
+    long long linesA = 1;
+    for (int k = 0; k < d - 1; ++k) linesA *= it.S[k];
+    long long sz[2] = {(d >= 2) ? (long long)(it.ax[d - 1].P / 2 + 1) * linesA : 0, 0};
+    long long Wo = it.ax[d - 1].P / 2 + 1;
+    int wsel = 0;
+    for (int k = d - 2; k >= 1; --k) {
+        long long O = 1;
+        for (int m = 0; m < k; ++m) O *= it.S[m];
+        Wo *= it.ax[k].P;
+        wsel ^= 1;
+        sz[wsel] = std::max(sz[wsel], Wo * O);
+    }
+    return sz[0] + sz[1];
+}
+
+template <typename real>
+static void tile_item(Item<real>& it, int idx, int cap, PassLists& pl) {
+    const int d = it.d;
+    const int Pl = it.ax[d - 1].P;
+    const int Ql = Pl / 2 + 1;
+    long long linesA = 1;
+    for (int k = 0; k < d - 1; ++k) linesA *= it.S[k];
+    // stage A
+    {
+        const int nl = std::max(1, std::min<int>(cap / Pl, (int)linesA));
+        for (long long l0 = 0; l0 < linesA; l0 += nl) {
+            const int n = (int)std::min<long long>(nl, linesA - l0);
+            pl.A.push_back(Tile{idx, (int)l0, 0, n});
+            pl.capA = std::max(pl.capA, n * Pl);
+        }
+        pl.pA = std::max(pl.pA, Pl);
+    }
+    // scratch sizes (two ping-pong regions)
+    long long sz[2] = {0, 0};
+    long long cur = (d >= 2) ? (long long)Ql * linesA : 0;
+    sz[0] = cur;
+    int wsel = 0;
+    long long Wo = Ql;   // transformed outer extent
+    for (int k = d - 2; k >= 1; --k) {
+        long long O = 1;
+        for (int m = 0; m < k; ++m) O *= it.S[m];
+        const int Pk = it.ax[k].P;
+        const int nl = std::max(1, std::min<int>(cap / Pk, (int)O));
+        for (long long wo = 0; wo < Wo; ++wo)
+            for (long long o0 = 0; o0 < O; o0 += nl) {
+                const int n = (int)std::min<long long>(nl, O - o0);
+                pl.mid[k].push_back(Tile{idx, (int)wo, (int)o0, n});
+                pl.capM[k] = std::max(pl.capM[k], n * Pk);
+            }
+        pl.pM[k] = std::max(pl.pM[k], Pk);
+        Wo *= Pk;
+        wsel ^= 1;
+        sz[wsel] = std::max(sz[wsel], Wo * O);
+    }
+    it.scr[0] = pl.scratch;
+    it.scr[1] = pl.scratch + sz[0];
+    pl.scratch += sz[0] + sz[1];
+    // final pass over q in [0, Wo)
+    if (d >= 2) {
+        const int P0 = it.ax[0].P;
+        const int nl = std::max(1, std::min<int>(cap / P0, (int)Wo));
+        it.tileF0 = (int)pl.F.size();
+        int cnt = 0;
+        for (long long q0 = 0; q0 < Wo; q0 += nl) {
+            const int n = (int)std::min<long long>(nl, Wo - q0);
+            pl.F.push_back(Tile{idx, (int)q0, 0, n});
+            pl.capF = std::max(pl.capF, n * P0);
+            ++cnt;
+        }
+        it.ntileF = cnt;
+        pl.pF = std::max(pl.pF, P0);
+    }
+}
+
+template <typename real>
+static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists& pl, int d, double* out_host) {
+    using C = typename Cpx<real>::T;
+    const int nitems = (int)items.size();
+    if (nitems == 0) return KDEFFT_OK;
+    KCHK(sync_twiddles(c));
+    // d = 1: the single stage-A tile of each item owns partial slot tileF0
+    if (d == 1) {
+        for (int i = 0; i < nitems; ++i) {
+            items[i].tileF0 = i;
+            items[i].ntileF = 1;
+        }
+    }
+    const size_t nF = (d == 1) ? (size_t)nitems : pl.F.size();
+    // upload items + tiles in one copy
+    const size_t bItems = sizeof(Item<real>) * nitems;
+    const size_t nt = pl.A.size() + pl.F.size() + [&] {
+        size_t s = 0;
+        for (int k = 0; k < MAXD; ++k) s += pl.mid[k].size();
+        return s;
+    }();
+    const size_t bTiles = sizeof(Tile) * nt;
+    const size_t bytes = bItems + bTiles;
+    KCHK(c->h_items.ensure(bytes));
+    KCHK(c->items.ensure(bytes));
+    // the pinned staging buffer may still be read by a previous copy
+    KCU(cudaStreamSynchronize(c->stream));
+    unsigned char* h = (unsigned char*)c->h_items.p;
+    std::memcpy(h, items.data(), bItems);
+    size_t o = bItems;
+    auto put = [&](const std::vector<Tile>& v) {
+        const size_t first = (o - bItems) / sizeof(Tile);
+        if (!v.empty()) std::memcpy(h + o, v.data(), sizeof(Tile) * v.size());
+        o += sizeof(Tile) * v.size();
+        return first;
+    };
+    const size_t offA = put(pl.A);
+    size_t offM[MAXD];
+    for (int k = 0; k < MAXD; ++k) offM[k] = put(pl.mid[k]);
+    const size_t offF = put(pl.F);
+    KCU(cudaMemcpyAsync(c->items.p, h, bytes, cudaMemcpyHostToDevice, c->stream));
+    const Item<real>* dItems = (const Item<real>*)c->items.p;
+    const Tile* dTiles = (const Tile*)((unsigned char*)c->items.p + bItems);
+    KCHK(c->scratch.ensure(sizeof(C) * (size_t)std::max<long long>(pl.scratch, 1)));
+    KCHK(c->partial.ensure(sizeof(double) * 2 * std::max<size_t>(nF, 1)));
+    KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
+    C* scr = (C*)c->scratch.p;
+    const C* tw = (const C*)(sizeof(real) == 4 ? c->tw32.p : c->tw64.p);
+    double* part = (double*)c->partial.p;
+    auto grid_of = [&](size_t ntiles) { return (int)std::min<size_t>(ntiles, (size_t)c->nsm * 4); };
+    // algorithmic bytes and FFT flops (5 P log2 P per line) of each pass
+    const double cs = (double)sizeof(C), rsz = (double)sizeof(real);
+    auto fft_flops = [](double P) { return 5.0 * P * std::log2(P); };
+    double bA = 0, fA = 0, bF = 0, fF = 0, bM[MAXD] = {0}, fM[MAXD] = {0};
+    for (const Tile& t : pl.A) {
+        const Item<real>& it = items[t.item];
+        const double P = it.ax[d - 1].P, Q = std::floor(P / 2) + 1;
+        fA += t.n * fft_flops(P);
+        if (it.kind == 1) bA += t.n * it.S[d - 1] * rsz;            // counts read
+        bA += (d == 1) ? Q * rsz : t.n * Q * cs;                      // spectrum read / half lines written
+    }
+    for (int k = 1; k <= d - 2; ++k)
+        for (const Tile& t : pl.mid[k]) {
+            const Item<real>& it = items[t.item];
+            const double P = it.ax[k].P;
+            fM[k] += t.n * fft_flops(P);
+            bM[k] += t.n * (it.S[k] + P) * cs;
+        }
+    for (const Tile& t : pl.F) {
+        const Item<real>& it = items[t.item];
+        const double P = it.ax[0].P;
+        fF += t.n * (fft_flops(P) + 4.0 * P);
+        bF += t.n * (it.S[0] * cs + P * rsz);
+    }
+    cudaEvent_t ev;
+    if (!pl.A.empty()) {
+        ev = prof_start(c);
+        KCU(launch_stage_a<real>(dItems, dTiles + offA, (int)pl.A.size(), pl.pA, pl.capA, scr, tw, part,
+                                 grid_of(pl.A.size()), c->stream));
+        prof_stop(c, ev, sizeof(real) == 4 ? "stage_a_f32" : "stage_a_f64", bA, fA);
+    }
+    for (int k = d - 2; k >= 1; --k)
+        if (!pl.mid[k].empty()) {
+            ev = prof_start(c);
+            KCU(launch_mid<real>(dItems, dTiles + offM[k], (int)pl.mid[k].size(), k, pl.pM[k], pl.capM[k], scr,
+                                 tw, grid_of(pl.mid[k].size()), c->stream));
+            prof_stop(c, ev, sizeof(real) == 4 ? "mid_f32" : "mid_f64", bM[k], fM[k]);
+        }
+    if (d >= 2 && !pl.F.empty()) {
+        ev = prof_start(c);
+        KCU(launch_final<real>(dItems, dTiles + offF, (int)pl.F.size(), pl.pF, pl.capF, scr, tw, part,
+                               grid_of(pl.F.size()), c->stream));
+        prof_stop(c, ev, sizeof(real) == 4 ? "final_f32" : "final_f64", bF, fF);
+    }
+    c->h2d += (int64_t)bytes;
+    if (out_host) {
+        ev = prof_start(c);
+        KCU(launch_reduce<real>(dItems, nitems, part, (double*)c->out.p, c->stream));
+        prof_stop(c, ev, "reduce", 16.0 * nF, 2.0 * nF);
+        KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
+        KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+        KCU(cudaStreamSynchronize(c->stream));
+        c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
+        std::memcpy(out_host, c->h_out.p, sizeof(double) * 2 * nitems);
+    } else {
+        KCU(cudaStreamSynchronize(c->stream));
+    }
+    prof_flush(c);
+    return KDEFFT_OK;
+}
+
+static int cap_elems(bool dbl) { return dbl ? 3072 : 6144; }
+
+// |F(c_zp)|^2 at padded sizes P (computed once per dataset and P)
+template <typename real>
+static int ensure_spectrum(kdefft_ds ds, const int* P, const real** out) {
+    std::vector<int> key(P, P + ds->d);
+    auto it = ds->spectra.find(key);
+    if (it != ds->spectra.end()) {
+        *out = (const real*)it->second->p;
+        return KDEFFT_OK;
+    }
+    auto buf = std::make_shared<DevBuf>();
+    KCHK(buf->ensure(sizeof(real) * spec_elems(ds->d, P)));
+    kdefft_ctx c = ds->ctx;
+    Item<real> item;
+    std::memset(&item, 0, sizeof(item));
+    item.d = ds->d;
+    item.kind = 1;
+    KCHK(fill_axes(c, ds->d, P, item));
+    for (int k = 0; k < ds->d; ++k) {
+        item.S[k] = (int)ds->M[k];
+        item.off[k] = 0;
+    }
+    item.counts = (const real*)ds->counts.p;
+    item.spec_out = (real*)buf->p;
+    std::vector<Item<real>> items{item};
+    PassLists pl;
+    tile_item(items[0], 0, cap_elems(sizeof(real) == 8), pl);
+    KCHK(launch_items<real>(c, items, pl, ds->d, nullptr));
+    ds->spectra[key] = buf;
+    *out = (const real*)buf->p;
+    return KDEFFT_OK;
+}
+
+// Evaluate every grid of rs (value = Eq. 25 for that lag kernel).
+template <typename real>
+static int run_requests(kdefft_ctx c, ReqSet& rs) {
+    if (rs.grids.empty()) return KDEFFT_OK;
+    const int d = rs.grids[0].ds->d;
+    HermiteIndex& hx = hindex();
+    // pair consecutive grids that share dataset, covariances and plan
+    std::vector<std::pair<int, int>> pairs;
+    for (size_t i = 0; i < rs.grids.size();) {
+        const GridReq& a = rs.grids[i];
+        if (i + 1 < rs.grids.size()) {
+            const GridReq& b = rs.grids[i + 1];
+            if (b.ds == a.ds && b.spec == a.spec && std::memcmp(a.L, b.L, sizeof(a.L)) == 0 &&
+                std::memcmp(a.P, b.P, sizeof(a.P)) == 0) {
+                pairs.push_back({(int)i, (int)i + 1});
+                i += 2;
+                continue;
+            }
+        }
+        pairs.push_back({(int)i, -1});
+        i += 1;
+    }
+    const int cap = cap_elems(sizeof(real) == 8);
+    // scratch budget per launch: split the items into batches
+    const long long budget = 1LL << 28;   // complex elements (2 GiB at FP32)
+    size_t pi = 0;
+    while (pi < pairs.size()) {
+        std::vector<Item<real>> items;
+        PassLists pl;
+        std::vector<std::pair<int, int>> batch;
+        while (pi < pairs.size()) {
+            const auto pr = pairs[pi];
+            const GridReq& g = rs.grids[pr.first];
+            const KSpec& sp = rs.specs[g.spec];
+            Item<real> it;
+            std::memset(&it, 0, sizeof(it));
+            it.d = d;
+            it.kind = 0;
+            KCHK(fill_axes(c, d, g.P, it));
+            long long ptot = 1;
+            for (int k = 0; k < d; ++k) {
+                it.S[k] = 2 * g.L[k] + 1;
+                it.off[k] = g.L[k];
+                it.delta[k] = (real)g.ds->delta[k];
+                ptot *= g.P[k];
+            }
+            it.nsig = sp.nsig;
+            for (int s = 0; s < sp.nsig; ++s) {
+                Mat inv;
+                double det;
+                if (!spd_inv_det(sp.sig[s], inv, det))
+                    return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)inv(a, b);
+                it.nrm[s] = (real)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
+            }
+            int R = 0;
+            const int gi[2] = {pr.first, pr.second};
+            for (int h = 0; h < 2; ++h) {
+                if (gi[h] < 0) {
+                    it.nterm[h] = 0;
+                    continue;
+                }
+                const std::vector<Term>& tl = rs.grids[gi[h]].terms;
+                if ((int)tl.size() > MAXTERM) return fail(KDEFFT_ERR_UNSUPPORTED, "too many kernel terms");
+                it.nterm[h] = (int)tl.size();
+                for (size_t m = 0; m < tl.size(); ++m) {
+                    int o = 0;
+                    for (int k = 0; k < d; ++k) o += tl[m].alpha[k];
+                    if (o > kRmax[d]) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high for d");
+                    R = std::max(R, o);
+                    const int hidx = hx.idx(d, tl[m].alpha);
+                    it.tsig[h][m] = (short)tl[m].sig;
+                    it.the[h][m] = (short)hidx;
+                    it.tw8[h][m] = (real)(((o & 1) ? -1.0 : 1.0) * tl[m].w);
+                }
+            }
+            it.R = R;
+            const real* spec = nullptr;
+            KCHK(ensure_spectrum<real>(g.ds, g.P, &spec));
+            it.spec = spec;
+            const double nn = (double)g.ds->n;
+            it.scale = 1.0 / (nn * nn * (double)ptot);
+            // would this item overflow the scratch budget?
+            if (!items.empty() && pl.scratch + scratch_need(it) > budget) break;
+            tile_item(it, (int)items.size(), cap, pl);
+            items.push_back(it);
+            batch.push_back(pr);
+            ++pi;
+        }
+        std::vector<double> out(2 * items.size());
+        KCHK(launch_items<real>(c, items, pl, d, out.data()));
+        for (size_t i = 0; i < batch.size(); ++i) {
+            rs.grids[batch[i].first].value = out[2 * i];
+            if (batch[i].second >= 0) rs.grids[batch[i].second].value = out[2 * i + 1];
+        }
+    }
+    return KDEFFT_OK;
+}
+
+static int run(kdefft_ctx c, ReqSet& rs) {
+    if (rs.grids.empty()) return KDEFFT_OK;
+    if (rs.grids[0].ds->opts.precision == KDEFFT_FP64) return run_requests<double>(c, rs);
+    return run_requests<float>(c, rs);
+}
+
+// ============================================================ objective assembly
+static void assemble_lscv(kdefft_ds ds, const Mat& H, const GridReq* g, double* val, double* grad) {
+    const int d = ds->d;
+    const double n = (double)ds->n;
+    Mat inv;
+    double det;
+    spd_inv_det(H, inv, det);
+    const double k0 = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
+    int gi = 0;
+    double c0;
+    if (!ds->opts.exact_loo) {
+        *val = g[0].value + 2.0 * k0 / n;
+        gi = 1;
+        c0 = 2.0 / n;
+    } else {
+        *val = g[0].value - 2.0 * n / (n - 1.0) * g[1].value + 2.0 / (n - 1.0) * k0;
+        gi = 2;
+        c0 = 2.0 / (n - 1.0);
+    }
+    if (grad) {
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) {
+                const double tie = (a == b) ? 1.0 : 2.0;
+                const double v = g[gi++].value + c0 * tie * (-0.5 * k0 * inv(a, b));
+                grad[a * d + b] = grad[b * d + a] = v;
+            }
+    }
+}
+
+static void assemble_scv(kdefft_ds ds, const Mat& H, const GridReq* g, double* val, double* grad) {
+    const int d = ds->d;
+    const double n = (double)ds->n;
+    Mat inv;
+    double det;
+    spd_inv_det(H, inv, det);
+    const double r0 = std::pow(4.0 * M_PI, -0.5 * d) / std::sqrt(det);
+    *val = r0 / n + g[0].value;
+    if (grad) {
+        int gi = 1;
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) {
+                const double tie = (a == b) ? 1.0 : 2.0;
+                const double v = g[gi++].value + tie * (-0.5 * r0 * inv(a, b)) / n;
+                grad[a * d + b] = grad[b * d + a] = v;
+            }
+    }
+}
+
+// psi_4 unique values -> Kronecker vector (Sec. 5 ordering)
+static void kron_expand(int d, int r, const std::vector<MultiIndex>& alphas, const GridReq* g, double* out) {
+    std::map<std::vector<int>, double> val;
+    for (size_t i = 0; i < alphas.size(); ++i) val[std::vector<int>(alphas[i].a, alphas[i].a + d)] = g[i].value;
+    long long total = 1;
+    for (int i = 0; i < r; ++i) total *= d;
+    for (long long pos = 0; pos < total; ++pos) {
+        std::vector<int> al(d, 0);
+        long long p = pos;
+        for (int i = 0; i < r; ++i) {
+            al[p % d]++;
+            p /= d;
+        }
+        out[pos] = val[al];
+    }
+}
+
+static void assemble_pi(kdefft_ds ds, const Mat& H, const double* psi4, double* val, double* grad) {
+    const int d = ds->d;
+    const double n = (double)ds->n;
+    Mat inv;
+    double det;
+    spd_inv_det(H, inv, det);
+    const double r0 = std::pow(4.0 * M_PI, -0.5 * d) / std::sqrt(det);
+    auto T = [&](int a, int b, int c, int e) { return psi4[((a * d + b) * d + c) * d + e]; };
+    double quad = 0.0;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b)
+            for (int c = 0; c < d; ++c)
+                for (int e = 0; e < d; ++e) quad += H(a, b) * H(c, e) * T(a, b, c, e);
+    *val = r0 / n + 0.25 * quad;
+    if (grad) {
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) {
+                double half = 0.0;
+                for (int c = 0; c < d; ++c)
+                    for (int e = 0; e < d; ++e) half += H(c, e) * T(a, b, c, e);
+                half *= 0.5;
+                const double tie = (a == b) ? 1.0 : 2.0;
+                const double v = tie * (half - 0.5 * r0 * inv(a, b) / n);
+                grad[a * d + b] = grad[b * d + a] = v;
+            }
+    }
+}
+
+static int write_out(kdefft_ctx c, double* dst, const double* src, size_t count) {
+    if (!dst || count == 0) return KDEFFT_OK;
+    if (is_device_ptr(dst)) {
+        c->h2d += (int64_t)(sizeof(double) * count);
+        KCU(cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+        KCU(cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(dst, src, sizeof(double) * count);
+    }
+    return KDEFFT_OK;
+}
+
+// ============================================================ C ABI
+extern "C" {
+
+int kdefft_opts_default(kdefft_opts* o) {
+    if (!o) return fail(KDEFFT_ERR_ARG, "opts is NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->tau = 3.7;
+    o->L_basis = KDEFFT_L_AUTO;
+    o->P_rule = KDEFFT_P_MINIMAL;
+    o->exact_loo = 0;
+    o->precision = KDEFFT_FP32;
+    o->binning = KDEFFT_BIN_LINEAR;
+    o->outside_policy = KDEFFT_OUTSIDE_ERROR;
+    return KDEFFT_OK;
+}
+
+const char* kdefft_strerror(int code) {
+    switch (code) {
+        case KDEFFT_OK: return "ok";
+        case KDEFFT_ERR_ARG: return "invalid argument";
+        case KDEFFT_ERR_NOT_SPD: return "matrix not symmetric positive definite";
+        case KDEFFT_ERR_OUTSIDE_GRID: return "sample point outside the grid";
+        case KDEFFT_ERR_CUDA: return "CUDA error";
+        case KDEFFT_ERR_ALLOC: return "allocation failed";
+        case KDEFFT_ERR_TIMEOUT: return "device wait timed out";
+        case KDEFFT_ERR_UNSUPPORTED: return "unsupported size";
+        default: return "unknown error";
+    }
+}
+
+const char* kdefft_last_error(void) { return g_err.c_str(); }
+
+int kdefft_create(kdefft_ctx* out, int device, void* stream) {
+    if (!out) return fail(KDEFFT_ERR_ARG, "ctx is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    KCU(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(KDEFFT_ERR_ARG, "no such CUDA device");
+    KCU(cudaSetDevice(device));
+    auto c = new kdefft_ctx_s();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return fail(KDEFFT_ERR_CUDA, "cudaGetDeviceProperties failed");
+    }
+    c->nsm = prop.multiProcessorCount;
+    int r = upload_tables();
+    if (r != KDEFFT_OK) {
+        delete c;
+        return r;
+    }
+    *out = c;
+    return KDEFFT_OK;
+}
+
+int kdefft_profile(kdefft_ctx c, int mode) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    if (mode == 1 || mode == 0) {
+        c->kstat.clear();
+        c->launches = c->h2d = c->d2h = 0;
+    }
+    c->prof = (mode != 0);
+    return KDEFFT_OK;
+}
+
+int kdefft_profile_read(kdefft_ctx c, kdefft_kstat* out, int cap, int* count, int64_t* launches, int64_t* h2d_bytes,
+                        int64_t* d2h_bytes) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    int i = 0;
+    for (auto& kv : c->kstat) {
+        if (out && i < cap) {
+            std::memset(&out[i], 0, sizeof(out[i]));
+            std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = kv.second.launches;
+            out[i].ms = kv.second.ms;
+            out[i].bytes = kv.second.bytes;
+            out[i].flops = kv.second.flops;
+        }
+        ++i;
+    }
+    if (count) *count = i;
+    if (launches) *launches = c->launches;
+    if (h2d_bytes) *h2d_bytes = c->h2d;
+    if (d2h_bytes) *d2h_bytes = c->d2h;
+    return KDEFFT_OK;
+}
+
+int kdefft_destroy(kdefft_ctx c) {
+    if (!c) return KDEFFT_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->tw32.release();
+    c->tw64.release();
+    c->scratch.release();
+    c->partial.release();
+    c->items.release();
+    c->tiles.release();
+    c->out.release();
+    c->h_items.release();
+    c->h_out.release();
+    for (auto& p : c->pending) {
+        c->evpool.push_back(p.a);
+        c->evpool.push_back(p.b);
+    }
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    delete c;
+    return KDEFFT_OK;
+}
+
+int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo, const double* hi,
+               const int64_t* M, const kdefft_opts* opts, kdefft_ds* out) {
+    if (!c || !out || !lo || !hi || !M) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (d < 1 || d > 4) return fail(KDEFFT_ERR_ARG, "d must be 1..4");
+    if (n < 1 || (!X)) return fail(KDEFFT_ERR_ARG, "need n >= 1 samples");
+    kdefft_opts o;
+    if (opts)
+        o = *opts;
+    else
+        kdefft_opts_default(&o);
+    if (!(o.tau > 0.0)) return fail(KDEFFT_ERR_ARG, "tau must be positive");
+    KCU(cudaSetDevice(c->device));
+    std::unique_ptr<kdefft_ds_s> ds(new kdefft_ds_s());
+    ds->ctx = c;
+    ds->d = d;
+    ds->n = n;
+    ds->opts = o;
+    GridDesc g;
+    std::memset(&g, 0, sizeof(g));
+    g.d = d;
+    ds->ncells = 1;
+    for (int k = 0; k < d; ++k) {
+        if (M[k] < 2 || M[k] > (1 << 20)) return fail(KDEFFT_ERR_ARG, "M_k must be in [2, 2^20]");
+        if (!(hi[k] > lo[k]) || !std::isfinite(lo[k]) || !std::isfinite(hi[k]))
+            return fail(KDEFFT_ERR_ARG, "need lo_k < hi_k, finite");
+        ds->lo[k] = lo[k];
+        ds->hi[k] = hi[k];
+        ds->M[k] = M[k];
+        ds->delta[k] = (hi[k] - lo[k]) / (double)(M[k] - 1);   // Eq. 16
+        g.lo[k] = ds->lo[k];
+        g.hi[k] = ds->hi[k];
+        g.delta[k] = ds->delta[k];
+        g.M[k] = M[k];
+        ds->ncells *= M[k];
+    }
+    if (ds->ncells > (1LL << 31)) return fail(KDEFFT_ERR_UNSUPPORTED, "grid too large");
+    // sample on the device
+    DevBuf xbuf;
+    const double* dX = X;
+    if (!is_device_ptr(X)) {
+        KCHK(xbuf.ensure(sizeof(double) * n * d));
+        KCU(cudaMemcpyAsync(xbuf.p, X, sizeof(double) * n * d, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)(sizeof(double) * n * d);
+        dX = (const double*)xbuf.p;
+    }
+    DevBuf misc;   // outside counter + moments
+    KCHK(misc.ensure(sizeof(double) * 64));
+    KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 64, c->stream));
+    unsigned long long* dOut = (unsigned long long*)misc.p;
+    double* dMean = (double*)misc.p + 8;
+    double* dCov = (double*)misc.p + 16;
+    const bool dbl = o.precision == KDEFFT_FP64;
+    KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));
+    KCU(cudaMemsetAsync(ds->counts.p, 0, (dbl ? 8 : 4) * (size_t)ds->ncells, c->stream));
+    cudaEvent_t evb = prof_start(c);
+    if (o.binning == KDEFFT_BIN_SIMPLE) {
+        c->launches++;   // the integer-to-real conversion
+        KCHK(ds->counts_i.ensure(4 * (size_t)ds->ncells));
+        KCU(cudaMemsetAsync(ds->counts_i.p, 0, 4 * (size_t)ds->ncells, c->stream));
+        KCU(launch_bin_simple(dX, n, g, (int*)ds->counts_i.p, ds->ncells, dOut, c->nsm, c->stream));
+        if (dbl)
+            KCU(launch_int_to_real<double>((int*)ds->counts_i.p, (double*)ds->counts.p, ds->ncells, c->stream));
+        else
+            KCU(launch_int_to_real<float>((int*)ds->counts_i.p, (float*)ds->counts.p, ds->ncells, c->stream));
+    } else if (dbl) {
+        KCU(launch_bin_linear<double>(dX, n, g, (double*)ds->counts.p, ds->ncells, dOut, c->nsm, c->stream));
+    } else {
+        KCU(launch_bin_linear<float>(dX, n, g, (float*)ds->counts.p, ds->ncells, dOut, c->nsm, c->stream));
+    }
+    prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
+    // moments for the normal-scale start point
+    c->launches += 2;
+    KCU(launch_moments(dX, n, d, 0, nullptr, dMean, c->nsm, c->stream));
+    double hm[8];
+    KCU(cudaMemcpyAsync(hm, dMean, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < d; ++k) hm[k] /= (double)n;
+    KCU(cudaMemcpyAsync(dMean, hm, sizeof(double) * 8, cudaMemcpyHostToDevice, c->stream));
+    KCU(launch_moments(dX, n, d, 1, dMean, dCov, c->nsm, c->stream));
+    unsigned long long nout = 0;
+    double hc[16];
+    KCU(cudaMemcpyAsync(&nout, dOut, sizeof(nout), cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaMemcpyAsync(hc, dCov, sizeof(double) * 16, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    for (int i = 0; i < d * d; ++i) ds->cov[i] = (n > 1) ? hc[i] / (double)(n - 1) : 0.0;
+    if (nout > 0 && o.outside_policy == KDEFFT_OUTSIDE_ERROR)
+        return fail(KDEFFT_ERR_OUTSIDE_GRID, std::to_string(nout) + " sample points outside the grid");
+    ds->dropped = (int64_t)nout;
+    xbuf.release();
+    misc.release();
+    *out = ds.release();
+    return KDEFFT_OK;
+}
+
+int kdefft_ds_destroy(kdefft_ds ds) {
+    if (!ds) return KDEFFT_OK;
+    cudaSetDevice(ds->ctx->device);
+    cudaStreamSynchronize(ds->ctx->stream);
+    ds->counts.release();
+    ds->counts_i.release();
+    for (auto& kv : ds->spectra) kv.second->release();
+    delete ds;
+    return KDEFFT_OK;
+}
+
+int kdefft_ds_set_opts(kdefft_ds ds, const kdefft_opts* o) {
+    if (!ds || !o) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    if (!(o->tau > 0.0)) return fail(KDEFFT_ERR_ARG, "tau must be positive");
+    ds->opts.tau = o->tau;
+    ds->opts.L_basis = o->L_basis;
+    ds->opts.P_rule = o->P_rule;
+    std::memcpy(ds->opts.P_fixed, o->P_fixed, sizeof(o->P_fixed));
+    ds->opts.exact_loo = o->exact_loo;
+    return KDEFFT_OK;
+}
+
+int kdefft_ds_info(kdefft_ds ds, int64_t* n, int* d, int64_t* dropped) {
+    if (!ds) return fail(KDEFFT_ERR_ARG, "NULL dataset");
+    if (n) *n = ds->n;
+    if (d) *d = ds->d;
+    if (dropped) *dropped = ds->dropped;
+    return KDEFFT_OK;
+}
+
+int kdefft_counts(kdefft_ds ds, void* dst, int dtype) {
+    if (!ds || !dst) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    kdefft_ctx c = ds->ctx;
+    KCU(cudaSetDevice(c->device));
+    const size_t nc = (size_t)ds->ncells;
+    const bool dbl = ds->opts.precision == KDEFFT_FP64;
+    if (dtype == KDEFFT_DT_I32) {
+        if (ds->opts.binning != KDEFFT_BIN_SIMPLE) return fail(KDEFFT_ERR_ARG, "integer counts need SIMPLE binning");
+        KCU(cudaMemcpyAsync(dst, ds->counts_i.p, 4 * nc, cudaMemcpyDefault, c->stream));
+    } else if ((dtype == KDEFFT_DT_F64) == dbl && (dtype == KDEFFT_DT_F32 || dtype == KDEFFT_DT_F64)) {
+        KCU(cudaMemcpyAsync(dst, ds->counts.p, (dbl ? 8 : 4) * nc, cudaMemcpyDefault, c->stream));
+    } else if (dtype == KDEFFT_DT_F32 || dtype == KDEFFT_DT_F64) {
+        // convert on the host
+        std::vector<unsigned char> tmp((dbl ? 8 : 4) * nc);
+        KCU(cudaMemcpyAsync(tmp.data(), ds->counts.p, tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+        KCU(cudaStreamSynchronize(c->stream));
+        std::vector<unsigned char> conv((dtype == KDEFFT_DT_F64 ? 8 : 4) * nc);
+        for (size_t i = 0; i < nc; ++i) {
+            const double v = dbl ? ((double*)tmp.data())[i] : (double)((float*)tmp.data())[i];
+            if (dtype == KDEFFT_DT_F64)
+                ((double*)conv.data())[i] = v;
+            else
+                ((float*)conv.data())[i] = (float)v;
+        }
+        KCU(cudaMemcpyAsync(dst, conv.data(), conv.size(), cudaMemcpyDefault, c->stream));
+    } else {
+        return fail(KDEFFT_ERR_ARG, "unknown dtype");
+    }
+    KCU(cudaStreamSynchronize(c->stream));
+    return KDEFFT_OK;
+}
+
+int kdefft_plan(kdefft_ds ds, int method, const double* H, const double* G, int* L_out, int* P_out) {
+    if (!ds || !H || !L_out || !P_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    const int d = ds->d;
+    Mat Hm, Gm;
+    KCHK(sym_check(H, d, Hm, "H"));
+    KCHK(spd_or_fail(Hm, "H"));
+    Mat basis = Hm;
+    if (method == KDEFFT_LSCV) {
+        if (ds->opts.L_basis == KDEFFT_L_WIDEST) basis = scaled(2.0, Hm);
+    } else if (method == KDEFFT_SCV) {
+        if (!G) return fail(KDEFFT_ERR_ARG, "SCV needs G");
+        KCHK(sym_check(G, d, Gm, "G"));
+        if (ds->opts.L_basis != KDEFFT_L_PAPER) basis = lin(2.0, Hm, 2.0, Gm);
+    } else if (method == KDEFFT_PI) {
+        if (!G) return fail(KDEFFT_ERR_ARG, "PI needs G");
+        KCHK(sym_check(G, d, Gm, "G"));
+        basis = Gm;
+    }
+    return plan_for(ds, basis, L_out, P_out);
+}
+
+static int check_common(kdefft_ds ds, const double* H, int nH) {
+    if (!ds || !H) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    if (nH < 1) return fail(KDEFFT_ERR_ARG, "nH must be >= 1");
+    if (cudaSetDevice(ds->ctx->device) != cudaSuccess) return fail(KDEFFT_ERR_CUDA, "cudaSetDevice failed");
+    return KDEFFT_OK;
+}
+
+int kdefft_psi(kdefft_ds ds, const double* H, int nH, int r, double* out) {
+    KCHK(check_common(ds, H, nH));
+    if (!out) return fail(KDEFFT_ERR_ARG, "NULL output");
+    const int d = ds->d;
+    if (r < 0 || (r & 1) || r > kRmax[d]) return fail(KDEFFT_ERR_ARG, "r must be even and within the order limit");
+    ReqSet rs;
+    std::vector<int> first(nH);
+    std::vector<MultiIndex> alphas;
+    for (int h = 0; h < nH; ++h) {
+        Mat Hm;
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hm, "H"));
+        KCHK(spd_or_fail(Hm, "H"));
+        KCHK(add_psi(rs, ds, Hm, r, first[h], alphas));
+    }
+    KCHK(run(ds->ctx, rs));
+    long long len = 1;
+    for (int i = 0; i < r; ++i) len *= d;
+    std::vector<double> res((size_t)len * nH);
+    for (int h = 0; h < nH; ++h) kron_expand(d, r, alphas, &rs.grids[first[h]], res.data() + (size_t)h * len);
+    return write_out(ds->ctx, out, res.data(), res.size());
+}
+
+static int eval_lscv(kdefft_ds ds, const double* H, int nH, std::vector<double>& val, std::vector<double>* grad) {
+    const int d = ds->d;
+    ReqSet rs;
+    std::vector<int> first(nH);
+    std::vector<Mat> Hs(nH);
+    for (int h = 0; h < nH; ++h) {
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
+        KCHK(add_lscv(rs, ds, Hs[h], grad != nullptr, first[h]));
+    }
+    KCHK(run(ds->ctx, rs));
+    val.assign(nH, 0.0);
+    if (grad) grad->assign((size_t)nH * d * d, 0.0);
+    for (int h = 0; h < nH; ++h)
+        assemble_lscv(ds, Hs[h], &rs.grids[first[h]], &val[h], grad ? grad->data() + (size_t)h * d * d : nullptr);
+    return KDEFFT_OK;
+}
+
+static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::vector<double>& val,
+                    std::vector<double>* grad) {
+    const int d = ds->d;
+    ReqSet rs;
+    std::vector<int> first(nH);
+    std::vector<Mat> Hs(nH);
+    for (int h = 0; h < nH; ++h) {
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
+        KCHK(add_scv(rs, ds, Hs[h], G, grad != nullptr, first[h]));
+    }
+    KCHK(run(ds->ctx, rs));
+    val.assign(nH, 0.0);
+    if (grad) grad->assign((size_t)nH * d * d, 0.0);
+    for (int h = 0; h < nH; ++h)
+        assemble_scv(ds, Hs[h], &rs.grids[first[h]], &val[h], grad ? grad->data() + (size_t)h * d * d : nullptr);
+    return KDEFFT_OK;
+}
+
+static int psi4_kron(kdefft_ds ds, const Mat& G, std::vector<double>& psi4) {
+    const int d = ds->d;
+    ReqSet rs;
+    int first;
+    std::vector<MultiIndex> alphas;
+    KCHK(spd_or_fail(G, "G"));
+    KCHK(add_psi(rs, ds, G, 4, first, alphas));
+    KCHK(run(ds->ctx, rs));
+    psi4.assign((size_t)d * d * d * d, 0.0);
+    kron_expand(d, 4, alphas, &rs.grids[first], psi4.data());
+    return KDEFFT_OK;
+}
+
+static int eval_pi(kdefft_ds ds, const double* H, int nH, const std::vector<double>& psi4, std::vector<double>& val,
+                   std::vector<double>* grad) {
+    const int d = ds->d;
+    val.assign(nH, 0.0);
+    if (grad) grad->assign((size_t)nH * d * d, 0.0);
+    for (int h = 0; h < nH; ++h) {
+        Mat Hm;
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hm, "H"));
+        KCHK(spd_or_fail(Hm, "H"));
+        assemble_pi(ds, Hm, psi4.data(), &val[h], grad ? grad->data() + (size_t)h * d * d : nullptr);
+    }
+    return KDEFFT_OK;
+}
+
+static int get_G(kdefft_ds ds, const double* G, Mat& Gm) {
+    const int d = ds->d;
+    if (G) {
+        KCHK(sym_check(G, d, Gm, "G"));
+    } else {
+        // normal-scale matrix (4/(d+2))^{2/(d+4)} n^{-2/(d+4)} S
+        const double f = std::pow(4.0 / (d + 2.0), 2.0 / (d + 4.0)) * std::pow((double)ds->n, -2.0 / (d + 4.0));
+        Gm = Mat();
+        Gm.d = d;
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) Gm(a, b) = f * ds->cov[a * d + b];
+    }
+    return spd_or_fail(Gm, "G");
+}
+
+int kdefft_lscv(kdefft_ds ds, const double* H, int nH, double* val, double* grad) {
+    KCHK(check_common(ds, H, nH));
+    if (!val) return fail(KDEFFT_ERR_ARG, "NULL output");
+    std::vector<double> v, g;
+    KCHK(eval_lscv(ds, H, nH, v, grad ? &g : nullptr));
+    KCHK(write_out(ds->ctx, val, v.data(), v.size()));
+    if (grad) KCHK(write_out(ds->ctx, grad, g.data(), g.size()));
+    return KDEFFT_OK;
+}
+
+int kdefft_scv(kdefft_ds ds, const double* H, int nH, const double* G, double* val, double* grad) {
+    KCHK(check_common(ds, H, nH));
+    if (!val || !G) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    Mat Gm;
+    KCHK(get_G(ds, G, Gm));
+    std::vector<double> v, g;
+    KCHK(eval_scv(ds, H, nH, Gm, v, grad ? &g : nullptr));
+    KCHK(write_out(ds->ctx, val, v.data(), v.size()));
+    if (grad) KCHK(write_out(ds->ctx, grad, g.data(), g.size()));
+    return KDEFFT_OK;
+}
+
+int kdefft_pi(kdefft_ds ds, const double* H, int nH, const double* G, double* val, double* grad) {
+    KCHK(check_common(ds, H, nH));
+    if (!val || !G) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    Mat Gm;
+    KCHK(get_G(ds, G, Gm));
+    std::vector<double> psi4, v, g;
+    KCHK(psi4_kron(ds, Gm, psi4));
+    KCHK(eval_pi(ds, H, nH, psi4, v, grad ? &g : nullptr));
+    KCHK(write_out(ds->ctx, val, v.data(), v.size()));
+    if (grad) KCHK(write_out(ds->ctx, grad, g.data(), g.size()));
+    return KDEFFT_OK;
+}
+
+int kdefft_eta02(kdefft_ds ds, const double* H, int nH, const double* G, double* val) {
+    KCHK(check_common(ds, H, nH));
+    if (!val || !G) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    const int d = ds->d;
+    if (kRmax[d] < 4) return fail(KDEFFT_ERR_UNSUPPORTED, "order 4 not available");
+    Mat Gm;
+    KCHK(get_G(ds, G, Gm));
+    ReqSet rs;
+    std::vector<int> first(nH);
+    for (int h = 0; h < nH; ++h) {
+        Mat Hm;
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hm, "H"));
+        KCHK(add_eta02(rs, ds, Hm, Gm, first[h]));
+    }
+    KCHK(run(ds->ctx, rs));
+    std::vector<double> v(nH);
+    for (int h = 0; h < nH; ++h) v[h] = rs.grids[first[h]].value;
+    return write_out(ds->ctx, val, v.data(), v.size());
+}
+
+int kdefft_batch_lscv(kdefft_ctx c, int nds, const kdefft_ds* dss, const int* nH_per_ds, const double* H,
+                      double* val, double* grad) {
+    if (!c || !dss || !nH_per_ds || !H || !val || nds < 1) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    KCU(cudaSetDevice(c->device));
+    const int d = dss[0]->d;
+    const int prec = dss[0]->opts.precision;
+    ReqSet rs;
+    std::vector<int> first;
+    std::vector<Mat> Hs;
+    std::vector<kdefft_ds> owner;
+    size_t off = 0;
+    for (int i = 0; i < nds; ++i) {
+        kdefft_ds ds = dss[i];
+        if (!ds || ds->ctx != c || ds->d != d || ds->opts.precision != prec)
+            return fail(KDEFFT_ERR_ARG, "datasets must share context, d and precision");
+        for (int h = 0; h < nH_per_ds[i]; ++h) {
+            Mat Hm;
+            KCHK(sym_check(H + (off + h) * d * d, d, Hm, "H"));
+            int f;
+            KCHK(add_lscv(rs, ds, Hm, grad != nullptr, f));
+            first.push_back(f);
+            Hs.push_back(Hm);
+            owner.push_back(ds);
+        }
+        off += nH_per_ds[i];
+    }
+    KCHK(run(c, rs));
+    const size_t nt = Hs.size();
+    std::vector<double> v(nt), g(grad ? nt * d * d : 0);
+    for (size_t h = 0; h < nt; ++h)
+        assemble_lscv(owner[h], Hs[h], &rs.grids[first[h]], &v[h], grad ? g.data() + h * d * d : nullptr);
+    std::memcpy(val, v.data(), sizeof(double) * nt);
+    if (grad) std::memcpy(grad, g.data(), sizeof(double) * g.size());
+    return KDEFFT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ optimiser
+// Parametrisation theta: H = R R^T with R lower triangular, R_ii = exp(theta),
+// off-diagonal entries free; row-major over the lower triangle.
+namespace {
+
+struct Opt {
+    int d;
+    int p;
+};
+
+Mat theta_to_H(const Opt& o, const double* th, Mat* Rout = nullptr) {
+    Mat R;
+    R.d = o.d;
+    int t = 0;
+    for (int i = 0; i < o.d; ++i)
+        for (int j = 0; j <= i; ++j) {
+            R(i, j) = (i == j) ? std::exp(th[t]) : th[t];
+            ++t;
+        }
+    Mat H;
+    H.d = o.d;
+    for (int i = 0; i < o.d; ++i)
+        for (int j = 0; j < o.d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k <= std::min(i, j); ++k) s += R(i, k) * R(j, k);
+            H(i, j) = s;
+        }
+    if (Rout) *Rout = R;
+    return H;
+}
+
+void H_to_theta(const Opt& o, const Mat& H, double* th) {
+    Mat R;
+    cholesky(H, R);
+    int t = 0;
+    for (int i = 0; i < o.d; ++i)
+        for (int j = 0; j <= i; ++j) {
+            th[t] = (i == j) ? std::log(R(i, i)) : R(i, j);
+            ++t;
+        }
+}
+
+// tied gradient g (d x d) of F(H) -> gradient in theta
+void grad_theta(const Opt& o, const double* th, const double* g, double* gt) {
+    Mat R;
+    theta_to_H(o, th, &R);
+    const int d = o.d;
+    // independent-entry derivative G_ind: off-diagonals are half the tied values
+    Mat Gi;
+    Gi.d = d;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) Gi(a, b) = (a == b) ? g[a * d + b] : 0.5 * g[a * d + b];
+    // dF/dR = 2 G_ind R
+    int t = 0;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += Gi(i, k) * R(k, j);
+            s *= 2.0;
+            gt[t] = (i == j) ? s * R(i, i) : s;
+            ++t;
+        }
+}
+
+}  // namespace
+
+extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
+                               int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
+    if (!ds || !H_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    if (method != KDEFFT_LSCV && method != KDEFFT_SCV && method != KDEFFT_PI)
+        return fail(KDEFFT_ERR_ARG, "unknown method");
+    if (n_starts < 1) n_starts = 1;
+    if (max_iter < 1) max_iter = 100;
+    KCU(cudaSetDevice(ds->ctx->device));
+    const int d = ds->d;
+    Opt o{d, d * (d + 1) / 2};
+    const int p = o.p;
+    Mat Hstart;
+    if (H0) {
+        KCHK(sym_check(H0, d, Hstart, "H0"));
+    } else {
+        KCHK(get_G(ds, nullptr, Hstart));
+    }
+    KCHK(spd_or_fail(Hstart, "H0"));
+    Mat Gm;
+    if (method != KDEFFT_LSCV) KCHK(get_G(ds, G, Gm));
+    std::vector<double> psi4;
+    if (method == KDEFFT_PI) KCHK(psi4_kron(ds, Gm, psi4));
+    int64_t evals = 0;
+
+    // batched evaluation of value + theta-gradient for a list of theta
+    auto evaluate = [&](const std::vector<std::vector<double>>& ths, std::vector<double>& f,
+                        std::vector<std::vector<double>>& gt) -> int {
+        const int m = (int)ths.size();
+        std::vector<double> Hs((size_t)m * d * d);
+        for (int i = 0; i < m; ++i) {
+            Mat H = theta_to_H(o, ths[i].data());
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) Hs[(size_t)i * d * d + a * d + b] = H(a, b);
+        }
+        std::vector<double> v, g;
+        int r;
+        if (method == KDEFFT_LSCV)
+            r = eval_lscv(ds, Hs.data(), m, v, &g);
+        else if (method == KDEFFT_SCV)
+            r = eval_scv(ds, Hs.data(), m, Gm, v, &g);
+        else
+            r = eval_pi(ds, Hs.data(), m, psi4, v, &g);
+        if (r != KDEFFT_OK) return r;
+        evals += m;
+        f = v;
+        gt.assign(m, std::vector<double>(p));
+        for (int i = 0; i < m; ++i) grad_theta(o, ths[i].data(), g.data() + (size_t)i * d * d, gt[i].data());
+        return KDEFFT_OK;
+    };
+
+    // start points: Hstart, then dilations and plane rotations of it
+    struct State {
+        std::vector<double> th, g, dir, Binv, th_try;
+        double f = 0.0, step = 1.0, slope = 0.0;
+        int iter = 0, ls = 0;
+        bool done = false;
+    };
+    std::vector<State> st(n_starts);
+    for (int s = 0; s < n_starts; ++s) {
+        Mat Hs = Hstart;
+        if (s > 0) {
+            const double fac = std::pow(2.0, ((s % 5) - 2) * 0.5);
+            const double ang = 0.35 * s;
+            const int a = (s - 1) % std::max(1, d - 1), b = (d > 1) ? a + 1 : a;
+            Mat Rt;
+            Rt.d = d;
+            for (int i = 0; i < d; ++i) Rt(i, i) = 1.0;
+            if (d > 1) {
+                Rt(a, a) = std::cos(ang);
+                Rt(b, b) = std::cos(ang);
+                Rt(a, b) = -std::sin(ang);
+                Rt(b, a) = std::sin(ang);
+            }
+            Mat T;
+            T.d = d;
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    double sum = 0.0;
+                    for (int k = 0; k < d; ++k)
+                        for (int l = 0; l < d; ++l) sum += Rt(i, k) * Hstart(k, l) * Rt(j, l);
+                    T(i, j) = fac * sum;
+                }
+            Hs = T;
+        }
+        st[s].th.resize(p);
+        H_to_theta(o, Hs, st[s].th.data());
+        st[s].Binv.assign((size_t)p * p, 0.0);
+        for (int i = 0; i < p; ++i) st[s].Binv[i * p + i] = 1.0;
+    }
+    {
+        std::vector<std::vector<double>> ths;
+        for (auto& s : st) ths.push_back(s.th);
+        std::vector<double> f;
+        std::vector<std::vector<double>> g;
+        KCHK(evaluate(ths, f, g));
+        for (int s = 0; s < n_starts; ++s) {
+            st[s].f = f[s];
+            st[s].g = g[s];
+            // initial inverse-Hessian scale: a unit step moves theta by ~0.1
+            double gn = 0.0;
+            for (double v : g[s]) gn = std::max(gn, std::fabs(v));
+            const double sc = (gn > 0) ? 0.1 / gn : 1.0;
+            for (int i = 0; i < p; ++i) st[s].Binv[i * p + i] = sc;
+        }
+    }
+    auto new_direction = [&](State& s) {
+        s.dir.assign(p, 0.0);
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) s.dir[i] -= s.Binv[i * p + j] * s.g[j];
+        s.slope = 0.0;
+        for (int i = 0; i < p; ++i) s.slope += s.dir[i] * s.g[i];
+        if (!(s.slope < 0.0)) {   // not a descent direction: reset to steepest descent
+            double gn = 0.0;
+            for (double v : s.g) gn = std::max(gn, std::fabs(v));
+            const double sc = (gn > 0) ? 0.1 / gn : 1.0;
+            std::fill(s.Binv.begin(), s.Binv.end(), 0.0);
+            for (int i = 0; i < p; ++i) {
+                s.Binv[i * p + i] = sc;
+                s.dir[i] = -sc * s.g[i];
+            }
+            s.slope = 0.0;
+            for (int i = 0; i < p; ++i) s.slope += s.dir[i] * s.g[i];
+        }
+        s.step = 1.0;
+        s.ls = 0;
+        s.th_try.resize(p);
+        for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+    };
+    for (auto& s : st) {
+        double gn = 0.0;
+        for (double v : s.g) gn = std::max(gn, std::fabs(v));
+        if (gn == 0.0) s.done = true;
+        else new_direction(s);
+    }
+    for (int round = 0; round < 40 * max_iter; ++round) {
+        std::vector<int> act;
+        std::vector<std::vector<double>> ths;
+        for (int s = 0; s < n_starts; ++s)
+            if (!st[s].done) {
+                act.push_back(s);
+                ths.push_back(st[s].th_try);
+            }
+        if (act.empty()) break;
+        std::vector<double> f;
+        std::vector<std::vector<double>> g;
+        KCHK(evaluate(ths, f, g));
+        for (size_t k = 0; k < act.size(); ++k) {
+            State& s = st[act[k]];
+            const double fn = f[k];
+            if (std::isfinite(fn) && fn <= s.f + 1e-4 * s.step * s.slope) {
+                // accept: BFGS update of the inverse Hessian
+                std::vector<double> sv(p), yv(p);
+                for (int i = 0; i < p; ++i) {
+                    sv[i] = s.th_try[i] - s.th[i];
+                    yv[i] = g[k][i] - s.g[i];
+                }
+                double sy = 0.0;
+                for (int i = 0; i < p; ++i) sy += sv[i] * yv[i];
+                if (sy > 1e-300) {
+                    std::vector<double> By(p, 0.0);
+                    for (int i = 0; i < p; ++i)
+                        for (int j = 0; j < p; ++j) By[i] += s.Binv[i * p + j] * yv[j];
+                    double yBy = 0.0;
+                    for (int i = 0; i < p; ++i) yBy += yv[i] * By[i];
+                    for (int i = 0; i < p; ++i)
+                        for (int j = 0; j < p; ++j)
+                            s.Binv[i * p + j] += ((sy + yBy) * sv[i] * sv[j]) / (sy * sy) -
+                                                 (By[i] * sv[j] + sv[i] * By[j]) / sy;
+                }
+                const double fold = s.f;
+                s.th = s.th_try;
+                s.f = fn;
+                s.g = g[k];
+                s.iter++;
+                double gn = 0.0, tn = 0.0;
+                for (int i = 0; i < p; ++i) {
+                    gn = std::max(gn, std::fabs(s.g[i]));
+                    tn = std::max(tn, std::fabs(sv[i]));
+                }
+                if (s.iter >= max_iter || std::fabs(fold - fn) <= 1e-12 * std::fabs(fn) + 1e-300 || tn < 1e-10 ||
+                    gn < 1e-12 * (std::fabs(fn) + 1e-300))
+                    s.done = true;
+                else
+                    new_direction(s);
+            } else {
+                s.step *= 0.5;
+                s.ls++;
+                if (s.ls > 30) {
+                    s.done = true;
+                } else {
+                    for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+                }
+            }
+        }
+    }
+    int best = 0;
+    for (int s = 1; s < n_starts; ++s)
+        if (st[s].f < st[best].f) best = s;
+    Mat Hb = theta_to_H(o, st[best].th.data());
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
+    if (f_out) *f_out = st[best].f;
+    if (n_evals) *n_evals = evals;
+    return KDEFFT_OK;
+}

@@ -1,0 +1,214 @@
+// Step 1 of Sec. 4: binning of the sample onto the grid.
+//
+// Linear binning (the multilinear rule the paper takes from Wand 1994):
+//   inside iff lo_k <= x_k <= hi_k on every axis (the grid range contains
+//   the data); t_k = (x_k - lo_k) / delta_k (FP64, subtraction and division
+//   rounded separately, no contraction), clamped to M_k - 1 because the
+//   rounding of delta_k can push a point at hi_k just past it
+//   l_k = floor(t_k), clamped to M_k - 2 on the upper edge; f_k = t_k - l_k
+//   corner l + b receives prod_k (b_k ? f_k : 1 - f_k), product in axis order.
+// Simple binning: weight 1 at l_k = floor(t_k + 1/2).
+//
+// Grids that fit in shared memory are accumulated per block there (one
+// privatised histogram per block, flushed with global atomics of the nonzero
+// cells); larger grids use global atomics directly.
+#include "engine.cuh"
+
+namespace kdefft {
+
+__device__ __forceinline__ bool locate(const double* __restrict__ x, const GridDesc& g, long long* l, double* f,
+                                       long long* base) {
+    long long b = 0;
+    for (int k = 0; k < g.d; ++k) {
+        if (!(x[k] >= g.lo[k] && x[k] <= g.hi[k])) return false;   // NaN fails too
+        const double top = (double)(g.M[k] - 1);
+        const double t = fmin(__ddiv_rn(__dsub_rn(x[k], g.lo[k]), g.delta[k]), top);
+        double lk = floor(t);
+        if (lk >= top) lk = top - 1.0;
+        f[k] = __dsub_rn(t, lk);
+        l[k] = (long long)lk;
+        b = b * g.M[k] + l[k];
+    }
+    *base = b;
+    return true;
+}
+
+__device__ __forceinline__ void atomic_acc(float* p, double w) { atomicAdd(p, (float)w); }
+__device__ __forceinline__ void atomic_acc(double* p, double w) { atomicAdd(p, w); }
+
+template <typename acc>
+__global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X, long long n, GridDesc g,
+                                                    acc* __restrict__ counts, long long ncells,
+                                                    unsigned long long* __restrict__ outside, int use_smem) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    acc* hist = reinterpret_cast<acc*>(smem_raw);
+    if (use_smem) {
+        for (long long c = threadIdx.x; c < ncells; c += blockDim.x) hist[c] = acc(0);
+        __syncthreads();
+    }
+    long long stride[MAXD];
+    {
+        long long s = 1;
+        for (int k = g.d - 1; k >= 0; --k) {
+            stride[k] = s;
+            s *= g.M[k];
+        }
+    }
+    const int ncorner = 1 << g.d;
+    unsigned long long nout = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double x[MAXD], f[MAXD];
+        long long l[MAXD], base;
+        for (int k = 0; k < g.d; ++k) x[k] = X[i * g.d + k];
+        if (!locate(x, g, l, f, &base)) {
+            ++nout;
+            continue;
+        }
+        for (int b = 0; b < ncorner; ++b) {
+            double w = 1.0;
+            long long idx = base;
+            for (int k = 0; k < g.d; ++k) {
+                const int bk = (b >> k) & 1;
+                w = __dmul_rn(w, bk ? f[k] : __dsub_rn(1.0, f[k]));
+                idx += bk * stride[k];
+            }
+            if (use_smem)
+                atomic_acc(hist + idx, w);
+            else
+                atomic_acc(counts + idx, w);
+        }
+    }
+    if (nout) atomicAdd(outside, nout);
+    if (use_smem) {
+        __syncthreads();
+        for (long long c = threadIdx.x; c < ncells; c += blockDim.x) {
+            const acc v = hist[c];
+            if (v != acc(0)) atomicAdd(counts + c, v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bin_simple(const double* __restrict__ X, long long n, GridDesc g,
+                                                    int* __restrict__ counts, unsigned long long* __restrict__ outside) {
+    unsigned long long nout = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long idx = 0;
+        bool ok = true;
+        for (int k = 0; k < g.d; ++k) {
+            const double x = X[i * g.d + k];
+            if (!(x >= g.lo[k] && x <= g.hi[k])) {
+                ok = false;
+                break;
+            }
+            const double t = fmin(__ddiv_rn(__dsub_rn(x, g.lo[k]), g.delta[k]), (double)(g.M[k] - 1));
+            const long long lk = (long long)floor(__dadd_rn(t, 0.5));
+            idx = idx * g.M[k] + lk;
+        }
+        if (!ok) {
+            ++nout;
+            continue;
+        }
+        atomicAdd(counts + idx, 1);
+    }
+    if (nout) atomicAdd(outside, nout);
+}
+
+template <typename real>
+__global__ void k_int_to_real(const int* __restrict__ src, real* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (real)src[i];
+}
+
+static int blocks_for(long long n, int nsm, int per_sm) {
+    long long b = (n + 255) / 256;
+    const long long cap = (long long)nsm * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename acc>
+cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, acc* counts, long long ncells,
+                              unsigned long long* outside, int nsm, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const size_t hist_bytes = sizeof(acc) * (size_t)ncells;
+    const int use_smem = hist_bytes <= 96 * 1024;
+    size_t sm = 0;
+    int grid;
+    if (use_smem) {
+        sm = hist_bytes;
+        cudaError_t e = cudaFuncSetAttribute(k_bin_linear<acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        grid = blocks_for(n, nsm, 2);
+    } else {
+        grid = blocks_for(n, nsm, 8);
+    }
+    k_bin_linear<acc><<<grid, 256, sm, st>>>(X, n, g, counts, ncells, outside, use_smem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_simple(const double* X, long long n, const GridDesc& g, int* counts, long long ncells,
+                              unsigned long long* outside, int nsm, cudaStream_t st) {
+    (void)ncells;
+    if (n <= 0) return cudaSuccess;
+    k_bin_simple<<<blocks_for(n, nsm, 8), 256, 0, st>>>(X, n, g, counts, outside);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_int_to_real(const int* src, real* dst, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_int_to_real<real><<<(int)b, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+// Sample moments for the normal-scale start point: pass 0 sums x_k, pass 1
+// sums (x_k - mean_k)(x_l - mean_l); FP64 block sums, atomically combined.
+__global__ void __launch_bounds__(256) k_moments(const double* __restrict__ X, long long n, int d, int pass,
+                                                 const double* __restrict__ mean, double* __restrict__ out) {
+    double acc[MAXD * MAXD];
+    const int nv = pass == 0 ? d : d * d;
+    for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double x[MAXD];
+        for (int k = 0; k < d; ++k) x[k] = X[i * d + k] - (pass ? mean[k] : 0.0);
+        if (pass == 0) {
+            for (int k = 0; k < d; ++k) acc[k] += x[k];
+        } else {
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) acc[a * d + b] += x[a] * x[b];
+        }
+    }
+    __shared__ double red[8][MAXD * MAXD];
+    for (int v = 0; v < nv; ++v) {
+        double t = acc[v];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][v] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        atomicAdd(out + threadIdx.x, t);
+    }
+}
+
+cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
+                           cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_moments<<<blocks_for(n, nsm, 2), 256, 0, st>>>(X, n, d, pass, mean, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_bin_linear<float>(const double*, long long, const GridDesc&, float*, long long,
+                                              unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_bin_linear<double>(const double*, long long, const GridDesc&, double*, long long,
+                                               unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_int_to_real<float>(const int*, float*, long long, cudaStream_t);
+template cudaError_t launch_int_to_real<double>(const int*, double*, long long, cudaStream_t);
+
+}  // namespace kdefft

@@ -1,0 +1,560 @@
+// Device kernels of the per-bandwidth hot path (Sec. 4 steps 2-4, Sec. 5):
+//
+//   stage_a   generates the sampled kernel k_j = sum_m w_m d^alpha phi_{Sigma_m}(delta (.) j)
+//             (Eq. 18 / Eq. 34, Gaussian partials via the multivariate Hermite
+//             recurrence) for a batch of lines along the last axis, directly in
+//             shared memory, and transforms them (first FFT pass of Eq. 22).
+//             For counts items it loads the grid counts instead (C = F(c_zp)).
+//   mid       one FFT pass along an interior axis (only the support lines of
+//             the axes not yet transformed are present: pruned transform).
+//   final     the FFT pass along axis 0 fused with the spectral multiply-and-
+//             reduce: sum_w |C_w|^2 K_w (discrete Parseval form of Eqs. 22-24,
+//             equal to n^2 prod(P) times Eq. 25 when P_k >= M_k + L_k), or, for
+//             counts items, the spectrum |C_w|^2.
+//   reduce    fixed-order FP64 sum of the per-tile partials, times n^-2/prod P.
+//
+// The 1-D transforms are mixed-radix (2, 3, 4, 5, 8) Stockham passes over
+// lines held in shared memory (self-sorting, ping-pong buffers), twiddles
+// exp(-2 pi i t/P) from an FP64-computed table staged in shared memory.
+#include "engine.cuh"
+
+namespace kdefft {
+
+__constant__ HEnt c_htab[HMAX * 4];
+__constant__ int c_hoff[5];
+
+cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total) {
+    cudaError_t e = cudaMemcpyToSymbol(c_htab, tab, sizeof(HEnt) * total);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_hoff, offsets, sizeof(int) * 5);
+}
+
+// ------------------------------------------------------------ complex helpers
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) { return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+// multiply by -i
+template <typename C>
+__device__ __forceinline__ C cmi(C a) { return C{a.y, -a.x}; }
+
+// ------------------------------------------------------------ small DFTs (forward, e^{-2 pi i nk/R})
+template <typename C, int R>
+struct Dft;
+
+template <typename C>
+struct Dft<C, 2> {
+    __device__ __forceinline__ static void run(C* v) {
+        C a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    }
+};
+
+template <typename C>
+struct Dft<C, 3> {
+    __device__ __forceinline__ static void run(C* v) {
+        using R_ = decltype(v[0].x);
+        const R_ s = R_(0.8660254037844386);   // sin(2 pi / 3)
+        C t1 = cadd(v[1], v[2]);
+        C t2 = csub(v[1], v[2]);
+        C m = C{v[0].x - R_(0.5) * t1.x, v[0].y - R_(0.5) * t1.y};
+        C r = C{s * t2.y, -s * t2.x};   // -i s t2
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    }
+};
+
+template <typename C>
+struct Dft<C, 4> {
+    __device__ __forceinline__ static void run(C* v) {
+        C a = cadd(v[0], v[2]);
+        C b = csub(v[0], v[2]);
+        C c = cadd(v[1], v[3]);
+        C e = cmi(csub(v[1], v[3]));
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, e);
+        v[3] = csub(b, e);
+    }
+};
+
+template <typename C>
+struct Dft<C, 5> {
+    __device__ __forceinline__ static void run(C* v) {
+        using R_ = decltype(v[0].x);
+        const R_ c1 = R_(0.30901699437494745);   // cos(2 pi/5)
+        const R_ c2 = R_(-0.8090169943749473);   // cos(4 pi/5)
+        const R_ s1 = R_(0.9510565162951535);    // sin(2 pi/5)
+        const R_ s2 = R_(0.5877852522924732);    // sin(4 pi/5)
+        C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        C x0 = v[0];
+        C p1 = C{x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y};
+        C p2 = C{x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y};
+        // q1 = s1 b1 + s2 b2, q2 = s2 b1 - s1 b2; X1 = p1 - i q1, X2 = p2 - i q2
+        C q1 = C{s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y};
+        C q2 = C{s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y};
+        v[0] = C{x0.x + a1.x + a2.x, x0.y + a1.y + a2.y};
+        v[1] = cadd(p1, cmi(q1));
+        v[4] = csub(p1, cmi(q1));
+        v[2] = cadd(p2, cmi(q2));
+        v[3] = csub(p2, cmi(q2));
+    }
+};
+
+template <typename C>
+struct Dft<C, 8> {
+    __device__ __forceinline__ static void run(C* v) {
+        using R_ = decltype(v[0].x);
+        const R_ h = R_(0.7071067811865476);     // sqrt(1/2)
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<C, 4>::run(e);
+        Dft<C, 4>::run(o);
+        // o_k *= exp(-2 pi i k / 8)
+        o[1] = C{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};
+        o[2] = cmi(o[2]);
+        o[3] = C{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// One radix-R Stockham pass over nl lines of length P (dense, stride P).
+template <typename C, int R>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int nl, int P,
+                                              int Ns, const C* __restrict__ tw) {
+    const int Pr = P / R;
+    const int total = nl * Pr;
+    const int tws = P / (Ns * R);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int line = t / Pr;
+        const int j = t - line * Pr;
+        const C* in = src + line * P;
+        C* out = dst + line * P;
+        const int k = j % Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[j + r * Pr];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
+        }
+        Dft<C, R>::run(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+    }
+}
+
+// Forward DFT of nl lines (length P) held in a; b is the other buffer.
+// Returns the buffer holding the result.  Ends with __syncthreads().
+template <typename C>
+__device__ C* smem_fft(C* a, C* b, int nl, const AxisPlan& ap, const C* tw) {
+    __syncthreads();
+    int Ns = 1;
+    C* src = a;
+    C* dst = b;
+    for (int s = 0; s < ap.nst; ++s) {
+        const int R = ap.radix[s];
+        switch (R) {
+            case 2: stockham_pass<C, 2>(src, dst, nl, ap.P, Ns, tw); break;
+            case 3: stockham_pass<C, 3>(src, dst, nl, ap.P, Ns, tw); break;
+            case 4: stockham_pass<C, 4>(src, dst, nl, ap.P, Ns, tw); break;
+            case 5: stockham_pass<C, 5>(src, dst, nl, ap.P, Ns, tw); break;
+            default: stockham_pass<C, 8>(src, dst, nl, ap.P, Ns, tw); break;
+        }
+        Ns *= R;
+        __syncthreads();
+        C* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+template <typename C>
+__device__ __forceinline__ void load_twiddles(C* tw, const C* pool, const AxisPlan& ap) {
+    for (int t = threadIdx.x; t < ap.P; t += blockDim.x) tw[t] = pool[ap.tw_off + t];
+}
+
+// ------------------------------------------------------------ kernel values
+// Value of the packed pair (grid A + i grid B) at lag vector j (d entries).
+template <typename real>
+__device__ void kernel_pair(const Item<real>& it, const int* j, real& va, real& vb) {
+    real x[MAXD];
+    const int d = it.d;
+#pragma unroll
+    for (int k = 0; k < MAXD; ++k) x[k] = (k < d) ? it.delta[k] * real(j[k]) : real(0);
+    real He[MAXSIG][HMAX];
+    real ex[MAXSIG];
+    const int nh = c_hoff[d] - c_hoff[d - 1];  // entries for this d (max order)
+    int ncount = 1;
+    // entries needed for order R: C(d+R, d); computed on the host into it.R-indexed table size
+    {
+        // graded order: count multi-indices with |alpha| <= R
+        long long c = 1;
+        for (int i = 1; i <= d; ++i) c = c * (it.R + i) / i;
+        ncount = (int)c;
+        if (ncount > nh) ncount = nh;
+    }
+    const HEnt* tab = c_htab + c_hoff[d - 1];
+    for (int s = 0; s < it.nsig; ++s) {
+        const real* L = it.lam[s];
+        real z[MAXD];
+        real q = 0;
+#pragma unroll
+        for (int a = 0; a < MAXD; ++a) {
+            real acc = 0;
+#pragma unroll
+            for (int b = 0; b < MAXD; ++b)
+                if (a < d && b < d) acc += L[a * MAXD + b] * x[b];
+            z[a] = acc;
+            q += x[a] * acc;
+        }
+        ex[s] = it.nrm[s] * exp(real(-0.5) * q);
+        real* h = He[s];
+        h[0] = real(1);
+        for (int t = 1; t < ncount; ++t) {
+            const HEnt e = tab[t];
+            real v = z[e.piv] * h[e.par];
+            for (int r = 0; r < e.nred; ++r) v -= real(e.rc[r]) * L[e.piv * MAXD + e.rj[r]] * h[e.ridx[r]];
+            h[t] = v;
+        }
+    }
+    real a = 0, b = 0;
+    for (int m = 0; m < it.nterm[0]; ++m) a += it.tw8[0][m] * He[it.tsig[0][m]][it.the[0][m]] * ex[it.tsig[0][m]];
+    for (int m = 0; m < it.nterm[1]; ++m) b += it.tw8[1][m] * He[it.tsig[1][m]][it.the[1][m]] * ex[it.tsig[1][m]];
+    va = a;
+    vb = b;
+}
+
+__device__ __forceinline__ int spec_weight_idx(int q, int wdiv) { return q / wdiv; }
+
+// weight of a last-axis frequency in the half-spectrum sum: 1 for w = 0 and
+// (P even) w = P/2, 2 otherwise
+__device__ __forceinline__ int half_weight(int w, int P) { return (w == 0 || 2 * w == P) ? 1 : 2; }
+
+template <typename real>
+__device__ void block_reduce2(double a, double b, double* out2) {
+    __shared__ double red[2][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = (l < nw) ? red[0][l] : 0.0;
+        b = (l < nw) ? red[1][l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (l == 0) {
+            out2[0] = a;
+            out2[1] = b;
+        }
+    }
+    __syncthreads();
+}
+
+// Spectral sink of a finished line batch: Y[c][w] for lines q = q0 + c.
+// kind 0: accumulate sum spec[q][w] * weight * Y; kind 1: spec_out = |Y|^2.
+template <typename real, typename C>
+__device__ void spectral_sink(const Item<real>& it, const C* Y, int nl, int P, int q0, int wdiv, int Plast,
+                              bool last_is_line, double* partial_out) {
+    double sa = 0.0, sb = 0.0;
+    if (it.kind == 0) {
+        real fa = 0, fb = 0;
+        int cnt = 0;
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P;
+            const int w = t - c * P;
+            const int q = q0 + c;
+            // d = 1: the line index is the last axis itself (w is w_{d-1})
+            const int wl = last_is_line ? w : q / wdiv;
+            const real s = it.spec[(long long)q * P + w] * real(half_weight(wl, Plast));
+            const C y = Y[t];
+            fa += s * y.x;
+            fb += s * y.y;
+            if (++cnt == 16) {
+                sa += (double)fa;
+                sb += (double)fb;
+                fa = fb = 0;
+                cnt = 0;
+            }
+        }
+        sa += (double)fa;
+        sb += (double)fb;
+        block_reduce2<real>(sa, sb, partial_out);
+    } else {
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P;
+            const int w = t - c * P;
+            const C y = Y[t];
+            it.spec_out[(long long)(q0 + c) * P + w] = y.x * y.x + y.y * y.y;
+        }
+    }
+}
+
+// ------------------------------------------------------------ stage A
+template <typename real>
+__global__ void __launch_bounds__(256) k_stage_a(const Item<real>* __restrict__ items, const Tile* __restrict__ tiles,
+                                                 int ntiles, int cap, typename Cpx<real>::T* __restrict__ scratch,
+                                                 const typename Cpx<real>::T* __restrict__ twpool,
+                                                 double* __restrict__ partial) {
+    using C = typename Cpx<real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufa = reinterpret_cast<C*>(smem_raw);
+    C* bufb = bufa + cap;
+    C* tw = bufb + cap;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile tl = tiles[ti];
+        const Item<real>& it = items[tl.item];
+        const int d = it.d;
+        const int ax = d - 1;
+        const AxisPlan& ap = it.ax[ax];
+        const int P = ap.P;
+        const int nl = tl.n;
+        __syncthreads();
+        load_twiddles(tw, twpool, ap);
+        // fill lines
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P;
+            const int p = t - c * P;
+            int idx = p + it.off[ax];
+            if (idx >= P) idx -= P;
+            C v = C{real(0), real(0)};
+            if (idx < it.S[ax]) {
+                const int line = tl.a + c;
+                if (it.kind == 1) {
+                    const long long M_last = it.S[ax];
+                    v.x = it.counts[(long long)line * M_last + idx];
+                } else {
+                    int j[MAXD];
+                    int rem = line;
+                    for (int k = d - 2; k >= 0; --k) {
+                        const int ik = rem % it.S[k];
+                        rem /= it.S[k];
+                        j[k] = ik - it.off[k];
+                    }
+                    j[ax] = idx - it.off[ax];
+                    real va, vb;
+                    kernel_pair(it, j, va, vb);
+                    v = C{va, vb};
+                }
+            }
+            bufa[t] = v;
+        }
+        C* Y = smem_fft(bufa, bufb, nl, ap, tw);
+        const int Q = P / 2 + 1;
+        if (d == 1) {
+            // the only axis: sink over w in [0, P/2]
+            // compact the half spectrum in place is unnecessary: sink reads Y[w], w < Q
+            double sa = 0.0, sb = 0.0;
+            if (it.kind == 0) {
+                for (int w = threadIdx.x; w < Q; w += blockDim.x) {
+                    const real s = it.spec[w] * real(half_weight(w, P));
+                    sa += (double)(s * Y[w].x);
+                    sb += (double)(s * Y[w].y);
+                }
+                block_reduce2<real>(sa, sb, partial + 2 * (long long)it.tileF0);
+            } else {
+                for (int w = threadIdx.x; w < Q; w += blockDim.x) it.spec_out[w] = Y[w].x * Y[w].x + Y[w].y * Y[w].y;
+            }
+        } else {
+            // write [w][line] for w < Q
+            long long nlines_tot = 1;
+            for (int k = 0; k < d - 1; ++k) nlines_tot *= it.S[k];
+            C* out = scratch + it.scr[0];
+            for (int t = threadIdx.x; t < nl * Q; t += blockDim.x) {
+                const int w = t / nl;
+                const int c = t - w * nl;
+                out[(long long)w * nlines_tot + tl.a + c] = Y[c * P + w];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ mid pass (axis k, 0 < k < d-1)
+template <typename real>
+__global__ void __launch_bounds__(256) k_mid(const Item<real>* __restrict__ items, const Tile* __restrict__ tiles,
+                                             int ntiles, int axis, int cap,
+                                             typename Cpx<real>::T* __restrict__ scratch,
+                                             const typename Cpx<real>::T* __restrict__ twpool) {
+    using C = typename Cpx<real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufa = reinterpret_cast<C*>(smem_raw);
+    C* bufb = bufa + cap;
+    C* tw = bufb + cap;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile tl = tiles[ti];
+        const Item<real>& it = items[tl.item];
+        const int d = it.d;
+        const AxisPlan& ap = it.ax[axis];
+        const int P = ap.P;
+        const int S = it.S[axis];
+        const int nl = tl.n;
+        // ping-pong: stage A wrote scr[0]; the pass for axis d-2 reads 0 writes 1, etc.
+        const int rsel = ((d - 2 - axis) & 1);
+        const C* in = scratch + it.scr[rsel];
+        C* out = scratch + it.scr[rsel ^ 1];
+        long long O = 1;
+        for (int k = 0; k < axis; ++k) O *= it.S[k];
+        __syncthreads();
+        load_twiddles(tw, twpool, ap);
+        const long long ibase = ((long long)tl.a * O + tl.b) * S;
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P;
+            const int p = t - c * P;
+            int idx = p + it.off[axis];
+            if (idx >= P) idx -= P;
+            C v = C{real(0), real(0)};
+            if (idx < S) v = in[ibase + (long long)c * S + idx];
+            bufa[t] = v;
+        }
+        C* Y = smem_fft(bufa, bufb, nl, ap, tw);
+        const long long obase = (long long)tl.a * P;
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int w = t / nl;
+            const int c = t - w * nl;
+            out[(obase + w) * O + tl.b + c] = Y[c * P + w];
+        }
+    }
+}
+
+// ------------------------------------------------------------ final pass (axis 0) + sink
+template <typename real>
+__global__ void __launch_bounds__(256) k_final(const Item<real>* __restrict__ items, const Tile* __restrict__ tiles,
+                                               int ntiles, int cap, typename Cpx<real>::T* __restrict__ scratch,
+                                               const typename Cpx<real>::T* __restrict__ twpool,
+                                               double* __restrict__ partial) {
+    using C = typename Cpx<real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* bufa = reinterpret_cast<C*>(smem_raw);
+    C* bufb = bufa + cap;
+    C* tw = bufb + cap;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile tl = tiles[ti];
+        const Item<real>& it = items[tl.item];
+        const int d = it.d;
+        const AxisPlan& ap = it.ax[0];
+        const int P = ap.P;
+        const int S = it.S[0];
+        const int nl = tl.n;
+        // input buffer: written by the last mid pass (axis 1) or by stage A (d = 2)
+        const int rsel = (d - 2) & 1;
+        const C* in = scratch + it.scr[rsel];
+        __syncthreads();
+        load_twiddles(tw, twpool, ap);
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P;
+            const int p = t - c * P;
+            int idx = p + it.off[0];
+            if (idx >= P) idx -= P;
+            C v = C{real(0), real(0)};
+            if (idx < S) v = in[(long long)(tl.a + c) * S + idx];
+            bufa[t] = v;
+        }
+        C* Y = smem_fft(bufa, bufb, nl, ap, tw);
+        int wdiv = 1;
+        for (int k = 1; k < d - 1; ++k) wdiv *= it.ax[k].P;
+        spectral_sink<real, C>(it, Y, nl, P, tl.a, wdiv, it.ax[d - 1].P, false,
+                               partial + 2 * (long long)ti);
+    }
+}
+
+// ------------------------------------------------------------ reduce
+template <typename real>
+__global__ void k_reduce(const Item<real>* __restrict__ items, int nitems, const double* __restrict__ partial,
+                         double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    const Item<real>& it = items[i];
+    if (it.kind != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int t = 0; t < it.ntileF; ++t) {
+        a += partial[2 * (long long)(it.tileF0 + t)];
+        b += partial[2 * (long long)(it.tileF0 + t) + 1];
+    }
+    out[2 * i] = a * it.scale;
+    out[2 * i + 1] = b * it.scale;
+}
+
+// ------------------------------------------------------------ launchers
+template <typename real>
+static size_t smem_bytes(int cap, int pmax) {
+    return sizeof(typename Cpx<real>::T) * (size_t)(2 * cap + pmax);
+}
+
+template <typename real>
+cudaError_t launch_stage_a(const Item<real>* items, const Tile* tiles, int ntiles, int pmax, int cap,
+                           typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, double* partial,
+                           int grid, cudaStream_t st) {
+    const size_t sm = smem_bytes<real>(cap, pmax);
+    cudaError_t e = cudaFuncSetAttribute(k_stage_a<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_stage_a<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, cap, scratch, twpool, partial);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_mid(const Item<real>* items, const Tile* tiles, int ntiles, int axis, int pmax, int cap,
+                       typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, int grid,
+                       cudaStream_t st) {
+    const size_t sm = smem_bytes<real>(cap, pmax);
+    cudaError_t e = cudaFuncSetAttribute(k_mid<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_mid<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, axis, cap, scratch, twpool);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_final(const Item<real>* items, const Tile* tiles, int ntiles, int pmax, int cap,
+                         typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, double* partial,
+                         int grid, cudaStream_t st) {
+    const size_t sm = smem_bytes<real>(cap, pmax);
+    cudaError_t e = cudaFuncSetAttribute(k_final<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_final<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, cap, scratch, twpool, partial);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* partial, double* out, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    k_reduce<real><<<(nitems + 127) / 128, 128, 0, st>>>(items, nitems, partial, out);
+    return cudaGetLastError();
+}
+
+#define KDEFFT_INST(real)                                                                                       \
+    template cudaError_t launch_stage_a<real>(const Item<real>*, const Tile*, int, int, int,                   \
+                                              typename Cpx<real>::T*, const typename Cpx<real>::T*, double*, \
+                                              int, cudaStream_t);                                             \
+    template cudaError_t launch_mid<real>(const Item<real>*, const Tile*, int, int, int, int,                  \
+                                          typename Cpx<real>::T*, const typename Cpx<real>::T*, int,           \
+                                          cudaStream_t);                                                      \
+    template cudaError_t launch_final<real>(const Item<real>*, const Tile*, int, int, int,                     \
+                                            typename Cpx<real>::T*, const typename Cpx<real>::T*, double*,     \
+                                            int, cudaStream_t);                                               \
+    template cudaError_t launch_reduce<real>(const Item<real>*, int, const double*, double*, cudaStream_t);
+
+KDEFFT_INST(float)
+KDEFFT_INST(double)
+
+}  // namespace kdefft

@@ -1,0 +1,138 @@
+// Internal interface between the host side of the library (api.cu) and the
+// device kernels (engine.cu, binning.cu).  Not part of the public C ABI.
+//
+// Data layout of the d-dimensional transform (Sec. 4, steps 2-4):
+//   A "work item" is one complex transform.  For a kernel item it carries two
+//   real lag kernels packed as k_A + i k_B (both are even, k_{-j} = k_j, so
+//   their transforms are real and come back as the real and imaginary parts);
+//   for a counts item it carries the grid counts.  Along axis k the input is
+//   nonzero only on S_k consecutive dense indices idx (the support
+//   |j_k| <= L_k of Eq. 25, or the M_k grid nodes); dense index idx sits at
+//   circular position p = (idx - off_k) mod P_k of the zero-padded line.
+//   Axes are transformed last to first.  After axes k..d-1 are done the
+//   scratch holds [w_{d-1}][w_{d-2}]..[w_k][i_0..i_{k-1}] (the last axis keeps
+//   only w_{d-1} in [0, P_{d-1}/2], the other half follows from the
+//   symmetry K(-w) = conj(K(w)) of a real input).  The final pass transforms
+//   axis 0 and either reduces against the count spectrum (kernel items) or
+//   writes |Y|^2 (counts items); the spectrum layout is [q][w_0] with
+//   q = flattened (w_{d-1}, .., w_1), w_{d-1} outermost.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kdefft {
+
+constexpr int MAXD = 4;
+constexpr int MAXSIG = 3;
+constexpr int MAXTERM = 40;
+constexpr int MAXST = 14;     // radix stages per axis (P <= 4096)
+constexpr int MAXP = 4096;
+constexpr int HMAX = 216;     // Hermite table entries: C(D+R, D) for (D,R) = (4,6) is 210
+
+// Recurrence program for the multivariate Hermite polynomials He_alpha(z;
+// Lambda), graded order (all |alpha| = 0, then 1, ...).  Entry t > 0:
+//   He[t] = z[piv] He[par] - sum_q rc[q] Lambda[piv][rj[q]] He[ridx[q]].
+struct HEnt {
+    uint16_t par;
+    uint8_t piv;
+    uint8_t nred;
+    uint8_t rj[MAXD];
+    uint8_t rc[MAXD];
+    uint16_t ridx[MAXD];
+};
+
+struct AxisPlan {
+    int P;
+    int nst;
+    int tw_off;                 // offset of exp(-2 pi i t / P), t < P, in the twiddle pool
+    unsigned char radix[MAXST];
+};
+
+template <typename real>
+struct Item {
+    int d;
+    int kind;                   // 0: kernel pair reduced against a spectrum; 1: counts -> |C|^2
+    AxisPlan ax[MAXD];
+    int S[MAXD];                // support length per axis
+    int off[MAXD];              // position p = (idx - off) mod P
+    int R;                      // highest derivative order in the terms
+    int nsig;                   // distinct covariances
+    real lam[MAXSIG][MAXD * MAXD];   // Sigma^{-1}, row stride MAXD
+    real nrm[MAXSIG];           // (2 pi)^{-d/2} |Sigma|^{-1/2}
+    real delta[MAXD];           // bin widths (Eq. 16)
+    int nterm[2];
+    short tsig[2][MAXTERM];
+    short the[2][MAXTERM];
+    real tw8[2][MAXTERM];       // weights, sign (-1)^{|alpha|} folded in
+    const real* spec;           // kind 0: count spectrum |C|^2, layout [q][w0]
+    const real* counts;         // kind 1: counts, row-major over M
+    real* spec_out;             // kind 1: output spectrum
+    long long scr[2];           // scratch offsets (complex elements)
+    int tileF0, ntileF;         // range of final-pass tiles (their partial sums)
+    double scale;               // n^-2 / prod P_k
+};
+
+// One unit of a pass: item index, then pass-specific fields
+//   stage A: a = first line, n = lines
+//   mid:     a = outer transformed index wo, b = first inner line o0, n = lines
+//   final:   a = first q, n = lines
+struct Tile {
+    int item;
+    int a;
+    int b;
+    int n;
+};
+
+template <typename real>
+struct Cpx;
+template <>
+struct Cpx<float> { using T = float2; };
+template <>
+struct Cpx<double> { using T = double2; };
+
+// Host-side launchers (engine.cu).  cap: complex elements per ping-pong
+// buffer in shared memory; pmax: largest P of the pass (its twiddles are
+// staged in shared memory); twpool: device table of all twiddles.
+template <typename real>
+cudaError_t launch_stage_a(const Item<real>* items, const Tile* tiles, int ntiles, int pmax, int cap,
+                           typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, double* partial,
+                           int grid, cudaStream_t st);
+template <typename real>
+cudaError_t launch_mid(const Item<real>* items, const Tile* tiles, int ntiles, int axis, int pmax, int cap,
+                       typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, int grid,
+                       cudaStream_t st);
+template <typename real>
+cudaError_t launch_final(const Item<real>* items, const Tile* tiles, int ntiles, int pmax, int cap,
+                         typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, double* partial,
+                         int grid, cudaStream_t st);
+template <typename real>
+cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* partial, double* out,
+                          cudaStream_t st);
+
+cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
+
+// Binning (binning.cu).  Grid node k along axis a is lo[a] + k delta[a],
+// k < M[a].  Counts accumulate into `counts` (zeroed by the caller);
+// `outside` counts the points with a coordinate outside [lo, hi] (or NaN),
+// which are never binned.
+struct GridDesc {
+    int d;
+    double lo[MAXD];
+    double hi[MAXD];
+    double delta[MAXD];
+    long long M[MAXD];
+};
+
+template <typename acc>
+cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, acc* counts, long long ncells,
+                              unsigned long long* outside, int nsm, cudaStream_t st);
+cudaError_t launch_bin_simple(const double* X, long long n, const GridDesc& g, int* counts, long long ncells,
+                              unsigned long long* outside, int nsm, cudaStream_t st);
+template <typename real>
+cudaError_t launch_int_to_real(const int* src, real* dst, long long n, cudaStream_t st);
+// pass 0: out[k] += sum_i X_ik; pass 1: out[a*d+b] += sum_i (X_ia - mean_a)(X_ib - mean_b)
+cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
+                           cudaStream_t st);
+
+}  // namespace kdefft

@@ -208,4 +208,6 @@ def small_case(n=200, d=2, M=24, seed=7, n_candidates=3):
     Hns = normal_scale(X)
     lo, hi = grid_range(X, Hns)
     Hc = candidates_around(np.random.default_rng(seed + 1), Hns, n_candidates)
-    return Workload(f"small-{d}d-n{n}-M{M}", X, lo, hi, [M] * d, Hc, G=Hns, extra={"H_NS": Hns})
+    Ms = [int(m) for m in M] if hasattr(M, "__len__") else [int(M)] * d
+    return Workload(f"small-{d}d-n{n}-M{'x'.join(map(str, Ms))}", X, lo, hi, Ms, Hc, G=Hns,
+                    extra={"H_NS": Hns})
