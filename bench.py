@@ -1,0 +1,351 @@
+"""Throughput benchmark: candidate-bandwidth objective evaluations per second.
+
+Workload (one "step" = the whole hot path on one dataset): the bivariate
+3-component normal mixture with n = 100000 samples on a 256 x 256 grid
+(synthetic.mixture_2d_large, seed 2): linear binning, count spectrum, then the
+full unconstrained LSCV minimisation and the full SCV minimisation (pilot G =
+normal-scale matrix) over the 3 free entries of H, each with exact gradients
+and `--n-starts` lock-step starts, FP32 arithmetic with FP64 reductions.
+metric = objective(+gradient) evaluations / step time.
+
+value     : device-timed (CUDA events on the library's stream), sample already
+            resident in HBM; L2 flushed (256 MiB write) before every step.
+e2e       : the same step through the C ABI with the sample in pinned host
+            memory (host->device copy inside the timed region) and host results.
+roofline  : the kernel with the largest summed CUDA-event time inside the timed
+            region; algorithmic flops (5 P log2 P per transformed line) and bytes
+            per launch, against the FP32 ALU peak and the measured HBM peak.
+cpu_baseline / --impl reference : the CPU FP64 oracle (test infrastructure)
+            on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload with its
+own seed (independent datasets, no data-path collective); value = all ranks'
+evaluations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate-H objective evals/sec (+grad) at stated rel err vs FP64; % HBM roofline"
+UNIT = "evals/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+PROFILE_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("engine.cu", "engine.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1511_07482_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kname):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    if not os.path.exists(PROFILE_FILE):
+        return None
+    try:
+        d = json.load(open(PROFILE_FILE))
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_hash():
+        return None
+    k = d.get("kernels", {}).get(kname)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1511_07482_gb300 import LSCV, SCV, Context, synthetic
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synthetic.mixture_2d_large(seed=2 + 1000 * rank)
+    X_dev = torch.from_numpy(w.X).to(dev)
+    X_pin = torch.from_numpy(w.X).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(X):
+        ds = ctx.bin(X, w.lo, w.hi, w.M)
+        H1, f1, e1 = ds.select_H(LSCV, n_starts=args.n_starts, max_iter=args.max_iter)
+        H2, f2, e2 = ds.select_H(SCV, G=w.G, n_starts=args.n_starts, max_iter=args.max_iter)
+        ds.close()
+        return e1 + e2, (H1, f1, H2, f2)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(X_dev)
+
+    # ---- device-resident timed region
+    times, evals = [], 0
+    clocks = Clocks(local)
+    ctx.profile(1)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e, res = step(X_dev)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(a.elapsed_time(b))
+        evals += e
+    kstats, launches, _, _ = ctx.profile_read()
+    ctx.profile(0)
+    clk = clocks.stop()
+    t_total = sum(times)
+
+    # ---- end-to-end through the C ABI with host buffers
+    e2e_times, e2e_evals = [], 0
+    ctx.profile(1)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e, _ = step(X_pin)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_times.append(a.elapsed_time(b))
+        e2e_evals += e
+    _, _, h2d, d2h = ctx.profile_read()
+    ctx.profile(0)
+
+    # max over ranks
+    tot = torch.tensor([t_total, float(evals), sum(e2e_times), float(e2e_evals)], dtype=torch.float64)
+    if world > 1:
+        tmax = tot.clone().to(dev)
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tmax[2:3], op=dist.ReduceOp.MAX)
+        s = tot.clone().to(dev)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        tot = torch.tensor([tmax[0].item(), s[1].item(), tmax[2].item(), s[3].item()], dtype=torch.float64)
+    value = tot[1].item() / (tot[0].item() / 1000.0)
+    e2e_value = tot[3].item() / (tot[2].item() / 1000.0)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    hbm, smmax, src = peaks()
+    # dominant kernel
+    kname = max(kstats, key=lambda k: kstats[k]["ms"]) if kstats else None
+    roof = None
+    if kname:
+        k = kstats[kname]
+        avg_s = k["ms"] / 1000.0 / max(k["launches"], 1)
+        fl = k["flops"] / max(k["launches"], 1)
+        by = k["bytes"] / max(k["launches"], 1)
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smmax * 1e6 / 1e12        # TFLOP/s
+        a_tf = fl / avg_s / 1e12
+        a_gb = by / avg_s / 1e9
+        if a_gb / hbm >= a_tf / alu_peak:
+            roof = {"bound": "hbm", "achieved": a_gb, "peak": hbm, "unit": "GB/s", "frac": a_gb / hbm}
+        else:
+            roof = {"bound": "alu", "achieved": a_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": a_tf / alu_peak}
+        roof.update({"kernel": kname, "peak_source": src, "launches": k["launches"],
+                     "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": by,
+                     "algorithmic_flops_per_launch": fl, "traffic": ncu_traffic(kname),
+                     "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kstats.values())})
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot[0].item() / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name + ": bin + full LSCV and SCV minimisation (3 free entries of H, "
+                               "adjoint gradients)", "n": w.n, "d": w.d, "grid": w.M,
+                   "n_starts": args.n_starts, "max_iter": args.max_iter, "precision": "fp32, fp64 reductions",
+                   "l2": "flushed by a 256 MiB device write before every step",
+                   "evals_per_step": evals / args.steps},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d / args.steps),
+                "d2h_bytes_per_step": int(d2h / args.steps)},
+        "gpu_launches": int(launches),
+        "kernel_times_ms": {k: round(v["ms"], 3) for k, v in kstats.items()},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, args, res)
+    print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_evals(w, Hs, G):
+    """The oracle's LSCV+gradient and SCV+gradient at the given H (FP64,
+    binned, the paper's FFT steps); returns (#evals, results)."""
+    from oracle import binning, functionals as F, rules, selectors as S
+    c = binning.bin_linear(w.X, w.lo, w.hi, w.M)
+    delta = rules.bin_width(w.lo, w.hi, w.M)
+    res = []
+    for H in Hs:
+        L = rules.support_L(rules.lambda_max(H), delta, w.M)
+        P = rules.P_minimal(w.M, L)
+        res.append(("lscv", S.lscv(lambda t: F.binned_fft(c, w.n, t, delta, L, P), H, w.n, grad=True)))
+        L2 = rules.support_L(rules.lambda_max(2 * H + 2 * G), delta, w.M)
+        P2 = rules.P_minimal(w.M, L2)
+        res.append(("scv", S.scv(lambda t: F.binned_fft(c, w.n, t, delta, L2, P2), H, G, w.n, grad=True)))
+    return 2 * len(Hs), res
+
+
+def cpu_baseline(w, args, gpu_res):
+    """The oracle, as it stands, on a bounded sample: binning of the full
+    sample plus LSCV+grad and SCV+grad at the GPU-selected LSCV bandwidth and
+    one more candidate; also the relative error of the GPU objective values
+    at those bandwidths."""
+    H1, f1, H2, f2 = gpu_res
+    t0 = time.perf_counter()
+    n_ev, res = oracle_evals(w, [H1], w.G)
+    # accuracy of the FP32 path at the selected H: compare with the oracle value
+    ref_lscv = res[0][1][0]
+    rel = abs(f1 - ref_lscv) / abs(ref_lscv)
+    i = 0
+    while time.perf_counter() - t0 < args.cpu_seconds:
+        k, _ = oracle_evals(w, [w.H[i % len(w.H)]], w.G)
+        n_ev += k
+        i += 1
+    dt = time.perf_counter() - t0
+    return {"value": n_ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{w.name}: {1 + i} oracle binnings of all n, each followed by LSCV+gradient and "
+                      f"SCV+gradient in FP64 (numpy FFT) at one bandwidth ({n_ev} evaluations, {dt:.1f} s)",
+            "rel_err_lscv_at_selected_H": rel}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return
+    from paper_1511_07482_gb300 import synthetic
+    w = synthetic.mixture_2d_large()
+    Hs = list(w.H[:4])
+    for _ in range(args.warmup):
+        oracle_evals(w, Hs, w.G)
+    t, ev = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        n_ev, _ = oracle_evals(w, Hs, w.G)
+        t += time.perf_counter() - t0
+        ev += n_ev
+    value = ev / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + ": bin + LSCV and SCV objective+gradient evaluations (oracle)",
+                      "n": w.n, "d": w.d, "grid": w.M},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"per step: oracle binning of all n plus {2 * len(Hs)} FP64 "
+                                      f"objective+gradient evaluations"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-starts", type=int, default=16)
+    ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -174,7 +174,11 @@ int kdefft_eta02(kdefft_ds ds, const double* H, int nH, const double* G, double*
  * the others are deterministic dilations/rotations of it) run in lock-step,
  * one batched evaluation per iteration; the best end point is returned.
  * H_out: d x d; f_out: objective at H_out; n_evals: total objective+gradient
- * evaluations (may be NULL). All host. */
+ * evaluations (may be NULL). All host.  Search domain: H numerically SPD
+ * with sqrt(H_kk) >= delta_k / 2 (bandwidths finer than half a bin are not
+ * resolved by the binned objective, which is unbounded below as H -> 0 when
+ * bins hold several points); trial points outside it are rejected by the line
+ * search.  Steps change the Cholesky diagonal by at most a factor e. */
 int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G,
                     int n_starts, int max_iter, double* H_out, double* f_out,
                     int64_t* n_evals);

@@ -1764,29 +1764,50 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
     if (method == KDEFFT_PI) KCHK(psi4_kron(ds, Gm, psi4));
     int64_t evals = 0;
 
+    // Domain of the search: H numerically SPD and resolvable by the grid,
+    // sqrt(H_kk) >= delta_k / 2 on every axis.  With binned data the objective
+    // is unbounded below as H -> 0 (a bin holding several points contributes
+    // a diagonal term of order -phi_H(0)), so bandwidths finer than the bins
+    // are outside the domain: such a trial point counts as f = +inf.
+    auto in_domain = [&](const Mat& H) {
+        Mat Lc;
+        if (!cholesky(H, Lc)) return false;
+        for (int k = 0; k < d; ++k)
+            if (!(std::sqrt(H(k, k)) >= 0.5 * ds->delta[k]) || !std::isfinite(H(k, k))) return false;
+        return true;
+    };
     // batched evaluation of value + theta-gradient for a list of theta
     auto evaluate = [&](const std::vector<std::vector<double>>& ths, std::vector<double>& f,
                         std::vector<std::vector<double>>& gt) -> int {
         const int m = (int)ths.size();
-        std::vector<double> Hs((size_t)m * d * d);
+        f.assign(m, INFINITY);
+        gt.assign(m, std::vector<double>(p, 0.0));
+        std::vector<int> idx;
+        std::vector<double> Hs;
         for (int i = 0; i < m; ++i) {
             Mat H = theta_to_H(o, ths[i].data());
+            if (!in_domain(H)) continue;
+            idx.push_back(i);
             for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) Hs[(size_t)i * d * d + a * d + b] = H(a, b);
+                for (int b = 0; b < d; ++b) Hs.push_back(H(a, b));
         }
+        const int mv = (int)idx.size();
+        if (mv == 0) return KDEFFT_OK;
         std::vector<double> v, g;
         int r;
         if (method == KDEFFT_LSCV)
-            r = eval_lscv(ds, Hs.data(), m, v, &g);
+            r = eval_lscv(ds, Hs.data(), mv, v, &g);
         else if (method == KDEFFT_SCV)
-            r = eval_scv(ds, Hs.data(), m, Gm, v, &g);
+            r = eval_scv(ds, Hs.data(), mv, Gm, v, &g);
         else
-            r = eval_pi(ds, Hs.data(), m, psi4, v, &g);
+            r = eval_pi(ds, Hs.data(), mv, psi4, v, &g);
         if (r != KDEFFT_OK) return r;
-        evals += m;
-        f = v;
-        gt.assign(m, std::vector<double>(p));
-        for (int i = 0; i < m; ++i) grad_theta(o, ths[i].data(), g.data() + (size_t)i * d * d, gt[i].data());
+        evals += mv;
+        for (int j = 0; j < mv; ++j) {
+            const int i = idx[j];
+            f[i] = v[j];
+            grad_theta(o, ths[i].data(), g.data() + (size_t)j * d * d, gt[i].data());
+        }
         return KDEFFT_OK;
     };
 
@@ -1838,6 +1859,7 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
         for (int s = 0; s < n_starts; ++s) {
             st[s].f = f[s];
             st[s].g = g[s];
+            if (!std::isfinite(f[s])) st[s].done = true;
             // initial inverse-Hessian scale: a unit step moves theta by ~0.1
             double gn = 0.0;
             for (double v : g[s]) gn = std::max(gn, std::fabs(v));
@@ -1863,12 +1885,19 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
             s.slope = 0.0;
             for (int i = 0; i < p; ++i) s.slope += s.dir[i] * s.g[i];
         }
+        double dm = 0.0;
+        for (double v : s.dir) dm = std::max(dm, std::fabs(v));
+        if (dm > 1.0) {   // at most a factor e per iteration on the Cholesky diagonal
+            for (double& v : s.dir) v /= dm;
+            s.slope /= dm;
+        }
         s.step = 1.0;
         s.ls = 0;
         s.th_try.resize(p);
         for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
     };
     for (auto& s : st) {
+        if (s.done) continue;
         double gn = 0.0;
         for (double v : s.g) gn = std::max(gn, std::fabs(v));
         if (gn == 0.0) s.done = true;
@@ -1938,6 +1967,7 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
     int best = 0;
     for (int s = 1; s < n_starts; ++s)
         if (st[s].f < st[best].f) best = s;
+    if (!std::isfinite(st[best].f)) return fail(KDEFFT_ERR_ARG, "no start point inside the search domain");
     Mat Hb = theta_to_H(o, st[best].th.data());
     for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
