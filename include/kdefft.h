@@ -192,6 +192,36 @@ int kdefft_batch_lscv(kdefft_ctx ctx, int nds, const kdefft_ds* ds,
                       const int* nH_per_ds, const double* H,
                       double* val, double* grad);
 
+/* LSCV value and gradient for one bandwidth without allocating any memory.
+ * The paper has no counterpart: this is for callers that cannot allocate at
+ * the point of the call -- code that runs under a device-memory budget fixed
+ * in advance, code called back from inside another framework's allocator, or
+ * latency-critical loops where a cudaMalloc (which synchronises the device and
+ * can fail) is not acceptable.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its work buffers live in one scratch array of
+ * KDEFFT_NOALLOC_SCRATCH_BYTES (32 MiB) inside the library image, which every
+ * GPU that loads the library holds until the process exits.
+ *   d: 1..3; M: d grid sizes; delta: d bin widths (Eq. 16); n: sample size;
+ *   counts: device pointer to prod M_k FP32 grid counts, row-major (e.g. from
+ *   kdefft_counts); H: d x d host array; tau: Eq. 26 multiplier (L_k from
+ *   lambda_max(H)); P_k: the minimal no-alias padding; stream: cudaStream_t;
+ *   out: device pointer to 1 + d*d FP64 values, LSCV(H) of Eq. 10 followed by
+ *   the d x d gradient (convention above).
+ * Runs on the calling thread's current device and returns without waiting
+ * for the GPU.  The first call on a device takes the scratch array's device
+ * address (cudaGetSymbolAddress) and uploads small constant tables; make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array, which keeps the previous call's contents (everything that must
+ * start at zero is written before it is read), so calls that overlap on the
+ * GPU -- on different streams, unordered -- race; order them on one stream.
+ * Errors: KDEFFT_ERR_ARG (bad sizes, out/counts not device memory, H not
+ * symmetric), KDEFFT_ERR_NOT_SPD, KDEFFT_ERR_UNSUPPORTED (the problem needs
+ * more than the scratch array holds, or P_k > 4096), KDEFFT_ERR_CUDA. */
+#define KDEFFT_NOALLOC_SCRATCH_BYTES (32u << 20)
+int kdefft_lscv_noalloc(int d, const int64_t* M, const double* delta, int64_t n,
+                        const float* counts, const double* H, double tau,
+                        void* stream, double* out);
+
 /* Instrumentation (no paper counterpart).  kdefft_profile(ctx, mode):
  * mode 1 resets the counters and turns per-kernel timing on, 2 turns it on
  * without a reset, 0 resets and turns it off.  With timing on, every kernel

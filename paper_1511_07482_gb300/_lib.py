@@ -29,6 +29,7 @@ EXPORTS = [
     "kdefft_ds_set_opts", "kdefft_ds_info", "kdefft_counts", "kdefft_plan", "kdefft_psi",
     "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
+    "kdefft_lscv_noalloc",
 ]
 
 
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
         "kdefft_profile": (I, [P, I]),
         "kdefft_profile_read": (I, [P, P, I, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64)]),
+        "kdefft_lscv_noalloc": (I, [I, P, P, I64, P, P, C.c_double, P, P]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -115,6 +117,27 @@ def _ptr_of(x):
     except ImportError:
         pass
     return _host_f64(x)
+
+
+def lscv_noalloc(M, delta, n, counts, H, out, tau=3.7, stream=None):
+    """LSCV(H) and gradient into `out` (a CUDA float64 tensor of 1 + d*d
+    values) from device-resident FP32 counts, through the entry point that
+    allocates nothing.  Asynchronous on `stream` (default: torch's current
+    stream); the caller synchronises."""
+    import torch
+    d = len(M)
+    M_a = np.ascontiguousarray(np.asarray(M, dtype=np.int64))
+    dl, pdl = _host_f64(delta)
+    Ha, pH = _host_f64(H)
+    if not (isinstance(counts, torch.Tensor) and counts.is_cuda and counts.dtype == torch.float32):
+        raise TypeError("counts must be a CUDA float32 tensor")
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64):
+        raise TypeError("out must be a CUDA float64 tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream(out.device).cuda_stream
+    _check(load().kdefft_lscv_noalloc(d, M_a.ctypes.data_as(C.c_void_p), pdl, int(n),
+                                      C.c_void_p(counts.data_ptr()), pH, float(tau), C.c_void_p(stream),
+                                      C.c_void_p(out.data_ptr())))
 
 
 def default_opts(**kw) -> Opts:
