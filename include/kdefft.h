@@ -192,6 +192,14 @@ int kdefft_batch_lscv(kdefft_ctx ctx, int nds, const kdefft_ds* ds,
                       const int* nH_per_ds, const double* H,
                       double* val, double* grad);
 
+/* Engine selection for the per-bandwidth transforms.  AUTO (default): for
+ * d = 2 one thread-block-cluster kernel per batch does all passes in shared
+ * and distributed shared memory whenever the work fits, else the multi-pass
+ * path; MULTIPASS: always the pass-per-axis kernels with a global scratch
+ * between passes (used for d >= 3).  Both compute the same sums. */
+enum { KDEFFT_ENGINE_AUTO = 0, KDEFFT_ENGINE_MULTIPASS = 1 };
+int kdefft_set_engine(kdefft_ctx ctx, int engine);
+
 /* LSCV value and gradient for one bandwidth without allocating any memory.
  * The paper has no counterpart: this is for callers that cannot allocate at
  * the point of the call -- code that runs under a device-memory budget fixed

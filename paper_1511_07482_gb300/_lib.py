@@ -29,8 +29,9 @@ EXPORTS = [
     "kdefft_ds_set_opts", "kdefft_ds_info", "kdefft_counts", "kdefft_plan", "kdefft_psi",
     "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
-    "kdefft_lscv_noalloc",
+    "kdefft_lscv_noalloc", "kdefft_set_engine",
 ]
+ENGINE_AUTO, ENGINE_MULTIPASS = 0, 1
 
 
 class Opts(C.Structure):
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
         "kdefft_profile_read": (I, [P, P, I, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64)]),
         "kdefft_lscv_noalloc": (I, [I, P, P, I64, P, P, C.c_double, P, P]),
+        "kdefft_set_engine": (I, [P, I]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -183,6 +185,10 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_engine(self, engine: int):
+        """ENGINE_AUTO (fused cluster kernel for d = 2) or ENGINE_MULTIPASS."""
+        _check(load().kdefft_set_engine(self.h, int(engine)))
 
     def profile(self, mode: int = 1):
         """1: reset counters and time every kernel with CUDA events; 2: keep

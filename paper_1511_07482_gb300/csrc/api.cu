@@ -385,6 +385,7 @@ struct kdefft_ctx_s {
         double ms = 0.0, bytes = 0.0, flops = 0.0;
     };
     bool prof = false;
+    bool fused = true;    // d = 2: single cluster kernel per batch when it fits
     std::map<std::string, KStat> kstat;
     struct Pending {
         std::string name;
@@ -942,6 +943,60 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
 
 static int cap_elems(bool dbl) { return dbl ? 3072 : 6144; }
 
+// d = 2, kernel items only: one cluster launch does every pass and the
+// reduction.  Returns KDEFFT_ERR_UNSUPPORTED (without launching) when the
+// items do not fit in shared memory for any cluster size; the caller then
+// takes the multi-pass path.
+template <typename real>
+static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* out_host) {
+    using C = typename Cpx<real>::T;
+    const int nitems = (int)items.size();
+    const size_t budget = 200 * 1024;
+    int cs = 2;
+    while (cs < 8 && (long long)nitems * cs < 2LL * c->nsm) cs *= 2;
+    int slab = 0, cap = 0, pmax = 0;
+    for (;;) {
+        slab = cap = pmax = 0;
+        for (const Item<real>& it : items) {
+            const int P1 = it.ax[1].P, P0 = it.ax[0].P, Q1 = P1 / 2 + 1;
+            const int lpc = (it.S[0] + cs - 1) / cs, cpc = (Q1 + cs - 1) / cs;
+            slab = std::max(slab, lpc * Q1);
+            cap = std::max(cap, std::max(lpc * P1, cpc * P0));
+            pmax = std::max(pmax, std::max(P0, P1));
+        }
+        if (sizeof(C) * (size_t)(slab + 2 * pmax + 2 * cap) <= budget) break;
+        if (cs >= 8) return KDEFFT_ERR_UNSUPPORTED;
+        cs *= 2;
+    }
+    KCHK(sync_twiddles(c));
+    const size_t bItems = sizeof(Item<real>) * nitems;
+    KCHK(c->h_items.ensure(bItems));
+    KCHK(c->items.ensure(bItems));
+    KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
+    KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
+    KCU(cudaStreamSynchronize(c->stream));
+    std::memcpy(c->h_items.p, items.data(), bItems);
+    KCU(cudaMemcpyAsync(c->items.p, c->h_items.p, bItems, cudaMemcpyHostToDevice, c->stream));
+    c->h2d += (int64_t)bItems;
+    double fl = 0.0, by = 0.0;
+    for (const Item<real>& it : items) {
+        const double P1 = it.ax[1].P, P0 = it.ax[0].P, Q1 = std::floor(P1 / 2) + 1;
+        fl += it.S[0] * 5.0 * P1 * std::log2(P1) + Q1 * (5.0 * P0 * std::log2(P0) + 4.0 * P0);
+        by += Q1 * P0 * sizeof(real);
+    }
+    const C* tw = (const C*)(sizeof(real) == 4 ? c->tw32.p : c->tw64.p);
+    cudaEvent_t ev = prof_start(c);
+    KCU(launch_fused2d<real>((const Item<real>*)c->items.p, nitems, cs, slab, cap, pmax, tw, (double*)c->out.p,
+                             c->stream));
+    prof_stop(c, ev, sizeof(real) == 4 ? "fused2d_f32" : "fused2d_f64", by, fl);
+    KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
+    std::memcpy(out_host, c->h_out.p, sizeof(double) * 2 * nitems);
+    prof_flush(c);
+    return KDEFFT_OK;
+}
+
 // |F(c_zp)|^2 at padded sizes P (computed once per dataset and P)
 template <typename real>
 static int ensure_spectrum(kdefft_ds ds, const int* P, const real** out) {
@@ -1065,7 +1120,12 @@ static int run_requests(kdefft_ctx c, ReqSet& rs) {
             ++pi;
         }
         std::vector<double> out(2 * items.size());
-        KCHK(launch_items<real>(c, items, pl, d, out.data()));
+        int fr = KDEFFT_ERR_UNSUPPORTED;
+        if (d == 2 && c->fused) fr = launch_fused<real>(c, items, out.data());
+        if (fr == KDEFFT_ERR_UNSUPPORTED)
+            KCHK(launch_items<real>(c, items, pl, d, out.data()));
+        else if (fr != KDEFFT_OK)
+            return fr;
         for (size_t i = 0; i < batch.size(); ++i) {
             rs.grids[batch[i].first].value = out[2 * i];
             if (batch[i].second >= 0) rs.grids[batch[i].second].value = out[2 * i + 1];
@@ -1239,6 +1299,14 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         return r;
     }
     *out = c;
+    return KDEFFT_OK;
+}
+
+int kdefft_set_engine(kdefft_ctx c, int engine) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    if (engine != KDEFFT_ENGINE_AUTO && engine != KDEFFT_ENGINE_MULTIPASS)
+        return fail(KDEFFT_ERR_ARG, "unknown engine");
+    c->fused = (engine == KDEFFT_ENGINE_AUTO);
     return KDEFFT_OK;
 }
 

@@ -16,7 +16,11 @@
 // The 1-D transforms are mixed-radix (2, 3, 4, 5, 8) Stockham passes over
 // lines held in shared memory (self-sorting, ping-pong buffers), twiddles
 // exp(-2 pi i t/P) from an FP64-computed table staged in shared memory.
+#include <cooperative_groups.h>
+
 #include "engine.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace kdefft {
 
@@ -496,6 +500,124 @@ __global__ void k_reduce(const Item<real>* __restrict__ items, int nitems, const
     out[2 * i + 1] = b * it.scale;
 }
 
+// ------------------------------------------------------------ fused 2-D path (one cluster per item)
+// d = 2 only.  The CS CTAs of a cluster split the S_0 generated lines of the
+// axis-1 pass (k_stage_a's work) and keep their half spectra (w_1 <= P_1/2) in
+// shared memory; after a cluster barrier each CTA gathers the axis-0 lines of
+// its share of the w_1 columns from the other CTAs' shared memory
+// (distributed shared memory), transforms them and reduces against the
+// spectrum (k_final's work); the per-CTA partial sums meet in rank 0's shared
+// memory and rank 0 writes the item's two scaled sums (k_reduce's work).
+template <typename real>
+__global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ items, int cs, int slab_elems,
+                                                 int cap, int pmax, const typename Cpx<real>::T* __restrict__ twpool,
+                                                 double* __restrict__ out) {
+    using C = typename Cpx<real>::T;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double cl_red[16][2];
+    C* slab = reinterpret_cast<C*>(smem_raw);
+    C* tw1 = slab + slab_elems;
+    C* tw0 = tw1 + pmax;
+    C* bufa = tw0 + pmax;
+    C* bufb = bufa + cap;
+    const int rank = (int)cluster.block_rank();
+    const int item = blockIdx.x / cs;
+    const Item<real>& it = items[item];
+    const AxisPlan& a1 = it.ax[1];
+    const AxisPlan& a0 = it.ax[0];
+    const int P1 = a1.P, P0 = a0.P, Q1 = P1 / 2 + 1;
+    const int S0 = it.S[0], S1 = it.S[1];
+    const int lpc = (S0 + cs - 1) / cs;
+    const int cpc = (Q1 + cs - 1) / cs;
+    load_twiddles(tw1, twpool, a1);
+    load_twiddles(tw0, twpool, a0);
+    // ---- axis-1 pass over my generated lines
+    const int l0 = rank * lpc;
+    const int nl = max(0, min(S0, l0 + lpc) - l0);
+    if (nl > 0) {
+        for (int t = threadIdx.x; t < nl * P1; t += blockDim.x) {
+            const int c = t / P1;
+            const int p = t - c * P1;
+            int idx = p + it.off[1];
+            if (idx >= P1) idx -= P1;
+            C v = C{real(0), real(0)};
+            if (idx < S1) {
+                int j[MAXD];
+                j[0] = l0 + c - it.off[0];
+                j[1] = idx - it.off[1];
+                real va, vb;
+                kernel_pair(it, j, va, vb);
+                v = C{va, vb};
+            }
+            bufa[t] = v;
+        }
+        C* Y = smem_fft(bufa, bufb, nl, a1, tw1);
+        for (int t = threadIdx.x; t < nl * Q1; t += blockDim.x) {
+            const int c = t / Q1;
+            const int q = t - c * Q1;
+            slab[c * Q1 + q] = Y[c * P1 + q];
+        }
+    }
+    cluster.sync();
+    // ---- axis-0 pass over my columns, gathered from the cluster's slabs
+    const int q0 = rank * cpc;
+    const int nq = max(0, min(Q1, q0 + cpc) - q0);
+    double sa = 0.0, sb = 0.0;
+    if (nq > 0) {
+        for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
+            const int c = t / P0;
+            const int p = t - c * P0;
+            int idx = p + it.off[0];
+            if (idx >= P0) idx -= P0;
+            C v = C{real(0), real(0)};
+            if (idx < S0) {
+                const int src = idx / lpc;
+                const C* rs = cluster.map_shared_rank(slab, src);
+                v = rs[(idx - src * lpc) * Q1 + q0 + c];
+            }
+            bufa[t] = v;
+        }
+        C* Y = smem_fft(bufa, bufb, nq, a0, tw0);
+        real fa = 0, fb = 0;
+        int cnt = 0;
+        for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
+            const int c = t / P0;
+            const int w = t - c * P0;
+            const int q = q0 + c;
+            const real s = it.spec[(long long)q * P0 + w] * real(half_weight(q, P1));
+            const C y = Y[t];
+            fa += s * y.x;
+            fb += s * y.y;
+            if (++cnt == 16) {
+                sa += (double)fa;
+                sb += (double)fb;
+                fa = fb = 0;
+                cnt = 0;
+            }
+        }
+        sa += (double)fa;
+        sb += (double)fb;
+    }
+    double part[2];
+    block_reduce2<real>(sa, sb, part);
+    if (threadIdx.x == 0) {
+        double* dst = cluster.map_shared_rank(&cl_red[0][0], 0);
+        dst[2 * rank] = part[0];
+        dst[2 * rank + 1] = part[1];
+    }
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int r = 0; r < cs; ++r) {
+            a += cl_red[r][0];
+            b += cl_red[r][1];
+        }
+        out[2 * item] = a * it.scale;
+        out[2 * item + 1] = b * it.scale;
+    }
+}
+
 // ------------------------------------------------------------ launchers
 template <typename real>
 static size_t smem_bytes(int cap, int pmax) {
@@ -542,6 +664,36 @@ cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* par
     return cudaGetLastError();
 }
 
+
+template <typename real>
+cudaError_t launch_fused2d(const Item<real>* items, int nitems, int cs, int slab_elems, int cap, int pmax,
+                           const typename Cpx<real>::T* twpool, double* out, cudaStream_t st) {
+    using C = typename Cpx<real>::T;
+    const size_t sm = sizeof(C) * (size_t)(slab_elems + 2 * pmax + 2 * cap);
+    static size_t set_bytes[2] = {0, 0};
+    const int ti = sizeof(real) == 4 ? 0 : 1;
+    if (sm > set_bytes[ti]) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_fused2d<real>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        set_bytes[ti] = sm;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nitems * cs), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fused2d<real>, items, cs, slab_elems, cap, pmax, twpool, out);
+}
+
 #define KDEFFT_INST(real)                                                                                       \
     template cudaError_t launch_stage_a<real>(const Item<real>*, const Tile*, int, int, int,                   \
                                               typename Cpx<real>::T*, const typename Cpx<real>::T*, double*, \
@@ -552,7 +704,9 @@ cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* par
     template cudaError_t launch_final<real>(const Item<real>*, const Tile*, int, int, int,                     \
                                             typename Cpx<real>::T*, const typename Cpx<real>::T*, double*,     \
                                             int, cudaStream_t);                                               \
-    template cudaError_t launch_reduce<real>(const Item<real>*, int, const double*, double*, cudaStream_t);
+    template cudaError_t launch_reduce<real>(const Item<real>*, int, const double*, double*, cudaStream_t);        \
+    template cudaError_t launch_fused2d<real>(const Item<real>*, int, int, int, int, int,                          \
+                                              const typename Cpx<real>::T*, double*, cudaStream_t);
 
 KDEFFT_INST(float)
 KDEFFT_INST(double)

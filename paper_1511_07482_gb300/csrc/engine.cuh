@@ -110,6 +110,14 @@ template <typename real>
 cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* partial, double* out,
                           cudaStream_t st);
 
+// d = 2: one thread-block cluster of cs CTAs per item does stage A, the
+// final pass and the reduction (out[2 i], out[2 i + 1], scaled).  slab_elems:
+// complex elements per CTA for the half spectra of its lines; cap: per
+// ping-pong buffer.
+template <typename real>
+cudaError_t launch_fused2d(const Item<real>* items, int nitems, int cs, int slab_elems, int cap, int pmax,
+                           const typename Cpx<real>::T* twpool, double* out, cudaStream_t st);
+
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
 
 // Binning (binning.cu).  Grid node k along axis a is lo[a] + k delta[a],

@@ -19,10 +19,11 @@ from paper_1511_07482_gb300 import synthetic
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
-    from paper_1511_07482_gb300 import Context
+@pytest.fixture(scope="module", params=["auto", "multipass"])
+def ctx(request):
+    from paper_1511_07482_gb300 import ENGINE_AUTO, ENGINE_MULTIPASS, Context
     c = Context(0)
+    c.set_engine(ENGINE_AUTO if request.param == "auto" else ENGINE_MULTIPASS)
     yield c
     c.close()
 
