@@ -268,11 +268,16 @@ static void enumerate(int d, int R, std::vector<MultiIndex>& out) {
 
 struct HermiteIndex {
     std::vector<MultiIndex> list[5];
-    std::map<std::vector<int>, int> index[5];
+    std::vector<int> code[5];   // alpha as base-9 digits -> position in the graded order
+    static int key(int d, const int* a) {
+        int k = 0;
+        for (int i = 0; i < d; ++i) k = k * 9 + a[i];
+        return k;
+    }
     int idx(int d, const int* a) const {
-        std::vector<int> k(a, a + d);
-        auto it = index[d].find(k);
-        return it == index[d].end() ? -1 : it->second;
+        for (int i = 0; i < d; ++i)
+            if (a[i] < 0 || a[i] > 8) return -1;
+        return code[d][key(d, a)];
     }
 };
 
@@ -282,8 +287,10 @@ static HermiteIndex& hindex() {
     if (!init) {
         for (int d = 1; d <= 4; ++d) {
             enumerate(d, kRmax[d], h.list[d]);
-            for (size_t t = 0; t < h.list[d].size(); ++t)
-                h.index[d][std::vector<int>(h.list[d][t].a, h.list[d][t].a + d)] = (int)t;
+            int n = 1;
+            for (int i = 0; i < d; ++i) n *= 9;
+            h.code[d].assign(n, -1);
+            for (size_t t = 0; t < h.list[d].size(); ++t) h.code[d][HermiteIndex::key(d, h.list[d][t].a)] = (int)t;
         }
         init = true;
     }
@@ -378,6 +385,7 @@ struct kdefft_ctx_s {
     size_t tw_dev_n = 0;              // twiddles resident on the device
     DevBuf scratch, partial, items, tiles, out;
     HostBuf h_items, h_out;
+    bool staging_free = true;   // no copy out of h_items is pending on the stream
     // counters: kernel launches and host<->device bytes (always), per-kernel
     // CUDA-event times and algorithmic bytes/flops (when profiling is on)
     struct KStat {
@@ -386,6 +394,8 @@ struct kdefft_ctx_s {
     };
     bool prof = false;
     bool fused = true;    // d = 2: single cluster kernel per batch when it fits
+    int* errflag = nullptr;   // device flag: a bounded device-side wait gave up
+    int max_cluster = 16;     // largest cluster the fused engine may launch
     std::map<std::string, KStat> kstat;
     struct Pending {
         std::string name;
@@ -395,6 +405,22 @@ struct kdefft_ctx_s {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
     int64_t launches = 0, h2d = 0, d2h = 0;
+};
+
+#include <chrono>
+// wall time of a host phase, accumulated under "host:*" when profiling is on
+struct HostTimer {
+    kdefft_ctx c;
+    const char* name;
+    std::chrono::steady_clock::time_point t0;
+    HostTimer(kdefft_ctx c_, const char* n) : c(c_), name(n), t0(std::chrono::steady_clock::now()) {}
+    ~HostTimer() {
+        if (!c->prof) return;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        auto& k = c->kstat[name];
+        k.launches++;
+        k.ms += ms;
+    }
 };
 
 static cudaEvent_t ev_get(kdefft_ctx c) {
@@ -856,7 +882,8 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
     KCHK(c->h_items.ensure(bytes));
     KCHK(c->items.ensure(bytes));
     // the pinned staging buffer may still be read by a previous copy
-    KCU(cudaStreamSynchronize(c->stream));
+    if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
+    c->staging_free = false;
     unsigned char* h = (unsigned char*)c->h_items.p;
     std::memcpy(h, items.data(), bItems);
     size_t o = bItems;
@@ -931,17 +958,32 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
         prof_stop(c, ev, "reduce", 16.0 * nF, 2.0 * nF);
         KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
         KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
-        KCU(cudaStreamSynchronize(c->stream));
+        {
+            HostTimer w(c, "host:wait");
+            KCU(cudaStreamSynchronize(c->stream));
+        }
         c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
         std::memcpy(out_host, c->h_out.p, sizeof(double) * 2 * nitems);
     } else {
         KCU(cudaStreamSynchronize(c->stream));
     }
+    c->staging_free = true;
     prof_flush(c);
     return KDEFFT_OK;
 }
 
 static int cap_elems(bool dbl) { return dbl ? 3072 : 6144; }
+
+// read and clear the device error flag (after a stream synchronisation)
+static int check_errflag(kdefft_ctx c) {
+    int h = 0;
+    KCU(cudaMemcpy(&h, c->errflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        KCU(cudaMemset(c->errflag, 0, sizeof(int)));
+        return fail(KDEFFT_ERR_TIMEOUT, "a device-side wait for a bulk copy timed out");
+    }
+    return KDEFFT_OK;
+}
 
 // d = 2, kernel items only: one cluster launch does every pass and the
 // reduction.  Returns KDEFFT_ERR_UNSUPPORTED (without launching) when the
@@ -952,20 +994,27 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     using C = typename Cpx<real>::T;
     const int nitems = (int)items.size();
     const size_t budget = 200 * 1024;
+    int rmax = 0;
+    for (const Item<real>& it : items) rmax = std::max(rmax, it.R);
+    if (rmax > 4) return KDEFFT_ERR_UNSUPPORTED;
     int cs = 2;
-    while (cs < 8 && (long long)nitems * cs < 2LL * c->nsm) cs *= 2;
-    int slab = 0, cap = 0, pmax = 0;
+    while (cs < c->max_cluster && (long long)nitems * cs < 2LL * c->nsm) cs *= 2;
+    int gat = 0, spcn = 0, cap = 0, pmax = 0;
     for (;;) {
-        slab = cap = pmax = 0;
+        gat = spcn = cap = pmax = 0;
         for (const Item<real>& it : items) {
             const int P1 = it.ax[1].P, P0 = it.ax[0].P, Q1 = P1 / 2 + 1;
             const int lpc = (it.S[0] + cs - 1) / cs, cpc = (Q1 + cs - 1) / cs;
-            slab = std::max(slab, lpc * Q1);
+            gat = std::max(gat, it.S[0] * cpc);
+            spcn = std::max(spcn, cpc * P0);
             cap = std::max(cap, std::max(lpc * P1, cpc * P0));
             pmax = std::max(pmax, std::max(P0, P1));
         }
-        if (sizeof(C) * (size_t)(slab + 2 * pmax + 2 * cap) <= budget) break;
-        if (cs >= 8) return KDEFFT_ERR_UNSUPPORTED;
+        gat = (gat + 1) & ~1;   // keeps the spectrum rows that follow 16-byte aligned for the bulk copy
+        const size_t need = sizeof(C) * (size_t)(gat + 2 * pmax + 2 * (cap + cap / 16 + 1)) +
+                            sizeof(real) * (size_t)(spcn + 4);
+        if (need <= budget) break;
+        if (cs >= c->max_cluster) return KDEFFT_ERR_UNSUPPORTED;
         cs *= 2;
     }
     KCHK(sync_twiddles(c));
@@ -974,8 +1023,9 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     KCHK(c->items.ensure(bItems));
     KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
     KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
-    KCU(cudaStreamSynchronize(c->stream));
+    if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
     std::memcpy(c->h_items.p, items.data(), bItems);
+    c->staging_free = false;
     KCU(cudaMemcpyAsync(c->items.p, c->h_items.p, bItems, cudaMemcpyHostToDevice, c->stream));
     c->h2d += (int64_t)bItems;
     double fl = 0.0, by = 0.0;
@@ -986,14 +1036,25 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     }
     const C* tw = (const C*)(sizeof(real) == 4 ? c->tw32.p : c->tw64.p);
     cudaEvent_t ev = prof_start(c);
-    KCU(launch_fused2d<real>((const Item<real>*)c->items.p, nitems, cs, slab, cap, pmax, tw, (double*)c->out.p,
-                             c->stream));
+    cudaError_t le = launch_fused2d<real>((const Item<real>*)c->items.p, nitems, rmax, cs, gat, spcn, cap, pmax, tw,
+                                          (double*)c->out.p, c->errflag, c->stream);
+    if (le == cudaErrorNotSupported && cs > 8) {
+        // a 16-CTA cluster does not fit this footprint on this device: stay at 8
+        c->max_cluster = 8;
+        return launch_fused<real>(c, items, out_host);
+    }
+    KCU(le);
     prof_stop(c, ev, sizeof(real) == 4 ? "fused2d_f32" : "fused2d_f64", by, fl);
     KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaStreamSynchronize(c->stream));
+    {
+        HostTimer w(c, "host:wait");
+        KCU(cudaStreamSynchronize(c->stream));
+    }
+    c->staging_free = true;
     c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
     std::memcpy(out_host, c->h_out.p, sizeof(double) * 2 * nitems);
     prof_flush(c);
+    KCHK(check_errflag(c));
     return KDEFFT_OK;
 }
 
@@ -1057,75 +1118,82 @@ static int run_requests(kdefft_ctx c, ReqSet& rs) {
     size_t pi = 0;
     while (pi < pairs.size()) {
         std::vector<Item<real>> items;
-        PassLists pl;
         std::vector<std::pair<int, int>> batch;
-        while (pi < pairs.size()) {
-            const auto pr = pairs[pi];
-            const GridReq& g = rs.grids[pr.first];
-            const KSpec& sp = rs.specs[g.spec];
-            Item<real> it;
-            std::memset(&it, 0, sizeof(it));
-            it.d = d;
-            it.kind = 0;
-            KCHK(fill_axes(c, d, g.P, it));
-            long long ptot = 1;
-            for (int k = 0; k < d; ++k) {
-                it.S[k] = 2 * g.L[k] + 1;
-                it.off[k] = g.L[k];
-                it.delta[k] = (real)g.ds->delta[k];
-                ptot *= g.P[k];
-            }
-            it.nsig = sp.nsig;
-            for (int s = 0; s < sp.nsig; ++s) {
-                Mat inv;
-                double det;
-                if (!spd_inv_det(sp.sig[s], inv, det))
-                    return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
-                for (int a = 0; a < d; ++a)
-                    for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)inv(a, b);
-                it.nrm[s] = (real)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
-            }
-            int R = 0;
-            const int gi[2] = {pr.first, pr.second};
-            for (int h = 0; h < 2; ++h) {
-                if (gi[h] < 0) {
-                    it.nterm[h] = 0;
-                    continue;
+        long long scratch = 0;
+        {
+            HostTimer hb(c, "host:build");
+            while (pi < pairs.size()) {
+                const auto pr = pairs[pi];
+                const GridReq& g = rs.grids[pr.first];
+                const KSpec& sp = rs.specs[g.spec];
+                Item<real> it;
+                std::memset(&it, 0, sizeof(it));
+                it.d = d;
+                it.kind = 0;
+                KCHK(fill_axes(c, d, g.P, it));
+                long long ptot = 1;
+                for (int k = 0; k < d; ++k) {
+                    it.S[k] = 2 * g.L[k] + 1;
+                    it.off[k] = g.L[k];
+                    it.delta[k] = (real)g.ds->delta[k];
+                    ptot *= g.P[k];
                 }
-                const std::vector<Term>& tl = rs.grids[gi[h]].terms;
-                if ((int)tl.size() > MAXTERM) return fail(KDEFFT_ERR_UNSUPPORTED, "too many kernel terms");
-                it.nterm[h] = (int)tl.size();
-                for (size_t m = 0; m < tl.size(); ++m) {
-                    int o = 0;
-                    for (int k = 0; k < d; ++k) o += tl[m].alpha[k];
-                    if (o > kRmax[d]) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high for d");
-                    R = std::max(R, o);
-                    const int hidx = hx.idx(d, tl[m].alpha);
-                    it.tsig[h][m] = (short)tl[m].sig;
-                    it.the[h][m] = (short)hidx;
-                    it.tw8[h][m] = (real)(((o & 1) ? -1.0 : 1.0) * tl[m].w);
+                it.nsig = sp.nsig;
+                for (int s = 0; s < sp.nsig; ++s) {
+                    Mat inv;
+                    double det;
+                    if (!spd_inv_det(sp.sig[s], inv, det))
+                        return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
+                    for (int a = 0; a < d; ++a)
+                        for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)inv(a, b);
+                    it.nrm[s] = (real)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
                 }
+                int R = 0;
+                const int gi[2] = {pr.first, pr.second};
+                for (int h = 0; h < 2; ++h) {
+                    if (gi[h] < 0) {
+                        it.nterm[h] = 0;
+                        continue;
+                    }
+                    const std::vector<Term>& tl = rs.grids[gi[h]].terms;
+                    if ((int)tl.size() > MAXTERM) return fail(KDEFFT_ERR_UNSUPPORTED, "too many kernel terms");
+                    it.nterm[h] = (int)tl.size();
+                    for (size_t m = 0; m < tl.size(); ++m) {
+                        int o = 0;
+                        for (int k = 0; k < d; ++k) o += tl[m].alpha[k];
+                        if (o > kRmax[d]) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high for d");
+                        R = std::max(R, o);
+                        const int hidx = hx.idx(d, tl[m].alpha);
+                        it.tsig[h][m] = (short)tl[m].sig;
+                        it.the[h][m] = (short)hidx;
+                        it.tw8[h][m] = (real)(((o & 1) ? -1.0 : 1.0) * tl[m].w);
+                    }
+                }
+                it.R = R;
+                const real* spec = nullptr;
+                KCHK(ensure_spectrum<real>(g.ds, g.P, &spec));
+                it.spec = spec;
+                const double nn = (double)g.ds->n;
+                it.scale = 1.0 / (nn * nn * (double)ptot);
+                // would this item overflow the multi-pass scratch budget?
+                const long long need = scratch_need(it);
+                if (!items.empty() && scratch + need > budget) break;
+                scratch += need;
+                items.push_back(it);
+                batch.push_back(pr);
+                ++pi;
             }
-            it.R = R;
-            const real* spec = nullptr;
-            KCHK(ensure_spectrum<real>(g.ds, g.P, &spec));
-            it.spec = spec;
-            const double nn = (double)g.ds->n;
-            it.scale = 1.0 / (nn * nn * (double)ptot);
-            // would this item overflow the scratch budget?
-            if (!items.empty() && pl.scratch + scratch_need(it) > budget) break;
-            tile_item(it, (int)items.size(), cap, pl);
-            items.push_back(it);
-            batch.push_back(pr);
-            ++pi;
         }
         std::vector<double> out(2 * items.size());
         int fr = KDEFFT_ERR_UNSUPPORTED;
         if (d == 2 && c->fused) fr = launch_fused<real>(c, items, out.data());
-        if (fr == KDEFFT_ERR_UNSUPPORTED)
+        if (fr == KDEFFT_ERR_UNSUPPORTED) {
+            PassLists pl;
+            for (size_t i = 0; i < items.size(); ++i) tile_item(items[i], (int)i, cap, pl);
             KCHK(launch_items<real>(c, items, pl, d, out.data()));
-        else if (fr != KDEFFT_OK)
+        } else if (fr != KDEFFT_OK) {
             return fr;
+        }
         for (size_t i = 0; i < batch.size(); ++i) {
             rs.grids[batch[i].first].value = out[2 * i];
             if (batch[i].second >= 0) rs.grids[batch[i].second].value = out[2 * i + 1];
@@ -1293,6 +1361,10 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         return fail(KDEFFT_ERR_CUDA, "cudaGetDeviceProperties failed");
     }
     c->nsm = prop.multiProcessorCount;
+    if (cudaMalloc(&c->errflag, sizeof(int)) != cudaSuccess || cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) {
+        delete c;
+        return fail(KDEFFT_ERR_ALLOC, "error flag allocation failed");
+    }
     int r = upload_tables();
     if (r != KDEFFT_OK) {
         delete c;
@@ -1360,6 +1432,7 @@ int kdefft_destroy(kdefft_ctx c) {
         c->evpool.push_back(p.b);
     }
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    if (c->errflag) cudaFree(c->errflag);
     delete c;
     return KDEFFT_OK;
 }
@@ -1847,6 +1920,7 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
     // batched evaluation of value + theta-gradient for a list of theta
     auto evaluate = [&](const std::vector<std::vector<double>>& ths, std::vector<double>& f,
                         std::vector<std::vector<double>>& gt) -> int {
+        HostTimer ht(ds->ctx, "host:eval");
         const int m = (int)ths.size();
         f.assign(m, INFINITY);
         gt.assign(m, std::vector<double>(p, 0.0));

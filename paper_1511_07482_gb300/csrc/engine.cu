@@ -131,6 +131,19 @@ struct Dft<C, 8> {
     }
 };
 
+// n / D for n < 2^20 and 2 <= D <= 4096 as a multiply-high with
+// m = ceil(2^32 / D): the rounding error n (m D - 2^32) / 2^32 < n D / 2^32
+// stays below 1/D of the fractional gap, so the quotient is exact.
+__device__ __forceinline__ uint32_t magic_of(uint32_t D) { return 0xFFFFFFFFu / D + 1u; }
+
+// Line buffers in shared memory carry one pad element after every 16
+// complex values: logical index i lives at i + i/16.  Stockham stores with
+// stride R (R = 2, 4, 8) then fall on distinct banks instead of 2..16-way
+// conflicts; unit-stride accesses stay contiguous.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_cap(int cap) { return cap + (cap >> 4) + 1; }
+__device__ __forceinline__ uint32_t qdiv(uint32_t n, uint32_t m) { return __umulhi(n, m); }
+
 // One radix-R Stockham pass over nl lines of length P (dense, stride P).
 template <typename C, int R>
 __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int nl, int P,
@@ -138,30 +151,31 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
     const int Pr = P / R;
     const int total = nl * Pr;
     const int tws = P / (Ns * R);
+    const uint32_t mPr = magic_of((uint32_t)max(Pr, 2));
+    const uint32_t mNs = magic_of((uint32_t)max(Ns, 2));
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int line = t / Pr;
+        const int line = (Pr == 1) ? t : (int)qdiv((uint32_t)t, mPr);
         const int j = t - line * Pr;
-        const C* in = src + line * P;
-        C* out = dst + line * P;
-        const int k = j % Ns;
+        const int lb = line * P;
+        const int k = (Ns == 1) ? 0 : j - (int)qdiv((uint32_t)j, mNs) * Ns;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[j + r * Pr];
+        for (int r = 0; r < R; ++r) v[r] = src[pad(lb + j + r * Pr)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
         }
         Dft<C, R>::run(v);
-        const int base = (j - k) * R + k;
+        const int base = lb + (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) dst[pad(base + r * Ns)] = v[r];
     }
 }
 
 // Forward DFT of nl lines (length P) held in a; b is the other buffer.
 // Returns the buffer holding the result.  Ends with __syncthreads().
 template <typename C>
-__device__ C* smem_fft(C* a, C* b, int nl, const AxisPlan& ap, const C* tw) {
+__device__ __forceinline__ C* smem_fft(C* a, C* b, int nl, const AxisPlan& ap, const C* tw) {
     __syncthreads();
     int Ns = 1;
     C* src = a;
@@ -192,7 +206,7 @@ __device__ __forceinline__ void load_twiddles(C* tw, const C* pool, const AxisPl
 // ------------------------------------------------------------ kernel values
 // Value of the packed pair (grid A + i grid B) at lag vector j (d entries).
 template <typename real>
-__device__ void kernel_pair(const Item<real>& it, const int* j, real& va, real& vb) {
+__device__ __forceinline__ void kernel_pair(const Item<real>& it, const int* j, real& va, real& vb) {
     real x[MAXD];
     const int d = it.d;
 #pragma unroll
@@ -293,7 +307,7 @@ __device__ void spectral_sink(const Item<real>& it, const C* Y, int nl, int P, i
             // d = 1: the line index is the last axis itself (w is w_{d-1})
             const int wl = last_is_line ? w : q / wdiv;
             const real s = it.spec[(long long)q * P + w] * real(half_weight(wl, Plast));
-            const C y = Y[t];
+            const C y = Y[pad(t)];
             fa += s * y.x;
             fb += s * y.y;
             if (++cnt == 16) {
@@ -310,7 +324,7 @@ __device__ void spectral_sink(const Item<real>& it, const C* Y, int nl, int P, i
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int c = t / P;
             const int w = t - c * P;
-            const C y = Y[t];
+            const C y = Y[pad(t)];
             it.spec_out[(long long)(q0 + c) * P + w] = y.x * y.x + y.y * y.y;
         }
     }
@@ -325,8 +339,8 @@ __global__ void __launch_bounds__(256) k_stage_a(const Item<real>* __restrict__ 
     using C = typename Cpx<real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufa = reinterpret_cast<C*>(smem_raw);
-    C* bufb = bufa + cap;
-    C* tw = bufb + cap;
+    C* bufb = bufa + padded_cap(cap);
+    C* tw = bufb + padded_cap(cap);
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile tl = tiles[ti];
         const Item<real>& it = items[tl.item];
@@ -363,7 +377,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const Item<real>* __restrict__ 
                     v = C{va, vb};
                 }
             }
-            bufa[t] = v;
+            bufa[pad(t)] = v;
         }
         C* Y = smem_fft(bufa, bufb, nl, ap, tw);
         const int Q = P / 2 + 1;
@@ -374,12 +388,15 @@ __global__ void __launch_bounds__(256) k_stage_a(const Item<real>* __restrict__ 
             if (it.kind == 0) {
                 for (int w = threadIdx.x; w < Q; w += blockDim.x) {
                     const real s = it.spec[w] * real(half_weight(w, P));
-                    sa += (double)(s * Y[w].x);
-                    sb += (double)(s * Y[w].y);
+                    sa += (double)(s * Y[pad(w)].x);
+                    sb += (double)(s * Y[pad(w)].y);
                 }
                 block_reduce2<real>(sa, sb, partial + 2 * (long long)it.tileF0);
             } else {
-                for (int w = threadIdx.x; w < Q; w += blockDim.x) it.spec_out[w] = Y[w].x * Y[w].x + Y[w].y * Y[w].y;
+                for (int w = threadIdx.x; w < Q; w += blockDim.x) {
+                    const C y = Y[pad(w)];
+                    it.spec_out[w] = y.x * y.x + y.y * y.y;
+                }
             }
         } else {
             // write [w][line] for w < Q
@@ -389,7 +406,7 @@ __global__ void __launch_bounds__(256) k_stage_a(const Item<real>* __restrict__ 
             for (int t = threadIdx.x; t < nl * Q; t += blockDim.x) {
                 const int w = t / nl;
                 const int c = t - w * nl;
-                out[(long long)w * nlines_tot + tl.a + c] = Y[c * P + w];
+                out[(long long)w * nlines_tot + tl.a + c] = Y[pad(c * P + w)];
             }
         }
     }
@@ -404,8 +421,8 @@ __global__ void __launch_bounds__(256) k_mid(const Item<real>* __restrict__ item
     using C = typename Cpx<real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufa = reinterpret_cast<C*>(smem_raw);
-    C* bufb = bufa + cap;
-    C* tw = bufb + cap;
+    C* bufb = bufa + padded_cap(cap);
+    C* tw = bufb + padded_cap(cap);
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile tl = tiles[ti];
         const Item<real>& it = items[tl.item];
@@ -430,14 +447,14 @@ __global__ void __launch_bounds__(256) k_mid(const Item<real>* __restrict__ item
             if (idx >= P) idx -= P;
             C v = C{real(0), real(0)};
             if (idx < S) v = in[ibase + (long long)c * S + idx];
-            bufa[t] = v;
+            bufa[pad(t)] = v;
         }
         C* Y = smem_fft(bufa, bufb, nl, ap, tw);
         const long long obase = (long long)tl.a * P;
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int w = t / nl;
             const int c = t - w * nl;
-            out[(obase + w) * O + tl.b + c] = Y[c * P + w];
+            out[(obase + w) * O + tl.b + c] = Y[pad(c * P + w)];
         }
     }
 }
@@ -451,8 +468,8 @@ __global__ void __launch_bounds__(256) k_final(const Item<real>* __restrict__ it
     using C = typename Cpx<real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* bufa = reinterpret_cast<C*>(smem_raw);
-    C* bufb = bufa + cap;
-    C* tw = bufb + cap;
+    C* bufb = bufa + padded_cap(cap);
+    C* tw = bufb + padded_cap(cap);
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile tl = tiles[ti];
         const Item<real>& it = items[tl.item];
@@ -473,7 +490,7 @@ __global__ void __launch_bounds__(256) k_final(const Item<real>* __restrict__ it
             if (idx >= P) idx -= P;
             C v = C{real(0), real(0)};
             if (idx < S) v = in[(long long)(tl.a + c) * S + idx];
-            bufa[t] = v;
+            bufa[pad(t)] = v;
         }
         C* Y = smem_fft(bufa, bufb, nl, ap, tw);
         int wdiv = 1;
@@ -500,104 +517,305 @@ __global__ void k_reduce(const Item<real>* __restrict__ items, int nitems, const
     out[2 * i + 1] = b * it.scale;
 }
 
-// ------------------------------------------------------------ fused 2-D path (one cluster per item)
-// d = 2 only.  The CS CTAs of a cluster split the S_0 generated lines of the
-// axis-1 pass (k_stage_a's work) and keep their half spectra (w_1 <= P_1/2) in
-// shared memory; after a cluster barrier each CTA gathers the axis-0 lines of
-// its share of the w_1 columns from the other CTAs' shared memory
-// (distributed shared memory), transforms them and reduces against the
-// spectrum (k_final's work); the per-CTA partial sums meet in rank 0's shared
-// memory and rank 0 writes the item's two scaled sums (k_reduce's work).
+// ------------------------------------------------------------ compile-time Hermite recurrence
+// The same graded enumeration and recurrence as the constant-memory table,
+// generated at compile time for fixed (D, R) so that the polynomials live in
+// registers and every index is a constant.
+constexpr int cx_binom(int n, int k) {
+    long long c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return (int)c;
+}
+
+template <int D, int R>
+struct HTab {
+    static constexpr int N = cx_binom(D + R, D);
+    int al[N][D];
+    int piv[N];
+    int par[N];
+    int nred[N];
+    int rj[N][D];
+    int rc[N][D];
+    int ridx[N][D];
+    constexpr int index_of(const int* a) const {
+        for (int t = 0; t < N; ++t) {
+            bool eq = true;
+            for (int k = 0; k < D; ++k) eq = eq && (al[t][k] == a[k]);
+            if (eq) return t;
+        }
+        return -1;
+    }
+    constexpr HTab() : al(), piv(), par(), nred(), rj(), rc(), ridx() {
+        int n = 0;
+        for (int o = 0; o <= R; ++o) {
+            // all alpha with |alpha| = o, alpha_0 descending, then alpha_1, ...
+            int a[D] = {};
+            a[0] = o;
+            for (;;) {
+                int used = 0;
+                for (int k = 0; k < D - 1; ++k) used += a[k];
+                a[D - 1] = o - used;
+                if (a[D - 1] >= 0) {
+                    for (int k = 0; k < D; ++k) al[n][k] = a[k];
+                    ++n;
+                }
+                int k = D - 2;
+                for (; k >= 0; --k)
+                    if (a[k] > 0) break;
+                if (k < 0) break;
+                a[k]--;
+                int pre = 0;
+                for (int m = 0; m <= k; ++m) pre += a[m];
+                if (k + 1 <= D - 2) {
+                    a[k + 1] = o - pre;
+                    for (int m = k + 2; m <= D - 2; ++m) a[m] = 0;
+                }
+            }
+        }
+        for (int t = 1; t < N; ++t) {
+            int p = 0;
+            while (al[t][p] == 0) ++p;
+            int beta[D] = {};
+            for (int k = 0; k < D; ++k) beta[k] = al[t][k];
+            beta[p] -= 1;
+            piv[t] = p;
+            par[t] = index_of(beta);
+            for (int j = 0; j < D; ++j)
+                if (beta[j] > 0) {
+                    int g[D] = {};
+                    for (int k = 0; k < D; ++k) g[k] = beta[k];
+                    g[j] -= 1;
+                    rj[t][nred[t]] = j;
+                    rc[t][nred[t]] = beta[j];
+                    ridx[t][nred[t]] = index_of(g);
+                    nred[t]++;
+                }
+        }
+    }
+};
+
+// Work-item fields the fused kernel reads in its inner loops, staged in
+// shared memory once per CTA, with the kernel terms expanded into dense
+// weights W[grid][covariance][Hermite index] (sign (-1)^{|alpha|} included).
+constexpr int WDENSE = 15;   // C(2 + 4, 2): d = 2 up to order 4
 template <typename real>
-__global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ items, int cs, int slab_elems,
-                                                 int cap, int pmax, const typename Cpx<real>::T* __restrict__ twpool,
-                                                 double* __restrict__ out) {
+struct FusedItem {
+    int S0, S1, off0, off1, nsig;
+    real delta0, delta1;
+    real lam[MAXSIG][4];
+    real nrm[MAXSIG];
+    real W[2][MAXSIG][WDENSE];
+    AxisPlan a0, a1;
+    const real* spec;
+    double scale;
+};
+
+// value of the packed pair at lag (j0, j1), d = 2, orders <= R
+template <typename real, int R>
+__device__ __forceinline__ void kernel_pair_2d(const FusedItem<real>& f, int j0, int j1, real& va, real& vb) {
+    constexpr HTab<2, R> ht{};
+    constexpr int N = HTab<2, R>::N;
+    const real x0 = f.delta0 * real(j0), x1 = f.delta1 * real(j1);
+    real a = 0, b = 0;
+#pragma unroll
+    for (int s = 0; s < MAXSIG; ++s) {
+        if (s < f.nsig) {
+            const real z0 = f.lam[s][0] * x0 + f.lam[s][1] * x1;
+            const real z1 = f.lam[s][2] * x0 + f.lam[s][3] * x1;
+            const real e = f.nrm[s] * exp(real(-0.5) * (x0 * z0 + x1 * z1));
+            real He[N];
+            He[0] = real(1);
+#pragma unroll
+            for (int t = 1; t < N; ++t) {
+                real v = (ht.piv[t] == 0 ? z0 : z1) * He[ht.par[t]];
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (r < ht.nred[t]) v -= real(ht.rc[t][r]) * f.lam[s][ht.piv[t] * 2 + ht.rj[t][r]] * He[ht.ridx[t][r]];
+                He[t] = v;
+            }
+            real pa = 0, pb = 0;
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                pa += f.W[0][s][t] * He[t];
+                pb += f.W[1][s][t] * He[t];
+            }
+            a += e * pa;
+            b += e * pb;
+        }
+    }
+    va = a;
+    vb = b;
+}
+
+// ------------------------------------------------------------ fused 2-D path (one cluster per item)
+// d = 2 only.  The cs CTAs of a cluster split the S_0 generated lines of the
+// axis-1 pass (k_stage_a's work).  Each CTA pushes the half spectrum of its
+// lines (w_1 <= P_1/2) straight into the gather buffer of the CTA that owns
+// each w_1 column (distributed shared memory stores); after one cluster
+// barrier every CTA holds the S_0 inputs of its axis-0 lines locally,
+// transforms them and reduces against the count spectrum (k_final's work),
+// whose rows were staged into shared memory by one bulk (TMA) copy issued
+// at kernel start.  The per-CTA partial sums meet in rank 0's shared memory
+// and rank 0 writes the item's two scaled sums (k_reduce's work).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// bounded wait on an mbarrier phase; returns false when the limit is hit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <typename real, int R>
+__global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ items, int cs, int gat_elems,
+                                                 int spc_elems, int cap, int pmax,
+                                                 const typename Cpx<real>::T* __restrict__ twpool,
+                                                 double* __restrict__ out, int* __restrict__ errflag) {
     using C = typename Cpx<real>::T;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double cl_red[16][2];
-    C* slab = reinterpret_cast<C*>(smem_raw);
-    C* tw1 = slab + slab_elems;
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ FusedItem<real> f;
+    C* gat = reinterpret_cast<C*>(smem_raw);                 // [S_0][cpc] inputs of my axis-0 lines
+    real* spc = reinterpret_cast<real*>(gat + gat_elems);    // [cpc][P_0] my spectrum rows
+    C* tw1 = reinterpret_cast<C*>(spc + spc_elems);
     C* tw0 = tw1 + pmax;
     C* bufa = tw0 + pmax;
-    C* bufb = bufa + cap;
+    C* bufb = bufa + padded_cap(cap);
     const int rank = (int)cluster.block_rank();
     const int item = blockIdx.x / cs;
-    const Item<real>& it = items[item];
-    const AxisPlan& a1 = it.ax[1];
-    const AxisPlan& a0 = it.ax[0];
-    const int P1 = a1.P, P0 = a0.P, Q1 = P1 / 2 + 1;
-    const int S0 = it.S[0], S1 = it.S[1];
+    {
+        const Item<real>& it = items[item];
+        if (threadIdx.x == 0) {
+            f.S0 = it.S[0];
+            f.S1 = it.S[1];
+            f.off0 = it.off[0];
+            f.off1 = it.off[1];
+            f.nsig = it.nsig;
+            f.delta0 = it.delta[0];
+            f.delta1 = it.delta[1];
+            for (int q = 0; q < MAXSIG; ++q) {
+                f.lam[q][0] = it.lam[q][0];
+                f.lam[q][1] = it.lam[q][1];
+                f.lam[q][2] = it.lam[q][MAXD];
+                f.lam[q][3] = it.lam[q][MAXD + 1];
+                f.nrm[q] = it.nrm[q];
+            }
+            f.a0 = it.ax[0];
+            f.a1 = it.ax[1];
+            f.spec = it.spec;
+            f.scale = it.scale;
+        }
+        real* Wf = &f.W[0][0][0];
+        for (int t = threadIdx.x; t < 2 * MAXSIG * WDENSE; t += blockDim.x) Wf[t] = real(0);
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int h = threadIdx.x;
+            for (int m = 0; m < it.nterm[h]; ++m) f.W[h][it.tsig[h][m]][it.the[h][m]] += it.tw8[h][m];
+        }
+        __syncthreads();
+    }
+    const int P1 = f.a1.P, P0 = f.a0.P, Q1 = P1 / 2 + 1;
+    const int S0 = f.S0, S1 = f.S1;
     const int lpc = (S0 + cs - 1) / cs;
     const int cpc = (Q1 + cs - 1) / cs;
-    load_twiddles(tw1, twpool, a1);
-    load_twiddles(tw0, twpool, a0);
+    const int q0 = rank * cpc;
+    const int nq = max(0, min(Q1, q0 + cpc) - q0);
+    // ---- stage my spectrum rows [q0, q0 + nq) x P_0 into shared memory
+    const size_t sbytes = sizeof(real) * (size_t)nq * P0;
+    const real* sg = f.spec + (size_t)q0 * P0;
+    const bool bulk = nq > 0 && (sbytes % 16 == 0) && (((uintptr_t)sg) % 16 == 0);
+    const uint32_t bar = smem_u32(&mbar);
+    if (bulk && threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)sbytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(spc)),
+            "l"(sg), "r"((uint32_t)sbytes), "r"(bar)
+            : "memory");
+    } else if (!bulk) {
+        for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) spc[t] = sg[t];
+    }
+    load_twiddles(tw1, twpool, f.a1);
+    load_twiddles(tw0, twpool, f.a0);
     // ---- axis-1 pass over my generated lines
     const int l0 = rank * lpc;
     const int nl = max(0, min(S0, l0 + lpc) - l0);
+    const uint32_t mP1 = magic_of((uint32_t)P1), mQ1 = magic_of((uint32_t)Q1);
+    const uint32_t mcpc = magic_of((uint32_t)max(cpc, 2));
+    const int off0 = f.off0, off1 = f.off1;
     if (nl > 0) {
         for (int t = threadIdx.x; t < nl * P1; t += blockDim.x) {
-            const int c = t / P1;
+            const int c = (int)qdiv((uint32_t)t, mP1);
             const int p = t - c * P1;
-            int idx = p + it.off[1];
+            int idx = p + off1;
             if (idx >= P1) idx -= P1;
             C v = C{real(0), real(0)};
             if (idx < S1) {
-                int j[MAXD];
-                j[0] = l0 + c - it.off[0];
-                j[1] = idx - it.off[1];
                 real va, vb;
-                kernel_pair(it, j, va, vb);
+                kernel_pair_2d<real, R>(f, l0 + c - off0, idx - off1, va, vb);
                 v = C{va, vb};
             }
-            bufa[t] = v;
+            bufa[pad(t)] = v;
         }
-        C* Y = smem_fft(bufa, bufb, nl, a1, tw1);
+        C* Y = smem_fft(bufa, bufb, nl, f.a1, tw1);
+        // push (line, w_1) to the owner of column w_1: gat[line][w_1 - q0_owner]
         for (int t = threadIdx.x; t < nl * Q1; t += blockDim.x) {
-            const int c = t / Q1;
+            const int c = (int)qdiv((uint32_t)t, mQ1);
             const int q = t - c * Q1;
-            slab[c * Q1 + q] = Y[c * P1 + q];
+            const int dst = (cpc == 1) ? q : (int)qdiv((uint32_t)q, mcpc);
+            C* g = cluster.map_shared_rank(gat, dst);
+            g[(l0 + c) * cpc + (q - dst * cpc)] = Y[pad(c * P1 + q)];
         }
     }
     cluster.sync();
-    // ---- axis-0 pass over my columns, gathered from the cluster's slabs
-    const int q0 = rank * cpc;
-    const int nq = max(0, min(Q1, q0 + cpc) - q0);
+    // ---- axis-0 pass over my columns
     double sa = 0.0, sb = 0.0;
+    const uint32_t mP0 = magic_of((uint32_t)P0);
     if (nq > 0) {
         for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
-            const int c = t / P0;
+            const int c = (int)qdiv((uint32_t)t, mP0);
             const int p = t - c * P0;
-            int idx = p + it.off[0];
+            int idx = p + off0;
             if (idx >= P0) idx -= P0;
-            C v = C{real(0), real(0)};
-            if (idx < S0) {
-                const int src = idx / lpc;
-                const C* rs = cluster.map_shared_rank(slab, src);
-                v = rs[(idx - src * lpc) * Q1 + q0 + c];
-            }
-            bufa[t] = v;
+            bufa[pad(t)] = (idx < S0) ? gat[idx * cpc + c] : C{real(0), real(0)};
         }
-        C* Y = smem_fft(bufa, bufb, nq, a0, tw0);
-        real fa = 0, fb = 0;
-        int cnt = 0;
-        for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
-            const int c = t / P0;
-            const int w = t - c * P0;
-            const int q = q0 + c;
-            const real s = it.spec[(long long)q * P0 + w] * real(half_weight(q, P1));
-            const C y = Y[t];
-            fa += s * y.x;
-            fb += s * y.y;
-            if (++cnt == 16) {
-                sa += (double)fa;
-                sb += (double)fb;
-                fa = fb = 0;
-                cnt = 0;
+        C* Y = smem_fft(bufa, bufb, nq, f.a0, tw0);
+        if (bulk && !mbar_wait(bar, 0)) {
+            if (threadIdx.x == 0) atomicOr(errflag, 1);
+        } else {
+            real fa = 0, fb = 0;
+            int cnt = 0;
+            for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
+                const int c = (int)qdiv((uint32_t)t, mP0);
+                const int q = q0 + c;
+                const real s = spc[t] * real(half_weight(q, P1));
+                const C y = Y[pad(t)];
+                fa += s * y.x;
+                fb += s * y.y;
+                if (++cnt == 16) {
+                    sa += (double)fa;
+                    sb += (double)fb;
+                    fa = fb = 0;
+                    cnt = 0;
+                }
             }
+            sa += (double)fa;
+            sb += (double)fb;
         }
-        sa += (double)fa;
-        sb += (double)fb;
     }
     double part[2];
     block_reduce2<real>(sa, sb, part);
@@ -613,15 +831,15 @@ __global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ 
             a += cl_red[r][0];
             b += cl_red[r][1];
         }
-        out[2 * item] = a * it.scale;
-        out[2 * item + 1] = b * it.scale;
+        out[2 * item] = a * f.scale;
+        out[2 * item + 1] = b * f.scale;
     }
 }
 
 // ------------------------------------------------------------ launchers
 template <typename real>
 static size_t smem_bytes(int cap, int pmax) {
-    return sizeof(typename Cpx<real>::T) * (size_t)(2 * cap + pmax);
+    return sizeof(typename Cpx<real>::T) * (size_t)(2 * padded_cap(cap) + pmax);
 }
 
 template <typename real>
@@ -665,19 +883,21 @@ cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* par
 }
 
 
-template <typename real>
-cudaError_t launch_fused2d(const Item<real>* items, int nitems, int cs, int slab_elems, int cap, int pmax,
-                           const typename Cpx<real>::T* twpool, double* out, cudaStream_t st) {
+template <typename real, int R>
+static cudaError_t launch_fused2d_r(const Item<real>* items, int nitems, int cs, int gat_elems, int spc_elems,
+                                   int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
+                                   cudaStream_t st) {
     using C = typename Cpx<real>::T;
-    const size_t sm = sizeof(C) * (size_t)(slab_elems + 2 * pmax + 2 * cap);
-    static size_t set_bytes[2] = {0, 0};
-    const int ti = sizeof(real) == 4 ? 0 : 1;
-    if (sm > set_bytes[ti]) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused2d<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // spectrum rows are real; keep the complex buffers after them 16-byte aligned
+    const int spc_pad = (spc_elems + 3) & ~3;
+    const size_t sm = sizeof(C) * (size_t)(gat_elems + 2 * pmax + 2 * padded_cap(cap)) + sizeof(real) * (size_t)spc_pad;
+    static size_t set_bytes = 0;
+    if (sm > set_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_fused2d<real>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_fused2d<real, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
-        set_bytes[ti] = sm;
+        set_bytes = sm;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nitems * cs), 1, 1);
@@ -691,7 +911,29 @@ cudaError_t launch_fused2d(const Item<real>* items, int nitems, int cs, int slab
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fused2d<real>, items, cs, slab_elems, cap, pmax, twpool, out);
+    if (cs > 8) {
+        // clusters above the portable size must be schedulable with this shared-memory footprint
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_fused2d<real, R>, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            return cudaErrorNotSupported;
+        }
+    }
+    return cudaLaunchKernelEx(&cfg, k_fused2d<real, R>, items, cs, gat_elems, spc_pad, cap, pmax, twpool, out,
+                              errflag);
+}
+
+template <typename real>
+cudaError_t launch_fused2d(const Item<real>* items, int nitems, int rmax, int cs, int gat_elems, int spc_elems,
+                           int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
+                           cudaStream_t st) {
+    if (rmax <= 0)
+        return launch_fused2d_r<real, 0>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
+    if (rmax <= 2)
+        return launch_fused2d_r<real, 2>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
+    if (rmax <= 4)
+        return launch_fused2d_r<real, 4>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
+    return cudaErrorNotSupported;
 }
 
 #define KDEFFT_INST(real)                                                                                       \
@@ -705,8 +947,8 @@ cudaError_t launch_fused2d(const Item<real>* items, int nitems, int cs, int slab
                                             typename Cpx<real>::T*, const typename Cpx<real>::T*, double*,     \
                                             int, cudaStream_t);                                               \
     template cudaError_t launch_reduce<real>(const Item<real>*, int, const double*, double*, cudaStream_t);        \
-    template cudaError_t launch_fused2d<real>(const Item<real>*, int, int, int, int, int,                          \
-                                              const typename Cpx<real>::T*, double*, cudaStream_t);
+    template cudaError_t launch_fused2d<real>(const Item<real>*, int, int, int, int, int, int, int,                \
+                                              const typename Cpx<real>::T*, double*, int*, cudaStream_t);
 
 KDEFFT_INST(float)
 KDEFFT_INST(double)

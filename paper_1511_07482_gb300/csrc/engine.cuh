@@ -111,12 +111,17 @@ cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* par
                           cudaStream_t st);
 
 // d = 2: one thread-block cluster of cs CTAs per item does stage A, the
-// final pass and the reduction (out[2 i], out[2 i + 1], scaled).  slab_elems:
-// complex elements per CTA for the half spectra of its lines; cap: per
-// ping-pong buffer.
+// final pass and the reduction (out[2 i], out[2 i + 1], scaled).
+// gat_elems: complex elements per CTA for the inputs of its axis-0 lines
+// (S_0 x columns per CTA); spc_elems: reals for its spectrum rows (columns x
+// P_0); cap: per ping-pong buffer.  errflag: set to 1 if a bounded wait on
+// the spectrum copy gave up.
+// rmax: highest derivative order among the items' terms (<= 4; larger
+// orders return cudaErrorNotSupported and the caller uses the multi-pass path).
 template <typename real>
-cudaError_t launch_fused2d(const Item<real>* items, int nitems, int cs, int slab_elems, int cap, int pmax,
-                           const typename Cpx<real>::T* twpool, double* out, cudaStream_t st);
+cudaError_t launch_fused2d(const Item<real>* items, int nitems, int rmax, int cs, int gat_elems, int spc_elems,
+                           int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
+                           cudaStream_t st);
 
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
 
