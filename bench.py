@@ -139,19 +139,60 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synthetic.mixture_2d_large(seed=2 + 1000 * rank)
-    X_dev = torch.from_numpy(w.X).to(dev)
-    X_pin = torch.from_numpy(w.X).pin_memory()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx = Context(local)
     stream = torch.cuda.current_stream(dev)
+    if args.workload == "select2d":
+        w = synthetic.mixture_2d_large(seed=2 + 1000 * rank)
+        X_dev = torch.from_numpy(w.X).to(dev)
+        X_pin = torch.from_numpy(w.X).pin_memory()
 
-    def step(X):
-        ds = ctx.bin(X, w.lo, w.hi, w.M)
-        H1, f1, e1 = ds.select_H(LSCV, n_starts=args.n_starts, max_iter=args.max_iter)
-        H2, f2, e2 = ds.select_H(SCV, G=w.G, n_starts=args.n_starts, max_iter=args.max_iter)
-        ds.close()
-        return e1 + e2, (H1, f1, H2, f2)
+        def step(X):
+            ds = ctx.bin(X, w.lo, w.hi, w.M)
+            H1, f1, e1 = ds.select_H(LSCV, n_starts=args.n_starts, max_iter=args.max_iter)
+            H2, f2, e2 = ds.select_H(SCV, G=w.G, n_starts=args.n_starts, max_iter=args.max_iter)
+            ds.close()
+            return e1 + e2, (H1, f1, H2, f2)
+        workload_desc = (w.name + ": bin + full LSCV and SCV minimisation (3 free entries of H, adjoint "
+                         "gradients)")
+    elif args.workload == "psi4_3d":
+        w = synthetic.mixture_3d(seed=3 + 1000 * rank)
+        X_dev = torch.from_numpy(w.X).to(dev)
+        X_pin = torch.from_numpy(w.X).pin_memory()
+
+        def step(X):
+            ds = ctx.bin(X, w.lo, w.hi, w.M)
+            ds.psi(w.H, 4)
+            ds.close()
+            return len(w.H), None
+        workload_desc = w.name + ": bin + psi_4 (15 unique partials) for 256 candidate H in one call"
+    elif args.workload == "uneven512":
+        ws = synthetic.batched_uneven(base_seed=4 + 100000 * rank)
+        w = ws[0]
+        X_dev = [torch.from_numpy(v.X).to(dev) for v in ws]
+        X_pin = [torch.from_numpy(v.X).pin_memory() for v in ws]
+
+        def step(Xs):
+            dss = [ctx.bin(X, v.lo, v.hi, v.M) for X, v in zip(Xs, ws)]
+            ctx.batch_lscv(dss, [v.H for v in ws])
+            for ds in dss:
+                ds.close()
+            return 16 * len(ws), None
+        workload_desc = "512 bivariate datasets (n log-uniform 1e3..1e5, grids 64^2..256^2): bin + LSCV and " \
+                        "gradient for 16 H each in one batched call"
+    else:  # plugin4d
+        w = synthetic.mixture_4d(seed=5 + 1000 * rank, n_candidates=16)
+        X_dev = torch.from_numpy(w.X).to(dev)
+        X_pin = torch.from_numpy(w.X).pin_memory()
+        from paper_1511_07482_gb300 import P_FIXED
+
+        def step(X):
+            ds = ctx.bin(X, w.lo, w.hi, w.M, P_rule=P_FIXED, P_fixed=w.P)
+            ds.pi(w.H, w.G, grad=True)
+            ds.eta02(w.H, w.G)
+            ds.close()
+            return 2 * len(w.H), None
+        workload_desc = w.name + ": bin + psi_4(G) + PI(H) with gradient and eta_{0,2}(H, G) for 16 H"
 
     def barrier():
         if world > 1:
@@ -241,8 +282,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot[0].item() / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name + ": bin + full LSCV and SCV minimisation (3 free entries of H, "
-                               "adjoint gradients)", "n": w.n, "d": w.d, "grid": w.M,
+        "config": {"workload": workload_desc, "n": w.n, "d": w.d, "grid": w.M,
                    "n_starts": args.n_starts, "max_iter": args.max_iter, "precision": "fp32, fp64 reductions",
                    "l2": "flushed by a 256 MiB device write before every step",
                    "evals_per_step": evals / args.steps},
@@ -254,7 +294,7 @@ def run_ours(args):
         "host_times_ms": {k[5:]: round(v["ms"], 3) for k, v in kstats.items() if k.startswith("host:")},
         "clocks": clk,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == "select2d":
         out["cpu_baseline"] = cpu_baseline(w, args, res)
     print(json.dumps(out))
     if world > 1:
@@ -339,6 +379,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-starts", type=int, default=16)
+    ap.add_argument("--workload", default="select2d", choices=["select2d", "psi4_3d", "uneven512", "plugin4d"],
+                    help="select2d (default): the n=1e5 bivariate selection workload; the others time the "
+                         "batched 3-D psi_4, 512-dataset LSCV and 4-D plug-in configurations")
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

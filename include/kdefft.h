@@ -150,7 +150,9 @@ int kdefft_lscv(kdefft_ds ds, const double* H, int nH, double* val, double* grad
  * n^-1 (4 pi)^{-d/2} |H|^{-1/2} + n^-2 sum_ij [phi_{2H+2G} - 2 phi_{H+2G}
  * + phi_{2G}](X_i - X_j).  The paper names SCV (Sec. 3) and defers its
  * formula (Sec. 5) to Chacon & Duong; this is that source's Gaussian form.
- * val/grad as kdefft_lscv. */
+ * The three Gaussian sums are reduced separately and combined in FP64 (the
+ * full kernel integrates to zero); the phi_2G sum depends on G, L and P
+ * only and is cached on the dataset.  val/grad as kdefft_lscv. */
 int kdefft_scv(kdefft_ds ds, const double* H, int nH, const double* G,
                double* val, double* grad);
 

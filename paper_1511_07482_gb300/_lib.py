@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -174,9 +175,13 @@ class Context:
         _check(lib.kdefft_create(C.byref(h), int(device), C.c_void_p(stream or 0)))
         self.h = h
         self.device = device
+        self._datasets = weakref.WeakSet()
 
     def close(self):
+        """Destroy the context and every dataset still open on it."""
         if self.h:
+            for ds in list(self._datasets):
+                ds.h = None          # freed by kdefft_destroy below
             load().kdefft_destroy(self.h)
             self.h = None
 
@@ -220,7 +225,9 @@ class Context:
         h = C.c_void_p()
         _check(load().kdefft_bin(self.h, px, n, d, plo, phi, M_a.ctypes.data_as(C.c_void_p), C.byref(o),
                                  C.byref(h)))
-        return Dataset(self, h, d, [int(m) for m in M_a])
+        ds = Dataset(self, h, d, [int(m) for m in M_a])
+        self._datasets.add(ds)
+        return ds
 
     def batch_lscv(self, datasets, H_per_ds, grad=True):
         """LSCV (+ gradient) for many datasets in one batched launch sequence."""
@@ -244,9 +251,9 @@ class Dataset:
         self.ctx, self.h, self.d, self.M = ctx, h, d, M
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             load().kdefft_ds_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -405,6 +405,7 @@ struct kdefft_ctx_s {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
     int64_t launches = 0, h2d = 0, d2h = 0;
+    std::vector<kdefft_ds> datasets;   // live datasets; destroyed with the context
 };
 
 #include <chrono>
@@ -477,8 +478,10 @@ struct kdefft_ds_s {
     kdefft_opts opts;
     DevBuf counts;        // float or double
     DevBuf counts_i;      // int32 (simple binning)
+    DevBuf counts64;      // FP64 copy of FP32 counts, made on first FP64 use
     std::map<std::vector<int>, std::shared_ptr<DevBuf>> spectra;
     double cov[16] = {0}; // sample covariance (d x d, row-major)
+    std::map<std::vector<double>, double> c2g;   // SCV phi_2G sums by (G, L, P)
 };
 
 static int twiddle_offset(kdefft_ctx c, int P) {
@@ -528,6 +531,7 @@ struct GridReq {
     int L[4];
     int P[4];
     std::vector<Term> terms;
+    bool fp64 = false;     // evaluate in FP64 even on an FP32 dataset
     double value = 0.0;    // result: n^-2 sum_w |C|^2 K / prod P  (= Eq. 25)
 };
 
@@ -671,7 +675,13 @@ static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool gr
         g.terms = std::move(t);
         rs.grids.push_back(std::move(g));
     };
-    push({Term{0, {0}, 1.0}, Term{1, {0}, -2.0}, Term{2, {0}, 1.0}});
+    // value: the two H-dependent Gaussians as separate grids (one packed pair);
+    // their difference and the H-independent phi_2G sum are combined in FP64,
+    // because the full SCV kernel integrates to zero and its transform near
+    // w = 0 would cancel in FP32
+    push({Term{0, {0}, 1.0}});
+    push({Term{1, {0}, 1.0}});
+    rs.grids[first].fp64 = rs.grids[first + 1].fp64 = true;
     if (grad) {
         for (int a = 0; a < d; ++a)
             for (int b = a; b < d; ++b) {
@@ -1062,6 +1072,7 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
 template <typename real>
 static int ensure_spectrum(kdefft_ds ds, const int* P, const real** out) {
     std::vector<int> key(P, P + ds->d);
+    key.push_back((int)sizeof(real));
     auto it = ds->spectra.find(key);
     if (it != ds->spectra.end()) {
         *out = (const real*)it->second->p;
@@ -1079,7 +1090,18 @@ static int ensure_spectrum(kdefft_ds ds, const int* P, const real** out) {
         item.S[k] = (int)ds->M[k];
         item.off[k] = 0;
     }
-    item.counts = (const real*)ds->counts.p;
+    const bool ds64 = ds->opts.precision == KDEFFT_FP64;
+    if (sizeof(real) == 8 && !ds64) {
+        // FP64 work on an FP32 dataset: widen the counts once
+        if (!ds->counts64.p) {
+            KCHK(ds->counts64.ensure(sizeof(double) * (size_t)ds->ncells));
+            c->launches++;
+            KCU(launch_f32_to_f64((const float*)ds->counts.p, (double*)ds->counts64.p, ds->ncells, c->stream));
+        }
+        item.counts = (const real*)ds->counts64.p;
+    } else {
+        item.counts = (const real*)ds->counts.p;
+    }
     item.spec_out = (real*)buf->p;
     std::vector<Item<real>> items{item};
     PassLists pl;
@@ -1092,25 +1114,25 @@ static int ensure_spectrum(kdefft_ds ds, const int* P, const real** out) {
 
 // Evaluate every grid of rs (value = Eq. 25 for that lag kernel).
 template <typename real>
-static int run_requests(kdefft_ctx c, ReqSet& rs) {
-    if (rs.grids.empty()) return KDEFFT_OK;
-    const int d = rs.grids[0].ds->d;
+static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
+    if (sel.empty()) return KDEFFT_OK;
+    const int d = rs.grids[sel[0]].ds->d;
     HermiteIndex& hx = hindex();
-    // pair consecutive grids that share dataset, covariances and plan
+    // pair consecutive selected grids that share dataset, covariances and plan
     std::vector<std::pair<int, int>> pairs;
-    for (size_t i = 0; i < rs.grids.size();) {
-        const GridReq& a = rs.grids[i];
-        if (i + 1 < rs.grids.size()) {
-            const GridReq& b = rs.grids[i + 1];
+    for (size_t u = 0; u < sel.size();) {
+        const GridReq& a = rs.grids[sel[u]];
+        if (u + 1 < sel.size()) {
+            const GridReq& b = rs.grids[sel[u + 1]];
             if (b.ds == a.ds && b.spec == a.spec && std::memcmp(a.L, b.L, sizeof(a.L)) == 0 &&
                 std::memcmp(a.P, b.P, sizeof(a.P)) == 0) {
-                pairs.push_back({(int)i, (int)i + 1});
-                i += 2;
+                pairs.push_back({sel[u], sel[u + 1]});
+                u += 2;
                 continue;
             }
         }
-        pairs.push_back({(int)i, -1});
-        i += 1;
+        pairs.push_back({sel[u], -1});
+        u += 1;
     }
     const int cap = cap_elems(sizeof(real) == 8);
     // scratch budget per launch: split the items into batches
@@ -1135,7 +1157,7 @@ static int run_requests(kdefft_ctx c, ReqSet& rs) {
                 for (int k = 0; k < d; ++k) {
                     it.S[k] = 2 * g.L[k] + 1;
                     it.off[k] = g.L[k];
-                    it.delta[k] = (real)g.ds->delta[k];
+                    it.delta[k] = g.ds->delta[k];
                     ptot *= g.P[k];
                 }
                 it.nsig = sp.nsig;
@@ -1145,8 +1167,8 @@ static int run_requests(kdefft_ctx c, ReqSet& rs) {
                     if (!spd_inv_det(sp.sig[s], inv, det))
                         return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
                     for (int a = 0; a < d; ++a)
-                        for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)inv(a, b);
-                    it.nrm[s] = (real)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
+                        for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = inv(a, b);
+                    it.nrm[s] = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
                 }
                 int R = 0;
                 const int gi[2] = {pr.first, pr.second};
@@ -1202,10 +1224,17 @@ static int run_requests(kdefft_ctx c, ReqSet& rs) {
     return KDEFFT_OK;
 }
 
+// Evaluate all grids: FP64 datasets and grids marked fp64 in double, the
+// rest in float.
 static int run(kdefft_ctx c, ReqSet& rs) {
     if (rs.grids.empty()) return KDEFFT_OK;
-    if (rs.grids[0].ds->opts.precision == KDEFFT_FP64) return run_requests<double>(c, rs);
-    return run_requests<float>(c, rs);
+    std::vector<int> s32, s64;
+    for (size_t i = 0; i < rs.grids.size(); ++i) {
+        const GridReq& g = rs.grids[i];
+        ((g.fp64 || g.ds->opts.precision == KDEFFT_FP64) ? s64 : s32).push_back((int)i);
+    }
+    KCHK(run_requests<double>(c, rs, s64));
+    return run_requests<float>(c, rs, s32);
 }
 
 // ============================================================ objective assembly
@@ -1237,16 +1266,16 @@ static void assemble_lscv(kdefft_ds ds, const Mat& H, const GridReq* g, double* 
     }
 }
 
-static void assemble_scv(kdefft_ds ds, const Mat& H, const GridReq* g, double* val, double* grad) {
+static void assemble_scv(kdefft_ds ds, const Mat& H, const GridReq* g, double c2g, double* val, double* grad) {
     const int d = ds->d;
     const double n = (double)ds->n;
     Mat inv;
     double det;
     spd_inv_det(H, inv, det);
     const double r0 = std::pow(4.0 * M_PI, -0.5 * d) / std::sqrt(det);
-    *val = r0 / n + g[0].value;
+    *val = r0 / n + (g[0].value - 2.0 * g[1].value + c2g);
     if (grad) {
-        int gi = 1;
+        int gi = 2;
         for (int a = 0; a < d; ++a)
             for (int b = a; b < d; ++b) {
                 const double tie = (a == b) ? 1.0 : 2.0;
@@ -1314,6 +1343,16 @@ static int write_out(kdefft_ctx c, double* dst, const double* src, size_t count)
 }
 
 // ============================================================ C ABI
+static void ds_free(kdefft_ds ds) {
+    cudaSetDevice(ds->ctx->device);
+    cudaStreamSynchronize(ds->ctx->stream);
+    ds->counts.release();
+    ds->counts_i.release();
+    ds->counts64.release();
+    for (auto& kv : ds->spectra) kv.second->release();
+    delete ds;
+}
+
 extern "C" {
 
 int kdefft_opts_default(kdefft_opts* o) {
@@ -1418,6 +1457,8 @@ int kdefft_destroy(kdefft_ctx c) {
     if (!c) return KDEFFT_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    for (kdefft_ds ds : c->datasets) ds_free(ds);
+    c->datasets.clear();
     c->tw32.release();
     c->tw64.release();
     c->scratch.release();
@@ -1530,17 +1571,17 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     xbuf.release();
     misc.release();
     *out = ds.release();
+    c->datasets.push_back(*out);
     return KDEFFT_OK;
 }
 
 int kdefft_ds_destroy(kdefft_ds ds) {
     if (!ds) return KDEFFT_OK;
-    cudaSetDevice(ds->ctx->device);
-    cudaStreamSynchronize(ds->ctx->stream);
-    ds->counts.release();
-    ds->counts_i.release();
-    for (auto& kv : ds->spectra) kv.second->release();
-    delete ds;
+    auto& v = ds->ctx->datasets;
+    auto it = std::find(v.begin(), v.end(), ds);
+    if (it == v.end()) return fail(KDEFFT_ERR_ARG, "unknown or already destroyed dataset");
+    v.erase(it);
+    ds_free(ds);
     return KDEFFT_OK;
 }
 
@@ -1662,21 +1703,56 @@ static int eval_lscv(kdefft_ds ds, const double* H, int nH, std::vector<double>&
     return KDEFFT_OK;
 }
 
+// n^-2 sum sum phi_{2G}(X_i - X_j) at truncation L and padding P: the
+// H-independent SCV term, cached per dataset
+static std::vector<double> c2g_key(const Mat& G, const int* L, const int* P, int d) {
+    std::vector<double> k;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) k.push_back(G(a, b));
+    for (int i = 0; i < d; ++i) {
+        k.push_back(L[i]);
+        k.push_back(P[i]);
+    }
+    return k;
+}
+
 static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::vector<double>& val,
                     std::vector<double>* grad) {
     const int d = ds->d;
     ReqSet rs;
     std::vector<int> first(nH);
     std::vector<Mat> Hs(nH);
+    std::vector<std::vector<double>> keys(nH);
+    std::map<std::vector<double>, int> missing;   // key -> grid index of its phi_2G request
     for (int h = 0; h < nH; ++h) {
         KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
         KCHK(add_scv(rs, ds, Hs[h], G, grad != nullptr, first[h]));
+        const GridReq& g0 = rs.grids[first[h]];
+        keys[h] = c2g_key(G, g0.L, g0.P, d);
+        if (!ds->c2g.count(keys[h]) && !missing.count(keys[h])) {
+            KSpec sp;
+            sp.nsig = 1;
+            sp.sig[0] = scaled(2.0, G);
+            const int si = (int)rs.specs.size();
+            rs.specs.push_back(sp);
+            GridReq g;
+            g.ds = ds;
+            g.spec = si;
+            std::memcpy(g.L, g0.L, sizeof(g.L));
+            std::memcpy(g.P, g0.P, sizeof(g.P));
+            g.terms = {Term{0, {0}, 1.0}};
+            g.fp64 = true;
+            missing[keys[h]] = (int)rs.grids.size();
+            rs.grids.push_back(std::move(g));
+        }
     }
     KCHK(run(ds->ctx, rs));
+    for (auto& kv : missing) ds->c2g[kv.first] = rs.grids[kv.second].value;
     val.assign(nH, 0.0);
     if (grad) grad->assign((size_t)nH * d * d, 0.0);
     for (int h = 0; h < nH; ++h)
-        assemble_scv(ds, Hs[h], &rs.grids[first[h]], &val[h], grad ? grad->data() + (size_t)h * d * d : nullptr);
+        assemble_scv(ds, Hs[h], &rs.grids[first[h]], ds->c2g[keys[h]], &val[h],
+                     grad ? grad->data() + (size_t)h * d * d : nullptr);
     return KDEFFT_OK;
 }
 

@@ -115,6 +115,19 @@ __global__ void __launch_bounds__(256) k_bin_simple(const double* __restrict__ X
     if (nout) atomicAdd(outside, nout);
 }
 
+__global__ void k_f32_to_f64(const float* __restrict__ src, double* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_f32_to_f64<<<(int)b, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 template <typename real>
 __global__ void k_int_to_real(const int* __restrict__ src, real* __restrict__ dst, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

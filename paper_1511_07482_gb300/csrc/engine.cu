@@ -204,13 +204,30 @@ __device__ __forceinline__ void load_twiddles(C* tw, const C* pool, const AxisPl
 }
 
 // ------------------------------------------------------------ kernel values
+// exp(a) for an FP64 argument a: exp(a) = exp(a_hi) exp(a_lo) with a_hi = a
+// rounded to the working type and |a_lo| <= ulp(a_hi)/2, exp(a_lo) = 1 + a_lo
+// to second order; the argument's own rounding never enters.
+__device__ __forceinline__ float exp_of(double a) {
+    const float ah = (float)a;
+    const float al = (float)(a - (double)ah);
+    const float e = expf(ah);
+    return fmaf(e, al, e);
+}
+__device__ __forceinline__ double exp_of_d(double a) { return exp(a); }
+template <typename real>
+__device__ __forceinline__ real exp_arg(double a);
+template <>
+__device__ __forceinline__ float exp_arg<float>(double a) { return exp_of(a); }
+template <>
+__device__ __forceinline__ double exp_arg<double>(double a) { return exp(a); }
+
 // Value of the packed pair (grid A + i grid B) at lag vector j (d entries).
 template <typename real>
 __device__ __forceinline__ void kernel_pair(const Item<real>& it, const int* j, real& va, real& vb) {
-    real x[MAXD];
+    double x[MAXD];
     const int d = it.d;
 #pragma unroll
-    for (int k = 0; k < MAXD; ++k) x[k] = (k < d) ? it.delta[k] * real(j[k]) : real(0);
+    for (int k = 0; k < MAXD; ++k) x[k] = (k < d) ? it.delta[k] * (double)j[k] : 0.0;
     real He[MAXSIG][HMAX];
     real ex[MAXSIG];
     const int nh = c_hoff[d] - c_hoff[d - 1];  // entries for this d (max order)
@@ -225,25 +242,25 @@ __device__ __forceinline__ void kernel_pair(const Item<real>& it, const int* j, 
     }
     const HEnt* tab = c_htab + c_hoff[d - 1];
     for (int s = 0; s < it.nsig; ++s) {
-        const real* L = it.lam[s];
+        const double* L = it.lam[s];
         real z[MAXD];
-        real q = 0;
+        double q = 0;
 #pragma unroll
         for (int a = 0; a < MAXD; ++a) {
-            real acc = 0;
+            double acc = 0;
 #pragma unroll
             for (int b = 0; b < MAXD; ++b)
                 if (a < d && b < d) acc += L[a * MAXD + b] * x[b];
-            z[a] = acc;
+            z[a] = (real)acc;
             q += x[a] * acc;
         }
-        ex[s] = it.nrm[s] * exp(real(-0.5) * q);
+        ex[s] = (real)it.nrm[s] * exp_arg<real>(-0.5 * q);
         real* h = He[s];
         h[0] = real(1);
         for (int t = 1; t < ncount; ++t) {
             const HEnt e = tab[t];
             real v = z[e.piv] * h[e.par];
-            for (int r = 0; r < e.nred; ++r) v -= real(e.rc[r]) * L[e.piv * MAXD + e.rj[r]] * h[e.ridx[r]];
+            for (int r = 0; r < e.nred; ++r) v -= real(e.rc[r]) * (real)L[e.piv * MAXD + e.rj[r]] * h[e.ridx[r]];
             h[t] = v;
         }
     }
@@ -601,8 +618,9 @@ constexpr int WDENSE = 15;   // C(2 + 4, 2): d = 2 up to order 4
 template <typename real>
 struct FusedItem {
     int S0, S1, off0, off1, nsig;
-    real delta0, delta1;
-    real lam[MAXSIG][4];
+    double delta0, delta1;
+    double lam[MAXSIG][4];
+    real laml[MAXSIG][4];   // the same in the working type, for the Hermite recurrence
     real nrm[MAXSIG];
     real W[2][MAXSIG][WDENSE];
     AxisPlan a0, a1;
@@ -615,14 +633,15 @@ template <typename real, int R>
 __device__ __forceinline__ void kernel_pair_2d(const FusedItem<real>& f, int j0, int j1, real& va, real& vb) {
     constexpr HTab<2, R> ht{};
     constexpr int N = HTab<2, R>::N;
-    const real x0 = f.delta0 * real(j0), x1 = f.delta1 * real(j1);
+    const double x0 = f.delta0 * (double)j0, x1 = f.delta1 * (double)j1;
     real a = 0, b = 0;
 #pragma unroll
     for (int s = 0; s < MAXSIG; ++s) {
         if (s < f.nsig) {
-            const real z0 = f.lam[s][0] * x0 + f.lam[s][1] * x1;
-            const real z1 = f.lam[s][2] * x0 + f.lam[s][3] * x1;
-            const real e = f.nrm[s] * exp(real(-0.5) * (x0 * z0 + x1 * z1));
+            const double zd0 = f.lam[s][0] * x0 + f.lam[s][1] * x1;
+            const double zd1 = f.lam[s][2] * x0 + f.lam[s][3] * x1;
+            const real z0 = (real)zd0, z1 = (real)zd1;
+            const real e = f.nrm[s] * exp_arg<real>(-0.5 * (x0 * zd0 + x1 * zd1));
             real He[N];
             He[0] = real(1);
 #pragma unroll
@@ -630,7 +649,7 @@ __device__ __forceinline__ void kernel_pair_2d(const FusedItem<real>& f, int j0,
                 real v = (ht.piv[t] == 0 ? z0 : z1) * He[ht.par[t]];
 #pragma unroll
                 for (int r = 0; r < 2; ++r)
-                    if (r < ht.nred[t]) v -= real(ht.rc[t][r]) * f.lam[s][ht.piv[t] * 2 + ht.rj[t][r]] * He[ht.ridx[t][r]];
+                    if (r < ht.nred[t]) v -= real(ht.rc[t][r]) * f.laml[s][ht.piv[t] * 2 + ht.rj[t][r]] * He[ht.ridx[t][r]];
                 He[t] = v;
             }
             real pa = 0, pb = 0;
@@ -709,7 +728,8 @@ __global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ 
                 f.lam[q][1] = it.lam[q][1];
                 f.lam[q][2] = it.lam[q][MAXD];
                 f.lam[q][3] = it.lam[q][MAXD + 1];
-                f.nrm[q] = it.nrm[q];
+                for (int e = 0; e < 4; ++e) f.laml[q][e] = (real)f.lam[q][e];
+                f.nrm[q] = (real)it.nrm[q];
             }
             f.a0 = it.ax[0];
             f.a1 = it.ax[1];

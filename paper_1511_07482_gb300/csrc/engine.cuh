@@ -58,9 +58,9 @@ struct Item {
     int off[MAXD];              // position p = (idx - off) mod P
     int R;                      // highest derivative order in the terms
     int nsig;                   // distinct covariances
-    real lam[MAXSIG][MAXD * MAXD];   // Sigma^{-1}, row stride MAXD
-    real nrm[MAXSIG];           // (2 pi)^{-d/2} |Sigma|^{-1/2}
-    real delta[MAXD];           // bin widths (Eq. 16)
+    double lam[MAXSIG][MAXD * MAXD];   // Sigma^{-1}, row stride MAXD (FP64: the quadratic form is FP64)
+    double nrm[MAXSIG];         // (2 pi)^{-d/2} |Sigma|^{-1/2}
+    double delta[MAXD];         // bin widths (Eq. 16)
     int nterm[2];
     short tsig[2][MAXTERM];
     short the[2][MAXTERM];
@@ -144,6 +144,7 @@ cudaError_t launch_bin_simple(const double* X, long long n, const GridDesc& g, i
                               unsigned long long* outside, int nsm, cudaStream_t st);
 template <typename real>
 cudaError_t launch_int_to_real(const int* src, real* dst, long long n, cudaStream_t st);
+cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t st);
 // pass 0: out[k] += sum_i X_ik; pass 1: out[a*d+b] += sum_i (X_ia - mean_a)(X_ib - mean_b)
 cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
                            cudaStream_t st);

@@ -359,7 +359,7 @@ extern "C" int kdefft_lscv_noalloc(int d, const int64_t* M, const double* delta,
             it.ax[k].tw_off = tw_off[k];
             it.S[k] = (i == 0) ? (int)M[k] : 2 * L[k] + 1;
             it.off[k] = (i == 0) ? 0 : L[k];
-            it.delta[k] = (float)delta[k];
+            it.delta[k] = delta[k];
         }
         it.scale = 1.0 / ((double)n * (double)n * (double)ptot);
     }
@@ -370,11 +370,11 @@ extern "C" int kdefft_lscv_noalloc(int d, const int64_t* M, const double* delta,
         it.nsig = 2;
         for (int a = 0; a < d; ++a)
             for (int b = 0; b < d; ++b) {
-                it.lam[0][a * MAXD + b] = (float)inv2[a * 4 + b];
-                it.lam[1][a * MAXD + b] = (float)inv[a * 4 + b];
+                it.lam[0][a * MAXD + b] = inv2[a * 4 + b];
+                it.lam[1][a * MAXD + b] = inv[a * 4 + b];
             }
-        it.nrm[0] = (float)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det2));
-        it.nrm[1] = (float)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
+        it.nrm[0] = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det2);
+        it.nrm[1] = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
         int al[MAXD] = {0};
         float w0 = 1.0f, w1 = -2.0f;
         if (g > 0) {
