@@ -112,9 +112,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kname):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+def ncu_traffic(kname, alg_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu capture (dram__bytes_read
+    + write of one captured launch), scaled to this run's launches by their
+    algorithmic bytes; None when the capture predates the current kernel
+    source."""
     if not os.path.exists(PROFILE_FILE):
         return None
     try:
@@ -124,7 +126,9 @@ def ncu_traffic(kname):
     if d.get("kernel_source_hash") != kernel_hash():
         return None
     k = d.get("kernels", {}).get(kname)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    if k is None:
+        return None
+    return k["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
 
 
 # ------------------------------------------------------------------ our arm
@@ -180,6 +184,18 @@ def run_ours(args):
             return 16 * len(ws), None
         workload_desc = "512 bivariate datasets (n log-uniform 1e3..1e5, grids 64^2..256^2): bin + LSCV and " \
                         "gradient for 16 H each in one batched call"
+    elif args.workload == "lscv_batch16":
+        w = synthetic.mixture_2d_large(seed=2 + 1000 * rank)
+        X_dev = torch.from_numpy(w.X).to(dev)
+        X_pin = torch.from_numpy(w.X).pin_memory()
+
+        def step(X):
+            ds = ctx.bin(X, w.lo, w.hi, w.M)
+            for _ in range(20):
+                ds.lscv(w.H, grad=True)
+            ds.close()
+            return 20 * len(w.H), None
+        workload_desc = w.name + ": bin + 20 batches of LSCV and gradient at 16 candidate H"
     else:  # plugin4d
         w = synthetic.mixture_4d(seed=5 + 1000 * rank, n_candidates=16)
         X_dev = torch.from_numpy(w.X).to(dev)
@@ -276,7 +292,7 @@ def run_ours(args):
             roof = {"bound": "alu", "achieved": a_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": a_tf / alu_peak}
         roof.update({"kernel": kname, "peak_source": src, "launches": k["launches"],
                      "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": by,
-                     "algorithmic_flops_per_launch": fl, "traffic": ncu_traffic(kname),
+                     "algorithmic_flops_per_launch": fl, "traffic": ncu_traffic(kname, by),
                      "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kernels.values())})
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -379,7 +395,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-starts", type=int, default=16)
-    ap.add_argument("--workload", default="select2d", choices=["select2d", "psi4_3d", "uneven512", "plugin4d"],
+    ap.add_argument("--workload", default="select2d", choices=["select2d", "psi4_3d", "uneven512", "plugin4d", "lscv_batch16"],
                     help="select2d (default): the n=1e5 bivariate selection workload; the others time the "
                          "batched 3-D psi_4, 512-dataset LSCV and 4-D plug-in configurations")
     ap.add_argument("--max-iter", type=int, default=60)
