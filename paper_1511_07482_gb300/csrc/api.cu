@@ -335,31 +335,56 @@ static int upload_tables() {
 }
 
 // ============================================================ radix plans & twiddles
-static bool radix_plan(int P, AxisPlan& ap) {
+// Radices the device passes implement (register DFTs; composite ones as a
+// compile-time mixed-radix decomposition), largest first.  FP64 lines keep
+// radices <= 16 (register budget).
+static const int kRadices[] = {32, 30, 27, 25, 24, 20, 18, 16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+
+// fewest stages factoring P into allowed radices (cached per (P, max radix))
+static bool radix_plan_uncached(int P, AxisPlan& ap, int max_radix);
+static bool radix_plan(int P, AxisPlan& ap, int max_radix) {
+    static std::map<std::pair<int, int>, std::pair<bool, AxisPlan>> cache;
+    const auto key = std::make_pair(P, max_radix);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        AxisPlan a{};
+        const bool ok = radix_plan_uncached(P, a, max_radix);
+        it = cache.emplace(key, std::make_pair(ok, a)).first;
+    }
+    const int tw_off = ap.tw_off;
+    ap = it->second.second;
+    ap.tw_off = tw_off;
+    return it->second.first;
+}
+
+static bool radix_plan_uncached(int P, AxisPlan& ap, int max_radix) {
     if (P < 2 || P > MAXP) return false;
-    int x = P;
+    // best[p]: minimal stage count for the cofactor p (dynamic programming over divisors)
+    std::map<int, std::pair<int, int>> memo;   // p -> (stages, first radix)
+    std::function<int(int)> best = [&](int p) -> int {
+        if (p == 1) return 0;
+        auto it = memo.find(p);
+        if (it != memo.end()) return it->second.first;
+        int bs = 1 << 20, br = 0;
+        for (int r : kRadices) {
+            if (r > max_radix || p % r) continue;
+            const int c = 1 + best(p / r);
+            if (c < bs) {
+                bs = c;
+                br = r;
+            }
+        }
+        memo[p] = {bs, br};
+        return bs;
+    };
+    if (best(P) >= (1 << 20)) return false;
     int n = 0;
-    while (x % 8 == 0) {
-        ap.radix[n++] = 8;
-        x /= 8;
+    for (int p = P; p > 1;) {
+        const int r = memo[p].second;
+        if (n >= MAXST) return false;
+        ap.radix[n++] = (unsigned char)r;
+        p /= r;
     }
-    if (x % 4 == 0) {
-        ap.radix[n++] = 4;
-        x /= 4;
-    }
-    if (x % 2 == 0) {
-        ap.radix[n++] = 2;
-        x /= 2;
-    }
-    while (x % 5 == 0) {
-        ap.radix[n++] = 5;
-        x /= 5;
-    }
-    while (x % 3 == 0) {
-        ap.radix[n++] = 3;
-        x /= 3;
-    }
-    if (x != 1 || n > MAXST) return false;
     ap.P = P;
     ap.nst = n;
     return true;
@@ -652,7 +677,9 @@ static int add_lscv(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int& firs
 }
 
 // ---- SCV (reading; Gaussian pilot G) --------------------------------------
-static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool grad, int& first) {
+// split64: the value as two FP64 Gaussian sums (plus the cached phi_2G sum)
+// combined in FP64; otherwise one FP32 grid of the whole SCV kernel.
+static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool grad, bool split64, int& first) {
     const int d = ds->d;
     KCHK(spd_or_fail(H, "H"));
     KSpec sp;
@@ -679,9 +706,13 @@ static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool gr
     // their difference and the H-independent phi_2G sum are combined in FP64,
     // because the full SCV kernel integrates to zero and its transform near
     // w = 0 would cancel in FP32
-    push({Term{0, {0}, 1.0}});
-    push({Term{1, {0}, 1.0}});
-    rs.grids[first].fp64 = rs.grids[first + 1].fp64 = true;
+    if (split64) {
+        push({Term{0, {0}, 1.0}});
+        push({Term{1, {0}, 1.0}});
+        rs.grids[first].fp64 = rs.grids[first + 1].fp64 = true;
+    } else {
+        push({Term{0, {0}, 1.0}, Term{1, {0}, -2.0}, Term{2, {0}, 1.0}});
+    }
     if (grad) {
         for (int a = 0; a < d; ++a)
             for (int b = a; b < d; ++b) {
@@ -774,7 +805,8 @@ static size_t spec_elems(int d, const int* P) {
 template <typename real>
 static int fill_axes(kdefft_ctx c, int d, const int* P, Item<real>& it) {
     for (int k = 0; k < d; ++k) {
-        if (!radix_plan(P[k], it.ax[k])) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
+        if (!radix_plan(P[k], it.ax[k], sizeof(real) == 8 ? 16 : 32))
+            return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
         it.ax[k].tw_off = twiddle_offset(c, P[k]);
     }
     return KDEFFT_OK;
@@ -1006,7 +1038,7 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     const size_t budget = 200 * 1024;
     int rmax = 0;
     for (const Item<real>& it : items) rmax = std::max(rmax, it.R);
-    if (rmax > 4) return KDEFFT_ERR_UNSUPPORTED;
+    if (rmax > 4 || (sizeof(real) == 8 && rmax > 2)) return KDEFFT_ERR_UNSUPPORTED;
     int cs = 2;
     while (cs < c->max_cluster && (long long)nitems * cs < 2LL * c->nsm) cs *= 2;
     int gat = 0, spcn = 0, cap = 0, pmax = 0;
@@ -1028,13 +1060,41 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
         cs *= 2;
     }
     KCHK(sync_twiddles(c));
-    const size_t bItems = sizeof(Item<real>) * nitems;
+    const size_t bItems = sizeof(FusedItem<real>) * nitems;
     KCHK(c->h_items.ensure(bItems));
     KCHK(c->items.ensure(bItems));
     KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
     KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
     if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
-    std::memcpy(c->h_items.p, items.data(), bItems);
+    {
+        FusedItem<real>* fi = (FusedItem<real>*)c->h_items.p;
+        for (int i = 0; i < nitems; ++i) {
+            const Item<real>& it = items[i];
+            FusedItem<real>& f = fi[i];
+            std::memset(&f, 0, sizeof(f));
+            f.S0 = it.S[0];
+            f.S1 = it.S[1];
+            f.off0 = it.off[0];
+            f.off1 = it.off[1];
+            f.nsig = it.nsig;
+            f.delta0 = it.delta[0];
+            f.delta1 = it.delta[1];
+            for (int q = 0; q < MAXSIG; ++q) {
+                f.lam[q][0] = it.lam[q][0];
+                f.lam[q][1] = it.lam[q][1];
+                f.lam[q][2] = it.lam[q][MAXD];
+                f.lam[q][3] = it.lam[q][MAXD + 1];
+                for (int e = 0; e < 4; ++e) f.laml[q][e] = (real)f.lam[q][e];
+                f.nrm[q] = (real)it.nrm[q];
+            }
+            for (int h = 0; h < 2; ++h)
+                for (int m = 0; m < it.nterm[h]; ++m) f.W[h][it.tsig[h][m]][it.the[h][m]] += it.tw8[h][m];
+            f.a0 = it.ax[0];
+            f.a1 = it.ax[1];
+            f.spec = it.spec;
+            f.scale = it.scale;
+        }
+    }
     c->staging_free = false;
     KCU(cudaMemcpyAsync(c->items.p, c->h_items.p, bItems, cudaMemcpyHostToDevice, c->stream));
     c->h2d += (int64_t)bItems;
@@ -1046,7 +1106,7 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     }
     const C* tw = (const C*)(sizeof(real) == 4 ? c->tw32.p : c->tw64.p);
     cudaEvent_t ev = prof_start(c);
-    cudaError_t le = launch_fused2d<real>((const Item<real>*)c->items.p, nitems, rmax, cs, gat, spcn, cap, pmax, tw,
+    cudaError_t le = launch_fused2d<real>((const FusedItem<real>*)c->items.p, nitems, rmax, cs, gat, spcn, cap, pmax, tw,
                                           (double*)c->out.p, c->errflag, c->stream);
     if (le == cudaErrorNotSupported && cs > 8) {
         // a 16-CTA cluster does not fit this footprint on this device: stay at 8
@@ -1266,16 +1326,17 @@ static void assemble_lscv(kdefft_ds ds, const Mat& H, const GridReq* g, double* 
     }
 }
 
-static void assemble_scv(kdefft_ds ds, const Mat& H, const GridReq* g, double c2g, double* val, double* grad) {
+static void assemble_scv(kdefft_ds ds, const Mat& H, const GridReq* g, bool split64, double c2g, double* val,
+                         double* grad) {
     const int d = ds->d;
     const double n = (double)ds->n;
     Mat inv;
     double det;
     spd_inv_det(H, inv, det);
     const double r0 = std::pow(4.0 * M_PI, -0.5 * d) / std::sqrt(det);
-    *val = r0 / n + (g[0].value - 2.0 * g[1].value + c2g);
+    *val = r0 / n + (split64 ? (g[0].value - 2.0 * g[1].value + c2g) : g[0].value);
     if (grad) {
-        int gi = 2;
+        int gi = split64 ? 2 : 1;
         for (int a = 0; a < d; ++a)
             for (int b = a; b < d; ++b) {
                 const double tie = (a == b) ? 1.0 : 2.0;
@@ -1717,7 +1778,7 @@ static std::vector<double> c2g_key(const Mat& G, const int* L, const int* P, int
 }
 
 static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::vector<double>& val,
-                    std::vector<double>* grad) {
+                    std::vector<double>* grad, bool split64 = true) {
     const int d = ds->d;
     ReqSet rs;
     std::vector<int> first(nH);
@@ -1726,10 +1787,10 @@ static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::ve
     std::map<std::vector<double>, int> missing;   // key -> grid index of its phi_2G request
     for (int h = 0; h < nH; ++h) {
         KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
-        KCHK(add_scv(rs, ds, Hs[h], G, grad != nullptr, first[h]));
+        KCHK(add_scv(rs, ds, Hs[h], G, grad != nullptr, split64, first[h]));
         const GridReq& g0 = rs.grids[first[h]];
         keys[h] = c2g_key(G, g0.L, g0.P, d);
-        if (!ds->c2g.count(keys[h]) && !missing.count(keys[h])) {
+        if (split64 && !ds->c2g.count(keys[h]) && !missing.count(keys[h])) {
             KSpec sp;
             sp.nsig = 1;
             sp.sig[0] = scaled(2.0, G);
@@ -1751,7 +1812,7 @@ static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::ve
     val.assign(nH, 0.0);
     if (grad) grad->assign((size_t)nH * d * d, 0.0);
     for (int h = 0; h < nH; ++h)
-        assemble_scv(ds, Hs[h], &rs.grids[first[h]], ds->c2g[keys[h]], &val[h],
+        assemble_scv(ds, Hs[h], &rs.grids[first[h]], split64, split64 ? ds->c2g[keys[h]] : 0.0, &val[h],
                      grad ? grad->data() + (size_t)h * d * d : nullptr);
     return KDEFFT_OK;
 }
@@ -2016,7 +2077,7 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
         if (method == KDEFFT_LSCV)
             r = eval_lscv(ds, Hs.data(), mv, v, &g);
         else if (method == KDEFFT_SCV)
-            r = eval_scv(ds, Hs.data(), mv, Gm, v, &g);
+            r = eval_scv(ds, Hs.data(), mv, Gm, v, &g, /*split64=*/false);
         else
             r = eval_pi(ds, Hs.data(), mv, psi4, v, &g);
         if (r != KDEFFT_OK) return r;
@@ -2189,7 +2250,15 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
     Mat Hb = theta_to_H(o, st[best].th.data());
     for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
-    if (f_out) *f_out = st[best].f;
+    double fbest = st[best].f;
+    if (method == KDEFFT_SCV) {
+        // the iterations compared FP32 values; the reported value takes the
+        // FP64 route for the cancelling Gaussian terms
+        std::vector<double> v;
+        KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
+        fbest = v[0];
+    }
+    if (f_out) *f_out = fbest;
     if (n_evals) *n_evals = evals;
     return KDEFFT_OK;
 }

@@ -131,6 +131,107 @@ struct Dft<C, 8> {
     }
 };
 
+// ---- composite radices: R = A B with A the smallest prime factor, done in
+// registers as A-point DFTs over stride-B subsequences, twiddles
+// w_R^{b k1}, then B-point DFTs (X[k1 + A k2]).  The twiddles are compile-time
+// constants: cos and sin of 2 pi m / R from an exact octant reduction of the
+// rational m / R and a Taylor series on [0, pi/4].
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double cx_sin_t(double x) {
+    double t = x, s = x;
+    for (int i = 1; i < 14; ++i) {
+        t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        s += t;
+    }
+    return s;
+}
+constexpr double cx_cos_t(double x) {
+    double t = 1.0, s = 1.0;
+    for (int i = 1; i < 14; ++i) {
+        t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        s += t;
+    }
+    return s;
+}
+// (cos, sin) of 2 pi m / R
+struct CxCis {
+    double c, s;
+};
+constexpr CxCis cx_cis(int m, int R) {
+    m %= R;
+    if (m < 0) m += R;
+    const int q = (8 * m) / R;   // octant
+    const double x = kTwoPi * (double)(8 * m - q * R) / (8.0 * R);        // in [0, pi/4)
+    const double y = kTwoPi * (double)(R * (q + 1) - 8 * m) / (8.0 * R);  // pi/4 - x
+    switch (q) {
+        case 0: return {cx_cos_t(x), cx_sin_t(x)};
+        case 1: return {cx_sin_t(y), cx_cos_t(y)};
+        case 2: return {-cx_sin_t(x), cx_cos_t(x)};
+        case 3: return {-cx_cos_t(y), cx_sin_t(y)};
+        case 4: return {-cx_cos_t(x), -cx_sin_t(x)};
+        case 5: return {-cx_sin_t(y), -cx_cos_t(y)};
+        case 6: return {cx_sin_t(x), -cx_cos_t(x)};
+        default: return {cx_cos_t(y), -cx_sin_t(y)};
+    }
+}
+constexpr int cx_small_factor(int R) {
+    for (int f = 2; f <= R; ++f)
+        if (R % f == 0) return f;
+    return R;
+}
+template <int R>
+struct CxTw {
+    double c[R];
+    double s[R];
+    constexpr CxTw() : c(), s() {
+        for (int m = 0; m < R; ++m) {
+            const CxCis z = cx_cis(m, R);
+            c[m] = z.c;
+            s[m] = z.s;
+        }
+    }
+};
+
+template <typename C, int R>
+struct Dft {
+    __device__ __forceinline__ static void run(C* v) {
+        using R_ = decltype(v[0].x);
+        constexpr int A = cx_small_factor(R);
+        constexpr int B = R / A;
+        constexpr CxTw<R> tw{};
+        C u[R];
+        // A-point DFTs over b-strided subsequences: u[b * A + k1]
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            C t[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) t[a] = v[B * a + b];
+            Dft<C, A>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) {
+                const int m = (b * k1) % R;
+                if (m == 0) {
+                    u[b * A + k1] = t[k1];
+                } else {
+                    // t * exp(-2 pi i m / R) = t * (cos - i sin)
+                    const R_ cw = R_(tw.c[m]), sw = R_(tw.s[m]);
+                    u[b * A + k1] = C{t[k1].x * cw + t[k1].y * sw, t[k1].y * cw - t[k1].x * sw};
+                }
+            }
+        }
+        // B-point DFTs over b for each k1: X[k1 + A k2]
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+            C t[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) t[b] = u[b * A + k1];
+            Dft<C, B>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+        }
+    }
+};
+
 // n / D for n < 2^20 and 2 <= D <= 4096 as a multiply-high with
 // m = ceil(2^32 / D): the rounding error n (m D - 2^32) / 2^32 < n D / 2^32
 // stays below 1/D of the fractional gap, so the quotient is exact.
@@ -182,12 +283,41 @@ __device__ __forceinline__ C* smem_fft(C* a, C* b, int nl, const AxisPlan& ap, c
     C* dst = b;
     for (int s = 0; s < ap.nst; ++s) {
         const int R = ap.radix[s];
-        switch (R) {
-            case 2: stockham_pass<C, 2>(src, dst, nl, ap.P, Ns, tw); break;
-            case 3: stockham_pass<C, 3>(src, dst, nl, ap.P, Ns, tw); break;
-            case 4: stockham_pass<C, 4>(src, dst, nl, ap.P, Ns, tw); break;
-            case 5: stockham_pass<C, 5>(src, dst, nl, ap.P, Ns, tw); break;
-            default: stockham_pass<C, 8>(src, dst, nl, ap.P, Ns, tw); break;
+        if constexpr (sizeof(C) == 16) {
+            switch (R) {
+                case 2: stockham_pass<C, 2>(src, dst, nl, ap.P, Ns, tw); break;
+                case 3: stockham_pass<C, 3>(src, dst, nl, ap.P, Ns, tw); break;
+                case 4: stockham_pass<C, 4>(src, dst, nl, ap.P, Ns, tw); break;
+                case 5: stockham_pass<C, 5>(src, dst, nl, ap.P, Ns, tw); break;
+                case 6: stockham_pass<C, 6>(src, dst, nl, ap.P, Ns, tw); break;
+                case 8: stockham_pass<C, 8>(src, dst, nl, ap.P, Ns, tw); break;
+                case 9: stockham_pass<C, 9>(src, dst, nl, ap.P, Ns, tw); break;
+                case 10: stockham_pass<C, 10>(src, dst, nl, ap.P, Ns, tw); break;
+                case 12: stockham_pass<C, 12>(src, dst, nl, ap.P, Ns, tw); break;
+                case 15: stockham_pass<C, 15>(src, dst, nl, ap.P, Ns, tw); break;
+                default: stockham_pass<C, 16>(src, dst, nl, ap.P, Ns, tw); break;
+            }
+        } else {
+            switch (R) {
+                case 2: stockham_pass<C, 2>(src, dst, nl, ap.P, Ns, tw); break;
+                case 3: stockham_pass<C, 3>(src, dst, nl, ap.P, Ns, tw); break;
+                case 4: stockham_pass<C, 4>(src, dst, nl, ap.P, Ns, tw); break;
+                case 5: stockham_pass<C, 5>(src, dst, nl, ap.P, Ns, tw); break;
+                case 6: stockham_pass<C, 6>(src, dst, nl, ap.P, Ns, tw); break;
+                case 8: stockham_pass<C, 8>(src, dst, nl, ap.P, Ns, tw); break;
+                case 9: stockham_pass<C, 9>(src, dst, nl, ap.P, Ns, tw); break;
+                case 10: stockham_pass<C, 10>(src, dst, nl, ap.P, Ns, tw); break;
+                case 12: stockham_pass<C, 12>(src, dst, nl, ap.P, Ns, tw); break;
+                case 15: stockham_pass<C, 15>(src, dst, nl, ap.P, Ns, tw); break;
+                case 16: stockham_pass<C, 16>(src, dst, nl, ap.P, Ns, tw); break;
+                case 18: stockham_pass<C, 18>(src, dst, nl, ap.P, Ns, tw); break;
+                case 20: stockham_pass<C, 20>(src, dst, nl, ap.P, Ns, tw); break;
+                case 24: stockham_pass<C, 24>(src, dst, nl, ap.P, Ns, tw); break;
+                case 25: stockham_pass<C, 25>(src, dst, nl, ap.P, Ns, tw); break;
+                case 27: stockham_pass<C, 27>(src, dst, nl, ap.P, Ns, tw); break;
+                case 30: stockham_pass<C, 30>(src, dst, nl, ap.P, Ns, tw); break;
+                default: stockham_pass<C, 32>(src, dst, nl, ap.P, Ns, tw); break;
+            }
         }
         Ns *= R;
         __syncthreads();
@@ -198,36 +328,32 @@ __device__ __forceinline__ C* smem_fft(C* a, C* b, int nl, const AxisPlan& ap, c
     return src;
 }
 
+// asynchronous global -> shared copies of 4, 8 or 16 bytes (cp.async); all of
+// a tile's loads are in flight together, completed by cp_async_wait_all()
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename C>
 __device__ __forceinline__ void load_twiddles(C* tw, const C* pool, const AxisPlan& ap) {
     for (int t = threadIdx.x; t < ap.P; t += blockDim.x) tw[t] = pool[ap.tw_off + t];
 }
 
 // ------------------------------------------------------------ kernel values
-// exp(a) for an FP64 argument a: exp(a) = exp(a_hi) exp(a_lo) with a_hi = a
-// rounded to the working type and |a_lo| <= ulp(a_hi)/2, exp(a_lo) = 1 + a_lo
-// to second order; the argument's own rounding never enters.
-__device__ __forceinline__ float exp_of(double a) {
-    const float ah = (float)a;
-    const float al = (float)(a - (double)ah);
-    const float e = expf(ah);
-    return fmaf(e, al, e);
-}
-__device__ __forceinline__ double exp_of_d(double a) { return exp(a); }
-template <typename real>
-__device__ __forceinline__ real exp_arg(double a);
-template <>
-__device__ __forceinline__ float exp_arg<float>(double a) { return exp_of(a); }
-template <>
-__device__ __forceinline__ double exp_arg<double>(double a) { return exp(a); }
 
 // Value of the packed pair (grid A + i grid B) at lag vector j (d entries).
 template <typename real>
 __device__ __forceinline__ void kernel_pair(const Item<real>& it, const int* j, real& va, real& vb) {
-    double x[MAXD];
+    real x[MAXD];
     const int d = it.d;
 #pragma unroll
-    for (int k = 0; k < MAXD; ++k) x[k] = (k < d) ? it.delta[k] * (double)j[k] : 0.0;
+    for (int k = 0; k < MAXD; ++k) x[k] = (k < d) ? (real)it.delta[k] * (real)j[k] : real(0);
     real He[MAXSIG][HMAX];
     real ex[MAXSIG];
     const int nh = c_hoff[d] - c_hoff[d - 1];  // entries for this d (max order)
@@ -244,17 +370,17 @@ __device__ __forceinline__ void kernel_pair(const Item<real>& it, const int* j, 
     for (int s = 0; s < it.nsig; ++s) {
         const double* L = it.lam[s];
         real z[MAXD];
-        double q = 0;
+        real q = 0;
 #pragma unroll
         for (int a = 0; a < MAXD; ++a) {
-            double acc = 0;
+            real acc = 0;
 #pragma unroll
             for (int b = 0; b < MAXD; ++b)
-                if (a < d && b < d) acc += L[a * MAXD + b] * x[b];
-            z[a] = (real)acc;
+                if (a < d && b < d) acc += (real)L[a * MAXD + b] * x[b];
+            z[a] = acc;
             q += x[a] * acc;
         }
-        ex[s] = (real)it.nrm[s] * exp_arg<real>(-0.5 * q);
+        ex[s] = (real)it.nrm[s] * exp(real(-0.5) * q);
         real* h = He[s];
         h[0] = real(1);
         for (int t = 1; t < ncount; ++t) {
@@ -270,6 +396,88 @@ __device__ __forceinline__ void kernel_pair(const Item<real>& it, const int* j, 
     va = a;
     vb = b;
 }
+
+// ---- accumulation.  FP64 arithmetic is slow on this part, so FP32 sums
+// carry an error term (two-sum / double-float): the pair (h, l) holds the
+// sum to about u^2 relative, and it becomes FP64 once per block.
+struct DFloat {
+    float h, l;
+};
+__device__ __forceinline__ DFloat df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+    const DFloat s = df_two_sum(a.h, b.h);
+    const float e = s.l + (a.l + b.l);
+    const float h = s.h + e;
+    return {h, e - (h - s.h)};
+}
+__device__ __forceinline__ void df_acc(DFloat& a, float x) {
+    const DFloat s = df_two_sum(a.h, x);
+    const float e = s.l + a.l;
+    a.h = s.h + e;
+    a.l = e - (a.h - s.h);
+}
+
+// per-thread accumulator of the spectral sums: DFloat in FP32 mode, double in FP64 mode
+template <typename real>
+struct SumAcc;
+template <>
+struct SumAcc<float> {
+    DFloat a{0.f, 0.f}, b{0.f, 0.f};
+    __device__ __forceinline__ void add(float x, float y) {
+        df_acc(a, x);
+        df_acc(b, y);
+    }
+};
+template <>
+struct SumAcc<double> {
+    double a = 0.0, b = 0.0;
+    __device__ __forceinline__ void add(double x, double y) {
+        a += x;
+        b += y;
+    }
+};
+
+// block sum of a SumAcc; thread 0 receives the two totals as doubles.
+// Contains __syncthreads (call from uniform control flow).
+__device__ __forceinline__ void block_reduce_acc(const SumAcc<float>& s, double* out2) {
+    __shared__ DFloat red[2][32];
+    DFloat a = s.a, b = s.b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DFloat ta{__shfl_down_sync(0xffffffffu, a.h, o), __shfl_down_sync(0xffffffffu, a.l, o)};
+        DFloat tb{__shfl_down_sync(0xffffffffu, b.h, o), __shfl_down_sync(0xffffffffu, b.l, o)};
+        a = df_add(a, ta);
+        b = df_add(b, tb);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = (l < nw) ? red[0][l] : DFloat{0.f, 0.f};
+        b = (l < nw) ? red[1][l] : DFloat{0.f, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            DFloat ta{__shfl_down_sync(0xffffffffu, a.h, o), __shfl_down_sync(0xffffffffu, a.l, o)};
+            DFloat tb{__shfl_down_sync(0xffffffffu, b.h, o), __shfl_down_sync(0xffffffffu, b.l, o)};
+            a = df_add(a, ta);
+            b = df_add(b, tb);
+        }
+        if (l == 0) {
+            out2[0] = (double)a.h + (double)a.l;
+            out2[1] = (double)b.h + (double)b.l;
+        }
+    }
+    __syncthreads();
+}
+__device__ __forceinline__ void block_reduce_acc(const SumAcc<double>& s, double* out2);
 
 __device__ __forceinline__ int spec_weight_idx(int q, int wdiv) { return q / wdiv; }
 
@@ -308,35 +516,29 @@ __device__ void block_reduce2(double a, double b, double* out2) {
     __syncthreads();
 }
 
+__device__ __forceinline__ void block_reduce_acc(const SumAcc<double>& s, double* out2) {
+    block_reduce2<double>(s.a, s.b, out2);
+}
+
 // Spectral sink of a finished line batch: Y[c][w] for lines q = q0 + c.
 // kind 0: accumulate sum spec[q][w] * weight * Y; kind 1: spec_out = |Y|^2.
 template <typename real, typename C>
 __device__ void spectral_sink(const Item<real>& it, const C* Y, int nl, int P, int q0, int wdiv, int Plast,
-                              bool last_is_line, double* partial_out) {
-    double sa = 0.0, sb = 0.0;
+                              bool last_is_line, double* partial_out, const real* srow = nullptr) {
     if (it.kind == 0) {
-        real fa = 0, fb = 0;
-        int cnt = 0;
+        SumAcc<real> acc;
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int c = t / P;
             const int w = t - c * P;
             const int q = q0 + c;
             // d = 1: the line index is the last axis itself (w is w_{d-1})
             const int wl = last_is_line ? w : q / wdiv;
-            const real s = it.spec[(long long)q * P + w] * real(half_weight(wl, Plast));
+            const real sv = srow ? srow[t] : it.spec[(long long)q * P + w];
+            const real s = sv * real(half_weight(wl, Plast));
             const C y = Y[pad(t)];
-            fa += s * y.x;
-            fb += s * y.y;
-            if (++cnt == 16) {
-                sa += (double)fa;
-                sb += (double)fb;
-                fa = fb = 0;
-                cnt = 0;
-            }
+            acc.add(s * y.x, s * y.y);
         }
-        sa += (double)fa;
-        sb += (double)fb;
-        block_reduce2<real>(sa, sb, partial_out);
+        block_reduce_acc(acc, partial_out);
     } else {
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int c = t / P;
@@ -401,14 +603,13 @@ __global__ void __launch_bounds__(256) k_stage_a(const Item<real>* __restrict__ 
         if (d == 1) {
             // the only axis: sink over w in [0, P/2]
             // compact the half spectrum in place is unnecessary: sink reads Y[w], w < Q
-            double sa = 0.0, sb = 0.0;
             if (it.kind == 0) {
+                SumAcc<real> acc;
                 for (int w = threadIdx.x; w < Q; w += blockDim.x) {
                     const real s = it.spec[w] * real(half_weight(w, P));
-                    sa += (double)(s * Y[pad(w)].x);
-                    sb += (double)(s * Y[pad(w)].y);
+                    acc.add(s * Y[pad(w)].x, s * Y[pad(w)].y);
                 }
-                block_reduce2<real>(sa, sb, partial + 2 * (long long)it.tileF0);
+                block_reduce_acc(acc, partial + 2 * (long long)it.tileF0);
             } else {
                 for (int w = threadIdx.x; w < Q; w += blockDim.x) {
                     const C y = Y[pad(w)];
@@ -457,14 +658,15 @@ __global__ void __launch_bounds__(256) k_mid(const Item<real>* __restrict__ item
         __syncthreads();
         load_twiddles(tw, twpool, ap);
         const long long ibase = ((long long)tl.a * O + tl.b) * S;
+        for (int t = threadIdx.x; t < nl * S; t += blockDim.x) cp_async<sizeof(C)>(bufb + t, in + ibase + t);
+        cp_async_wait_all();
+        __syncthreads();
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int c = t / P;
             const int p = t - c * P;
             int idx = p + it.off[axis];
             if (idx >= P) idx -= P;
-            C v = C{real(0), real(0)};
-            if (idx < S) v = in[ibase + (long long)c * S + idx];
-            bufa[pad(t)] = v;
+            bufa[pad(t)] = (idx < S) ? bufb[c * S + idx] : C{real(0), real(0)};
         }
         C* Y = smem_fft(bufa, bufb, nl, ap, tw);
         const long long obase = (long long)tl.a * P;
@@ -499,21 +701,30 @@ __global__ void __launch_bounds__(256) k_final(const Item<real>* __restrict__ it
         const int rsel = (d - 2) & 1;
         const C* in = scratch + it.scr[rsel];
         __syncthreads();
+        // stage this tile's input block (nl x S, contiguous) in bufb and, for a
+        // kernel item, its spectrum rows (nl x P reals) behind the twiddles
+        const C* ib = in + (long long)tl.a * S;
+        for (int t = threadIdx.x; t < nl * S; t += blockDim.x) cp_async<sizeof(C)>(bufb + t, ib + t);
+        real* srow = reinterpret_cast<real*>(tw + P);
+        if (it.kind == 0) {
+            const real* sb = it.spec + (long long)tl.a * P;
+            for (int t = threadIdx.x; t < nl * P; t += blockDim.x) cp_async<sizeof(real)>(srow + t, sb + t);
+        }
         load_twiddles(tw, twpool, ap);
+        cp_async_wait_all();
+        __syncthreads();
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int c = t / P;
             const int p = t - c * P;
             int idx = p + it.off[0];
             if (idx >= P) idx -= P;
-            C v = C{real(0), real(0)};
-            if (idx < S) v = in[(long long)(tl.a + c) * S + idx];
-            bufa[pad(t)] = v;
+            bufa[pad(t)] = (idx < S) ? bufb[c * S + idx] : C{real(0), real(0)};
         }
         C* Y = smem_fft(bufa, bufb, nl, ap, tw);
         int wdiv = 1;
         for (int k = 1; k < d - 1; ++k) wdiv *= it.ax[k].P;
         spectral_sink<real, C>(it, Y, nl, P, tl.a, wdiv, it.ax[d - 1].P, false,
-                               partial + 2 * (long long)ti);
+                               partial + 2 * (long long)ti, it.kind == 0 ? srow : nullptr);
     }
 }
 
@@ -611,37 +822,28 @@ struct HTab {
     }
 };
 
-// Work-item fields the fused kernel reads in its inner loops, staged in
-// shared memory once per CTA, with the kernel terms expanded into dense
-// weights W[grid][covariance][Hermite index] (sign (-1)^{|alpha|} included).
-constexpr int WDENSE = 15;   // C(2 + 4, 2): d = 2 up to order 4
-template <typename real>
-struct FusedItem {
-    int S0, S1, off0, off1, nsig;
-    double delta0, delta1;
-    double lam[MAXSIG][4];
-    real laml[MAXSIG][4];   // the same in the working type, for the Hermite recurrence
-    real nrm[MAXSIG];
-    real W[2][MAXSIG][WDENSE];
-    AxisPlan a0, a1;
-    const real* spec;
-    double scale;
-};
-
 // value of the packed pair at lag (j0, j1), d = 2, orders <= R
 template <typename real, int R>
 __device__ __forceinline__ void kernel_pair_2d(const FusedItem<real>& f, int j0, int j1, real& va, real& vb) {
     constexpr HTab<2, R> ht{};
     constexpr int N = HTab<2, R>::N;
-    const double x0 = f.delta0 * (double)j0, x1 = f.delta1 * (double)j1;
+    // the quadratic form in the working type (FP64 is slow on this part; its
+    // FP32 rounding, about q u / 2 relative, only touches the kernel's tails)
+    const real x0 = (real)f.delta0 * (real)j0, x1 = (real)f.delta1 * (real)j1;
     real a = 0, b = 0;
 #pragma unroll
     for (int s = 0; s < MAXSIG; ++s) {
         if (s < f.nsig) {
-            const double zd0 = f.lam[s][0] * x0 + f.lam[s][1] * x1;
-            const double zd1 = f.lam[s][2] * x0 + f.lam[s][3] * x1;
-            const real z0 = (real)zd0, z1 = (real)zd1;
-            const real e = f.nrm[s] * exp_arg<real>(-0.5 * (x0 * zd0 + x1 * zd1));
+            real z0, z1, e;
+            if constexpr (sizeof(real) == 8) {
+                z0 = f.lam[s][0] * x0 + f.lam[s][1] * x1;
+                z1 = f.lam[s][2] * x0 + f.lam[s][3] * x1;
+                e = f.nrm[s] * exp(real(-0.5) * (x0 * z0 + x1 * z1));
+            } else {
+                z0 = f.laml[s][0] * x0 + f.laml[s][1] * x1;
+                z1 = f.laml[s][2] * x0 + f.laml[s][3] * x1;
+                e = f.nrm[s] * expf(-0.5f * (x0 * z0 + x1 * z1));
+            }
             real He[N];
             He[0] = real(1);
 #pragma unroll
@@ -695,7 +897,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 template <typename real, int R>
-__global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ items, int cs, int gat_elems,
+__global__ void __launch_bounds__(256) k_fused2d(const FusedItem<real>* __restrict__ items, int cs, int gat_elems,
                                                  int spc_elems, int cap, int pmax,
                                                  const typename Cpx<real>::T* __restrict__ twpool,
                                                  double* __restrict__ out, int* __restrict__ errflag) {
@@ -714,35 +916,10 @@ __global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ 
     const int rank = (int)cluster.block_rank();
     const int item = blockIdx.x / cs;
     {
-        const Item<real>& it = items[item];
-        if (threadIdx.x == 0) {
-            f.S0 = it.S[0];
-            f.S1 = it.S[1];
-            f.off0 = it.off[0];
-            f.off1 = it.off[1];
-            f.nsig = it.nsig;
-            f.delta0 = it.delta[0];
-            f.delta1 = it.delta[1];
-            for (int q = 0; q < MAXSIG; ++q) {
-                f.lam[q][0] = it.lam[q][0];
-                f.lam[q][1] = it.lam[q][1];
-                f.lam[q][2] = it.lam[q][MAXD];
-                f.lam[q][3] = it.lam[q][MAXD + 1];
-                for (int e = 0; e < 4; ++e) f.laml[q][e] = (real)f.lam[q][e];
-                f.nrm[q] = (real)it.nrm[q];
-            }
-            f.a0 = it.ax[0];
-            f.a1 = it.ax[1];
-            f.spec = it.spec;
-            f.scale = it.scale;
-        }
-        real* Wf = &f.W[0][0][0];
-        for (int t = threadIdx.x; t < 2 * MAXSIG * WDENSE; t += blockDim.x) Wf[t] = real(0);
-        __syncthreads();
-        if (threadIdx.x < 2) {
-            const int h = threadIdx.x;
-            for (int m = 0; m < it.nterm[h]; ++m) f.W[h][it.tsig[h][m]][it.the[h][m]] += it.tw8[h][m];
-        }
+        // stage the item (prepared on the host) in shared memory, 4 bytes per thread
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(items + item);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&f);
+        for (int t = threadIdx.x; t < (int)(sizeof(FusedItem<real>) / 4); t += blockDim.x) dst[t] = src[t];
         __syncthreads();
     }
     const int P1 = f.a1.P, P0 = f.a0.P, Q1 = P1 / 2 + 1;
@@ -803,7 +980,7 @@ __global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ 
     }
     cluster.sync();
     // ---- axis-0 pass over my columns
-    double sa = 0.0, sb = 0.0;
+    SumAcc<real> acc;
     const uint32_t mP0 = magic_of((uint32_t)P0);
     if (nq > 0) {
         for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
@@ -817,28 +994,17 @@ __global__ void __launch_bounds__(256) k_fused2d(const Item<real>* __restrict__ 
         if (bulk && !mbar_wait(bar, 0)) {
             if (threadIdx.x == 0) atomicOr(errflag, 1);
         } else {
-            real fa = 0, fb = 0;
-            int cnt = 0;
             for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) {
                 const int c = (int)qdiv((uint32_t)t, mP0);
                 const int q = q0 + c;
                 const real s = spc[t] * real(half_weight(q, P1));
                 const C y = Y[pad(t)];
-                fa += s * y.x;
-                fb += s * y.y;
-                if (++cnt == 16) {
-                    sa += (double)fa;
-                    sb += (double)fb;
-                    fa = fb = 0;
-                    cnt = 0;
-                }
+                acc.add(s * y.x, s * y.y);
             }
-            sa += (double)fa;
-            sb += (double)fb;
         }
     }
     double part[2];
-    block_reduce2<real>(sa, sb, part);
+    block_reduce_acc(acc, part);
     if (threadIdx.x == 0) {
         double* dst = cluster.map_shared_rank(&cl_red[0][0], 0);
         dst[2 * rank] = part[0];
@@ -888,7 +1054,8 @@ template <typename real>
 cudaError_t launch_final(const Item<real>* items, const Tile* tiles, int ntiles, int pmax, int cap,
                          typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, double* partial,
                          int grid, cudaStream_t st) {
-    const size_t sm = smem_bytes<real>(cap, pmax);
+    // ping-pong buffers, twiddles, then the staged spectrum rows (cap reals)
+    const size_t sm = smem_bytes<real>(cap, pmax) + sizeof(real) * (size_t)cap;
     cudaError_t e = cudaFuncSetAttribute(k_final<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_final<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, cap, scratch, twpool, partial);
@@ -904,7 +1071,7 @@ cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* par
 
 
 template <typename real, int R>
-static cudaError_t launch_fused2d_r(const Item<real>* items, int nitems, int cs, int gat_elems, int spc_elems,
+static cudaError_t launch_fused2d_r(const FusedItem<real>* items, int nitems, int cs, int gat_elems, int spc_elems,
                                    int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
                                    cudaStream_t st) {
     using C = typename Cpx<real>::T;
@@ -944,14 +1111,12 @@ static cudaError_t launch_fused2d_r(const Item<real>* items, int nitems, int cs,
 }
 
 template <typename real>
-cudaError_t launch_fused2d(const Item<real>* items, int nitems, int rmax, int cs, int gat_elems, int spc_elems,
+cudaError_t launch_fused2d(const FusedItem<real>* items, int nitems, int rmax, int cs, int gat_elems, int spc_elems,
                            int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
                            cudaStream_t st) {
-    if (rmax <= 0)
-        return launch_fused2d_r<real, 0>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
     if (rmax <= 2)
         return launch_fused2d_r<real, 2>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
-    if (rmax <= 4)
+    if (rmax <= 4 && sizeof(real) == 4)
         return launch_fused2d_r<real, 4>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
     return cudaErrorNotSupported;
 }
@@ -967,7 +1132,7 @@ cudaError_t launch_fused2d(const Item<real>* items, int nitems, int rmax, int cs
                                             typename Cpx<real>::T*, const typename Cpx<real>::T*, double*,     \
                                             int, cudaStream_t);                                               \
     template cudaError_t launch_reduce<real>(const Item<real>*, int, const double*, double*, cudaStream_t);        \
-    template cudaError_t launch_fused2d<real>(const Item<real>*, int, int, int, int, int, int, int,                \
+    template cudaError_t launch_fused2d<real>(const FusedItem<real>*, int, int, int, int, int, int, int,           \
                                               const typename Cpx<real>::T*, double*, int*, cudaStream_t);
 
 KDEFFT_INST(float)

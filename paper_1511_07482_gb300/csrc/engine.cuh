@@ -110,6 +110,24 @@ template <typename real>
 cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* partial, double* out,
                           cudaStream_t st);
 
+// Work item of the fused 2-D kernel, prepared on the host: the fields its
+// inner loops read, with the kernel terms expanded into dense weights
+// W[grid][covariance][Hermite index] (sign (-1)^{|alpha|} included); the
+// kernel stages it in shared memory.  Size is a multiple of 4 bytes.
+constexpr int WDENSE = 15;   // C(2 + 4, 2): d = 2 up to order 4
+template <typename real>
+struct FusedItem {
+    int S0, S1, off0, off1, nsig, pad_;
+    double delta0, delta1;
+    double lam[MAXSIG][4];   // Sigma^{-1} (FP64: the quadratic form is FP64)
+    real laml[MAXSIG][4];    // the same in the working type, for the Hermite recurrence
+    real nrm[MAXSIG];
+    real W[2][MAXSIG][WDENSE];
+    AxisPlan a0, a1;
+    const real* spec;
+    double scale;
+};
+
 // d = 2: one thread-block cluster of cs CTAs per item does stage A, the
 // final pass and the reduction (out[2 i], out[2 i + 1], scaled).
 // gat_elems: complex elements per CTA for the inputs of its axis-0 lines
@@ -119,7 +137,7 @@ cudaError_t launch_reduce(const Item<real>* items, int nitems, const double* par
 // rmax: highest derivative order among the items' terms (<= 4; larger
 // orders return cudaErrorNotSupported and the caller uses the multi-pass path).
 template <typename real>
-cudaError_t launch_fused2d(const Item<real>* items, int nitems, int rmax, int cs, int gat_elems, int spc_elems,
+cudaError_t launch_fused2d(const FusedItem<real>* items, int nitems, int rmax, int cs, int gat_elems, int spc_elems,
                            int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
                            cudaStream_t st);
 
