@@ -194,12 +194,16 @@ int kdefft_batch_lscv(kdefft_ctx ctx, int nds, const kdefft_ds* ds,
                       const int* nH_per_ds, const double* H,
                       double* val, double* grad);
 
-/* Engine selection for the per-bandwidth transforms.  AUTO (default): for
- * d = 2 one thread-block-cluster kernel per batch does all passes in shared
- * and distributed shared memory whenever the work fits, else the multi-pass
- * path; MULTIPASS: always the pass-per-axis kernels with a global scratch
- * between passes (used for d >= 3).  Both compute the same sums. */
-enum { KDEFFT_ENGINE_AUTO = 0, KDEFFT_ENGINE_MULTIPASS = 1 };
+/* Engine selection.  AUTO (default): for d = 2 one thread-block-cluster
+ * kernel per batch does all passes in shared and distributed shared memory
+ * whenever the work fits, else the multi-pass path; and kdefft_select_H on a
+ * d = 2 FP32 dataset (LSCV of Eq. 10 or SCV, minimal padding) runs the whole
+ * multi-start search in one device-resident launch (one cluster per start).
+ * HOST_SELECT: as AUTO but the search is driven from the host, one batched
+ * launch per round.  MULTIPASS: the pass-per-axis kernels with a global
+ * scratch between passes (always used for d >= 3), host-driven search.  All
+ * compute the same sums. */
+enum { KDEFFT_ENGINE_AUTO = 0, KDEFFT_ENGINE_MULTIPASS = 1, KDEFFT_ENGINE_HOST_SELECT = 2 };
 int kdefft_set_engine(kdefft_ctx ctx, int engine);
 
 /* LSCV value and gradient for one bandwidth without allocating any memory.

@@ -32,7 +32,7 @@ EXPORTS = [
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine",
 ]
-ENGINE_AUTO, ENGINE_MULTIPASS = 0, 1
+ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT = 0, 1, 2
 
 
 class Opts(C.Structure):

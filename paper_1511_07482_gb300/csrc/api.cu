@@ -12,7 +12,9 @@
 //   - objective assembly in FP64 (adding 2 n^-1 K_H(0) etc.);
 //   - the quasi-Newton bandwidth optimiser of kdefft_select_H.
 #include <algorithm>
+#include <array>
 #include <functional>
+#include <set>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -421,6 +423,8 @@ struct kdefft_ctx_s {
     bool fused = true;    // d = 2: single cluster kernel per batch when it fits
     int* errflag = nullptr;   // device flag: a bounded device-side wait gave up
     int max_cluster = 16;     // largest cluster the fused engine may launch
+    bool device_select = true;   // d = 2 FP32 selections run as one device-resident launch
+    DevBuf sel_buf;           // device tables and start states of the device-resident selection
     std::map<std::string, KStat> kstat;
     struct Pending {
         std::string name;
@@ -1128,48 +1132,72 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     return KDEFFT_OK;
 }
 
-// |F(c_zp)|^2 at padded sizes P (computed once per dataset and P)
-template <typename real>
-static int ensure_spectrum(kdefft_ds ds, const int* P, const real** out) {
+static std::vector<int> spectrum_key(const kdefft_ds ds, const int* P, size_t realsize) {
     std::vector<int> key(P, P + ds->d);
-    key.push_back((int)sizeof(real));
-    auto it = ds->spectra.find(key);
-    if (it != ds->spectra.end()) {
-        *out = (const real*)it->second->p;
+    key.push_back((int)realsize);
+    return key;
+}
+
+// |F(c_zp)|^2 for every (dataset, P) in `need` that is not cached yet,
+// computed in one batched launch sequence (split by the scratch budget)
+template <typename real>
+static int ensure_spectra(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& need) {
+    std::vector<Item<real>> items;
+    std::vector<std::pair<kdefft_ds, std::vector<int>>> keys;
+    std::vector<std::shared_ptr<DevBuf>> bufs;
+    const long long budget = 1LL << 28;
+    long long scratch = 0;
+    auto flush = [&]() -> int {
+        if (items.empty()) return KDEFFT_OK;
+        PassLists pl;
+        for (size_t i = 0; i < items.size(); ++i) tile_item(items[i], (int)i, cap_elems(sizeof(real) == 8), pl);
+        KCHK(launch_items<real>(c, items, pl, items[0].d, nullptr));
+        for (size_t i = 0; i < keys.size(); ++i) keys[i].first->spectra[keys[i].second] = bufs[i];
+        items.clear();
+        keys.clear();
+        bufs.clear();
+        scratch = 0;
         return KDEFFT_OK;
-    }
-    auto buf = std::make_shared<DevBuf>();
-    KCHK(buf->ensure(sizeof(real) * spec_elems(ds->d, P)));
-    kdefft_ctx c = ds->ctx;
-    Item<real> item;
-    std::memset(&item, 0, sizeof(item));
-    item.d = ds->d;
-    item.kind = 1;
-    KCHK(fill_axes(c, ds->d, P, item));
-    for (int k = 0; k < ds->d; ++k) {
-        item.S[k] = (int)ds->M[k];
-        item.off[k] = 0;
-    }
-    const bool ds64 = ds->opts.precision == KDEFFT_FP64;
-    if (sizeof(real) == 8 && !ds64) {
-        // FP64 work on an FP32 dataset: widen the counts once
-        if (!ds->counts64.p) {
-            KCHK(ds->counts64.ensure(sizeof(double) * (size_t)ds->ncells));
-            c->launches++;
-            KCU(launch_f32_to_f64((const float*)ds->counts.p, (double*)ds->counts64.p, ds->ncells, c->stream));
+    };
+    std::set<std::pair<kdefft_ds, std::vector<int>>> queued;
+    for (const auto& np : need) {
+        kdefft_ds ds = np.first;
+        const int* P = np.second.data();
+        std::vector<int> key = spectrum_key(ds, P, sizeof(real));
+        if (ds->spectra.count(key) || queued.count({ds, key})) continue;
+        queued.insert({ds, key});
+        auto buf = std::make_shared<DevBuf>();
+        KCHK(buf->ensure(sizeof(real) * spec_elems(ds->d, P)));
+        Item<real> item;
+        std::memset(&item, 0, sizeof(item));
+        item.d = ds->d;
+        item.kind = 1;
+        KCHK(fill_axes(c, ds->d, P, item));
+        for (int k = 0; k < ds->d; ++k) {
+            item.S[k] = (int)ds->M[k];
+            item.off[k] = 0;
         }
-        item.counts = (const real*)ds->counts64.p;
-    } else {
-        item.counts = (const real*)ds->counts.p;
+        const bool ds64 = ds->opts.precision == KDEFFT_FP64;
+        if (sizeof(real) == 8 && !ds64) {
+            // FP64 work on an FP32 dataset: widen the counts once
+            if (!ds->counts64.p) {
+                KCHK(ds->counts64.ensure(sizeof(double) * (size_t)ds->ncells));
+                c->launches++;
+                KCU(launch_f32_to_f64((const float*)ds->counts.p, (double*)ds->counts64.p, ds->ncells, c->stream));
+            }
+            item.counts = (const real*)ds->counts64.p;
+        } else {
+            item.counts = (const real*)ds->counts.p;
+        }
+        item.spec_out = (real*)buf->p;
+        const long long sn = scratch_need(item);
+        if (!items.empty() && scratch + sn > budget) KCHK(flush());
+        scratch += sn;
+        items.push_back(item);
+        keys.push_back({ds, key});
+        bufs.push_back(buf);
     }
-    item.spec_out = (real*)buf->p;
-    std::vector<Item<real>> items{item};
-    PassLists pl;
-    tile_item(items[0], 0, cap_elems(sizeof(real) == 8), pl);
-    KCHK(launch_items<real>(c, items, pl, ds->d, nullptr));
-    ds->spectra[key] = buf;
-    *out = (const real*)buf->p;
-    return KDEFFT_OK;
+    return flush();
 }
 
 // Evaluate every grid of rs (value = Eq. 25 for that lag kernel).
@@ -1195,6 +1223,18 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
         u += 1;
     }
     const int cap = cap_elems(sizeof(real) == 8);
+    // count spectra first, all missing ones in one launch sequence
+    {
+        HostTimer hs(c, "host:spectra");
+        std::vector<std::pair<kdefft_ds, std::array<int, 4>>> need;
+        std::set<std::pair<kdefft_ds, std::array<int, 4>>> seen;
+        for (const auto& pr : pairs) {
+            const GridReq& g = rs.grids[pr.first];
+            std::array<int, 4> P{g.P[0], g.P[1], g.P[2], g.P[3]};
+            if (seen.insert({g.ds, P}).second) need.push_back({g.ds, P});
+        }
+        KCHK(ensure_spectra<real>(c, need));
+    }
     // scratch budget per launch: split the items into batches
     const long long budget = 1LL << 28;   // complex elements (2 GiB at FP32)
     size_t pi = 0;
@@ -1252,9 +1292,9 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
                     }
                 }
                 it.R = R;
-                const real* spec = nullptr;
-                KCHK(ensure_spectrum<real>(g.ds, g.P, &spec));
-                it.spec = spec;
+                auto sp_it = g.ds->spectra.find(spectrum_key(g.ds, g.P, sizeof(real)));
+                if (sp_it == g.ds->spectra.end()) return fail(KDEFFT_ERR_CUDA, "count spectrum missing");
+                it.spec = (const real*)sp_it->second->p;
                 const double nn = (double)g.ds->n;
                 it.scale = 1.0 / (nn * nn * (double)ptot);
                 // would this item overflow the multi-pass scratch budget?
@@ -1476,9 +1516,10 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
 
 int kdefft_set_engine(kdefft_ctx c, int engine) {
     if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
-    if (engine != KDEFFT_ENGINE_AUTO && engine != KDEFFT_ENGINE_MULTIPASS)
+    if (engine != KDEFFT_ENGINE_AUTO && engine != KDEFFT_ENGINE_MULTIPASS && engine != KDEFFT_ENGINE_HOST_SELECT)
         return fail(KDEFFT_ERR_ARG, "unknown engine");
-    c->fused = (engine == KDEFFT_ENGINE_AUTO);
+    c->fused = (engine != KDEFFT_ENGINE_MULTIPASS);
+    c->device_select = (engine == KDEFFT_ENGINE_AUTO);
     return KDEFFT_OK;
 }
 
@@ -1527,6 +1568,7 @@ int kdefft_destroy(kdefft_ctx c) {
     c->items.release();
     c->tiles.release();
     c->out.release();
+    c->sel_buf.release();
     c->h_items.release();
     c->h_out.release();
     for (auto& p : c->pending) {
@@ -1585,12 +1627,14 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
         c->h2d += (int64_t)(sizeof(double) * n * d);
         dX = (const double*)xbuf.p;
     }
-    DevBuf misc;   // outside counter + moments
-    KCHK(misc.ensure(sizeof(double) * 64));
-    KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 64, c->stream));
+    // outside counter | mean | block partials of the moments
+    const int mblk = moments_blocks(n, c->nsm);
+    DevBuf misc;
+    KCHK(misc.ensure(sizeof(double) * (16 + (size_t)mblk * d * d)));
+    KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
     unsigned long long* dOut = (unsigned long long*)misc.p;
     double* dMean = (double*)misc.p + 8;
-    double* dCov = (double*)misc.p + 16;
+    double* dPart = (double*)misc.p + 16;
     const bool dbl = o.precision == KDEFFT_FP64;
     KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));
     KCU(cudaMemsetAsync(ds->counts.p, 0, (dbl ? 8 : 4) * (size_t)ds->ncells, c->stream));
@@ -1605,25 +1649,42 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
         else
             KCU(launch_int_to_real<float>((int*)ds->counts_i.p, (float*)ds->counts.p, ds->ncells, c->stream));
     } else if (dbl) {
-        KCU(launch_bin_linear<double>(dX, n, g, (double*)ds->counts.p, ds->ncells, dOut, c->nsm, c->stream));
+        KCU(launch_bin_linear<double>(dX, n, g, (double*)ds->counts.p, ds->ncells, dOut, 1.0, c->nsm, c->stream));
     } else {
-        KCU(launch_bin_linear<float>(dX, n, g, (float*)ds->counts.p, ds->ncells, dOut, c->nsm, c->stream));
+        // fixed point with K fractional bits; a cell's total (<= n 2^K) stays below 2^63
+        int K = 32;
+        while (K > 8 && (double)n * std::ldexp(1.0, K) >= std::ldexp(1.0, 63)) --K;
+        c->launches++;   // the fixed-point-to-FP32 conversion
+        DevBuf fix;
+        KCHK(fix.ensure(8 * (size_t)ds->ncells));
+        KCU(cudaMemsetAsync(fix.p, 0, 8 * (size_t)ds->ncells, c->stream));
+        KCU(launch_bin_linear<unsigned long long>(dX, n, g, (unsigned long long*)fix.p, ds->ncells, dOut,
+                                                  std::ldexp(1.0, K), c->nsm, c->stream));
+        KCU(launch_fix_to_f32((const unsigned long long*)fix.p, (float*)ds->counts.p, ds->ncells, std::ldexp(1.0, -K),
+                              c->stream));
+        KCU(cudaStreamSynchronize(c->stream));   // before the temporary is freed
     }
     prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
     // moments for the normal-scale start point
     c->launches += 2;
-    KCU(launch_moments(dX, n, d, 0, nullptr, dMean, c->nsm, c->stream));
-    double hm[8];
-    KCU(cudaMemcpyAsync(hm, dMean, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+    // (block partials summed here in block order: the same start point from run to run)
+    std::vector<double> part((size_t)mblk * d * d);
+    KCU(launch_moments(dX, n, d, 0, nullptr, dPart, c->nsm, c->stream));
+    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * d, cudaMemcpyDeviceToHost, c->stream));
     KCU(cudaStreamSynchronize(c->stream));
+    double hm[8] = {0};
+    for (int b = 0; b < mblk; ++b)
+        for (int k = 0; k < d; ++k) hm[k] += part[(size_t)b * d + k];
     for (int k = 0; k < d; ++k) hm[k] /= (double)n;
     KCU(cudaMemcpyAsync(dMean, hm, sizeof(double) * 8, cudaMemcpyHostToDevice, c->stream));
-    KCU(launch_moments(dX, n, d, 1, dMean, dCov, c->nsm, c->stream));
+    KCU(launch_moments(dX, n, d, 1, dMean, dPart, c->nsm, c->stream));
     unsigned long long nout = 0;
-    double hc[16];
+    double hc[16] = {0};
     KCU(cudaMemcpyAsync(&nout, dOut, sizeof(nout), cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaMemcpyAsync(hc, dCov, sizeof(double) * 16, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * d * d, cudaMemcpyDeviceToHost, c->stream));
     KCU(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < mblk; ++b)
+        for (int v = 0; v < d * d; ++v) hc[v] += part[(size_t)b * d * d + v];
     prof_flush(c);
     for (int i = 0; i < d * d; ++i) ds->cov[i] = (n > 1) ? hc[i] / (double)(n - 1) : 0.0;
     if (nout > 0 && o.outside_policy == KDEFFT_OUTSIDE_ERROR)
@@ -2018,6 +2079,178 @@ void grad_theta(const Opt& o, const double* th, const double* g, double* gt) {
 
 }  // namespace
 
+// Device-resident selection for d = 2 (FP32 dataset, LSCV of Eq. 10 or SCV,
+// minimal padding): returns KDEFFT_ERR_UNSUPPORTED without side effects when
+// the case is not covered, so that the caller runs the host optimiser.
+static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::vector<std::vector<double>>& th0,
+                           int max_iter, std::vector<std::vector<double>>& th_out, std::vector<double>& f_out,
+                           int64_t* evals_out) {
+    kdefft_ctx c = ds->ctx;
+    if (!c->device_select || ds->d != 2 || ds->opts.precision != KDEFFT_FP32 || ds->opts.P_rule != KDEFFT_P_MINIMAL ||
+        ds->opts.L_basis == KDEFFT_L_FULL || (method == KDEFFT_LSCV && ds->opts.exact_loo) ||
+        (method == KDEFFT_SCV && ds->opts.L_basis == KDEFFT_L_PAPER) ||
+        (method != KDEFFT_LSCV && method != KDEFFT_SCV))
+        return KDEFFT_ERR_UNSUPPORTED;
+    const int nst = (int)th0.size();
+    const int M0 = (int)ds->M[0], M1 = (int)ds->M[1];
+    auto pmin = [](int m) {
+        int p = m;
+        while (!is_smooth(p)) ++p;
+        return p;
+    };
+    // cluster size, batch size and support cap from the shared-memory budget
+    // The two packed pairs are transformed together: the gather holds both
+    // and a batch holds `chunk` lines of each.  The largest support cap that
+    // fits comes first, then the largest batch at that cap.
+    const size_t budget = 110 * 1024;   // two CTAs per SM
+    int cs = 16, Lcap = std::max(M0, M1) - 1, chunk = 0;
+    int gat = 0, spc = 0, cap = 0, pmax = 0;
+    for (;;) {
+        const int L0 = std::min(Lcap, M0 - 1), L1 = std::min(Lcap, M1 - 1);
+        const int P0 = pmin(M0 + L0), P1 = pmin(M1 + L1);
+        if (P0 > MAXP || P1 > MAXP) return KDEFFT_ERR_UNSUPPORTED;
+        const int cpc = (P1 / 2 + 1 + cs - 1) / cs;
+        gat = (2 * (2 * std::max(L0, L1) + 1) * cpc + 1) & ~1;
+        spc = cpc * P0;
+        pmax = std::max(P0, P1);
+        for (chunk = 8; chunk >= 3; --chunk) {
+            cap = 2 * chunk * pmax;
+            const size_t need =
+                sizeof(float2) * (size_t)(gat + 2 * pmax + 2 * (cap + cap / 16 + 1)) + sizeof(float) * spc;
+            if (need <= budget) break;
+        }
+        if (chunk >= 3) break;
+        if (Lcap <= 8) return KDEFFT_ERR_UNSUPPORTED;
+        Lcap = Lcap * 3 / 4;
+    }
+    // the (L0, L1) pairs met as lambda grows: breakpoints of ceil(tau s / delta_k)
+    std::vector<double> brk;
+    for (int k = 0; k < 2; ++k)
+        for (int m = 0; m <= Lcap + 1; ++m) brk.push_back(m * ds->delta[k] / ds->opts.tau);
+    std::sort(brk.begin(), brk.end());
+    std::vector<std::array<int, 4>> pairsP;
+    std::set<std::pair<int, int>> seenP;
+    auto Lof = [&](double sq, int k) {
+        double v = std::ceil(ds->opts.tau * sq / ds->delta[k]);
+        const double cap_ = (double)(ds->M[k] - 1);
+        if (!(v <= cap_)) v = cap_;
+        if (v < 1.0) v = 1.0;
+        return (int)v;
+    };
+    for (size_t i = 0; i + 1 < brk.size(); ++i)
+        for (double t : {0.0, 0.5, 1.0}) {
+            const double sq = brk[i] + t * (brk[i + 1] - brk[i]);
+            const int L0 = Lof(sq, 0), L1 = Lof(sq, 1);
+            if (L0 > Lcap || L1 > Lcap) continue;
+            const int P0 = pmin(M0 + L0), P1 = pmin(M1 + L1);
+            if (seenP.insert({P0, P1}).second) pairsP.push_back({P0, P1, 0, 0});
+        }
+    if (pairsP.empty() || pairsP.size() > 256) return KDEFFT_ERR_UNSUPPORTED;
+    {
+        std::vector<std::pair<kdefft_ds, std::array<int, 4>>> need;
+        for (auto& pp : pairsP) need.push_back({ds, pp});
+        KCHK(ensure_spectra<float>(c, need));
+    }
+    std::vector<SelSpec> specs;
+    for (auto& pp : pairsP) {
+        SelSpec sp{};
+        sp.P0 = pp[0];
+        sp.P1 = pp[1];
+        if (!radix_plan(sp.P0, sp.a0, 32) || !radix_plan(sp.P1, sp.a1, 32)) return KDEFFT_ERR_UNSUPPORTED;
+        sp.a0.tw_off = twiddle_offset(c, sp.P0);
+        sp.a1.tw_off = twiddle_offset(c, sp.P1);
+        auto it = ds->spectra.find(spectrum_key(ds, pp.data(), sizeof(float)));
+        if (it == ds->spectra.end()) return fail(KDEFFT_ERR_CUDA, "count spectrum missing");
+        sp.spec = (const float*)it->second->p;
+        sp.scale = 1.0 / ((double)ds->n * (double)ds->n * (double)sp.P0 * (double)sp.P1);
+        {   // two packed pairs: S_0 axis-1 lines and Q_1 axis-0 columns each, one read of the spectrum
+            const double P0d = sp.P0, P1d = sp.P1, Q1 = std::floor(P1d / 2) + 1;
+            sp.fl_line = 2.0 * 5.0 * P1d * std::log2(P1d);
+            sp.fl_fix = 2.0 * Q1 * (5.0 * P0d * std::log2(P0d) + 4.0 * P0d);
+            sp.by = Q1 * P0d * sizeof(float);
+        }
+        specs.push_back(sp);
+    }
+    KCHK(sync_twiddles(c));
+    std::vector<int> ptab(2 * (Lcap + 1));
+    for (int L = 0; L <= Lcap; ++L) {
+        ptab[L] = pmin(M0 + L);
+        ptab[Lcap + 1 + L] = pmin(M1 + L);
+    }
+    // device tables: specs | ptab | starts
+    const size_t bS = sizeof(SelSpec) * specs.size(), bP = sizeof(int) * ptab.size(), bT = sizeof(SelStart) * nst;
+    const size_t oP = (bS + 255) & ~(size_t)255, oT = (oP + bP + 255) & ~(size_t)255;
+    KCHK(c->sel_buf.ensure(oT + bT));
+    std::vector<unsigned char> hb(oT + bT, 0);
+    std::memcpy(hb.data(), specs.data(), bS);
+    std::memcpy(hb.data() + oP, ptab.data(), bP);
+    std::vector<SelStart> st(nst);
+    for (int i = 0; i < nst; ++i) {
+        std::memset(&st[i], 0, sizeof(SelStart));
+        for (int k = 0; k < 3; ++k) st[i].th[k] = th0[i][k];
+    }
+    std::memcpy(hb.data() + oT, st.data(), bT);
+    unsigned char* db = (unsigned char*)c->sel_buf.p;
+    KCU(cudaMemcpyAsync(db, hb.data(), hb.size(), cudaMemcpyHostToDevice, c->stream));
+    c->h2d += (int64_t)hb.size();
+    SelectParams prm{};
+    prm.method = (method == KDEFFT_LSCV) ? 0 : 1;
+    prm.max_iter = max_iter;
+    prm.cs = cs;
+    prm.nspec = (int)specs.size();
+    prm.widest = (method == KDEFFT_LSCV && ds->opts.L_basis == KDEFFT_L_WIDEST) ? 1 : 0;
+    prm.M0 = M0;
+    prm.M1 = M1;
+    prm.Lcap = Lcap;
+    prm.chunk = chunk;
+    prm.gat_elems = gat;
+    prm.spc_elems = (spc + 3) & ~3;
+    prm.cap = cap;
+    prm.pmax = pmax;
+    prm.n = (double)ds->n;
+    prm.tau = ds->opts.tau;
+    prm.delta0 = ds->delta[0];
+    prm.delta1 = ds->delta[1];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) prm.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gm(a, b) : 0.0;
+    prm.ptab0 = (const int*)(db + oP);
+    prm.ptab1 = (const int*)(db + oP) + (Lcap + 1);
+    prm.specs = (const SelSpec*)db;
+    prm.errflag = c->errflag;
+    cudaEvent_t ev = prof_start(c);
+    cudaError_t le = launch_select2d(prm, (SelStart*)(db + oT), nst, (const float2*)c->tw32.p, c->stream);
+    if (le == cudaErrorNotSupported) return KDEFFT_ERR_UNSUPPORTED;
+    KCU(le);
+    prof_stop(c, ev, "select2d_f32", 0.0, 0.0);
+    KCU(cudaMemcpyAsync(st.data(), db + oT, bT, cudaMemcpyDeviceToHost, c->stream));
+    {
+        HostTimer w(c, "host:wait");
+        KCU(cudaStreamSynchronize(c->stream));
+    }
+    c->d2h += (int64_t)bT;
+    if (c->prof && !c->pending.empty() && ev) {   // the work is known once the searches have ended
+        double fl = 0.0, by = 0.0;
+        for (const SelStart& s : st) {
+            fl += s.flops;
+            by += s.bytes;
+        }
+        c->pending.back().flops = fl;
+        c->pending.back().bytes = by;
+    }
+    prof_flush(c);
+    KCHK(check_errflag(c));
+    th_out.assign(nst, std::vector<double>(3));
+    f_out.assign(nst, INFINITY);
+    int64_t ev_total = 0;
+    for (int i = 0; i < nst; ++i) {
+        for (int k = 0; k < 3; ++k) th_out[i][k] = st[i].th[k];
+        f_out[i] = st[i].f;
+        ev_total += st[i].evals;
+    }
+    *evals_out = ev_total;
+    return KDEFFT_OK;
+}
+
 extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
                                int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
     if (!ds || !H_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
@@ -2128,6 +2361,32 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
         H_to_theta(o, Hs, st[s].th.data());
         st[s].Binv.assign((size_t)p * p, 0.0);
         for (int i = 0; i < p; ++i) st[s].Binv[i * p + i] = 1.0;
+    }
+    if (d == 2) {
+        std::vector<std::vector<double>> ths, tho;
+        for (auto& s : st) ths.push_back(s.th);
+        std::vector<double> fo;
+        int64_t dev_evals = 0;
+        const int r = device_select2d(ds, method, Gm, ths, max_iter, tho, fo, &dev_evals);
+        if (r == KDEFFT_OK) {
+            int best = 0;
+            for (int s = 1; s < n_starts; ++s)
+                if (fo[s] < fo[best]) best = s;
+            if (!std::isfinite(fo[best])) return fail(KDEFFT_ERR_ARG, "no start point inside the search domain");
+            Mat Hb = theta_to_H(o, tho[best].data());
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
+            double fbest = fo[best];
+            if (method == KDEFFT_SCV) {
+                std::vector<double> v;
+                KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
+                fbest = v[0];
+            }
+            if (f_out) *f_out = fbest;
+            if (n_evals) *n_evals = dev_evals;
+            return KDEFFT_OK;
+        }
+        if (r != KDEFFT_ERR_UNSUPPORTED) return r;
     }
     {
         std::vector<std::vector<double>> ths;

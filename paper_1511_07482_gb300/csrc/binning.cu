@@ -12,6 +12,13 @@
 // Grids that fit in shared memory are accumulated per block there (one
 // privatised histogram per block, flushed with global atomics of the nonzero
 // cells); larger grids use global atomics directly.
+//
+// FP32 counts are accumulated in 64-bit fixed point (each weight rounded to
+// a multiple of 2^-K, K = 32 for samples below 2^31 points): integer sums do
+// not depend on the order of the atomic additions, so the counts, and every
+// objective value computed from them, are the same from run to run, and the
+// rounding of a weight (<= 2^-33) stays far below the FP32 rounding of the
+// count itself.  FP64 counts use FP64 atomics.
 #include "engine.cuh"
 
 namespace kdefft {
@@ -33,13 +40,16 @@ __device__ __forceinline__ bool locate(const double* __restrict__ x, const GridD
     return true;
 }
 
-__device__ __forceinline__ void atomic_acc(float* p, double w) { atomicAdd(p, (float)w); }
-__device__ __forceinline__ void atomic_acc(double* p, double w) { atomicAdd(p, w); }
+__device__ __forceinline__ void atomic_acc(double* p, double w, double) { atomicAdd(p, w); }
+__device__ __forceinline__ void atomic_acc(unsigned long long* p, double w, double qscale) {
+    atomicAdd(p, __double2ull_rn(w * qscale));
+}
 
 template <typename acc>
 __global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X, long long n, GridDesc g,
                                                     acc* __restrict__ counts, long long ncells,
-                                                    unsigned long long* __restrict__ outside, int use_smem) {
+                                                    unsigned long long* __restrict__ outside, int use_smem,
+                                                    double qscale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     acc* hist = reinterpret_cast<acc*>(smem_raw);
     if (use_smem) {
@@ -74,9 +84,9 @@ __global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X
                 idx += bk * stride[k];
             }
             if (use_smem)
-                atomic_acc(hist + idx, w);
+                atomic_acc(hist + idx, w, qscale);
             else
-                atomic_acc(counts + idx, w);
+                atomic_acc(counts + idx, w, qscale);
         }
     }
     if (nout) atomicAdd(outside, nout);
@@ -128,6 +138,20 @@ cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaSt
     return cudaGetLastError();
 }
 
+__global__ void k_fix_to_f32(const unsigned long long* __restrict__ src, float* __restrict__ dst, long long n,
+                             double unit) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (float)((double)src[i] * unit);
+}
+
+cudaError_t launch_fix_to_f32(const unsigned long long* src, float* dst, long long n, double unit, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_fix_to_f32<<<(int)b, 256, 0, st>>>(src, dst, n, unit);
+    return cudaGetLastError();
+}
+
 template <typename real>
 __global__ void k_int_to_real(const int* __restrict__ src, real* __restrict__ dst, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -144,7 +168,7 @@ static int blocks_for(long long n, int nsm, int per_sm) {
 
 template <typename acc>
 cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, acc* counts, long long ncells,
-                              unsigned long long* outside, int nsm, cudaStream_t st) {
+                              unsigned long long* outside, double qscale, int nsm, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t hist_bytes = sizeof(acc) * (size_t)ncells;
     const int use_smem = hist_bytes <= 96 * 1024;
@@ -158,7 +182,7 @@ cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, a
     } else {
         grid = blocks_for(n, nsm, 8);
     }
-    k_bin_linear<acc><<<grid, 256, sm, st>>>(X, n, g, counts, ncells, outside, use_smem);
+    k_bin_linear<acc><<<grid, 256, sm, st>>>(X, n, g, counts, ncells, outside, use_smem, qscale);
     return cudaGetLastError();
 }
 
@@ -206,21 +230,24 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ X, l
     if (threadIdx.x < nv) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
-        atomicAdd(out + threadIdx.x, t);
+        out[(size_t)blockIdx.x * nv + threadIdx.x] = t;   // block partial; summed in block order by the host
     }
 }
+
+int moments_blocks(long long n, int nsm) { return blocks_for(n, nsm, 2); }
 
 cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
                            cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_moments<<<blocks_for(n, nsm, 2), 256, 0, st>>>(X, n, d, pass, mean, out);
+    k_moments<<<moments_blocks(n, nsm), 256, 0, st>>>(X, n, d, pass, mean, out);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_bin_linear<float>(const double*, long long, const GridDesc&, float*, long long,
-                                              unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_bin_linear<unsigned long long>(const double*, long long, const GridDesc&,
+                                                           unsigned long long*, long long, unsigned long long*, double,
+                                                           int, cudaStream_t);
 template cudaError_t launch_bin_linear<double>(const double*, long long, const GridDesc&, double*, long long,
-                                               unsigned long long*, int, cudaStream_t);
+                                               unsigned long long*, double, int, cudaStream_t);
 template cudaError_t launch_int_to_real<float>(const int*, float*, long long, cudaStream_t);
 template cudaError_t launch_int_to_real<double>(const int*, double*, long long, cudaStream_t);
 

@@ -16,6 +16,8 @@
 // The 1-D transforms are mixed-radix (2, 3, 4, 5, 8) Stockham passes over
 // lines held in shared memory (self-sorting, ping-pong buffers), twiddles
 // exp(-2 pi i t/P) from an FP64-computed table staged in shared memory.
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "engine.cuh"
@@ -1022,6 +1024,549 @@ __global__ void __launch_bounds__(256) k_fused2d(const FusedItem<real>* __restri
     }
 }
 
+// ------------------------------------------------------------ device-resident selection (d = 2, FP32)
+// One cluster per start.  Each round, rank 0 (one thread, FP64 host-style
+// algebra) turns the trial Cholesky parameters into H, checks the search
+// domain, picks L (Eq. 26) and P, and writes the two packed work items of the
+// objective and its gradient (value + dH_00, dH_01 + dH_11); the cluster
+// evaluates both with the fused pipeline below; rank 0 assembles the value
+// and gradient and applies the line search / BFGS update that the host
+// optimiser uses.  Every loop is bounded.
+
+// the four grids of both packed pairs at lag (j0, j1): item 1 carries only
+// its weights (covariances are those of item 0)
+__device__ __forceinline__ void kernel_quad_2d(const FusedItem<float>& f, const FusedItem<float>& g, int j0, int j1,
+                                               float* v) {
+    constexpr HTab<2, 2> ht{};
+    constexpr int N = HTab<2, 2>::N;
+    const float x0 = (float)f.delta0 * (float)j0, x1 = (float)f.delta1 * (float)j1;
+    float a0 = 0, b0 = 0, a1 = 0, b1 = 0;
+#pragma unroll
+    for (int s = 0; s < MAXSIG; ++s) {
+        if (s < f.nsig) {
+            const float z0 = f.laml[s][0] * x0 + f.laml[s][1] * x1;
+            const float z1 = f.laml[s][2] * x0 + f.laml[s][3] * x1;
+            const float e = f.nrm[s] * expf(-0.5f * (x0 * z0 + x1 * z1));
+            float He[N];
+            He[0] = 1.f;
+#pragma unroll
+            for (int t = 1; t < N; ++t) {
+                float w = (ht.piv[t] == 0 ? z0 : z1) * He[ht.par[t]];
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (r < ht.nred[t]) w -= float(ht.rc[t][r]) * f.laml[s][ht.piv[t] * 2 + ht.rj[t][r]] * He[ht.ridx[t][r]];
+                He[t] = w;
+            }
+            float pa0 = 0, pb0 = 0, pa1 = 0, pb1 = 0;
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                pa0 += f.W[0][s][t] * He[t];
+                pb0 += f.W[1][s][t] * He[t];
+                pa1 += g.W[0][s][t] * He[t];
+                pb1 += g.W[1][s][t] * He[t];
+            }
+            a0 += e * pa0;
+            b0 += e * pb0;
+            a1 += e * pa1;
+            b1 += e * pb1;
+        }
+    }
+    v[0] = a0;
+    v[1] = b0;
+    v[2] = a1;
+    v[3] = b1;
+}
+
+// Both packed pairs of one bandwidth (same H, L, P and spectrum, different
+// weights) evaluated together by the cluster: lines and columns of the two
+// pairs share every barrier, the twiddles, the staged spectrum rows and the
+// reduction.  gat holds 2 x S_0 x cpc values (pair-major).  res4 (rank 0):
+// the four scaled sums (pair 0 grids A, B; pair 1 grids A, B).
+__device__ __forceinline__ void sel_eval2(cg::cluster_group& cluster, const FusedItem<float>& f,
+                                          const FusedItem<float>& g2, int cs, int rank, int chunk, float2* gat,
+                                          float* spc, float2* tw1, float2* tw0, float2* bufa, float2* bufb,
+                                          const float2* twpool, double* cl_red, double* res4) {
+    using C = float2;
+    const int P1 = f.a1.P, P0 = f.a0.P, Q1 = P1 / 2 + 1;
+    const int S0 = f.S0, S1 = f.S1;
+    const int lpc = (S0 + cs - 1) / cs;
+    const int cpc = (Q1 + cs - 1) / cs;
+    const int q0 = rank * cpc;
+    const int nq = max(0, min(Q1, q0 + cpc) - q0);
+    const int l0 = rank * lpc;
+    const int nl = max(0, min(S0, l0 + lpc) - l0);
+    const int gpair = S0 * cpc;   // gather elements per pair
+    const float* sg = f.spec + (size_t)q0 * P0;
+    for (int t = threadIdx.x; t < nq * P0; t += blockDim.x) cp_async<4>(spc + t, sg + t);
+    load_twiddles(tw1, twpool, f.a1);
+    load_twiddles(tw0, twpool, f.a0);
+    __syncthreads();
+    const uint32_t mP1 = magic_of((uint32_t)P1), mQ1 = magic_of((uint32_t)Q1), mP0 = magic_of((uint32_t)P0);
+    const uint32_t mcpc = magic_of((uint32_t)max(cpc, 2));
+    const int off0 = f.off0, off1 = f.off1;
+    // axis-1 pass: lines [pair 0: nc lines][pair 1: nc lines]
+    for (int c0 = 0; c0 < nl; c0 += chunk) {
+        const int nc = min(chunk, nl - c0);
+        for (int t = threadIdx.x; t < nc * P1; t += blockDim.x) {
+            const int c = (int)qdiv((uint32_t)t, mP1);
+            const int p = t - c * P1;
+            int idx = p + off1;
+            if (idx >= P1) idx -= P1;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (idx < S1) kernel_quad_2d(f, g2, l0 + c0 + c - off0, idx - off1, v);
+            bufa[pad(t)] = C{v[0], v[1]};
+            bufa[pad(t + nc * P1)] = C{v[2], v[3]};
+        }
+        C* Y = smem_fft(bufa, bufb, 2 * nc, f.a1, tw1);
+        for (int t = threadIdx.x; t < 2 * nc * Q1; t += blockDim.x) {
+            const int cc = (int)qdiv((uint32_t)t, mQ1);   // pair * nc + line
+            const int q = t - cc * Q1;
+            const int pr = cc >= nc ? 1 : 0;
+            const int c = cc - pr * nc;
+            const int dst = (cpc == 1) ? q : (int)qdiv((uint32_t)q, mcpc);
+            C* gg = cluster.map_shared_rank(gat, dst);
+            gg[pr * gpair + (l0 + c0 + c) * cpc + (q - dst * cpc)] = Y[pad(cc * P1 + q)];
+        }
+        __syncthreads();
+    }
+    cp_async_wait_all();
+    cluster.sync();
+    // axis-0 pass: lines [pair 0: nc columns][pair 1: nc columns]
+    SumAcc<float> acc0, acc1;
+    for (int c0 = 0; c0 < nq; c0 += chunk) {
+        const int nc = min(chunk, nq - c0);
+        for (int t = threadIdx.x; t < 2 * nc * P0; t += blockDim.x) {
+            const int cc = (int)qdiv((uint32_t)t, mP0);
+            const int p = t - cc * P0;
+            const int pr = cc >= nc ? 1 : 0;
+            const int c = cc - pr * nc;
+            int idx = p + off0;
+            if (idx >= P0) idx -= P0;
+            bufa[pad(t)] = (idx < S0) ? gat[pr * gpair + idx * cpc + c0 + c] : C{0.f, 0.f};
+        }
+        C* Y = smem_fft(bufa, bufb, 2 * nc, f.a0, tw0);
+        for (int t = threadIdx.x; t < 2 * nc * P0; t += blockDim.x) {
+            const int cc = (int)qdiv((uint32_t)t, mP0);
+            const int w = t - cc * P0;
+            const int pr = cc >= nc ? 1 : 0;
+            const int c = cc - pr * nc;
+            const int q = q0 + c0 + c;
+            const float sv = spc[(c0 + c) * P0 + w] * float(half_weight(q, P1));
+            const C y = Y[pad(t)];
+            if (pr)
+                acc1.add(sv * y.x, sv * y.y);
+            else
+                acc0.add(sv * y.x, sv * y.y);
+        }
+        __syncthreads();
+    }
+    double part0[2], part1[2];
+    block_reduce_acc(acc0, part0);
+    block_reduce_acc(acc1, part1);
+    // every CTA receives every partial, so that each forms the same four sums
+    // (same order, same rounding) and can run its own copy of the optimiser
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < cs; ++r) {
+            double* dst = cluster.map_shared_rank(cl_red, r);
+            dst[4 * rank + 0] = part0[0];
+            dst[4 * rank + 1] = part0[1];
+            dst[4 * rank + 2] = part1[0];
+            dst[4 * rank + 3] = part1[1];
+        }
+    }
+    cluster.sync();
+    if (threadIdx.x < 4) {
+        double r = 0.0;
+        for (int k = 0; k < cs; ++k) r += cl_red[4 * k + threadIdx.x];
+        res4[threadIdx.x] = r * f.scale;
+    }
+}
+
+// optimiser state of one start (each CTA of its cluster holds a copy)
+struct SelOpt {
+    double th[3], g[3], dir[3], Binv[9], th_try[3];
+    double f, step, slope;
+    double flops, bytes;
+    int iter, ls, done, evals, status, first;
+};
+
+// H = R R^T, R = [[e^t0, 0], [t1, e^t2]] (sel_prepare)
+// Warp 0 of a CTA: trial point theta -> H, R and the two work items; every
+// lane returns false when H is outside the search domain (or needs a support
+// beyond Lcap / a size with no spectrum).  The independent FP64 chains (the
+// two exponentials, each covariance's inverse and normalisation, each axis'
+// support, the domain tests) run on separate lanes, so that their long
+// dependent sequences overlap.  Every CTA of a cluster computes the same
+// items from the same theta.
+__device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<float>* it, double* Hs, double* Rs,
+                            double* aux) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const double ex = exp(lane == 0 ? th[0] : th[2]);
+    const double r00 = __shfl_sync(FULL, ex, 0), r11 = __shfl_sync(FULL, ex, 1), r10 = th[1];
+    double H[4];
+    H[0] = r00 * r00;
+    H[1] = r00 * r10;
+    H[2] = r10 * r00;
+    H[3] = r10 * r10 + r11 * r11;
+    const double a = H[0], b = H[1], c = H[3];
+    const double det = a * c - b * b;
+    // covariances: LSCV {2H, H}; SCV {2H + 2G, H + 2G, 2G}
+    const int nsig = (p.method == 0) ? 2 : 3;
+    const double gco = (p.method == 0) ? 0.0 : 2.0;
+    // lane s < nsig: inverse and normalisation of covariance s
+    double iv0 = 0.0, iv1 = 0.0, iv3 = 0.0, nr = 0.0;
+    if (lane < nsig) {
+        const double hco = (lane == 0) ? 2.0 : (lane == 1 ? 1.0 : 0.0);
+        double Ss[4];
+        for (int e = 0; e < 4; ++e) Ss[e] = hco * H[e] + gco * p.G[e];
+        const double dt = Ss[0] * Ss[3] - Ss[1] * Ss[1];
+        iv0 = Ss[3] / dt;
+        iv1 = -Ss[1] / dt;
+        iv3 = Ss[0] / dt;
+        nr = 1.0 / (6.283185307179586 * sqrt(dt));
+    }
+    // lanes 8, 9: support along axis k from lambda_max of H (LSCV, paper
+    // rule), 2H (LSCV widest) or 2H + 2G (SCV)
+    int Lk = 0;
+    bool dom = true;
+    if (lane == 8 || lane == 9) {
+        const int k = lane - 8;
+        const double bs = (p.method == 1 || p.widest) ? 2.0 : 1.0;
+        double B[4];
+        for (int e = 0; e < 4; ++e) B[e] = bs * H[e] + gco * p.G[e];
+        const double tr = 0.5 * (B[0] + B[3]);
+        const double dd = 0.5 * (B[0] - B[3]);
+        const double lam = tr + sqrt(dd * dd + B[1] * B[1]);
+        const double dl = k == 0 ? p.delta0 : p.delta1;
+        const int Mk = k == 0 ? p.M0 : p.M1;
+        double v = ceil(p.tau * sqrt(fabs(lam)) / dl);
+        if (!(v <= (double)(Mk - 1))) v = (double)(Mk - 1);
+        if (v < 1.0) v = 1.0;
+        Lk = (int)v;
+    }
+    // lanes 16, 17: the bandwidth is at least half a bin wide along each axis
+    if (lane == 16) dom = sqrt(a) >= 0.5 * p.delta0;
+    if (lane == 17) dom = sqrt(c) >= 0.5 * p.delta1;
+    const bool inside = __all_sync(FULL, dom) && a > 0.0 && det > 0.0;
+    const int L0 = __shfl_sync(FULL, Lk, 8), L1 = __shfl_sync(FULL, Lk, 9);
+    if (!inside || L0 > p.Lcap || L1 > p.Lcap) return false;
+    const int P0 = p.ptab0[L0], P1 = p.ptab1[L1];
+    int si = -1;
+    for (int i0 = 0; i0 < p.nspec && si < 0; i0 += 32) {
+        const int i = i0 + lane;
+        const unsigned m = __ballot_sync(FULL, i < p.nspec && p.specs[i].P0 == P0 && p.specs[i].P1 == P1);
+        if (m) si = i0 + __ffs(m) - 1;
+    }
+    if (si < 0) {
+        if (lane == 0) atomicOr(p.errflag, 2);
+        return false;
+    }
+    const SelSpec& sp = p.specs[si];
+    // covariance rows of both items, then the headers, then the weights
+    if (lane < nsig) {
+        const double iv[4] = {iv0, iv1, iv1, iv3};
+        for (int q = 0; q < 2; ++q) {
+            for (int e = 0; e < 4; ++e) {
+                it[q].lam[lane][e] = iv[e];
+                it[q].laml[lane][e] = (float)iv[e];
+            }
+            it[q].nrm[lane] = (float)nr;
+        }
+    } else if (lane < MAXSIG) {
+        for (int q = 0; q < 2; ++q) {
+            for (int e = 0; e < 4; ++e) {
+                it[q].lam[lane][e] = 0.0;
+                it[q].laml[lane][e] = 0.f;
+            }
+            it[q].nrm[lane] = 0.f;
+        }
+    }
+    if (lane < 2) {
+        FusedItem<float>& f = it[lane];
+        f.S0 = 2 * L0 + 1;
+        f.S1 = 2 * L1 + 1;
+        f.off0 = L0;
+        f.off1 = L1;
+        f.nsig = nsig;
+        f.pad_ = 0;
+        f.delta0 = p.delta0;
+        f.delta1 = p.delta1;
+        f.a0 = sp.a0;
+        f.a1 = sp.a1;
+        f.spec = sp.spec;
+        f.scale = sp.scale;
+    }
+    constexpr int NW = 2 * MAXSIG * WDENSE;
+    for (int t = lane; t < 2 * NW; t += 32) {
+        const int q = t / NW, r = t - q * NW;
+        (&it[q].W[0][0][0])[r] = 0.f;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // Hermite indices (d = 2, graded): 0 -> (0,0), 3 -> (2,0), 4 -> (1,1), 5 -> (0,2)
+        it[0].W[0][0][0] = 1.f;
+        it[0].W[0][1][0] = -2.f;
+        if (p.method != 0) it[0].W[0][2][0] = 1.f;
+        it[0].W[1][0][3] = 1.f;   // d^2/dH00: s_00 = 1
+        it[0].W[1][1][3] = -1.f;
+        it[1].W[0][0][4] = 2.f;   // tied off-diagonal: s_01 = 2
+        it[1].W[0][1][4] = -2.f;
+        it[1].W[1][0][5] = 1.f;
+        it[1].W[1][1][5] = -1.f;
+        for (int e = 0; e < 4; ++e) Hs[e] = H[e];
+        Rs[0] = r00;
+        Rs[1] = r10;
+        Rs[2] = r11;
+        aux[0] = det;
+        aux[1] = sp.fl_fix + (double)(2 * L0 + 1) * sp.fl_line;
+        aux[2] = sp.by;
+    }
+    return true;
+}
+
+// objective, gradient in H (tied convention) -> value and theta-gradient
+__device__ void sel_assemble(const SelectParams& p, const double* H, const double* Rm, const double* r0,
+                             const double* r1, double det, double* f, double* gt) {
+    const double rdet = 1.0 / det;
+    const double hi00 = H[3] * rdet, hi01 = -H[1] * rdet, hi11 = H[0] * rdet;
+    double g00, g01, g11;
+    if (p.method == 0) {
+        const double k0 = 0.15915494309189535 * sqrt(rdet);   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
+        const double c0 = 2.0 / p.n;
+        *f = r0[0] + c0 * k0;
+        g00 = r0[1] + c0 * (-0.5 * k0 * hi00);
+        g01 = r1[0] + c0 * 2.0 * (-0.5 * k0 * hi01);
+        g11 = r1[1] + c0 * (-0.5 * k0 * hi11);
+    } else {
+        const double rk = 0.07957747154594767 * sqrt(rdet);   // (4 pi)^-1 |H|^-1/2
+        *f = rk / p.n + r0[0];
+        g00 = r0[1] + (-0.5 * rk * hi00) / p.n;
+        g01 = r1[0] + 2.0 * (-0.5 * rk * hi01) / p.n;
+        g11 = r1[1] + (-0.5 * rk * hi11) / p.n;
+    }
+    // dF/dR = 2 G_ind R (G_ind off-diagonal = g01 / 2), chain rule to theta
+    const double G00 = g00, G01 = 0.5 * g01, G11 = g11;
+    const double R00 = Rm[0], R10 = Rm[1], R11 = Rm[2];
+    const double d00 = 2.0 * (G00 * R00 + G01 * R10);
+    const double d10 = 2.0 * (G01 * R00 + G11 * R10);
+    const double d11 = 2.0 * (G11 * R11);
+    gt[0] = d00 * R00;
+    gt[1] = d10;
+    gt[2] = d11 * R11;
+}
+
+__device__ void sel_new_direction(SelOpt& s) {
+    for (int i = 0; i < 3; ++i) {
+        double v = 0.0;
+        for (int j = 0; j < 3; ++j) v -= s.Binv[i * 3 + j] * s.g[j];
+        s.dir[i] = v;
+    }
+    s.slope = s.dir[0] * s.g[0] + s.dir[1] * s.g[1] + s.dir[2] * s.g[2];
+    if (!(s.slope < 0.0)) {
+        const double gn = fmax(fabs(s.g[0]), fmax(fabs(s.g[1]), fabs(s.g[2])));
+        const double sc = (gn > 0) ? 0.1 / gn : 1.0;
+        for (int i = 0; i < 9; ++i) s.Binv[i] = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            s.Binv[i * 4] = sc;
+            s.dir[i] = -sc * s.g[i];
+        }
+        s.slope = s.dir[0] * s.g[0] + s.dir[1] * s.g[1] + s.dir[2] * s.g[2];
+    }
+    const double dm = fmax(fabs(s.dir[0]), fmax(fabs(s.dir[1]), fabs(s.dir[2])));
+    if (dm > 1.0) {
+        for (int i = 0; i < 3; ++i) s.dir[i] /= dm;
+        s.slope /= dm;
+    }
+    s.step = 1.0;
+    s.ls = 0;
+    for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+}
+
+// consume the evaluation (fn, gn) of the trial point th_try
+__device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter) {
+    if (s.first) {
+        s.first = 0;
+        s.f = fn;
+        for (int i = 0; i < 3; ++i) {
+            s.th[i] = s.th_try[i];
+            s.g[i] = gn[i];
+        }
+        if (!isfinite(fn)) {
+            s.done = 1;
+            s.status = 2;
+            return;
+        }
+        const double gm = fmax(fabs(gn[0]), fmax(fabs(gn[1]), fabs(gn[2])));
+        const double sc = (gm > 0) ? 0.1 / gm : 1.0;
+        for (int i = 0; i < 9; ++i) s.Binv[i] = 0.0;
+        for (int i = 0; i < 3; ++i) s.Binv[i * 4] = sc;
+        if (gm == 0.0) {
+            s.done = 1;
+            return;
+        }
+        sel_new_direction(s);
+        return;
+    }
+    if (isfinite(fn) && fn <= s.f + 1e-4 * s.step * s.slope) {
+        double sv[3], yv[3], sy = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            sv[i] = s.th_try[i] - s.th[i];
+            yv[i] = gn[i] - s.g[i];
+            sy += sv[i] * yv[i];
+        }
+        if (sy > 1e-300) {
+            double By[3], yBy = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                By[i] = 0.0;
+                for (int j = 0; j < 3; ++j) By[i] += s.Binv[i * 3 + j] * yv[j];
+                yBy += yv[i] * By[i];
+            }
+            const double rsy = 1.0 / sy;   // one FP64 division for the nine entries
+            const double c1 = (sy + yBy) * rsy * rsy;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    s.Binv[i * 3 + j] += c1 * sv[i] * sv[j] - (By[i] * sv[j] + sv[i] * By[j]) * rsy;
+        }
+        const double fold = s.f;
+        double gm = 0.0, tn = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            s.th[i] = s.th_try[i];
+            s.g[i] = gn[i];
+            gm = fmax(gm, fabs(gn[i]));
+            tn = fmax(tn, fabs(sv[i]));
+        }
+        s.f = fn;
+        s.iter++;
+        if (s.iter >= max_iter) {
+            s.done = 1;
+            s.status = 1;
+        } else if (fabs(fold - fn) <= 1e-12 * fabs(fn) + 1e-300 || tn < 1e-10 || gm < 1e-12 * (fabs(fn) + 1e-300)) {
+            s.done = 1;
+        } else {
+            sel_new_direction(s);
+        }
+    } else {
+        s.step *= 0.5;
+        s.ls++;
+        if (s.ls > 30) {
+            s.done = 1;
+        } else {
+            for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+        }
+    }
+}
+
+// One cluster per start.  Every CTA keeps its own copy of the optimiser
+// state and runs the same deterministic steps on the same sums (each CTA
+// receives every partial), so the copies stay identical and a round needs
+// only the two cluster barriers of the evaluation itself.
+__global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __restrict__ starts,
+                                                  const float2* __restrict__ twpool) {
+    using C = float2;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double cl_red[64];
+    __shared__ double res[2][2];
+    __shared__ FusedItem<float> items[2];
+    __shared__ SelOpt opt;
+    __shared__ int ctl[2];              // [valid, done] of this round
+    __shared__ double Hs[4], Rs[3], aux[3];
+    C* gat = reinterpret_cast<C*>(smem_raw);
+    float* spc = reinterpret_cast<float*>(gat + p.gat_elems);
+    C* tw1 = reinterpret_cast<C*>(spc + p.spc_elems);
+    C* tw0 = tw1 + p.pmax;
+    C* bufa = tw0 + p.pmax;
+    C* bufb = bufa + padded_cap(p.cap);
+    const int rank = (int)cluster.block_rank();
+    const int start = blockIdx.x / p.cs;
+    if (threadIdx.x == 0) {
+        const SelStart& st = starts[start];
+        for (int i = 0; i < 3; ++i) opt.th_try[i] = st.th[i];
+        opt.first = 1;
+        opt.done = 0;
+        opt.iter = 0;
+        opt.evals = 0;
+        opt.status = 0;
+        opt.f = INFINITY;
+        opt.flops = 0.0;
+        opt.bytes = 0.0;
+    }
+    __syncthreads();
+    const int max_rounds = 40 * p.max_iter + 2;
+    for (int round = 0; round < max_rounds; ++round) {
+        if (threadIdx.x < 32) {
+            const int dn = opt.done;
+            const bool v = dn ? false : sel_prepare(p, opt.th_try, items, Hs, Rs, aux);
+            if (threadIdx.x == 0) {
+                ctl[0] = v ? 1 : 0;
+                ctl[1] = dn;
+            }
+        }
+        __syncthreads();
+        const int valid = ctl[0], done = ctl[1];
+        if (done) break;
+        if (valid) {
+            sel_eval2(cluster, items[0], items[1], p.cs, rank, p.chunk, gat, spc, tw1, tw0, bufa, bufb, twpool, cl_red,
+                      &res[0][0]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double fn = INFINITY, gt[3] = {0.0, 0.0, 0.0};
+            if (valid) {
+                sel_assemble(p, Hs, Rs, res[0], res[1], aux[0], &fn, gt);
+                opt.evals++;
+                opt.flops += aux[1];
+                opt.bytes += aux[2];
+            }
+            sel_update(opt, fn, gt, p.max_iter);
+        }
+        __syncthreads();
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        SelStart& st = starts[start];
+        for (int i = 0; i < 3; ++i) st.th[i] = opt.th[i];
+        st.f = opt.f;
+        st.evals = opt.evals;
+        st.iters = opt.iter;
+        st.status = opt.done ? opt.status : 1;
+        st.flops = opt.flops;
+        st.bytes = opt.bytes;
+    }
+}
+
+cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts, const float2* twpool,
+                            cudaStream_t st) {
+    const size_t sm = sizeof(float2) * (size_t)(prm.gat_elems + 2 * prm.pmax + 2 * padded_cap(prm.cap)) +
+                      sizeof(float) * (size_t)prm.spc_elems;
+    static size_t set_bytes = 0;
+    if (sm > set_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_select2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_select2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        set_bytes = sm;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nstarts * prm.cs), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)prm.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_select2d, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return cudaErrorNotSupported;
+    }
+    return cudaLaunchKernelEx(&cfg, k_select2d, prm, starts, twpool);
+}
+
 // ------------------------------------------------------------ launchers
 template <typename real>
 static size_t smem_bytes(int cap, int pmax) {
@@ -1099,11 +1644,18 @@ static cudaError_t launch_fused2d_r(const FusedItem<real>* items, int nitems, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (cs > 8) {
-        // clusters above the portable size must be schedulable with this shared-memory footprint
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_fused2d<real, R>, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            return cudaErrorNotSupported;
+        // clusters above the portable size must be schedulable with this
+        // shared-memory footprint (checked once per footprint)
+        static size_t ok_bytes = 0, bad_bytes = ~(size_t)0;
+        if (sm > ok_bytes) {
+            if (sm >= bad_bytes) return cudaErrorNotSupported;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_fused2d<real, R>, &cfg) != cudaSuccess || nclusters < 1) {
+                cudaGetLastError();
+                bad_bytes = std::min(bad_bytes, sm);
+                return cudaErrorNotSupported;
+            }
+            ok_bytes = sm;
         }
     }
     return cudaLaunchKernelEx(&cfg, k_fused2d<real, R>, items, cs, gat_elems, spc_pad, cap, pmax, twpool, out,

@@ -141,6 +141,42 @@ cudaError_t launch_fused2d(const FusedItem<real>* items, int nitems, int rmax, i
                            int cap, int pmax, const typename Cpx<real>::T* twpool, double* out, int* errflag,
                            cudaStream_t st);
 
+// ---- device-resident bandwidth selection (d = 2, FP32): one cluster per
+// start runs the whole quasi-Newton search; see k_select2d in engine.cu.
+struct SelSpec {            // one padded-size pair and its count spectrum
+    int P0, P1;
+    AxisPlan a0, a1;
+    const float* spec;
+    double scale;           // 1 / (n^2 P_0 P_1)
+    double fl_line, fl_fix, by;   // algorithmic work of one evaluation: fl_fix + S_0 fl_line flops, by bytes
+};
+struct SelStart {           // in: start point; out: end point
+    double th[3];           // Cholesky parameters (log R00, R10, log R11)
+    double f;
+    double flops, bytes;    // out: algorithmic work of this start's evaluations
+    int evals, iters, status;   // status: 0 converged / stalled, 1 iteration cap, 2 no valid start
+};
+struct SelectParams {
+    int method;             // 0: LSCV (Eq. 10), 1: SCV (whole kernel in FP32)
+    int max_iter;
+    int cs;                 // CTAs per cluster
+    int nspec;
+    int widest;             // LSCV: support from lambda_max(2H) instead of lambda_max(H)
+    int M0, M1;
+    int Lcap;               // trial points needing a larger support are outside the search
+    int chunk;              // lines (and columns) per shared-memory batch
+    int gat_elems, spc_elems, cap, pmax;   // shared-memory layout (complex / real elements)
+    double n, tau;
+    double delta0, delta1;
+    double G[4];            // SCV pilot, row-major
+    const int* ptab0;       // P_0 for support L_0 (index L_0 <= Lcap)
+    const int* ptab1;
+    const SelSpec* specs;
+    int* errflag;
+};
+cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts,
+                            const float2* twpool, cudaStream_t st);
+
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
 
 // Binning (binning.cu).  Grid node k along axis a is lo[a] + k delta[a],
@@ -155,15 +191,21 @@ struct GridDesc {
     long long M[MAXD];
 };
 
+// acc = double (FP64 atomics) or unsigned long long (fixed point: each
+// weight is added as round(w * qscale))
 template <typename acc>
 cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, acc* counts, long long ncells,
-                              unsigned long long* outside, int nsm, cudaStream_t st);
+                              unsigned long long* outside, double qscale, int nsm, cudaStream_t st);
+// dst[i] = (float)(src[i] * unit)
+cudaError_t launch_fix_to_f32(const unsigned long long* src, float* dst, long long n, double unit, cudaStream_t st);
 cudaError_t launch_bin_simple(const double* X, long long n, const GridDesc& g, int* counts, long long ncells,
                               unsigned long long* outside, int nsm, cudaStream_t st);
 template <typename real>
 cudaError_t launch_int_to_real(const int* src, real* dst, long long n, cudaStream_t st);
 cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t st);
-// pass 0: out[k] += sum_i X_ik; pass 1: out[a*d+b] += sum_i (X_ia - mean_a)(X_ib - mean_b)
+// pass 0: out[blk*d + k] = block sums of X_ik; pass 1: out[blk*d*d + a*d+b] =
+// block sums of (X_ia - mean_a)(X_ib - mean_b), blk < moments_blocks(n, nsm)
+int moments_blocks(long long n, int nsm);
 cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
                            cudaStream_t st);
 
