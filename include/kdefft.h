@@ -185,6 +185,19 @@ int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G,
                     int n_starts, int max_iter, double* H_out, double* f_out,
                     int64_t* n_evals);
 
+/* The same minimisation with the derivative-free Nelder-Mead method the
+ * paper's experiments use (Sec. 6: reflection 1.0, contraction 0.5,
+ * expansion 2.0), for parity with its selections.  Simplex in the same
+ * Cholesky parameters theta (log diagonal), initial vertices theta_0 and
+ * theta_0 + 0.1 e_i; shrink towards the best vertex by the contraction
+ * factor; stop when f_worst - f_best <= 2^-26 (|f_best| + 2^-26) or after
+ * max_iter objective evaluations per start (max_iter < 1: 500).  Only
+ * objective values are evaluated.  Same arguments, domain, starts and
+ * errors as kdefft_select_H. */
+int kdefft_select_H_nm(kdefft_ds ds, int method, const double* H0, const double* G,
+                       int n_starts, int max_iter, double* H_out, double* f_out,
+                       int64_t* n_evals);
+
 /* LSCV(H) and its gradient for many datasets at once: dataset i gets
  * nH_per_ds[i] consecutive bandwidths from H; every (dataset, H) unit runs
  * in one batched launch sequence.  val: total nH FP64; grad: NULL or total

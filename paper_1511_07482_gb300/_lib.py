@@ -28,7 +28,7 @@ DT_F32, DT_F64, DT_I32 = 0, 1, 2
 EXPORTS = [
     "kdefft_opts_default", "kdefft_create", "kdefft_destroy", "kdefft_bin", "kdefft_ds_destroy",
     "kdefft_ds_set_opts", "kdefft_ds_info", "kdefft_counts", "kdefft_plan", "kdefft_psi",
-    "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H",
+    "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H", "kdefft_select_H_nm",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine",
 ]
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "kdefft_pi": (I, [P, P, I, P, P, P]),
         "kdefft_eta02": (I, [P, P, I, P, P]),
         "kdefft_select_H": (I, [P, I, P, P, I, I, P, P, P]),
+        "kdefft_select_H_nm": (I, [P, I, P, P, I, I, P, P, P]),
         "kdefft_batch_lscv": (I, [P, I, P, P, P, P, P]),
         "kdefft_profile": (I, [P, I]),
         "kdefft_profile_read": (I, [P, P, I, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -329,12 +330,19 @@ class Dataset:
         _check(load().kdefft_eta02(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p)))
         return val
 
-    def select_H(self, method=LSCV, H0=None, G=None, n_starts=1, max_iter=100):
+    def select_H(self, method=LSCV, H0=None, G=None, n_starts=1, max_iter=None, optimizer="bfgs"):
+        """Minimise the objective over H: optimizer "bfgs" (quasi-Newton on
+        the exact gradients, max_iter iterations, default 100) or
+        "nelder-mead" (the paper's derivative-free parity mode, max_iter
+        objective evaluations per start, default 500)."""
+        if optimizer not in ("bfgs", "nelder-mead"):
+            raise ValueError("optimizer must be 'bfgs' or 'nelder-mead'")
         Ha, pH = _host_f64(H0) if H0 is not None else (None, None)
         Ga, pG = _host_f64(G) if G is not None else (None, None)
         Hout = np.zeros((self.d, self.d))
         f = C.c_double()
         ne = C.c_int64()
-        _check(load().kdefft_select_H(self.h, method, pH, pG, int(n_starts), int(max_iter),
-                                      Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
+        fn = load().kdefft_select_H if optimizer == "bfgs" else load().kdefft_select_H_nm
+        _check(fn(self.h, method, pH, pG, int(n_starts), int(max_iter or 0),
+                  Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
         return Hout, f.value, ne.value

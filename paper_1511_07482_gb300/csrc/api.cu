@@ -2100,29 +2100,43 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     };
     // cluster size, batch size and support cap from the shared-memory budget
     // The two packed pairs are transformed together: the gather holds both
-    // and a batch holds `chunk` lines of each.  The largest support cap that
-    // fits comes first, then the largest batch at that cap.
-    const size_t budget = 110 * 1024;   // two CTAs per SM
-    int cs = 16, Lcap = std::max(M0, M1) - 1, chunk = 0;
-    int gat = 0, spc = 0, cap = 0, pmax = 0;
-    for (;;) {
-        const int L0 = std::min(Lcap, M0 - 1), L1 = std::min(Lcap, M1 - 1);
-        const int P0 = pmin(M0 + L0), P1 = pmin(M1 + L1);
-        if (P0 > MAXP || P1 > MAXP) return KDEFFT_ERR_UNSUPPORTED;
-        const int cpc = (P1 / 2 + 1 + cs - 1) / cs;
-        gat = (2 * (2 * std::max(L0, L1) + 1) * cpc + 1) & ~1;
-        spc = cpc * P0;
-        pmax = std::max(P0, P1);
-        for (chunk = 8; chunk >= 3; --chunk) {
-            cap = 2 * chunk * pmax;
-            const size_t need =
-                sizeof(float2) * (size_t)(gat + 2 * pmax + 2 * (cap + cap / 16 + 1)) + sizeof(float) * spc;
-            if (need <= budget) break;
+    // and a batch holds `chunk` lines of each.  For a cluster size and a
+    // shared-memory budget, the largest support cap that fits comes first,
+    // then the largest batch at that cap.
+    struct Layout {
+        int cs = 0, Lcap = 0, chunk = 0, gat = 0, spc = 0, cap = 0, pmax = 0;
+    };
+    auto size_for = [&](int cs, size_t budget, Layout& lay) {
+        int Lcap = std::max(M0, M1) - 1;
+        for (;;) {
+            const int L0 = std::min(Lcap, M0 - 1), L1 = std::min(Lcap, M1 - 1);
+            const int P0 = pmin(M0 + L0), P1 = pmin(M1 + L1);
+            if (P0 <= MAXP && P1 <= MAXP) {
+                const int cpc = (P1 / 2 + 1 + cs - 1) / cs;
+                const int gat = (2 * (2 * std::max(L0, L1) + 1) * cpc + 1) & ~1;
+                const int spc = cpc * P0, pmax = std::max(P0, P1);
+                for (int chunk = 8; chunk >= 3; --chunk) {
+                    const int cap = 2 * chunk * pmax;
+                    const size_t need =
+                        sizeof(float2) * (size_t)(gat + 2 * pmax + 2 * (cap + cap / 16 + 1)) + sizeof(float) * spc;
+                    if (need <= budget) {
+                        lay = Layout{cs, Lcap, chunk, gat, spc, cap, pmax};
+                        return true;
+                    }
+                }
+            }
+            if (Lcap <= 8) return false;
+            Lcap = Lcap * 3 / 4;
         }
-        if (chunk >= 3) break;
-        if (Lcap <= 8) return KDEFFT_ERR_UNSUPPORTED;
-        Lcap = Lcap * 3 / 4;
-    }
+    };
+    // 16-CTA clusters, two CTAs per SM.  (Measured: smaller clusters, which
+    // let every start of a 16-start search be resident at once, lose more to
+    // the larger share of each CTA than they gain from the absent second
+    // wave.)
+    Layout lay;
+    if (!size_for(16, 110 * 1024, lay)) return KDEFFT_ERR_UNSUPPORTED;
+    const int cs = lay.cs, Lcap = lay.Lcap, chunk = lay.chunk, gat = lay.gat, spc = lay.spc, cap = lay.cap,
+              pmax = lay.pmax;
     // the (L0, L1) pairs met as lambda grows: breakpoints of ceil(tau s / delta_k)
     std::vector<double> brk;
     for (int k = 0; k < 2; ++k)
@@ -2251,13 +2265,13 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     return KDEFFT_OK;
 }
 
-extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
-                               int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
+static int select_H_impl(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts, int max_iter,
+                         bool nelder_mead, double* H_out, double* f_out, int64_t* n_evals) {
     if (!ds || !H_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
     if (method != KDEFFT_LSCV && method != KDEFFT_SCV && method != KDEFFT_PI)
         return fail(KDEFFT_ERR_ARG, "unknown method");
     if (n_starts < 1) n_starts = 1;
-    if (max_iter < 1) max_iter = 100;
+    if (max_iter < 1) max_iter = nelder_mead ? 500 : 100;
     KCU(cudaSetDevice(ds->ctx->device));
     const int d = ds->d;
     Opt o{d, d * (d + 1) / 2};
@@ -2323,6 +2337,36 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
         return KDEFFT_OK;
     };
 
+    // batched evaluation of values only
+    auto evaluate_values = [&](const std::vector<std::vector<double>>& ths, std::vector<double>& f) -> int {
+        HostTimer ht(ds->ctx, "host:eval");
+        const int m = (int)ths.size();
+        f.assign(m, INFINITY);
+        std::vector<int> idx;
+        std::vector<double> Hs;
+        for (int i = 0; i < m; ++i) {
+            Mat H = theta_to_H(o, ths[i].data());
+            if (!in_domain(H)) continue;
+            idx.push_back(i);
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) Hs.push_back(H(a, b));
+        }
+        const int mv = (int)idx.size();
+        if (mv == 0) return KDEFFT_OK;
+        std::vector<double> v;
+        int r;
+        if (method == KDEFFT_LSCV)
+            r = eval_lscv(ds, Hs.data(), mv, v, nullptr);
+        else if (method == KDEFFT_SCV)
+            r = eval_scv(ds, Hs.data(), mv, Gm, v, nullptr, /*split64=*/false);
+        else
+            r = eval_pi(ds, Hs.data(), mv, psi4, v, nullptr);
+        if (r != KDEFFT_OK) return r;
+        evals += mv;
+        for (int j = 0; j < mv; ++j) f[idx[j]] = v[j];
+        return KDEFFT_OK;
+    };
+
     // start points: Hstart, then dilations and plane rotations of it
     struct State {
         std::vector<double> th, g, dir, Binv, th_try;
@@ -2361,6 +2405,160 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
         H_to_theta(o, Hs, st[s].th.data());
         st[s].Binv.assign((size_t)p * p, 0.0);
         for (int i = 0; i < p; ++i) st[s].Binv[i * p + i] = 1.0;
+    }
+    // the reported value at the chosen point: SCV iterations compare FP32
+    // values, the reported one takes the FP64 route for the cancelling terms
+    auto report = [&](const std::vector<double>& th, double f) -> int {
+        if (!std::isfinite(f)) return fail(KDEFFT_ERR_ARG, "no start point inside the search domain");
+        Mat Hb = theta_to_H(o, th.data());
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
+        if (method == KDEFFT_SCV) {
+            std::vector<double> v;
+            KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
+            f = v[0];
+        }
+        if (f_out) *f_out = f;
+        if (n_evals) *n_evals = evals;
+        return KDEFFT_OK;
+    };
+    if (nelder_mead) {
+        // Nelder-Mead on theta with the factors of Sec. 6 (reflection 1,
+        // contraction 0.5, expansion 2; shrink towards the best vertex by
+        // the contraction factor), initial simplex theta_0 + 0.1 e_i, stop
+        // when f_worst - f_best <= reltol (|f_best| + reltol) with
+        // reltol = 2^-26 or after max_iter objective evaluations per start.
+        // Starts run in lock-step: every round evaluates the pending points
+        // of all starts in one batched call (values only).
+        const double alpha = 1.0, beta = 0.5, gamma = 2.0, reltol = 1.4901161193847656e-8;
+        struct NM {
+            std::vector<std::vector<double>> x, pend;
+            std::vector<double> fx, c, xr, xe, xc;
+            double fr = 0.0;
+            int phase = 0, nev = 0, worst = 0, second = 0, best = 0;
+            bool outside = false, done = false;
+        };
+        std::vector<NM> nm(n_starts);
+        for (int s = 0; s < n_starts; ++s) {
+            NM& q = nm[s];
+            q.x.assign(p + 1, st[s].th);
+            for (int i = 0; i < p; ++i) q.x[i + 1][i] += 0.1;
+            q.pend = q.x;
+            q.fx.assign(p + 1, INFINITY);
+        }
+        auto lin = [&](const std::vector<double>& a, const std::vector<double>& b, double t) {
+            std::vector<double> r(p);
+            for (int i = 0; i < p; ++i) r[i] = a[i] + t * (b[i] - a[i]);   // a + t (b - a)
+            return r;
+        };
+        auto begin_iteration = [&](NM& q) {
+            q.best = q.worst = 0;
+            for (int i = 1; i <= p; ++i) {
+                if (q.fx[i] < q.fx[q.best]) q.best = i;
+                if (q.fx[i] >= q.fx[q.worst]) q.worst = i;
+            }
+            q.second = (q.worst == q.best) ? (q.best + 1) % (p + 1) : q.best;
+            for (int i = 0; i <= p; ++i)
+                if (i != q.worst && q.fx[i] >= q.fx[q.second]) q.second = i;
+            const double fb = q.fx[q.best], fw = q.fx[q.worst];
+            if (!std::isfinite(fb) || q.nev >= max_iter || (std::isfinite(fw) && fw - fb <= reltol * (std::fabs(fb) + reltol))) {
+                q.done = true;
+                q.pend.clear();
+                return;
+            }
+            q.c.assign(p, 0.0);
+            for (int i = 0; i <= p; ++i)
+                if (i != q.worst)
+                    for (int k = 0; k < p; ++k) q.c[k] += q.x[i][k] / p;
+            q.xr = lin(q.c, q.x[q.worst], -alpha);   // c + alpha (c - x_worst)
+            q.pend = {q.xr};
+            q.phase = 1;
+        };
+        auto consume = [&](NM& q, const std::vector<double>& v) {
+            q.nev += (int)v.size();
+            switch (q.phase) {
+                case 0:
+                    q.fx = v;
+                    begin_iteration(q);
+                    break;
+                case 1:
+                    q.fr = v[0];
+                    if (q.fr < q.fx[q.best]) {
+                        q.xe = lin(q.c, q.xr, gamma);   // c + gamma (x_r - c)
+                        q.pend = {q.xe};
+                        q.phase = 2;
+                    } else if (q.fr < q.fx[q.second]) {
+                        q.x[q.worst] = q.xr;
+                        q.fx[q.worst] = q.fr;
+                        begin_iteration(q);
+                    } else {
+                        q.outside = q.fr < q.fx[q.worst];
+                        q.xc = q.outside ? lin(q.c, q.xr, beta) : lin(q.c, q.x[q.worst], beta);
+                        q.pend = {q.xc};
+                        q.phase = 3;
+                    }
+                    break;
+                case 2:
+                    if (v[0] < q.fr) {
+                        q.x[q.worst] = q.xe;
+                        q.fx[q.worst] = v[0];
+                    } else {
+                        q.x[q.worst] = q.xr;
+                        q.fx[q.worst] = q.fr;
+                    }
+                    begin_iteration(q);
+                    break;
+                case 3:
+                    if (q.outside ? v[0] <= q.fr : v[0] < q.fx[q.worst]) {
+                        q.x[q.worst] = q.xc;
+                        q.fx[q.worst] = v[0];
+                        begin_iteration(q);
+                    } else {
+                        q.pend.clear();
+                        for (int i = 0; i <= p; ++i)
+                            if (i != q.best) {
+                                q.x[i] = lin(q.x[q.best], q.x[i], beta);
+                                q.pend.push_back(q.x[i]);
+                            }
+                        q.phase = 4;
+                    }
+                    break;
+                default: {
+                    int k = 0;
+                    for (int i = 0; i <= p; ++i)
+                        if (i != q.best) q.fx[i] = v[k++];
+                    begin_iteration(q);
+                }
+            }
+        };
+        for (int round = 0; round < 4 * max_iter + 8; ++round) {
+            std::vector<std::vector<double>> ths;
+            std::vector<std::pair<int, int>> owner;   // (start, count)
+            for (int s = 0; s < n_starts; ++s)
+                if (!nm[s].done && !nm[s].pend.empty()) {
+                    owner.push_back({s, (int)nm[s].pend.size()});
+                    for (auto& t : nm[s].pend) ths.push_back(t);
+                }
+            if (owner.empty()) break;
+            std::vector<double> f;
+            KCHK(evaluate_values(ths, f));
+            size_t k = 0;
+            for (auto& ow : owner) {
+                std::vector<double> v(f.begin() + k, f.begin() + k + ow.second);
+                k += ow.second;
+                consume(nm[ow.first], v);
+            }
+        }
+        int bs = 0, bv = 0;
+        double fb = INFINITY;
+        for (int s = 0; s < n_starts; ++s)
+            for (int i = 0; i <= p; ++i)
+                if (nm[s].fx[i] < fb) {
+                    fb = nm[s].fx[i];
+                    bs = s;
+                    bv = i;
+                }
+        return report(nm[bs].x[bv], fb);
     }
     if (d == 2) {
         std::vector<std::vector<double>> ths, tho;
@@ -2505,19 +2703,15 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
     int best = 0;
     for (int s = 1; s < n_starts; ++s)
         if (st[s].f < st[best].f) best = s;
-    if (!std::isfinite(st[best].f)) return fail(KDEFFT_ERR_ARG, "no start point inside the search domain");
-    Mat Hb = theta_to_H(o, st[best].th.data());
-    for (int a = 0; a < d; ++a)
-        for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
-    double fbest = st[best].f;
-    if (method == KDEFFT_SCV) {
-        // the iterations compared FP32 values; the reported value takes the
-        // FP64 route for the cancelling Gaussian terms
-        std::vector<double> v;
-        KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
-        fbest = v[0];
-    }
-    if (f_out) *f_out = fbest;
-    if (n_evals) *n_evals = evals;
-    return KDEFFT_OK;
+    return report(st[best].th, st[best].f);
+}
+
+extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
+                               int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
+    return select_H_impl(ds, method, H0, G, n_starts, max_iter, false, H_out, f_out, n_evals);
+}
+
+extern "C" int kdefft_select_H_nm(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
+                                  int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
+    return select_H_impl(ds, method, H0, G, n_starts, max_iter, true, H_out, f_out, n_evals);
 }

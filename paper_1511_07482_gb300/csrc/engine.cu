@@ -1535,10 +1535,14 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     }
 }
 
-cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts, const float2* twpool,
-                            cudaStream_t st) {
-    const size_t sm = sizeof(float2) * (size_t)(prm.gat_elems + 2 * prm.pmax + 2 * padded_cap(prm.cap)) +
-                      sizeof(float) * (size_t)prm.spc_elems;
+static size_t select2d_smem(const SelectParams& prm) {
+    return sizeof(float2) * (size_t)(prm.gat_elems + 2 * prm.pmax + 2 * padded_cap(prm.cap)) +
+           sizeof(float) * (size_t)prm.spc_elems;
+}
+
+static cudaError_t select2d_config(const SelectParams& prm, int nstarts, cudaStream_t st, cudaLaunchConfig_t& cfg,
+                                   cudaLaunchAttribute* attr) {
+    const size_t sm = select2d_smem(prm);
     static size_t set_bytes = 0;
     if (sm > set_bytes) {
         cudaError_t e = cudaFuncSetAttribute(k_select2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1547,18 +1551,26 @@ cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstar
         if (e != cudaSuccess) return e;
         set_bytes = sm;
     }
-    cudaLaunchConfig_t cfg = {};
+    cfg = cudaLaunchConfig_t{};
     cfg.gridDim = dim3((unsigned)(nstarts * prm.cs), 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)prm.cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts, const float2* twpool,
+                            cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = select2d_config(prm, nstarts, st, cfg, attr);
+    if (e != cudaSuccess) return e;
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, k_select2d, &cfg) != cudaSuccess || nclusters < 1) {
         cudaGetLastError();

@@ -296,6 +296,43 @@ def test_batch_matches_single(ctx):
         k += len(w.H)
 
 
+def _gauss_case(n=3000, seed=81):
+    """A correlated bivariate Gaussian sample: its LSCV and SCV have one minimum."""
+    rng = np.random.default_rng(seed)
+    X = rng.multivariate_normal([0.0, 1.0], [[1.0, 0.5], [0.5, 2.0]], size=n)
+    Hns = synthetic.normal_scale(X)
+    lo, hi = synthetic.grid_range(X, Hns)
+    return X, lo, hi, Hns
+
+
+@pytest.mark.parametrize("method", ["lscv", "scv"])
+def test_nelder_mead_parity_mode(ctx, method):
+    """The paper's derivative-free search (Sec. 6: reflection 1, contraction
+    0.5, expansion 2) on a Gaussian sample: the value returned is the
+    objective at the H returned, the evaluation budget per start is kept, the
+    end point is at least as good as the gradient search's from the same
+    starts (the support L_k steps with H, Eq. 26, so the binned objective is
+    piecewise smooth and a line search can stop at a step; the simplex does
+    not), and a gradient search started there improves it by less than the
+    FP32 value tolerance: a numerical minimum."""
+    from paper_1511_07482_gb300 import LSCV, SCV
+    X, lo, hi, Hns = _gauss_case()
+    ds = ctx.bin(X, lo, hi, [80, 72])
+    m = LSCV if method == "lscv" else SCV
+    Hb, fb, _ = ds.select_H(m, G=Hns, n_starts=4, max_iter=100)
+    Hn, fn, ne = ds.select_H(m, G=Hns, n_starts=4, max_iter=400, optimizer="nelder-mead")
+    assert ne <= 4 * (400 + 3)
+    v = ds.scv(Hn, Hns)[0] if m == SCV else ds.lscv(Hn)[0]
+    assert v == pytest.approx(fn, rel=1e-6)
+    assert fn <= fb + 1e-5 * abs(fb)
+    assert fn == pytest.approx(fb, rel=5e-3)
+    Hp, fp, _ = ds.select_H(m, H0=Hn, G=Hns, n_starts=1, max_iter=100)
+    assert fp >= fn - 1e-5 * abs(fn)
+    with pytest.raises(ValueError):
+        ds.select_H(m, G=Hns, optimizer="simplex")
+    ds.close()
+
+
 @pytest.mark.parametrize("method", ["lscv", "scv"])
 def test_device_resident_selection_matches_host_driven(method):
     """The device-resident search (one cluster per start) and the
@@ -306,10 +343,7 @@ def test_device_resident_selection_matches_host_driven(method):
     another basin, so there each engine is held to its own objective: the
     value it returns is the objective at the H it returns."""
     from paper_1511_07482_gb300 import ENGINE_AUTO, ENGINE_HOST_SELECT, LSCV, SCV, Context
-    rng = np.random.default_rng(81)
-    X = rng.multivariate_normal([0.0, 1.0], [[1.0, 0.5], [0.5, 2.0]], size=3000)
-    Hns = synthetic.normal_scale(X)
-    lo, hi = synthetic.grid_range(X, Hns)
+    X, lo, hi, Hns = _gauss_case()
     mix = _case(2, [80, 72], n=3000, seed=81)
     m = LSCV if method == "lscv" else SCV
     res = {}
