@@ -53,6 +53,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(base: int, rank: int, stride: int = 1000) -> int:
+    """Seed of this rank's replica of the workload: independent datasets per
+    rank, the same on every run."""
+    return base + stride * rank
+
+
+def combine_ranks(local, world: int, device=None):
+    """[time_ms, evals, e2e_time_ms, e2e_evals] of this rank -> the whole
+    job's: times are the maximum over ranks (the job ends with its slowest
+    rank), evaluation counts the sum over ranks."""
+    if world == 1:
+        return [float(v) for v in local]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in local], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return [mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -147,7 +168,7 @@ def run_ours(args):
     ctx = Context(local)
     stream = torch.cuda.current_stream(dev)
     if args.workload == "select2d":
-        w = synthetic.mixture_2d_large(seed=2 + 1000 * rank)
+        w = synthetic.mixture_2d_large(seed=rank_seed(2, rank))
         X_dev = torch.from_numpy(w.X).to(dev)
         X_pin = torch.from_numpy(w.X).pin_memory()
 
@@ -160,7 +181,7 @@ def run_ours(args):
         workload_desc = (w.name + ": bin + full LSCV and SCV minimisation (3 free entries of H, adjoint "
                          "gradients)")
     elif args.workload == "psi4_3d":
-        w = synthetic.mixture_3d(seed=3 + 1000 * rank)
+        w = synthetic.mixture_3d(seed=rank_seed(3, rank))
         X_dev = torch.from_numpy(w.X).to(dev)
         X_pin = torch.from_numpy(w.X).pin_memory()
 
@@ -171,7 +192,7 @@ def run_ours(args):
             return len(w.H), None
         workload_desc = w.name + ": bin + psi_4 (15 unique partials) for 256 candidate H in one call"
     elif args.workload == "uneven512":
-        ws = synthetic.batched_uneven(base_seed=4 + 100000 * rank)
+        ws = synthetic.batched_uneven(base_seed=rank_seed(4, rank, 100000))
         w = ws[0]
         X_dev = [torch.from_numpy(v.X).to(dev) for v in ws]
         X_pin = [torch.from_numpy(v.X).pin_memory() for v in ws]
@@ -185,7 +206,7 @@ def run_ours(args):
         workload_desc = "512 bivariate datasets (n log-uniform 1e3..1e5, grids 64^2..256^2): bin + LSCV and " \
                         "gradient for 16 H each in one batched call"
     elif args.workload == "lscv_batch16":
-        w = synthetic.mixture_2d_large(seed=2 + 1000 * rank)
+        w = synthetic.mixture_2d_large(seed=rank_seed(2, rank))
         X_dev = torch.from_numpy(w.X).to(dev)
         X_pin = torch.from_numpy(w.X).pin_memory()
 
@@ -197,7 +218,7 @@ def run_ours(args):
             return 20 * len(w.H), None
         workload_desc = w.name + ": bin + 20 batches of LSCV and gradient at 16 candidate H"
     else:  # plugin4d
-        w = synthetic.mixture_4d(seed=5 + 1000 * rank, n_candidates=16)
+        w = synthetic.mixture_4d(seed=rank_seed(5, rank), n_candidates=16)
         X_dev = torch.from_numpy(w.X).to(dev)
         X_pin = torch.from_numpy(w.X).pin_memory()
         from paper_1511_07482_gb300 import P_FIXED
@@ -256,14 +277,7 @@ def run_ours(args):
     ctx.profile(0)
 
     # max over ranks
-    tot = torch.tensor([t_total, float(evals), sum(e2e_times), float(e2e_evals)], dtype=torch.float64)
-    if world > 1:
-        tmax = tot.clone().to(dev)
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tmax[2:3], op=dist.ReduceOp.MAX)
-        s = tot.clone().to(dev)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        tot = torch.tensor([tmax[0].item(), s[1].item(), tmax[2].item(), s[3].item()], dtype=torch.float64)
+    tot = torch.tensor(combine_ranks([t_total, evals, sum(e2e_times), e2e_evals], world, dev), dtype=torch.float64)
     value = tot[1].item() / (tot[0].item() / 1000.0)
     e2e_value = tot[3].item() / (tot[2].item() / 1000.0)
 
