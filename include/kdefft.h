@@ -219,6 +219,33 @@ int kdefft_batch_lscv(kdefft_ctx ctx, int nds, const kdefft_ds* ds,
 enum { KDEFFT_ENGINE_AUTO = 0, KDEFFT_ENGINE_MULTIPASS = 1, KDEFFT_ENGINE_HOST_SELECT = 2 };
 int kdefft_set_engine(kdefft_ctx ctx, int engine);
 
+/* Autotuner (off by default).  When on, the first batch of each shape
+ * (dimension, precision, and the number of work items, largest padded size
+ * and largest support, each rounded up to a power of two) is run once per
+ * candidate configuration -- engine (fused cluster kernel for d = 2 /
+ * multi-pass), multi-pass tile capacity (1/2, 1 and 3/2 of the default
+ * lines x padded size per CTA batch), largest FFT radix (32 or 16 in FP32,
+ * 16 or 8 in FP64) -- each timed on the host clock over the whole batch;
+ * the fastest is kept for the shape and its results are the batch's.  Later
+ * batches of the shape use it directly.  Results of different candidates
+ * agree within the FP32 (FP64) tolerance of the evaluation. */
+int kdefft_set_autotune(kdefft_ctx ctx, int on);
+
+/* CUDA graphs (on by default).  A batch's launch sequence (staging copy,
+ * kernels, result copy) is captured once into a CUDA graph under its
+ * launch signature -- every device and pinned-host pointer, size, tile
+ * count and launch shape -- and replayed when a later batch has the same
+ * signature (the work items themselves are data read at replay time).  At
+ * most 64 graphs per context; the cache is emptied when full.  Disabled while
+ * profiling is on (kdefft_profile), so that each kernel keeps its own CUDA
+ * events. */
+int kdefft_set_graphs(kdefft_ctx ctx, int on);
+
+/* Counters of the two above since the context was created: shapes tuned,
+ * graphs captured, graph replays.  Any pointer may be NULL. */
+int kdefft_runtime_stats(kdefft_ctx ctx, int64_t* shapes_tuned,
+                         int64_t* graphs_captured, int64_t* graph_replays);
+
 /* LSCV value and gradient for one bandwidth without allocating any memory.
  * The paper has no counterpart: this is for callers that cannot allocate at
  * the point of the call -- code that runs under a device-memory budget fixed

@@ -30,7 +30,8 @@ EXPORTS = [
     "kdefft_ds_set_opts", "kdefft_ds_info", "kdefft_counts", "kdefft_plan", "kdefft_psi",
     "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H", "kdefft_select_H_nm",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
-    "kdefft_lscv_noalloc", "kdefft_set_engine",
+    "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
+    "kdefft_runtime_stats",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT = 0, 1, 2
 
@@ -87,6 +88,9 @@ def load(path: str = LIB_PATH):
                                     C.POINTER(C.c_int64)]),
         "kdefft_lscv_noalloc": (I, [I, P, P, I64, P, P, C.c_double, P, P]),
         "kdefft_set_engine": (I, [P, I]),
+        "kdefft_set_autotune": (I, [P, I]),
+        "kdefft_set_graphs": (I, [P, I]),
+        "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -195,6 +199,21 @@ class Context:
     def set_engine(self, engine: int):
         """ENGINE_AUTO (fused cluster kernel for d = 2) or ENGINE_MULTIPASS."""
         _check(load().kdefft_set_engine(self.h, int(engine)))
+
+    def set_autotune(self, on: bool = True):
+        """Time the candidate engine / tile / radix configurations on the first
+        batch of each shape and keep the fastest (kdefft_set_autotune)."""
+        _check(load().kdefft_set_autotune(self.h, int(bool(on))))
+
+    def set_graphs(self, on: bool = True):
+        """Replay repeated batch launch sequences from CUDA graphs (default on)."""
+        _check(load().kdefft_set_graphs(self.h, int(bool(on))))
+
+    def runtime_stats(self):
+        """{"shapes_tuned", "graphs_captured", "graph_replays"} since creation."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().kdefft_runtime_stats(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"shapes_tuned": a.value, "graphs_captured": b.value, "graph_replays": c.value}
 
     def profile(self, mode: int = 1):
         """1: reset counters and time every kernel with CUDA events; 2: keep

@@ -425,6 +425,7 @@ struct kdefft_ctx_s {
     int max_cluster = 16;     // largest cluster the fused engine may launch
     bool device_select = true;   // d = 2 FP32 selections run as one device-resident launch
     DevBuf sel_buf;           // device tables and start states of the device-resident selection
+    DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
     std::map<std::string, KStat> kstat;
     struct Pending {
         std::string name;
@@ -435,6 +436,22 @@ struct kdefft_ctx_s {
     std::vector<cudaEvent_t> evpool;
     int64_t launches = 0, h2d = 0, d2h = 0;
     std::vector<kdefft_ds> datasets;   // live datasets; destroyed with the context
+    // CUDA graphs of repeated launch sequences, keyed by launch signature
+    bool graphs = true;
+    cudaStream_t cap_stream = nullptr;   // capture stream, created on first use
+    struct GraphEntry {
+        cudaGraphExec_t exec;
+        int64_t launches;
+    };
+    std::map<std::vector<long long>, GraphEntry> gcache;
+    int64_t graphs_captured = 0, graph_replays = 0;
+    // autotuner: engine, tile capacity and radix cap per batch shape
+    struct Knobs {
+        int fused, cap, maxr;
+    };
+    bool autotune = false;
+    std::map<std::array<long long, 5>, Knobs> tuned;
+    int64_t keys_tuned = 0;
 };
 
 #include <chrono>
@@ -494,6 +511,53 @@ static void prof_flush(kdefft_ctx c) {
         c->evpool.push_back(p.b);
     }
     c->pending.clear();
+}
+
+// Run the stream work of one batch (`issue`: the copies and launches it
+// enqueues on c->stream) directly, or replay it from a CUDA graph cached
+// under its launch signature `sig` (every pointer, size and launch shape the
+// work depends on; the pinned staging buffers are read when the graph runs,
+// so new contents need no new graph).  Direct while profiling, so that
+// every kernel keeps its own CUDA events.
+template <typename F>
+static int run_graph(kdefft_ctx c, const std::vector<long long>& sig, F&& issue) {
+    if (!c->graphs || c->prof) return issue();
+    auto it = c->gcache.find(sig);
+    if (it == c->gcache.end()) {
+        if (!c->cap_stream) KCU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (c->gcache.size() >= 64) {
+            for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
+            c->gcache.clear();
+        }
+        // capture on the library's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); replay on the caller's
+        cudaStream_t user = c->stream;
+        const int64_t l0 = c->launches;
+        KCU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+        c->stream = c->cap_stream;
+        const int r = issue();
+        c->stream = user;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (r != KDEFFT_OK) {
+            if (g) cudaGraphDestroy(g);
+            c->launches = l0;
+            return r;
+        }
+        KCU(e);
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        KCU(ei);
+        it = c->gcache.emplace(sig, kdefft_ctx_s::GraphEntry{ex, c->launches - l0}).first;
+        c->launches = l0;
+        c->graphs_captured++;
+    } else {
+        c->graph_replays++;
+    }
+    c->launches += it->second.launches;
+    KCU(cudaGraphLaunch(it->second.exec, c->stream));
+    return KDEFFT_OK;
 }
 
 struct kdefft_ds_s {
@@ -807,9 +871,10 @@ static size_t spec_elems(int d, const int* P) {
 }
 
 template <typename real>
-static int fill_axes(kdefft_ctx c, int d, const int* P, Item<real>& it) {
+static int fill_axes(kdefft_ctx c, int d, const int* P, Item<real>& it, int maxr = 0) {
+    if (maxr <= 0) maxr = sizeof(real) == 8 ? 16 : 32;
     for (int k = 0; k < d; ++k) {
-        if (!radix_plan(P[k], it.ax[k], sizeof(real) == 8 ? 16 : 32))
+        if (!radix_plan(P[k], it.ax[k], maxr))
             return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
         it.ax[k].tw_off = twiddle_offset(c, P[k]);
     }
@@ -943,7 +1008,6 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
     size_t offM[MAXD];
     for (int k = 0; k < MAXD; ++k) offM[k] = put(pl.mid[k]);
     const size_t offF = put(pl.F);
-    KCU(cudaMemcpyAsync(c->items.p, h, bytes, cudaMemcpyHostToDevice, c->stream));
     const Item<real>* dItems = (const Item<real>*)c->items.p;
     const Tile* dTiles = (const Tile*)((unsigned char*)c->items.p + bItems);
     KCHK(c->scratch.ensure(sizeof(C) * (size_t)std::max<long long>(pl.scratch, 1)));
@@ -977,33 +1041,68 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
         fF += t.n * (fft_flops(P) + 4.0 * P);
         bF += t.n * (it.S[0] * cs + P * rsz);
     }
-    cudaEvent_t ev;
-    if (!pl.A.empty()) {
-        ev = prof_start(c);
-        KCU(launch_stage_a<real>(dItems, dTiles + offA, (int)pl.A.size(), pl.pA, pl.capA, scr, tw, part,
-                                 grid_of(pl.A.size()), c->stream));
-        prof_stop(c, ev, sizeof(real) == 4 ? "stage_a_f32" : "stage_a_f64", bA, fA);
+    std::vector<long long> sig = {1,
+                                  (long long)sizeof(real),
+                                  d,
+                                  nitems,
+                                  out_host ? 1 : 0,
+                                  (long long)(uintptr_t)c->items.p,
+                                  (long long)(uintptr_t)h,
+                                  (long long)bytes,
+                                  (long long)(uintptr_t)scr,
+                                  (long long)(uintptr_t)tw,
+                                  (long long)(uintptr_t)part,
+                                  (long long)(uintptr_t)c->out.p,
+                                  (long long)(uintptr_t)c->h_out.p,
+                                  (long long)pl.A.size(),
+                                  pl.pA,
+                                  pl.capA,
+                                  (long long)offA,
+                                  (long long)pl.F.size(),
+                                  pl.pF,
+                                  pl.capF,
+                                  (long long)offF};
+    for (int k = 0; k < MAXD; ++k) {
+        sig.push_back((long long)pl.mid[k].size());
+        sig.push_back(pl.pM[k]);
+        sig.push_back(pl.capM[k]);
+        sig.push_back((long long)offM[k]);
     }
-    for (int k = d - 2; k >= 1; --k)
-        if (!pl.mid[k].empty()) {
+    if (out_host) KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
+    sig[12] = (long long)(uintptr_t)c->h_out.p;
+    auto issue = [&]() -> int {
+        KCU(cudaMemcpyAsync(c->items.p, h, bytes, cudaMemcpyHostToDevice, c->stream));
+        cudaEvent_t ev;
+        if (!pl.A.empty()) {
             ev = prof_start(c);
-            KCU(launch_mid<real>(dItems, dTiles + offM[k], (int)pl.mid[k].size(), k, pl.pM[k], pl.capM[k], scr,
-                                 tw, grid_of(pl.mid[k].size()), c->stream));
-            prof_stop(c, ev, sizeof(real) == 4 ? "mid_f32" : "mid_f64", bM[k], fM[k]);
+            KCU(launch_stage_a<real>(dItems, dTiles + offA, (int)pl.A.size(), pl.pA, pl.capA, scr, tw, part,
+                                     grid_of(pl.A.size()), c->stream));
+            prof_stop(c, ev, sizeof(real) == 4 ? "stage_a_f32" : "stage_a_f64", bA, fA);
         }
-    if (d >= 2 && !pl.F.empty()) {
-        ev = prof_start(c);
-        KCU(launch_final<real>(dItems, dTiles + offF, (int)pl.F.size(), pl.pF, pl.capF, scr, tw, part,
-                               grid_of(pl.F.size()), c->stream));
-        prof_stop(c, ev, sizeof(real) == 4 ? "final_f32" : "final_f64", bF, fF);
-    }
+        for (int k = d - 2; k >= 1; --k)
+            if (!pl.mid[k].empty()) {
+                ev = prof_start(c);
+                KCU(launch_mid<real>(dItems, dTiles + offM[k], (int)pl.mid[k].size(), k, pl.pM[k], pl.capM[k], scr,
+                                     tw, grid_of(pl.mid[k].size()), c->stream));
+                prof_stop(c, ev, sizeof(real) == 4 ? "mid_f32" : "mid_f64", bM[k], fM[k]);
+            }
+        if (d >= 2 && !pl.F.empty()) {
+            ev = prof_start(c);
+            KCU(launch_final<real>(dItems, dTiles + offF, (int)pl.F.size(), pl.pF, pl.capF, scr, tw, part,
+                                   grid_of(pl.F.size()), c->stream));
+            prof_stop(c, ev, sizeof(real) == 4 ? "final_f32" : "final_f64", bF, fF);
+        }
+        if (out_host) {
+            ev = prof_start(c);
+            KCU(launch_reduce<real>(dItems, nitems, part, (double*)c->out.p, c->stream));
+            prof_stop(c, ev, "reduce", 16.0 * nF, 2.0 * nF);
+            KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+        }
+        return KDEFFT_OK;
+    };
+    KCHK(run_graph(c, sig, issue));
     c->h2d += (int64_t)bytes;
     if (out_host) {
-        ev = prof_start(c);
-        KCU(launch_reduce<real>(dItems, nitems, part, (double*)c->out.p, c->stream));
-        prof_stop(c, ev, "reduce", 16.0 * nF, 2.0 * nF);
-        KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
-        KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
         {
             HostTimer w(c, "host:wait");
             KCU(cudaStreamSynchronize(c->stream));
@@ -1100,8 +1199,6 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
         }
     }
     c->staging_free = false;
-    KCU(cudaMemcpyAsync(c->items.p, c->h_items.p, bItems, cudaMemcpyHostToDevice, c->stream));
-    c->h2d += (int64_t)bItems;
     double fl = 0.0, by = 0.0;
     for (const Item<real>& it : items) {
         const double P1 = it.ax[1].P, P0 = it.ax[0].P, Q1 = std::floor(P1 / 2) + 1;
@@ -1109,17 +1206,45 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
         by += Q1 * P0 * sizeof(real);
     }
     const C* tw = (const C*)(sizeof(real) == 4 ? c->tw32.p : c->tw64.p);
-    cudaEvent_t ev = prof_start(c);
-    cudaError_t le = launch_fused2d<real>((const FusedItem<real>*)c->items.p, nitems, rmax, cs, gat, spcn, cap, pmax, tw,
-                                          (double*)c->out.p, c->errflag, c->stream);
-    if (le == cudaErrorNotSupported && cs > 8) {
-        // a 16-CTA cluster does not fit this footprint on this device: stay at 8
+    const std::vector<long long> sig = {2,
+                                        (long long)sizeof(real),
+                                        nitems,
+                                        rmax,
+                                        cs,
+                                        gat,
+                                        spcn,
+                                        cap,
+                                        pmax,
+                                        (long long)(uintptr_t)c->items.p,
+                                        (long long)(uintptr_t)c->h_items.p,
+                                        (long long)(uintptr_t)tw,
+                                        (long long)(uintptr_t)c->out.p,
+                                        (long long)(uintptr_t)c->h_out.p};
+    bool too_big = false;   // a 16-CTA cluster of this footprint does not fit the device
+    auto issue = [&]() -> int {
+        KCU(cudaMemcpyAsync(c->items.p, c->h_items.p, bItems, cudaMemcpyHostToDevice, c->stream));
+        cudaEvent_t ev = prof_start(c);
+        cudaError_t le = launch_fused2d<real>((const FusedItem<real>*)c->items.p, nitems, rmax, cs, gat, spcn, cap,
+                                              pmax, tw, (double*)c->out.p, c->errflag, c->stream);
+        if (le == cudaErrorNotSupported && cs > 8) {
+            too_big = true;
+            return KDEFFT_ERR_UNSUPPORTED;
+        }
+        KCU(le);
+        prof_stop(c, ev, sizeof(real) == 4 ? "fused2d_f32" : "fused2d_f64", by, fl);
+        KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+        return KDEFFT_OK;
+    };
+    const int ir = run_graph(c, sig, issue);
+    if (too_big) {
+        // stay at 8-CTA clusters from now on
+        KCU(cudaStreamSynchronize(c->stream));
+        c->staging_free = true;
         c->max_cluster = 8;
         return launch_fused<real>(c, items, out_host);
     }
-    KCU(le);
-    prof_stop(c, ev, sizeof(real) == 4 ? "fused2d_f32" : "fused2d_f64", by, fl);
-    KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+    KCHK(ir);
+    c->h2d += (int64_t)bItems;
     {
         HostTimer w(c, "host:wait");
         KCU(cudaStreamSynchronize(c->stream));
@@ -1201,6 +1326,94 @@ static int ensure_spectra(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, s
 }
 
 // Evaluate every grid of rs (value = Eq. 25 for that lag kernel).
+// One batch of work items through the chosen engine: the fused cluster
+// kernel (d = 2) when allowed and the work fits, else the multi-pass path
+// with tile capacity kb.cap; radix plans capped at kb.maxr.
+template <typename real>
+static int run_knobs(kdefft_ctx c, std::vector<Item<real>>& items, int d, const kdefft_ctx_s::Knobs& kb,
+                     std::vector<double>& out) {
+    for (Item<real>& it : items) {
+        int P[MAXD] = {0};
+        for (int k = 0; k < d; ++k) P[k] = it.ax[k].P;
+        KCHK(fill_axes(c, d, P, it, kb.maxr));
+    }
+    int fr = KDEFFT_ERR_UNSUPPORTED;
+    if (d == 2 && kb.fused) fr = launch_fused<real>(c, items, out.data());
+    if (fr == KDEFFT_ERR_UNSUPPORTED) {
+        PassLists pl;
+        for (size_t i = 0; i < items.size(); ++i) tile_item(items[i], (int)i, kb.cap, pl);
+        KCHK(launch_items<real>(c, items, pl, d, out.data()));
+    } else if (fr != KDEFFT_OK) {
+        return fr;
+    }
+    return KDEFFT_OK;
+}
+
+// Autotuner: the first batch of a shape (dimension, precision, number of
+// items, largest padded size, largest support; the last three rounded up to
+// powers of two) runs once per candidate -- engine (fused / multi-pass),
+// multi-pass tile capacity (1/2, 1, 3/2 of the default), radix cap (32 / 16
+// in FP32, 16 / 8 in FP64) -- timed on the host clock around the whole batch
+// (staging, launches, copies, wait); the fastest is cached for the shape and
+// its results are the batch's.  Off: the default knobs.
+template <typename real>
+static int dispatch_batch(kdefft_ctx c, std::vector<Item<real>>& items, int d, int cap, std::vector<double>& out) {
+    const bool dbl = sizeof(real) == 8;
+    kdefft_ctx_s::Knobs def{(d == 2 && c->fused) ? 1 : 0, cap, dbl ? 16 : 32};
+    if (!c->autotune) return run_knobs<real>(c, items, d, def, out);
+    auto pow2 = [](long long v) {
+        long long p = 1;
+        while (p < v) p *= 2;
+        return p;
+    };
+    long long pmax = 0, smax = 0;
+    for (const Item<real>& it : items) {
+        long long sp = 1;
+        for (int k = 0; k < d; ++k) {
+            pmax = std::max<long long>(pmax, it.ax[k].P);
+            sp *= it.S[k];
+        }
+        smax = std::max(smax, sp);
+    }
+    const std::array<long long, 5> key{d, dbl ? 1 : 0, pow2((long long)items.size()), pow2(pmax), pow2(smax)};
+    auto hit = c->tuned.find(key);
+    if (hit != c->tuned.end()) return run_knobs<real>(c, items, d, hit->second, out);
+    std::vector<kdefft_ctx_s::Knobs> cand;
+    const int radix[2] = {dbl ? 16 : 32, dbl ? 8 : 16};
+    if (d == 2 && c->fused)
+        for (int r : radix) cand.push_back({1, cap, r});
+    for (int cm : {2, 4, 6})   // tile capacity cap / 2, cap, 3 cap / 2
+        for (int r : radix) {
+            const int cc = cap * cm / 4;
+            // every line fits a batch, and the largest pass's shared memory
+            // (two padded ping-pong buffers, twiddles, staged spectrum) fits a CTA
+            const size_t sm = (2 * sizeof(real)) * (size_t)(2 * (cc + cc / 16 + 1) + pmax) + sizeof(real) * cc;
+            if (cc < pmax || sm > 220 * 1024) continue;
+            cand.push_back({0, cc, r});
+        }
+    double best_t = INFINITY;
+    kdefft_ctx_s::Knobs best = def;
+    std::vector<double> o(out.size());
+    for (const auto& kb : cand) {
+        // one untimed run (first-use set-up), one timed
+        const int r0 = run_knobs<real>(c, items, d, kb, o);
+        if (r0 == KDEFFT_ERR_UNSUPPORTED) continue;
+        KCHK(r0);
+        const auto t0 = std::chrono::steady_clock::now();
+        KCHK(run_knobs<real>(c, items, d, kb, o));
+        const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (t < best_t) {
+            best_t = t;
+            best = kb;
+            out = o;
+        }
+    }
+    if (!std::isfinite(best_t)) return run_knobs<real>(c, items, d, def, out);
+    c->tuned[key] = best;
+    c->keys_tuned++;
+    return KDEFFT_OK;
+}
+
 template <typename real>
 static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
     if (sel.empty()) return KDEFFT_OK;
@@ -1307,15 +1520,7 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
             }
         }
         std::vector<double> out(2 * items.size());
-        int fr = KDEFFT_ERR_UNSUPPORTED;
-        if (d == 2 && c->fused) fr = launch_fused<real>(c, items, out.data());
-        if (fr == KDEFFT_ERR_UNSUPPORTED) {
-            PassLists pl;
-            for (size_t i = 0; i < items.size(); ++i) tile_item(items[i], (int)i, cap, pl);
-            KCHK(launch_items<real>(c, items, pl, d, out.data()));
-        } else if (fr != KDEFFT_OK) {
-            return fr;
-        }
+        KCHK(dispatch_batch<real>(c, items, d, cap, out));
         for (size_t i = 0; i < batch.size(); ++i) {
             rs.grids[batch[i].first].value = out[2 * i];
             if (batch[i].second >= 0) rs.grids[batch[i].second].value = out[2 * i + 1];
@@ -1523,6 +1728,26 @@ int kdefft_set_engine(kdefft_ctx c, int engine) {
     return KDEFFT_OK;
 }
 
+int kdefft_set_autotune(kdefft_ctx c, int on) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    c->autotune = (on != 0);
+    return KDEFFT_OK;
+}
+
+int kdefft_set_graphs(kdefft_ctx c, int on) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    c->graphs = (on != 0);
+    return KDEFFT_OK;
+}
+
+int kdefft_runtime_stats(kdefft_ctx c, int64_t* shapes_tuned, int64_t* graphs_captured, int64_t* graph_replays) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    if (shapes_tuned) *shapes_tuned = c->keys_tuned;
+    if (graphs_captured) *graphs_captured = c->graphs_captured;
+    if (graph_replays) *graph_replays = c->graph_replays;
+    return KDEFFT_OK;
+}
+
 int kdefft_profile(kdefft_ctx c, int mode) {
     if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
     if (mode == 1 || mode == 0) {
@@ -1569,6 +1794,7 @@ int kdefft_destroy(kdefft_ctx c) {
     c->tiles.release();
     c->out.release();
     c->sel_buf.release();
+    c->binfix.release();
     c->h_items.release();
     c->h_out.release();
     for (auto& p : c->pending) {
@@ -1576,6 +1802,9 @@ int kdefft_destroy(kdefft_ctx c) {
         c->evpool.push_back(p.b);
     }
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
+    c->gcache.clear();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->errflag) cudaFree(c->errflag);
     delete c;
     return KDEFFT_OK;
@@ -1655,14 +1884,13 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
         int K = 32;
         while (K > 8 && (double)n * std::ldexp(1.0, K) >= std::ldexp(1.0, 63)) --K;
         c->launches++;   // the fixed-point-to-FP32 conversion
-        DevBuf fix;
+        DevBuf& fix = c->binfix;
         KCHK(fix.ensure(8 * (size_t)ds->ncells));
         KCU(cudaMemsetAsync(fix.p, 0, 8 * (size_t)ds->ncells, c->stream));
         KCU(launch_bin_linear<unsigned long long>(dX, n, g, (unsigned long long*)fix.p, ds->ncells, dOut,
                                                   std::ldexp(1.0, K), c->nsm, c->stream));
         KCU(launch_fix_to_f32((const unsigned long long*)fix.p, (float*)ds->counts.p, ds->ncells, std::ldexp(1.0, -K),
                               c->stream));
-        KCU(cudaStreamSynchronize(c->stream));   // before the temporary is freed
     }
     prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
     // moments for the normal-scale start point
