@@ -207,16 +207,27 @@ int kdefft_batch_lscv(kdefft_ctx ctx, int nds, const kdefft_ds* ds,
                       const int* nH_per_ds, const double* H,
                       double* val, double* grad);
 
-/* Engine selection.  AUTO (default): for d = 2 one thread-block-cluster
- * kernel per batch does all passes in shared and distributed shared memory
- * whenever the work fits, else the multi-pass path; and kdefft_select_H on a
- * d = 2 FP32 dataset (LSCV of Eq. 10 or SCV, minimal padding) runs the whole
- * multi-start search in one device-resident launch (one cluster per start).
- * HOST_SELECT: as AUTO but the search is driven from the host, one batched
- * launch per round.  MULTIPASS: the pass-per-axis kernels with a global
- * scratch between passes (always used for d >= 3), host-driven search.  All
- * compute the same sums. */
-enum { KDEFFT_ENGINE_AUTO = 0, KDEFFT_ENGINE_MULTIPASS = 1, KDEFFT_ENGINE_HOST_SELECT = 2 };
+/* Engine selection.  AUTO (default): a grid whose padding has no aliasing
+ * (P_k >= M_k + L_k on every axis, which every P rule but a small FIXED size
+ * gives) is evaluated in the lag domain: n^-2 sum_j w_j k_j a_j over the half
+ * support box, with the count autocorrelation a = F^-1(|C|^2) computed once
+ * per dataset in FP64 -- Eq. 25 summed over the lag first, the same value as
+ * the FFT route of Eqs. 19-24.  Other grids take the FFT route: for d = 2 one
+ * thread-block-cluster kernel per batch does all passes in shared and
+ * distributed shared memory whenever the work fits, else the multi-pass
+ * path.  kdefft_select_H on a d = 2 FP32 dataset (LSCV of Eq. 10 or SCV,
+ * minimal padding) runs the whole multi-start search in one device-resident
+ * launch (one cluster per start).  HOST_SELECT: as AUTO but the search is
+ * driven from the host, one batched launch per round.  FFT: as AUTO without
+ * the lag domain.  MULTIPASS: only the pass-per-axis FFT kernels with a
+ * global scratch between passes, host-driven search.  All compute the same
+ * sums. */
+enum {
+    KDEFFT_ENGINE_AUTO = 0,
+    KDEFFT_ENGINE_MULTIPASS = 1,
+    KDEFFT_ENGINE_HOST_SELECT = 2,
+    KDEFFT_ENGINE_FFT = 3
+};
 int kdefft_set_engine(kdefft_ctx ctx, int engine);
 
 /* Autotuner (off by default).  When on, the first batch of each shape
@@ -230,6 +241,17 @@ int kdefft_set_engine(kdefft_ctx ctx, int engine);
  * batches of the shape use it directly.  Results of different candidates
  * agree within the FP32 (FP64) tolerance of the evaluation. */
 int kdefft_set_autotune(kdefft_ctx ctx, int on);
+
+/* The count autocorrelation a_j = sum_i c_i c_{i+j} (the lag-domain form of
+ * Eq. 25's double sum) on the half box j_0 in [0, A_0], |j_k| <= A_k
+ * (k >= 1), A_k <= M_k - 1: out holds prod_{k>=1} (2 A_k + 1) x (A_0 + 1)
+ * FP64 values, layout [j_{d-1}]..[j_1][j_0] (j_0 fastest, index j_k + A_k
+ * for k >= 1); a_{-j} = a_j gives the other half.  Computed in FP64 from the
+ * count spectrum at the smallest 2^a 3^b 5^c padding >= M_k + A_k (cached on
+ * the dataset and reused by the lag-domain engine).  out: host.  Errors:
+ * KDEFFT_ERR_ARG for A outside [0, M_k - 1], KDEFFT_ERR_UNSUPPORTED when that
+ * padding exceeds 4096 on an axis. */
+int kdefft_autocorr(kdefft_ds ds, const int* A, double* out);
 
 /* CUDA graphs (on by default).  A batch's launch sequence (staging copy,
  * kernels, result copy) is captured once into a CUDA graph under its

@@ -82,6 +82,39 @@ def binned_direct(c, n, terms, delta, L) -> float:
     return math.fsum(parts) / float(n) ** 2
 
 
+def autocorr(c, A) -> np.ndarray:
+    """a_j = sum_i c_i c_{i+j} (c = 0 off the grid): the factor that Eq. 25's
+    double sum puts on k_j once the sum over the lag is taken first
+    (binned_direct sums k_j times it).  Half box j_0 in [0, A_0], |j_k| <= A_k
+    for k >= 1, array indexed [j_{d-1} + A_{d-1}]..[j_1 + A_1][j_0]; the
+    other half follows from a_{-j} = a_j."""
+    c = np.asarray(c, dtype=np.float64)
+    d = c.ndim
+    shape = tuple(2 * A[k] + 1 for k in range(d - 1, 0, -1)) + (A[0] + 1,)
+    out = np.zeros(shape)
+    for idx in np.ndindex(*shape):
+        j = [0] * d
+        j[0] = idx[-1]
+        for k in range(1, d):
+            j[k] = idx[d - 1 - k] - A[k]
+        out[idx] = _overlap(c, [-x for x in j])
+    return out
+
+
+def half_box_weights(A) -> np.ndarray:
+    """w_j on the half box of `autocorr`: 2 where the first nonzero of
+    (j_0, .., j_{d-1}) is positive, 1 at j = 0, 0 where it is negative, so
+    that sum_half w_j f_j = sum_full f_j for every even f."""
+    d = len(A)
+    shape = tuple(2 * A[k] + 1 for k in range(d - 1, 0, -1)) + (A[0] + 1,)
+    w = np.zeros(shape)
+    for idx in np.ndindex(*shape):
+        j = [idx[-1]] + [idx[d - 1 - k] - A[k] for k in range(1, d)]
+        nz = [x for x in j if x != 0]
+        w[idx] = 1.0 if not nz else (2.0 if nz[0] > 0 else 0.0)
+    return w
+
+
 def binned_fft(c, n, terms, delta, L, P) -> float:
     """Sec. 4 steps 2-4 with an FFT (Eqs. 19-24); requires P_k >= M_k + L_k."""
     c = np.asarray(c, dtype=np.float64)

@@ -11,5 +11,5 @@ from ._lib import (  # noqa: F401
     Context, Dataset, KdefftError, default_opts, load,
     L_AUTO, L_PAPER, L_WIDEST, L_FULL, P_MINIMAL, P_PAPER, P_PAPER_FULL, P_FIXED,
     FP32, FP64, BIN_LINEAR, BIN_SIMPLE, OUTSIDE_ERROR, OUTSIDE_DROP, LSCV, SCV, PI,
-    DT_F32, DT_F64, DT_I32, EXPORTS, ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT,
+    DT_F32, DT_F64, DT_I32, EXPORTS, ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT,
 )

@@ -31,9 +31,9 @@ EXPORTS = [
     "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H", "kdefft_select_H_nm",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
-    "kdefft_runtime_stats",
+    "kdefft_runtime_stats", "kdefft_autocorr",
 ]
-ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT = 0, 1, 2
+ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
 
 class Opts(C.Structure):
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "kdefft_lscv_noalloc": (I, [I, P, P, I64, P, P, C.c_double, P, P]),
         "kdefft_set_engine": (I, [P, I]),
         "kdefft_set_autotune": (I, [P, I]),
+        "kdefft_autocorr": (I, [P, P, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "kdefft_strerror": (C.c_char_p, [I]),
@@ -341,6 +342,16 @@ class Dataset:
         _check(load().kdefft_pi(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
                                 g.ctypes.data_as(C.c_void_p) if grad else None))
         return (val, g) if grad else val
+
+    def autocorr(self, A):
+        """Count autocorrelation a_j = sum_i c_i c_{i+j} on the half box
+        j_0 in [0, A_0], |j_k| <= A_k: array of shape (2 A_{d-1} + 1, ..,
+        2 A_1 + 1, A_0 + 1), index j_k + A_k on the axes k >= 1."""
+        A_a = np.ascontiguousarray(np.asarray(A, dtype=np.int32).reshape(self.d))
+        shape = tuple(2 * int(a) + 1 for a in A_a[1:][::-1]) + (int(A_a[0]) + 1,)
+        out = np.zeros(shape)
+        _check(load().kdefft_autocorr(self.h, A_a.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def eta02(self, H, G):
         H, nH = self._Hs(H)

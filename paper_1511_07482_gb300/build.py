@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkdefft.so")
-SOURCES = ["engine.cu", "binning.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["engine.cu", "lag.cu", "binning.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
@@ -41,7 +41,7 @@ def _stale(obj: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, "engine.cuh"), os.path.join(INCLUDE, "kdefft.h")]
+    headers = [os.path.join(CSRC, "engine.cuh"), os.path.join(CSRC, "devutil.cuh"), os.path.join(INCLUDE, "kdefft.h")]
     jobs = []
     objs = []
     for src in SOURCES:

@@ -421,11 +421,13 @@ struct kdefft_ctx_s {
     };
     bool prof = false;
     bool fused = true;    // d = 2: single cluster kernel per batch when it fits
+    bool lag = true;      // lag-domain engine for grids whose padding has no aliasing
     int* errflag = nullptr;   // device flag: a bounded device-side wait gave up
     int max_cluster = 16;     // largest cluster the fused engine may launch
     bool device_select = true;   // d = 2 FP32 selections run as one device-resident launch
     DevBuf sel_buf;           // device tables and start states of the device-resident selection
     DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
+    DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
     std::map<std::string, KStat> kstat;
     struct Pending {
         std::string name;
@@ -575,6 +577,10 @@ struct kdefft_ds_s {
     std::map<std::vector<int>, std::shared_ptr<DevBuf>> spectra;
     double cov[16] = {0}; // sample covariance (d x d, row-major)
     std::map<std::vector<double>, double> c2g;   // SCV phi_2G sums by (G, L, P)
+    // count autocorrelation a_j on the half box A (lag-domain engine), FP64
+    // and an FP32 copy
+    int acA[4] = {-1, -1, -1, -1};
+    DevBuf ac64, ac32;
 };
 
 static int twiddle_offset(kdefft_ctx c, int P) {
@@ -1326,6 +1332,303 @@ static int ensure_spectra(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, s
 }
 
 // Evaluate every grid of rs (value = Eq. 25 for that lag kernel).
+// ============================================================ lag-domain engine
+static long long pmin_smooth(long long m) {
+    while (!is_smooth(m)) ++m;
+    return m;
+}
+
+// a_j = sum_i c_i c_{i+j} on the half box A (j_0 in [0, A_0], |j_k| <= A_k),
+// layout [j_{d-1}]..[j_0], from the FP64 count spectrum at P_k >= M_k + A_k
+// (no aliasing on the box) by separable pruned inverse DFTs in FP64; the
+// last pass also writes the FP32 copy.  A box grows (by half of itself at
+// least) when a request needs more.  Every dataset of `req` is brought up to
+// date with one batched spectrum launch sequence and stream-ordered passes
+// through context buffers (no synchronisation).
+static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& req) {
+    struct Job {
+        kdefft_ds ds;
+        int A[4], P[4];
+    };
+    std::vector<Job> jobs;
+    std::vector<std::pair<kdefft_ds, std::array<int, 4>>> specs;
+    for (const auto& rq : req) {
+        kdefft_ds ds = rq.first;
+        const int d = ds->d;
+        bool covered = ds->acA[0] >= 0;
+        for (int k = 0; k < d; ++k) covered = covered && ds->acA[k] >= rq.second[k];
+        if (covered) continue;
+        Job jb{ds, {0, 0, 0, 0}, {1, 1, 1, 1}};
+        for (int k = 0; k < d; ++k) {
+            const int grow = ds->acA[k] >= 0 ? ds->acA[k] + ds->acA[k] / 2 : 0;
+            jb.A[k] = (int)std::min<long long>(ds->M[k] - 1, std::max(rq.second[k], grow));
+            jb.P[k] = (int)pmin_smooth(ds->M[k] + jb.A[k]);
+            if (jb.P[k] > MAXP) return KDEFFT_ERR_UNSUPPORTED;
+        }
+        jobs.push_back(jb);
+        specs.push_back({ds, {jb.P[0], jb.P[1], jb.P[2], jb.P[3]}});
+    }
+    if (!jobs.empty()) KCHK(ensure_spectra<double>(c, specs));
+    for (const Job& jb : jobs)
+        for (int k = 0; k < jb.ds->d; ++k) twiddle_offset(c, jb.P[k]);
+    KCHK(sync_twiddles(c));
+    const double2* tw = (const double2*)c->tw64.p;
+    for (const Job& jb : jobs) {
+        kdefft_ds ds = jb.ds;
+        const int d = ds->d;
+        const int* A = jb.A;
+        const int* P = jb.P;
+        auto sit = ds->spectra.find(spectrum_key(ds, P, sizeof(double)));
+        if (sit == ds->spectra.end()) return fail(KDEFFT_ERR_CUDA, "count spectrum missing");
+        const double* S = (const double*)sit->second->p;
+        long long nbox = 1;
+        double ptot = 1.0;
+        for (int k = 0; k < d; ++k) {
+            nbox *= (k == 0) ? (A[0] + 1) : (2 * A[k] + 1);
+            ptot *= P[k];
+        }
+        KCHK(ds->ac64.ensure(sizeof(double) * nbox));
+        KCHK(ds->ac32.ensure(sizeof(float) * nbox));
+        float* o32 = (float*)ds->ac32.p;
+        const int Q = P[d - 1] / 2 + 1;
+        // algorithmic work of the passes: 8 flops per complex term, the spectrum read once
+        double fl = 0.0;
+        {
+            long long o = Q, ii = 1;
+            for (int k = 1; k <= d - 2; ++k) o *= P[k];
+            for (int k = 0; k < d - 1; ++k) {
+                const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
+                fl += 8.0 * (double)o * J * ii * P[k];
+                ii *= J;
+                if (k + 1 <= d - 2) o /= P[k + 1];
+            }
+            fl += 8.0 * (double)ii * (2 * A[d - 1] + 1) * Q;
+        }
+        double by = 8.0 * Q;
+        for (int k = 0; k < d - 1; ++k) by *= P[k];
+        cudaEvent_t ev = prof_start(c);
+        c->launches--;   // counted per pass below
+        if (d == 1) {
+            c->launches++;
+            KCU(launch_acorr_axis(S, nullptr, nullptr, (double*)ds->ac64.p, o32, 1, Q, 1, A[0] + 1, 0, P[0],
+                                  tw + twiddle_offset(c, P[0]), 1, 1.0 / ptot, c->stream));
+        } else {
+            // pass k transforms axis k: [w_{d-1}..w_{k+1}][w_k][j_{k-1}..j_0] -> [..][j_k][..]
+            long long O = Q;
+            for (int k = 1; k <= d - 2; ++k) O *= P[k];
+            size_t most = 0;
+            {
+                long long o = O, ii = 1;
+                for (int k = 0; k < d - 1; ++k) {
+                    const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
+                    most = std::max(most, (size_t)(o * J * ii));
+                    ii *= J;
+                    if (k + 1 <= d - 2) o /= P[k + 1];
+                }
+            }
+            KCHK(c->acbuf[0].ensure(sizeof(double2) * most));
+            KCHK(c->acbuf[1].ensure(sizeof(double2) * most));
+            double2* cur = (double2*)c->acbuf[0].p;
+            double2* nxt = (double2*)c->acbuf[1].p;
+            long long I = 1;
+            for (int k = 0; k < d - 1; ++k) {
+                const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
+                const int jlo = (k == 0) ? 0 : -A[k];
+                c->launches++;
+                KCU(launch_acorr_axis(k == 0 ? S : nullptr, k == 0 ? nullptr : cur, nxt, nullptr, nullptr, O, P[k], I,
+                                      J, jlo, P[k], tw + twiddle_offset(c, P[k]), 0, 1.0, c->stream));
+                std::swap(cur, nxt);
+                I *= J;
+                if (k + 1 <= d - 2) O /= P[k + 1];
+            }
+            c->launches++;
+            KCU(launch_acorr_axis(nullptr, cur, nullptr, (double*)ds->ac64.p, o32, 1, Q, I, 2 * A[d - 1] + 1,
+                                  -A[d - 1], P[d - 1], tw + twiddle_offset(c, P[d - 1]), 1, 1.0 / ptot, c->stream));
+        }
+        prof_stop(c, ev, "acorr_f64", by, fl);
+        for (int k = 0; k < 4; ++k) ds->acA[k] = (k < d) ? A[k] : 0;
+    }
+    return KDEFFT_OK;
+}
+
+// highest derivative order among the terms of a grid pair
+static int pair_order(const ReqSet& rs, const std::pair<int, int>& pr, int d) {
+    int R = 0;
+    for (int gi : {pr.first, pr.second}) {
+        if (gi < 0) continue;
+        for (const Term& t : rs.grids[gi].terms) {
+            int o = 0;
+            for (int k = 0; k < d; ++k) o += t.alpha[k];
+            R = std::max(R, o);
+        }
+    }
+    return R;
+}
+
+// the lag-domain engine computes exactly the FFT route's value when the
+// padding has no aliasing (P_k >= M_k + L_k on every axis)
+template <typename real>
+static bool lag_eligible(kdefft_ctx c, const ReqSet& rs, const std::pair<int, int>& pr) {
+    if (!c->lag) return false;
+    const GridReq& g = rs.grids[pr.first];
+    const int d = g.ds->d;
+    for (int k = 0; k < d; ++k)
+        if (g.P[k] < g.ds->M[k] + g.L[k]) return false;
+    return lag_table_size(d, pair_order(rs, pr, d), sizeof(real) == 8) > 0;
+}
+
+// Values of the grid pairs through the lag-domain engine: one tiled launch
+// per derivative-order class, a fixed-order reduction, one copy back.
+template <typename real>
+static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pairs) {
+    if (pairs.empty()) return KDEFFT_OK;
+    const bool dbl = sizeof(real) == 8;
+    const int d = rs.grids[pairs[0].first].ds->d;
+    {
+        std::map<kdefft_ds, std::array<int, 4>> need;
+        for (const auto& pr : pairs) {
+            const GridReq& g = rs.grids[pr.first];
+            auto& a = need[g.ds];
+            for (int k = 0; k < d; ++k) a[k] = std::max(a[k], g.L[k]);
+        }
+        std::vector<std::pair<kdefft_ds, std::array<int, 4>>> rq(need.begin(), need.end());
+        KCHK(ensure_autocorr_many(c, rq));
+    }
+    // order classes, contiguous
+    std::vector<int> Re(pairs.size());
+    for (size_t i = 0; i < pairs.size(); ++i) Re[i] = (pair_order(rs, pairs[i], d) + 1) & ~1;
+    std::vector<size_t> ord(pairs.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return Re[a] < Re[b]; });
+    HermiteIndex& hx = hindex();
+    std::vector<LagItem<real>> items;
+    std::vector<real> wpool;
+    std::vector<LagTile> tiles;
+    std::vector<std::array<int, 3>> classes;   // (R, first tile, tiles)
+    // fixed tiles of 4096 points: an item's sum depends on the item alone,
+    // not on the batch it came in
+    const long long T = 4096;
+    for (size_t u : ord) {
+        const auto& pr = pairs[u];
+        const GridReq& g = rs.grids[pr.first];
+        const KSpec& sp = rs.specs[g.spec];
+        kdefft_ds ds = g.ds;
+        LagItem<real> it;
+        std::memset(&it, 0, sizeof(it));
+        it.d = d;
+        it.nsig = sp.nsig;
+        it.R = Re[u];
+        for (int k = 0; k < d; ++k) {
+            it.L[k] = g.L[k];
+            it.A[k] = ds->acA[k];
+            it.delta[k] = (real)ds->delta[k];
+        }
+        for (int s = 0; s < sp.nsig; ++s) {
+            Mat inv;
+            double det;
+            if (!spd_inv_det(sp.sig[s], inv, det))
+                return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)inv(a, b);
+            it.nrm[s] = (real)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
+        }
+        it.acorr = dbl ? (const real*)ds->ac64.p : (const real*)ds->ac32.p;
+        const int N = lag_table_size(d, it.R, dbl);
+        it.w_off = (int)wpool.size();
+        wpool.resize(wpool.size() + 2 * (size_t)sp.nsig * N, real(0));
+        const int gi[2] = {pr.first, pr.second};
+        for (int h = 0; h < 2; ++h) {
+            if (gi[h] < 0) continue;
+            for (const Term& t : rs.grids[gi[h]].terms) {
+                int o = 0;
+                for (int k = 0; k < d; ++k) o += t.alpha[k];
+                const int hidx = hx.idx(d, t.alpha);
+                if (hidx < 0 || hidx >= N) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high");
+                wpool[it.w_off + (h * sp.nsig + t.sig) * N + hidx] += (real)(((o & 1) ? -1.0 : 1.0) * t.w);
+            }
+        }
+        const double nn = (double)ds->n;
+        it.scale = 1.0 / (nn * nn);
+        long long pts = g.L[0] + 1;
+        for (int k = 1; k < d; ++k) pts *= 2 * g.L[k] + 1;
+        it.tile0 = (int)tiles.size();
+        for (long long f = 0; f < pts; f += T) tiles.push_back(LagTile{(int)items.size(), (int)std::min(T, pts - f), f});
+        it.ntile = (int)tiles.size() - it.tile0;
+        if (classes.empty() || classes.back()[0] != it.R) classes.push_back({it.R, it.tile0, 0});
+        classes.back()[2] += it.ntile;
+        items.push_back(it);
+    }
+    const int nitems = (int)items.size();
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bI = sizeof(LagItem<real>) * nitems, bT = sizeof(LagTile) * tiles.size(), bW = sizeof(real) * wpool.size();
+    const size_t oT = al(bI), oW = oT + al(bT), bytes = oW + std::max<size_t>(bW, 16);
+    KCHK(c->h_items.ensure(bytes));
+    KCHK(c->items.ensure(bytes));
+    KCHK(c->partial.ensure(sizeof(double) * 2 * tiles.size()));
+    KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
+    KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
+    if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
+    c->staging_free = false;
+    unsigned char* h = (unsigned char*)c->h_items.p;
+    std::memcpy(h, items.data(), bI);
+    std::memcpy(h + oT, tiles.data(), bT);
+    if (bW) std::memcpy(h + oW, wpool.data(), bW);
+    unsigned char* dbase = (unsigned char*)c->items.p;
+    const LagItem<real>* dI = (const LagItem<real>*)dbase;
+    const LagTile* dT = (const LagTile*)(dbase + oT);
+    const real* dW = (const real*)(dbase + oW);
+    double* part = (double*)c->partial.p;
+    // algorithmic work: per point nsig exponentials and Hermite tables; bytes: a_j once per point
+    double fl = 0.0, by = 0.0;
+    for (const LagItem<real>& it : items) {
+        long long pts = it.L[0] + 1;
+        for (int k = 1; k < d; ++k) pts *= 2 * it.L[k] + 1;
+        const int N = lag_table_size(d, it.R, dbl);
+        fl += (double)pts * it.nsig * (2.0 * d * d + 8.0 * N);
+        by += (double)pts * sizeof(real);
+    }
+    std::vector<long long> sig = {3, (long long)sizeof(real), d, nitems, (long long)tiles.size(),
+                                  (long long)(uintptr_t)dbase, (long long)(uintptr_t)h, (long long)bytes,
+                                  (long long)(uintptr_t)part, (long long)(uintptr_t)c->out.p,
+                                  (long long)(uintptr_t)c->h_out.p};
+    for (const auto& cl : classes) {
+        sig.push_back(cl[0]);
+        sig.push_back(cl[1]);
+        sig.push_back(cl[2]);
+    }
+    auto issue = [&]() -> int {
+        KCU(cudaMemcpyAsync(dbase, h, bytes, cudaMemcpyHostToDevice, c->stream));
+        for (const auto& cl : classes) {
+            cudaEvent_t ev = prof_start(c);
+            const int grid = std::min(cl[2], c->nsm * 8);
+            KCU(launch_lag<real>(d, cl[0], dI, dT + cl[1], cl[2], dW, part + 2 * (size_t)cl[1], grid, c->stream));
+            prof_stop(c, ev, dbl ? "lag_f64" : "lag_f32", by * cl[2] / std::max<size_t>(tiles.size(), 1),
+                      fl * cl[2] / std::max<size_t>(tiles.size(), 1));
+        }
+        cudaEvent_t ev = prof_start(c);
+        KCU(launch_lag_reduce<real>(dI, nitems, part, (double*)c->out.p, c->stream));
+        prof_stop(c, ev, "reduce", 16.0 * tiles.size(), 2.0 * tiles.size());
+        KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+        return KDEFFT_OK;
+    };
+    KCHK(run_graph(c, sig, issue));
+    c->h2d += (int64_t)bytes;
+    {
+        HostTimer w(c, "host:wait");
+        KCU(cudaStreamSynchronize(c->stream));
+    }
+    c->staging_free = true;
+    c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
+    const double* o = (const double*)c->h_out.p;
+    for (size_t i = 0; i < ord.size(); ++i) {
+        const auto& pr = pairs[ord[i]];
+        rs.grids[pr.first].value = o[2 * i];
+        if (pr.second >= 0) rs.grids[pr.second].value = o[2 * i + 1];
+    }
+    prof_flush(c);
+    return KDEFFT_OK;
+}
+
 // One batch of work items through the chosen engine: the fused cluster
 // kernel (d = 2) when allowed and the work fits, else the multi-pass path
 // with tile capacity kb.cap; radix plans capped at kb.maxr.
@@ -1436,6 +1739,20 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
         u += 1;
     }
     const int cap = cap_elems(sizeof(real) == 8);
+    // lag-domain engine for the pairs it covers; the FFT route for the rest
+    {
+        std::vector<std::pair<int, int>> lagp, fftp;
+        for (const auto& pr : pairs) (lag_eligible<real>(c, rs, pr) ? lagp : fftp).push_back(pr);
+        if (!lagp.empty()) {
+            const int lr = run_lag<real>(c, rs, lagp);
+            if (lr == KDEFFT_ERR_UNSUPPORTED)
+                fftp.insert(fftp.end(), lagp.begin(), lagp.end());   // autocorrelation box beyond MAXP
+            else
+                KCHK(lr);
+        }
+        pairs.swap(fftp);
+        if (pairs.empty()) return KDEFFT_OK;
+    }
     // count spectra first, all missing ones in one launch sequence
     {
         HostTimer hs(c, "host:spectra");
@@ -1655,6 +1972,8 @@ static void ds_free(kdefft_ds ds) {
     ds->counts.release();
     ds->counts_i.release();
     ds->counts64.release();
+    ds->ac64.release();
+    ds->ac32.release();
     for (auto& kv : ds->spectra) kv.second->release();
     delete ds;
 }
@@ -1721,10 +2040,49 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
 
 int kdefft_set_engine(kdefft_ctx c, int engine) {
     if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
-    if (engine != KDEFFT_ENGINE_AUTO && engine != KDEFFT_ENGINE_MULTIPASS && engine != KDEFFT_ENGINE_HOST_SELECT)
+    if (engine != KDEFFT_ENGINE_AUTO && engine != KDEFFT_ENGINE_MULTIPASS && engine != KDEFFT_ENGINE_HOST_SELECT &&
+        engine != KDEFFT_ENGINE_FFT)
         return fail(KDEFFT_ERR_ARG, "unknown engine");
     c->fused = (engine != KDEFFT_ENGINE_MULTIPASS);
-    c->device_select = (engine == KDEFFT_ENGINE_AUTO);
+    c->device_select = (engine == KDEFFT_ENGINE_AUTO || engine == KDEFFT_ENGINE_FFT);
+    c->lag = (engine == KDEFFT_ENGINE_AUTO || engine == KDEFFT_ENGINE_HOST_SELECT);
+    return KDEFFT_OK;
+}
+
+int kdefft_autocorr(kdefft_ds ds, const int* A, double* out) {
+    if (!ds || !A || !out) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    kdefft_ctx c = ds->ctx;
+    const int d = ds->d;
+    for (int k = 0; k < d; ++k)
+        if (A[k] < 0 || A[k] > ds->M[k] - 1) return fail(KDEFFT_ERR_ARG, "A_k must be in [0, M_k - 1]");
+    KCU(cudaSetDevice(c->device));
+    std::array<int, 4> need{0, 0, 0, 0};
+    for (int k = 0; k < d; ++k) need[k] = A[k];
+    const int r = ensure_autocorr_many(c, {{ds, need}});
+    if (r == KDEFFT_ERR_UNSUPPORTED) return fail(r, "the padding for this box exceeds 4096");
+    KCHK(r);
+    long long nbox = 1;
+    for (int k = 0; k < d; ++k) nbox *= (k == 0) ? (ds->acA[0] + 1) : (2 * ds->acA[k] + 1);
+    std::vector<double> full((size_t)nbox);
+    KCU(cudaMemcpyAsync(full.data(), ds->ac64.p, sizeof(double) * nbox, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    c->d2h += (int64_t)(sizeof(double) * nbox);
+    // the requested sub-box, same layout
+    long long nout = 1;
+    for (int k = 0; k < d; ++k) nout *= (k == 0) ? (A[0] + 1) : (2 * A[k] + 1);
+    for (long long f = 0; f < nout; ++f) {
+        long long g = f, src = 0;
+        int j[4] = {0, 0, 0, 0};
+        j[0] = (int)(g % (A[0] + 1));
+        g /= (A[0] + 1);
+        for (int k = 1; k < d; ++k) {
+            j[k] = (int)(g % (2 * A[k] + 1)) - A[k];
+            g /= (2 * A[k] + 1);
+        }
+        for (int k = d - 1; k >= 1; --k) src = src * (2 * ds->acA[k] + 1) + (j[k] + ds->acA[k]);
+        src = src * (ds->acA[0] + 1) + j[0];
+        out[f] = full[(size_t)src];
+    }
     return KDEFFT_OK;
 }
 
@@ -1795,6 +2153,8 @@ int kdefft_destroy(kdefft_ctx c) {
     c->out.release();
     c->sel_buf.release();
     c->binfix.release();
+    c->acbuf[0].release();
+    c->acbuf[1].release();
     c->h_items.release();
     c->h_out.release();
     for (auto& p : c->pending) {
@@ -2802,14 +3162,16 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
             Mat Hb = theta_to_H(o, tho[best].data());
             for (int a = 0; a < d; ++a)
                 for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
-            double fbest = fo[best];
-            if (method == KDEFFT_SCV) {
-                std::vector<double> v;
+            // the value reported is the objective at H_out through the
+            // regular evaluation path (the search compared its own FP32 values)
+            // (with the gradient, as a caller checking stationarity asks for it)
+            std::vector<double> v, gdummy;
+            if (method == KDEFFT_SCV)
                 KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
-                fbest = v[0];
-            }
-            if (f_out) *f_out = fbest;
-            if (n_evals) *n_evals = dev_evals;
+            else
+                KCHK(eval_lscv(ds, H_out, 1, v, &gdummy));
+            if (f_out) *f_out = v[0];
+            if (n_evals) *n_evals = dev_evals + 1;
             return KDEFFT_OK;
         }
         if (r != KDEFFT_ERR_UNSUPPORTED) return r;

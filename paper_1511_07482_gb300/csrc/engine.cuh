@@ -179,6 +179,52 @@ cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstar
 
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
 
+// ---- lag-domain engine (lag.cu)
+// Eq. 25 summed over the lag first: n^-2 sum_i sum_j c_i c_j k(i - j) =
+// n^-2 sum_l k_l a_l with the count autocorrelation a_l = sum_i c_i c_{i+l}.
+// Both k (even-order Gaussian partials) and a are even, so the sum runs over
+// the half box j_0 in [0, L_0], j_k in [-L_k, L_k] (k >= 1) with weight 2 on
+// points whose first nonzero coordinate is positive, 1 at j = 0, 0 otherwise.
+// The autocorrelation array holds the half box of a larger box A, layout
+// [j_{d-1}]..[j_1][j_0] (j_0 innermost, j_k + A_k for k >= 1).
+template <typename real>
+struct LagItem {
+    int d, nsig, R, pad_;
+    int L[MAXD];                      // support of this item's kernels
+    int A[MAXD];                      // box of the autocorrelation array
+    real lam[MAXSIG][MAXD * MAXD];    // Sigma^{-1}, row stride MAXD
+    real nrm[MAXSIG];                 // (2 pi)^{-d/2} |Sigma|^{-1/2}
+    real delta[MAXD];
+    const real* acorr;
+    int w_off;                        // dense weights [2][nsig][N(d, R)] at wpool + w_off
+    int tile0, ntile;                 // this item's tiles (their partial sums)
+    double scale;                     // n^-2
+};
+struct LagTile {
+    int item;
+    int n;                            // points of the item's half box in this tile
+    long long first;                  // first flat index (j_0 fastest)
+};
+// Number of Hermite entries C(d + R, d) of the compile-time tables, or 0 when
+// no lag kernel is instantiated for (d, R, real) (the caller uses the FFT path).
+int lag_table_size(int d, int R, bool dbl);
+template <typename real>
+cudaError_t launch_lag(int d, int R, const LagItem<real>* items, const LagTile* tiles, int ntiles, const real* wpool,
+                       double* partial, int grid, cudaStream_t st);
+template <typename real>
+cudaError_t launch_lag_reduce(const LagItem<real>* items, int nitems, const double* partial, double* out,
+                              cudaStream_t st);
+// One separable pass of the inverse DFT that turns the FP64 count spectrum
+// into the autocorrelation: out[o][jj][i] = sum_{w < W} h(w) in[o][w][i]
+// e^{+2 pi i w (jlo + jj) / P}, h(w) = 1, or for the half-spectrum axis
+// (half != 0) 1 at w = 0 and w = P/2 and 2 elsewhere.  in: real (in_r) or
+// complex (in_c); out: complex (out_c), or the real part times `scale`
+// (out_r, and rounded to FP32 into out_r32 when given).  tw: exp(-2 pi i t
+// / P), t < P.
+cudaError_t launch_acorr_axis(const double* in_r, const double2* in_c, double2* out_c, double* out_r, float* out_r32,
+                              long long O, int W, long long I, int J, int jlo, int P, const double2* tw, int half,
+                              double scale, cudaStream_t st);
+
 // Binning (binning.cu).  Grid node k along axis a is lo[a] + k delta[a],
 // k < M[a].  Counts accumulate into `counts` (zeroed by the caller);
 // `outside` counts the points with a coordinate outside [lo, hi] (or NaN),

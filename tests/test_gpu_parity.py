@@ -24,11 +24,14 @@ from paper_1511_07482_gb300 import synthetic
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["auto", "multipass"])
+@pytest.fixture(scope="module", params=["auto", "fft", "multipass"])
 def ctx(request):
-    from paper_1511_07482_gb300 import ENGINE_AUTO, ENGINE_MULTIPASS, Context
+    """auto: the lag-domain engine wherever the padding has no aliasing;
+    fft: the FFT route (fused cluster kernel for d = 2); multipass: the
+    pass-per-axis FFT kernels only."""
+    from paper_1511_07482_gb300 import ENGINE_AUTO, ENGINE_FFT, ENGINE_MULTIPASS, Context
     c = Context(0)
-    c.set_engine(ENGINE_AUTO if request.param == "auto" else ENGINE_MULTIPASS)
+    c.set_engine({"auto": ENGINE_AUTO, "fft": ENGINE_FFT, "multipass": ENGINE_MULTIPASS}[request.param])
     yield c
     c.close()
 

@@ -220,6 +220,42 @@ def test_parseval_form_and_aliasing():
     assert abs(bad - ref) > 1e-4 * abs(ref)
 
 
+@pytest.mark.parametrize("d,M", [(1, [23]), (2, [9, 7]), (3, [5, 6, 4])])
+def test_autocorrelation_pins(d, M):
+    """a_0 = sum c^2; the half box with its weights covers every lag once,
+    so over the whole lag range sum_full a_j = (sum c)^2; a brute-force
+    double loop over cell pairs gives the same a_j; the half-box form
+    n^-2 sum_half w_j k_j a_j is Eq. 25 (binned_direct)."""
+    rng = np.random.default_rng(40 + d)
+    c = rng.uniform(0.0, 2.0, size=M)
+    A = [m - 1 for m in M]
+    a = F.autocorr(c, A)
+    w = F.half_box_weights(A)
+    zero = tuple(A[k] for k in range(d - 1, 0, -1)) + (0,)
+    assert a[zero] == pytest.approx(float(np.sum(c * c)), rel=1e-14)
+    assert float(np.sum(w * a)) == pytest.approx(float(np.sum(c)) ** 2, rel=1e-13)
+    # brute force over pairs of cells (i, i'), lag j = i' - i, on a few lags
+    cells = list(np.ndindex(*M))
+    for jj in [(1,) + (0,) * (d - 1), tuple([0] + [-1] * (d - 1)) if d > 1 else (2,), tuple(A)]:
+        want = sum(c[i] * c[i2] for i in cells for i2 in cells
+                   if all(i2[k] - i[k] == jj[k] for k in range(d)))
+        idx = tuple(jj[k] + A[k] for k in range(d - 1, 0, -1)) + (jj[0],)
+        assert a[idx] == pytest.approx(want, rel=1e-13, abs=1e-13)
+    # the engine's formula: half box, weights, lag kernel
+    delta = np.full(d, 0.3)
+    H = _spd(np.random.default_rng(7), d, 0.3)
+    L = [min(3, m - 1) for m in M]
+    terms = S.lscv_T_terms(H)
+    k = F.lag_kernel(terms, delta, L)      # full box, index j_k + L_k
+    aL = F.autocorr(c, L)
+    wL = F.half_box_weights(L)
+    tot = 0.0
+    for idx in np.ndindex(*aL.shape):
+        j = [idx[-1]] + [idx[d - 1 - q] - L[q] for q in range(1, d)]
+        tot += wL[idx] * aL[idx] * k[tuple(j[q] + L[q] for q in range(d))]
+    assert tot / 300.0 ** 2 == pytest.approx(F.binned_direct(c, 300, terms, delta, L), rel=1e-12)
+
+
 def test_binned_equals_direct_on_nodes():
     """All points on nodes and L = M - 1: binned sum = direct sum."""
     rng = np.random.default_rng(2)
