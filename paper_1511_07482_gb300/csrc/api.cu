@@ -2681,6 +2681,97 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
         return KDEFFT_ERR_UNSUPPORTED;
     const int nst = (int)th0.size();
     const int M0 = (int)ds->M[0], M1 = (int)ds->M[1];
+    if (c->lag) {
+        // Lag domain: one CTA per start.  The autocorrelation box covers 2.5
+        // times the largest support among the starts (the bandwidth may grow
+        // about 6-fold beyond the widest start); trial points needing more are
+        // outside this search's domain.
+        const Opt o{2, 3};
+        int Lmax[2] = {1, 1};
+        for (const auto& th : th0) {
+            const Mat H = theta_to_H(o, th.data());
+            double B[4];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    const double h = H(a, b);
+                    if (method == KDEFFT_SCV)
+                        B[a * 2 + b] = 2.0 * h + 2.0 * Gm(a, b);
+                    else
+                        B[a * 2 + b] = (ds->opts.L_basis == KDEFFT_L_WIDEST ? 2.0 : 1.0) * h;
+                }
+            const double tr = 0.5 * (B[0] + B[3]), dd = 0.5 * (B[0] - B[3]);
+            const double lam = tr + std::sqrt(dd * dd + B[1] * B[1]);
+            for (int k = 0; k < 2; ++k) {
+                double v = std::ceil(ds->opts.tau * std::sqrt(std::fabs(lam)) / ds->delta[k]);
+                if (!(v <= (double)(ds->M[k] - 1))) v = (double)(ds->M[k] - 1);
+                Lmax[k] = std::max(Lmax[k], (int)std::max(1.0, v));
+            }
+        }
+        std::array<int, 4> need{0, 0, 0, 0};
+        for (int k = 0; k < 2; ++k)
+            need[k] = (int)std::min<long long>(ds->M[k] - 1, std::max(8, (int)std::ceil(2.5 * Lmax[k])));
+        const int ar = ensure_autocorr_many(c, {{ds, need}});
+        if (ar == KDEFFT_ERR_UNSUPPORTED) return KDEFFT_ERR_UNSUPPORTED;
+        KCHK(ar);
+        const size_t bT = sizeof(SelStart) * nst;
+        KCHK(c->sel_buf.ensure(bT));
+        std::vector<SelStart> st(nst);
+        for (int i = 0; i < nst; ++i) {
+            std::memset(&st[i], 0, sizeof(SelStart));
+            for (int k = 0; k < 3; ++k) st[i].th[k] = th0[i][k];
+        }
+        SelStart* dst = (SelStart*)c->sel_buf.p;
+        KCU(cudaMemcpyAsync(dst, st.data(), bT, cudaMemcpyHostToDevice, c->stream));
+        c->h2d += (int64_t)bT;
+        SelectParams prm{};
+        prm.method = (method == KDEFFT_LSCV) ? 0 : 1;
+        prm.max_iter = max_iter;
+        prm.widest = (method == KDEFFT_LSCV && ds->opts.L_basis == KDEFFT_L_WIDEST) ? 1 : 0;
+        prm.M0 = M0;
+        prm.M1 = M1;
+        prm.Lcap = ds->acA[0];
+        prm.Lcap1 = ds->acA[1];
+        prm.n = (double)ds->n;
+        prm.tau = ds->opts.tau;
+        prm.delta0 = ds->delta[0];
+        prm.delta1 = ds->delta[1];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) prm.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gm(a, b) : 0.0;
+        prm.errflag = c->errflag;
+        prm.acorr = (const float*)ds->ac32.p;
+        prm.A0 = ds->acA[0];
+        prm.A1 = ds->acA[1];
+        cudaEvent_t ev = prof_start(c);
+        KCU(launch_select2d_lag(prm, dst, nst, c->stream));
+        prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
+        KCU(cudaMemcpyAsync(st.data(), dst, bT, cudaMemcpyDeviceToHost, c->stream));
+        {
+            HostTimer w(c, "host:wait");
+            KCU(cudaStreamSynchronize(c->stream));
+        }
+        c->d2h += (int64_t)bT;
+        if (c->prof && !c->pending.empty() && ev) {
+            double fl = 0.0, by = 0.0;
+            for (const SelStart& x : st) {
+                fl += x.flops;
+                by += x.bytes;
+            }
+            c->pending.back().flops = fl;
+            c->pending.back().bytes = by;
+        }
+        prof_flush(c);
+        KCHK(check_errflag(c));
+        th_out.assign(nst, std::vector<double>(3));
+        f_out.assign(nst, INFINITY);
+        int64_t ev_total = 0;
+        for (int i = 0; i < nst; ++i) {
+            for (int k = 0; k < 3; ++k) th_out[i][k] = st[i].th[k];
+            f_out[i] = st[i].f;
+            ev_total += st[i].evals;
+        }
+        *evals_out = ev_total;
+        return KDEFFT_OK;
+    }
     auto pmin = [](int m) {
         int p = m;
         while (!is_smooth(p)) ++p;
@@ -2804,6 +2895,7 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     prm.M0 = M0;
     prm.M1 = M1;
     prm.Lcap = Lcap;
+    prm.Lcap1 = Lcap;
     prm.chunk = chunk;
     prm.gat_elems = gat;
     prm.spc_elems = (spc + 3) & ~3;

@@ -1059,19 +1059,19 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
     if (lane == 17) dom = sqrt(c) >= 0.5 * p.delta1;
     const bool inside = __all_sync(FULL, dom) && a > 0.0 && det > 0.0;
     const int L0 = __shfl_sync(FULL, Lk, 8), L1 = __shfl_sync(FULL, Lk, 9);
-    if (!inside || L0 > p.Lcap || L1 > p.Lcap) return false;
-    const int P0 = p.ptab0[L0], P1 = p.ptab1[L1];
+    if (!inside || L0 > p.Lcap || L1 > p.Lcap1) return false;
+    // FFT route: the count spectrum of the padded size for (L0, L1)
     int si = -1;
-    for (int i0 = 0; i0 < p.nspec && si < 0; i0 += 32) {
+    const int P0 = p.acorr ? 0 : p.ptab0[L0], P1 = p.acorr ? 0 : p.ptab1[L1];
+    for (int i0 = 0; !p.acorr && i0 < p.nspec && si < 0; i0 += 32) {
         const int i = i0 + lane;
         const unsigned m = __ballot_sync(FULL, i < p.nspec && p.specs[i].P0 == P0 && p.specs[i].P1 == P1);
         if (m) si = i0 + __ffs(m) - 1;
     }
-    if (si < 0) {
+    if (!p.acorr && si < 0) {
         if (lane == 0) atomicOr(p.errflag, 2);
         return false;
     }
-    const SelSpec& sp = p.specs[si];
     // covariance rows of both items, then the headers, then the weights
     if (lane < nsig) {
         const double iv[4] = {iv0, iv1, iv1, iv3};
@@ -1101,10 +1101,16 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         f.pad_ = 0;
         f.delta0 = p.delta0;
         f.delta1 = p.delta1;
-        f.a0 = sp.a0;
-        f.a1 = sp.a1;
-        f.spec = sp.spec;
-        f.scale = sp.scale;
+        if (p.acorr) {   // lag domain: n^-2, no transform
+            f.spec = nullptr;
+            f.scale = 1.0 / (p.n * p.n);
+        } else {
+            const SelSpec& sp = p.specs[si];
+            f.a0 = sp.a0;
+            f.a1 = sp.a1;
+            f.spec = sp.spec;
+            f.scale = sp.scale;
+        }
     }
     constexpr int NW = 2 * MAXSIG * WDENSE;
     for (int t = lane; t < 2 * NW; t += 32) {
@@ -1128,8 +1134,15 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         Rs[1] = r10;
         Rs[2] = r11;
         aux[0] = det;
-        aux[1] = sp.fl_fix + (double)(2 * L0 + 1) * sp.fl_line;
-        aux[2] = sp.by;
+        if (p.acorr) {   // half box points: two exponentials (LSCV) or three (SCV) and four weighted sums each
+            const double pts = (double)(L0 + 1) * (2 * L1 + 1);
+            aux[1] = pts * nsig * (8.0 + 4.0 * 2.0 * 6.0);
+            aux[2] = pts * sizeof(float);
+        } else {
+            const SelSpec& sp = p.specs[si];
+            aux[1] = sp.fl_fix + (double)(2 * L0 + 1) * sp.fl_line;
+            aux[2] = sp.by;
+        }
     }
     return true;
 }
@@ -1342,6 +1355,109 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
         st.flops = opt.flops;
         st.bytes = opt.bytes;
     }
+}
+
+// Both packed pairs of one bandwidth in the lag domain by one CTA: the half
+// box j_0 in [0, L_0], |j_1| <= L_1 (j_0 fastest, so that neighbouring
+// threads read neighbouring a_j), weights 2 / 1 / 0, four compensated sums,
+// every thread of the CTA receiving the four scaled totals in res4.
+__device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const FusedItem<float>& g,
+                                             const float* __restrict__ acorr, int A0, int A1, double* res4) {
+    const int L0 = f.off0, L1 = f.off1;
+    const int n0 = L0 + 1;
+    const int total = n0 * (2 * L1 + 1);
+    const uint32_t mn0 = magic_of((uint32_t)max(n0, 2));
+    SumAcc<float> acc0, acc1;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int q = (n0 == 1) ? t : (int)qdiv((uint32_t)t, mn0);
+        const int j0 = t - q * n0;
+        const int j1 = q - L1;
+        const int wt = (j0 > 0 || j1 > 0) ? 2 : (j1 == 0 ? 1 : 0);
+        if (!wt) continue;
+        const float av = acorr[(long long)(j1 + A1) * (A0 + 1) + j0];
+        float v[4];
+        kernel_quad_2d(f, g, j0, j1, v);
+        const float wa = (float)wt * av;
+        acc0.add(wa * v[0], wa * v[1]);
+        acc1.add(wa * v[2], wa * v[3]);
+    }
+    double part0[2], part1[2];
+    block_reduce_acc(acc0, part0);
+    block_reduce_acc(acc1, part1);
+    if (threadIdx.x == 0) {
+        res4[0] = part0[0] * f.scale;
+        res4[1] = part0[1] * f.scale;
+        res4[2] = part1[0] * f.scale;
+        res4[3] = part1[1] * f.scale;
+    }
+}
+
+// One CTA per start runs the whole quasi-Newton search with lag-domain
+// evaluations against the count autocorrelation (FP32 copy, L2-resident).
+__global__ void __launch_bounds__(256) k_select2d_lag(SelectParams p, SelStart* __restrict__ starts) {
+    __shared__ double res[2][2];
+    __shared__ FusedItem<float> items[2];
+    __shared__ SelOpt opt;
+    __shared__ int ctl[2];
+    __shared__ double Hs[4], Rs[3], aux[3];
+    const int start = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const SelStart& st = starts[start];
+        for (int i = 0; i < 3; ++i) opt.th_try[i] = st.th[i];
+        opt.first = 1;
+        opt.done = 0;
+        opt.iter = 0;
+        opt.evals = 0;
+        opt.status = 0;
+        opt.f = INFINITY;
+        opt.flops = 0.0;
+        opt.bytes = 0.0;
+    }
+    __syncthreads();
+    const int max_rounds = 40 * p.max_iter + 2;
+    for (int round = 0; round < max_rounds; ++round) {
+        if (threadIdx.x < 32) {
+            const int dn = opt.done;
+            const bool v = dn ? false : sel_prepare(p, opt.th_try, items, Hs, Rs, aux);
+            if (threadIdx.x == 0) {
+                ctl[0] = v ? 1 : 0;
+                ctl[1] = dn;
+            }
+        }
+        __syncthreads();
+        const int valid = ctl[0], done = ctl[1];
+        if (done) break;
+        if (valid) {
+            sel_eval_lag(items[0], items[1], p.acorr, p.A0, p.A1, &res[0][0]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double fn = INFINITY, gt[3] = {0.0, 0.0, 0.0};
+            if (valid) {
+                sel_assemble(p, Hs, Rs, res[0], res[1], aux[0], &fn, gt);
+                opt.evals++;
+                opt.flops += aux[1];
+                opt.bytes += aux[2];
+            }
+            sel_update(opt, fn, gt, p.max_iter);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        SelStart& st = starts[start];
+        for (int i = 0; i < 3; ++i) st.th[i] = opt.th[i];
+        st.f = opt.f;
+        st.evals = opt.evals;
+        st.iters = opt.iter;
+        st.status = opt.done ? opt.status : 1;
+        st.flops = opt.flops;
+        st.bytes = opt.bytes;
+    }
+}
+
+cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st) {
+    k_select2d_lag<<<nstarts, 256, 0, st>>>(prm, starts);
+    return cudaGetLastError();
 }
 
 static size_t select2d_smem(const SelectParams& prm) {

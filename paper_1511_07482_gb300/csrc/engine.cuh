@@ -163,7 +163,7 @@ struct SelectParams {
     int nspec;
     int widest;             // LSCV: support from lambda_max(2H) instead of lambda_max(H)
     int M0, M1;
-    int Lcap;               // trial points needing a larger support are outside the search
+    int Lcap, Lcap1;        // trial points needing a larger support (axis 0, axis 1) are outside the search
     int chunk;              // lines (and columns) per shared-memory batch
     int gat_elems, spc_elems, cap, pmax;   // shared-memory layout (complex / real elements)
     double n, tau;
@@ -173,9 +173,15 @@ struct SelectParams {
     const int* ptab1;
     const SelSpec* specs;
     int* errflag;
+    // lag domain (k_select2d_lag): the FP32 count autocorrelation on the half
+    // box [j_1 + A1][j_0], j_0 in [0, A0]; null for the FFT route
+    const float* acorr;
+    int A0, A1;
 };
 cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts,
                             const float2* twpool, cudaStream_t st);
+// the same search in the lag domain: one CTA per start (prm.acorr set)
+cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st);
 
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
 
