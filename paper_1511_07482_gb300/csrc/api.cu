@@ -2945,6 +2945,13 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     return KDEFFT_OK;
 }
 
+// The line search gives up after this many halvings (the step then moves
+// theta by under 2.5e-4 of the quasi-Newton step): the binned objective
+// steps where a support L_k changes with H (Eq. 26), and a sufficient-
+// decrease test at smaller steps only measures those steps.  The
+// device-resident search uses the same limit.
+static constexpr int kMaxHalvings = 12;
+
 static int select_H_impl(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts, int max_iter,
                          bool nelder_mead, double* H_out, double* f_out, int64_t* n_evals) {
     if (!ds || !H_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
@@ -3374,7 +3381,7 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
             } else {
                 s.step *= 0.5;
                 s.ls++;
-                if (s.ls > 30) {
+                if (s.ls > kMaxHalvings) {
                     s.done = true;
                 } else {
                     for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];

@@ -991,6 +991,29 @@ __device__ __forceinline__ void sel_eval2(cg::cluster_group& cluster, const Fuse
     }
 }
 
+// FP64 reciprocal and reciprocal square root from FP32 seeds refined by
+// Newton-Raphson steps (each step squares the relative error): a few ulp of
+// FP64 in a handful of FMAs, where the FP64 division and square root of
+// this part are long dependent sequences.  Arguments outside the FP32 range
+// take the FP64 operation.
+__device__ __forceinline__ double rcp64(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+__device__ __forceinline__ double rsqrt64(double x) {   // x > 0
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx, y * y, 1.5);
+    y = y * fma(-hx, y * y, 1.5);
+    return y;
+}
+__device__ __forceinline__ double sqrt64(double x) { return x > 0.0 ? x * rsqrt64(x) : 0.0; }
+
 // optimiser state of one start (each CTA of its cluster holds a copy)
 struct SelOpt {
     double th[3], g[3], dir[3], Binv[9], th_try[3];
@@ -1011,7 +1034,10 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
                             double* aux) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const double ex = exp(lane == 0 ? th[0] : th[2]);
+    // the Cholesky diagonal to FP32 accuracy (the trial point is evaluated
+    // at this H; the value reported for the end point is recomputed at the
+    // FP64 bandwidth)
+    const double ex = (double)expf((float)(lane == 0 ? th[0] : th[2]));
     const double r00 = __shfl_sync(FULL, ex, 0), r11 = __shfl_sync(FULL, ex, 1), r10 = th[1];
     double H[4];
     H[0] = r00 * r00;
@@ -1030,10 +1056,11 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         double Ss[4];
         for (int e = 0; e < 4; ++e) Ss[e] = hco * H[e] + gco * p.G[e];
         const double dt = Ss[0] * Ss[3] - Ss[1] * Ss[1];
-        iv0 = Ss[3] / dt;
-        iv1 = -Ss[1] / dt;
-        iv3 = Ss[0] / dt;
-        nr = 1.0 / (6.283185307179586 * sqrt(dt));
+        const double rdt = rcp64(dt);
+        iv0 = Ss[3] * rdt;
+        iv1 = -Ss[1] * rdt;
+        iv3 = Ss[0] * rdt;
+        nr = 0.15915494309189535 * rsqrt64(dt);   // 1 / (2 pi sqrt(det))
     }
     // lanes 8, 9: support along axis k from lambda_max of H (LSCV, paper
     // rule), 2H (LSCV widest) or 2H + 2G (SCV)
@@ -1046,17 +1073,17 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         for (int e = 0; e < 4; ++e) B[e] = bs * H[e] + gco * p.G[e];
         const double tr = 0.5 * (B[0] + B[3]);
         const double dd = 0.5 * (B[0] - B[3]);
-        const double lam = tr + sqrt(dd * dd + B[1] * B[1]);
+        const double lam = tr + sqrt64(dd * dd + B[1] * B[1]);
         const double dl = k == 0 ? p.delta0 : p.delta1;
         const int Mk = k == 0 ? p.M0 : p.M1;
-        double v = ceil(p.tau * sqrt(fabs(lam)) / dl);
+        double v = ceil(p.tau * sqrt64(fabs(lam)) * rcp64(dl));
         if (!(v <= (double)(Mk - 1))) v = (double)(Mk - 1);
         if (v < 1.0) v = 1.0;
         Lk = (int)v;
     }
     // lanes 16, 17: the bandwidth is at least half a bin wide along each axis
-    if (lane == 16) dom = sqrt(a) >= 0.5 * p.delta0;
-    if (lane == 17) dom = sqrt(c) >= 0.5 * p.delta1;
+    if (lane == 16) dom = a >= 0.25 * p.delta0 * p.delta0;   // sqrt(H_00) >= delta_0 / 2
+    if (lane == 17) dom = c >= 0.25 * p.delta1 * p.delta1;
     const bool inside = __all_sync(FULL, dom) && a > 0.0 && det > 0.0;
     const int L0 = __shfl_sync(FULL, Lk, 8), L1 = __shfl_sync(FULL, Lk, 9);
     if (!inside || L0 > p.Lcap || L1 > p.Lcap1) return false;
@@ -1150,22 +1177,24 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
 // objective, gradient in H (tied convention) -> value and theta-gradient
 __device__ void sel_assemble(const SelectParams& p, const double* H, const double* Rm, const double* r0,
                              const double* r1, double det, double* f, double* gt) {
-    const double rdet = 1.0 / det;
+    const double rdet = rcp64(det);
+    const double rsd = rsqrt64(det);   // |H|^-1/2
+    const double rn = rcp64(p.n);
     const double hi00 = H[3] * rdet, hi01 = -H[1] * rdet, hi11 = H[0] * rdet;
     double g00, g01, g11;
     if (p.method == 0) {
-        const double k0 = 0.15915494309189535 * sqrt(rdet);   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
-        const double c0 = 2.0 / p.n;
+        const double k0 = 0.15915494309189535 * rsd;   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
+        const double c0 = 2.0 * rn;
         *f = r0[0] + c0 * k0;
         g00 = r0[1] + c0 * (-0.5 * k0 * hi00);
         g01 = r1[0] + c0 * 2.0 * (-0.5 * k0 * hi01);
         g11 = r1[1] + c0 * (-0.5 * k0 * hi11);
     } else {
-        const double rk = 0.07957747154594767 * sqrt(rdet);   // (4 pi)^-1 |H|^-1/2
-        *f = rk / p.n + r0[0];
-        g00 = r0[1] + (-0.5 * rk * hi00) / p.n;
-        g01 = r1[0] + 2.0 * (-0.5 * rk * hi01) / p.n;
-        g11 = r1[1] + (-0.5 * rk * hi11) / p.n;
+        const double rk = 0.07957747154594767 * rsd;   // (4 pi)^-1 |H|^-1/2
+        *f = rk * rn + r0[0];
+        g00 = r0[1] + (-0.5 * rk * hi00) * rn;
+        g01 = r1[0] + 2.0 * (-0.5 * rk * hi01) * rn;
+        g11 = r1[1] + (-0.5 * rk * hi11) * rn;
     }
     // dF/dR = 2 G_ind R (G_ind off-diagonal = g01 / 2), chain rule to theta
     const double G00 = g00, G01 = 0.5 * g01, G11 = g11;
@@ -1187,7 +1216,7 @@ __device__ void sel_new_direction(SelOpt& s) {
     s.slope = s.dir[0] * s.g[0] + s.dir[1] * s.g[1] + s.dir[2] * s.g[2];
     if (!(s.slope < 0.0)) {
         const double gn = fmax(fabs(s.g[0]), fmax(fabs(s.g[1]), fabs(s.g[2])));
-        const double sc = (gn > 0) ? 0.1 / gn : 1.0;
+        const double sc = (gn > 0) ? 0.1 * rcp64(gn) : 1.0;
         for (int i = 0; i < 9; ++i) s.Binv[i] = 0.0;
         for (int i = 0; i < 3; ++i) {
             s.Binv[i * 4] = sc;
@@ -1197,13 +1226,20 @@ __device__ void sel_new_direction(SelOpt& s) {
     }
     const double dm = fmax(fabs(s.dir[0]), fmax(fabs(s.dir[1]), fabs(s.dir[2])));
     if (dm > 1.0) {
-        for (int i = 0; i < 3; ++i) s.dir[i] /= dm;
-        s.slope /= dm;
+        const double r = rcp64(dm);
+        for (int i = 0; i < 3; ++i) s.dir[i] *= r;
+        s.slope *= r;
     }
     s.step = 1.0;
     s.ls = 0;
     for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
 }
+
+// The line search gives up after this many halvings (the step then moves
+// theta by under 2.5e-4 of the quasi-Newton step): the binned objective
+// steps where a support L_k changes with H (Eq. 26), and a sufficient-
+// decrease test at smaller steps only measures those steps.
+constexpr int kMaxHalvings = 12;
 
 // consume the evaluation (fn, gn) of the trial point th_try
 __device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter) {
@@ -1220,7 +1256,7 @@ __device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter)
             return;
         }
         const double gm = fmax(fabs(gn[0]), fmax(fabs(gn[1]), fabs(gn[2])));
-        const double sc = (gm > 0) ? 0.1 / gm : 1.0;
+        const double sc = (gm > 0) ? 0.1 * rcp64(gm) : 1.0;
         for (int i = 0; i < 9; ++i) s.Binv[i] = 0.0;
         for (int i = 0; i < 3; ++i) s.Binv[i * 4] = sc;
         if (gm == 0.0) {
@@ -1244,7 +1280,7 @@ __device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter)
                 for (int j = 0; j < 3; ++j) By[i] += s.Binv[i * 3 + j] * yv[j];
                 yBy += yv[i] * By[i];
             }
-            const double rsy = 1.0 / sy;   // one FP64 division for the nine entries
+            const double rsy = rcp64(sy);
             const double c1 = (sy + yBy) * rsy * rsy;
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j)
@@ -1271,7 +1307,7 @@ __device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter)
     } else {
         s.step *= 0.5;
         s.ls++;
-        if (s.ls > 30) {
+        if (s.ls > kMaxHalvings) {
             s.done = 1;
         } else {
             for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
@@ -1359,8 +1395,8 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
 
 // Both packed pairs of one bandwidth in the lag domain by one CTA: the half
 // box j_0 in [0, L_0], |j_1| <= L_1 (j_0 fastest, so that neighbouring
-// threads read neighbouring a_j), weights 2 / 1 / 0, four compensated sums,
-// every thread of the CTA receiving the four scaled totals in res4.
+// threads read neighbouring a_j), weights 2 / 1 / 0, four compensated sums;
+// thread 0 receives the four scaled totals in res4.
 __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const FusedItem<float>& g,
                                              const float* __restrict__ acorr, int A0, int A1, double* res4) {
     const int L0 = f.off0, L1 = f.off1;
@@ -1381,20 +1417,41 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const Fu
         acc0.add(wa * v[0], wa * v[1]);
         acc1.add(wa * v[2], wa * v[3]);
     }
-    double part0[2], part1[2];
-    block_reduce_acc(acc0, part0);
-    block_reduce_acc(acc1, part1);
-    if (threadIdx.x == 0) {
-        res4[0] = part0[0] * f.scale;
-        res4[1] = part0[1] * f.scale;
-        res4[2] = part1[0] * f.scale;
-        res4[3] = part1[1] * f.scale;
+    // one block reduction of the four compensated sums
+    __shared__ DFloat red4[4][32];
+    DFloat v4[4] = {acc0.a, acc0.b, acc1.a, acc1.b};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const DFloat t{__shfl_down_sync(0xffffffffu, v4[e].h, o), __shfl_down_sync(0xffffffffu, v4[e].l, o)};
+            v4[e] = df_add(v4[e], t);
+        }
+    const int wi = threadIdx.x >> 5, li = threadIdx.x & 31;
+    if (li == 0)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red4[e][wi] = v4[e];
+    __syncthreads();
+    if (wi == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v4[e] = (li < nw) ? red4[e][li] : DFloat{0.f, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const DFloat t{__shfl_down_sync(0xffffffffu, v4[e].h, o), __shfl_down_sync(0xffffffffu, v4[e].l, o)};
+                v4[e] = df_add(v4[e], t);
+            }
+        if (li == 0)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) res4[e] = ((double)v4[e].h + (double)v4[e].l) * f.scale;
     }
 }
 
 // One CTA per start runs the whole quasi-Newton search with lag-domain
 // evaluations against the count autocorrelation (FP32 copy, L2-resident).
-__global__ void __launch_bounds__(256) k_select2d_lag(SelectParams p, SelStart* __restrict__ starts) {
+__global__ void __launch_bounds__(512) k_select2d_lag(SelectParams p, SelStart* __restrict__ starts) {
     __shared__ double res[2][2];
     __shared__ FusedItem<float> items[2];
     __shared__ SelOpt opt;
@@ -1456,7 +1513,7 @@ __global__ void __launch_bounds__(256) k_select2d_lag(SelectParams p, SelStart* 
 }
 
 cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st) {
-    k_select2d_lag<<<nstarts, 256, 0, st>>>(prm, starts);
+    k_select2d_lag<<<nstarts, 512, 0, st>>>(prm, starts);
     return cudaGetLastError();
 }
 
