@@ -17,11 +17,77 @@
 namespace kdefft {
 
 // ------------------------------------------------------------ autocorrelation passes
-__global__ void __launch_bounds__(256) k_acorr_axis(const double* __restrict__ in_r, const double2* __restrict__ in_c,
-                                                    double2* __restrict__ out_c, double* __restrict__ out_r,
-                                                    float* __restrict__ out_r32, long long O, int W, long long I,
-                                                    int J, int jlo, int P,
+// twiddles exp(-2 pi i t / P) of one size in shared memory when they fit
+constexpr int kTwSmem = 2048;
+
+// Pass over the innermost axis of the real spectrum (layout [o][w], one row
+// of W values per o): one CTA per row, the row and the twiddles staged in
+// shared memory, one warp per output lag, the lanes splitting the sum.
+__global__ void __launch_bounds__(256) k_acorr_row(const double* __restrict__ in_r, double2* __restrict__ out_c,
+                                                   double* __restrict__ out_r, float* __restrict__ out_r32,
+                                                   long long O, int W, int J, int jlo, int P,
+                                                   const double2* __restrict__ tw, int half, double scale) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double2* stw = reinterpret_cast<double2*>(sm_raw);
+    const bool tws = P <= kTwSmem;
+    double* row = reinterpret_cast<double*>(stw + (tws ? P : 0));
+    if (tws)
+        for (int t = threadIdx.x; t < P; t += blockDim.x) stw[t] = tw[t];
+    const double2* T = tws ? stw : tw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long o = blockIdx.x; o < O; o += gridDim.x) {
+        __syncthreads();   // the previous row's readers are done (and the twiddles are in)
+        for (int w = threadIdx.x; w < W; w += blockDim.x) row[w] = in_r[o * W + w];
+        __syncthreads();
+        for (int jj = warp; jj < J; jj += nw) {
+            int step = (jlo + jj) % P;
+            if (step < 0) step += P;
+            // position (w step) mod P for w = lane, lane + 32, ...
+            int pos = (int)(((long long)lane * step) % P);
+            const int adv = (int)((32LL * step) % P);
+            double sr = 0.0, si = 0.0;
+            for (int w = lane; w < W; w += 32) {
+                const double2 t = T[pos];
+                const double h = (half && w != 0 && 2 * w != P) ? 2.0 : 1.0;
+                const double x = h * row[w];
+                sr = fma(x, t.x, sr);
+                si = fma(-x, t.y, si);
+                pos += adv;
+                if (pos >= P) pos -= P;
+            }
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) {
+                sr += __shfl_down_sync(0xffffffffu, sr, sh);
+                si += __shfl_down_sync(0xffffffffu, si, sh);
+            }
+            if (lane == 0) {
+                const long long idx = o * J + jj;
+                if (out_r) {
+                    out_r[idx] = sr * scale;
+                    if (out_r32) out_r32[idx] = (float)(sr * scale);
+                } else {
+                    out_c[idx] = make_double2(sr, si);
+                }
+            }
+        }
+    }
+}
+
+// Pass over an outer axis of complex data [o][w][i] -> [o][jj][i]: one
+// thread per output, i fastest (coalesced reads, one twiddle per warp and
+// step), twiddles in shared memory.
+__global__ void __launch_bounds__(256) k_acorr_axis(const double2* __restrict__ in_c, double2* __restrict__ out_c,
+                                                    double* __restrict__ out_r, float* __restrict__ out_r32,
+                                                    long long O, int W, long long I, int J, int jlo, int P,
                                                     const double2* __restrict__ tw, int half, double scale) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double2* stw = reinterpret_cast<double2*>(sm_raw);
+    const bool tws = P <= kTwSmem;
+    if (tws) {
+        for (int t = threadIdx.x; t < P; t += blockDim.x) stw[t] = tw[t];
+        __syncthreads();
+    }
+    const double2* T = tws ? stw : tw;
     const long long total = O * (long long)J * I;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -35,27 +101,20 @@ __global__ void __launch_bounds__(256) k_acorr_axis(const double* __restrict__ i
         double sr = 0.0, si = 0.0;
         const long long base = o * (long long)W * I + i;
         for (int w = 0; w < W; ++w) {
-            const double2 t = tw[pos];   // exp(-2 pi i pos / P); the pass uses its conjugate
-            double xr, xi;
-            if (in_r) {
-                xr = in_r[base + (long long)w * I];
-                xi = 0.0;
-            } else {
-                const double2 x = in_c[base + (long long)w * I];
-                xr = x.x;
-                xi = x.y;
-            }
+            const double2 t = T[pos];   // exp(-2 pi i pos / P); the pass uses its conjugate
+            const double2 x = in_c[base + (long long)w * I];
             const double h = (half && w != 0 && 2 * w != P) ? 2.0 : 1.0;
-            sr += h * (xr * t.x + xi * t.y);
-            si += h * (xi * t.x - xr * t.y);
+            sr = fma(h * x.x, t.x, fma(h * x.y, t.y, sr));
+            si = fma(h * x.y, t.x, fma(-h * x.x, t.y, si));
             pos += step;
             if (pos >= P) pos -= P;
         }
         if (out_r) {
             out_r[idx] = sr * scale;
             if (out_r32) out_r32[idx] = (float)(sr * scale);
-        } else
+        } else {
             out_c[idx] = make_double2(sr, si);
+        }
     }
 }
 
@@ -64,9 +123,23 @@ cudaError_t launch_acorr_axis(const double* in_r, const double2* in_c, double2* 
                               double scale, cudaStream_t st) {
     const long long total = O * (long long)J * I;
     if (total <= 0) return cudaSuccess;
+    const size_t twb = (P <= kTwSmem) ? sizeof(double2) * (size_t)P : 0;
+    if (in_r) {   // innermost axis of the real spectrum (I = 1)
+        if (I != 1) return cudaErrorInvalidValue;
+        const size_t sm = twb + sizeof(double) * (size_t)W;
+        static size_t set_bytes = 48 * 1024;
+        if (sm > set_bytes) {
+            cudaError_t e = cudaFuncSetAttribute(k_acorr_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            set_bytes = sm;
+        }
+        const long long b = O < 65535 ? O : 65535;
+        k_acorr_row<<<(int)b, 256, sm, st>>>(in_r, out_c, out_r, out_r32, O, W, J, jlo, P, tw, half, scale);
+        return cudaGetLastError();
+    }
     long long b = (total + 255) / 256;
     if (b > 65535) b = 65535;
-    k_acorr_axis<<<(int)b, 256, 0, st>>>(in_r, in_c, out_c, out_r, out_r32, O, W, I, J, jlo, P, tw, half, scale);
+    k_acorr_axis<<<(int)b, 256, twb, st>>>(in_c, out_c, out_r, out_r32, O, W, I, J, jlo, P, tw, half, scale);
     return cudaGetLastError();
 }
 
