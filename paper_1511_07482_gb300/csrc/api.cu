@@ -2732,6 +2732,8 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
         prm.Lcap = ds->acA[0];
         prm.Lcap1 = ds->acA[1];
         prm.n = (double)ds->n;
+        prm.inv_n = 1.0 / prm.n;
+        prm.inv_n2 = 1.0 / (prm.n * prm.n);
         prm.tau = ds->opts.tau;
         prm.delta0 = ds->delta[0];
         prm.delta1 = ds->delta[1];
@@ -2902,6 +2904,8 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     prm.cap = cap;
     prm.pmax = pmax;
     prm.n = (double)ds->n;
+    prm.inv_n = 1.0 / prm.n;
+    prm.inv_n2 = 1.0 / (prm.n * prm.n);
     prm.tau = ds->opts.tau;
     prm.delta0 = ds->delta[0];
     prm.delta1 = ds->delta[1];

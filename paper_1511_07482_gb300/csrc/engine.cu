@@ -1014,78 +1014,65 @@ __device__ __forceinline__ double rsqrt64(double x) {   // x > 0
 }
 __device__ __forceinline__ double sqrt64(double x) { return x > 0.0 ? x * rsqrt64(x) : 0.0; }
 
-// optimiser state of one start (each CTA of its cluster holds a copy)
+// Optimiser state of one start (each CTA of its cluster holds a copy).  The
+// search only compares FP32 evaluations and the value reported for its end
+// point is recomputed at the FP64 bandwidth, so the quasi-Newton algebra is
+// FP32 (FP64 arithmetic is slow on this part); the objective values and the
+// parameters theta stay FP64.
 struct SelOpt {
-    double th[3], g[3], dir[3], Binv[9], th_try[3];
-    double f, step, slope;
+    double th[3], th_try[3];
+    float g[3], dir[3], Binv[9];
+    double f;
+    float step, slope;
     double flops, bytes;
     int iter, ls, done, evals, status, first;
 };
 
-// H = R R^T, R = [[e^t0, 0], [t1, e^t2]] (sel_prepare)
+// H = R R^T, R = [[e^t0, 0], [t1, e^t2]].
 // Warp 0 of a CTA: trial point theta -> H, R and the two work items; every
 // lane returns false when H is outside the search domain (or needs a support
-// beyond Lcap / a size with no spectrum).  The independent FP64 chains (the
-// two exponentials, each covariance's inverse and normalisation, each axis'
-// support, the domain tests) run on separate lanes, so that their long
-// dependent sequences overlap.  Every CTA of a cluster computes the same
-// items from the same theta.
+// beyond the cap / a size with no spectrum).  All lanes run the same
+// straight-line FP32 code (lane s < nsig keeps covariance s), with the
+// determinants in FP64 where a strongly correlated H would cancel.  Every CTA
+// of a cluster computes the same items from the same theta.
 __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<float>* it, double* Hs, double* Rs,
                             double* aux) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    // the Cholesky diagonal to FP32 accuracy (the trial point is evaluated
-    // at this H; the value reported for the end point is recomputed at the
-    // FP64 bandwidth)
-    const double ex = (double)expf((float)(lane == 0 ? th[0] : th[2]));
-    const double r00 = __shfl_sync(FULL, ex, 0), r11 = __shfl_sync(FULL, ex, 1), r10 = th[1];
-    double H[4];
-    H[0] = r00 * r00;
-    H[1] = r00 * r10;
-    H[2] = r10 * r00;
-    H[3] = r10 * r10 + r11 * r11;
-    const double a = H[0], b = H[1], c = H[3];
-    const double det = a * c - b * b;
+    const float r00 = expf((float)th[0]), r11 = expf((float)th[2]), r10 = (float)th[1];
+    const float H[4] = {r00 * r00, r00 * r10, r10 * r00, fmaf(r10, r10, r11 * r11)};
+    const float a = H[0], b = H[1], c = H[3];
+    const double det = (double)a * (double)c - (double)b * (double)b;
     // covariances: LSCV {2H, H}; SCV {2H + 2G, H + 2G, 2G}
     const int nsig = (p.method == 0) ? 2 : 3;
-    const double gco = (p.method == 0) ? 0.0 : 2.0;
-    // lane s < nsig: inverse and normalisation of covariance s
-    double iv0 = 0.0, iv1 = 0.0, iv3 = 0.0, nr = 0.0;
-    if (lane < nsig) {
-        const double hco = (lane == 0) ? 2.0 : (lane == 1 ? 1.0 : 0.0);
-        double Ss[4];
-        for (int e = 0; e < 4; ++e) Ss[e] = hco * H[e] + gco * p.G[e];
-        const double dt = Ss[0] * Ss[3] - Ss[1] * Ss[1];
-        const double rdt = rcp64(dt);
-        iv0 = Ss[3] * rdt;
-        iv1 = -Ss[1] * rdt;
-        iv3 = Ss[0] * rdt;
-        nr = 0.15915494309189535 * rsqrt64(dt);   // 1 / (2 pi sqrt(det))
-    }
-    // lanes 8, 9: support along axis k from lambda_max of H (LSCV, paper
-    // rule), 2H (LSCV widest) or 2H + 2G (SCV)
-    int Lk = 0;
-    bool dom = true;
-    if (lane == 8 || lane == 9) {
-        const int k = lane - 8;
-        const double bs = (p.method == 1 || p.widest) ? 2.0 : 1.0;
-        double B[4];
-        for (int e = 0; e < 4; ++e) B[e] = bs * H[e] + gco * p.G[e];
-        const double tr = 0.5 * (B[0] + B[3]);
-        const double dd = 0.5 * (B[0] - B[3]);
-        const double lam = tr + sqrt64(dd * dd + B[1] * B[1]);
-        const double dl = k == 0 ? p.delta0 : p.delta1;
-        const int Mk = k == 0 ? p.M0 : p.M1;
-        double v = ceil(p.tau * sqrt64(fabs(lam)) * rcp64(dl));
-        if (!(v <= (double)(Mk - 1))) v = (double)(Mk - 1);
-        if (v < 1.0) v = 1.0;
-        Lk = (int)v;
-    }
-    // lanes 16, 17: the bandwidth is at least half a bin wide along each axis
-    if (lane == 16) dom = a >= 0.25 * p.delta0 * p.delta0;   // sqrt(H_00) >= delta_0 / 2
-    if (lane == 17) dom = c >= 0.25 * p.delta1 * p.delta1;
-    const bool inside = __all_sync(FULL, dom) && a > 0.0 && det > 0.0;
-    const int L0 = __shfl_sync(FULL, Lk, 8), L1 = __shfl_sync(FULL, Lk, 9);
+    const float gco = (p.method == 0) ? 0.f : 2.f;
+    const float G[4] = {(float)p.G[0], (float)p.G[1], (float)p.G[2], (float)p.G[3]};
+    const int sl = lane < nsig ? lane : 0;
+    const float hco = (sl == 0) ? 2.f : (sl == 1 ? 1.f : 0.f);
+    float Ss[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Ss[e] = fmaf(hco, H[e], gco * G[e]);
+    const double dts = (double)Ss[0] * (double)Ss[3] - (double)Ss[1] * (double)Ss[1];
+    const float rdt = __frcp_rn((float)dts);
+    const float iv0 = Ss[3] * rdt, iv1 = -Ss[1] * rdt, iv3 = Ss[0] * rdt;
+    const float nr = 0.15915494f * rsqrtf((float)dts);   // 1 / (2 pi sqrt(det))
+    // supports from lambda_max of H (LSCV, paper rule), 2H (LSCV widest) or 2H + 2G (SCV)
+    const float bs = (p.method == 1 || p.widest) ? 2.f : 1.f;
+    float B[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) B[e] = fmaf(bs, H[e], gco * G[e]);
+    const float tr = 0.5f * (B[0] + B[3]), dd = 0.5f * (B[0] - B[3]);
+    const float sq = sqrtf(fabsf(tr + sqrtf(fmaf(dd, dd, B[1] * B[1]))));
+    const float tau = (float)p.tau;
+    float v0 = ceilf(tau * sq * __frcp_rn((float)p.delta0));
+    float v1 = ceilf(tau * sq * __frcp_rn((float)p.delta1));
+    v0 = fminf(fmaxf(v0, 1.f), (float)(p.M0 - 1));
+    v1 = fminf(fmaxf(v1, 1.f), (float)(p.M1 - 1));
+    const int L0 = (int)v0, L1 = (int)v1;
+    // the bandwidth is at least half a bin wide along each axis
+    const float d0 = (float)p.delta0, d1 = (float)p.delta1;
+    const bool inside = a > 0.f && det > 0.0 && a >= 0.25f * d0 * d0 && c >= 0.25f * d1 * d1 && !(v0 != v0) &&
+                        !(v1 != v1);
     if (!inside || L0 > p.Lcap || L1 > p.Lcap1) return false;
     // FFT route: the count spectrum of the padded size for (L0, L1)
     int si = -1;
@@ -1100,22 +1087,14 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         return false;
     }
     // covariance rows of both items, then the headers, then the weights
-    if (lane < nsig) {
-        const double iv[4] = {iv0, iv1, iv1, iv3};
+    if (lane < MAXSIG) {
+        const bool on = lane < nsig;
+        const float iv[4] = {on ? iv0 : 0.f, on ? iv1 : 0.f, on ? iv1 : 0.f, on ? iv3 : 0.f};
+#pragma unroll
         for (int q = 0; q < 2; ++q) {
-            for (int e = 0; e < 4; ++e) {
-                it[q].lam[lane][e] = iv[e];
-                it[q].laml[lane][e] = (float)iv[e];
-            }
-            it[q].nrm[lane] = (float)nr;
-        }
-    } else if (lane < MAXSIG) {
-        for (int q = 0; q < 2; ++q) {
-            for (int e = 0; e < 4; ++e) {
-                it[q].lam[lane][e] = 0.0;
-                it[q].laml[lane][e] = 0.f;
-            }
-            it[q].nrm[lane] = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) it[q].laml[lane][e] = iv[e];
+            it[q].nrm[lane] = on ? nr : 0.f;
         }
     }
     if (lane < 2) {
@@ -1130,7 +1109,7 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         f.delta1 = p.delta1;
         if (p.acorr) {   // lag domain: n^-2, no transform
             f.spec = nullptr;
-            f.scale = 1.0 / (p.n * p.n);
+            f.scale = p.inv_n2;
         } else {
             const SelSpec& sp = p.specs[si];
             f.a0 = sp.a0;
@@ -1140,12 +1119,13 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         }
     }
     constexpr int NW = 2 * MAXSIG * WDENSE;
-    for (int t = lane; t < 2 * NW; t += 32) {
-        const int q = t / NW, r = t - q * NW;
-        (&it[q].W[0][0][0])[r] = 0.f;
-    }
+    if (!p.acorr)   // the FFT route's generic evaluator reads dense weights; the lag route has them built in
+        for (int t = lane; t < 2 * NW; t += 32) {
+            const int q = t / NW, r = t - q * NW;
+            (&it[q].W[0][0][0])[r] = 0.f;
+        }
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && !p.acorr) {
         // Hermite indices (d = 2, graded): 0 -> (0,0), 3 -> (2,0), 4 -> (1,1), 5 -> (0,2)
         it[0].W[0][0][0] = 1.f;
         it[0].W[0][1][0] = -2.f;
@@ -1156,12 +1136,14 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         it[1].W[0][1][4] = -2.f;
         it[1].W[1][0][5] = 1.f;
         it[1].W[1][1][5] = -1.f;
-        for (int e = 0; e < 4; ++e) Hs[e] = H[e];
+    }
+    if (lane == 0) {
+        for (int e = 0; e < 4; ++e) Hs[e] = (double)H[e];
         Rs[0] = r00;
         Rs[1] = r10;
         Rs[2] = r11;
         aux[0] = det;
-        if (p.acorr) {   // half box points: two exponentials (LSCV) or three (SCV) and four weighted sums each
+        if (p.acorr) {   // half box points: per covariance a quadratic form (8) and four six-term weighted sums (48)
             const double pts = (double)(L0 + 1) * (2 * L1 + 1);
             aux[1] = pts * nsig * (8.0 + 4.0 * 2.0 * 6.0);
             aux[2] = pts * sizeof(float);
@@ -1175,33 +1157,35 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
 }
 
 // objective, gradient in H (tied convention) -> value and theta-gradient
+// (FP32 algebra; the value is the FP64 sum of the device sums and the
+// closed-form term)
 __device__ void sel_assemble(const SelectParams& p, const double* H, const double* Rm, const double* r0,
-                             const double* r1, double det, double* f, double* gt) {
-    const double rdet = rcp64(det);
-    const double rsd = rsqrt64(det);   // |H|^-1/2
-    const double rn = rcp64(p.n);
-    const double hi00 = H[3] * rdet, hi01 = -H[1] * rdet, hi11 = H[0] * rdet;
-    double g00, g01, g11;
+                             const double* r1, double det, double* f, float* gt) {
+    const float rdet = __frcp_rn((float)det);
+    const float rsd = rsqrtf((float)det);   // |H|^-1/2
+    const float rn = (float)p.inv_n;
+    const float hi00 = (float)H[3] * rdet, hi01 = -(float)H[1] * rdet, hi11 = (float)H[0] * rdet;
+    float g00, g01, g11;
     if (p.method == 0) {
-        const double k0 = 0.15915494309189535 * rsd;   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
-        const double c0 = 2.0 * rn;
-        *f = r0[0] + c0 * k0;
-        g00 = r0[1] + c0 * (-0.5 * k0 * hi00);
-        g01 = r1[0] + c0 * 2.0 * (-0.5 * k0 * hi01);
-        g11 = r1[1] + c0 * (-0.5 * k0 * hi11);
+        const float k0 = 0.15915494f * rsd;   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
+        const float c0 = 2.f * rn;
+        *f = r0[0] + (double)(c0 * k0);
+        g00 = (float)r0[1] + c0 * (-0.5f * k0 * hi00);
+        g01 = (float)r1[0] + c0 * 2.f * (-0.5f * k0 * hi01);
+        g11 = (float)r1[1] + c0 * (-0.5f * k0 * hi11);
     } else {
-        const double rk = 0.07957747154594767 * rsd;   // (4 pi)^-1 |H|^-1/2
-        *f = rk * rn + r0[0];
-        g00 = r0[1] + (-0.5 * rk * hi00) * rn;
-        g01 = r1[0] + 2.0 * (-0.5 * rk * hi01) * rn;
-        g11 = r1[1] + (-0.5 * rk * hi11) * rn;
+        const float rk = 0.07957747f * rsd;   // (4 pi)^-1 |H|^-1/2
+        *f = (double)(rk * rn) + r0[0];
+        g00 = (float)r0[1] + (-0.5f * rk * hi00) * rn;
+        g01 = (float)r1[0] + 2.f * (-0.5f * rk * hi01) * rn;
+        g11 = (float)r1[1] + (-0.5f * rk * hi11) * rn;
     }
     // dF/dR = 2 G_ind R (G_ind off-diagonal = g01 / 2), chain rule to theta
-    const double G00 = g00, G01 = 0.5 * g01, G11 = g11;
-    const double R00 = Rm[0], R10 = Rm[1], R11 = Rm[2];
-    const double d00 = 2.0 * (G00 * R00 + G01 * R10);
-    const double d10 = 2.0 * (G01 * R00 + G11 * R10);
-    const double d11 = 2.0 * (G11 * R11);
+    const float G00 = g00, G01 = 0.5f * g01, G11 = g11;
+    const float R00 = (float)Rm[0], R10 = (float)Rm[1], R11 = (float)Rm[2];
+    const float d00 = 2.f * (G00 * R00 + G01 * R10);
+    const float d10 = 2.f * (G01 * R00 + G11 * R10);
+    const float d11 = 2.f * (G11 * R11);
     gt[0] = d00 * R00;
     gt[1] = d10;
     gt[2] = d11 * R11;
@@ -1209,30 +1193,30 @@ __device__ void sel_assemble(const SelectParams& p, const double* H, const doubl
 
 __device__ void sel_new_direction(SelOpt& s) {
     for (int i = 0; i < 3; ++i) {
-        double v = 0.0;
+        float v = 0.f;
         for (int j = 0; j < 3; ++j) v -= s.Binv[i * 3 + j] * s.g[j];
         s.dir[i] = v;
     }
     s.slope = s.dir[0] * s.g[0] + s.dir[1] * s.g[1] + s.dir[2] * s.g[2];
-    if (!(s.slope < 0.0)) {
-        const double gn = fmax(fabs(s.g[0]), fmax(fabs(s.g[1]), fabs(s.g[2])));
-        const double sc = (gn > 0) ? 0.1 * rcp64(gn) : 1.0;
-        for (int i = 0; i < 9; ++i) s.Binv[i] = 0.0;
+    if (!(s.slope < 0.f)) {
+        const float gn = fmaxf(fabsf(s.g[0]), fmaxf(fabsf(s.g[1]), fabsf(s.g[2])));
+        const float sc = (gn > 0.f) ? 0.1f * __frcp_rn(gn) : 1.f;
+        for (int i = 0; i < 9; ++i) s.Binv[i] = 0.f;
         for (int i = 0; i < 3; ++i) {
             s.Binv[i * 4] = sc;
             s.dir[i] = -sc * s.g[i];
         }
         s.slope = s.dir[0] * s.g[0] + s.dir[1] * s.g[1] + s.dir[2] * s.g[2];
     }
-    const double dm = fmax(fabs(s.dir[0]), fmax(fabs(s.dir[1]), fabs(s.dir[2])));
-    if (dm > 1.0) {
-        const double r = rcp64(dm);
+    const float dm = fmaxf(fabsf(s.dir[0]), fmaxf(fabsf(s.dir[1]), fabsf(s.dir[2])));
+    if (dm > 1.f) {
+        const float r = __frcp_rn(dm);
         for (int i = 0; i < 3; ++i) s.dir[i] *= r;
         s.slope *= r;
     }
-    s.step = 1.0;
+    s.step = 1.f;
     s.ls = 0;
-    for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+    for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + (double)(s.step * s.dir[i]);
 }
 
 // The line search gives up after this many halvings (the step then moves
@@ -1242,7 +1226,7 @@ __device__ void sel_new_direction(SelOpt& s) {
 constexpr int kMaxHalvings = 12;
 
 // consume the evaluation (fn, gn) of the trial point th_try
-__device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter) {
+__device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) {
     if (s.first) {
         s.first = 0;
         s.f = fn;
@@ -1255,70 +1239,67 @@ __device__ void sel_update(SelOpt& s, double fn, const double* gn, int max_iter)
             s.status = 2;
             return;
         }
-        const double gm = fmax(fabs(gn[0]), fmax(fabs(gn[1]), fabs(gn[2])));
-        const double sc = (gm > 0) ? 0.1 * rcp64(gm) : 1.0;
-        for (int i = 0; i < 9; ++i) s.Binv[i] = 0.0;
+        const float gm = fmaxf(fabsf(gn[0]), fmaxf(fabsf(gn[1]), fabsf(gn[2])));
+        const float sc = (gm > 0.f) ? 0.1f * __frcp_rn(gm) : 1.f;
+        for (int i = 0; i < 9; ++i) s.Binv[i] = 0.f;
         for (int i = 0; i < 3; ++i) s.Binv[i * 4] = sc;
-        if (gm == 0.0) {
+        if (gm == 0.f) {
             s.done = 1;
             return;
         }
         sel_new_direction(s);
         return;
     }
-    if (isfinite(fn) && fn <= s.f + 1e-4 * s.step * s.slope) {
-        double sv[3], yv[3], sy = 0.0;
+    if (isfinite(fn) && fn <= s.f + 1e-4 * (double)(s.step * s.slope)) {
+        float sv[3], yv[3], sy = 0.f;
         for (int i = 0; i < 3; ++i) {
-            sv[i] = s.th_try[i] - s.th[i];
+            sv[i] = (float)(s.th_try[i] - s.th[i]);
             yv[i] = gn[i] - s.g[i];
             sy += sv[i] * yv[i];
         }
-        if (sy > 1e-300) {
-            double By[3], yBy = 0.0;
+        if (sy > 1e-30f) {
+            float By[3], yBy = 0.f;
             for (int i = 0; i < 3; ++i) {
-                By[i] = 0.0;
+                By[i] = 0.f;
                 for (int j = 0; j < 3; ++j) By[i] += s.Binv[i * 3 + j] * yv[j];
                 yBy += yv[i] * By[i];
             }
-            const double rsy = rcp64(sy);
-            const double c1 = (sy + yBy) * rsy * rsy;
+            const float rsy = __frcp_rn(sy);
+            const float c1 = (sy + yBy) * rsy * rsy;
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j)
                     s.Binv[i * 3 + j] += c1 * sv[i] * sv[j] - (By[i] * sv[j] + sv[i] * By[j]) * rsy;
         }
         const double fold = s.f;
-        double gm = 0.0, tn = 0.0;
+        float gm = 0.f, tn = 0.f;
         for (int i = 0; i < 3; ++i) {
             s.th[i] = s.th_try[i];
             s.g[i] = gn[i];
-            gm = fmax(gm, fabs(gn[i]));
-            tn = fmax(tn, fabs(sv[i]));
+            gm = fmaxf(gm, fabsf(gn[i]));
+            tn = fmaxf(tn, fabsf(sv[i]));
         }
         s.f = fn;
         s.iter++;
         if (s.iter >= max_iter) {
             s.done = 1;
             s.status = 1;
-        } else if (fabs(fold - fn) <= 1e-12 * fabs(fn) + 1e-300 || tn < 1e-10 || gm < 1e-12 * (fabs(fn) + 1e-300)) {
+        } else if (fabs(fold - fn) <= 1e-12 * fabs(fn) + 1e-300 || tn < 1e-10f ||
+                   (double)gm < 1e-12 * (fabs(fn) + 1e-300)) {
             s.done = 1;
         } else {
             sel_new_direction(s);
         }
     } else {
-        s.step *= 0.5;
+        s.step *= 0.5f;
         s.ls++;
         if (s.ls > kMaxHalvings) {
             s.done = 1;
         } else {
-            for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+            for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + (double)(s.step * s.dir[i]);
         }
     }
 }
 
-// One cluster per start.  Every CTA keeps its own copy of the optimiser
-// state and runs the same deterministic steps on the same sums (each CTA
-// receives every partial), so the copies stay identical and a round needs
-// only the two cluster barriers of the evaluation itself.
 __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __restrict__ starts,
                                                   const float2* __restrict__ twpool) {
     using C = float2;
@@ -1370,7 +1351,8 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            double fn = INFINITY, gt[3] = {0.0, 0.0, 0.0};
+            double fn = INFINITY;
+            float gt[3] = {0.f, 0.f, 0.f};
             if (valid) {
                 sel_assemble(p, Hs, Rs, res[0], res[1], aux[0], &fn, gt);
                 opt.evals++;
@@ -1393,49 +1375,88 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     }
 }
 
-// Both packed pairs of one bandwidth in the lag domain by one CTA: the half
-// box j_0 in [0, L_0], |j_1| <= L_1 (j_0 fastest, so that neighbouring
-// threads read neighbouring a_j), weights 2 / 1 / 0, four compensated sums;
-// thread 0 receives the four scaled totals in res4.
-__device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const FusedItem<float>& g,
-                                             const float* __restrict__ acorr, int A0, int A1, double* res4) {
+// The four grids of the search at lag x = (delta_0 j_0, delta_1 j_1): the
+// objective's kernel and its derivatives in H_00, H_01 (tied), H_11, from
+// the Gaussians of the covariances Sigma_s (LSCV: 2H, H; SCV: 2H + 2G,
+// H + 2G, 2G) and the order-2 Hermite terms He_(2,0) = z_0^2 - L_00,
+// He_(1,1) = z_0 z_1 - L_01, He_(0,2) = z_1^2 - L_11, z = L x (heat
+// equation: d phi_S / dS_ab = 1/2 d_a d_b phi_S).  For LSCV, Sigma_1 =
+// Sigma_0 / 2, so L_1 = 2 L_0, z_1 = 2 z_0 and phi_H's exponent is twice
+// phi_2H's: one exponential serves both.
+template <int METHOD>
+__device__ __forceinline__ void sel_grids(const FusedItem<float>& f, float x0, float x1, float* v) {
+    const float a00 = f.laml[0][0], a01 = f.laml[0][1], a11 = f.laml[0][3];
+    const float z0 = fmaf(a00, x0, a01 * x1), z1 = fmaf(a01, x0, a11 * x1);
+    const float q0 = fmaf(x0, z0, x1 * z1);
+    const float u = expf(-0.5f * q0);
+    const float e0 = f.nrm[0] * u;
+    const float h3 = fmaf(z0, z0, -a00), h4 = fmaf(z0, z1, -a01), h5 = fmaf(z1, z1, -a11);
+    if constexpr (METHOD == 0) {
+        const float e1 = f.nrm[1] * (u * u);
+        const float g3 = fmaf(4.f * z0, z0, -2.f * a00), g4 = fmaf(4.f * z0, z1, -2.f * a01),
+                    g5 = fmaf(4.f * z1, z1, -2.f * a11);
+        v[0] = fmaf(-2.f, e1, e0);
+        v[1] = fmaf(e0, h3, -e1 * g3);
+        v[2] = 2.f * fmaf(e0, h4, -e1 * g4);
+        v[3] = fmaf(e0, h5, -e1 * g5);
+    } else {
+        const float b00 = f.laml[1][0], b01 = f.laml[1][1], b11 = f.laml[1][3];
+        const float y0 = fmaf(b00, x0, b01 * x1), y1 = fmaf(b01, x0, b11 * x1);
+        const float e1 = f.nrm[1] * expf(-0.5f * fmaf(x0, y0, x1 * y1));
+        const float c00 = f.laml[2][0], c01 = f.laml[2][1], c11 = f.laml[2][3];
+        const float w0 = fmaf(c00, x0, c01 * x1), w1 = fmaf(c01, x0, c11 * x1);
+        const float e2 = f.nrm[2] * expf(-0.5f * fmaf(x0, w0, x1 * w1));
+        v[0] = fmaf(-2.f, e1, e0 + e2);
+        v[1] = fmaf(e0, h3, -e1 * fmaf(y0, y0, -b00));
+        v[2] = 2.f * fmaf(e0, h4, -e1 * fmaf(y0, y1, -b01));
+        v[3] = fmaf(e0, h5, -e1 * fmaf(y1, y1, -b11));
+    }
+}
+
+// One bandwidth of the search in the lag domain by one CTA: the half box
+// j_0 in [0, L_0], |j_1| <= L_1 (j_0 fastest, so that neighbouring threads
+// read neighbouring a_j), weights 2 / 1 / 0, four compensated sums; thread 0
+// receives the four scaled totals in res4.
+template <int METHOD>
+__device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const float* __restrict__ acorr, int A0,
+                                             int A1, double* res4) {
     const int L0 = f.off0, L1 = f.off1;
     const int n0 = L0 + 1;
     const int total = n0 * (2 * L1 + 1);
     const uint32_t mn0 = magic_of((uint32_t)max(n0, 2));
-    SumAcc<float> acc0, acc1;
+    const float d0 = (float)f.delta0, d1 = (float)f.delta1;
+    // a thread holds a few points: plain FP32 sums there and across its warp
+    // (the search compares values to FP32 accuracy; the reported value is
+    // recomputed), compensated sums across the warps
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int q = (n0 == 1) ? t : (int)qdiv((uint32_t)t, mn0);
         const int j0 = t - q * n0;
         const int j1 = q - L1;
         const int wt = (j0 > 0 || j1 > 0) ? 2 : (j1 == 0 ? 1 : 0);
         if (!wt) continue;
-        const float av = acorr[(long long)(j1 + A1) * (A0 + 1) + j0];
+        const float av = acorr[(j1 + A1) * (A0 + 1) + j0];
         float v[4];
-        kernel_quad_2d(f, g, j0, j1, v);
+        sel_grids<METHOD>(f, d0 * (float)j0, d1 * (float)j1, v);
         const float wa = (float)wt * av;
-        acc0.add(wa * v[0], wa * v[1]);
-        acc1.add(wa * v[2], wa * v[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s4[e] = fmaf(wa, v[e], s4[e]);
     }
-    // one block reduction of the four compensated sums
-    __shared__ DFloat red4[4][32];
-    DFloat v4[4] = {acc0.a, acc0.b, acc1.a, acc1.b};
+    __shared__ float red4[4][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const DFloat t{__shfl_down_sync(0xffffffffu, v4[e].h, o), __shfl_down_sync(0xffffffffu, v4[e].l, o)};
-            v4[e] = df_add(v4[e], t);
-        }
+        for (int e = 0; e < 4; ++e) s4[e] += __shfl_down_sync(0xffffffffu, s4[e], o);
     const int wi = threadIdx.x >> 5, li = threadIdx.x & 31;
     if (li == 0)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) red4[e][wi] = v4[e];
+        for (int e = 0; e < 4; ++e) red4[e][wi] = s4[e];
     __syncthreads();
     if (wi == 0) {
         const int nw = (blockDim.x + 31) >> 5;
+        DFloat v4[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v4[e] = (li < nw) ? red4[e][li] : DFloat{0.f, 0.f};
+        for (int e = 0; e < 4; ++e) v4[e] = DFloat{(li < nw) ? red4[e][li] : 0.f, 0.f};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -1451,13 +1472,23 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const Fu
 
 // One CTA per start runs the whole quasi-Newton search with lag-domain
 // evaluations against the count autocorrelation (FP32 copy, L2-resident).
-__global__ void __launch_bounds__(512) k_select2d_lag(SelectParams p, SelStart* __restrict__ starts) {
+__global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelStart* __restrict__ starts, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double res[2][2];
     __shared__ FusedItem<float> items[2];
     __shared__ SelOpt opt;
     __shared__ int ctl[2];
     __shared__ double Hs[4], Rs[3], aux[3];
     const int start = blockIdx.x;
+    // the autocorrelation box is fixed for the whole search: staged once in
+    // shared memory when it fits (stage != 0)
+    const float* acorr = p.acorr;
+    if (stage) {
+        float* sa = reinterpret_cast<float*>(smem_raw);
+        const int nbox = (p.A0 + 1) * (2 * p.A1 + 1);
+        for (int t = threadIdx.x; t < nbox; t += blockDim.x) sa[t] = p.acorr[t];
+        acorr = sa;
+    }
     if (threadIdx.x == 0) {
         const SelStart& st = starts[start];
         for (int i = 0; i < 3; ++i) opt.th_try[i] = st.th[i];
@@ -1485,11 +1516,15 @@ __global__ void __launch_bounds__(512) k_select2d_lag(SelectParams p, SelStart* 
         const int valid = ctl[0], done = ctl[1];
         if (done) break;
         if (valid) {
-            sel_eval_lag(items[0], items[1], p.acorr, p.A0, p.A1, &res[0][0]);
+            if (p.method == 0)
+                sel_eval_lag<0>(items[0], acorr, p.A0, p.A1, &res[0][0]);
+            else
+                sel_eval_lag<1>(items[0], acorr, p.A0, p.A1, &res[0][0]);
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            double fn = INFINITY, gt[3] = {0.0, 0.0, 0.0};
+            double fn = INFINITY;
+            float gt[3] = {0.f, 0.f, 0.f};
             if (valid) {
                 sel_assemble(p, Hs, Rs, res[0], res[1], aux[0], &fn, gt);
                 opt.evals++;
@@ -1513,7 +1548,17 @@ __global__ void __launch_bounds__(512) k_select2d_lag(SelectParams p, SelStart* 
 }
 
 cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st) {
-    k_select2d_lag<<<nstarts, 512, 0, st>>>(prm, starts);
+    const size_t box = sizeof(float) * (size_t)(prm.A0 + 1) * (size_t)(2 * prm.A1 + 1);
+    const size_t limit = 200 * 1024;
+    const int stage = box <= limit ? 1 : 0;
+    const size_t sm = stage ? box : 0;
+    static size_t set_bytes = 48 * 1024;
+    if (sm > set_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_select2d_lag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+        if (e != cudaSuccess) return e;
+        set_bytes = limit;
+    }
+    k_select2d_lag<<<nstarts, 1024, sm, st>>>(prm, starts, stage);
     return cudaGetLastError();
 }
 

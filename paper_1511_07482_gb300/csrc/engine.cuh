@@ -167,6 +167,7 @@ struct SelectParams {
     int chunk;              // lines (and columns) per shared-memory batch
     int gat_elems, spc_elems, cap, pmax;   // shared-memory layout (complex / real elements)
     double n, tau;
+    double inv_n, inv_n2;   // 1/n, 1/n^2
     double delta0, delta1;
     double G[4];            // SCV pilot, row-major
     const int* ptab0;       // P_0 for support L_0 (index L_0 <= Lcap)
