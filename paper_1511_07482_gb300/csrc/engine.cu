@@ -1548,15 +1548,18 @@ __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelStart*
 }
 
 cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st) {
+    // dynamic shared memory for the staged box: up to `limit` on top of the
+    // kernel's static shared memory (the attribute is set once, before any
+    // launch, so that no box size falls between the default limit and it)
     const size_t box = sizeof(float) * (size_t)(prm.A0 + 1) * (size_t)(2 * prm.A1 + 1);
     const size_t limit = 200 * 1024;
     const int stage = box <= limit ? 1 : 0;
     const size_t sm = stage ? box : 0;
-    static size_t set_bytes = 48 * 1024;
-    if (sm > set_bytes) {
+    static bool set = false;
+    if (!set) {
         cudaError_t e = cudaFuncSetAttribute(k_select2d_lag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
         if (e != cudaSuccess) return e;
-        set_bytes = limit;
+        set = true;
     }
     k_select2d_lag<<<nstarts, 1024, sm, st>>>(prm, starts, stage);
     return cudaGetLastError();
