@@ -218,6 +218,24 @@ def run_ours(args):
             ds.close()
             return 20 * len(w.H), None
         workload_desc = w.name + ": bin + 20 batches of LSCV and gradient at 16 candidate H"
+    elif args.workload == "qr_e8":
+        # the V-statistics experiment's shape: a bivariate N(0, I) sample,
+        # M = 100 per axis, Q_r for total derivative orders 0, 2, 4, 6, 8
+        rng = np.random.default_rng(rank_seed(8, rank))
+        Xq = rng.standard_normal((10000, 2))
+        Sq = synthetic.normal_scale(Xq)
+        loq, hiq = synthetic.grid_range(Xq, Sq)
+        w = synthetic.Workload("normal-2d-n10000-M100", Xq, loq, hiq, [100, 100], [Sq], G=Sq)
+        X_dev = torch.from_numpy(Xq).to(dev)
+        X_pin = torch.from_numpy(Xq).pin_memory()
+
+        def step(X):
+            ds = ctx.bin(X, loq, hiq, [100, 100])
+            for r in (0, 2, 4, 6, 8):
+                ds.qr(Sq, r)
+            ds.close()
+            return 5, None
+        workload_desc = "normal-2d-n10000-M100: bin + Q_r (Eq. 32) for total derivative orders 0, 2, 4, 6, 8"
     else:  # plugin4d
         w = synthetic.mixture_4d(seed=rank_seed(5, rank), n_candidates=16)
         X_dev = torch.from_numpy(w.X).to(dev)
@@ -413,7 +431,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-starts", type=int, default=16)
-    ap.add_argument("--workload", default="select2d", choices=["select2d", "psi4_3d", "uneven512", "plugin4d", "lscv_batch16"],
+    ap.add_argument("--workload", default="select2d", choices=["select2d", "psi4_3d", "uneven512", "plugin4d", "lscv_batch16", "qr_e8"],
                     help="select2d (default): the n=1e5 bivariate selection workload; the others time the "
                          "batched 3-D psi_4, 512-dataset LSCV and 4-D plug-in configurations")
     ap.add_argument("--max-iter", type=int, default=60)

@@ -168,6 +168,22 @@ int kdefft_pi(kdefft_ds ds, const double* H, int nH, const double* G,
  * the FFT.  val: nH FP64, host or device. */
 int kdefft_eta02(kdefft_ds ds, const double* H, int nH, const double* G, double* val);
 
+/* V-statistic Q_r(Sigma) = n^-2 sum_ij eta(X_i - X_j; Sigma) (Eq. 32) with
+ * eta = Laplacian^{r/2} phi_Sigma = (vec^T I)^{(x) r/2} D^{(x) r} phi_Sigma
+ * (Eq. 31's eta_{r/2}): r is the total derivative order, even, at most the
+ * order limit for d (8 for d <= 3, 6 for d = 4).  One value per Sigma (nS
+ * row-major d x d SPD matrices); support from lambda_max(Sigma) (Eq. 26).
+ * out: nS FP64, host or device. */
+int kdefft_qr(kdefft_ds ds, const double* Sigma, int nS, int r, double* out);
+
+/* LSCV_r(H) for estimating the r-th density derivative (Eq. 36; with the
+ * dataset's exact_loo option, Eq. 35), with eta_{r,0}(.; H) = Laplacian^r
+ * phi_H, kernels of order 2r (2r at most the order limit for d).  The
+ * n ~ n-1 form adds 2 n^-1 eta_r(0; H) (reading of Eq. 36's last term,
+ * which is 2 n^-1 K_H(0) at r = 0).  Values only.  val: nH FP64, host or
+ * device. */
+int kdefft_lscv_r(kdefft_ds ds, const double* H, int nH, int r, double* val);
+
 /* Minimise `method` (KDEFFT_LSCV or _SCV or _PI) over H in F, the SPD
  * matrices (Eq. 9), with a quasi-Newton method on the Cholesky factor of H
  * (log diagonal) using the exact gradients.  H0: start (NULL: the normal-scale

@@ -31,7 +31,7 @@ EXPORTS = [
     "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H", "kdefft_select_H_nm",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
-    "kdefft_runtime_stats", "kdefft_autocorr",
+    "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
         "kdefft_set_engine": (I, [P, I]),
         "kdefft_set_autotune": (I, [P, I]),
         "kdefft_autocorr": (I, [P, P, P]),
+        "kdefft_qr": (I, [P, P, I, I, P]),
+        "kdefft_lscv_r": (I, [P, P, I, I, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "kdefft_strerror": (C.c_char_p, [I]),
@@ -351,6 +353,22 @@ class Dataset:
         shape = tuple(2 * int(a) + 1 for a in A_a[1:][::-1]) + (int(A_a[0]) + 1,)
         out = np.zeros(shape)
         _check(load().kdefft_autocorr(self.h, A_a.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def qr(self, Sigma, r):
+        """Q_r(Sigma) (Eq. 32), eta = Laplacian^{r/2} phi_Sigma; r = total
+        derivative order (even).  One value per Sigma."""
+        S, nS = self._Hs(Sigma)
+        out = np.zeros(nS)
+        _check(load().kdefft_qr(self.h, S.ctypes.data_as(C.c_void_p), nS, int(r), out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def lscv_r(self, H, r):
+        """LSCV_r(H) (Eq. 36, or Eq. 35 with exact_loo) for the r-th density
+        derivative; values."""
+        H, nH = self._Hs(H)
+        out = np.zeros(nH)
+        _check(load().kdefft_lscv_r(self.h, H.ctypes.data_as(C.c_void_p), nH, int(r), out.ctypes.data_as(C.c_void_p)))
         return out
 
     def eta02(self, H, G):

@@ -832,6 +832,123 @@ static int add_psi(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first, st
 }
 
 // ---- eta_{0,2}(x; B, Sigma) = (vec^T B)^{(x)2} D^{(x)4} phi_Sigma (Eq. 30) ----
+// ---- eta_m (Eq. 31), Q_r (Eq. 32), LSCV_r (Eqs. 35-36) --------------------
+// eta_m(x; Sigma) = (vec^T I)^{(x)m} D^{(x)2m} phi_Sigma = Laplacian^m phi_Sigma
+//                 = sum_{|beta| = m} m! / beta! d^{2 beta} phi_Sigma,
+// appended as terms of covariance `sig` scaled by `scale`.
+static void laplacian_power_terms(int d, int m, int sig, double scale, std::vector<Term>& out) {
+    std::vector<MultiIndex> all;
+    enumerate(d, m, all);
+    double mf = 1.0;
+    for (int i = 2; i <= m; ++i) mf *= i;
+    for (const MultiIndex& b : all) {
+        int o = 0;
+        double den = 1.0;
+        for (int k = 0; k < d; ++k) {
+            o += b.a[k];
+            for (int i = 2; i <= b.a[k]; ++i) den *= i;
+        }
+        if (o != m) continue;
+        Term t{sig, {0, 0, 0, 0}, scale * mf / den};
+        for (int k = 0; k < d; ++k) t.alpha[k] = 2 * b.a[k];
+        out.push_back(t);
+    }
+}
+
+// d^alpha phi_Sigma at x = 0: (-1)^{|alpha|} He_alpha(0; Lambda) phi_Sigma(0),
+// He_0 = 1, He_{beta + e_i}(0) = -sum_j beta_j Lambda_ij He_{beta - e_j}(0)
+// (the Hermite recurrence of the kernels at z = 0), FP64.
+static double dphi_at0(const Mat& Sigma, const int* alpha) {
+    const int d = Sigma.d;
+    Mat inv;
+    double det;
+    spd_inv_det(Sigma, inv, det);
+    std::map<std::vector<int>, double> memo;
+    std::function<double(const std::vector<int>&)> he = [&](const std::vector<int>& a) -> double {
+        int tot = 0;
+        for (int v : a) tot += v;
+        if (tot == 0) return 1.0;
+        auto it = memo.find(a);
+        if (it != memo.end()) return it->second;
+        int i = 0;
+        while (a[i] == 0) ++i;
+        std::vector<int> b = a;
+        b[i]--;
+        double v = 0.0;
+        for (int j = 0; j < d; ++j)
+            if (b[j] > 0) {
+                std::vector<int> c = b;
+                c[j]--;
+                v -= b[j] * inv(i, j) * he(c);
+            }
+        memo[a] = v;
+        return v;
+    };
+    std::vector<int> a(alpha, alpha + d);
+    int tot = 0;
+    for (int v : a) tot += v;
+    const double phi0 = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
+    return ((tot & 1) ? -1.0 : 1.0) * he(a) * phi0;
+}
+
+// one grid: eta_m(.; Sigma) with support from lambda_max(Sigma)
+static int add_eta_m(ReqSet& rs, kdefft_ds ds, const Mat& Sg, int m, int& first) {
+    KCHK(spd_or_fail(Sg, "Sigma"));
+    KSpec sp;
+    sp.nsig = 1;
+    sp.sig[0] = Sg;
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    KCHK(plan_for(ds, Sg, L, P));
+    first = (int)rs.grids.size();
+    GridReq g;
+    g.ds = ds;
+    g.spec = si;
+    std::memcpy(g.L, L, sizeof(L));
+    std::memcpy(g.P, P, sizeof(P));
+    laplacian_power_terms(ds->d, m, 0, 1.0, g.terms);
+    rs.grids.push_back(std::move(g));
+    return KDEFFT_OK;
+}
+
+// LSCV_r grids: Eq. 36 one grid eta_r(.; 2H) - 2 eta_r(.; H); Eq. 35 (exact
+// leave-one-out) the two sums separately
+static int add_lscv_r(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first) {
+    KCHK(spd_or_fail(H, "H"));
+    KSpec sp;
+    sp.nsig = 2;
+    sp.sig[0] = scaled(2.0, H);
+    sp.sig[1] = H;
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    const Mat& basis = (ds->opts.L_basis == KDEFFT_L_WIDEST) ? sp.sig[0] : H;
+    KCHK(plan_for(ds, basis, L, P));
+    first = (int)rs.grids.size();
+    auto push = [&](std::vector<Term> t) {
+        GridReq g;
+        g.ds = ds;
+        g.spec = si;
+        std::memcpy(g.L, L, sizeof(L));
+        std::memcpy(g.P, P, sizeof(P));
+        g.terms = std::move(t);
+        rs.grids.push_back(std::move(g));
+    };
+    std::vector<Term> a, b;
+    if (!ds->opts.exact_loo) {
+        laplacian_power_terms(ds->d, r, 0, 1.0, a);
+        laplacian_power_terms(ds->d, r, 1, -2.0, a);
+        push(a);
+    } else {
+        laplacian_power_terms(ds->d, r, 0, 1.0, a);
+        laplacian_power_terms(ds->d, r, 1, 1.0, b);
+        push(a);
+        push(b);
+    }
+    return KDEFFT_OK;
+}
+
 static int add_eta02(ReqSet& rs, kdefft_ds ds, const Mat& B, const Mat& Sg, int& first) {
     const int d = ds->d;
     KSpec sp;
@@ -2560,6 +2677,56 @@ int kdefft_eta02(kdefft_ds ds, const double* H, int nH, const double* G, double*
     KCHK(run(ds->ctx, rs));
     std::vector<double> v(nH);
     for (int h = 0; h < nH; ++h) v[h] = rs.grids[first[h]].value;
+    return write_out(ds->ctx, val, v.data(), v.size());
+}
+
+int kdefft_qr(kdefft_ds ds, const double* Sigma, int nS, int r, double* out) {
+    KCHK(check_common(ds, Sigma, nS));
+    if (!out) return fail(KDEFFT_ERR_ARG, "NULL output");
+    const int d = ds->d;
+    if (r < 0 || (r & 1) || r > kRmax[d]) return fail(KDEFFT_ERR_ARG, "r must be even and within the order limit");
+    ReqSet rs;
+    std::vector<int> first(nS);
+    for (int i = 0; i < nS; ++i) {
+        Mat Sg;
+        KCHK(sym_check(Sigma + (size_t)i * d * d, d, Sg, "Sigma"));
+        KCHK(add_eta_m(rs, ds, Sg, r / 2, first[i]));
+    }
+    KCHK(run(ds->ctx, rs));
+    std::vector<double> v(nS);
+    for (int i = 0; i < nS; ++i) v[i] = rs.grids[first[i]].value;
+    return write_out(ds->ctx, out, v.data(), v.size());
+}
+
+int kdefft_lscv_r(kdefft_ds ds, const double* H, int nH, int r, double* val) {
+    KCHK(check_common(ds, H, nH));
+    if (!val) return fail(KDEFFT_ERR_ARG, "NULL output");
+    const int d = ds->d;
+    if (r < 0 || 2 * r > kRmax[d]) return fail(KDEFFT_ERR_ARG, "2r must be within the order limit");
+    ReqSet rs;
+    std::vector<int> first(nH);
+    std::vector<Mat> Hs(nH);
+    for (int h = 0; h < nH; ++h) {
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
+        KCHK(add_lscv_r(rs, ds, Hs[h], r, first[h]));
+    }
+    KCHK(run(ds->ctx, rs));
+    const double n = (double)ds->n;
+    const double sgn = (r & 1) ? -1.0 : 1.0;
+    std::vector<double> v(nH);
+    for (int h = 0; h < nH; ++h) {
+        // eta_r(0; H) = sum_beta r!/beta! d^{2 beta} phi_H(0)
+        std::vector<Term> t0;
+        laplacian_power_terms(d, r, 0, 1.0, t0);
+        double e0 = 0.0;
+        for (const Term& t : t0) e0 += t.w * dphi_at0(Hs[h], t.alpha);
+        if (!ds->opts.exact_loo) {
+            v[h] = sgn * (rs.grids[first[h]].value + 2.0 * e0 / n);   // Eq. 36
+        } else {
+            const double A = rs.grids[first[h]].value, B = rs.grids[first[h] + 1].value;
+            v[h] = sgn * (A - 2.0 / (n * (n - 1.0)) * (n * n * B - n * e0));   // Eq. 35
+        }
+    }
     return write_out(ds->ctx, val, v.data(), v.size());
 }
 
