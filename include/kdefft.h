@@ -176,6 +176,17 @@ int kdefft_eta02(kdefft_ds ds, const double* H, int nH, const double* G, double*
  * out: nS FP64, host or device. */
 int kdefft_qr(kdefft_ds ds, const double* Sigma, int nS, int r, double* out);
 
+/* V-statistic of Eq. 29, n^-2 sum_ij eta_{r,s}(X_i - X_j; A, B, Sigma), with
+ * eta_{r,s} = {(vec^T A)^{(x)r} (x) (vec^T B)^{(x)s}} D^{(x)2r+2s} phi_Sigma
+ * (Eq. 30), the building block of the plug-in and SCV selectors for density
+ * derivative estimation.  A, B: symmetric d x d (NULL: the identity);
+ * Sigma: nS SPD d x d; 2(r + s) at most the order limit for d and at most
+ * 40 distinct partials.  eta_{0,2} with B = H, Sigma = G is kdefft_eta02;
+ * A = I, s = 0 is the eta of kdefft_qr with order 2r.  out: nS FP64, host or
+ * device. */
+int kdefft_eta_rs(kdefft_ds ds, const double* A, const double* B, const double* Sigma, int nS, int r, int s,
+                  double* out);
+
 /* LSCV_r(H) for estimating the r-th density derivative (Eq. 36; with the
  * dataset's exact_loo option, Eq. 35), with eta_{r,0}(.; H) = Laplacian^r
  * phi_H, kernels of order 2r (2r at most the order limit for d).  The

@@ -177,6 +177,33 @@ def eta02_terms(B, Sigma):
     return [(wt, np.asarray(Sigma, dtype=np.float64), al) for al, wt in w.items() if wt != 0.0]
 
 
+def eta_rs_terms(A, B, Sigma, r, s):
+    """eta_{r,s}(x; A, B, Sigma) = {(vec^T A)^{(x)r} (x) (vec^T B)^{(x)s}}
+    D^{(x)2r+2s} phi_Sigma(x) (Eq. 30): the Kronecker vector's entry at the
+    index tuple (i_1, .., i_{2r+2s}) is prod_k A_{i_{2k-1} i_{2k}} (first r
+    pairs) prod_k B_{..} (last s pairs), and the derivative entry is
+    d_{i_1} .. d_{i_{2r+2s}} phi_Sigma; collected by multi-index."""
+    import itertools
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    d = A.shape[0]
+    w: dict = {}
+    for idx in itertools.product(range(d), repeat=2 * (r + s)):
+        c = 1.0
+        for k in range(r):
+            c *= A[idx[2 * k], idx[2 * k + 1]]
+        for k in range(s):
+            c *= B[idx[2 * r + 2 * k], idx[2 * r + 2 * k + 1]]
+        if c == 0.0:
+            continue
+        al = [0] * d
+        for i in idx:
+            al[i] += 1
+        al = tuple(al)
+        w[al] = w.get(al, 0.0) + c
+    return [(wt, np.asarray(Sigma, dtype=np.float64), al) for al, wt in w.items() if wt != 0.0]
+
+
 def eta_r_terms(Sigma, r):
     """eta_r(x; Sigma) = (vec^T I)^{(x)r} D^{(x)2r} phi_Sigma = Laplacian^r
     phi_Sigma (Eq. 31) = sum_{|beta| = r} r!/beta! d^{2 beta} phi_Sigma."""

@@ -31,7 +31,7 @@ EXPORTS = [
     "kdefft_lscv", "kdefft_scv", "kdefft_pi", "kdefft_eta02", "kdefft_select_H", "kdefft_select_H_nm",
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
-    "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r",
+    "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "kdefft_autocorr": (I, [P, P, P]),
         "kdefft_qr": (I, [P, P, I, I, P]),
         "kdefft_lscv_r": (I, [P, P, I, I, P]),
+        "kdefft_eta_rs": (I, [P, P, P, P, I, I, I, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "kdefft_strerror": (C.c_char_p, [I]),
@@ -361,6 +362,17 @@ class Dataset:
         S, nS = self._Hs(Sigma)
         out = np.zeros(nS)
         _check(load().kdefft_qr(self.h, S.ctypes.data_as(C.c_void_p), nS, int(r), out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def eta_rs(self, Sigma, r, s, A=None, B=None):
+        """n^-2 sum_ij eta_{r,s}(X_i - X_j; A, B, Sigma) (Eqs. 29-30) for each
+        Sigma; A, B default to the identity."""
+        S, nS = self._Hs(Sigma)
+        Aa, pA = _host_f64(A) if A is not None else (None, None)
+        Ba, pB = _host_f64(B) if B is not None else (None, None)
+        out = np.zeros(nS)
+        _check(load().kdefft_eta_rs(self.h, pA, pB, S.ctypes.data_as(C.c_void_p), nS, int(r), int(s),
+                                    out.ctypes.data_as(C.c_void_p)))
         return out
 
     def lscv_r(self, H, r):

@@ -949,6 +949,56 @@ static int add_lscv_r(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first)
     return KDEFFT_OK;
 }
 
+// eta_{r,s}(x; A, B, Sigma) = {(vec^T A)^{(x)r} (x) (vec^T B)^{(x)s}} D^{(x)2r+2s} phi_Sigma
+// (Eq. 30): the sum over index tuples of prod A_{pair} prod B_{pair} times the
+// derivative along the tuple, collected by multi-index; support from
+// lambda_max(Sigma)
+static int add_eta_rs(ReqSet& rs, kdefft_ds ds, const Mat& A, const Mat& B, const Mat& Sg, int r, int s, int& first) {
+    const int d = ds->d;
+    KCHK(spd_or_fail(Sg, "Sigma"));
+    KSpec sp;
+    sp.nsig = 1;
+    sp.sig[0] = Sg;
+    const int si = (int)rs.specs.size();
+    rs.specs.push_back(sp);
+    int L[4], P[4];
+    KCHK(plan_for(ds, Sg, L, P));
+    first = (int)rs.grids.size();
+    std::map<std::vector<int>, double> w;
+    std::vector<int> al(MAXD, 0);
+    std::function<void(int, double)> pairs = [&](int k, double c) {
+        if (c == 0.0) return;
+        if (k == r + s) {
+            w[al] += c;
+            return;
+        }
+        const Mat& M = (k < r) ? A : B;
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                al[a]++;
+                al[b]++;
+                pairs(k + 1, c * M(a, b));
+                al[a]--;
+                al[b]--;
+            }
+    };
+    pairs(0, 1.0);
+    GridReq g;
+    g.ds = ds;
+    g.spec = si;
+    std::memcpy(g.L, L, sizeof(L));
+    std::memcpy(g.P, P, sizeof(P));
+    for (auto& kv : w) {
+        if (kv.second == 0.0) continue;
+        Term t{0, {0, 0, 0, 0}, kv.second};
+        for (int k = 0; k < MAXD; ++k) t.alpha[k] = kv.first[k];
+        g.terms.push_back(t);
+    }
+    if ((int)g.terms.size() > MAXTERM) return fail(KDEFFT_ERR_UNSUPPORTED, "too many kernel terms");
+    rs.grids.push_back(std::move(g));
+    return KDEFFT_OK;
+}
+
 static int add_eta02(ReqSet& rs, kdefft_ds ds, const Mat& B, const Mat& Sg, int& first) {
     const int d = ds->d;
     KSpec sp;
@@ -2691,6 +2741,30 @@ int kdefft_qr(kdefft_ds ds, const double* Sigma, int nS, int r, double* out) {
         Mat Sg;
         KCHK(sym_check(Sigma + (size_t)i * d * d, d, Sg, "Sigma"));
         KCHK(add_eta_m(rs, ds, Sg, r / 2, first[i]));
+    }
+    KCHK(run(ds->ctx, rs));
+    std::vector<double> v(nS);
+    for (int i = 0; i < nS; ++i) v[i] = rs.grids[first[i]].value;
+    return write_out(ds->ctx, out, v.data(), v.size());
+}
+
+int kdefft_eta_rs(kdefft_ds ds, const double* A, const double* B, const double* Sigma, int nS, int r, int s,
+                  double* out) {
+    KCHK(check_common(ds, Sigma, nS));
+    if (!out) return fail(KDEFFT_ERR_ARG, "NULL output");
+    const int d = ds->d;
+    if (r < 0 || s < 0 || 2 * (r + s) > kRmax[d]) return fail(KDEFFT_ERR_ARG, "2(r + s) must be within the order limit");
+    Mat Am, Bm;
+    Am.d = Bm.d = d;
+    for (int i = 0; i < d; ++i) Am(i, i) = Bm(i, i) = 1.0;
+    if (A) KCHK(sym_check(A, d, Am, "A"));
+    if (B) KCHK(sym_check(B, d, Bm, "B"));
+    ReqSet rs;
+    std::vector<int> first(nS);
+    for (int i = 0; i < nS; ++i) {
+        Mat Sg;
+        KCHK(sym_check(Sigma + (size_t)i * d * d, d, Sg, "Sigma"));
+        KCHK(add_eta_rs(rs, ds, Am, Bm, Sg, r, s, first[i]));
     }
     KCHK(run(ds->ctx, rs));
     std::vector<double> v(nS);

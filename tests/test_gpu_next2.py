@@ -118,3 +118,23 @@ def test_lscv_r_exact_leave_one_out():
         ds.lscv_r(Hns, 5)          # order 10 is beyond the tables
     ds.close()
     c0.close()
+
+
+@pytest.mark.parametrize("d,M,r,s", [(2, [56, 50], 1, 1), (2, [56, 50], 0, 3), (2, [56, 50], 2, 2), (3, [18, 16, 14], 1, 2)])
+def test_eta_rs_matches_oracle(ctx, d, M, r, s):
+    """Eqs. 29-30 for general (r, s) with full A, B; r = 0, s = 2 agrees with
+    the plug-in functional's eta_{0,2} entry point."""
+    w = synthetic.small_case(n=3000, d=d, M=M, seed=95 + d, n_candidates=2)
+    ds = ctx.bin(w.X, w.lo, w.hi, M)
+    A, B, Sg = w.H[0], w.H[1], w.extra["H_NS"]
+    got = ds.eta_rs(Sg, r, s, A=A, B=B)[0]
+    c = binning.bin_linear(w.X, w.lo, w.hi, M)
+    delta = rules.bin_width(w.lo, w.hi, M)
+    L = rules.support_L(rules.lambda_max(Sg), delta, M)
+    terms = S.eta_rs_terms(A, B, Sg, r, s)
+    ref = F.binned_direct(c, w.n, terms, delta, L)
+    assert _err(got, ref, _abs_functional(c, w.n, terms, delta, L)) <= 1e-5, (got, ref)
+    if (r, s) == (0, 3):
+        e02 = ds.eta_rs(Sg, 0, 2, B=B)[0]
+        assert e02 == pytest.approx(ds.eta02(B, Sg)[0], rel=1e-6)
+    ds.close()

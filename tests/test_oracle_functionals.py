@@ -445,3 +445,37 @@ def test_eta_r_is_iterated_laplacian():
         want = float(f.subs({x0: pt[0, 0], x1: pt[0, 1]}))
         got = float(gauss.kernel_eval(pt, S.eta_r_terms(Sg, r))[0])
         assert got == pytest.approx(want, rel=1e-10)
+
+
+def test_eta_rs_reduces_to_eta02_and_eta_r():
+    """Eq. 30 in general: r = 0, s = 2 gives eta_{0,2} (Eq. 30's special
+    case used by the plug-in functional); A = I, s = 0 gives the iterated
+    Laplacian eta_r (Eq. 31); swapping (A, r) with (B, s) permutes the
+    Kronecker factors of a symmetric derivative tensor and changes
+    nothing; and at a point the weights reproduce the brute-force
+    contraction of the full Kronecker vectors."""
+    rng = np.random.default_rng(12)
+    for d in (2, 3):
+        A = _spd(rng, d, 0.5)
+        B = _spd(rng, d, 0.7)
+        Sg = _spd(rng, d, 0.4)
+        as_dict = lambda terms: {a: w for w, _, a in terms}
+        e02 = as_dict(S.eta02_terms(B, Sg))
+        g02 = as_dict(S.eta_rs_terms(A, B, Sg, 0, 2))
+        assert e02.keys() == g02.keys() and all(abs(e02[k] - g02[k]) <= 1e-12 * abs(e02[k]) for k in e02)
+        for m in (1, 2):
+            er = as_dict(S.eta_r_terms(Sg, m))
+            gr = as_dict(S.eta_rs_terms(np.eye(d), B, Sg, m, 0))
+            assert er.keys() == gr.keys() and all(abs(er[k] - gr[k]) <= 1e-12 * abs(er[k]) for k in er)
+        x = rng.standard_normal(d) * 0.3
+        v1 = gauss.kernel_eval(x, S.eta_rs_terms(A, B, Sg, 1, 1))
+        v2 = gauss.kernel_eval(x, S.eta_rs_terms(B, A, Sg, 1, 1))
+        assert v1 == pytest.approx(v2, rel=1e-12)
+        # brute force at x: sum over all index tuples of A_ab B_ce d_a d_b d_c d_e phi
+        want = 0.0
+        for a, b, c, e in itertools.product(range(d), repeat=4):
+            al = [0] * d
+            for i in (a, b, c, e):
+                al[i] += 1
+            want += A[a, b] * B[c, e] * float(gauss.gauss_deriv(x, Sg, tuple(al)))
+        assert v1 == pytest.approx(want, rel=1e-10)
