@@ -187,6 +187,26 @@ int kdefft_qr(kdefft_ds ds, const double* Sigma, int nS, int r, double* out);
 int kdefft_eta_rs(kdefft_ds ds, const double* A, const double* B, const double* Sigma, int nS, int r, int s,
                   double* out);
 
+/* The binned kernel density estimate (Eq. 1 with the sample replaced by its
+ * bin counts) at every grid node: f_hat(g) = n^-1 sum_{|l_k| <= L_k}
+ * c_{g-l} K_H(delta (.) l), the convolution that the FFT steps of Sec. 4
+ * evaluate, truncated at the support L of Eq. 26 (from lambda_max(H)).
+ * out: prod M_k FP64, row-major over the grid (last axis fastest), host or
+ * device.  FP32 linear-binned datasets (else KDEFFT_ERR_UNSUPPORTED). */
+int kdefft_kde_grid(kdefft_ds ds, const double* H, double* out);
+
+/* Integrated squared error (Eq. 37) of the binned estimate against a normal
+ * mixture f = sum_m w_m phi_{S_m}(. - mu_m), in closed form:
+ *   int f_hat^2 = n^-2 sum_ij phi_2H(g_i - g_j) c_i c_j (the binned double
+ *                 sum, as every functional here),
+ *   int f_hat f = n^-1 sum_g c_g sum_m w_m phi_{H + S_m}(x_g - mu_m),
+ *   int f^2     = sum_lm w_l w_m phi_{S_l + S_m}(mu_l - mu_m),
+ * ISE = the first - 2 the second + the third.  K in 1..64 components; w: K;
+ * mu: K x d; S: K x d x d SPD.  out: nH FP64, host or device.  FP32
+ * linear-binned datasets. */
+int kdefft_ise_mixture(kdefft_ds ds, const double* H, int nH, int K, const double* w, const double* mu,
+                       const double* S, double* out);
+
 /* LSCV_r(H) for estimating the r-th density derivative (Eq. 36; with the
  * dataset's exact_loo option, Eq. 35), with eta_{r,0}(.; H) = Laplacian^r
  * phi_H, kernels of order 2r (2r at most the order limit for d).  The

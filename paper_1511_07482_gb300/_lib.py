@@ -32,6 +32,7 @@ EXPORTS = [
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
+    "kdefft_kde_grid", "kdefft_ise_mixture",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH):
         "kdefft_qr": (I, [P, P, I, I, P]),
         "kdefft_lscv_r": (I, [P, P, I, I, P]),
         "kdefft_eta_rs": (I, [P, P, P, P, I, I, I, P]),
+        "kdefft_kde_grid": (I, [P, P, P]),
+        "kdefft_ise_mixture": (I, [P, P, I, I, P, P, P, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "kdefft_strerror": (C.c_char_p, [I]),
@@ -373,6 +376,26 @@ class Dataset:
         out = np.zeros(nS)
         _check(load().kdefft_eta_rs(self.h, pA, pB, S.ctypes.data_as(C.c_void_p), nS, int(r), int(s),
                                     out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def kde_grid(self, H):
+        """The binned kernel density estimate at every grid node (shape M)."""
+        Ha, pH = _host_f64(H)
+        out = np.zeros(self.M)
+        _check(load().kdefft_kde_grid(self.h, pH, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def ise_mixture(self, H, weights, means, covs):
+        """ISE of the binned estimate at each H against the normal mixture
+        sum_m w_m phi_{S_m}(. - mu_m) (closed form)."""
+        H, nH = self._Hs(H)
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).ravel())
+        mu = np.ascontiguousarray(np.asarray(means, dtype=np.float64).reshape(len(w), self.d))
+        S = np.ascontiguousarray(np.asarray(covs, dtype=np.float64).reshape(len(w), self.d, self.d))
+        out = np.zeros(nH)
+        _check(load().kdefft_ise_mixture(self.h, H.ctypes.data_as(C.c_void_p), nH, len(w),
+                                         w.ctypes.data_as(C.c_void_p), mu.ctypes.data_as(C.c_void_p),
+                                         S.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
         return out
 
     def lscv_r(self, H, r):

@@ -428,6 +428,7 @@ struct kdefft_ctx_s {
     DevBuf sel_buf;           // device tables and start states of the device-resident selection
     DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
     DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
+    DevBuf kdebuf;            // stencil table / outputs of the grid estimate and the mixture term
     std::map<std::string, KStat> kstat;
     struct Pending {
         std::string name;
@@ -2322,6 +2323,7 @@ int kdefft_destroy(kdefft_ctx c) {
     c->binfix.release();
     c->acbuf[0].release();
     c->acbuf[1].release();
+    c->kdebuf.release();
     c->h_items.release();
     c->h_out.release();
     for (auto& p : c->pending) {
@@ -2770,6 +2772,152 @@ int kdefft_eta_rs(kdefft_ds ds, const double* A, const double* B, const double* 
     std::vector<double> v(nS);
     for (int i = 0; i < nS; ++i) v[i] = rs.grids[first[i]].value;
     return write_out(ds->ctx, out, v.data(), v.size());
+}
+
+static KdeDesc kde_desc(kdefft_ds ds, const int* L) {
+    KdeDesc g;
+    std::memset(&g, 0, sizeof(g));
+    g.d = ds->d;
+    g.ncells = ds->ncells;
+    g.nstencil = 1;
+    for (int k = 0; k < ds->d; ++k) {
+        g.M[k] = ds->M[k];
+        g.L[k] = L ? L[k] : 0;
+        g.nstencil *= 2 * g.L[k] + 1;
+        g.lo[k] = ds->lo[k];
+        g.delta[k] = ds->delta[k];
+    }
+    g.inv_n = 1.0 / (double)ds->n;
+    return g;
+}
+
+int kdefft_kde_grid(kdefft_ds ds, const double* H, double* out) {
+    KCHK(check_common(ds, H, 1));
+    if (!out) return fail(KDEFFT_ERR_ARG, "NULL output");
+    if (ds->opts.precision != KDEFFT_FP32 || ds->opts.binning != KDEFFT_BIN_LINEAR)
+        return fail(KDEFFT_ERR_UNSUPPORTED, "the grid estimate takes FP32 linear-binned datasets");
+    kdefft_ctx c = ds->ctx;
+    const int d = ds->d;
+    Mat Hm;
+    KCHK(sym_check(H, d, Hm, "H"));
+    KCHK(spd_or_fail(Hm, "H"));
+    int L[4] = {0, 0, 0, 0}, P[4];
+    KCHK(plan_for(ds, Hm, L, P));
+    const KdeDesc g = kde_desc(ds, L);
+    // stencil K_H(delta (.) l), last axis fastest, FP64 on the host
+    Mat inv;
+    double det;
+    spd_inv_det(Hm, inv, det);
+    const double nrm = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
+    std::vector<float> tab((size_t)g.nstencil);
+    for (long long s = 0; s < g.nstencil; ++s) {
+        long long r = s;
+        double x[4] = {0, 0, 0, 0};
+        for (int k = d - 1; k >= 0; --k) {
+            const int w = 2 * L[k] + 1;
+            x[k] = ds->delta[k] * (double)((int)(r % w) - L[k]);
+            r /= w;
+        }
+        double q = 0.0;
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) q += x[a] * inv(a, b) * x[b];
+        tab[(size_t)s] = (float)(nrm * std::exp(-0.5 * q));
+    }
+    const size_t bt = (sizeof(float) * tab.size() + 255) & ~(size_t)255;
+    KCHK(c->kdebuf.ensure(bt + sizeof(double) * (size_t)ds->ncells));
+    float* dtab = (float*)c->kdebuf.p;
+    double* dout = (double*)((unsigned char*)c->kdebuf.p + bt);
+    KCU(cudaMemcpyAsync(dtab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, c->stream));
+    c->h2d += (int64_t)(sizeof(float) * tab.size());
+    cudaEvent_t ev = prof_start(c);
+    KCU(launch_kde_grid((const float*)ds->counts.p, g, dtab, dout, c->nsm, c->stream));
+    prof_stop(c, ev, "kde_grid", 8.0 * (double)ds->ncells + 4.0 * (double)g.nstencil,
+              2.0 * (double)ds->ncells * (double)g.nstencil);
+    if (is_device_ptr(out)) {
+        KCU(cudaMemcpyAsync(out, dout, sizeof(double) * ds->ncells, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        KCU(cudaMemcpyAsync(out, dout, sizeof(double) * ds->ncells, cudaMemcpyDeviceToHost, c->stream));
+        c->d2h += (int64_t)(sizeof(double) * ds->ncells);
+    }
+    KCU(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    return KDEFFT_OK;
+}
+
+int kdefft_ise_mixture(kdefft_ds ds, const double* H, int nH, int K, const double* w, const double* mu,
+                       const double* S, double* out) {
+    KCHK(check_common(ds, H, nH));
+    if (!out || !w || !mu || !S || K < 1 || K > 64) return fail(KDEFFT_ERR_ARG, "need 1..64 mixture components");
+    if (ds->opts.precision != KDEFFT_FP32 || ds->opts.binning != KDEFFT_BIN_LINEAR)
+        return fail(KDEFFT_ERR_UNSUPPORTED, "the mixture ISE takes FP32 linear-binned datasets");
+    kdefft_ctx c = ds->ctx;
+    const int d = ds->d;
+    std::vector<Mat> Sm(K);
+    for (int m = 0; m < K; ++m) {
+        KCHK(sym_check(S + (size_t)m * d * d, d, Sm[m], "mixture covariance"));
+        KCHK(spd_or_fail(Sm[m], "mixture covariance"));
+    }
+    auto gauss_at = [&](const Mat& Sg, const double* x) {   // phi_Sg(x), FP64
+        Mat inv;
+        double det;
+        spd_inv_det(Sg, inv, det);
+        double q = 0.0;
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) q += x[a] * inv(a, b) * x[b];
+        return std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det) * std::exp(-0.5 * q);
+    };
+    // int f^2 = sum_lm w_l w_m phi_{S_l + S_m}(mu_l - mu_m), closed form
+    double ff = 0.0;
+    for (int a = 0; a < K; ++a)
+        for (int b = 0; b < K; ++b) {
+            double x[4];
+            for (int k = 0; k < d; ++k) x[k] = mu[(size_t)a * d + k] - mu[(size_t)b * d + k];
+            ff += w[a] * w[b] * gauss_at(lin(1.0, Sm[a], 1.0, Sm[b]), x);
+        }
+    // int f_hat^2 = n^-2 sum_ij phi_2H (binned, the lag-domain or FFT engine)
+    ReqSet rs;
+    std::vector<int> first(nH);
+    std::vector<Mat> Hs(nH);
+    for (int h = 0; h < nH; ++h) {
+        KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
+        KCHK(add_eta_m(rs, ds, scaled(2.0, Hs[h]), 0, first[h]));
+    }
+    KCHK(run(c, rs));
+    // int f_hat f = n^-1 sum_g c_g sum_m w_m phi_{H + S_m}(x_g - mu_m)
+    const KdeDesc g = kde_desc(ds, nullptr);
+    const int nb = std::max(1, std::min(c->nsm * 4, (int)((ds->ncells + 255) / 256)));
+    const size_t bc = (sizeof(MixComp) * K + 255) & ~(size_t)255;
+    KCHK(c->kdebuf.ensure(bc + sizeof(double) * nb));
+    MixComp* dcomp = (MixComp*)c->kdebuf.p;
+    double* dpart = (double*)((unsigned char*)c->kdebuf.p + bc);
+    std::vector<double> v(nH), part(nb);
+    for (int h = 0; h < nH; ++h) {
+        std::vector<MixComp> comps(K);
+        for (int m = 0; m < K; ++m) {
+            std::memset(&comps[m], 0, sizeof(MixComp));
+            const Mat Sc = lin(1.0, Hs[h], 1.0, Sm[m]);
+            Mat inv;
+            double det;
+            spd_inv_det(Sc, inv, det);
+            for (int k = 0; k < d; ++k) comps[m].mu[k] = mu[(size_t)m * d + k];
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) comps[m].lam[a * MAXD + b] = inv(a, b);
+            comps[m].nrm = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
+            comps[m].w = w[m];
+        }
+        KCU(cudaMemcpyAsync(dcomp, comps.data(), sizeof(MixComp) * K, cudaMemcpyHostToDevice, c->stream));
+        cudaEvent_t ev = prof_start(c);
+        KCU(launch_mix_dot((const float*)ds->counts.p, g, dcomp, K, dpart, nb, c->stream));
+        prof_stop(c, ev, "mix_dot", 4.0 * (double)ds->ncells, 12.0 * (double)ds->ncells * K);
+        KCU(cudaMemcpyAsync(part.data(), dpart, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+        KCU(cudaStreamSynchronize(c->stream));
+        double cross = 0.0;
+        for (int b = 0; b < nb; ++b) cross += part[b];
+        cross /= (double)ds->n;
+        v[h] = rs.grids[first[h]].value - 2.0 * cross + ff;
+    }
+    prof_flush(c);
+    return write_out(c, out, v.data(), v.size());
 }
 
 int kdefft_lscv_r(kdefft_ds ds, const double* H, int nH, int r, double* val) {

@@ -232,6 +232,29 @@ cudaError_t launch_acorr_axis(const double* in_r, const double2* in_c, double2* 
                               long long O, int W, long long I, int J, int jlo, int P, const double2* tw, int half,
                               double scale, cudaStream_t st);
 
+// ---- kernel density estimate on the grid and mixture cross term (kde.cu)
+struct KdeDesc {
+    int d;
+    long long M[MAXD];
+    int L[MAXD];                 // stencil half-widths
+    long long ncells, nstencil;  // prod M, prod (2 L_k + 1)
+    double lo[MAXD], delta[MAXD];
+    double inv_n;
+};
+struct MixComp {                 // w (2 pi)^{-d/2} |S|^{-1/2} exp(-(x - mu)^T S^-1 (x - mu) / 2)
+    double mu[MAXD];
+    double lam[MAXD * MAXD];     // S^-1, row stride MAXD
+    double nrm;                  // (2 pi)^{-d/2} |S|^{-1/2}
+    double w;
+};
+// out[g] = n^-1 sum_l c[g - l] ktab[l] for every grid node (ktab: the stencil,
+// last axis fastest); counts FP32
+cudaError_t launch_kde_grid(const float* counts, const KdeDesc& g, const float* ktab, double* out, int nsm,
+                            cudaStream_t st);
+// partial[b] (b < nblocks) = block b's share of sum_g c_g sum_m (comps[m] at x_g)
+cudaError_t launch_mix_dot(const float* counts, const KdeDesc& g, const MixComp* comps, int ncomp, double* partial,
+                           int nblocks, cudaStream_t st);
+
 // Binning (binning.cu).  Grid node k along axis a is lo[a] + k delta[a],
 // k < M[a].  Counts accumulate into `counts` (zeroed by the caller);
 // `outside` counts the points with a coordinate outside [lo, hi] (or NaN),

@@ -1,0 +1,75 @@
+"""Pins of the oracle's grid estimate and mixture ISE (Eqs. 1, 37) against
+facts fixed by the mathematics: the estimate integrates to one (Riemann
+sum over a grid that holds the sample and its kernel mass), equals a direct
+sum over the nodes for a single point on a node, the ISE is non-negative,
+int f^2 matches quadrature, and the binned ISE approaches the exact one as
+the grid is refined (second-order binning error)."""
+import numpy as np
+import pytest
+
+from oracle import binning, kde, rules
+
+
+def _mixture():
+    w = np.array([0.6, 0.4])
+    mu = np.array([[-0.5, 0.0], [0.8, 0.5]])
+    S = np.array([[[0.3, 0.1], [0.1, 0.2]], [[0.2, -0.05], [-0.05, 0.4]]])
+    return w, mu, S
+
+
+def _sample(n, seed):
+    rng = np.random.default_rng(seed)
+    w, mu, S = _mixture()
+    lab = rng.choice(2, n, p=w)
+    X = np.array([rng.multivariate_normal(mu[l], S[l]) for l in lab])
+    return X
+
+
+def test_grid_estimate_integrates_to_one_and_single_point():
+    X = _sample(300, 1)
+    H = np.array([[0.05, 0.01], [0.01, 0.04]])
+    lo, hi = X.min(0) - 1.5, X.max(0) + 1.5
+    M = [70, 64]
+    c = binning.bin_linear(X, lo, hi, M)
+    delta = rules.bin_width(lo, hi, M)
+    L = rules.support_L(rules.lambda_max(H), delta, M)
+    f = kde.kde_grid(c, X.shape[0], H, delta, L)
+    assert float(np.sum(f)) * float(np.prod(delta)) == pytest.approx(1.0, abs=2e-3)
+    # one point on a node: f(g) = K_H(x_g - x_point) within the support
+    c1 = np.zeros(M)
+    c1[30, 31] = 1.0
+    f1 = kde.kde_grid(c1, 1, H, delta, L)
+    from oracle.gauss import gauss_density
+    g = np.array([33, 29])
+    x = (g - np.array([30, 31])) * delta
+    assert f1[33, 29] == pytest.approx(float(gauss_density(x[None, :], H)[0]), rel=1e-12)
+    assert f1[30 + L[0] + 1, 31] == 0.0      # outside the truncated stencil
+
+
+def test_mixture_square_integral_matches_quadrature():
+    w, mu, S = _mixture()
+    from oracle.gauss import gauss_density
+    xs = np.linspace(-5, 5, 401)
+    h = xs[1] - xs[0]
+    G = np.stack(np.meshgrid(xs, xs, indexing="ij"), axis=-1).reshape(-1, 2)
+    f = sum(wm * gauss_density(G - m[None, :], Sm) for wm, m, Sm in zip(w, mu, S))
+    assert kde.mixture_sq_integral(w, mu, S) == pytest.approx(float(np.sum(f * f)) * h * h, rel=1e-6)
+
+
+def test_ise_nonnegative_and_binning_converges():
+    X = _sample(400, 2)
+    w, mu, S = _mixture()
+    H = np.array([[0.06, 0.01], [0.01, 0.05]])
+    exact = kde.ise_mixture_exact(X, H, w, mu, S)
+    assert exact > 0.0
+    lo, hi = X.min(0) - 2.0, X.max(0) + 2.0
+    errs = []
+    for m in (40, 80, 160):
+        M = [m, m]
+        c = binning.bin_linear(X, lo, hi, M)
+        delta = rules.bin_width(lo, hi, M)
+        L2 = [mm - 1 for mm in M]
+        b = kde.ise_mixture_binned(c, X.shape[0], lo, delta, H, w, mu, S, L2)
+        assert b > 0.0
+        errs.append(abs(b - exact))
+    assert errs[1] < errs[0] / 2.5 and errs[2] < errs[1] / 2.5   # about 4x per halving of delta
