@@ -232,6 +232,19 @@ int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G,
                     int n_starts, int max_iter, double* H_out, double* f_out,
                     int64_t* n_evals);
 
+/* Bandwidth classes (Sec. 3): F, full SPD matrices (the paper's subject);
+ * D, diagonal matrices; S, scalar multiples h^2 I of the identity. */
+enum { KDEFFT_H_FULL = 0, KDEFFT_H_DIAG = 1, KDEFFT_H_SCALAR = 2 };
+
+/* kdefft_select_H (optimizer 0) or kdefft_select_H_nm (optimizer 1) with H
+ * restricted to a class: D searches the log square roots of the diagonal,
+ * S the log of h; starts are the class projections of the usual starts
+ * (the diagonal of each start for D, h^2 = the geometric mean of its
+ * diagonal for S).  The device-resident d = 2 search covers F only; D and S
+ * run the host-driven search.  Same arguments, domain and errors otherwise. */
+int kdefft_select_H_class(kdefft_ds ds, int method, int hclass, int optimizer, const double* H0, const double* G,
+                          int n_starts, int max_iter, double* H_out, double* f_out, int64_t* n_evals);
+
 /* The same minimisation with the derivative-free Nelder-Mead method the
  * paper's experiments use (Sec. 6: reflection 1.0, contraction 0.5,
  * expansion 2.0), for parity with its selections.  Simplex in the same

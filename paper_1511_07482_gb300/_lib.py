@@ -32,7 +32,7 @@ EXPORTS = [
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
-    "kdefft_kde_grid", "kdefft_ise_mixture",
+    "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "kdefft_lscv_r": (I, [P, P, I, I, P]),
         "kdefft_eta_rs": (I, [P, P, P, P, I, I, I, P]),
         "kdefft_kde_grid": (I, [P, P, P]),
+        "kdefft_select_H_class": (I, [P, I, I, I, P, P, I, I, P, P, P]),
         "kdefft_ise_mixture": (I, [P, P, I, I, P, P, P, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -413,19 +414,29 @@ class Dataset:
         _check(load().kdefft_eta02(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p)))
         return val
 
-    def select_H(self, method=LSCV, H0=None, G=None, n_starts=1, max_iter=None, optimizer="bfgs"):
+    def select_H(self, method=LSCV, H0=None, G=None, n_starts=1, max_iter=None, optimizer="bfgs", hclass="full"):
         """Minimise the objective over H: optimizer "bfgs" (quasi-Newton on
         the exact gradients, max_iter iterations, default 100) or
         "nelder-mead" (the paper's derivative-free parity mode, max_iter
-        objective evaluations per start, default 500)."""
+        objective evaluations per start, default 500); hclass "full" (the
+        SPD matrices), "diag" or "scalar" (Sec. 3's constrained classes)."""
         if optimizer not in ("bfgs", "nelder-mead"):
             raise ValueError("optimizer must be 'bfgs' or 'nelder-mead'")
+        classes = {"full": 0, "diag": 1, "scalar": 2}
+        if hclass not in classes:
+            raise ValueError("hclass must be 'full', 'diag' or 'scalar'")
         Ha, pH = _host_f64(H0) if H0 is not None else (None, None)
         Ga, pG = _host_f64(G) if G is not None else (None, None)
         Hout = np.zeros((self.d, self.d))
         f = C.c_double()
         ne = C.c_int64()
-        fn = load().kdefft_select_H if optimizer == "bfgs" else load().kdefft_select_H_nm
-        _check(fn(self.h, method, pH, pG, int(n_starts), int(max_iter or 0),
-                  Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
+        lib = load()
+        if hclass == "full":
+            fn = lib.kdefft_select_H if optimizer == "bfgs" else lib.kdefft_select_H_nm
+            _check(fn(self.h, method, pH, pG, int(n_starts), int(max_iter or 0),
+                      Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
+        else:
+            _check(lib.kdefft_select_H_class(self.h, method, classes[hclass], 0 if optimizer == "bfgs" else 1, pH,
+                                             pG, int(n_starts), int(max_iter or 0),
+                                             Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
         return Hout, f.value, ne.value

@@ -2995,20 +2995,31 @@ int kdefft_batch_lscv(kdefft_ctx c, int nds, const kdefft_ds* dss, const int* nH
 // off-diagonal entries free; row-major over the lower triangle.
 namespace {
 
+// Search parameters theta of a bandwidth class (Sec. 3): F, the full SPD
+// matrices, through the Cholesky factor R (H = R R^T, log diagonal, p =
+// d(d+1)/2); D, the diagonal ones, H = diag(e^{2 theta_k}) (p = d); S, the
+// scalar ones, H = e^{2 theta} I (p = 1).
 struct Opt {
     int d;
     int p;
+    int cls = KDEFFT_H_FULL;
 };
+
+static int class_params(int d, int cls) { return cls == KDEFFT_H_FULL ? d * (d + 1) / 2 : (cls == KDEFFT_H_DIAG ? d : 1); }
 
 Mat theta_to_H(const Opt& o, const double* th, Mat* Rout = nullptr) {
     Mat R;
     R.d = o.d;
-    int t = 0;
-    for (int i = 0; i < o.d; ++i)
-        for (int j = 0; j <= i; ++j) {
-            R(i, j) = (i == j) ? std::exp(th[t]) : th[t];
-            ++t;
-        }
+    if (o.cls == KDEFFT_H_DIAG || o.cls == KDEFFT_H_SCALAR) {
+        for (int i = 0; i < o.d; ++i) R(i, i) = std::exp(o.cls == KDEFFT_H_DIAG ? th[i] : th[0]);
+    } else {
+        int t = 0;
+        for (int i = 0; i < o.d; ++i)
+            for (int j = 0; j <= i; ++j) {
+                R(i, j) = (i == j) ? std::exp(th[t]) : th[t];
+                ++t;
+            }
+    }
     Mat H;
     H.d = o.d;
     for (int i = 0; i < o.d; ++i)
@@ -3022,6 +3033,16 @@ Mat theta_to_H(const Opt& o, const double* th, Mat* Rout = nullptr) {
 }
 
 void H_to_theta(const Opt& o, const Mat& H, double* th) {
+    if (o.cls == KDEFFT_H_DIAG) {   // the diagonal of H (the start projected onto D)
+        for (int i = 0; i < o.d; ++i) th[i] = 0.5 * std::log(H(i, i));
+        return;
+    }
+    if (o.cls == KDEFFT_H_SCALAR) {   // h^2 = geometric mean of the diagonal
+        double s = 0.0;
+        for (int i = 0; i < o.d; ++i) s += std::log(H(i, i));
+        th[0] = 0.5 * s / o.d;
+        return;
+    }
     Mat R;
     cholesky(H, R);
     int t = 0;
@@ -3035,8 +3056,18 @@ void H_to_theta(const Opt& o, const Mat& H, double* th) {
 // tied gradient g (d x d) of F(H) -> gradient in theta
 void grad_theta(const Opt& o, const double* th, const double* g, double* gt) {
     Mat R;
-    theta_to_H(o, th, &R);
+    const Mat H = theta_to_H(o, th, &R);
     const int d = o.d;
+    if (o.cls == KDEFFT_H_DIAG) {   // dH_kk / dtheta_k = 2 H_kk
+        for (int k = 0; k < d; ++k) gt[k] = 2.0 * H(k, k) * g[k * d + k];
+        return;
+    }
+    if (o.cls == KDEFFT_H_SCALAR) {   // dH / dtheta = 2 h^2 I
+        double tr = 0.0;
+        for (int k = 0; k < d; ++k) tr += g[k * d + k];
+        gt[0] = 2.0 * H(0, 0) * tr;
+        return;
+    }
     // independent-entry derivative G_ind: off-diagonals are half the tied values
     Mat Gi;
     Gi.d = d;
@@ -3346,7 +3377,7 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
 static constexpr int kMaxHalvings = 12;
 
 static int select_H_impl(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts, int max_iter,
-                         bool nelder_mead, double* H_out, double* f_out, int64_t* n_evals) {
+                         bool nelder_mead, double* H_out, double* f_out, int64_t* n_evals, int hclass = KDEFFT_H_FULL) {
     if (!ds || !H_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
     if (method != KDEFFT_LSCV && method != KDEFFT_SCV && method != KDEFFT_PI)
         return fail(KDEFFT_ERR_ARG, "unknown method");
@@ -3354,7 +3385,9 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
     if (max_iter < 1) max_iter = nelder_mead ? 500 : 100;
     KCU(cudaSetDevice(ds->ctx->device));
     const int d = ds->d;
-    Opt o{d, d * (d + 1) / 2};
+    if (hclass != KDEFFT_H_FULL && hclass != KDEFFT_H_DIAG && hclass != KDEFFT_H_SCALAR)
+        return fail(KDEFFT_ERR_ARG, "unknown bandwidth class");
+    Opt o{d, class_params(d, hclass), hclass};
     const int p = o.p;
     Mat Hstart;
     if (H0) {
@@ -3453,6 +3486,7 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
         double f = 0.0, step = 1.0, slope = 0.0;
         int iter = 0, ls = 0;
         bool done = false;
+        bool fresh = true;   // the current direction comes from a reset (scaled steepest descent)
     };
     std::vector<State> st(n_starts);
     for (int s = 0; s < n_starts; ++s) {
@@ -3640,7 +3674,7 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
                 }
         return report(nm[bs].x[bv], fb);
     }
-    if (d == 2) {
+    if (d == 2 && hclass == KDEFFT_H_FULL) {
         std::vector<std::vector<double>> ths, tho;
         for (auto& s : st) ths.push_back(s.th);
         std::vector<double> fo;
@@ -3767,14 +3801,25 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
                     tn = std::max(tn, std::fabs(sv[i]));
                 }
                 if (s.iter >= max_iter || std::fabs(fold - fn) <= 1e-12 * std::fabs(fn) + 1e-300 || tn < 1e-10 ||
-                    gn < 1e-12 * (std::fabs(fn) + 1e-300))
+                    gn < 1e-12 * (std::fabs(fn) + 1e-300)) {
                     s.done = true;
-                else
+                } else {
+                    s.fresh = false;
                     new_direction(s);
+                }
             } else {
                 s.step *= 0.5;
                 s.ls++;
-                if (s.ls > kMaxHalvings) {
+                if (s.ls > kMaxHalvings && !s.fresh) {
+                    // restart: the quasi-Newton model failed here; scaled steepest descent once
+                    double gm = 0.0;
+                    for (double v : s.g) gm = std::max(gm, std::fabs(v));
+                    const double sc = (gm > 0) ? 0.1 / gm : 1.0;
+                    std::fill(s.Binv.begin(), s.Binv.end(), 0.0);
+                    for (int i = 0; i < p; ++i) s.Binv[i * p + i] = sc;
+                    s.fresh = true;
+                    new_direction(s);
+                } else if (s.ls > kMaxHalvings) {
                     s.done = true;
                 } else {
                     for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
@@ -3796,4 +3841,11 @@ extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const
 extern "C" int kdefft_select_H_nm(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
                                   int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
     return select_H_impl(ds, method, H0, G, n_starts, max_iter, true, H_out, f_out, n_evals);
+}
+
+extern "C" int kdefft_select_H_class(kdefft_ds ds, int method, int hclass, int optimizer, const double* H0,
+                                     const double* G, int n_starts, int max_iter, double* H_out, double* f_out,
+                                     int64_t* n_evals) {
+    if (optimizer != 0 && optimizer != 1) return fail(KDEFFT_ERR_ARG, "optimizer: 0 quasi-Newton, 1 Nelder-Mead");
+    return select_H_impl(ds, method, H0, G, n_starts, max_iter, optimizer == 1, H_out, f_out, n_evals, hclass);
 }

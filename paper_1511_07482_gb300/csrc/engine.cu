@@ -1026,6 +1026,7 @@ struct SelOpt {
     float step, slope;
     double flops, bytes;
     int iter, ls, done, evals, status, first;
+    int fresh;   // the current direction comes from a reset (scaled steepest descent)
 };
 
 // H = R R^T, R = [[e^t0, 0], [t1, e^t2]].
@@ -1247,6 +1248,7 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
             s.done = 1;
             return;
         }
+        s.fresh = 1;
         sel_new_direction(s);
         return;
     }
@@ -1287,12 +1289,21 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
                    (double)gm < 1e-12 * (fabs(fn) + 1e-300)) {
             s.done = 1;
         } else {
+            s.fresh = 0;
             sel_new_direction(s);
         }
     } else {
         s.step *= 0.5f;
         s.ls++;
-        if (s.ls > kMaxHalvings) {
+        if (s.ls > kMaxHalvings && !s.fresh) {
+            // restart: the quasi-Newton model failed here; scaled steepest descent once
+            const float gm = fmaxf(fabsf(s.g[0]), fmaxf(fabsf(s.g[1]), fabsf(s.g[2])));
+            const float sc = (gm > 0.f) ? 0.1f * __frcp_rn(gm) : 1.f;
+            for (int i = 0; i < 9; ++i) s.Binv[i] = 0.f;
+            for (int i = 0; i < 3; ++i) s.Binv[i * 4] = sc;
+            s.fresh = 1;
+            sel_new_direction(s);
+        } else if (s.ls > kMaxHalvings) {
             s.done = 1;
         } else {
             for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + (double)(s.step * s.dir[i]);
@@ -1330,6 +1341,7 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
         opt.f = INFINITY;
         opt.flops = 0.0;
         opt.bytes = 0.0;
+        opt.fresh = 0;
     }
     __syncthreads();
     const int max_rounds = 40 * p.max_iter + 2;
@@ -1500,6 +1512,7 @@ __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelStart*
         opt.f = INFINITY;
         opt.flops = 0.0;
         opt.bytes = 0.0;
+        opt.fresh = 0;
     }
     __syncthreads();
     const int max_rounds = 40 * p.max_iter + 2;
