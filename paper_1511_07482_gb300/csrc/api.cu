@@ -428,6 +428,7 @@ struct kdefft_ctx_s {
     DevBuf sel_buf;           // device tables and start states of the device-resident selection
     DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
     DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
+    DevBuf acjobs;            // job table of the batched autocorrelation passes
     DevBuf kdebuf;            // stencil table / outputs of the grid estimate and the mixture term
     std::map<std::string, KStat> kstat;
     struct Pending {
@@ -1541,81 +1542,125 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
         for (int k = 0; k < jb.ds->d; ++k) twiddle_offset(c, jb.P[k]);
     KCHK(sync_twiddles(c));
     const double2* tw = (const double2*)c->tw64.p;
-    for (const Job& jb : jobs) {
+    // Per dataset, the sizes of its passes; pass buffers at offsets in the
+    // two context pools; then every pass level is one launch over all
+    // datasets of that dimension (level k transforms axis k: [w_{d-1} ..
+    // w_{k+1}][w_k][j_{k-1} .. j_0] -> [..][j_k][..]; the last level is the
+    // half-spectrum axis, written as real FP64 and FP32).
+    struct Plan {
+        const double* S;
+        long long O0;      // rows of the innermost pass
+        size_t most;       // complex elements of the largest intermediate
+        size_t off;        // offset in the pools
+        double ptot;
+        int Q;
+    };
+    std::vector<Plan> plan(jobs.size());
+    size_t pool = 0;
+    double fl = 0.0, by = 0.0;
+    for (size_t u = 0; u < jobs.size(); ++u) {
+        const Job& jb = jobs[u];
         kdefft_ds ds = jb.ds;
         const int d = ds->d;
         const int* A = jb.A;
         const int* P = jb.P;
         auto sit = ds->spectra.find(spectrum_key(ds, P, sizeof(double)));
         if (sit == ds->spectra.end()) return fail(KDEFFT_ERR_CUDA, "count spectrum missing");
-        const double* S = (const double*)sit->second->p;
+        Plan& pl = plan[u];
+        pl.S = (const double*)sit->second->p;
+        pl.Q = P[d - 1] / 2 + 1;
+        pl.ptot = 1.0;
         long long nbox = 1;
-        double ptot = 1.0;
         for (int k = 0; k < d; ++k) {
             nbox *= (k == 0) ? (A[0] + 1) : (2 * A[k] + 1);
-            ptot *= P[k];
+            pl.ptot *= P[k];
         }
         KCHK(ds->ac64.ensure(sizeof(double) * nbox));
         KCHK(ds->ac32.ensure(sizeof(float) * nbox));
-        float* o32 = (float*)ds->ac32.p;
-        const int Q = P[d - 1] / 2 + 1;
-        // algorithmic work of the passes: 8 flops per complex term, the spectrum read once
-        double fl = 0.0;
+        pl.O0 = pl.Q;
+        for (int k = 1; k <= d - 2; ++k) pl.O0 *= P[k];
+        pl.most = 0;
         {
-            long long o = Q, ii = 1;
-            for (int k = 1; k <= d - 2; ++k) o *= P[k];
+            long long o = pl.O0, ii = 1;
             for (int k = 0; k < d - 1; ++k) {
                 const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
+                pl.most = std::max(pl.most, (size_t)(o * J * ii));
                 fl += 8.0 * (double)o * J * ii * P[k];
                 ii *= J;
                 if (k + 1 <= d - 2) o /= P[k + 1];
             }
-            fl += 8.0 * (double)ii * (2 * A[d - 1] + 1) * Q;
+            fl += 8.0 * (double)ii * (2 * A[d - 1] + 1) * pl.Q;
         }
-        double by = 8.0 * Q;
-        for (int k = 0; k < d - 1; ++k) by *= P[k];
+        pl.off = pool;
+        pool += (pl.most + 1) & ~(size_t)1;
+        double b = 8.0 * pl.Q;
+        for (int k = 0; k < d - 1; ++k) b *= P[k];
+        by += b;
+    }
+    if (!jobs.empty()) {
+        KCHK(c->acbuf[0].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
+        KCHK(c->acbuf[1].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
+        // one table slice per launch (at most MAXD launches per dataset), so
+        // that no launch waits for the previous one's table to be read
+        KCHK(c->acjobs.ensure(sizeof(AcorrJob) * jobs.size() * MAXD));
+        AcorrJob* jd = (AcorrJob*)c->acjobs.p;
+        size_t slot = 0;
+        double2* pool0 = (double2*)c->acbuf[0].p;
+        double2* pool1 = (double2*)c->acbuf[1].p;
         cudaEvent_t ev = prof_start(c);
-        c->launches--;   // counted per pass below
-        if (d == 1) {
-            c->launches++;
-            KCU(launch_acorr_axis(S, nullptr, nullptr, (double*)ds->ac64.p, o32, 1, Q, 1, A[0] + 1, 0, P[0],
-                                  tw + twiddle_offset(c, P[0]), 1, 1.0 / ptot, c->stream));
-        } else {
-            // pass k transforms axis k: [w_{d-1}..w_{k+1}][w_k][j_{k-1}..j_0] -> [..][j_k][..]
-            long long O = Q;
-            for (int k = 1; k <= d - 2; ++k) O *= P[k];
-            size_t most = 0;
-            {
-                long long o = O, ii = 1;
-                for (int k = 0; k < d - 1; ++k) {
-                    const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
-                    most = std::max(most, (size_t)(o * J * ii));
-                    ii *= J;
-                    if (k + 1 <= d - 2) o /= P[k + 1];
+        c->launches--;   // counted per launch below
+        for (int dim = 1; dim <= MAXD; ++dim) {
+            std::vector<size_t> sel;
+            for (size_t u = 0; u < jobs.size(); ++u)
+                if (jobs[u].ds->d == dim) sel.push_back(u);
+            if (sel.empty()) continue;
+            // level k of every selected dataset
+            std::vector<long long> O(sel.size()), I(sel.size(), 1);
+            for (size_t v = 0; v < sel.size(); ++v) O[v] = plan[sel[v]].O0;
+            for (int k = 0; k < dim; ++k) {
+                const bool last = (k == dim - 1);
+                std::vector<AcorrJob> tab(sel.size());
+                for (size_t v = 0; v < sel.size(); ++v) {
+                    const Job& jb = jobs[sel[v]];
+                    const Plan& pl = plan[sel[v]];
+                    AcorrJob& a = tab[v];
+                    std::memset(&a, 0, sizeof(a));
+                    // ping-pong: level k reads pool (k+1)&1, writes pool k&1
+                    double2* rd = ((k & 1) ? pool0 : pool1) + pl.off;
+                    double2* wr = ((k & 1) ? pool1 : pool0) + pl.off;
+                    a.in_r = (k == 0) ? pl.S : nullptr;
+                    a.in_c = (k == 0) ? nullptr : rd;
+                    a.O = last ? 1 : O[v];
+                    a.I = I[v];
+                    a.W = last ? pl.Q : jb.P[k];
+                    a.J = (k == 0) ? jb.A[0] + 1 : 2 * jb.A[k] + 1;
+                    a.jlo = (k == 0) ? 0 : -jb.A[k];
+                    a.P = jb.P[k];
+                    a.tw_off = twiddle_offset(c, jb.P[k]);
+                    a.half = last ? 1 : 0;
+                    a.scale = last ? 1.0 / pl.ptot : 1.0;
+                    if (last) {
+                        a.out_r = (double*)jb.ds->ac64.p;
+                        a.out_r32 = (float*)jb.ds->ac32.p;
+                    } else {
+                        a.out_c = wr;
+                    }
+                }
+                c->launches++;
+                KCU(launch_acorr_many(tab.data(), jd + slot, (int)tab.size(), k == 0, tw, c->stream));
+                slot += tab.size();
+                for (size_t v = 0; v < sel.size(); ++v) {
+                    const Job& jb = jobs[sel[v]];
+                    const int J = (k == 0) ? jb.A[0] + 1 : 2 * jb.A[k] + 1;
+                    I[v] *= J;
+                    if (k + 1 <= dim - 2) O[v] /= jb.P[k + 1];
                 }
             }
-            KCHK(c->acbuf[0].ensure(sizeof(double2) * most));
-            KCHK(c->acbuf[1].ensure(sizeof(double2) * most));
-            double2* cur = (double2*)c->acbuf[0].p;
-            double2* nxt = (double2*)c->acbuf[1].p;
-            long long I = 1;
-            for (int k = 0; k < d - 1; ++k) {
-                const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
-                const int jlo = (k == 0) ? 0 : -A[k];
-                c->launches++;
-                KCU(launch_acorr_axis(k == 0 ? S : nullptr, k == 0 ? nullptr : cur, nxt, nullptr, nullptr, O, P[k], I,
-                                      J, jlo, P[k], tw + twiddle_offset(c, P[k]), 0, 1.0, c->stream));
-                std::swap(cur, nxt);
-                I *= J;
-                if (k + 1 <= d - 2) O /= P[k + 1];
-            }
-            c->launches++;
-            KCU(launch_acorr_axis(nullptr, cur, nullptr, (double*)ds->ac64.p, o32, 1, Q, I, 2 * A[d - 1] + 1,
-                                  -A[d - 1], P[d - 1], tw + twiddle_offset(c, P[d - 1]), 1, 1.0 / ptot, c->stream));
         }
         prof_stop(c, ev, "acorr_f64", by, fl);
-        for (int k = 0; k < 4; ++k) ds->acA[k] = (k < d) ? A[k] : 0;
     }
+    for (const Job& jb : jobs)
+        for (int k = 0; k < 4; ++k) jb.ds->acA[k] = (k < jb.ds->d) ? jb.A[k] : 0;
     return KDEFFT_OK;
 }
 
@@ -2323,6 +2368,7 @@ int kdefft_destroy(kdefft_ctx c) {
     c->binfix.release();
     c->acbuf[0].release();
     c->acbuf[1].release();
+    c->acjobs.release();
     c->kdebuf.release();
     c->h_items.release();
     c->h_out.release();

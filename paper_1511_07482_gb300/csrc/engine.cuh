@@ -222,15 +222,30 @@ template <typename real>
 cudaError_t launch_lag_reduce(const LagItem<real>* items, int nitems, const double* partial, double* out,
                               cudaStream_t st);
 // One separable pass of the inverse DFT that turns the FP64 count spectrum
-// into the autocorrelation: out[o][jj][i] = sum_{w < W} h(w) in[o][w][i]
-// e^{+2 pi i w (jlo + jj) / P}, h(w) = 1, or for the half-spectrum axis
-// (half != 0) 1 at w = 0 and w = P/2 and 2 elsewhere.  in: real (in_r) or
-// complex (in_c); out: complex (out_c), or the real part times `scale`
-// (out_r, and rounded to FP32 into out_r32 when given).  tw: exp(-2 pi i t
-// / P), t < P.
-cudaError_t launch_acorr_axis(const double* in_r, const double2* in_c, double2* out_c, double* out_r, float* out_r32,
-                              long long O, int W, long long I, int J, int jlo, int P, const double2* tw, int half,
-                              double scale, cudaStream_t st);
+// into the autocorrelation, for one dataset: out[o][jj][i] = sum_{w < W} h(w)
+// in[o][w][i] e^{+2 pi i w (jlo + jj) / P}, h(w) = 1, or for the
+// half-spectrum axis (half != 0) 1 at w = 0 and w = P/2 and 2 elsewhere.  in:
+// real (in_r) or complex (in_c); out: complex (out_c), or the real part times
+// `scale` (out_r, and rounded to FP32 into out_r32 when given).  Twiddles
+// exp(-2 pi i t / P), t < P, at twpool + tw_off.  blk0: the job's first
+// block in a launch over many jobs (set by the launcher).
+struct AcorrJob {
+    const double* in_r;
+    const double2* in_c;
+    double2* out_c;
+    double* out_r;
+    float* out_r32;
+    long long O, I;
+    int W, J, jlo, P, tw_off, half;
+    double scale;
+    long long blk0;
+};
+// All jobs' passes in one launch: inner = the innermost axis of a real
+// spectrum (I = 1; one CTA per row), else an outer axis of complex data.
+// jobs_h: host table (rewritten with each job's blk0), jobs_d: device space
+// for it (n entries).
+cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, bool inner, const double2* twpool,
+                              cudaStream_t st);
 
 // ---- kernel density estimate on the grid and mixture cross term (kde.cu)
 struct KdeDesc {
