@@ -199,13 +199,13 @@ def run_ours(args):
         X_pin = [torch.from_numpy(v.X).pin_memory() for v in ws]
 
         def step(Xs):
-            dss = [ctx.bin(X, v.lo, v.hi, v.M) for X, v in zip(Xs, ws)]
+            dss = ctx.bin_many(Xs, [v.lo for v in ws], [v.hi for v in ws], [v.M for v in ws])
             ctx.batch_lscv(dss, [v.H for v in ws])
             for ds in dss:
                 ds.close()
             return 16 * len(ws), None
-        workload_desc = "512 bivariate datasets (n log-uniform 1e3..1e5, grids 64^2..256^2): bin + LSCV and " \
-                        "gradient for 16 H each in one batched call"
+        workload_desc = "512 bivariate datasets (n log-uniform 1e3..1e5, grids 64^2..256^2): batched binning + " \
+                        "LSCV and gradient for 16 H each in one batched call"
     elif args.workload == "lscv_batch16":
         w = synthetic.mixture_2d_large(seed=rank_seed(2, rank))
         X_dev = torch.from_numpy(w.X).to(dev)

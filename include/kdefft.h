@@ -113,6 +113,18 @@ int kdefft_destroy(kdefft_ctx ctx);
 int kdefft_bin(kdefft_ctx ctx, const double* X, int64_t n, int d,
                const double* lo, const double* hi, const int64_t* M,
                const kdefft_opts* opts, kdefft_ds* out);
+
+/* kdefft_bin for nds datasets of the same d at once (Sec. 4 step 1 for
+ * each): X[i] is dataset i's n[i] x d sample (host or device), lo/hi its
+ * grid range (nds x d), M its grid (nds x d).  FP32 linear binning runs as
+ * a few launches over all datasets (binning, conversion, the two moment
+ * passes) with two synchronisations in total, and the datasets' counts
+ * share one allocation (freed with the last of them); other precisions and
+ * rules bin one dataset at a time.  out: nds handles.  On error no dataset
+ * is created. */
+int kdefft_bin_many(kdefft_ctx ctx, int nds, const double* const* X, const int64_t* n, int d,
+                    const double* lo, const double* hi, const int64_t* M, const kdefft_opts* opts,
+                    kdefft_ds* out);
 int kdefft_ds_destroy(kdefft_ds ds);
 
 /* Replace the dataset's per-call options (tau, L_basis, P_rule, P_fixed,

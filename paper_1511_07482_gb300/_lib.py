@@ -32,7 +32,7 @@ EXPORTS = [
     "kdefft_batch_lscv", "kdefft_profile", "kdefft_profile_read", "kdefft_strerror", "kdefft_last_error",
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
-    "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class",
+    "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class", "kdefft_bin_many",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "kdefft_eta_rs": (I, [P, P, P, P, I, I, I, P]),
         "kdefft_kde_grid": (I, [P, P, P]),
         "kdefft_select_H_class": (I, [P, I, I, I, P, P, I, I, P, P, P]),
+        "kdefft_bin_many": (I, [P, I, P, P, I, P, P, P, C.POINTER(Opts), P]),
         "kdefft_ise_mixture": (I, [P, P, I, I, P, P, P, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -256,6 +257,29 @@ class Context:
         ds = Dataset(self, h, d, [int(m) for m in M_a])
         self._datasets.add(ds)
         return ds
+
+    def bin_many(self, Xs, los, his, Ms, **opts):
+        """Bin many datasets of the same dimension in one call (a few
+        batched launches): one Dataset per sample."""
+        nds = len(Xs)
+        keep = [_ptr_of(X) for X in Xs]
+        d = int(keep[0][0].shape[1])
+        ptrs = (C.c_void_p * nds)(*[p for _, p in keep])
+        n = np.ascontiguousarray(np.array([int(k.shape[0]) for k, _ in keep], dtype=np.int64))
+        lo = np.ascontiguousarray(np.asarray(los, dtype=np.float64).reshape(nds, d))
+        hi = np.ascontiguousarray(np.asarray(his, dtype=np.float64).reshape(nds, d))
+        M = np.ascontiguousarray(np.asarray(Ms, dtype=np.int64).reshape(nds, d))
+        o = default_opts(**opts)
+        hs = (C.c_void_p * nds)()
+        _check(load().kdefft_bin_many(self.h, nds, C.cast(ptrs, C.c_void_p), n.ctypes.data_as(C.c_void_p), d,
+                                      lo.ctypes.data_as(C.c_void_p), hi.ctypes.data_as(C.c_void_p),
+                                      M.ctypes.data_as(C.c_void_p), C.byref(o), C.cast(hs, C.c_void_p)))
+        out = []
+        for i in range(nds):
+            ds = Dataset(self, C.c_void_p(hs[i]), d, [int(m) for m in M[i]])
+            self._datasets.add(ds)
+            out.append(ds)
+        return out
 
     def batch_lscv(self, datasets, H_per_ds, grad=True):
         """LSCV (+ gradient) for many datasets in one batched launch sequence."""

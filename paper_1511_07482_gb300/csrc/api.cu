@@ -52,13 +52,21 @@ static int fail(int code, const std::string& msg) {
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
+    bool owner = true;   // false: a view into memory another buffer owns
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf() { release(); }
+    void view(void* q, size_t bytes) {
+        release();
+        p = q;
+        cap = bytes;
+        owner = false;
+    }
     int ensure(size_t bytes) {
         if (bytes <= cap) return KDEFFT_OK;
-        if (p) cudaFree(p);
+        if (p && owner) cudaFree(p);
+        owner = true;
         p = nullptr;
         cap = 0;
         size_t want = std::max(bytes, (size_t)4096);
@@ -71,9 +79,10 @@ struct DevBuf {
         return KDEFFT_OK;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p && owner) cudaFree(p);
         p = nullptr;
         cap = 0;
+        owner = true;
     }
 };
 
@@ -429,6 +438,7 @@ struct kdefft_ctx_s {
     DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
     DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
     DevBuf acjobs;            // job table of the batched autocorrelation passes
+    DevBuf binjobs;           // job tables of the batched binning
     DevBuf kdebuf;            // stencil table / outputs of the grid estimate and the mixture term
     std::map<std::string, KStat> kstat;
     struct Pending {
@@ -583,6 +593,7 @@ struct kdefft_ds_s {
     // and an FP32 copy
     int acA[4] = {-1, -1, -1, -1};
     DevBuf ac64, ac32;
+    std::shared_ptr<DevBuf> pool;   // memory that `counts` views (datasets binned together share one)
 };
 
 static int twiddle_offset(kdefft_ctx c, int P) {
@@ -2369,6 +2380,7 @@ int kdefft_destroy(kdefft_ctx c) {
     c->acbuf[0].release();
     c->acbuf[1].release();
     c->acjobs.release();
+    c->binjobs.release();
     c->kdebuf.release();
     c->h_items.release();
     c->h_out.release();
@@ -2497,6 +2509,164 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     misc.release();
     *out = ds.release();
     c->datasets.push_back(*out);
+    return KDEFFT_OK;
+}
+
+int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t* n, int d, const double* lo,
+                    const double* hi, const int64_t* M, const kdefft_opts* opts, kdefft_ds* out) {
+    if (!c || !X || !n || !lo || !hi || !M || !out || nds < 1) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    if (d < 1 || d > 4) return fail(KDEFFT_ERR_ARG, "d must be 1..4");
+    for (int i = 0; i < nds; ++i) out[i] = nullptr;
+    kdefft_opts o;
+    if (opts)
+        o = *opts;
+    else
+        kdefft_opts_default(&o);
+    if (!(o.tau > 0.0)) return fail(KDEFFT_ERR_ARG, "tau must be positive");
+    if (o.precision != KDEFFT_FP32 || o.binning != KDEFFT_BIN_LINEAR) {
+        // other precisions and rules: one dataset at a time
+        for (int i = 0; i < nds; ++i) {
+            const int r = kdefft_bin(c, X[i], n[i], d, lo + (size_t)i * d, hi + (size_t)i * d, M + (size_t)i * d, &o,
+                                     &out[i]);
+            if (r != KDEFFT_OK) {
+                for (int j = 0; j < i; ++j) kdefft_ds_destroy(out[j]);
+                return r;
+            }
+        }
+        return KDEFFT_OK;
+    }
+    KCU(cudaSetDevice(c->device));
+    std::vector<std::unique_ptr<kdefft_ds_s>> dss(nds);
+    std::vector<BinJob> jobs(nds);
+    long long totx = 0, totcells = 0;
+    std::vector<long long> xoff(nds, -1), coff(nds);
+    int K = 32;
+    for (int i = 0; i < nds; ++i) {
+        if (n[i] < 1 || !X[i]) return fail(KDEFFT_ERR_ARG, "need n >= 1 samples for every dataset");
+        dss[i].reset(new kdefft_ds_s());
+        kdefft_ds_s& ds = *dss[i];
+        ds.ctx = c;
+        ds.d = d;
+        ds.n = n[i];
+        ds.opts = o;
+        BinJob& jb = jobs[i];
+        std::memset(&jb, 0, sizeof(jb));
+        jb.g.d = d;
+        ds.ncells = 1;
+        for (int k = 0; k < d; ++k) {
+            const double l = lo[(size_t)i * d + k], h = hi[(size_t)i * d + k];
+            const int64_t m = M[(size_t)i * d + k];
+            if (m < 2 || m > (1 << 20)) return fail(KDEFFT_ERR_ARG, "M_k must be in [2, 2^20]");
+            if (!(h > l) || !std::isfinite(l) || !std::isfinite(h)) return fail(KDEFFT_ERR_ARG, "need lo_k < hi_k, finite");
+            ds.lo[k] = l;
+            ds.hi[k] = h;
+            ds.M[k] = m;
+            ds.delta[k] = (h - l) / (double)(m - 1);   // Eq. 16
+            jb.g.lo[k] = l;
+            jb.g.hi[k] = h;
+            jb.g.delta[k] = ds.delta[k];
+            jb.g.M[k] = m;
+            ds.ncells *= m;
+        }
+        if (ds.ncells > (1LL << 31)) return fail(KDEFFT_ERR_UNSUPPORTED, "grid too large");
+        while (K > 8 && (double)n[i] * std::ldexp(1.0, K) >= std::ldexp(1.0, 63)) --K;
+        if (!is_device_ptr(X[i])) {
+            xoff[i] = totx;
+            totx += n[i] * d;
+        }
+        coff[i] = totcells;
+        totcells += (ds.ncells + 3) & ~3LL;   // 16-byte aligned views
+        jb.n = n[i];
+        jb.ncells = ds.ncells;
+        jb.mblk = (int)std::min<long long>(64, (n[i] + 255) / 256);
+    }
+    // device memory: the samples given on the host, the counts of every
+    // dataset (one pool the datasets share), fixed-point accumulators, and
+    // outside counters | means | moment partials
+    DevBuf xbuf;
+    if (totx) KCHK(xbuf.ensure(sizeof(double) * totx));
+    auto pool = std::make_shared<DevBuf>();
+    KCHK(pool->ensure(sizeof(float) * std::max<long long>(totcells, 1)));
+    KCHK(c->binfix.ensure(8 * (size_t)std::max<long long>(totcells, 1)));
+    long long totpart = 0;
+    for (int i = 0; i < nds; ++i) totpart += (long long)jobs[i].mblk * d * d;
+    DevBuf misc;
+    const size_t nmisc = (size_t)nds * (1 + 4) + (size_t)totpart;
+    KCHK(misc.ensure(sizeof(double) * nmisc));
+    KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * nds, c->stream));
+    KCU(cudaMemsetAsync(c->binfix.p, 0, 8 * (size_t)totcells, c->stream));
+    unsigned long long* dOut = (unsigned long long*)misc.p;
+    double* dMean = (double*)misc.p + nds;
+    double* dPart = dMean + (size_t)nds * 4;
+    KCHK(c->binjobs.ensure(sizeof(BinJob) * nds * 4));
+    BinJob* jd = (BinJob*)c->binjobs.p;
+    long long po = 0;
+    for (int i = 0; i < nds; ++i) {
+        BinJob& jb = jobs[i];
+        if (xoff[i] >= 0) {
+            double* dst = (double*)xbuf.p + xoff[i];
+            KCU(cudaMemcpyAsync(dst, X[i], sizeof(double) * n[i] * d, cudaMemcpyHostToDevice, c->stream));
+            c->h2d += (int64_t)(sizeof(double) * n[i] * d);
+            jb.X = dst;
+        } else {
+            jb.X = X[i];
+        }
+        jb.fix = (unsigned long long*)c->binfix.p + coff[i];
+        jb.counts = (float*)pool->p + coff[i];
+        jb.outside = dOut + i;
+        jb.part = dPart + po;
+        jb.mean = dMean + (size_t)i * 4;
+        po += (long long)jb.mblk * d * d;
+        dss[i]->pool = pool;
+        dss[i]->counts.view(jb.counts, sizeof(float) * (size_t)dss[i]->ncells);
+    }
+    const double qscale = std::ldexp(1.0, K);
+    double by = 0.0, fl = 0.0;
+    for (int i = 0; i < nds; ++i) {
+        by += (double)n[i] * d * 8.0 + 4.0 * (double)dss[i]->ncells;
+        fl += (double)n[i] * (1 << d) * 2.0;
+    }
+    cudaEvent_t evb = prof_start(c);
+    c->launches++;   // phases 0 and 1
+    KCU(launch_bin_many(jobs.data(), jd, nds, 0, qscale, c->stream));
+    KCU(launch_bin_many(jobs.data(), jd + nds, nds, 1, qscale, c->stream));
+    prof_stop(c, evb, "bin", by, fl);
+    c->launches += 2;   // the two moment passes
+    KCU(launch_bin_many(jobs.data(), jd + 2 * nds, nds, 2, qscale, c->stream));
+    std::vector<double> part((size_t)totpart);
+    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * totpart, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    std::vector<double> means((size_t)nds * 4, 0.0);
+    po = 0;
+    for (int i = 0; i < nds; ++i) {
+        for (int b = 0; b < jobs[i].mblk; ++b)
+            for (int k = 0; k < d; ++k) means[(size_t)i * 4 + k] += part[(size_t)(po + (long long)b * d + k)];
+        for (int k = 0; k < d; ++k) means[(size_t)i * 4 + k] /= (double)n[i];
+        po += (long long)jobs[i].mblk * d * d;
+    }
+    KCU(cudaMemcpyAsync(dMean, means.data(), sizeof(double) * nds * 4, cudaMemcpyHostToDevice, c->stream));
+    KCU(launch_bin_many(jobs.data(), jd + 3 * nds, nds, 3, qscale, c->stream));
+    std::vector<unsigned long long> nout(nds);
+    KCU(cudaMemcpyAsync(nout.data(), dOut, sizeof(unsigned long long) * nds, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * totpart, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    po = 0;
+    for (int i = 0; i < nds; ++i) {
+        double hc[16] = {0};
+        for (int b = 0; b < jobs[i].mblk; ++b)
+            for (int v = 0; v < d * d; ++v) hc[v] += part[(size_t)(po + (long long)b * d * d + v)];
+        po += (long long)jobs[i].mblk * d * d;
+        for (int v = 0; v < d * d; ++v) dss[i]->cov[v] = (n[i] > 1) ? hc[v] / (double)(n[i] - 1) : 0.0;
+        if (nout[i] > 0 && o.outside_policy == KDEFFT_OUTSIDE_ERROR)
+            return fail(KDEFFT_ERR_OUTSIDE_GRID, "dataset " + std::to_string(i) + ": " + std::to_string(nout[i]) +
+                                                     " sample points outside the grid");
+        dss[i]->dropped = (int64_t)nout[i];
+    }
+    for (int i = 0; i < nds; ++i) {
+        out[i] = dss[i].release();
+        c->datasets.push_back(out[i]);
+    }
     return KDEFFT_OK;
 }
 

@@ -243,6 +243,117 @@ cudaError_t launch_moments(const double* X, long long n, int d, int pass, const 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ batched binning
+__device__ __forceinline__ int bin_job_of(const BinJob* __restrict__ jobs, int n, long long b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].blk0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kBinPtsPerBlock = 256 * 8;
+constexpr int kCellsPerBlock = 256 * 4;
+
+__global__ void __launch_bounds__(256) k_bin_many(const BinJob* __restrict__ jobs, int njobs, int phase,
+                                                  double qscale) {
+    const BinJob& jb = jobs[bin_job_of(jobs, njobs, blockIdx.x)];
+    const long long b = (long long)blockIdx.x - jb.blk0;
+    const GridDesc& g = jb.g;
+    const int d = g.d;
+    if (phase == 0) {
+        long long stride[MAXD];
+        {
+            long long s = 1;
+            for (int k = d - 1; k >= 0; --k) {
+                stride[k] = s;
+                s *= g.M[k];
+            }
+        }
+        const int ncorner = 1 << d;
+        unsigned long long nout = 0;
+        const long long i0 = b * kBinPtsPerBlock;
+        const long long i1 = i0 + kBinPtsPerBlock < jb.n ? i0 + kBinPtsPerBlock : jb.n;
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            double x[MAXD], f[MAXD];
+            long long l[MAXD], base;
+            for (int k = 0; k < d; ++k) x[k] = jb.X[i * d + k];
+            if (!locate(x, g, l, f, &base)) {
+                ++nout;
+                continue;
+            }
+            for (int c = 0; c < ncorner; ++c) {
+                double w = 1.0;
+                long long idx = base;
+                for (int k = 0; k < d; ++k) {
+                    const int bk = (c >> k) & 1;
+                    w = __dmul_rn(w, bk ? f[k] : __dsub_rn(1.0, f[k]));
+                    idx += bk * stride[k];
+                }
+                atomicAdd(jb.fix + idx, __double2ull_rn(w * qscale));
+            }
+        }
+        if (nout) atomicAdd(jb.outside, nout);
+    } else if (phase == 1) {
+        const double unit = 1.0 / qscale;
+        const long long c0 = b * kCellsPerBlock;
+        const long long c1 = c0 + kCellsPerBlock < jb.ncells ? c0 + kCellsPerBlock : jb.ncells;
+        for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) jb.counts[c] = (float)((double)jb.fix[c] * unit);
+    } else {
+        // moments: block b of mblk takes the points i = b, b + mblk, ... in steps of blockDim
+        const int nv = (phase == 2) ? d : d * d;
+        double acc[MAXD * MAXD];
+        for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+        for (long long i = b * blockDim.x + threadIdx.x; i < jb.n; i += (long long)jb.mblk * blockDim.x) {
+            double x[MAXD];
+            for (int k = 0; k < d; ++k) x[k] = jb.X[i * d + k] - (phase == 3 ? jb.mean[k] : 0.0);
+            if (phase == 2) {
+                for (int k = 0; k < d; ++k) acc[k] += x[k];
+            } else {
+                for (int a = 0; a < d; ++a)
+                    for (int c = 0; c < d; ++c) acc[a * d + c] += x[a] * x[c];
+            }
+        }
+        __shared__ double red[8][MAXD * MAXD];
+        for (int v = 0; v < nv; ++v) {
+            double t = acc[v];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][v] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+            jb.part[b * nv + threadIdx.x] = t;
+        }
+    }
+}
+
+cudaError_t launch_bin_many(BinJob* jobs_h, BinJob* jobs_d, int n, int phase, double qscale, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = 0;
+    for (int k = 0; k < n; ++k) {
+        BinJob& jb = jobs_h[k];
+        jb.blk0 = blocks;
+        if (phase == 0)
+            blocks += (jb.n + kBinPtsPerBlock - 1) / kBinPtsPerBlock;
+        else if (phase == 1)
+            blocks += (jb.ncells + kCellsPerBlock - 1) / kCellsPerBlock;
+        else
+            blocks += jb.mblk;
+    }
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(jobs_d, jobs_h, sizeof(BinJob) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_bin_many<<<(unsigned)blocks, 256, 0, st>>>(jobs_d, n, phase, qscale);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_bin_linear<unsigned long long>(const double*, long long, const GridDesc&,
                                                            unsigned long long*, long long, unsigned long long*, double,
                                                            int, cudaStream_t);

@@ -294,6 +294,27 @@ cudaError_t launch_bin_simple(const double* X, long long n, const GridDesc& g, i
 template <typename real>
 cudaError_t launch_int_to_real(const int* src, real* dst, long long n, cudaStream_t st);
 cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t st);
+// Batched binning of many datasets (FP32 linear binning in fixed point):
+// one launch per phase over a job table, each CTA within one job.
+//   phase 0: bin the points into the job's fixed-point accumulators
+//            (fix, zeroed by the caller) and count the outside points;
+//   phase 1: convert the accumulators to FP32 counts;
+//   phase 2: the job's mblk block partials of the coordinate sums (mean
+//            pass) or, phase 3, of the centred products (mean given).
+struct BinJob {
+    const double* X;
+    long long n, ncells;
+    GridDesc g;
+    unsigned long long* fix;
+    float* counts;
+    unsigned long long* outside;
+    double* part;          // mblk x d (phase 2) or mblk x d x d (phase 3)
+    const double* mean;    // phase 3
+    int mblk;
+    long long blk0;        // set by the launcher
+};
+cudaError_t launch_bin_many(BinJob* jobs_h, BinJob* jobs_d, int n, int phase, double qscale, cudaStream_t st);
+
 // pass 0: out[blk*d + k] = block sums of X_ik; pass 1: out[blk*d*d + a*d+b] =
 // block sums of (X_ia - mean_a)(X_ib - mean_b), blk < moments_blocks(n, nsm)
 int moments_blocks(long long n, int nsm);
