@@ -175,8 +175,8 @@ def run_ours(args):
 
         def step(X):
             ds = ctx.bin(X, w.lo, w.hi, w.M)
-            H1, f1, e1 = ds.select_H(LSCV, n_starts=args.n_starts, max_iter=args.max_iter)
-            H2, f2, e2 = ds.select_H(SCV, G=w.G, n_starts=args.n_starts, max_iter=args.max_iter)
+            (H1, f1, e1), (H2, f2, e2) = ds.select_H_many([LSCV, SCV], G=w.G, n_starts=args.n_starts,
+                                                          max_iter=args.max_iter)
             ds.close()
             return e1 + e2, (H1, f1, H2, f2)
         workload_desc = (w.name + ": bin + full LSCV and SCV minimisation (3 free entries of H, adjoint "

@@ -244,6 +244,18 @@ int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G,
                     int n_starts, int max_iter, double* H_out, double* f_out,
                     int64_t* n_evals);
 
+/* Several criteria minimised on one dataset: methods[m] (KDEFFT_LSCV, _SCV
+ * or _PI) for m < nmethods, each with the arguments and the result of
+ * kdefft_select_H (the same starts from H0, the same G).  H_out: nmethods x
+ * d x d; f_out and n_evals: nmethods each (may be NULL).  Where the
+ * device-resident d = 2 search covers two of the criteria they run in one
+ * launch, one CTA per start of either, against one autocorrelation box
+ * sized for both; the others run one after another.  Every result is the
+ * one kdefft_select_H gives for that criterion on a dataset whose
+ * autocorrelation box is already this large. */
+int kdefft_select_H_multi(kdefft_ds ds, int nmethods, const int* methods, const double* H0, const double* G,
+                          int n_starts, int max_iter, double* H_out, double* f_out, int64_t* n_evals);
+
 /* Bandwidth classes (Sec. 3): F, full SPD matrices (the paper's subject);
  * D, diagonal matrices; S, scalar multiples h^2 I of the identity. */
 enum { KDEFFT_H_FULL = 0, KDEFFT_H_DIAG = 1, KDEFFT_H_SCALAR = 2 };
@@ -339,6 +351,19 @@ int kdefft_set_graphs(kdefft_ctx ctx, int on);
  * graphs captured, graph replays.  Any pointer may be NULL. */
 int kdefft_runtime_stats(kdefft_ctx ctx, int64_t* shapes_tuned,
                          int64_t* graphs_captured, int64_t* graph_replays);
+
+/* Device memory of datasets.  Blocks a destroyed dataset (or a growing
+ * buffer of one) held go back to a per-context cache and serve later
+ * datasets of the context, in the order of its stream, so that binning a
+ * dataset per step allocates nothing once the cache holds blocks of the
+ * sizes needed.  At most 16 GiB stay cached (the largest free blocks beyond
+ * that are released); an allocation that fails releases the cache and
+ * retries once.  kdefft_memory_stats: bytes held in free blocks, blocks
+ * served from the cache, blocks allocated from CUDA (any pointer may be
+ * NULL).  kdefft_trim releases every free block (synchronising the device,
+ * as cudaFree does).  The context releases them when destroyed. */
+int kdefft_memory_stats(kdefft_ctx ctx, int64_t* cached_bytes, int64_t* hits, int64_t* misses);
+int kdefft_trim(kdefft_ctx ctx);
 
 /* LSCV value and gradient for one bandwidth without allocating any memory.
  * The paper has no counterpart: this is for callers that cannot allocate at

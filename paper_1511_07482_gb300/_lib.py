@@ -33,6 +33,7 @@ EXPORTS = [
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
     "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class", "kdefft_bin_many",
+    "kdefft_select_H_multi", "kdefft_memory_stats", "kdefft_trim",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -100,6 +101,9 @@ def load(path: str = LIB_PATH):
         "kdefft_ise_mixture": (I, [P, P, I, I, P, P, P, P]),
         "kdefft_set_graphs": (I, [P, I]),
         "kdefft_runtime_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "kdefft_memory_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "kdefft_trim": (I, [P]),
+        "kdefft_select_H_multi": (I, [P, I, P, P, P, I, I, P, P, P]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -223,6 +227,16 @@ class Context:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _check(load().kdefft_runtime_stats(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return {"shapes_tuned": a.value, "graphs_captured": b.value, "graph_replays": c.value}
+
+    def memory_stats(self):
+        """{"cached_bytes", "hits", "misses"} of the context's block cache."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().kdefft_memory_stats(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"cached_bytes": a.value, "hits": b.value, "misses": c.value}
+
+    def trim(self):
+        """Release the cached free device blocks."""
+        _check(load().kdefft_trim(self.h))
 
     def profile(self, mode: int = 1):
         """1: reset counters and time every kernel with CUDA events; 2: keep
@@ -464,3 +478,19 @@ class Dataset:
                                              pG, int(n_starts), int(max_iter or 0),
                                              Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
         return Hout, f.value, ne.value
+
+    def select_H_many(self, methods, H0=None, G=None, n_starts=1, max_iter=None):
+        """select_H (quasi-Newton, full H) for several criteria on this
+        dataset; two criteria the device search covers share one launch.
+        Returns [(H, f, evals)] in the order of `methods`."""
+        ms = np.ascontiguousarray(np.asarray(methods, dtype=np.int32))
+        k = int(ms.size)
+        Ha, pH = _host_f64(H0) if H0 is not None else (None, None)
+        Ga, pG = _host_f64(G) if G is not None else (None, None)
+        Hout = np.zeros((k, self.d, self.d))
+        f = np.zeros(k)
+        ne = np.zeros(k, dtype=np.int64)
+        _check(load().kdefft_select_H_multi(self.h, k, ms.ctypes.data_as(C.c_void_p), pH, pG, int(n_starts),
+                                            int(max_iter or 0), Hout.ctypes.data_as(C.c_void_p),
+                                            f.ctypes.data_as(C.c_void_p), ne.ctypes.data_as(C.c_void_p)))
+        return [(Hout[m], float(f[m]), int(ne[m])) for m in range(k)]

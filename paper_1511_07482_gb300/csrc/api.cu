@@ -49,11 +49,52 @@ static int fail(int code, const std::string& msg) {
     } while (0)
 
 // ============================================================ buffers
+// Device blocks of datasets return, when a dataset is destroyed or a buffer
+// grows, to their context's cache and are reused by later datasets.  All of
+// a context's work runs in the order of its stream, so a block taken from
+// the cache is only touched after the work that used it before.  A dataset
+// per step then costs no cudaMalloc and no cudaFree (each cudaFree
+// synchronises the device).
+struct BlockCache {
+    std::multimap<size_t, void*> blocks;   // capacity -> free block
+    size_t bytes = 0;                      // held in free blocks
+    size_t limit = (size_t)16 << 30;       // free blocks beyond this are returned to CUDA
+    int64_t hits = 0, misses = 0;
+    // a free block of at least `want` bytes and at most twice that, or null
+    void* take(size_t want, size_t& cap) {
+        auto it = blocks.lower_bound(want);
+        if (it == blocks.end() || it->first > 2 * want) return nullptr;
+        cap = it->first;
+        void* q = it->second;
+        blocks.erase(it);
+        bytes -= cap;
+        ++hits;
+        return q;
+    }
+    void give(void* q, size_t cap) {
+        blocks.emplace(cap, q);
+        bytes += cap;
+        while (bytes > limit && !blocks.empty()) {   // the largest go first
+            auto it = std::prev(blocks.end());
+            cudaFree(it->second);
+            bytes -= it->first;
+            blocks.erase(it);
+        }
+    }
+    void trim() {
+        for (auto& kv : blocks) cudaFree(kv.second);
+        blocks.clear();
+        bytes = 0;
+    }
+};
+
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
     bool owner = true;   // false: a view into memory another buffer owns
+    BlockCache* cache = nullptr;   // where owned blocks come from and go back to (null: cudaMalloc / cudaFree)
     DevBuf() = default;
+    explicit DevBuf(BlockCache* bc) : cache(bc) {}
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf() { release(); }
@@ -65,21 +106,41 @@ struct DevBuf {
     }
     int ensure(size_t bytes) {
         if (bytes <= cap) return KDEFFT_OK;
-        if (p && owner) cudaFree(p);
-        owner = true;
-        p = nullptr;
-        cap = 0;
+        release();
         size_t want = std::max(bytes, (size_t)4096);
+        if (cache) {
+            size_t got = 0;
+            if (void* q = cache->take(want, got)) {
+                p = q;
+                cap = got;
+                return KDEFFT_OK;
+            }
+            ++cache->misses;
+        }
         want = want + want / 4;
-        if (cudaMalloc(&p, want) != cudaSuccess) {
-            p = nullptr;
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, want);
+        if (e != cudaSuccess && cache && cache->bytes) {   // give the cached blocks back and try once more
+            cudaGetLastError();
+            cache->trim();
+            q = nullptr;
+            e = cudaMalloc(&q, want);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
             return fail(KDEFFT_ERR_ALLOC, "device allocation of " + std::to_string(want) + " bytes failed");
         }
+        p = q;
         cap = want;
         return KDEFFT_OK;
     }
     void release() {
-        if (p && owner) cudaFree(p);
+        if (p && owner) {
+            if (cache)
+                cache->give(p, cap);
+            else
+                cudaFree(p);
+        }
         p = nullptr;
         cap = 0;
         owner = true;
@@ -434,6 +495,7 @@ struct kdefft_ctx_s {
     int* errflag = nullptr;   // device flag: a bounded device-side wait gave up
     int max_cluster = 16;     // largest cluster the fused engine may launch
     bool device_select = true;   // d = 2 FP32 selections run as one device-resident launch
+    BlockCache cache;         // freed dataset blocks for reuse (declared before the buffers it serves)
     DevBuf sel_buf;           // device tables and start states of the device-resident selection
     DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
     DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
@@ -595,6 +657,11 @@ struct kdefft_ds_s {
     DevBuf ac64, ac32;
     std::shared_ptr<DevBuf> pool;   // memory that `counts` views (datasets binned together share one)
 };
+
+// dataset buffers draw on the context's block cache
+static void attach_cache(kdefft_ds_s& ds, kdefft_ctx c) {
+    for (DevBuf* b : {&ds.counts, &ds.counts_i, &ds.counts64, &ds.ac64, &ds.ac32}) b->cache = &c->cache;
+}
 
 static int twiddle_offset(kdefft_ctx c, int P) {
     auto it = c->tw_off.find(P);
@@ -1477,7 +1544,7 @@ static int ensure_spectra(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, s
         std::vector<int> key = spectrum_key(ds, P, sizeof(real));
         if (ds->spectra.count(key) || queued.count({ds, key})) continue;
         queued.insert({ds, key});
-        auto buf = std::make_shared<DevBuf>();
+        auto buf = std::make_shared<DevBuf>(&c->cache);
         KCHK(buf->ensure(sizeof(real) * spec_elems(ds->d, P)));
         Item<real> item;
         std::memset(&item, 0, sizeof(item));
@@ -2330,6 +2397,22 @@ int kdefft_runtime_stats(kdefft_ctx c, int64_t* shapes_tuned, int64_t* graphs_ca
     return KDEFFT_OK;
 }
 
+int kdefft_memory_stats(kdefft_ctx c, int64_t* cached_bytes, int64_t* hits, int64_t* misses) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    if (cached_bytes) *cached_bytes = (int64_t)c->cache.bytes;
+    if (hits) *hits = c->cache.hits;
+    if (misses) *misses = c->cache.misses;
+    return KDEFFT_OK;
+}
+
+int kdefft_trim(kdefft_ctx c) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    KCU(cudaSetDevice(c->device));
+    KCU(cudaStreamSynchronize(c->stream));
+    c->cache.trim();
+    return KDEFFT_OK;
+}
+
 int kdefft_profile(kdefft_ctx c, int mode) {
     if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
     if (mode == 1 || mode == 0) {
@@ -2368,6 +2451,7 @@ int kdefft_destroy(kdefft_ctx c) {
     cudaStreamSynchronize(c->stream);
     for (kdefft_ds ds : c->datasets) ds_free(ds);
     c->datasets.clear();
+    c->cache.trim();
     c->tw32.release();
     c->tw64.release();
     c->scratch.release();
@@ -2412,6 +2496,7 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     KCU(cudaSetDevice(c->device));
     std::unique_ptr<kdefft_ds_s> ds(new kdefft_ds_s());
     ds->ctx = c;
+    attach_cache(*ds, c);
     ds->d = d;
     ds->n = n;
     ds->opts = o;
@@ -2435,7 +2520,7 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     }
     if (ds->ncells > (1LL << 31)) return fail(KDEFFT_ERR_UNSUPPORTED, "grid too large");
     // sample on the device
-    DevBuf xbuf;
+    DevBuf xbuf(&c->cache);
     const double* dX = X;
     if (!is_device_ptr(X)) {
         KCHK(xbuf.ensure(sizeof(double) * n * d));
@@ -2445,7 +2530,7 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     }
     // outside counter | mean | block partials of the moments
     const int mblk = moments_blocks(n, c->nsm);
-    DevBuf misc;
+    DevBuf misc(&c->cache);
     KCHK(misc.ensure(sizeof(double) * (16 + (size_t)mblk * d * d)));
     KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
     unsigned long long* dOut = (unsigned long long*)misc.p;
@@ -2546,6 +2631,7 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
         dss[i].reset(new kdefft_ds_s());
         kdefft_ds_s& ds = *dss[i];
         ds.ctx = c;
+        attach_cache(ds, c);
         ds.d = d;
         ds.n = n[i];
         ds.opts = o;
@@ -2583,14 +2669,14 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
     // device memory: the samples given on the host, the counts of every
     // dataset (one pool the datasets share), fixed-point accumulators, and
     // outside counters | means | moment partials
-    DevBuf xbuf;
+    DevBuf xbuf(&c->cache);
     if (totx) KCHK(xbuf.ensure(sizeof(double) * totx));
-    auto pool = std::make_shared<DevBuf>();
+    auto pool = std::make_shared<DevBuf>(&c->cache);
     KCHK(pool->ensure(sizeof(float) * std::max<long long>(totcells, 1)));
     KCHK(c->binfix.ensure(8 * (size_t)std::max<long long>(totcells, 1)));
     long long totpart = 0;
     for (int i = 0; i < nds; ++i) totpart += (long long)jobs[i].mblk * d * d;
-    DevBuf misc;
+    DevBuf misc(&c->cache);
     const size_t nmisc = (size_t)nds * (1 + 4) + (size_t)totpart;
     KCHK(misc.ensure(sizeof(double) * nmisc));
     KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * nds, c->stream));
@@ -3303,35 +3389,39 @@ void grad_theta(const Opt& o, const double* th, const double* g, double* gt) {
 
 }  // namespace
 
-// Device-resident selection for d = 2 (FP32 dataset, LSCV of Eq. 10 or SCV,
-// minimal padding): returns KDEFFT_ERR_UNSUPPORTED without side effects when
-// the case is not covered, so that the caller runs the host optimiser.
-static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::vector<std::vector<double>>& th0,
-                           int max_iter, std::vector<std::vector<double>>& th_out, std::vector<double>& f_out,
-                           int64_t* evals_out) {
+// Whether the device-resident search covers a criterion on this dataset:
+// d = 2, FP32, minimal padding, LSCV of Eq. 10 or SCV.
+static bool select2d_covered(kdefft_ds ds, int method) {
     kdefft_ctx c = ds->ctx;
-    if (!c->device_select || ds->d != 2 || ds->opts.precision != KDEFFT_FP32 || ds->opts.P_rule != KDEFFT_P_MINIMAL ||
-        ds->opts.L_basis == KDEFFT_L_FULL || (method == KDEFFT_LSCV && ds->opts.exact_loo) ||
-        (method == KDEFFT_SCV && ds->opts.L_basis == KDEFFT_L_PAPER) ||
-        (method != KDEFFT_LSCV && method != KDEFFT_SCV))
-        return KDEFFT_ERR_UNSUPPORTED;
-    const int nst = (int)th0.size();
-    const int M0 = (int)ds->M[0], M1 = (int)ds->M[1];
-    if (c->lag) {
-        // Lag domain: one CTA per start.  The autocorrelation box covers 2.5
-        // times the largest support among the starts (the bandwidth may grow
-        // about 6-fold beyond the widest start); trial points needing more are
-        // outside this search's domain.
-        const Opt o{2, 3};
-        int Lmax[2] = {1, 1};
-        for (const auto& th : th0) {
+    return c->device_select && ds->d == 2 && ds->opts.precision == KDEFFT_FP32 &&
+           ds->opts.P_rule == KDEFFT_P_MINIMAL && ds->opts.L_basis != KDEFFT_L_FULL &&
+           !(method == KDEFFT_LSCV && ds->opts.exact_loo) && !(method == KDEFFT_SCV && ds->opts.L_basis == KDEFFT_L_PAPER) &&
+           (method == KDEFFT_LSCV || method == KDEFFT_SCV);
+}
+
+// The lag-domain device search for one or two criteria on one dataset in one
+// launch, one CTA per start.  The autocorrelation box covers 2.5 times the
+// largest support among all starts of all criteria (the bandwidth may grow
+// about 6-fold beyond the widest start); trial points needing more are
+// outside the search's domain.
+static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, const std::vector<Mat>& Gms,
+                               const std::vector<std::vector<std::vector<double>>>& th0s, int max_iter,
+                               std::vector<std::vector<std::vector<double>>>& th_outs,
+                               std::vector<std::vector<double>>& f_outs, std::vector<int64_t>& evals_out) {
+    kdefft_ctx c = ds->ctx;
+    const int nm = (int)methods.size();
+    if (nm < 1 || nm > 2) return KDEFFT_ERR_UNSUPPORTED;
+    const Opt o{2, 3};
+    int Lmax[2] = {1, 1};
+    for (int m = 0; m < nm; ++m)
+        for (const auto& th : th0s[m]) {
             const Mat H = theta_to_H(o, th.data());
             double B[4];
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b) {
                     const double h = H(a, b);
-                    if (method == KDEFFT_SCV)
-                        B[a * 2 + b] = 2.0 * h + 2.0 * Gm(a, b);
+                    if (methods[m] == KDEFFT_SCV)
+                        B[a * 2 + b] = 2.0 * h + 2.0 * Gms[m](a, b);
                     else
                         B[a * 2 + b] = (ds->opts.L_basis == KDEFFT_L_WIDEST ? 2.0 : 1.0) * h;
                 }
@@ -3343,71 +3433,108 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
                 Lmax[k] = std::max(Lmax[k], (int)std::max(1.0, v));
             }
         }
-        std::array<int, 4> need{0, 0, 0, 0};
-        for (int k = 0; k < 2; ++k)
-            need[k] = (int)std::min<long long>(ds->M[k] - 1, std::max(8, (int)std::ceil(2.5 * Lmax[k])));
-        const int ar = ensure_autocorr_many(c, {{ds, need}});
-        if (ar == KDEFFT_ERR_UNSUPPORTED) return KDEFFT_ERR_UNSUPPORTED;
-        KCHK(ar);
-        const size_t bT = sizeof(SelStart) * nst;
-        KCHK(c->sel_buf.ensure(bT));
-        std::vector<SelStart> st(nst);
-        for (int i = 0; i < nst; ++i) {
-            std::memset(&st[i], 0, sizeof(SelStart));
-            for (int k = 0; k < 3; ++k) st[i].th[k] = th0[i][k];
+    std::array<int, 4> need{0, 0, 0, 0};
+    for (int k = 0; k < 2; ++k)
+        need[k] = (int)std::min<long long>(ds->M[k] - 1, std::max(8, (int)std::ceil(2.5 * Lmax[k])));
+    const int ar = ensure_autocorr_many(c, {{ds, need}});
+    if (ar == KDEFFT_ERR_UNSUPPORTED) return KDEFFT_ERR_UNSUPPORTED;
+    KCHK(ar);
+    std::vector<int> first(nm + 1, 0);
+    for (int m = 0; m < nm; ++m) first[m + 1] = first[m] + (int)th0s[m].size();
+    const int nst = first[nm];
+    const size_t bT = sizeof(SelStart) * nst;
+    KCHK(c->sel_buf.ensure(bT));
+    std::vector<SelStart> st(nst);
+    for (int m = 0; m < nm; ++m)
+        for (int i = 0; i < (int)th0s[m].size(); ++i) {
+            SelStart& x = st[first[m] + i];
+            std::memset(&x, 0, sizeof(SelStart));
+            for (int k = 0; k < 3; ++k) x.th[k] = th0s[m][i][k];
         }
-        SelStart* dst = (SelStart*)c->sel_buf.p;
-        KCU(cudaMemcpyAsync(dst, st.data(), bT, cudaMemcpyHostToDevice, c->stream));
-        c->h2d += (int64_t)bT;
-        SelectParams prm{};
-        prm.method = (method == KDEFFT_LSCV) ? 0 : 1;
-        prm.max_iter = max_iter;
-        prm.widest = (method == KDEFFT_LSCV && ds->opts.L_basis == KDEFFT_L_WIDEST) ? 1 : 0;
-        prm.M0 = M0;
-        prm.M1 = M1;
-        prm.Lcap = ds->acA[0];
-        prm.Lcap1 = ds->acA[1];
-        prm.n = (double)ds->n;
-        prm.inv_n = 1.0 / prm.n;
-        prm.inv_n2 = 1.0 / (prm.n * prm.n);
-        prm.tau = ds->opts.tau;
-        prm.delta0 = ds->delta[0];
-        prm.delta1 = ds->delta[1];
+    SelStart* dst = (SelStart*)c->sel_buf.p;
+    KCU(cudaMemcpyAsync(dst, st.data(), bT, cudaMemcpyHostToDevice, c->stream));
+    c->h2d += (int64_t)bT;
+    SelectParams prm[2]{};
+    for (int m = 0; m < nm; ++m) {
+        SelectParams& q = prm[m];
+        const int method = methods[m];
+        q.method = (method == KDEFFT_LSCV) ? 0 : 1;
+        q.max_iter = max_iter;
+        q.widest = (method == KDEFFT_LSCV && ds->opts.L_basis == KDEFFT_L_WIDEST) ? 1 : 0;
+        q.M0 = (int)ds->M[0];
+        q.M1 = (int)ds->M[1];
+        q.Lcap = ds->acA[0];
+        q.Lcap1 = ds->acA[1];
+        q.n = (double)ds->n;
+        q.inv_n = 1.0 / q.n;
+        q.inv_n2 = 1.0 / (q.n * q.n);
+        q.tau = ds->opts.tau;
+        q.delta0 = ds->delta[0];
+        q.delta1 = ds->delta[1];
         for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) prm.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gm(a, b) : 0.0;
-        prm.errflag = c->errflag;
-        prm.acorr = (const float*)ds->ac32.p;
-        prm.A0 = ds->acA[0];
-        prm.A1 = ds->acA[1];
-        cudaEvent_t ev = prof_start(c);
-        KCU(launch_select2d_lag(prm, dst, nst, c->stream));
-        prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
-        KCU(cudaMemcpyAsync(st.data(), dst, bT, cudaMemcpyDeviceToHost, c->stream));
-        {
-            HostTimer w(c, "host:wait");
-            KCU(cudaStreamSynchronize(c->stream));
+            for (int b = 0; b < 2; ++b) q.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gms[m](a, b) : 0.0;
+        q.errflag = c->errflag;
+        q.acorr = (const float*)ds->ac32.p;
+        q.A0 = ds->acA[0];
+        q.A1 = ds->acA[1];
+    }
+    if (nm == 1) prm[1] = prm[0];
+    cudaEvent_t ev = prof_start(c);
+    KCU(launch_select2d_lag(prm[0], prm[1], first[1], dst, nst, c->stream));
+    prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
+    KCU(cudaMemcpyAsync(st.data(), dst, bT, cudaMemcpyDeviceToHost, c->stream));
+    {
+        HostTimer w(c, "host:wait");
+        KCU(cudaStreamSynchronize(c->stream));
+    }
+    c->d2h += (int64_t)bT;
+    if (c->prof && !c->pending.empty() && ev) {
+        double fl = 0.0, by = 0.0;
+        for (const SelStart& x : st) {
+            fl += x.flops;
+            by += x.bytes;
         }
-        c->d2h += (int64_t)bT;
-        if (c->prof && !c->pending.empty() && ev) {
-            double fl = 0.0, by = 0.0;
-            for (const SelStart& x : st) {
-                fl += x.flops;
-                by += x.bytes;
-            }
-            c->pending.back().flops = fl;
-            c->pending.back().bytes = by;
+        c->pending.back().flops = fl;
+        c->pending.back().bytes = by;
+    }
+    prof_flush(c);
+    KCHK(check_errflag(c));
+    th_outs.assign(nm, {});
+    f_outs.assign(nm, {});
+    evals_out.assign(nm, 0);
+    for (int m = 0; m < nm; ++m) {
+        const int k = first[m + 1] - first[m];
+        th_outs[m].assign(k, std::vector<double>(3));
+        f_outs[m].assign(k, INFINITY);
+        for (int i = 0; i < k; ++i) {
+            const SelStart& x = st[first[m] + i];
+            for (int e = 0; e < 3; ++e) th_outs[m][i][e] = x.th[e];
+            f_outs[m][i] = x.f;
+            evals_out[m] += x.evals;
         }
-        prof_flush(c);
-        KCHK(check_errflag(c));
-        th_out.assign(nst, std::vector<double>(3));
-        f_out.assign(nst, INFINITY);
-        int64_t ev_total = 0;
-        for (int i = 0; i < nst; ++i) {
-            for (int k = 0; k < 3; ++k) th_out[i][k] = st[i].th[k];
-            f_out[i] = st[i].f;
-            ev_total += st[i].evals;
-        }
-        *evals_out = ev_total;
+    }
+    return KDEFFT_OK;
+}
+
+// Device-resident selection for d = 2 (FP32 dataset, LSCV of Eq. 10 or SCV,
+// minimal padding): returns KDEFFT_ERR_UNSUPPORTED without side effects when
+// the case is not covered, so that the caller runs the host optimiser.
+static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::vector<std::vector<double>>& th0,
+                           int max_iter, std::vector<std::vector<double>>& th_out, std::vector<double>& f_out,
+                           int64_t* evals_out) {
+    kdefft_ctx c = ds->ctx;
+    if (!select2d_covered(ds, method)) return KDEFFT_ERR_UNSUPPORTED;
+    const int nst = (int)th0.size();
+    const int M0 = (int)ds->M[0], M1 = (int)ds->M[1];
+    if (c->lag) {
+        std::vector<std::vector<std::vector<double>>> tho;
+        std::vector<std::vector<double>> fo;
+        std::vector<int64_t> ev;
+        const int r = device_select2d_lag(ds, {method}, {Gm}, {th0}, max_iter, tho, fo, ev);
+        if (r != KDEFFT_OK) return r;
+        th_out = tho[0];
+        f_out = fo[0];
+        *evals_out = ev[0];
         return KDEFFT_OK;
     }
     auto pmin = [](int m) {
@@ -3592,6 +3719,65 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
 // device-resident search uses the same limit.
 static constexpr int kMaxHalvings = 12;
 
+// Start points of the multi-start search: Hstart, then dilations (factors
+// 2^{-1}..2^{1} in half powers of two) and plane rotations of it.
+static std::vector<Mat> start_bandwidths(const Mat& Hstart, int n_starts) {
+    const int d = Hstart.d;
+    std::vector<Mat> out(n_starts, Hstart);
+    for (int s = 1; s < n_starts; ++s) {
+        const double fac = std::pow(2.0, ((s % 5) - 2) * 0.5);
+        const double ang = 0.35 * s;
+        const int a = (s - 1) % std::max(1, d - 1), b = (d > 1) ? a + 1 : a;
+        Mat Rt;
+        Rt.d = d;
+        for (int i = 0; i < d; ++i) Rt(i, i) = 1.0;
+        if (d > 1) {
+            Rt(a, a) = std::cos(ang);
+            Rt(b, b) = std::cos(ang);
+            Rt(a, b) = -std::sin(ang);
+            Rt(b, a) = std::sin(ang);
+        }
+        Mat T;
+        T.d = d;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                double sum = 0.0;
+                for (int k = 0; k < d; ++k)
+                    for (int l = 0; l < d; ++l) sum += Rt(i, k) * Hstart(k, l) * Rt(j, l);
+                T(i, j) = fac * sum;
+            }
+        out[s] = T;
+    }
+    return out;
+}
+
+// End of a device-resident search: the best start's end point, and the
+// objective there through the regular evaluation path (the search compared
+// its own FP32 values; SCV takes the FP64 route for its cancelling terms).
+// The LSCV value is evaluated with its gradient, as a caller checking
+// stationarity asks for it.
+static int finish_device_select(kdefft_ds ds, int method, const Mat& Gm, const std::vector<std::vector<double>>& tho,
+                                const std::vector<double>& fo, int64_t dev_evals, double* H_out, double* f_out,
+                                int64_t* n_evals) {
+    const int d = ds->d;
+    const Opt o{d, class_params(d, KDEFFT_H_FULL)};
+    int best = 0;
+    for (int s = 1; s < (int)fo.size(); ++s)
+        if (fo[s] < fo[best]) best = s;
+    if (!std::isfinite(fo[best])) return fail(KDEFFT_ERR_ARG, "no start point inside the search domain");
+    Mat Hb = theta_to_H(o, tho[best].data());
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
+    std::vector<double> v, gdummy;
+    if (method == KDEFFT_SCV)
+        KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
+    else
+        KCHK(eval_lscv(ds, H_out, 1, v, &gdummy));
+    if (f_out) *f_out = v[0];
+    if (n_evals) *n_evals = dev_evals + 1;
+    return KDEFFT_OK;
+}
+
 static int select_H_impl(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts, int max_iter,
                          bool nelder_mead, double* H_out, double* f_out, int64_t* n_evals, int hclass = KDEFFT_H_FULL) {
     if (!ds || !H_out) return fail(KDEFFT_ERR_ARG, "NULL argument");
@@ -3705,36 +3891,14 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
         bool fresh = true;   // the current direction comes from a reset (scaled steepest descent)
     };
     std::vector<State> st(n_starts);
-    for (int s = 0; s < n_starts; ++s) {
-        Mat Hs = Hstart;
-        if (s > 0) {
-            const double fac = std::pow(2.0, ((s % 5) - 2) * 0.5);
-            const double ang = 0.35 * s;
-            const int a = (s - 1) % std::max(1, d - 1), b = (d > 1) ? a + 1 : a;
-            Mat Rt;
-            Rt.d = d;
-            for (int i = 0; i < d; ++i) Rt(i, i) = 1.0;
-            if (d > 1) {
-                Rt(a, a) = std::cos(ang);
-                Rt(b, b) = std::cos(ang);
-                Rt(a, b) = -std::sin(ang);
-                Rt(b, a) = std::sin(ang);
-            }
-            Mat T;
-            T.d = d;
-            for (int i = 0; i < d; ++i)
-                for (int j = 0; j < d; ++j) {
-                    double sum = 0.0;
-                    for (int k = 0; k < d; ++k)
-                        for (int l = 0; l < d; ++l) sum += Rt(i, k) * Hstart(k, l) * Rt(j, l);
-                    T(i, j) = fac * sum;
-                }
-            Hs = T;
+    {
+        const std::vector<Mat> Hs0 = start_bandwidths(Hstart, n_starts);
+        for (int s = 0; s < n_starts; ++s) {
+            st[s].th.resize(p);
+            H_to_theta(o, Hs0[s], st[s].th.data());
+            st[s].Binv.assign((size_t)p * p, 0.0);
+            for (int i = 0; i < p; ++i) st[s].Binv[i * p + i] = 1.0;
         }
-        st[s].th.resize(p);
-        H_to_theta(o, Hs, st[s].th.data());
-        st[s].Binv.assign((size_t)p * p, 0.0);
-        for (int i = 0; i < p; ++i) st[s].Binv[i * p + i] = 1.0;
     }
     // the reported value at the chosen point: SCV iterations compare FP32
     // values, the reported one takes the FP64 route for the cancelling terms
@@ -3896,26 +4060,7 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
         std::vector<double> fo;
         int64_t dev_evals = 0;
         const int r = device_select2d(ds, method, Gm, ths, max_iter, tho, fo, &dev_evals);
-        if (r == KDEFFT_OK) {
-            int best = 0;
-            for (int s = 1; s < n_starts; ++s)
-                if (fo[s] < fo[best]) best = s;
-            if (!std::isfinite(fo[best])) return fail(KDEFFT_ERR_ARG, "no start point inside the search domain");
-            Mat Hb = theta_to_H(o, tho[best].data());
-            for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
-            // the value reported is the objective at H_out through the
-            // regular evaluation path (the search compared its own FP32 values)
-            // (with the gradient, as a caller checking stationarity asks for it)
-            std::vector<double> v, gdummy;
-            if (method == KDEFFT_SCV)
-                KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
-            else
-                KCHK(eval_lscv(ds, H_out, 1, v, &gdummy));
-            if (f_out) *f_out = v[0];
-            if (n_evals) *n_evals = dev_evals + 1;
-            return KDEFFT_OK;
-        }
+        if (r == KDEFFT_OK) return finish_device_select(ds, method, Gm, tho, fo, dev_evals, H_out, f_out, n_evals);
         if (r != KDEFFT_ERR_UNSUPPORTED) return r;
     }
     {
@@ -4052,6 +4197,71 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
 extern "C" int kdefft_select_H(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,
                                int max_iter, double* H_out, double* f_out, int64_t* n_evals) {
     return select_H_impl(ds, method, H0, G, n_starts, max_iter, false, H_out, f_out, n_evals);
+}
+
+extern "C" int kdefft_select_H_multi(kdefft_ds ds, int nmethods, const int* methods, const double* H0,
+                                     const double* G, int n_starts, int max_iter, double* H_out, double* f_out,
+                                     int64_t* n_evals) {
+    if (!ds || !methods || !H_out || nmethods < 1) return fail(KDEFFT_ERR_ARG, "NULL argument or no criterion");
+    for (int m = 0; m < nmethods; ++m)
+        if (methods[m] != KDEFFT_LSCV && methods[m] != KDEFFT_SCV && methods[m] != KDEFFT_PI)
+            return fail(KDEFFT_ERR_ARG, "unknown method");
+    KCU(cudaSetDevice(ds->ctx->device));
+    const int d = ds->d;
+    if (n_starts < 1) n_starts = 1;
+    if (max_iter < 1) max_iter = 100;
+    // criteria the device-resident search covers go pairwise into one launch;
+    // the others run one after another
+    std::vector<int> dev, host;
+    for (int m = 0; m < nmethods; ++m)
+        (ds->ctx->lag && select2d_covered(ds, methods[m]) ? dev : host).push_back(m);
+    if (!dev.empty()) {
+        Mat Hstart;
+        if (H0) {
+            KCHK(sym_check(H0, d, Hstart, "H0"));
+        } else {
+            KCHK(get_G(ds, nullptr, Hstart));
+        }
+        KCHK(spd_or_fail(Hstart, "H0"));
+        const Opt o{d, class_params(d, KDEFFT_H_FULL)};
+        std::vector<std::vector<double>> th0;
+        for (const Mat& H : start_bandwidths(Hstart, n_starts)) {
+            std::vector<double> th(o.p);
+            H_to_theta(o, H, th.data());
+            th0.push_back(th);
+        }
+        for (size_t k = 0; k < dev.size(); k += 2) {
+            std::vector<int> ms, idx;
+            std::vector<Mat> Gms;
+            for (size_t q = k; q < std::min(dev.size(), k + 2); ++q) {
+                const int m = dev[q];
+                Mat Gm;
+                if (methods[m] != KDEFFT_LSCV) KCHK(get_G(ds, G, Gm));
+                ms.push_back(methods[m]);
+                idx.push_back(m);
+                Gms.push_back(Gm);
+            }
+            std::vector<std::vector<std::vector<double>>> tho;
+            std::vector<std::vector<double>> fo;
+            std::vector<int64_t> ev;
+            const int r = device_select2d_lag(ds, ms, Gms, std::vector<std::vector<std::vector<double>>>(ms.size(), th0),
+                                              max_iter, tho, fo, ev);
+            if (r == KDEFFT_ERR_UNSUPPORTED) {
+                for (int m : idx) host.push_back(m);
+                continue;
+            }
+            KCHK(r);
+            for (size_t q = 0; q < ms.size(); ++q) {
+                const int m = idx[q];
+                KCHK(finish_device_select(ds, ms[q], Gms[q], tho[q], fo[q], ev[q], H_out + (size_t)m * d * d,
+                                          f_out ? f_out + m : nullptr, n_evals ? n_evals + m : nullptr));
+            }
+        }
+    }
+    for (int m : host)
+        KCHK(select_H_impl(ds, methods[m], H0, G, n_starts, max_iter, false, H_out + (size_t)m * d * d,
+                           f_out ? f_out + m : nullptr, n_evals ? n_evals + m : nullptr));
+    return KDEFFT_OK;
 }
 
 extern "C" int kdefft_select_H_nm(kdefft_ds ds, int method, const double* H0, const double* G, int n_starts,

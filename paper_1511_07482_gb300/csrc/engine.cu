@@ -1483,24 +1483,12 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
 }
 
 // One CTA per start runs the whole quasi-Newton search with lag-domain
-// evaluations against the count autocorrelation (FP32 copy, L2-resident).
-__global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelStart* __restrict__ starts, int stage) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double res[2][2];
-    __shared__ FusedItem<float> items[2];
-    __shared__ SelOpt opt;
-    __shared__ int ctl[2];
-    __shared__ double Hs[4], Rs[3], aux[3];
-    const int start = blockIdx.x;
-    // the autocorrelation box is fixed for the whole search: staged once in
-    // shared memory when it fits (stage != 0)
-    const float* acorr = p.acorr;
-    if (stage) {
-        float* sa = reinterpret_cast<float*>(smem_raw);
-        const int nbox = (p.A0 + 1) * (2 * p.A1 + 1);
-        for (int t = threadIdx.x; t < nbox; t += blockDim.x) sa[t] = p.acorr[t];
-        acorr = sa;
-    }
+// evaluations against the count autocorrelation (staged in shared memory, or
+// read from the L2-resident FP32 copy).  The search state lives in the
+// caller's shared memory; `start` indexes the start table.
+__device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* __restrict__ starts, int start,
+                                               const float* acorr, double (*res)[2], FusedItem<float>* items,
+                                               SelOpt& opt, int* ctl, double* Hs, double* Rs, double* aux) {
     if (threadIdx.x == 0) {
         const SelStart& st = starts[start];
         for (int i = 0; i < 3; ++i) opt.th_try[i] = st.th[i];
@@ -1560,7 +1548,34 @@ __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelStart*
     }
 }
 
-cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st) {
+// Two searches on one dataset in one launch: CTAs [0, nfirst) run criterion
+// p, the rest criterion q (the same autocorrelation box).  A single search
+// passes q = p.
+__global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelectParams q, int nfirst,
+                                                       SelStart* __restrict__ starts, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double res[2][2];
+    __shared__ FusedItem<float> items[2];
+    __shared__ SelOpt opt;
+    __shared__ int ctl[2];
+    __shared__ double Hs[4], Rs[3], aux[3];
+    // the autocorrelation box is fixed for the whole search: staged once in
+    // shared memory when it fits (stage != 0)
+    const float* acorr = p.acorr;
+    if (stage) {
+        float* sa = reinterpret_cast<float*>(smem_raw);
+        const int nbox = (p.A0 + 1) * (2 * p.A1 + 1);
+        for (int t = threadIdx.x; t < nbox; t += blockDim.x) sa[t] = p.acorr[t];
+        acorr = sa;
+    }
+    if ((int)blockIdx.x < nfirst)
+        sel_search_lag(p, starts, blockIdx.x, acorr, res, items, opt, ctl, Hs, Rs, aux);
+    else
+        sel_search_lag(q, starts, blockIdx.x, acorr, res, items, opt, ctl, Hs, Rs, aux);
+}
+
+cudaError_t launch_select2d_lag(const SelectParams& prm, const SelectParams& prm2, int nfirst, SelStart* starts,
+                                int nstarts, cudaStream_t st) {
     // dynamic shared memory for the staged box: up to `limit` on top of the
     // kernel's static shared memory (the attribute is set once, before any
     // launch, so that no box size falls between the default limit and it)
@@ -1574,7 +1589,7 @@ cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int n
         if (e != cudaSuccess) return e;
         set = true;
     }
-    k_select2d_lag<<<nstarts, 1024, sm, st>>>(prm, starts, stage);
+    k_select2d_lag<<<nstarts, 1024, sm, st>>>(prm, prm2, nfirst, starts, stage);
     return cudaGetLastError();
 }
 

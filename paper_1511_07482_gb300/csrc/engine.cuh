@@ -181,8 +181,11 @@ struct SelectParams {
 };
 cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts,
                             const float2* twpool, cudaStream_t st);
-// the same search in the lag domain: one CTA per start (prm.acorr set)
-cudaError_t launch_select2d_lag(const SelectParams& prm, SelStart* starts, int nstarts, cudaStream_t st);
+// the same search in the lag domain: one CTA per start (prm.acorr set).
+// Starts [0, nfirst) search with prm, the rest with prm2; both share the
+// autocorrelation box (acorr, A0, A1) of prm.
+cudaError_t launch_select2d_lag(const SelectParams& prm, const SelectParams& prm2, int nfirst, SelStart* starts,
+                                int nstarts, cudaStream_t st);
 
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
 
