@@ -93,6 +93,7 @@ struct DevBuf {
     size_t cap = 0;
     bool owner = true;   // false: a view into memory another buffer owns
     BlockCache* cache = nullptr;   // where owned blocks come from and go back to (null: cudaMalloc / cudaFree)
+    int64_t* gen = nullptr;        // bumped whenever the block changes (graphs that captured it go stale)
     DevBuf() = default;
     explicit DevBuf(BlockCache* bc) : cache(bc) {}
     DevBuf(const DevBuf&) = delete;
@@ -113,6 +114,7 @@ struct DevBuf {
             if (void* q = cache->take(want, got)) {
                 p = q;
                 cap = got;
+                if (gen) ++*gen;
                 return KDEFFT_OK;
             }
             ++cache->misses;
@@ -132,6 +134,7 @@ struct DevBuf {
         }
         p = q;
         cap = want;
+        if (gen) ++*gen;
         return KDEFFT_OK;
     }
     void release() {
@@ -140,6 +143,7 @@ struct DevBuf {
                 cache->give(p, cap);
             else
                 cudaFree(p);
+            if (gen) ++*gen;
         }
         p = nullptr;
         cap = 0;
@@ -150,6 +154,7 @@ struct DevBuf {
 struct HostBuf {
     void* p = nullptr;
     size_t cap = 0;
+    int64_t* gen = nullptr;   // as DevBuf::gen
     HostBuf() = default;
     HostBuf(const HostBuf&) = delete;
     HostBuf& operator=(const HostBuf&) = delete;
@@ -161,6 +166,7 @@ struct HostBuf {
         cap = 0;
         size_t want = std::max(bytes, (size_t)4096);
         want = want + want / 4;
+        if (gen) ++*gen;
         if (cudaMallocHost(&p, want) != cudaSuccess) {
             p = nullptr;
             return fail(KDEFFT_ERR_ALLOC, "pinned host allocation failed");
@@ -169,7 +175,10 @@ struct HostBuf {
         return KDEFFT_OK;
     }
     void release() {
-        if (p) cudaFreeHost(p);
+        if (p) {
+            cudaFreeHost(p);
+            if (gen) ++*gen;
+        }
         p = nullptr;
         cap = 0;
     }
@@ -520,6 +529,11 @@ struct kdefft_ctx_s {
         int64_t launches;
     };
     std::map<std::vector<long long>, GraphEntry> gcache;
+    // A captured graph holds the context buffers it copied to and from: when
+    // one of them is reallocated (even at the same address) every graph is
+    // dropped, since the driver may keep the old allocation's mapping in a
+    // copy node.
+    int64_t buf_gen = 0, graph_gen = 0;
     int64_t graphs_captured = 0, graph_replays = 0;
     // autotuner: engine, tile capacity and radix cap per batch shape
     struct Knobs {
@@ -595,16 +609,25 @@ static void prof_flush(kdefft_ctx c) {
 // work depends on; the pinned staging buffers are read when the graph runs,
 // so new contents need no new graph).  Direct while profiling, so that
 // every kernel keeps its own CUDA events.
+// Destroy every cached graph once the work launched so far is done.
+static int drop_graphs(kdefft_ctx c) {
+    KCU(cudaStreamSynchronize(c->stream));
+    for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
+    c->gcache.clear();
+    return KDEFFT_OK;
+}
+
 template <typename F>
 static int run_graph(kdefft_ctx c, const std::vector<long long>& sig, F&& issue) {
     if (!c->graphs || c->prof) return issue();
+    if (c->graph_gen != c->buf_gen) {   // a buffer some graph uses was reallocated
+        if (!c->gcache.empty()) KCHK(drop_graphs(c));
+        c->graph_gen = c->buf_gen;
+    }
     auto it = c->gcache.find(sig);
     if (it == c->gcache.end()) {
         if (!c->cap_stream) KCU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-        if (c->gcache.size() >= 64) {
-            for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
-            c->gcache.clear();
-        }
+        if (c->gcache.size() >= 64) KCHK(drop_graphs(c));
         // capture on the library's own stream (the caller's may be the legacy
         // default stream, which cannot be captured); replay on the caller's
         cudaStream_t user = c->stream;
@@ -625,6 +648,14 @@ static int run_graph(kdefft_ctx c, const std::vector<long long>& sig, F&& issue)
         const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         KCU(ei);
+        if (c->graph_gen != c->buf_gen) {   // the capture itself reallocated a buffer: run it once, keep nothing
+            const cudaError_t el = cudaGraphLaunch(ex, c->stream);
+            const cudaError_t es = cudaStreamSynchronize(c->stream);
+            cudaGraphExecDestroy(ex);
+            KCU(el);
+            KCU(es);
+            return KDEFFT_OK;
+        }
         it = c->gcache.emplace(sig, kdefft_ctx_s::GraphEntry{ex, c->launches - l0}).first;
         c->launches = l0;
         c->graphs_captured++;
@@ -881,7 +912,19 @@ static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool gr
 }
 
 // ---- psi_r (Eq. 13): one grid per unique multi-index |alpha| = r ----------
-static int add_psi(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first, std::vector<MultiIndex>& alphas) {
+// the multi-indices alpha with |alpha| = r in graded order (the unique
+// partials of psi_r)
+static std::vector<MultiIndex> order_alphas(int d, int r) {
+    std::vector<MultiIndex> alphas;
+    for (const MultiIndex& m : hindex().list[d]) {
+        int o = 0;
+        for (int k = 0; k < d; ++k) o += m.a[k];
+        if (o == r) alphas.push_back(m);
+    }
+    return alphas;
+}
+
+static int add_psi(ReqSet& rs, kdefft_ds ds, const Mat& H, const std::vector<MultiIndex>& alphas, int& first) {
     const int d = ds->d;
     KSpec sp;
     sp.nsig = 1;
@@ -891,22 +934,16 @@ static int add_psi(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first, st
     int L[4], P[4];
     KCHK(plan_for(ds, H, L, P));
     first = (int)rs.grids.size();
-    alphas.clear();
-    for (const MultiIndex& m : hindex().list[d]) {
-        int o = 0;
-        for (int k = 0; k < d; ++k) o += m.a[k];
-        if (o == r) alphas.push_back(m);
-    }
     for (const MultiIndex& m : alphas) {
-        GridReq g;
+        rs.grids.emplace_back();
+        GridReq& g = rs.grids.back();
         g.ds = ds;
         g.spec = si;
         std::memcpy(g.L, L, sizeof(L));
         std::memcpy(g.P, P, sizeof(P));
         Term t{0, {0}, 1.0};
         for (int k = 0; k < MAXD; ++k) t.alpha[k] = (k < d) ? m.a[k] : 0;
-        g.terms = {t};
-        rs.grids.push_back(std::move(g));
+        g.terms.assign(1, t);
     }
     return KDEFFT_OK;
 }
@@ -1592,7 +1629,16 @@ static long long pmin_smooth(long long m) {
 // least) when a request needs more.  Every dataset of `req` is brought up to
 // date with one batched spectrum launch sequence and stream-ordered passes
 // through context buffers (no synchronisation).
+// lines per CTA of an autocorrelation pass of length P: as many as fit 96 KB
+// of shared memory (two resident CTAs per SM), at least one
+static int acorr_lines(int P) {
+    int nl = 1;
+    while (nl < 64 && acorr_smem_bytes(P, nl + 1) <= (size_t)96 * 1024) ++nl;
+    return nl;
+}
+
 static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& req) {
+    HostTimer ht(c, "host:acorr");
     struct Job {
         kdefft_ds ds;
         int A[4], P[4];
@@ -1659,15 +1705,16 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
         for (int k = 1; k <= d - 2; ++k) pl.O0 *= P[k];
         pl.most = 0;
         {
+            // a length-P complex transform per line: 5 P log2 P flops
             long long o = pl.O0, ii = 1;
             for (int k = 0; k < d - 1; ++k) {
                 const int J = (k == 0) ? A[0] + 1 : 2 * A[k] + 1;
                 pl.most = std::max(pl.most, (size_t)(o * J * ii));
-                fl += 8.0 * (double)o * J * ii * P[k];
+                fl += 5.0 * P[k] * std::log2((double)P[k]) * (double)(o * ii);
                 ii *= J;
                 if (k + 1 <= d - 2) o /= P[k + 1];
             }
-            fl += 8.0 * (double)ii * (2 * A[d - 1] + 1) * pl.Q;
+            fl += 5.0 * P[d - 1] * std::log2((double)P[d - 1]) * (double)ii;
         }
         pl.off = pool;
         pool += (pl.most + 1) & ~(size_t)1;
@@ -1713,8 +1760,9 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                     a.W = last ? pl.Q : jb.P[k];
                     a.J = (k == 0) ? jb.A[0] + 1 : 2 * jb.A[k] + 1;
                     a.jlo = (k == 0) ? 0 : -jb.A[k];
-                    a.P = jb.P[k];
-                    a.tw_off = twiddle_offset(c, jb.P[k]);
+                    a.ap.tw_off = twiddle_offset(c, jb.P[k]);
+                    if (!radix_plan(jb.P[k], a.ap, 16)) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
+                    a.nl = acorr_lines(jb.P[k]);
                     a.half = last ? 1 : 0;
                     a.scale = last ? 1.0 / pl.ptot : 1.0;
                     if (last) {
@@ -1725,7 +1773,7 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                     }
                 }
                 c->launches++;
-                KCU(launch_acorr_many(tab.data(), jd + slot, (int)tab.size(), k == 0, tw, c->stream));
+                KCU(launch_acorr_many(tab.data(), jd + slot, (int)tab.size(), tw, c->stream));
                 slot += tab.size();
                 for (size_t v = 0; v < sel.size(); ++v) {
                     const Job& jb = jobs[sel[v]];
@@ -1785,6 +1833,7 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         std::vector<std::pair<kdefft_ds, std::array<int, 4>>> rq(need.begin(), need.end());
         KCHK(ensure_autocorr_many(c, rq));
     }
+    HostTimer hbuild(c, "host:lag_build");
     // order classes, contiguous
     std::vector<int> Re(pairs.size());
     for (size_t i = 0; i < pairs.size(); ++i) Re[i] = (pair_order(rs, pairs[i], d) + 1) & ~1;
@@ -1796,6 +1845,16 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     std::vector<real> wpool;
     std::vector<LagTile> tiles;
     std::vector<std::array<int, 3>> classes;   // (R, first tile, tiles)
+    items.reserve(pairs.size());
+    tiles.reserve(pairs.size() * 4);
+    // inverse covariances and normalisations once per kernel spec (the
+    // pairs of one bandwidth share them)
+    struct SpecInv {
+        bool done = false;
+        double lam[MAXSIG][MAXD * MAXD];
+        double nrm[MAXSIG];
+    };
+    std::vector<SpecInv> sinv(rs.specs.size());
     // fixed tiles of 4096 points: an item's sum depends on the item alone,
     // not on the batch it came in
     const long long T = 4096;
@@ -1814,14 +1873,23 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
             it.A[k] = ds->acA[k];
             it.delta[k] = (real)ds->delta[k];
         }
+        SpecInv& si = sinv[g.spec];
+        if (!si.done) {
+            for (int s = 0; s < sp.nsig; ++s) {
+                Mat inv;
+                double det;
+                if (!spd_inv_det(sp.sig[s], inv, det))
+                    return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) si.lam[s][a * MAXD + b] = inv(a, b);
+                si.nrm[s] = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
+            }
+            si.done = true;
+        }
         for (int s = 0; s < sp.nsig; ++s) {
-            Mat inv;
-            double det;
-            if (!spd_inv_det(sp.sig[s], inv, det))
-                return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
             for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)inv(a, b);
-            it.nrm[s] = (real)(std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det));
+                for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)si.lam[s][a * MAXD + b];
+            it.nrm[s] = (real)si.nrm[s];
         }
         it.acorr = dbl ? (const real*)ds->ac64.p : (const real*)ds->ac32.p;
         const int N = lag_table_size(d, it.R, dbl);
@@ -2141,6 +2209,7 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
 // rest in float.
 static int run(kdefft_ctx c, ReqSet& rs) {
     if (rs.grids.empty()) return KDEFFT_OK;
+    HostTimer ht(c, "host:run");
     std::vector<int> s32, s64;
     for (size_t i = 0; i < rs.grids.size(); ++i) {
         const GridReq& g = rs.grids[i];
@@ -2200,20 +2269,29 @@ static void assemble_scv(kdefft_ds ds, const Mat& H, const GridReq* g, bool spli
 }
 
 // psi_4 unique values -> Kronecker vector (Sec. 5 ordering)
-static void kron_expand(int d, int r, const std::vector<MultiIndex>& alphas, const GridReq* g, double* out) {
-    std::map<std::vector<int>, double> val;
-    for (size_t i = 0; i < alphas.size(); ++i) val[std::vector<int>(alphas[i].a, alphas[i].a + d)] = g[i].value;
+// Position in the Kronecker-ordered d^r vector -> index of its multi-index
+// in `alphas` (a flat index i_1 + d i_2 + ... counts how often each axis
+// occurs); one map serves every bandwidth of a call.
+static std::vector<int> kron_map(int d, int r, const std::vector<MultiIndex>& alphas) {
+    std::vector<int> code(9 * 9 * 9 * 9, -1);
+    for (size_t i = 0; i < alphas.size(); ++i) code[HermiteIndex::key(d, alphas[i].a)] = (int)i;
     long long total = 1;
     for (int i = 0; i < r; ++i) total *= d;
+    std::vector<int> map((size_t)total);
     for (long long pos = 0; pos < total; ++pos) {
-        std::vector<int> al(d, 0);
+        int al[MAXD] = {0, 0, 0, 0};
         long long p = pos;
         for (int i = 0; i < r; ++i) {
             al[p % d]++;
             p /= d;
         }
-        out[pos] = val[al];
+        map[(size_t)pos] = code[HermiteIndex::key(d, al)];
     }
+    return map;
+}
+
+static void kron_expand(const std::vector<int>& map, const GridReq* g, double* out) {
+    for (size_t pos = 0; pos < map.size(); ++pos) out[pos] = g[map[pos]].value;
 }
 
 static void assemble_pi(kdefft_ds ds, const Mat& H, const double* psi4, double* val, double* grad) {
@@ -2258,6 +2336,7 @@ static int write_out(kdefft_ctx c, double* dst, const double* src, size_t count)
 
 // ============================================================ C ABI
 static void ds_free(kdefft_ds ds) {
+    HostTimer ht(ds->ctx, "host:close");
     cudaSetDevice(ds->ctx->device);
     cudaStreamSynchronize(ds->ctx->stream);
     ds->counts.release();
@@ -2316,6 +2395,11 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         return fail(KDEFFT_ERR_CUDA, "cudaGetDeviceProperties failed");
     }
     c->nsm = prop.multiProcessorCount;
+    for (DevBuf* b : {&c->tw32, &c->tw64, &c->scratch, &c->partial, &c->items, &c->tiles, &c->out, &c->sel_buf,
+                      &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf})
+        b->gen = &c->buf_gen;
+    c->h_items.gen = &c->buf_gen;
+    c->h_out.gen = &c->buf_gen;
     if (cudaMalloc(&c->errflag, sizeof(int)) != cudaSuccess || cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) {
         delete c;
         return fail(KDEFFT_ERR_ALLOC, "error flag allocation failed");
@@ -2484,6 +2568,7 @@ int kdefft_destroy(kdefft_ctx c) {
 int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo, const double* hi,
                const int64_t* M, const kdefft_opts* opts, kdefft_ds* out) {
     if (!c || !out || !lo || !hi || !M) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    HostTimer ht(c, "host:bin");
     *out = nullptr;
     if (d < 1 || d > 4) return fail(KDEFFT_ERR_ARG, "d must be 1..4");
     if (n < 1 || (!X)) return fail(KDEFFT_ERR_ARG, "need n >= 1 samples");
@@ -2600,6 +2685,7 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
 int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t* n, int d, const double* lo,
                     const double* hi, const int64_t* M, const kdefft_opts* opts, kdefft_ds* out) {
     if (!c || !X || !n || !lo || !hi || !M || !out || nds < 1) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    HostTimer ht(c, "host:bin");
     if (d < 1 || d > 4) return fail(KDEFFT_ERR_ARG, "d must be 1..4");
     for (int i = 0; i < nds; ++i) out[i] = nullptr;
     kdefft_opts o;
@@ -2847,23 +2933,29 @@ static int check_common(kdefft_ds ds, const double* H, int nH) {
 
 int kdefft_psi(kdefft_ds ds, const double* H, int nH, int r, double* out) {
     KCHK(check_common(ds, H, nH));
+    HostTimer ht(ds->ctx, "host:psi");
     if (!out) return fail(KDEFFT_ERR_ARG, "NULL output");
     const int d = ds->d;
     if (r < 0 || (r & 1) || r > kRmax[d]) return fail(KDEFFT_ERR_ARG, "r must be even and within the order limit");
     ReqSet rs;
     std::vector<int> first(nH);
-    std::vector<MultiIndex> alphas;
-    for (int h = 0; h < nH; ++h) {
-        Mat Hm;
-        KCHK(sym_check(H + (size_t)h * d * d, d, Hm, "H"));
-        KCHK(spd_or_fail(Hm, "H"));
-        KCHK(add_psi(rs, ds, Hm, r, first[h], alphas));
+    const std::vector<MultiIndex> alphas = order_alphas(d, r);
+    {
+        HostTimer hq(ds->ctx, "host:psi_requests");
+        rs.specs.reserve(nH);
+        rs.grids.reserve((size_t)nH * alphas.size());
+        for (int h = 0; h < nH; ++h) {
+            Mat Hm;
+            KCHK(sym_check(H + (size_t)h * d * d, d, Hm, "H"));
+            KCHK(spd_or_fail(Hm, "H"));
+            KCHK(add_psi(rs, ds, Hm, alphas, first[h]));
+        }
     }
     KCHK(run(ds->ctx, rs));
-    long long len = 1;
-    for (int i = 0; i < r; ++i) len *= d;
-    std::vector<double> res((size_t)len * nH);
-    for (int h = 0; h < nH; ++h) kron_expand(d, r, alphas, &rs.grids[first[h]], res.data() + (size_t)h * len);
+    const std::vector<int> map = kron_map(d, r, alphas);
+    const size_t len = map.size();
+    std::vector<double> res(len * nH);
+    for (int h = 0; h < nH; ++h) kron_expand(map, &rs.grids[first[h]], res.data() + (size_t)h * len);
     return write_out(ds->ctx, out, res.data(), res.size());
 }
 
@@ -2941,12 +3033,12 @@ static int psi4_kron(kdefft_ds ds, const Mat& G, std::vector<double>& psi4) {
     const int d = ds->d;
     ReqSet rs;
     int first;
-    std::vector<MultiIndex> alphas;
+    const std::vector<MultiIndex> alphas = order_alphas(d, 4);
     KCHK(spd_or_fail(G, "G"));
-    KCHK(add_psi(rs, ds, G, 4, first, alphas));
+    KCHK(add_psi(rs, ds, G, alphas, first));
     KCHK(run(ds->ctx, rs));
     psi4.assign((size_t)d * d * d * d, 0.0);
-    kron_expand(d, 4, alphas, &rs.grids[first], psi4.data());
+    kron_expand(kron_map(d, 4, alphas), &rs.grids[first], psi4.data());
     return KDEFFT_OK;
 }
 

@@ -616,6 +616,115 @@ __global__ void __launch_bounds__(256) k_final(const Item<real>* __restrict__ it
     }
 }
 
+// ------------------------------------------------------------ autocorrelation passes
+// One pass of the count autocorrelation a = F^-1(|C|^2) (FP64) along one
+// axis, for many datasets in one launch.  A line holds the W spectrum values
+// along the axis (weights h_w: 2 on the interior of a half-spectrum axis,
+// else 1), zero-extended to the padded size P; its inverse DFT of length P
+// runs in shared memory and the J lags jlo .. jlo + J - 1 are kept.  The
+// inverse comes from the forward transform:
+//   sum_w x_w e^{+2 pi i w j / P} = conj(sum_w conj(x_w) e^{-2 pi i w j / P}).
+// Line l = o I + i of a pass reads (o, w, i) at (o W + w) I + i and writes
+// lag jj to (o J + jj) I + i; the real spectrum of the first pass has I = 1.
+__device__ __forceinline__ int acorr_job_of(const AcorrJob* __restrict__ jobs, int n, long long b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].blk0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_acorr_fft(const AcorrJob* __restrict__ jobs, int njobs,
+                                                   const double2* __restrict__ twpool) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const AcorrJob& jb = jobs[acorr_job_of(jobs, njobs, blockIdx.x)];
+    const int P = jb.ap.P, W = jb.W, J = jb.J, cap = jb.nl;
+    const long long I = jb.I;
+    double2* bufa = reinterpret_cast<double2*>(smem_raw);
+    double2* bufb = bufa + padded_cap(cap * P);
+    double2* tw = bufb + padded_cap(cap * P);
+    const long long l0 = ((long long)blockIdx.x - jb.blk0) * cap;
+    const int nl = (int)min((long long)cap, jb.O * I - l0);
+    load_twiddles(tw, twpool, jb.ap);
+    auto hw = [&](int w) { return (jb.half && w != 0 && 2 * w != P) ? 2.0 : 1.0; };
+    if (I == 1) {   // consecutive lines are rows: w fastest
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P, w = t - c * P;
+            double2 x = make_double2(0.0, 0.0);
+            if (w < W) {
+                const long long at = (l0 + c) * W + w;
+                const double h = hw(w);
+                x = jb.in_r ? make_double2(h * jb.in_r[at], 0.0) : make_double2(h * jb.in_c[at].x, -h * jb.in_c[at].y);
+            }
+            bufa[pad(t)] = x;
+        }
+    } else {        // consecutive lines are consecutive i: line fastest
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int w = t / nl, c = t - w * nl;
+            double2 x = make_double2(0.0, 0.0);
+            if (w < W) {
+                const long long l = l0 + c, o = l / I, i = l - o * I;
+                const double2 v = jb.in_c[(o * W + w) * I + i];
+                const double h = hw(w);
+                x = make_double2(h * v.x, -h * v.y);
+            }
+            bufa[pad(c * P + w)] = x;
+        }
+    }
+    const double2* Y = smem_fft(bufa, bufb, nl, jb.ap, tw);
+    for (int t = threadIdx.x; t < nl * J; t += blockDim.x) {
+        int c, jj;
+        if (I == 1) {
+            c = t / J;
+            jj = t - c * J;
+        } else {
+            jj = t / nl;
+            c = t - jj * nl;
+        }
+        int j = (jb.jlo + jj) % P;
+        if (j < 0) j += P;
+        const double2 y = Y[pad(c * P + j)];
+        const long long l = l0 + c, o = l / I, i = l - o * I;
+        const long long at = (o * J + jj) * I + i;
+        if (jb.out_r) {
+            jb.out_r[at] = y.x * jb.scale;
+            if (jb.out_r32) jb.out_r32[at] = (float)(y.x * jb.scale);
+        } else {
+            jb.out_c[at] = make_double2(y.x, -y.y);
+        }
+    }
+}
+
+cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, const double2* twpool, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = 0;
+    size_t sm = 0;
+    for (int k = 0; k < n; ++k) {
+        AcorrJob& jb = jobs_h[k];
+        if (jb.nl < 1 || jb.ap.P < 2 || jb.W > jb.ap.P || (!jb.in_r && !jb.in_c) || (jb.in_r && jb.I != 1))
+            return cudaErrorInvalidValue;
+        jb.blk0 = blocks;
+        blocks += (jb.O * jb.I + jb.nl - 1) / jb.nl;
+        sm = std::max(sm, acorr_smem_bytes(jb.ap.P, jb.nl));
+    }
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(jobs_d, jobs_h, sizeof(AcorrJob) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    static size_t set = 48 * 1024;
+    if (sm > set) {
+        e = cudaFuncSetAttribute(k_acorr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        set = sm;
+    }
+    k_acorr_fft<<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, twpool);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ reduce
 template <typename real>
 __global__ void k_reduce(const Item<real>* __restrict__ items, int nitems, const double* __restrict__ partial,

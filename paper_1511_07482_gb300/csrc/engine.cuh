@@ -233,22 +233,26 @@ cudaError_t launch_lag_reduce(const LagItem<real>* items, int nitems, const doub
 // exp(-2 pi i t / P), t < P, at twpool + tw_off.  blk0: the job's first
 // block in a launch over many jobs (set by the launcher).
 struct AcorrJob {
-    const double* in_r;
-    const double2* in_c;
-    double2* out_c;
-    double* out_r;
-    float* out_r32;
-    long long O, I;
-    int W, J, jlo, P, tw_off, half;
+    const double* in_r;          // real input (the count spectrum; first pass, I = 1), or
+    const double2* in_c;         // complex input of a later pass
+    double2* out_c;              // complex output of a pass before the last, or
+    double* out_r;               // real part of the last pass (times scale), with
+    float* out_r32;              // its FP32 copy
+    long long O, I;              // lines O I; element (o, w, i) at (o W + w) I + i
+    int W, J, jlo, half;         // W values per line (<= P); lags jlo .. jlo + J - 1; half: weights 2 inside
+    int nl;                      // lines per CTA
+    AxisPlan ap;                 // the length-P transform (radix stages, twiddle offset)
     double scale;
     long long blk0;
 };
-// All jobs' passes in one launch: inner = the innermost axis of a real
-// spectrum (I = 1; one CTA per row), else an outer axis of complex data.
+// shared memory of an autocorrelation pass: two line buffers and P twiddles
+__host__ __device__ constexpr size_t acorr_smem_bytes(int P, int nl) {
+    return sizeof(double2) * ((size_t)2 * (size_t)(nl * P + ((nl * P) >> 4) + 1) + (size_t)P);
+}
+// All jobs' passes of one level in one launch (one CTA per nl lines).
 // jobs_h: host table (rewritten with each job's blk0), jobs_d: device space
 // for it (n entries).
-cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, bool inner, const double2* twpool,
-                              cudaStream_t st);
+cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, const double2* twpool, cudaStream_t st);
 
 // ---- kernel density estimate on the grid and mixture cross term (kde.cu)
 struct KdeDesc {

@@ -1,10 +1,7 @@
 // Lag-domain evaluation of the binned functionals (Eq. 25 with the sum over
-// the lag done first) and the count autocorrelation it needs.
+// the lag done first) against the count autocorrelation (whose passes run
+// in engine.cu with the other transforms).
 //
-//   acorr_axis  one pass of the pruned inverse DFT a = F^-1(|C|^2) (FP64):
-//               the count spectrum of Eq. 22 at a padded size P >= M + A has
-//               no aliasing at lags |j_k| <= A_k, so a_j = sum_i c_i c_{i+j}
-//               exactly (up to rounding) on that box.
 //   lag         per work item (two kernels of the same covariances and
 //               support, as in the FFT path), sum over the half lag box of
 //               w_j k_j a_j, w_j in {0, 1, 2}; kernels from the
@@ -17,158 +14,6 @@
 #include "engine.cuh"
 
 namespace kdefft {
-
-// ------------------------------------------------------------ autocorrelation passes
-// twiddles exp(-2 pi i t / P) of one size in shared memory when they fit
-constexpr int kTwSmem = 2048;
-
-// the job owning block b (jobs in increasing blk0)
-__device__ __forceinline__ int acorr_job_of(const AcorrJob* __restrict__ jobs, int n, long long b) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].blk0 <= b)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// Innermost axis of the real spectrum (layout [o][w], one row of W values
-// per o): one CTA per (job, row), the row and the twiddles staged in shared
-// memory, one warp per output lag, the lanes splitting the sum.
-__global__ void __launch_bounds__(256) k_acorr_row(const AcorrJob* __restrict__ jobs, int njobs,
-                                                   const double2* __restrict__ twpool) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    const AcorrJob& jb = jobs[acorr_job_of(jobs, njobs, blockIdx.x)];
-    const long long o = (long long)blockIdx.x - jb.blk0;
-    const int P = jb.P, W = jb.W, J = jb.J;
-    const bool tws = P <= kTwSmem;
-    double2* stw = reinterpret_cast<double2*>(sm_raw);
-    double* row = reinterpret_cast<double*>(stw + (tws ? P : 0));
-    const double2* tw = twpool + jb.tw_off;
-    if (tws)
-        for (int t = threadIdx.x; t < P; t += blockDim.x) stw[t] = tw[t];
-    for (int w = threadIdx.x; w < W; w += blockDim.x) row[w] = jb.in_r[o * W + w];
-    __syncthreads();
-    const double2* T = tws ? stw : tw;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int jj = warp; jj < J; jj += nw) {
-        int step = (jb.jlo + jj) % P;
-        if (step < 0) step += P;
-        // position (w step) mod P for w = lane, lane + 32, ...
-        int pos = (int)(((long long)lane * step) % P);
-        const int adv = (int)((32LL * step) % P);
-        double sr = 0.0, si = 0.0;
-        for (int w = lane; w < W; w += 32) {
-            const double2 t = T[pos];
-            const double h = (jb.half && w != 0 && 2 * w != P) ? 2.0 : 1.0;
-            const double x = h * row[w];
-            sr = fma(x, t.x, sr);
-            si = fma(-x, t.y, si);
-            pos += adv;
-            if (pos >= P) pos -= P;
-        }
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) {
-            sr += __shfl_down_sync(0xffffffffu, sr, sh);
-            si += __shfl_down_sync(0xffffffffu, si, sh);
-        }
-        if (lane == 0) {
-            const long long idx = o * J + jj;
-            if (jb.out_r) {
-                jb.out_r[idx] = sr * jb.scale;
-                if (jb.out_r32) jb.out_r32[idx] = (float)(sr * jb.scale);
-            } else {
-                jb.out_c[idx] = make_double2(sr, si);
-            }
-        }
-    }
-}
-
-// Outer axis of complex data [o][w][i] -> [o][jj][i]: one thread per output,
-// i fastest (coalesced reads, one twiddle per warp and step), each CTA within
-// one job, twiddles in shared memory.
-__global__ void __launch_bounds__(256) k_acorr_axis(const AcorrJob* __restrict__ jobs, int njobs,
-                                                    const double2* __restrict__ twpool) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    const AcorrJob& jb = jobs[acorr_job_of(jobs, njobs, blockIdx.x)];
-    const int P = jb.P, W = jb.W, J = jb.J;
-    const long long I = jb.I;
-    const bool tws = P <= kTwSmem;
-    double2* stw = reinterpret_cast<double2*>(sm_raw);
-    const double2* tw = twpool + jb.tw_off;
-    if (tws) {
-        for (int t = threadIdx.x; t < P; t += blockDim.x) stw[t] = tw[t];
-        __syncthreads();
-    }
-    const double2* T = tws ? stw : tw;
-    const long long total = jb.O * (long long)J * I;
-    const long long idx = ((long long)blockIdx.x - jb.blk0) * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const long long i = idx % I;
-    const long long r = idx / I;
-    const int jj = (int)(r % J);
-    const long long o = r / J;
-    int step = (jb.jlo + jj) % P;
-    if (step < 0) step += P;
-    int pos = 0;
-    double sr = 0.0, si = 0.0;
-    const long long base = o * (long long)W * I + i;
-    for (int w = 0; w < W; ++w) {
-        const double2 t = T[pos];   // exp(-2 pi i pos / P); the pass uses its conjugate
-        const double2 x = jb.in_c[base + (long long)w * I];
-        const double h = (jb.half && w != 0 && 2 * w != P) ? 2.0 : 1.0;
-        sr = fma(h * x.x, t.x, fma(h * x.y, t.y, sr));
-        si = fma(h * x.y, t.x, fma(-h * x.x, t.y, si));
-        pos += step;
-        if (pos >= P) pos -= P;
-    }
-    if (jb.out_r) {
-        jb.out_r[idx] = sr * jb.scale;
-        if (jb.out_r32) jb.out_r32[idx] = (float)(sr * jb.scale);
-    } else {
-        jb.out_c[idx] = make_double2(sr, si);
-    }
-}
-
-cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, bool inner, const double2* twpool,
-                              cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    long long blocks = 0;
-    size_t sm = 0;
-    for (int k = 0; k < n; ++k) {
-        AcorrJob& jb = jobs_h[k];
-        jb.blk0 = blocks;
-        const size_t twb = (jb.P <= kTwSmem) ? sizeof(double2) * (size_t)jb.P : 0;
-        if (inner) {
-            if (jb.I != 1 || !jb.in_r) return cudaErrorInvalidValue;
-            blocks += jb.O;
-            sm = std::max(sm, twb + sizeof(double) * (size_t)jb.W);
-        } else {
-            blocks += (jb.O * (long long)jb.J * jb.I + 255) / 256;
-            sm = std::max(sm, twb);
-        }
-    }
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemcpyAsync(jobs_d, jobs_h, sizeof(AcorrJob) * n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    static size_t set_row = 48 * 1024, set_axis = 48 * 1024;
-    size_t& set = inner ? set_row : set_axis;
-    if (sm > set) {
-        e = cudaFuncSetAttribute(inner ? (const void*)k_acorr_row : (const void*)k_acorr_axis,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        set = sm;
-    }
-    if (inner)
-        k_acorr_row<<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, twpool);
-    else
-        k_acorr_axis<<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, twpool);
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------ lag evaluation
 template <typename real, int D, int R>

@@ -44,6 +44,27 @@ def test_graph_replay_gives_the_direct_bits(engine):
     assert st_off["graphs_captured"] == 0 and st_off["graph_replays"] == 0
 
 
+def test_graphs_are_recaptured_after_buffers_grow():
+    """A captured graph copies through the context's staging buffers; once a
+    larger batch has reallocated them, the small batch is captured again
+    (never replayed against the old allocations) and gives the same bits."""
+    w = synthetic.small_case(n=3000, d=2, M=[64, 60], seed=73, n_candidates=4)
+    c = _ctx()
+    ds = c.bin(w.X, w.lo, w.hi, w.M)
+    small = [ds.lscv(w.H, grad=True) for _ in range(2)]
+    st1 = c.runtime_stats()
+    assert st1["graph_replays"] >= 1
+    big = np.concatenate([w.H * s for s in (0.6, 0.8, 1.0, 1.25, 1.5, 2.0, 2.5, 3.0)] * 8)
+    ds.lscv(big, grad=True)
+    st2 = c.runtime_stats()
+    again = ds.lscv(w.H, grad=True)
+    st3 = c.runtime_stats()
+    assert st3["graphs_captured"] == st2["graphs_captured"] + 1
+    assert np.array_equal(again[0], small[0][0]) and np.array_equal(again[1], small[0][1])
+    ds.close()
+    c.close()
+
+
 def test_graphs_are_bypassed_while_profiling():
     w = synthetic.small_case(n=2000, d=3, M=[20, 18, 16], seed=72, n_candidates=2)
     c = _ctx()
