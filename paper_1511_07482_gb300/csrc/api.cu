@@ -492,6 +492,7 @@ struct kdefft_ctx_s {
     DevBuf scratch, partial, items, tiles, out;
     HostBuf h_items, h_out;
     bool staging_free = true;   // no copy out of h_items is pending on the stream
+    cudaEvent_t staging_ev = nullptr;   // recorded after the last copy out of h_items
     // counters: kernel launches and host<->device bytes (always), per-kernel
     // CUDA-event times and algorithmic bytes/flops (when profiling is on)
     struct KStat {
@@ -509,6 +510,9 @@ struct kdefft_ctx_s {
     DevBuf binfix;            // fixed-point accumulators of FP32 linear binning (stream-ordered reuse)
     DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
     DevBuf acjobs;            // job table of the batched autocorrelation passes
+    HostBuf h_acjobs;         // its pinned staging copy, free once acjobs_ev has passed
+    cudaEvent_t acjobs_ev = nullptr;
+    bool acjobs_free = true;
     DevBuf binjobs;           // job tables of the batched binning
     DevBuf kdebuf;            // stencil table / outputs of the grid estimate and the mixture term
     std::map<std::string, KStat> kstat;
@@ -591,6 +595,7 @@ static void prof_stop(kdefft_ctx c, cudaEvent_t a, const char* name, double byte
 static void prof_flush(kdefft_ctx c) {
     for (auto& p : c->pending) {
         float ms = 0.f;
+        cudaEventSynchronize(p.b);   // launches may still be in flight
         cudaEventElapsedTime(&ms, p.a, p.b);
         auto& k = c->kstat[p.name];
         k.launches++;
@@ -603,12 +608,6 @@ static void prof_flush(kdefft_ctx c) {
     c->pending.clear();
 }
 
-// Run the stream work of one batch (`issue`: the copies and launches it
-// enqueues on c->stream) directly, or replay it from a CUDA graph cached
-// under its launch signature `sig` (every pointer, size and launch shape the
-// work depends on; the pinned staging buffers are read when the graph runs,
-// so new contents need no new graph).  Direct while profiling, so that
-// every kernel keeps its own CUDA events.
 // Destroy every cached graph once the work launched so far is done.
 static int drop_graphs(kdefft_ctx c) {
     KCU(cudaStreamSynchronize(c->stream));
@@ -617,6 +616,31 @@ static int drop_graphs(kdefft_ctx c) {
     return KDEFFT_OK;
 }
 
+// The pinned staging buffer h_items feeds one host-to-device copy per
+// batch.  Before the host rewrites it, the previous copy out of it must be
+// done: an event recorded right after that copy marks it (the kernels that
+// follow may still run).
+static int staging_wait(kdefft_ctx c) {
+    if (!c->staging_free) {
+        KCU(cudaEventSynchronize(c->staging_ev));
+        c->staging_free = true;
+    }
+    return KDEFFT_OK;
+}
+
+static int staging_upload(kdefft_ctx c, void* dst, size_t bytes) {
+    KCU(cudaMemcpyAsync(dst, c->h_items.p, bytes, cudaMemcpyHostToDevice, c->stream));
+    KCU(cudaEventRecord(c->staging_ev, c->stream));
+    c->staging_free = false;
+    return KDEFFT_OK;
+}
+
+// Run the stream work of one batch (`issue`: the copies and launches it
+// enqueues on c->stream) directly, or replay it from a CUDA graph cached
+// under its launch signature `sig` (every pointer, size and launch shape the
+// work depends on; the pinned staging buffers are read when the graph runs,
+// so new contents need no new graph).  Direct while profiling, so that
+// every kernel keeps its own CUDA events.
 template <typename F>
 static int run_graph(kdefft_ctx c, const std::vector<long long>& sig, F&& issue) {
     if (!c->graphs || c->prof) return issue();
@@ -1280,11 +1304,11 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
     }();
     const size_t bTiles = sizeof(Tile) * nt;
     const size_t bytes = bItems + bTiles;
+    // the pinned staging buffer may still be read by a previous copy (also
+    // before it is reallocated)
+    KCHK(staging_wait(c));
     KCHK(c->h_items.ensure(bytes));
     KCHK(c->items.ensure(bytes));
-    // the pinned staging buffer may still be read by a previous copy
-    if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
-    c->staging_free = false;
     unsigned char* h = (unsigned char*)c->h_items.p;
     std::memcpy(h, items.data(), bItems);
     size_t o = bItems;
@@ -1361,7 +1385,6 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
     if (out_host) KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
     sig[12] = (long long)(uintptr_t)c->h_out.p;
     auto issue = [&]() -> int {
-        KCU(cudaMemcpyAsync(c->items.p, h, bytes, cudaMemcpyHostToDevice, c->stream));
         cudaEvent_t ev;
         if (!pl.A.empty()) {
             ev = prof_start(c);
@@ -1390,6 +1413,7 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
         }
         return KDEFFT_OK;
     };
+    KCHK(staging_upload(c, c->items.p, bytes));
     KCHK(run_graph(c, sig, issue));
     c->h2d += (int64_t)bytes;
     if (out_host) {
@@ -1399,10 +1423,10 @@ static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists&
         }
         c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
         std::memcpy(out_host, c->h_out.p, sizeof(double) * 2 * nitems);
-    } else {
-        KCU(cudaStreamSynchronize(c->stream));
+        c->staging_free = true;
     }
-    c->staging_free = true;
+    // without host results (count spectra) the launches stay in flight; the
+    // next user of the staging buffer waits for the copy out of it
     prof_flush(c);
     return KDEFFT_OK;
 }
@@ -1454,11 +1478,11 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
     }
     KCHK(sync_twiddles(c));
     const size_t bItems = sizeof(FusedItem<real>) * nitems;
+    KCHK(staging_wait(c));
     KCHK(c->h_items.ensure(bItems));
     KCHK(c->items.ensure(bItems));
     KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
     KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
-    if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
     {
         FusedItem<real>* fi = (FusedItem<real>*)c->h_items.p;
         for (int i = 0; i < nitems; ++i) {
@@ -1488,7 +1512,6 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
             f.scale = it.scale;
         }
     }
-    c->staging_free = false;
     double fl = 0.0, by = 0.0;
     for (const Item<real>& it : items) {
         const double P1 = it.ax[1].P, P0 = it.ax[0].P, Q1 = std::floor(P1 / 2) + 1;
@@ -1512,7 +1535,6 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
                                         (long long)(uintptr_t)c->h_out.p};
     bool too_big = false;   // a 16-CTA cluster of this footprint does not fit the device
     auto issue = [&]() -> int {
-        KCU(cudaMemcpyAsync(c->items.p, c->h_items.p, bItems, cudaMemcpyHostToDevice, c->stream));
         cudaEvent_t ev = prof_start(c);
         cudaError_t le = launch_fused2d<real>((const FusedItem<real>*)c->items.p, nitems, rmax, cs, gat, spcn, cap,
                                               pmax, tw, (double*)c->out.p, c->errflag, c->stream);
@@ -1525,6 +1547,7 @@ static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* ou
         KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
         return KDEFFT_OK;
     };
+    KCHK(staging_upload(c, c->items.p, bItems));
     const int ir = run_graph(c, sig, issue);
     if (too_big) {
         // stay at 8-CTA clusters from now on
@@ -1725,15 +1748,21 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
     if (!jobs.empty()) {
         KCHK(c->acbuf[0].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
         KCHK(c->acbuf[1].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
-        // one table slice per launch (at most MAXD launches per dataset), so
-        // that no launch waits for the previous one's table to be read
+        // one table slice per launch (at most MAXD launches per dataset); all
+        // slices go up in one copy from pinned memory, so that the host does
+        // not wait for the stream (a pageable copy would)
         KCHK(c->acjobs.ensure(sizeof(AcorrJob) * jobs.size() * MAXD));
         AcorrJob* jd = (AcorrJob*)c->acjobs.p;
-        size_t slot = 0;
         double2* pool0 = (double2*)c->acbuf[0].p;
         double2* pool1 = (double2*)c->acbuf[1].p;
-        cudaEvent_t ev = prof_start(c);
-        c->launches--;   // counted per launch below
+        std::vector<AcorrJob> all;
+        struct Launch {
+            size_t slot;
+            int n;
+            long long blocks;
+            size_t sm;
+        };
+        std::vector<Launch> lv;
         for (int dim = 1; dim <= MAXD; ++dim) {
             std::vector<size_t> sel;
             for (size_t u = 0; u < jobs.size(); ++u)
@@ -1744,11 +1773,12 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
             for (size_t v = 0; v < sel.size(); ++v) O[v] = plan[sel[v]].O0;
             for (int k = 0; k < dim; ++k) {
                 const bool last = (k == dim - 1);
-                std::vector<AcorrJob> tab(sel.size());
+                const size_t slot = all.size();
+                all.resize(slot + sel.size());
                 for (size_t v = 0; v < sel.size(); ++v) {
                     const Job& jb = jobs[sel[v]];
                     const Plan& pl = plan[sel[v]];
-                    AcorrJob& a = tab[v];
+                    AcorrJob& a = all[slot + v];
                     std::memset(&a, 0, sizeof(a));
                     // ping-pong: level k reads pool (k+1)&1, writes pool k&1
                     double2* rd = ((k & 1) ? pool0 : pool1) + pl.off;
@@ -1772,9 +1802,9 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                         a.out_c = wr;
                     }
                 }
-                c->launches++;
-                KCU(launch_acorr_many(tab.data(), jd + slot, (int)tab.size(), tw, c->stream));
-                slot += tab.size();
+                Launch L{slot, (int)sel.size(), 0, 0};
+                KCU(acorr_plan(all.data() + slot, L.n, &L.blocks, &L.sm));
+                lv.push_back(L);
                 for (size_t v = 0; v < sel.size(); ++v) {
                     const Job& jb = jobs[sel[v]];
                     const int J = (k == 0) ? jb.A[0] + 1 : 2 * jb.A[k] + 1;
@@ -1782,6 +1812,18 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                     if (k + 1 <= dim - 2) O[v] /= jb.P[k + 1];
                 }
             }
+        }
+        if (!c->acjobs_free) KCU(cudaEventSynchronize(c->acjobs_ev));
+        KCHK(c->h_acjobs.ensure(sizeof(AcorrJob) * all.size()));
+        std::memcpy(c->h_acjobs.p, all.data(), sizeof(AcorrJob) * all.size());
+        KCU(cudaMemcpyAsync(jd, c->h_acjobs.p, sizeof(AcorrJob) * all.size(), cudaMemcpyHostToDevice, c->stream));
+        KCU(cudaEventRecord(c->acjobs_ev, c->stream));
+        c->acjobs_free = false;
+        cudaEvent_t ev = prof_start(c);
+        c->launches--;   // counted per launch below
+        for (const Launch& L : lv) {
+            c->launches++;
+            KCU(launch_acorr(jd + L.slot, L.n, L.blocks, L.sm, tw, c->stream));
         }
         prof_stop(c, ev, "acorr_f64", by, fl);
     }
@@ -1921,13 +1963,12 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t bI = sizeof(LagItem<real>) * nitems, bT = sizeof(LagTile) * tiles.size(), bW = sizeof(real) * wpool.size();
     const size_t oT = al(bI), oW = oT + al(bT), bytes = oW + std::max<size_t>(bW, 16);
+    KCHK(staging_wait(c));
     KCHK(c->h_items.ensure(bytes));
     KCHK(c->items.ensure(bytes));
     KCHK(c->partial.ensure(sizeof(double) * 2 * tiles.size()));
     KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
     KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
-    if (!c->staging_free) KCU(cudaStreamSynchronize(c->stream));
-    c->staging_free = false;
     unsigned char* h = (unsigned char*)c->h_items.p;
     std::memcpy(h, items.data(), bI);
     std::memcpy(h + oT, tiles.data(), bT);
@@ -1956,7 +1997,6 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         sig.push_back(cl[2]);
     }
     auto issue = [&]() -> int {
-        KCU(cudaMemcpyAsync(dbase, h, bytes, cudaMemcpyHostToDevice, c->stream));
         for (const auto& cl : classes) {
             cudaEvent_t ev = prof_start(c);
             const int grid = std::min(cl[2], c->nsm * 8);
@@ -1970,6 +2010,7 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
         return KDEFFT_OK;
     };
+    KCHK(staging_upload(c, dbase, bytes));
     KCHK(run_graph(c, sig, issue));
     c->h2d += (int64_t)bytes;
     {
@@ -2400,6 +2441,11 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         b->gen = &c->buf_gen;
     c->h_items.gen = &c->buf_gen;
     c->h_out.gen = &c->buf_gen;
+    if (cudaEventCreateWithFlags(&c->staging_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->acjobs_ev, cudaEventDisableTiming) != cudaSuccess) {
+        delete c;
+        return fail(KDEFFT_ERR_CUDA, "event creation failed");
+    }
     if (cudaMalloc(&c->errflag, sizeof(int)) != cudaSuccess || cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) {
         delete c;
         return fail(KDEFFT_ERR_ALLOC, "error flag allocation failed");
@@ -2560,6 +2606,9 @@ int kdefft_destroy(kdefft_ctx c) {
     for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
     c->gcache.clear();
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->staging_ev) cudaEventDestroy(c->staging_ev);
+    if (c->acjobs_ev) cudaEventDestroy(c->acjobs_ev);
+    c->h_acjobs.release();
     if (c->errflag) cudaFree(c->errflag);
     delete c;
     return KDEFFT_OK;
@@ -3560,6 +3609,9 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
         q.n = (double)ds->n;
         q.inv_n = 1.0 / q.n;
         q.inv_n2 = 1.0 / (q.n * q.n);
+        q.inv_nf = (float)q.inv_n;
+        q.inv_n2h = (float)q.inv_n2;
+        q.inv_n2l = (float)(q.inv_n2 - (double)q.inv_n2h);
         q.tau = ds->opts.tau;
         q.delta0 = ds->delta[0];
         q.delta1 = ds->delta[1];
@@ -3761,6 +3813,9 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     prm.n = (double)ds->n;
     prm.inv_n = 1.0 / prm.n;
     prm.inv_n2 = 1.0 / (prm.n * prm.n);
+    prm.inv_nf = (float)prm.inv_n;
+    prm.inv_n2h = (float)prm.inv_n2;
+    prm.inv_n2l = (float)(prm.inv_n2 - (double)prm.inv_n2h);
     prm.tau = ds->opts.tau;
     prm.delta0 = ds->delta[0];
     prm.delta1 = ds->delta[1];

@@ -699,8 +699,7 @@ __global__ void __launch_bounds__(256) k_acorr_fft(const AcorrJob* __restrict__ 
     }
 }
 
-cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, const double2* twpool, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+cudaError_t acorr_plan(AcorrJob* jobs_h, int n, long long* blocks_out, size_t* sm_out) {
     long long blocks = 0;
     size_t sm = 0;
     for (int k = 0; k < n; ++k) {
@@ -711,13 +710,18 @@ cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, const d
         blocks += (jb.O * jb.I + jb.nl - 1) / jb.nl;
         sm = std::max(sm, acorr_smem_bytes(jb.ap.P, jb.nl));
     }
-    if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemcpyAsync(jobs_d, jobs_h, sizeof(AcorrJob) * n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
+    *blocks_out = blocks;
+    *sm_out = sm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_acorr(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const double2* twpool,
+                         cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
     static size_t set = 48 * 1024;
     if (sm > set) {
-        e = cudaFuncSetAttribute(k_acorr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(k_acorr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         set = sm;
     }
@@ -1129,30 +1133,41 @@ __device__ __forceinline__ double sqrt64(double x) { return x > 0.0 ? x * rsqrt6
 // FP32 (FP64 arithmetic is slow on this part); the objective values and the
 // parameters theta stay FP64.
 struct SelOpt {
-    double th[3], th_try[3];
+    float th[3], th_try[3];
     float g[3], dir[3], Binv[9];
-    double f;
+    DFloat f;                 // objective at th, an unevaluated FP32 pair
     float step, slope;
-    double flops, bytes;
+    long long pts;            // lag route: half-box points evaluated
+    double flops, bytes;      // FFT route: algorithmic work of the evaluations
     int iter, ls, done, evals, status, first;
     int fresh;   // the current direction comes from a reset (scaled steepest descent)
 };
+
+// a c - b^2 to about one FP32 ulp of the result however much the two
+// products cancel (Kahan's 2 x 2 determinant with fused multiply-adds)
+__device__ __forceinline__ float det2(float a, float b, float c) {
+    const float w = b * b;
+    const float e = fmaf(-b, b, w);   // w - b^2, exactly
+    return fmaf(a, c, -w) + e;
+}
 
 // H = R R^T, R = [[e^t0, 0], [t1, e^t2]].
 // Warp 0 of a CTA: trial point theta -> H, R and the two work items; every
 // lane returns false when H is outside the search domain (or needs a support
 // beyond the cap / a size with no spectrum).  All lanes run the same
 // straight-line FP32 code (lane s < nsig keeps covariance s), with the
-// determinants in FP64 where a strongly correlated H would cancel.  Every CTA
-// of a cluster computes the same items from the same theta.
-__device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<float>* it, double* Hs, double* Rs,
-                            double* aux) {
+// determinants in the compensated form of det2, which keeps a strongly
+// correlated H's cancellation exact.  Every CTA of a cluster computes the
+// same items from the same theta.  aux: determinant of H, work of the
+// evaluation (lag route: half-box points; FFT route: flops), bytes.
+__device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<float>* it, float* Hs, float* Rs,
+                            float* aux) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const float r00 = expf((float)th[0]), r11 = expf((float)th[2]), r10 = (float)th[1];
+    const float r00 = expf(th[0]), r11 = expf(th[2]), r10 = th[1];
     const float H[4] = {r00 * r00, r00 * r10, r10 * r00, fmaf(r10, r10, r11 * r11)};
     const float a = H[0], b = H[1], c = H[3];
-    const double det = (double)a * (double)c - (double)b * (double)b;
+    const float det = det2(a, b, c);
     // covariances: LSCV {2H, H}; SCV {2H + 2G, H + 2G, 2G}
     const int nsig = (p.method == 0) ? 2 : 3;
     const float gco = (p.method == 0) ? 0.f : 2.f;
@@ -1162,10 +1177,10 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
     float Ss[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) Ss[e] = fmaf(hco, H[e], gco * G[e]);
-    const double dts = (double)Ss[0] * (double)Ss[3] - (double)Ss[1] * (double)Ss[1];
-    const float rdt = __frcp_rn((float)dts);
+    const float dts = det2(Ss[0], Ss[1], Ss[3]);
+    const float rdt = __frcp_rn(dts);
     const float iv0 = Ss[3] * rdt, iv1 = -Ss[1] * rdt, iv3 = Ss[0] * rdt;
-    const float nr = 0.15915494f * rsqrtf((float)dts);   // 1 / (2 pi sqrt(det))
+    const float nr = 0.15915494f * rsqrtf(dts);   // 1 / (2 pi sqrt(det))
     // supports from lambda_max of H (LSCV, paper rule), 2H (LSCV widest) or 2H + 2G (SCV)
     const float bs = (p.method == 1 || p.widest) ? 2.f : 1.f;
     float B[4];
@@ -1181,7 +1196,7 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
     const int L0 = (int)v0, L1 = (int)v1;
     // the bandwidth is at least half a bin wide along each axis
     const float d0 = (float)p.delta0, d1 = (float)p.delta1;
-    const bool inside = a > 0.f && det > 0.0 && a >= 0.25f * d0 * d0 && c >= 0.25f * d1 * d1 && !(v0 != v0) &&
+    const bool inside = a > 0.f && det > 0.f && a >= 0.25f * d0 * d0 && c >= 0.25f * d1 * d1 && !(v0 != v0) &&
                         !(v1 != v1);
     if (!inside || L0 > p.Lcap || L1 > p.Lcap1) return false;
     // FFT route: the count spectrum of the padded size for (L0, L1)
@@ -1248,47 +1263,47 @@ __device__ bool sel_prepare(const SelectParams& p, const double* th, FusedItem<f
         it[1].W[1][1][5] = -1.f;
     }
     if (lane == 0) {
-        for (int e = 0; e < 4; ++e) Hs[e] = (double)H[e];
+        for (int e = 0; e < 4; ++e) Hs[e] = H[e];
         Rs[0] = r00;
         Rs[1] = r10;
         Rs[2] = r11;
         aux[0] = det;
-        if (p.acorr) {   // half box points: per covariance a quadratic form (8) and four six-term weighted sums (48)
-            const double pts = (double)(L0 + 1) * (2 * L1 + 1);
-            aux[1] = pts * nsig * (8.0 + 4.0 * 2.0 * 6.0);
-            aux[2] = pts * sizeof(float);
+        if (p.acorr) {   // half-box points (exact in FP32 below 2^24)
+            aux[1] = (float)((L0 + 1) * (2 * L1 + 1));
+            aux[2] = 0.f;
         } else {
             const SelSpec& sp = p.specs[si];
-            aux[1] = sp.fl_fix + (double)(2 * L0 + 1) * sp.fl_line;
-            aux[2] = sp.by;
+            aux[1] = (float)(sp.fl_fix + (double)(2 * L0 + 1) * sp.fl_line);
+            aux[2] = (float)sp.by;
         }
     }
     return true;
 }
 
 // objective, gradient in H (tied convention) -> value and theta-gradient
-// (FP32 algebra; the value is the FP64 sum of the device sums and the
-// closed-form term)
-__device__ void sel_assemble(const SelectParams& p, const double* H, const double* Rm, const double* r0,
-                             const double* r1, double det, double* f, float* gt) {
-    const float rdet = __frcp_rn((float)det);
-    const float rsd = rsqrtf((float)det);   // |H|^-1/2
-    const float rn = (float)p.inv_n;
-    const float hi00 = (float)H[3] * rdet, hi01 = -(float)H[1] * rdet, hi11 = (float)H[0] * rdet;
+// (FP32 algebra; the value is the FP32 pair sum of the device sum r[0] and
+// the closed-form term; r[1..3]: the sums of the three derivative grids)
+__device__ void sel_assemble(const SelectParams& p, const float* H, const float* Rm, const DFloat* r, float det,
+                             DFloat* f, float* gt) {
+    const float rdet = __frcp_rn(det);
+    const float rsd = rsqrtf(det);   // |H|^-1/2
+    const float rn = p.inv_nf;
+    const float hi00 = H[3] * rdet, hi01 = -H[1] * rdet, hi11 = H[0] * rdet;
+    const float r1 = r[1].h + r[1].l, r2 = r[2].h + r[2].l, r3 = r[3].h + r[3].l;
     float g00, g01, g11;
     if (p.method == 0) {
         const float k0 = 0.15915494f * rsd;   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
         const float c0 = 2.f * rn;
-        *f = r0[0] + (double)(c0 * k0);
-        g00 = (float)r0[1] + c0 * (-0.5f * k0 * hi00);
-        g01 = (float)r1[0] + c0 * 2.f * (-0.5f * k0 * hi01);
-        g11 = (float)r1[1] + c0 * (-0.5f * k0 * hi11);
+        *f = df_add(r[0], DFloat{c0 * k0, 0.f});
+        g00 = r1 + c0 * (-0.5f * k0 * hi00);
+        g01 = r2 + c0 * 2.f * (-0.5f * k0 * hi01);
+        g11 = r3 + c0 * (-0.5f * k0 * hi11);
     } else {
         const float rk = 0.07957747f * rsd;   // (4 pi)^-1 |H|^-1/2
-        *f = (double)(rk * rn) + r0[0];
-        g00 = (float)r0[1] + (-0.5f * rk * hi00) * rn;
-        g01 = (float)r1[0] + 2.f * (-0.5f * rk * hi01) * rn;
-        g11 = (float)r1[1] + (-0.5f * rk * hi11) * rn;
+        *f = df_add(r[0], DFloat{rk * rn, 0.f});
+        g00 = r1 + (-0.5f * rk * hi00) * rn;
+        g01 = r2 + 2.f * (-0.5f * rk * hi01) * rn;
+        g11 = r3 + (-0.5f * rk * hi11) * rn;
     }
     // dF/dR = 2 G_ind R (G_ind off-diagonal = g01 / 2), chain rule to theta
     const float G00 = g00, G01 = 0.5f * g01, G11 = g11;
@@ -1326,7 +1341,7 @@ __device__ void sel_new_direction(SelOpt& s) {
     }
     s.step = 1.f;
     s.ls = 0;
-    for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + (double)(s.step * s.dir[i]);
+    for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
 }
 
 // The line search gives up after this many halvings (the step then moves
@@ -1335,8 +1350,10 @@ __device__ void sel_new_direction(SelOpt& s) {
 // decrease test at smaller steps only measures those steps.
 constexpr int kMaxHalvings = 12;
 
-// consume the evaluation (fn, gn) of the trial point th_try
-__device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) {
+// consume the evaluation (fn, gn) of the trial point th_try.  The value is
+// an FP32 pair: the difference of two nearby values (Sterbenz: the leading
+// parts subtract exactly) keeps about 14 digits.
+__device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) {
     if (s.first) {
         s.first = 0;
         s.f = fn;
@@ -1344,7 +1361,7 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
             s.th[i] = s.th_try[i];
             s.g[i] = gn[i];
         }
-        if (!isfinite(fn)) {
+        if (!isfinite(fn.h)) {
             s.done = 1;
             s.status = 2;
             return;
@@ -1361,10 +1378,11 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
         sel_new_direction(s);
         return;
     }
-    if (isfinite(fn) && fn <= s.f + 1e-4 * (double)(s.step * s.slope)) {
+    const float df = (fn.h - s.f.h) + (fn.l - s.f.l);   // fn - f
+    if (isfinite(fn.h) && df <= 1e-4f * (s.step * s.slope)) {
         float sv[3], yv[3], sy = 0.f;
         for (int i = 0; i < 3; ++i) {
-            sv[i] = (float)(s.th_try[i] - s.th[i]);
+            sv[i] = s.th_try[i] - s.th[i];
             yv[i] = gn[i] - s.g[i];
             sy += sv[i] * yv[i];
         }
@@ -1381,7 +1399,6 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
                 for (int j = 0; j < 3; ++j)
                     s.Binv[i * 3 + j] += c1 * sv[i] * sv[j] - (By[i] * sv[j] + sv[i] * By[j]) * rsy;
         }
-        const double fold = s.f;
         float gm = 0.f, tn = 0.f;
         for (int i = 0; i < 3; ++i) {
             s.th[i] = s.th_try[i];
@@ -1394,8 +1411,7 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
         if (s.iter >= max_iter) {
             s.done = 1;
             s.status = 1;
-        } else if (fabs(fold - fn) <= 1e-12 * fabs(fn) + 1e-300 || tn < 1e-10f ||
-                   (double)gm < 1e-12 * (fabs(fn) + 1e-300)) {
+        } else if (fabsf(df) <= 1e-12f * fabsf(fn.h) + 1e-30f || tn < 1e-10f || gm < 1e-12f * (fabsf(fn.h) + 1e-30f)) {
             s.done = 1;
         } else {
             s.fresh = 0;
@@ -1415,7 +1431,7 @@ __device__ void sel_update(SelOpt& s, double fn, const float* gn, int max_iter) 
         } else if (s.ls > kMaxHalvings) {
             s.done = 1;
         } else {
-            for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + (double)(s.step * s.dir[i]);
+            for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
         }
     }
 }
@@ -1430,7 +1446,7 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     __shared__ FusedItem<float> items[2];
     __shared__ SelOpt opt;
     __shared__ int ctl[2];              // [valid, done] of this round
-    __shared__ double Hs[4], Rs[3], aux[3];
+    __shared__ float Hs[4], Rs[3], aux[3];
     C* gat = reinterpret_cast<C*>(smem_raw);
     float* spc = reinterpret_cast<float*>(gat + p.gat_elems);
     C* tw1 = reinterpret_cast<C*>(spc + p.spc_elems);
@@ -1441,13 +1457,14 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     const int start = blockIdx.x / p.cs;
     if (threadIdx.x == 0) {
         const SelStart& st = starts[start];
-        for (int i = 0; i < 3; ++i) opt.th_try[i] = st.th[i];
+        for (int i = 0; i < 3; ++i) opt.th_try[i] = (float)st.th[i];
         opt.first = 1;
         opt.done = 0;
         opt.iter = 0;
         opt.evals = 0;
         opt.status = 0;
-        opt.f = INFINITY;
+        opt.f = DFloat{INFINITY, 0.f};
+        opt.pts = 0;
         opt.flops = 0.0;
         opt.bytes = 0.0;
         opt.fresh = 0;
@@ -1472,13 +1489,20 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            double fn = INFINITY;
+            DFloat fn{INFINITY, 0.f};
             float gt[3] = {0.f, 0.f, 0.f};
             if (valid) {
-                sel_assemble(p, Hs, Rs, res[0], res[1], aux[0], &fn, gt);
+                // the cluster sums arrive in FP64: split each into an FP32 pair
+                DFloat r[4];
+                const double rv[4] = {res[0][0], res[0][1], res[1][0], res[1][1]};
+                for (int e = 0; e < 4; ++e) {
+                    const float h = (float)rv[e];
+                    r[e] = DFloat{h, (float)(rv[e] - (double)h)};
+                }
+                sel_assemble(p, Hs, Rs, r, aux[0], &fn, gt);
                 opt.evals++;
-                opt.flops += aux[1];
-                opt.bytes += aux[2];
+                opt.flops += (double)aux[1];
+                opt.bytes += (double)aux[2];
             }
             sel_update(opt, fn, gt, p.max_iter);
         }
@@ -1487,7 +1511,7 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     if (rank == 0 && threadIdx.x == 0) {
         SelStart& st = starts[start];
         for (int i = 0; i < 3; ++i) st.th[i] = opt.th[i];
-        st.f = opt.f;
+        st.f = (double)opt.f.h + (double)opt.f.l;
         st.evals = opt.evals;
         st.iters = opt.iter;
         st.status = opt.done ? opt.status : 1;
@@ -1540,7 +1564,7 @@ __device__ __forceinline__ void sel_grids(const FusedItem<float>& f, float x0, f
 // receives the four scaled totals in res4.
 template <int METHOD>
 __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const float* __restrict__ acorr, int A0,
-                                             int A1, double* res4) {
+                                             int A1, DFloat scale, DFloat* res4) {
     const int L0 = f.off0, L1 = f.off1;
     const int n0 = L0 + 1;
     const int total = n0 * (2 * L1 + 1);
@@ -1587,7 +1611,12 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
             }
         if (li == 0)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) res4[e] = ((double)v4[e].h + (double)v4[e].l) * f.scale;
+            for (int e = 0; e < 4; ++e) {   // times n^-2 as FP32 pairs
+                const float ph = v4[e].h * scale.h;
+                const float pl = fmaf(v4[e].h, scale.h, -ph) + fmaf(v4[e].h, scale.l, v4[e].l * scale.h);
+                const float h = ph + pl;
+                res4[e] = DFloat{h, pl - (h - ph)};
+            }
     }
 }
 
@@ -1596,17 +1625,18 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
 // read from the L2-resident FP32 copy).  The search state lives in the
 // caller's shared memory; `start` indexes the start table.
 __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* __restrict__ starts, int start,
-                                               const float* acorr, double (*res)[2], FusedItem<float>* items,
-                                               SelOpt& opt, int* ctl, double* Hs, double* Rs, double* aux) {
+                                               const float* acorr, DFloat* res, FusedItem<float>* items,
+                                               SelOpt& opt, int* ctl, float* Hs, float* Rs, float* aux) {
     if (threadIdx.x == 0) {
         const SelStart& st = starts[start];
-        for (int i = 0; i < 3; ++i) opt.th_try[i] = st.th[i];
+        for (int i = 0; i < 3; ++i) opt.th_try[i] = (float)st.th[i];
         opt.first = 1;
         opt.done = 0;
         opt.iter = 0;
         opt.evals = 0;
         opt.status = 0;
-        opt.f = INFINITY;
+        opt.f = DFloat{INFINITY, 0.f};
+        opt.pts = 0;
         opt.flops = 0.0;
         opt.bytes = 0.0;
         opt.fresh = 0;
@@ -1626,34 +1656,37 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
         const int valid = ctl[0], done = ctl[1];
         if (done) break;
         if (valid) {
+            const DFloat sc{p.inv_n2h, p.inv_n2l};
             if (p.method == 0)
-                sel_eval_lag<0>(items[0], acorr, p.A0, p.A1, &res[0][0]);
+                sel_eval_lag<0>(items[0], acorr, p.A0, p.A1, sc, res);
             else
-                sel_eval_lag<1>(items[0], acorr, p.A0, p.A1, &res[0][0]);
+                sel_eval_lag<1>(items[0], acorr, p.A0, p.A1, sc, res);
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            double fn = INFINITY;
+            DFloat fn{INFINITY, 0.f};
             float gt[3] = {0.f, 0.f, 0.f};
             if (valid) {
-                sel_assemble(p, Hs, Rs, res[0], res[1], aux[0], &fn, gt);
+                sel_assemble(p, Hs, Rs, res, aux[0], &fn, gt);
                 opt.evals++;
-                opt.flops += aux[1];
-                opt.bytes += aux[2];
+                opt.pts += (long long)aux[1];
             }
             sel_update(opt, fn, gt, p.max_iter);
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        // per half-box point and covariance: a quadratic form (8 flops) and
+        // four six-term weighted sums (48); 4 bytes of autocorrelation
+        const double nsig = (p.method == 0) ? 2.0 : 3.0;
         SelStart& st = starts[start];
         for (int i = 0; i < 3; ++i) st.th[i] = opt.th[i];
-        st.f = opt.f;
+        st.f = (double)opt.f.h + (double)opt.f.l;
         st.evals = opt.evals;
         st.iters = opt.iter;
         st.status = opt.done ? opt.status : 1;
-        st.flops = opt.flops;
-        st.bytes = opt.bytes;
+        st.flops = (double)opt.pts * nsig * 56.0;
+        st.bytes = (double)opt.pts * sizeof(float);
     }
 }
 
@@ -1663,11 +1696,11 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
 __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelectParams q, int nfirst,
                                                        SelStart* __restrict__ starts, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double res[2][2];
+    __shared__ DFloat res[4];
     __shared__ FusedItem<float> items[2];
     __shared__ SelOpt opt;
     __shared__ int ctl[2];
-    __shared__ double Hs[4], Rs[3], aux[3];
+    __shared__ float Hs[4], Rs[3], aux[3];
     // the autocorrelation box is fixed for the whole search: staged once in
     // shared memory when it fits (stage != 0)
     const float* acorr = p.acorr;

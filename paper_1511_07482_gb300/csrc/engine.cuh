@@ -168,6 +168,8 @@ struct SelectParams {
     int gat_elems, spc_elems, cap, pmax;   // shared-memory layout (complex / real elements)
     double n, tau;
     double inv_n, inv_n2;   // 1/n, 1/n^2
+    float inv_nf;           // 1/n in FP32
+    float inv_n2h, inv_n2l; // 1/n^2 as an FP32 pair (h + l)
     double delta0, delta1;
     double G[4];            // SCV pilot, row-major
     const int* ptab0;       // P_0 for support L_0 (index L_0 <= Lcap)
@@ -250,9 +252,12 @@ __host__ __device__ constexpr size_t acorr_smem_bytes(int P, int nl) {
     return sizeof(double2) * ((size_t)2 * (size_t)(nl * P + ((nl * P) >> 4) + 1) + (size_t)P);
 }
 // All jobs' passes of one level in one launch (one CTA per nl lines).
-// jobs_h: host table (rewritten with each job's blk0), jobs_d: device space
-// for it (n entries).
-cudaError_t launch_acorr_many(AcorrJob* jobs_h, AcorrJob* jobs_d, int n, const double2* twpool, cudaStream_t st);
+// acorr_plan (host) checks the table, writes each job's blk0 and returns the
+// CTA count and shared memory of the launch; launch_acorr runs the table
+// once it is on the device.
+cudaError_t acorr_plan(AcorrJob* jobs_h, int n, long long* blocks, size_t* sm);
+cudaError_t launch_acorr(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const double2* twpool,
+                         cudaStream_t st);
 
 // ---- kernel density estimate on the grid and mixture cross term (kde.cu)
 struct KdeDesc {
