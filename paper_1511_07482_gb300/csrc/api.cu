@@ -3530,6 +3530,14 @@ void grad_theta(const Opt& o, const double* th, const double* g, double* gt) {
 
 }  // namespace
 
+// FP32 copies of the search parameters (rounded once here, not per round)
+static void params_f32(SelectParams& q) {
+    q.tauf = (float)q.tau;
+    q.d0f = (float)q.delta0;
+    q.d1f = (float)q.delta1;
+    for (int e = 0; e < 4; ++e) q.Gf[e] = (float)q.G[e];
+}
+
 // Whether the device-resident search covers a criterion on this dataset:
 // d = 2, FP32, minimal padding, LSCV of Eq. 10 or SCV.
 static bool select2d_covered(kdefft_ds ds, int method) {
@@ -3617,6 +3625,7 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
         q.delta1 = ds->delta[1];
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) q.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gms[m](a, b) : 0.0;
+        params_f32(q);
         q.errflag = c->errflag;
         q.acorr = (const float*)ds->ac32.p;
         q.A0 = ds->acA[0];
@@ -3821,6 +3830,7 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     prm.delta1 = ds->delta[1];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) prm.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gm(a, b) : 0.0;
+    params_f32(prm);
     prm.ptab0 = (const int*)(db + oP);
     prm.ptab1 = (const int*)(db + oP) + (Lcap + 1);
     prm.specs = (const SelSpec*)db;

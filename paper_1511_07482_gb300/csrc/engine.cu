@@ -1171,7 +1171,7 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
     // covariances: LSCV {2H, H}; SCV {2H + 2G, H + 2G, 2G}
     const int nsig = (p.method == 0) ? 2 : 3;
     const float gco = (p.method == 0) ? 0.f : 2.f;
-    const float G[4] = {(float)p.G[0], (float)p.G[1], (float)p.G[2], (float)p.G[3]};
+    const float G[4] = {p.Gf[0], p.Gf[1], p.Gf[2], p.Gf[3]};
     const int sl = lane < nsig ? lane : 0;
     const float hco = (sl == 0) ? 2.f : (sl == 1 ? 1.f : 0.f);
     float Ss[4];
@@ -1188,14 +1188,14 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
     for (int e = 0; e < 4; ++e) B[e] = fmaf(bs, H[e], gco * G[e]);
     const float tr = 0.5f * (B[0] + B[3]), dd = 0.5f * (B[0] - B[3]);
     const float sq = sqrtf(fabsf(tr + sqrtf(fmaf(dd, dd, B[1] * B[1]))));
-    const float tau = (float)p.tau;
-    float v0 = ceilf(tau * sq * __frcp_rn((float)p.delta0));
-    float v1 = ceilf(tau * sq * __frcp_rn((float)p.delta1));
+    const float tau = p.tauf;
+    float v0 = ceilf(tau * sq * __frcp_rn(p.d0f));
+    float v1 = ceilf(tau * sq * __frcp_rn(p.d1f));
     v0 = fminf(fmaxf(v0, 1.f), (float)(p.M0 - 1));
     v1 = fminf(fmaxf(v1, 1.f), (float)(p.M1 - 1));
     const int L0 = (int)v0, L1 = (int)v1;
     // the bandwidth is at least half a bin wide along each axis
-    const float d0 = (float)p.delta0, d1 = (float)p.delta1;
+    const float d0 = p.d0f, d1 = p.d1f;
     const bool inside = a > 0.f && det > 0.f && a >= 0.25f * d0 * d0 && c >= 0.25f * d1 * d1 && !(v0 != v0) &&
                         !(v1 != v1);
     if (!inside || L0 > p.Lcap || L1 > p.Lcap1) return false;
@@ -1564,12 +1564,12 @@ __device__ __forceinline__ void sel_grids(const FusedItem<float>& f, float x0, f
 // receives the four scaled totals in res4.
 template <int METHOD>
 __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const float* __restrict__ acorr, int A0,
-                                             int A1, DFloat scale, DFloat* res4) {
+                                             int A1, float d0f, float d1f, DFloat scale, DFloat* res4) {
     const int L0 = f.off0, L1 = f.off1;
     const int n0 = L0 + 1;
     const int total = n0 * (2 * L1 + 1);
     const uint32_t mn0 = magic_of((uint32_t)max(n0, 2));
-    const float d0 = (float)f.delta0, d1 = (float)f.delta1;
+    const float d0 = d0f, d1 = d1f;
     // a thread holds a few points: plain FP32 sums there and across its warp
     // (the search compares values to FP32 accuracy; the reported value is
     // recomputed), compensated sums across the warps
@@ -1658,9 +1658,9 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
         if (valid) {
             const DFloat sc{p.inv_n2h, p.inv_n2l};
             if (p.method == 0)
-                sel_eval_lag<0>(items[0], acorr, p.A0, p.A1, sc, res);
+                sel_eval_lag<0>(items[0], acorr, p.A0, p.A1, p.d0f, p.d1f, sc, res);
             else
-                sel_eval_lag<1>(items[0], acorr, p.A0, p.A1, sc, res);
+                sel_eval_lag<1>(items[0], acorr, p.A0, p.A1, p.d0f, p.d1f, sc, res);
             __syncthreads();
         }
         if (threadIdx.x == 0) {

@@ -170,6 +170,8 @@ struct SelectParams {
     double inv_n, inv_n2;   // 1/n, 1/n^2
     float inv_nf;           // 1/n in FP32
     float inv_n2h, inv_n2l; // 1/n^2 as an FP32 pair (h + l)
+    float tauf, d0f, d1f;   // tau, delta_0, delta_1 rounded to FP32
+    float Gf[4];            // G rounded to FP32
     double delta0, delta1;
     double G[4];            // SCV pilot, row-major
     const int* ptab0;       // P_0 for support L_0 (index L_0 <= Lcap)
