@@ -360,6 +360,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h / args.steps)},
         "gpu_launches": int(launches),
         "kernel_times_ms": {k: round(v["ms"], 3) for k, v in kstats.items() if not k.startswith("host:")},
+        "kernel_work": {k: {"launches": v["launches"], "alg_bytes": v["bytes"], "alg_flops": v["flops"]}
+                        for k, v in kstats.items() if not k.startswith("host:")},
         "host_times_ms": {k[5:]: round(v["ms"], 3) for k, v in kstats.items() if k.startswith("host:")},
         "profiled_ms_per_step": sum(prof_times) / args.steps,
         "clocks": clk,
