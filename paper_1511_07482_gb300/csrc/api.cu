@@ -1587,8 +1587,21 @@ static int ensure_spectra(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, s
     long long scratch = 0;
     auto flush = [&]() -> int {
         if (items.empty()) return KDEFFT_OK;
+        // lines per tile: the default capacity, unless that leaves fewer than
+        // two tiles per SM in the first pass (one small grid): then fewer
+        // lines per tile, down to one line
+        long long work = 0;   // complex elements of the first pass
+        int pmax = 2;
+        for (const Item<real>& it : items) {
+            long long lines = 1;
+            for (int k = 0; k < it.d - 1; ++k) lines *= it.S[k];
+            work += lines * it.ax[it.d - 1].P;
+            for (int k = 0; k < it.d; ++k) pmax = std::max(pmax, it.ax[k].P);
+        }
+        const int cap = (int)std::max<long long>(pmax, std::min<long long>(cap_elems(sizeof(real) == 8),
+                                                                             work / (2LL * c->nsm)));
         PassLists pl;
-        for (size_t i = 0; i < items.size(); ++i) tile_item(items[i], (int)i, cap_elems(sizeof(real) == 8), pl);
+        for (size_t i = 0; i < items.size(); ++i) tile_item(items[i], (int)i, cap, pl);
         KCHK(launch_items<real>(c, items, pl, items[0].d, nullptr));
         for (size_t i = 0; i < keys.size(); ++i) keys[i].first->spectra[keys[i].second] = bufs[i];
         items.clear();
@@ -1652,12 +1665,14 @@ static long long pmin_smooth(long long m) {
 // least) when a request needs more.  Every dataset of `req` is brought up to
 // date with one batched spectrum launch sequence and stream-ordered passes
 // through context buffers (no synchronisation).
-// lines per CTA of an autocorrelation pass of length P: as many as fit 96 KB
-// of shared memory (two resident CTAs per SM), at least one
-static int acorr_lines(int P) {
+// lines per CTA of an autocorrelation pass of length P over `lines` lines:
+// as many as fit 96 KB of shared memory (two resident CTAs per SM), but no
+// more than leave two CTAs per SM busy; at least one
+static int acorr_lines(int P, long long lines, int nsm) {
     int nl = 1;
     while (nl < 64 && acorr_smem_bytes(P, nl + 1) <= (size_t)96 * 1024) ++nl;
-    return nl;
+    const long long spread = std::max<long long>(1, lines / (2LL * nsm));
+    return (int)std::min<long long>(nl, spread);
 }
 
 static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& req) {
@@ -1792,7 +1807,7 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                     a.jlo = (k == 0) ? 0 : -jb.A[k];
                     a.ap.tw_off = twiddle_offset(c, jb.P[k]);
                     if (!radix_plan(jb.P[k], a.ap, 16)) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
-                    a.nl = acorr_lines(jb.P[k]);
+                    a.nl = acorr_lines(jb.P[k], a.O * a.I, c->nsm);
                     a.half = last ? 1 : 0;
                     a.scale = last ? 1.0 / pl.ptot : 1.0;
                     if (last) {
