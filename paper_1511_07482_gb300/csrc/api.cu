@@ -1912,9 +1912,10 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         double nrm[MAXSIG];
     };
     std::vector<SpecInv> sinv(rs.specs.size());
-    // fixed tiles of 4096 points: an item's sum depends on the item alone,
-    // not on the batch it came in
-    const long long T = 4096;
+    // fixed tiles (4096 points in FP32, 512 in FP64, whose slower points need
+    // more CTAs in flight): an item's sum depends on the item alone, not on
+    // the batch it came in
+    const long long T = dbl ? 512 : 4096;
     for (size_t u : ord) {
         const auto& pr = pairs[u];
         const GridReq& g = rs.grids[pr.first];
