@@ -2716,17 +2716,11 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     }
     prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
     // moments for the normal-scale start point
-    c->launches += 2;
-    // (block partials summed here in block order: the same start point from run to run)
+    c->launches += 3;
+    // (block partials summed in block order: the same start point from run to run)
     std::vector<double> part((size_t)mblk * d * d);
     KCU(launch_moments(dX, n, d, 0, nullptr, dPart, c->nsm, c->stream));
-    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * d, cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaStreamSynchronize(c->stream));
-    double hm[8] = {0};
-    for (int b = 0; b < mblk; ++b)
-        for (int k = 0; k < d; ++k) hm[k] += part[(size_t)b * d + k];
-    for (int k = 0; k < d; ++k) hm[k] /= (double)n;
-    KCU(cudaMemcpyAsync(dMean, hm, sizeof(double) * 8, cudaMemcpyHostToDevice, c->stream));
+    KCU(launch_moments_mean(dPart, mblk, d, n, dMean, c->stream));
     KCU(launch_moments(dX, n, d, 1, dMean, dPart, c->nsm, c->stream));
     unsigned long long nout = 0;
     double hc[16] = {0};
@@ -3667,7 +3661,7 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
         c->pending.back().bytes = by;
     }
     prof_flush(c);
-    KCHK(check_errflag(c));
+    // (k_select2d_lag has no bounded waits, so it never raises the error flag)
     th_outs.assign(nm, {});
     f_outs.assign(nm, {});
     evals_out.assign(nm, 0);

@@ -234,6 +234,22 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ X, l
     }
 }
 
+// the sample mean from the first pass's block partials, summed in block
+// order (the same result from run to run), for the second pass on the device
+__global__ void k_moments_mean(const double* __restrict__ part, int nblk, int d, long long n,
+                               double* __restrict__ mean) {
+    const int k = threadIdx.x;
+    if (k >= d) return;
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += part[(size_t)b * d + k];
+    mean[k] = t / (double)n;
+}
+
+cudaError_t launch_moments_mean(const double* part, int nblk, int d, long long n, double* mean, cudaStream_t st) {
+    k_moments_mean<<<1, 32, 0, st>>>(part, nblk, d, n, mean);
+    return cudaGetLastError();
+}
+
 int moments_blocks(long long n, int nsm) { return blocks_for(n, nsm, 2); }
 
 cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
