@@ -511,6 +511,7 @@ struct kdefft_ctx_s {
     DevBuf acbuf[2];          // pass buffers of the autocorrelation (stream-ordered reuse)
     DevBuf acjobs;            // job table of the batched autocorrelation passes
     HostBuf h_acjobs;         // its pinned staging copy, free once acjobs_ev has passed
+    HostBuf h_sel;            // pinned start / end table of the lag-domain device search
     cudaEvent_t acjobs_ev = nullptr;
     bool acjobs_free = true;
     DevBuf binjobs;           // job tables of the batched binning
@@ -2625,6 +2626,7 @@ int kdefft_destroy(kdefft_ctx c) {
     if (c->staging_ev) cudaEventDestroy(c->staging_ev);
     if (c->acjobs_ev) cudaEventDestroy(c->acjobs_ev);
     c->h_acjobs.release();
+    c->h_sel.release();
     if (c->errflag) cudaFree(c->errflag);
     delete c;
     return KDEFFT_OK;
@@ -3603,7 +3605,11 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
     const int nst = first[nm];
     const size_t bT = sizeof(SelStart) * nst;
     KCHK(c->sel_buf.ensure(bT));
-    std::vector<SelStart> st(nst);
+    // pinned start table: the copy and the search launch queue behind the
+    // autocorrelation passes without the host waiting for them (the table is
+    // free again after the synchronisation at the end of every search)
+    KCHK(c->h_sel.ensure(bT));
+    SelStart* st = (SelStart*)c->h_sel.p;
     for (int m = 0; m < nm; ++m)
         for (int i = 0; i < (int)th0s[m].size(); ++i) {
             SelStart& x = st[first[m] + i];
@@ -3611,7 +3617,7 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
             for (int k = 0; k < 3; ++k) x.th[k] = th0s[m][i][k];
         }
     SelStart* dst = (SelStart*)c->sel_buf.p;
-    KCU(cudaMemcpyAsync(dst, st.data(), bT, cudaMemcpyHostToDevice, c->stream));
+    KCU(cudaMemcpyAsync(dst, st, bT, cudaMemcpyHostToDevice, c->stream));
     c->h2d += (int64_t)bT;
     SelectParams prm[2]{};
     for (int m = 0; m < nm; ++m) {
@@ -3645,7 +3651,7 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
     cudaEvent_t ev = prof_start(c);
     KCU(launch_select2d_lag(prm[0], prm[1], first[1], dst, nst, c->stream));
     prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
-    KCU(cudaMemcpyAsync(st.data(), dst, bT, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaMemcpyAsync(st, dst, bT, cudaMemcpyDeviceToHost, c->stream));
     {
         HostTimer w(c, "host:wait");
         KCU(cudaStreamSynchronize(c->stream));
@@ -3653,9 +3659,9 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
     c->d2h += (int64_t)bT;
     if (c->prof && !c->pending.empty() && ev) {
         double fl = 0.0, by = 0.0;
-        for (const SelStart& x : st) {
-            fl += x.flops;
-            by += x.bytes;
+        for (int i = 0; i < nst; ++i) {
+            fl += st[i].flops;
+            by += st[i].bytes;
         }
         c->pending.back().flops = fl;
         c->pending.back().bytes = by;
