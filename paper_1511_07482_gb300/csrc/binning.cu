@@ -16,9 +16,12 @@
 // FP32 counts are accumulated in 64-bit fixed point (each weight rounded to
 // a multiple of 2^-K, K = 32 for samples below 2^31 points): integer sums do
 // not depend on the order of the atomic additions, so the counts, and every
-// objective value computed from them, are the same from run to run, and the
-// rounding of a weight (<= 2^-33) stays far below the FP32 rounding of the
-// count itself.  FP64 counts use FP64 atomics.
+// objective value computed from them, are the same from run to run.  Their
+// corner weights are FP32 products of the FP64 fractions rounded to FP32: a
+// weight's relative error of a few 2^-24 matches the FP32 rounding of the
+// count itself.  FP64 counts use FP64 weights and FP64 atomics.
+#include <type_traits>
+
 #include "engine.cuh"
 
 namespace kdefft {
@@ -40,9 +43,15 @@ __device__ __forceinline__ bool locate(const double* __restrict__ x, const GridD
     return true;
 }
 
-__device__ __forceinline__ void atomic_acc(double* p, double w, double) { atomicAdd(p, w); }
-__device__ __forceinline__ void atomic_acc(unsigned long long* p, double w, double qscale) {
-    atomicAdd(p, __double2ull_rn(w * qscale));
+// Fixed-point weight of a corner (units of 2^-K, qscale = 2^K) from FP32
+// factors: the location t, l, f stays FP64 as above, but the corner product
+// only feeds an FP32 count, and a few FP32 roundings of the weight stay at
+// the level of that count's own rounding (FP64 arithmetic is slow here).
+__device__ __forceinline__ unsigned long long corner_fixed(int d, int c, const float* ff, const float* gg,
+                                                           float qscale) {
+    float w = 1.f;
+    for (int k = 0; k < d; ++k) w *= ((c >> k) & 1) ? ff[k] : gg[k];
+    return __float2ull_rn(w * qscale);
 }
 
 template <typename acc>
@@ -65,6 +74,8 @@ __global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X
         }
     }
     const int ncorner = 1 << g.d;
+    constexpr bool fixed = std::is_same<acc, unsigned long long>::value;
+    const float qs = (float)qscale;   // 2^K, exact
     unsigned long long nout = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -75,18 +86,23 @@ __global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X
             ++nout;
             continue;
         }
-        for (int b = 0; b < ncorner; ++b) {
-            double w = 1.0;
-            long long idx = base;
+        float ff[MAXD], gg[MAXD];
+        if constexpr (fixed)
             for (int k = 0; k < g.d; ++k) {
-                const int bk = (b >> k) & 1;
-                w = __dmul_rn(w, bk ? f[k] : __dsub_rn(1.0, f[k]));
-                idx += bk * stride[k];
+                ff[k] = (float)f[k];
+                gg[k] = 1.f - ff[k];
             }
-            if (use_smem)
-                atomic_acc(hist + idx, w, qscale);
-            else
-                atomic_acc(counts + idx, w, qscale);
+        for (int b = 0; b < ncorner; ++b) {
+            long long idx = base;
+            for (int k = 0; k < g.d; ++k) idx += ((b >> k) & 1) * stride[k];
+            acc* dst = use_smem ? hist + idx : counts + idx;
+            if constexpr (fixed) {
+                atomicAdd(dst, corner_fixed(g.d, b, ff, gg, qs));
+            } else {
+                double w = 1.0;
+                for (int k = 0; k < g.d; ++k) w = __dmul_rn(w, ((b >> k) & 1) ? f[k] : __dsub_rn(1.0, f[k]));
+                atomicAdd(dst, w);
+            }
         }
     }
     if (nout) atomicAdd(outside, nout);
@@ -236,17 +252,24 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ X, l
 
 // the sample mean from the first pass's block partials, summed in block
 // order (the same result from run to run), for the second pass on the device
-__global__ void k_moments_mean(const double* __restrict__ part, int nblk, int d, long long n,
-                               double* __restrict__ mean) {
+// (the partials are staged in shared memory by the whole block first, so
+// that the ordered sum waits on no global load)
+__global__ void __launch_bounds__(256) k_moments_mean(const double* __restrict__ part, int nblk, int d, long long n,
+                                                      double* __restrict__ mean) {
+    extern __shared__ double sp[];
+    for (int t = threadIdx.x; t < nblk * d; t += blockDim.x) sp[t] = part[t];
+    __syncthreads();
     const int k = threadIdx.x;
     if (k >= d) return;
     double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += part[(size_t)b * d + k];
+    for (int b = 0; b < nblk; ++b) t += sp[(size_t)b * d + k];
     mean[k] = t / (double)n;
 }
 
 cudaError_t launch_moments_mean(const double* part, int nblk, int d, long long n, double* mean, cudaStream_t st) {
-    k_moments_mean<<<1, 32, 0, st>>>(part, nblk, d, n, mean);
+    const size_t sm = sizeof(double) * (size_t)nblk * d;   // nblk <= 2 per SM: a few KB
+    if (sm > 48 * 1024) return cudaErrorInvalidValue;
+    k_moments_mean<<<1, 256, sm, st>>>(part, nblk, d, n, mean);
     return cudaGetLastError();
 }
 
@@ -302,15 +325,16 @@ __global__ void __launch_bounds__(256) k_bin_many(const BinJob* __restrict__ job
                 ++nout;
                 continue;
             }
+            float ff[MAXD], gg[MAXD];
+            for (int k = 0; k < d; ++k) {
+                ff[k] = (float)f[k];
+                gg[k] = 1.f - ff[k];
+            }
+            const float qs = (float)qscale;
             for (int c = 0; c < ncorner; ++c) {
-                double w = 1.0;
                 long long idx = base;
-                for (int k = 0; k < d; ++k) {
-                    const int bk = (c >> k) & 1;
-                    w = __dmul_rn(w, bk ? f[k] : __dsub_rn(1.0, f[k]));
-                    idx += bk * stride[k];
-                }
-                atomicAdd(jb.fix + idx, __double2ull_rn(w * qscale));
+                for (int k = 0; k < d; ++k) idx += ((c >> k) & 1) * stride[k];
+                atomicAdd(jb.fix + idx, corner_fixed(d, c, ff, gg, qs));
             }
         }
         if (nout) atomicAdd(jb.outside, nout);
