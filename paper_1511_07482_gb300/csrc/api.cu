@@ -2680,13 +2680,12 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
         c->h2d += (int64_t)(sizeof(double) * n * d);
         dX = (const double*)xbuf.p;
     }
-    // outside counter | mean | block partials of the moments
+    // outside counter | block partials of the moments
     const int mblk = moments_blocks(n, c->nsm);
     DevBuf misc(&c->cache);
-    KCHK(misc.ensure(sizeof(double) * (16 + (size_t)mblk * d * d)));
+    KCHK(misc.ensure(sizeof(double) * (16 + (size_t)mblk * (d + d * d))));
     KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
     unsigned long long* dOut = (unsigned long long*)misc.p;
-    double* dMean = (double*)misc.p + 8;
     double* dPart = (double*)misc.p + 16;
     const bool dbl = o.precision == KDEFFT_FP64;
     KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));
@@ -2717,22 +2716,26 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
                               c->stream));
     }
     prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
-    // moments for the normal-scale start point
-    c->launches += 3;
-    // (block partials summed in block order: the same start point from run to run)
-    std::vector<double> part((size_t)mblk * d * d);
-    KCU(launch_moments(dX, n, d, 0, nullptr, dPart, c->nsm, c->stream));
-    KCU(launch_moments_mean(dPart, mblk, d, n, dMean, c->stream));
-    KCU(launch_moments(dX, n, d, 1, dMean, dPart, c->nsm, c->stream));
+    // covariance for the normal-scale start point, in one pass shifted by the
+    // grid's centre (block partials summed in block order: the same start
+    // point from run to run)
+    c->launches += 1;
+    const int nv = d + d * d;
+    std::vector<double> part((size_t)mblk * nv);
+    Shift sh{};
+    for (int k = 0; k < d; ++k) sh.s[k] = 0.5 * (lo[k] + hi[k]);
+    KCU(launch_moments_shifted(dX, n, d, sh, dPart, c->nsm, c->stream));
     unsigned long long nout = 0;
-    double hc[16] = {0};
+    double hs[20] = {0};
     KCU(cudaMemcpyAsync(&nout, dOut, sizeof(nout), cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * d * d, cudaMemcpyDeviceToHost, c->stream));
+    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * nv, cudaMemcpyDeviceToHost, c->stream));
     KCU(cudaStreamSynchronize(c->stream));
     for (int b = 0; b < mblk; ++b)
-        for (int v = 0; v < d * d; ++v) hc[v] += part[(size_t)b * d * d + v];
+        for (int v = 0; v < nv; ++v) hs[v] += part[(size_t)b * nv + v];
     prof_flush(c);
-    for (int i = 0; i < d * d; ++i) ds->cov[i] = (n > 1) ? hc[i] / (double)(n - 1) : 0.0;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b)
+            ds->cov[a * d + b] = (n > 1) ? (hs[d + a * d + b] - hs[a] * hs[b] / (double)n) / (double)(n - 1) : 0.0;
     if (nout > 0 && o.outside_policy == KDEFFT_OUTSIDE_ERROR)
         return fail(KDEFFT_ERR_OUTSIDE_GRID, std::to_string(nout) + " sample points outside the grid");
     ds->dropped = (int64_t)nout;

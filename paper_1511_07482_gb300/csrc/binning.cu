@@ -250,6 +250,43 @@ __global__ void __launch_bounds__(256) k_moments(const double* __restrict__ X, l
     }
 }
 
+// One pass for the covariance: block sums of x - s and (x - s)(x - s)^T
+// with a fixed shift s inside the data (the grid's centre), from which
+// cov = (S2 - S1 S1^T / n) / (n - 1); with s near the mean the subtraction
+// loses little.  out: per block d + d^2 values.
+__global__ void __launch_bounds__(256) k_moments_shifted(const double* __restrict__ X, long long n, int d, Shift sh,
+                                                         double* __restrict__ out) {
+    double acc[MAXD + MAXD * MAXD];
+    const int nv = d + d * d;
+    for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double x[MAXD];
+        for (int k = 0; k < d; ++k) x[k] = X[i * d + k] - sh.s[k];
+        for (int k = 0; k < d; ++k) acc[k] += x[k];
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) acc[d + a * d + b] += x[a] * x[b];
+    }
+    __shared__ double red[8][MAXD + MAXD * MAXD];
+    for (int v = 0; v < nv; ++v) {
+        double t = acc[v];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][v] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        out[(size_t)blockIdx.x * nv + threadIdx.x] = t;   // block partial; summed in block order by the host
+    }
+}
+
+cudaError_t launch_moments_shifted(const double* X, long long n, int d, const Shift& sh, double* out, int nsm,
+                                   cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_moments_shifted<<<moments_blocks(n, nsm), 256, 0, st>>>(X, n, d, sh, out);
+    return cudaGetLastError();
+}
+
 // the sample mean from the first pass's block partials, summed in block
 // order (the same result from run to run), for the second pass on the device
 // (the partials are staged in shared memory by the whole block first, so
