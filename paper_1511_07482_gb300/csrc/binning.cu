@@ -219,38 +219,8 @@ cudaError_t launch_int_to_real(const int* src, real* dst, long long n, cudaStrea
     return cudaGetLastError();
 }
 
-// Sample moments for the normal-scale start point: pass 0 sums x_k, pass 1
-// sums (x_k - mean_k)(x_l - mean_l); FP64 block sums, atomically combined.
-__global__ void __launch_bounds__(256) k_moments(const double* __restrict__ X, long long n, int d, int pass,
-                                                 const double* __restrict__ mean, double* __restrict__ out) {
-    double acc[MAXD * MAXD];
-    const int nv = pass == 0 ? d : d * d;
-    for (int v = 0; v < nv; ++v) acc[v] = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double x[MAXD];
-        for (int k = 0; k < d; ++k) x[k] = X[i * d + k] - (pass ? mean[k] : 0.0);
-        if (pass == 0) {
-            for (int k = 0; k < d; ++k) acc[k] += x[k];
-        } else {
-            for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) acc[a * d + b] += x[a] * x[b];
-        }
-    }
-    __shared__ double red[8][MAXD * MAXD];
-    for (int v = 0; v < nv; ++v) {
-        double t = acc[v];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][v] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < nv) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
-        out[(size_t)blockIdx.x * nv + threadIdx.x] = t;   // block partial; summed in block order by the host
-    }
-}
-
-// One pass for the covariance: block sums of x - s and (x - s)(x - s)^T
+// Sample covariance for the normal-scale start point, in one pass: FP64
+// block sums of x - s and (x - s)(x - s)^T
 // with a fixed shift s inside the data (the grid's centre), from which
 // cov = (S2 - S1 S1^T / n) / (n - 1); with s near the mean the subtraction
 // loses little.  out: per block d + d^2 values.
@@ -287,37 +257,8 @@ cudaError_t launch_moments_shifted(const double* X, long long n, int d, const Sh
     return cudaGetLastError();
 }
 
-// the sample mean from the first pass's block partials, summed in block
-// order (the same result from run to run), for the second pass on the device
-// (the partials are staged in shared memory by the whole block first, so
-// that the ordered sum waits on no global load)
-__global__ void __launch_bounds__(256) k_moments_mean(const double* __restrict__ part, int nblk, int d, long long n,
-                                                      double* __restrict__ mean) {
-    extern __shared__ double sp[];
-    for (int t = threadIdx.x; t < nblk * d; t += blockDim.x) sp[t] = part[t];
-    __syncthreads();
-    const int k = threadIdx.x;
-    if (k >= d) return;
-    double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += sp[(size_t)b * d + k];
-    mean[k] = t / (double)n;
-}
-
-cudaError_t launch_moments_mean(const double* part, int nblk, int d, long long n, double* mean, cudaStream_t st) {
-    const size_t sm = sizeof(double) * (size_t)nblk * d;   // nblk <= 2 per SM: a few KB
-    if (sm > 48 * 1024) return cudaErrorInvalidValue;
-    k_moments_mean<<<1, 256, sm, st>>>(part, nblk, d, n, mean);
-    return cudaGetLastError();
-}
-
 int moments_blocks(long long n, int nsm) { return blocks_for(n, nsm, 2); }
 
-cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
-                           cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_moments<<<moments_blocks(n, nsm), 256, 0, st>>>(X, n, d, pass, mean, out);
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------ batched binning
 __device__ __forceinline__ int bin_job_of(const BinJob* __restrict__ jobs, int n, long long b) {

@@ -329,18 +329,14 @@ struct BinJob {
 };
 cudaError_t launch_bin_many(BinJob* jobs_h, BinJob* jobs_d, int n, int phase, double qscale, cudaStream_t st);
 
-// pass 0: out[blk*d + k] = block sums of X_ik; pass 1: out[blk*d*d + a*d+b] =
-// block sums of (X_ia - mean_a)(X_ib - mean_b), blk < moments_blocks(n, nsm)
+// blocks of the moment launches (at most two per SM)
 int moments_blocks(long long n, int nsm);
-// one pass: per block sums of x - s and (x - s)(x - s)^T (d + d^2 values)
+// one pass: per block b, out[b (d + d^2) + k] = sum of x_k - s_k and
+// out[b (d + d^2) + d + a d + c] = sum of (x_a - s_a)(x_c - s_c)
 struct Shift {
     double s[MAXD];
 };
 cudaError_t launch_moments_shifted(const double* X, long long n, int d, const Shift& sh, double* out, int nsm,
                                    cudaStream_t st);
-// mean[k] = (sum of the first pass's block partials in block order) / n
-cudaError_t launch_moments_mean(const double* part, int nblk, int d, long long n, double* mean, cudaStream_t st);
-cudaError_t launch_moments(const double* X, long long n, int d, int pass, const double* mean, double* out, int nsm,
-                           cudaStream_t st);
 
 }  // namespace kdefft
