@@ -480,6 +480,7 @@ static bool is_smooth(long long x) {
 
 // ============================================================ context & dataset
 struct kdefft_ds_s;
+struct ReqSet;
 
 struct kdefft_ctx_s {
     int device = 0;
@@ -491,6 +492,16 @@ struct kdefft_ctx_s {
     size_t tw_dev_n = 0;              // twiddles resident on the device
     DevBuf scratch, partial, items, tiles, out;
     HostBuf h_items, h_out;
+    // lag-domain results on their way to h_out, not yet read: run_lag returns
+    // without waiting, and flush_reads (at the end of run()) waits once for
+    // all of them
+    struct PendingRead {
+        ReqSet* rs;
+        std::vector<std::pair<int, int>> pairs;   // grid pairs in the order of their results
+        size_t off;                               // first double in h_out
+    };
+    std::vector<PendingRead> pend_reads;
+    size_t hout_used = 0;       // doubles of h_out holding pending results
     bool staging_free = true;   // no copy out of h_items is pending on the stream
     cudaEvent_t staging_ev = nullptr;   // recorded after the last copy out of h_items
     // counters: kernel launches and host<->device bytes (always), per-kernel
@@ -1282,11 +1293,30 @@ static void tile_item(Item<real>& it, int idx, int cap, PassLists& pl) {
     }
 }
 
+// Wait for the pending lag-domain results and store them in their requests.
+static int flush_reads(kdefft_ctx c) {
+    if (c->pend_reads.empty()) return KDEFFT_OK;
+    {
+        HostTimer w(c, "host:wait");
+        KCU(cudaStreamSynchronize(c->stream));
+    }
+    const double* o = (const double*)c->h_out.p;
+    for (const auto& pr : c->pend_reads)
+        for (size_t i = 0; i < pr.pairs.size(); ++i) {
+            pr.rs->grids[pr.pairs[i].first].value = o[pr.off + 2 * i];
+            if (pr.pairs[i].second >= 0) pr.rs->grids[pr.pairs[i].second].value = o[pr.off + 2 * i + 1];
+        }
+    c->pend_reads.clear();
+    c->hout_used = 0;
+    return KDEFFT_OK;
+}
+
 template <typename real>
 static int launch_items(kdefft_ctx c, std::vector<Item<real>>& items, PassLists& pl, int d, double* out_host) {
     using C = typename Cpx<real>::T;
     const int nitems = (int)items.size();
     if (nitems == 0) return KDEFFT_OK;
+    if (out_host) KCHK(flush_reads(c));   // h_out is about to be rewritten
     KCHK(sync_twiddles(c));
     // d = 1: the single stage-A tile of each item owns partial slot tileF0
     if (d == 1) {
@@ -1453,6 +1483,7 @@ template <typename real>
 static int launch_fused(kdefft_ctx c, std::vector<Item<real>>& items, double* out_host) {
     using C = typename Cpx<real>::T;
     const int nitems = (int)items.size();
+    KCHK(flush_reads(c));   // h_out is about to be rewritten
     const size_t budget = 200 * 1024;
     int rmax = 0;
     for (const Item<real>& it : items) rmax = std::max(rmax, it.R);
@@ -1985,7 +2016,13 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     KCHK(c->items.ensure(bytes));
     KCHK(c->partial.ensure(sizeof(double) * 2 * tiles.size()));
     KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
-    KCHK(c->h_out.ensure(sizeof(double) * 2 * nitems));
+    // results go behind those of earlier lag launches still on their way
+    const size_t need = 2 * (size_t)nitems;
+    if (c->h_out.cap < sizeof(double) * (c->hout_used + need)) {
+        KCHK(flush_reads(c));
+        KCHK(c->h_out.ensure(sizeof(double) * need));
+    }
+    const size_t off = c->hout_used;
     unsigned char* h = (unsigned char*)c->h_items.p;
     std::memcpy(h, items.data(), bI);
     std::memcpy(h + oT, tiles.data(), bT);
@@ -2007,7 +2044,7 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     std::vector<long long> sig = {3, (long long)sizeof(real), d, nitems, (long long)tiles.size(),
                                   (long long)(uintptr_t)dbase, (long long)(uintptr_t)h, (long long)bytes,
                                   (long long)(uintptr_t)part, (long long)(uintptr_t)c->out.p,
-                                  (long long)(uintptr_t)c->h_out.p};
+                                  (long long)(uintptr_t)c->h_out.p, (long long)off};
     for (const auto& cl : classes) {
         sig.push_back(cl[0]);
         sig.push_back(cl[1]);
@@ -2024,24 +2061,19 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         cudaEvent_t ev = prof_start(c);
         KCU(launch_lag_reduce<real>(dI, nitems, part, (double*)c->out.p, c->stream));
         prof_stop(c, ev, "reduce", 16.0 * tiles.size(), 2.0 * tiles.size());
-        KCU(cudaMemcpyAsync(c->h_out.p, c->out.p, sizeof(double) * 2 * nitems, cudaMemcpyDeviceToHost, c->stream));
+        KCU(cudaMemcpyAsync((double*)c->h_out.p + off, c->out.p, sizeof(double) * need, cudaMemcpyDeviceToHost,
+                            c->stream));
         return KDEFFT_OK;
     };
     KCHK(staging_upload(c, dbase, bytes));
     KCHK(run_graph(c, sig, issue));
     c->h2d += (int64_t)bytes;
-    {
-        HostTimer w(c, "host:wait");
-        KCU(cudaStreamSynchronize(c->stream));
-    }
-    c->staging_free = true;
-    c->d2h += (int64_t)(sizeof(double) * 2 * nitems);
-    const double* o = (const double*)c->h_out.p;
-    for (size_t i = 0; i < ord.size(); ++i) {
-        const auto& pr = pairs[ord[i]];
-        rs.grids[pr.first].value = o[2 * i];
-        if (pr.second >= 0) rs.grids[pr.second].value = o[2 * i + 1];
-    }
+    c->d2h += (int64_t)(sizeof(double) * need);
+    kdefft_ctx_s::PendingRead pr{&rs, {}, off};
+    pr.pairs.reserve(ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) pr.pairs.push_back(pairs[ord[i]]);
+    c->pend_reads.push_back(std::move(pr));
+    c->hout_used += need;
     prof_flush(c);
     return KDEFFT_OK;
 }
@@ -2273,8 +2305,12 @@ static int run(kdefft_ctx c, ReqSet& rs) {
         const GridReq& g = rs.grids[i];
         ((g.fp64 || g.ds->opts.precision == KDEFFT_FP64) ? s64 : s32).push_back((int)i);
     }
-    KCHK(run_requests<double>(c, rs, s64));
-    return run_requests<float>(c, rs, s32);
+    int r = run_requests<double>(c, rs, s64);
+    if (r == KDEFFT_OK) r = run_requests<float>(c, rs, s32);
+    // the lag launches of both precisions are in flight: one wait for all
+    // (also on an error, as the pending reads point into rs)
+    const int f = flush_reads(c);
+    return r != KDEFFT_OK ? r : f;
 }
 
 // ============================================================ objective assembly
@@ -3023,20 +3059,39 @@ int kdefft_psi(kdefft_ds ds, const double* H, int nH, int r, double* out) {
     return write_out(ds->ctx, out, res.data(), res.size());
 }
 
-static int eval_lscv(kdefft_ds ds, const double* H, int nH, std::vector<double>& val, std::vector<double>* grad) {
+// LSCV at nH bandwidths in two halves around run(): the requests, then the
+// assembly, so that several criteria can share one run()
+struct LscvJob {
+    std::vector<int> first;
+    std::vector<Mat> Hs;
+};
+
+static int lscv_requests(ReqSet& rs, kdefft_ds ds, const double* H, int nH, bool grad, LscvJob& j) {
     const int d = ds->d;
-    ReqSet rs;
-    std::vector<int> first(nH);
-    std::vector<Mat> Hs(nH);
+    j.first.assign(nH, 0);
+    j.Hs.assign(nH, Mat());
     for (int h = 0; h < nH; ++h) {
-        KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
-        KCHK(add_lscv(rs, ds, Hs[h], grad != nullptr, first[h]));
+        KCHK(sym_check(H + (size_t)h * d * d, d, j.Hs[h], "H"));
+        KCHK(add_lscv(rs, ds, j.Hs[h], grad, j.first[h]));
     }
-    KCHK(run(ds->ctx, rs));
+    return KDEFFT_OK;
+}
+
+static void lscv_assemble(const ReqSet& rs, kdefft_ds ds, const LscvJob& j, std::vector<double>& val,
+                          std::vector<double>* grad) {
+    const int d = ds->d, nH = (int)j.first.size();
     val.assign(nH, 0.0);
     if (grad) grad->assign((size_t)nH * d * d, 0.0);
     for (int h = 0; h < nH; ++h)
-        assemble_lscv(ds, Hs[h], &rs.grids[first[h]], &val[h], grad ? grad->data() + (size_t)h * d * d : nullptr);
+        assemble_lscv(ds, j.Hs[h], &rs.grids[j.first[h]], &val[h], grad ? grad->data() + (size_t)h * d * d : nullptr);
+}
+
+static int eval_lscv(kdefft_ds ds, const double* H, int nH, std::vector<double>& val, std::vector<double>* grad) {
+    ReqSet rs;
+    LscvJob j;
+    KCHK(lscv_requests(rs, ds, H, nH, grad != nullptr, j));
+    KCHK(run(ds->ctx, rs));
+    lscv_assemble(rs, ds, j, val, grad);
     return KDEFFT_OK;
 }
 
@@ -3053,17 +3108,31 @@ static std::vector<double> c2g_key(const Mat& G, const int* L, const int* P, int
     return k;
 }
 
-static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::vector<double>& val,
-                    std::vector<double>* grad, bool split64 = true) {
-    const int d = ds->d;
-    ReqSet rs;
-    std::vector<int> first(nH);
-    std::vector<Mat> Hs(nH);
-    std::vector<std::vector<double>> keys(nH);
+// SCV at nH bandwidths in the same two halves (the phi_2G sums missing from
+// the dataset's cache are requested too, and cached by the assembly)
+struct ScvJob {
+    std::vector<int> first;
+    std::vector<Mat> Hs;
+    std::vector<std::vector<double>> keys;
     std::map<std::vector<double>, int> missing;   // key -> grid index of its phi_2G request
+    bool split64 = true;
+};
+
+static int scv_requests(ReqSet& rs, kdefft_ds ds, const double* H, int nH, const Mat& G, bool grad, bool split64,
+                        ScvJob& j) {
+    const int d = ds->d;
+    j.first.assign(nH, 0);
+    j.Hs.assign(nH, Mat());
+    j.keys.assign(nH, {});
+    j.missing.clear();
+    j.split64 = split64;
+    std::vector<int>& first = j.first;
+    std::vector<Mat>& Hs = j.Hs;
+    std::vector<std::vector<double>>& keys = j.keys;
+    std::map<std::vector<double>, int>& missing = j.missing;
     for (int h = 0; h < nH; ++h) {
         KCHK(sym_check(H + (size_t)h * d * d, d, Hs[h], "H"));
-        KCHK(add_scv(rs, ds, Hs[h], G, grad != nullptr, split64, first[h]));
+        KCHK(add_scv(rs, ds, Hs[h], G, grad, split64, first[h]));
         const GridReq& g0 = rs.grids[first[h]];
         keys[h] = c2g_key(G, g0.L, g0.P, d);
         if (split64 && !ds->c2g.count(keys[h]) && !missing.count(keys[h])) {
@@ -3083,13 +3152,27 @@ static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::ve
             rs.grids.push_back(std::move(g));
         }
     }
-    KCHK(run(ds->ctx, rs));
-    for (auto& kv : missing) ds->c2g[kv.first] = rs.grids[kv.second].value;
+    return KDEFFT_OK;
+}
+
+static void scv_assemble(const ReqSet& rs, kdefft_ds ds, const ScvJob& j, std::vector<double>& val,
+                         std::vector<double>* grad) {
+    const int d = ds->d, nH = (int)j.first.size();
+    for (const auto& kv : j.missing) ds->c2g[kv.first] = rs.grids[kv.second].value;
     val.assign(nH, 0.0);
     if (grad) grad->assign((size_t)nH * d * d, 0.0);
     for (int h = 0; h < nH; ++h)
-        assemble_scv(ds, Hs[h], &rs.grids[first[h]], split64, split64 ? ds->c2g[keys[h]] : 0.0, &val[h],
+        assemble_scv(ds, j.Hs[h], &rs.grids[j.first[h]], j.split64, j.split64 ? ds->c2g[j.keys[h]] : 0.0, &val[h],
                      grad ? grad->data() + (size_t)h * d * d : nullptr);
+}
+
+static int eval_scv(kdefft_ds ds, const double* H, int nH, const Mat& G, std::vector<double>& val,
+                    std::vector<double>* grad, bool split64 = true) {
+    ReqSet rs;
+    ScvJob j;
+    KCHK(scv_requests(rs, ds, H, nH, G, grad != nullptr, split64, j));
+    KCHK(run(ds->ctx, rs));
+    scv_assemble(rs, ds, j, val, grad);
     return KDEFFT_OK;
 }
 
@@ -3932,9 +4015,8 @@ static std::vector<Mat> start_bandwidths(const Mat& Hstart, int n_starts) {
 // its own FP32 values; SCV takes the FP64 route for its cancelling terms).
 // The LSCV value is evaluated with its gradient, as a caller checking
 // stationarity asks for it.
-static int finish_device_select(kdefft_ds ds, int method, const Mat& Gm, const std::vector<std::vector<double>>& tho,
-                                const std::vector<double>& fo, int64_t dev_evals, double* H_out, double* f_out,
-                                int64_t* n_evals) {
+static int device_best(kdefft_ds ds, const std::vector<std::vector<double>>& tho, const std::vector<double>& fo,
+                       double* H_out) {
     const int d = ds->d;
     const Opt o{d, class_params(d, KDEFFT_H_FULL)};
     int best = 0;
@@ -3944,6 +4026,13 @@ static int finish_device_select(kdefft_ds ds, int method, const Mat& Gm, const s
     Mat Hb = theta_to_H(o, tho[best].data());
     for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) H_out[a * d + b] = Hb(a, b);
+    return KDEFFT_OK;
+}
+
+static int finish_device_select(kdefft_ds ds, int method, const Mat& Gm, const std::vector<std::vector<double>>& tho,
+                                const std::vector<double>& fo, int64_t dev_evals, double* H_out, double* f_out,
+                                int64_t* n_evals) {
+    KCHK(device_best(ds, tho, fo, H_out));
     std::vector<double> v, gdummy;
     if (method == KDEFFT_SCV)
         KCHK(eval_scv(ds, H_out, 1, Gm, v, nullptr, /*split64=*/true));
@@ -4427,10 +4516,37 @@ extern "C" int kdefft_select_H_multi(kdefft_ds ds, int nmethods, const int* meth
                 continue;
             }
             KCHK(r);
-            for (size_t q = 0; q < ms.size(); ++q) {
-                const int m = idx[q];
-                KCHK(finish_device_select(ds, ms[q], Gms[q], tho[q], fo[q], ev[q], H_out + (size_t)m * d * d,
-                                          f_out ? f_out + m : nullptr, n_evals ? n_evals + m : nullptr));
+            if (ms.size() == 2 && ms[0] != ms[1]) {
+                // LSCV and SCV: both end-point values (the same requests as
+                // finish_device_select's) in one run, one wait
+                const int qL = ms[0] == KDEFFT_LSCV ? 0 : 1, qS = 1 - qL;
+                double* HL = H_out + (size_t)idx[qL] * d * d;
+                double* HS = H_out + (size_t)idx[qS] * d * d;
+                KCHK(device_best(ds, tho[qL], fo[qL], HL));
+                KCHK(device_best(ds, tho[qS], fo[qS], HS));
+                ReqSet rs;
+                LscvJob jl;
+                ScvJob js;
+                KCHK(lscv_requests(rs, ds, HL, 1, true, jl));
+                KCHK(scv_requests(rs, ds, HS, 1, Gms[qS], false, /*split64=*/true, js));
+                KCHK(run(ds->ctx, rs));
+                std::vector<double> vl, gl, vs;
+                lscv_assemble(rs, ds, jl, vl, &gl);
+                scv_assemble(rs, ds, js, vs, nullptr);
+                if (f_out) {
+                    f_out[idx[qL]] = vl[0];
+                    f_out[idx[qS]] = vs[0];
+                }
+                if (n_evals) {
+                    n_evals[idx[qL]] = ev[qL] + 1;
+                    n_evals[idx[qS]] = ev[qS] + 1;
+                }
+            } else {
+                for (size_t q = 0; q < ms.size(); ++q) {
+                    const int m = idx[q];
+                    KCHK(finish_device_select(ds, ms[q], Gms[q], tho[q], fo[q], ev[q], H_out + (size_t)m * d * d,
+                                              f_out ? f_out + m : nullptr, n_evals ? n_evals + m : nullptr));
+                }
             }
         }
     }
