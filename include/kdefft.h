@@ -100,6 +100,9 @@ int kdefft_opts_default(kdefft_opts* opts);
  * Fails with KDEFFT_ERR_CUDA when no usable GPU is present: there is no CPU
  * fallback. */
 int kdefft_create(kdefft_ctx* ctx, int device, void* stream);
+/* Destroy a context and every dataset still open on it.  A handle that is
+ * not live (destroyed already, or never created) is KDEFFT_ERR_ARG; NULL is
+ * a no-op.  The same holds for kdefft_ds_destroy. */
 int kdefft_destroy(kdefft_ctx ctx);
 
 /* Step 1 of Sec. 4: bin the sample X (n x d FP64 row-major; host or device)

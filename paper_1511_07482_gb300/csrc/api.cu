@@ -20,6 +20,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -2429,6 +2430,20 @@ static int write_out(kdefft_ctx c, double* dst, const double* src, size_t count)
 }
 
 // ============================================================ C ABI
+// Handles the library has handed out and not yet destroyed: a destroy call
+// checks its handle here before touching it, so that a second destroy of the
+// same handle is an error, not a use after free.
+static std::mutex g_live_mu;
+static std::set<const void*> g_live;
+static void live_add(const void* h) {
+    std::lock_guard<std::mutex> g(g_live_mu);
+    g_live.insert(h);
+}
+static bool live_take(const void* h) {
+    std::lock_guard<std::mutex> g(g_live_mu);
+    return g_live.erase(h) > 0;
+}
+
 static void ds_free(kdefft_ds ds) {
     HostTimer ht(ds->ctx, "host:close");
     cudaSetDevice(ds->ctx->device);
@@ -2509,6 +2524,7 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         return r;
     }
     *out = c;
+    live_add(c);
     return KDEFFT_OK;
 }
 
@@ -2630,9 +2646,13 @@ int kdefft_profile_read(kdefft_ctx c, kdefft_kstat* out, int cap, int* count, in
 
 int kdefft_destroy(kdefft_ctx c) {
     if (!c) return KDEFFT_OK;
+    if (!live_take(c)) return fail(KDEFFT_ERR_ARG, "unknown or already destroyed context");
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (kdefft_ds ds : c->datasets) ds_free(ds);
+    for (kdefft_ds ds : c->datasets) {
+        live_take(ds);
+        ds_free(ds);
+    }
     c->datasets.clear();
     c->cache.trim();
     c->tw32.release();
@@ -2779,6 +2799,7 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     misc.release();
     *out = ds.release();
     c->datasets.push_back(*out);
+    live_add(*out);
     return KDEFFT_OK;
 }
 
@@ -2938,12 +2959,14 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
     for (int i = 0; i < nds; ++i) {
         out[i] = dss[i].release();
         c->datasets.push_back(out[i]);
+        live_add(out[i]);
     }
     return KDEFFT_OK;
 }
 
 int kdefft_ds_destroy(kdefft_ds ds) {
     if (!ds) return KDEFFT_OK;
+    if (!live_take(ds)) return fail(KDEFFT_ERR_ARG, "unknown or already destroyed dataset");
     auto& v = ds->ctx->datasets;
     auto it = std::find(v.begin(), v.end(), ds);
     if (it == v.end()) return fail(KDEFFT_ERR_ARG, "unknown or already destroyed dataset");
@@ -3207,6 +3230,7 @@ static int get_G(kdefft_ds ds, const double* G, Mat& Gm) {
     const int d = ds->d;
     if (G) {
         KCHK(sym_check(G, d, Gm, "G"));
+        KCHK(spd_or_fail(Gm, "G"));
     } else {
         // normal-scale matrix (4/(d+2))^{2/(d+4)} n^{-2/(d+4)} S
         const double f = std::pow(4.0 / (d + 2.0), 2.0 / (d + 4.0)) * std::pow((double)ds->n, -2.0 / (d + 4.0));
