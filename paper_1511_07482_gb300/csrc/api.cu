@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -771,13 +772,59 @@ struct KSpec {
     Mat sig[MAXSIG];
 };
 
+// The terms of one grid: up to four held inline (no allocation per grid,
+// which dominates building a request set of thousands of bandwidths), more
+// in a vector.
+class TermVec {
+    static constexpr int kInline = 4;
+    Term in_[kInline];
+    int n_ = 0;
+    std::vector<Term> ex_;   // all terms once there are more than kInline
+
+public:
+    TermVec() = default;
+    TermVec(std::initializer_list<Term> l) { *this = l; }
+    TermVec(const std::vector<Term>& v) { *this = v; }
+    int size() const { return ex_.empty() ? n_ : (int)ex_.size(); }
+    bool empty() const { return size() == 0; }
+    const Term* begin() const { return ex_.empty() ? in_ : ex_.data(); }
+    const Term* end() const { return begin() + size(); }
+    const Term& operator[](int i) const { return begin()[i]; }
+    void clear() {
+        n_ = 0;
+        ex_.clear();
+    }
+    void push_back(const Term& t) {
+        if (ex_.empty() && n_ < kInline) {
+            in_[n_++] = t;
+            return;
+        }
+        if (ex_.empty()) ex_.assign(in_, in_ + n_);
+        ex_.push_back(t);
+    }
+    void assign(int n, const Term& t) {
+        clear();
+        for (int i = 0; i < n; ++i) push_back(t);
+    }
+    TermVec& operator=(const std::vector<Term>& v) {
+        clear();
+        for (const Term& t : v) push_back(t);
+        return *this;
+    }
+    TermVec& operator=(std::initializer_list<Term> l) {
+        clear();
+        for (const Term& t : l) push_back(t);
+        return *this;
+    }
+};
+
 // One real lag kernel to be reduced against a dataset's spectrum.
 struct GridReq {
     kdefft_ds ds;
     int spec;              // index into the request set's KSpec list
     int L[4];
     int P[4];
-    std::vector<Term> terms;
+    TermVec terms;
     bool fp64 = false;     // evaluate in FP64 even on an FP32 dataset
     double value = 0.0;    // result: n^-2 sum_w |C|^2 K / prod P  (= Eq. 25)
 };
@@ -868,7 +915,7 @@ static int add_lscv(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int& firs
     const Mat& basis = (ds->opts.L_basis == KDEFFT_L_WIDEST) ? sp.sig[0] : H;
     KCHK(plan_for(ds, basis, L, P));
     first = (int)rs.grids.size();
-    auto push = [&](std::vector<Term> t) {
+    auto push = [&](TermVec t) {
         GridReq g;
         g.ds = ds;
         g.spec = si;
@@ -915,7 +962,7 @@ static int add_scv(ReqSet& rs, kdefft_ds ds, const Mat& H, const Mat& G, bool gr
     const Mat& basis = (ds->opts.L_basis == KDEFFT_L_PAPER) ? H : sp.sig[0];
     KCHK(plan_for(ds, basis, L, P));
     first = (int)rs.grids.size();
-    auto push = [&](std::vector<Term> t) {
+    auto push = [&](TermVec t) {
         GridReq g;
         g.ds = ds;
         g.spec = si;
@@ -990,7 +1037,8 @@ static int add_psi(ReqSet& rs, kdefft_ds ds, const Mat& H, const std::vector<Mul
 // eta_m(x; Sigma) = (vec^T I)^{(x)m} D^{(x)2m} phi_Sigma = Laplacian^m phi_Sigma
 //                 = sum_{|beta| = m} m! / beta! d^{2 beta} phi_Sigma,
 // appended as terms of covariance `sig` scaled by `scale`.
-static void laplacian_power_terms(int d, int m, int sig, double scale, std::vector<Term>& out) {
+template <typename V>
+static void laplacian_power_terms(int d, int m, int sig, double scale, V& out) {
     std::vector<MultiIndex> all;
     enumerate(d, m, all);
     double mf = 1.0;
@@ -1080,7 +1128,7 @@ static int add_lscv_r(ReqSet& rs, kdefft_ds ds, const Mat& H, int r, int& first)
     const Mat& basis = (ds->opts.L_basis == KDEFFT_L_WIDEST) ? sp.sig[0] : H;
     KCHK(plan_for(ds, basis, L, P));
     first = (int)rs.grids.size();
-    auto push = [&](std::vector<Term> t) {
+    auto push = [&](TermVec t) {
         GridReq g;
         g.ds = ds;
         g.spec = si;
@@ -2257,7 +2305,7 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
                         it.nterm[h] = 0;
                         continue;
                     }
-                    const std::vector<Term>& tl = rs.grids[gi[h]].terms;
+                    const TermVec& tl = rs.grids[gi[h]].terms;
                     if ((int)tl.size() > MAXTERM) return fail(KDEFFT_ERR_UNSUPPORTED, "too many kernel terms");
                     it.nterm[h] = (int)tl.size();
                     for (size_t m = 0; m < tl.size(); ++m) {
