@@ -120,8 +120,8 @@ int kdefft_bin(kdefft_ctx ctx, const double* X, int64_t n, int d,
 /* kdefft_bin for nds datasets of the same d at once (Sec. 4 step 1 for
  * each): X[i] is dataset i's n[i] x d sample (host or device), lo/hi its
  * grid range (nds x d), M its grid (nds x d).  FP32 linear binning runs as
- * a few launches over all datasets (binning, conversion, the two moment
- * passes) with two synchronisations in total, and the datasets' counts
+ * three launches over all datasets (binning, conversion, the one-pass
+ * covariance) with one synchronisation in total, and the datasets' counts
  * share one allocation (freed with the last of them); other precisions and
  * rules bin one dataset at a time.  out: nds handles.  On error no dataset
  * is created. */

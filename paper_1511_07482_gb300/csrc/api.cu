@@ -2930,16 +2930,16 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
     auto pool = std::make_shared<DevBuf>(&c->cache);
     KCHK(pool->ensure(sizeof(float) * std::max<long long>(totcells, 1)));
     KCHK(c->binfix.ensure(8 * (size_t)std::max<long long>(totcells, 1)));
+    const int nv = d + d * d;
     long long totpart = 0;
-    for (int i = 0; i < nds; ++i) totpart += (long long)jobs[i].mblk * d * d;
+    for (int i = 0; i < nds; ++i) totpart += (long long)jobs[i].mblk * nv;
     DevBuf misc(&c->cache);
-    const size_t nmisc = (size_t)nds * (1 + 4) + (size_t)totpart;
+    const size_t nmisc = (size_t)nds + (size_t)totpart;
     KCHK(misc.ensure(sizeof(double) * nmisc));
     KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * nds, c->stream));
     KCU(cudaMemsetAsync(c->binfix.p, 0, 8 * (size_t)totcells, c->stream));
     unsigned long long* dOut = (unsigned long long*)misc.p;
-    double* dMean = (double*)misc.p + nds;
-    double* dPart = dMean + (size_t)nds * 4;
+    double* dPart = (double*)misc.p + nds;
     KCHK(c->binjobs.ensure(sizeof(BinJob) * nds * 4));
     BinJob* jd = (BinJob*)c->binjobs.p;
     long long po = 0;
@@ -2957,8 +2957,8 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
         jb.counts = (float*)pool->p + coff[i];
         jb.outside = dOut + i;
         jb.part = dPart + po;
-        jb.mean = dMean + (size_t)i * 4;
-        po += (long long)jb.mblk * d * d;
+        for (int k = 0; k < d; ++k) jb.shift[k] = 0.5 * (lo[(size_t)i * d + k] + hi[(size_t)i * d + k]);
+        po += (long long)jb.mblk * nv;
         dss[i]->pool = pool;
         dss[i]->counts.view(jb.counts, sizeof(float) * (size_t)dss[i]->ncells);
     }
@@ -2973,21 +2973,9 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
     KCU(launch_bin_many(jobs.data(), jd, nds, 0, qscale, c->stream));
     KCU(launch_bin_many(jobs.data(), jd + nds, nds, 1, qscale, c->stream));
     prof_stop(c, evb, "bin", by, fl);
-    c->launches += 2;   // the two moment passes
+    c->launches += 1;   // the one-pass covariance
     KCU(launch_bin_many(jobs.data(), jd + 2 * nds, nds, 2, qscale, c->stream));
     std::vector<double> part((size_t)totpart);
-    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * totpart, cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaStreamSynchronize(c->stream));
-    std::vector<double> means((size_t)nds * 4, 0.0);
-    po = 0;
-    for (int i = 0; i < nds; ++i) {
-        for (int b = 0; b < jobs[i].mblk; ++b)
-            for (int k = 0; k < d; ++k) means[(size_t)i * 4 + k] += part[(size_t)(po + (long long)b * d + k)];
-        for (int k = 0; k < d; ++k) means[(size_t)i * 4 + k] /= (double)n[i];
-        po += (long long)jobs[i].mblk * d * d;
-    }
-    KCU(cudaMemcpyAsync(dMean, means.data(), sizeof(double) * nds * 4, cudaMemcpyHostToDevice, c->stream));
-    KCU(launch_bin_many(jobs.data(), jd + 3 * nds, nds, 3, qscale, c->stream));
     std::vector<unsigned long long> nout(nds);
     KCU(cudaMemcpyAsync(nout.data(), dOut, sizeof(unsigned long long) * nds, cudaMemcpyDeviceToHost, c->stream));
     KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * totpart, cudaMemcpyDeviceToHost, c->stream));
@@ -2995,11 +2983,14 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
     prof_flush(c);
     po = 0;
     for (int i = 0; i < nds; ++i) {
-        double hc[16] = {0};
+        double hs[20] = {0};
         for (int b = 0; b < jobs[i].mblk; ++b)
-            for (int v = 0; v < d * d; ++v) hc[v] += part[(size_t)(po + (long long)b * d * d + v)];
-        po += (long long)jobs[i].mblk * d * d;
-        for (int v = 0; v < d * d; ++v) dss[i]->cov[v] = (n[i] > 1) ? hc[v] / (double)(n[i] - 1) : 0.0;
+            for (int v = 0; v < nv; ++v) hs[v] += part[(size_t)(po + (long long)b * nv + v)];
+        po += (long long)jobs[i].mblk * nv;
+        const double ni = (double)n[i];
+        for (int a = 0; a < d; ++a)
+            for (int e = 0; e < d; ++e)
+                dss[i]->cov[a * d + e] = (n[i] > 1) ? (hs[d + a * d + e] - hs[a] * hs[e] / ni) / (ni - 1.0) : 0.0;
         if (nout[i] > 0 && o.outside_policy == KDEFFT_OUTSIDE_ERROR)
             return fail(KDEFFT_ERR_OUTSIDE_GRID, "dataset " + std::to_string(i) + ": " + std::to_string(nout[i]) +
                                                      " sample points outside the grid");

@@ -322,21 +322,20 @@ __global__ void __launch_bounds__(256) k_bin_many(const BinJob* __restrict__ job
         const long long c1 = c0 + kCellsPerBlock < jb.ncells ? c0 + kCellsPerBlock : jb.ncells;
         for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) jb.counts[c] = (float)((double)jb.fix[c] * unit);
     } else {
-        // moments: block b of mblk takes the points i = b, b + mblk, ... in steps of blockDim
-        const int nv = (phase == 2) ? d : d * d;
-        double acc[MAXD * MAXD];
+        // covariance in one pass, shifted by the grid's centre (as
+        // k_moments_shifted): block b of mblk takes the points i = b, b + mblk,
+        // ... in steps of blockDim
+        const int nv = d + d * d;
+        double acc[MAXD + MAXD * MAXD];
         for (int v = 0; v < nv; ++v) acc[v] = 0.0;
         for (long long i = b * blockDim.x + threadIdx.x; i < jb.n; i += (long long)jb.mblk * blockDim.x) {
             double x[MAXD];
-            for (int k = 0; k < d; ++k) x[k] = jb.X[i * d + k] - (phase == 3 ? jb.mean[k] : 0.0);
-            if (phase == 2) {
-                for (int k = 0; k < d; ++k) acc[k] += x[k];
-            } else {
-                for (int a = 0; a < d; ++a)
-                    for (int c = 0; c < d; ++c) acc[a * d + c] += x[a] * x[c];
-            }
+            for (int k = 0; k < d; ++k) x[k] = jb.X[i * d + k] - jb.shift[k];
+            for (int k = 0; k < d; ++k) acc[k] += x[k];
+            for (int a = 0; a < d; ++a)
+                for (int c = 0; c < d; ++c) acc[d + a * d + c] += x[a] * x[c];
         }
-        __shared__ double red[8][MAXD * MAXD];
+        __shared__ double red[8][MAXD + MAXD * MAXD];
         for (int v = 0; v < nv; ++v) {
             double t = acc[v];
             for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);

@@ -322,8 +322,8 @@ struct BinJob {
     unsigned long long* fix;
     float* counts;
     unsigned long long* outside;
-    double* part;          // mblk x d (phase 2) or mblk x d x d (phase 3)
-    const double* mean;    // phase 3
+    double* part;          // phase 2: mblk x (d + d^2) sums of x - shift and (x - shift)(x - shift)^T
+    double shift[MAXD];    // phase 2: the grid's centre
     int mblk;
     long long blk0;        // set by the launcher
 };
