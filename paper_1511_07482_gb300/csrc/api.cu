@@ -2794,7 +2794,10 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     double* dPart = (double*)misc.p + 16;
     const bool dbl = o.precision == KDEFFT_FP64;
     KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));
-    KCU(cudaMemsetAsync(ds->counts.p, 0, (dbl ? 8 : 4) * (size_t)ds->ncells, c->stream));
+    // only FP64 linear binning accumulates into the counts themselves; the
+    // other paths write every cell from their own accumulators
+    if (dbl && o.binning != KDEFFT_BIN_SIMPLE)
+        KCU(cudaMemsetAsync(ds->counts.p, 0, 8 * (size_t)ds->ncells, c->stream));
     cudaEvent_t evb = prof_start(c);
     if (o.binning == KDEFFT_BIN_SIMPLE) {
         c->launches++;   // the integer-to-real conversion
