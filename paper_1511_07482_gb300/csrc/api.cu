@@ -525,6 +525,7 @@ struct kdefft_ctx_s {
     DevBuf acjobs;            // job table of the batched autocorrelation passes
     HostBuf h_acjobs;         // its pinned staging copy, free once acjobs_ev has passed
     HostBuf h_sel;            // pinned start / end table of the lag-domain device search
+    HostBuf h_binres;         // pinned outside count and moment partials of a binning
     cudaEvent_t acjobs_ev = nullptr;
     bool acjobs_free = true;
     DevBuf binjobs;           // job tables of the batched binning
@@ -2558,6 +2559,7 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         b->gen = &c->buf_gen;
     c->h_items.gen = &c->buf_gen;
     c->h_out.gen = &c->buf_gen;
+    c->h_binres.gen = &c->buf_gen;
     if (cudaEventCreateWithFlags(&c->staging_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->acjobs_ev, cudaEventDisableTiming) != cudaSuccess) {
         delete c;
@@ -2568,6 +2570,7 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         return fail(KDEFFT_ERR_ALLOC, "error flag allocation failed");
     }
     int r = upload_tables();
+    if (r == KDEFFT_OK && prepare_binning() != cudaSuccess) r = fail(KDEFFT_ERR_CUDA, "binning kernel attributes");
     if (r != KDEFFT_OK) {
         delete c;
         return r;
@@ -2732,6 +2735,7 @@ int kdefft_destroy(kdefft_ctx c) {
     if (c->acjobs_ev) cudaEventDestroy(c->acjobs_ev);
     c->h_acjobs.release();
     c->h_sel.release();
+    c->h_binres.release();
     if (c->errflag) cudaFree(c->errflag);
     delete c;
     return KDEFFT_OK;
@@ -2787,57 +2791,90 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     }
     // outside counter | block partials of the moments
     const int mblk = moments_blocks(n, c->nsm);
+    const int nv = d + d * d;
     DevBuf misc(&c->cache);
-    KCHK(misc.ensure(sizeof(double) * (16 + (size_t)mblk * (d + d * d))));
-    KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
+    KCHK(misc.ensure(sizeof(double) * (16 + (size_t)mblk * nv)));
     unsigned long long* dOut = (unsigned long long*)misc.p;
     double* dPart = (double*)misc.p + 16;
     const bool dbl = o.precision == KDEFFT_FP64;
-    KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));
-    // only FP64 linear binning accumulates into the counts themselves; the
-    // other paths write every cell from their own accumulators
-    if (dbl && o.binning != KDEFFT_BIN_SIMPLE)
-        KCU(cudaMemsetAsync(ds->counts.p, 0, 8 * (size_t)ds->ncells, c->stream));
-    cudaEvent_t evb = prof_start(c);
-    if (o.binning == KDEFFT_BIN_SIMPLE) {
-        c->launches++;   // the integer-to-real conversion
-        KCHK(ds->counts_i.ensure(4 * (size_t)ds->ncells));
-        KCU(cudaMemsetAsync(ds->counts_i.p, 0, 4 * (size_t)ds->ncells, c->stream));
-        KCU(launch_bin_simple(dX, n, g, (int*)ds->counts_i.p, ds->ncells, dOut, c->nsm, c->stream));
-        if (dbl)
-            KCU(launch_int_to_real<double>((int*)ds->counts_i.p, (double*)ds->counts.p, ds->ncells, c->stream));
-        else
-            KCU(launch_int_to_real<float>((int*)ds->counts_i.p, (float*)ds->counts.p, ds->ncells, c->stream));
-    } else if (dbl) {
-        KCU(launch_bin_linear<double>(dX, n, g, (double*)ds->counts.p, ds->ncells, dOut, 1.0, c->nsm, c->stream));
-    } else {
-        // fixed point with K fractional bits; a cell's total (<= n 2^K) stays below 2^63
-        int K = 32;
-        while (K > 8 && (double)n * std::ldexp(1.0, K) >= std::ldexp(1.0, 63)) --K;
-        c->launches++;   // the fixed-point-to-FP32 conversion
-        DevBuf& fix = c->binfix;
-        KCHK(fix.ensure(8 * (size_t)ds->ncells));
-        KCU(cudaMemsetAsync(fix.p, 0, 8 * (size_t)ds->ncells, c->stream));
-        KCU(launch_bin_linear<unsigned long long>(dX, n, g, (unsigned long long*)fix.p, ds->ncells, dOut,
-                                                  std::ldexp(1.0, K), c->nsm, c->stream));
-        KCU(launch_fix_to_f32((const unsigned long long*)fix.p, (float*)ds->counts.p, ds->ncells, std::ldexp(1.0, -K),
-                              c->stream));
-    }
-    prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
     // covariance for the normal-scale start point, in one pass shifted by the
     // grid's centre (block partials summed in block order: the same start
     // point from run to run)
-    c->launches += 1;
-    const int nv = d + d * d;
-    std::vector<double> part((size_t)mblk * nv);
     Shift sh{};
     for (int k = 0; k < d; ++k) sh.s[k] = 0.5 * (lo[k] + hi[k]);
-    KCU(launch_moments_shifted(dX, n, d, sh, dPart, c->nsm, c->stream));
     unsigned long long nout = 0;
+    std::vector<double> part((size_t)mblk * nv);
+    if (!dbl && o.binning != KDEFFT_BIN_SIMPLE) {
+        // FP32 linear binning: the launch sequence (zeroing, binning, fixed
+        // point to FP32, moments, copies of the outside count and the moment
+        // partials to pinned memory) replays as a CUDA graph when its
+        // pointers and sizes repeat
+        int K = 32;   // fixed point with K fractional bits; a cell's total (<= n 2^K) stays below 2^63
+        while (K > 8 && (double)n * std::ldexp(1.0, K) >= std::ldexp(1.0, 63)) --K;
+        DevBuf& fix = c->binfix;
+        KCHK(fix.ensure(8 * (size_t)ds->ncells));
+        KCHK(ds->counts.ensure(4 * (size_t)ds->ncells));
+        const size_t nres = 1 + (size_t)mblk * nv;
+        KCHK(c->h_binres.ensure(sizeof(double) * nres));
+        double* hres = (double*)c->h_binres.p;
+        std::vector<long long> sig = {4, (long long)(uintptr_t)dX, n, d, K, (long long)(uintptr_t)fix.p,
+                                      (long long)(uintptr_t)ds->counts.p, (long long)(uintptr_t)misc.p,
+                                      (long long)(uintptr_t)hres, mblk, ds->ncells, c->nsm};
+        for (int k = 0; k < d; ++k) {
+            long long bits[3];
+            std::memcpy(&bits[0], &g.lo[k], 8);
+            std::memcpy(&bits[1], &g.hi[k], 8);
+            std::memcpy(&bits[2], &g.delta[k], 8);
+            sig.insert(sig.end(), {bits[0], bits[1], bits[2], g.M[k]});
+        }
+        auto issue = [&]() -> int {
+            KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
+            KCU(cudaMemsetAsync(fix.p, 0, 8 * (size_t)ds->ncells, c->stream));
+            cudaEvent_t evb = prof_start(c);
+            c->launches++;   // the fixed-point-to-FP32 conversion
+            KCU(launch_bin_linear<unsigned long long>(dX, n, g, (unsigned long long*)fix.p, ds->ncells, dOut,
+                                                      std::ldexp(1.0, K), c->nsm, c->stream));
+            KCU(launch_fix_to_f32((const unsigned long long*)fix.p, (float*)ds->counts.p, ds->ncells,
+                                  std::ldexp(1.0, -K), c->stream));
+            prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * 4.0, (double)n * (1 << d) * 2.0);
+            c->launches += 1;
+            KCU(launch_moments_shifted(dX, n, d, sh, dPart, c->nsm, c->stream));
+            KCU(cudaMemcpyAsync(hres, dOut, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            KCU(cudaMemcpyAsync(hres + 1, dPart, sizeof(double) * mblk * nv, cudaMemcpyDeviceToHost, c->stream));
+            return KDEFFT_OK;
+        };
+        KCHK(run_graph(c, sig, issue));
+        KCU(cudaStreamSynchronize(c->stream));
+        std::memcpy(&nout, hres, sizeof(nout));
+        std::memcpy(part.data(), hres + 1, sizeof(double) * mblk * nv);
+    } else {
+        KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
+        KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));
+        // only FP64 linear binning accumulates into the counts themselves; the
+        // other paths write every cell from their own accumulators
+        if (dbl && o.binning != KDEFFT_BIN_SIMPLE)
+            KCU(cudaMemsetAsync(ds->counts.p, 0, 8 * (size_t)ds->ncells, c->stream));
+        cudaEvent_t evb = prof_start(c);
+        if (o.binning == KDEFFT_BIN_SIMPLE) {
+            c->launches++;   // the integer-to-real conversion
+            KCHK(ds->counts_i.ensure(4 * (size_t)ds->ncells));
+            KCU(cudaMemsetAsync(ds->counts_i.p, 0, 4 * (size_t)ds->ncells, c->stream));
+            KCU(launch_bin_simple(dX, n, g, (int*)ds->counts_i.p, ds->ncells, dOut, c->nsm, c->stream));
+            if (dbl)
+                KCU(launch_int_to_real<double>((int*)ds->counts_i.p, (double*)ds->counts.p, ds->ncells, c->stream));
+            else
+                KCU(launch_int_to_real<float>((int*)ds->counts_i.p, (float*)ds->counts.p, ds->ncells, c->stream));
+        } else {
+            KCU(launch_bin_linear<double>(dX, n, g, (double*)ds->counts.p, ds->ncells, dOut, 1.0, c->nsm, c->stream));
+        }
+        prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * (dbl ? 8.0 : 4.0), (double)n * (1 << d) * 2.0);
+        c->launches += 1;
+        KCU(launch_moments_shifted(dX, n, d, sh, dPart, c->nsm, c->stream));
+        KCU(cudaMemcpyAsync(&nout, dOut, sizeof(nout), cudaMemcpyDeviceToHost, c->stream));
+        KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * nv, cudaMemcpyDeviceToHost, c->stream));
+        KCU(cudaStreamSynchronize(c->stream));
+    }
     double hs[20] = {0};
-    KCU(cudaMemcpyAsync(&nout, dOut, sizeof(nout), cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaMemcpyAsync(part.data(), dPart, sizeof(double) * mblk * nv, cudaMemcpyDeviceToHost, c->stream));
-    KCU(cudaStreamSynchronize(c->stream));
     for (int b = 0; b < mblk; ++b)
         for (int v = 0; v < nv; ++v) hs[v] += part[(size_t)b * nv + v];
     prof_flush(c);

@@ -191,9 +191,7 @@ cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, a
     size_t sm = 0;
     int grid;
     if (use_smem) {
-        sm = hist_bytes;
-        cudaError_t e = cudaFuncSetAttribute(k_bin_linear<acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+        sm = hist_bytes;   // within the 96 KB set once by prepare_binning (no attribute call here: graph capture)
         grid = blocks_for(n, nsm, 2);
     } else {
         grid = blocks_for(n, nsm, 8);
@@ -369,6 +367,13 @@ cudaError_t launch_bin_many(BinJob* jobs_h, BinJob* jobs_d, int n, int phase, do
     if (e != cudaSuccess) return e;
     k_bin_many<<<(unsigned)blocks, 256, 0, st>>>(jobs_d, n, phase, qscale);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_binning() {
+    cudaError_t e = cudaFuncSetAttribute(k_bin_linear<unsigned long long>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bin_linear<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
 template cudaError_t launch_bin_linear<unsigned long long>(const double*, long long, const GridDesc&,

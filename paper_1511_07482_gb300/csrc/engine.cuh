@@ -328,6 +328,8 @@ struct BinJob {
     long long blk0;        // set by the launcher
 };
 cudaError_t launch_bin_many(BinJob* jobs_h, BinJob* jobs_d, int n, int phase, double qscale, cudaStream_t st);
+// one-time kernel attributes of the binning launches (before any graph capture)
+cudaError_t prepare_binning();
 
 // blocks of the moment launches (at most two per SM)
 int moments_blocks(long long n, int nsm);
