@@ -2,12 +2,15 @@
 //
 // Linear binning (the multilinear rule the paper takes from Wand 1994):
 //   inside iff lo_k <= x_k <= hi_k on every axis (the grid range contains
-//   the data); t_k = (x_k - lo_k) / delta_k (FP64, subtraction and division
-//   rounded separately, no contraction), clamped to M_k - 1 because the
-//   rounding of delta_k can push a point at hi_k just past it
+//   the data); t_k = (x_k - lo_k) * (1 / delta_k) (FP64, each operation
+//   rounded separately, no contraction; within two ulps of the quotient),
+//   clamped to M_k - 1 because the rounding of delta_k can push a point at
+//   hi_k just past it
 //   l_k = floor(t_k), clamped to M_k - 2 on the upper edge; f_k = t_k - l_k
 //   corner l + b receives prod_k (b_k ? f_k : 1 - f_k), product in axis order.
-// Simple binning: weight 1 at l_k = floor(t_k + 1/2).
+// Simple binning: weight 1 at l_k = floor(t_k + 1/2), with t_k the quotient
+// (x_k - lo_k) / delta_k itself, so that the cells match the oracle's bit for
+// bit.
 //
 // Grids that fit in shared memory are accumulated per block there (one
 // privatised histogram per block, flushed with global atomics of the nonzero
@@ -26,13 +29,21 @@
 
 namespace kdefft {
 
-__device__ __forceinline__ bool locate(const double* __restrict__ x, const GridDesc& g, long long* l, double* f,
-                                       long long* base) {
+// Linear binning locates a point with t = (x - lo) * (1 / delta): one FP64
+// multiply instead of a division (FP64 is slow on this part).  t is within
+// two ulps of the oracle's (x - lo) / delta, so a point moves to the next
+// cell only within two ulps of a node, where its weight there is ~1e-16.
+struct Recip {
+    double v[MAXD];
+};
+
+__device__ __forceinline__ bool locate(const double* __restrict__ x, const GridDesc& g, const Recip& inv, long long* l,
+                                       double* f, long long* base) {
     long long b = 0;
     for (int k = 0; k < g.d; ++k) {
         if (!(x[k] >= g.lo[k] && x[k] <= g.hi[k])) return false;   // NaN fails too
         const double top = (double)(g.M[k] - 1);
-        const double t = fmin(__ddiv_rn(__dsub_rn(x[k], g.lo[k]), g.delta[k]), top);
+        const double t = fmin(__dmul_rn(__dsub_rn(x[k], g.lo[k]), inv.v[k]), top);
         double lk = floor(t);
         if (lk >= top) lk = top - 1.0;
         f[k] = __dsub_rn(t, lk);
@@ -55,7 +66,7 @@ __device__ __forceinline__ unsigned long long corner_fixed(int d, int c, const f
 }
 
 template <typename acc>
-__global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X, long long n, GridDesc g,
+__global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X, long long n, GridDesc g, Recip inv,
                                                     acc* __restrict__ counts, long long ncells,
                                                     unsigned long long* __restrict__ outside, int use_smem,
                                                     double qscale) {
@@ -82,7 +93,7 @@ __global__ void __launch_bounds__(256) k_bin_linear(const double* __restrict__ X
         double x[MAXD], f[MAXD];
         long long l[MAXD], base;
         for (int k = 0; k < g.d; ++k) x[k] = X[i * g.d + k];
-        if (!locate(x, g, l, f, &base)) {
+        if (!locate(x, g, inv, l, f, &base)) {
             ++nout;
             continue;
         }
@@ -196,7 +207,9 @@ cudaError_t launch_bin_linear(const double* X, long long n, const GridDesc& g, a
     } else {
         grid = blocks_for(n, nsm, 8);
     }
-    k_bin_linear<acc><<<grid, 256, sm, st>>>(X, n, g, counts, ncells, outside, use_smem, qscale);
+    Recip inv{};
+    for (int k = 0; k < g.d; ++k) inv.v[k] = 1.0 / g.delta[k];
+    k_bin_linear<acc><<<grid, 256, sm, st>>>(X, n, g, inv, counts, ncells, outside, use_smem, qscale);
     return cudaGetLastError();
 }
 
@@ -290,6 +303,8 @@ __global__ void __launch_bounds__(256) k_bin_many(const BinJob* __restrict__ job
             }
         }
         const int ncorner = 1 << d;
+        Recip inv{};   // the same correctly rounded reciprocals as launch_bin_linear's
+        for (int k = 0; k < d; ++k) inv.v[k] = __drcp_rn(g.delta[k]);
         unsigned long long nout = 0;
         const long long i0 = b * kBinPtsPerBlock;
         const long long i1 = i0 + kBinPtsPerBlock < jb.n ? i0 + kBinPtsPerBlock : jb.n;
@@ -297,7 +312,7 @@ __global__ void __launch_bounds__(256) k_bin_many(const BinJob* __restrict__ job
             double x[MAXD], f[MAXD];
             long long l[MAXD], base;
             for (int k = 0; k < d; ++k) x[k] = jb.X[i * d + k];
-            if (!locate(x, g, l, f, &base)) {
+            if (!locate(x, g, inv, l, f, &base)) {
                 ++nout;
                 continue;
             }
