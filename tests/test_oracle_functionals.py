@@ -479,3 +479,66 @@ def test_eta_rs_reduces_to_eta02_and_eta_r():
                 al[i] += 1
             want += A[a, b] * B[c, e] * float(gauss.gauss_deriv(x, Sg, tuple(al)))
         assert v1 == pytest.approx(want, rel=1e-10)
+
+
+def test_lscv_r_is_cross_validation_of_the_derivative():
+    """Eq. 35 is least-squares cross-validation of the r-th derivative
+    estimate: up to the constant int |D^r f|^2 it is
+
+        int |D^{(x)r} f_hat|^2 - 2 (-1)^r n^-1 sum_i Lap^r f_hat_{-i}(X_i),
+
+    since int D^r f_hat . D^r f = (-1)^r int f Lap^r f_hat (integration by
+    parts) and f_hat_{-i} leaves X_i out.  Both parts are computed here
+    without the Hermite partials: the first by a Riemann sum of the squared
+    gradient (r = 1, d = 2) or second derivative (r = 2, d = 1) written out
+    by hand, the second by central finite differences of the leave-one-out
+    density."""
+    rng = np.random.default_rng(31)
+    # r = 1, d = 2
+    n = 30
+    X = 0.6 * _mix(rng, n, 2)
+    H = np.array([[0.2, 0.05], [0.05, 0.15]])
+    Hi = np.linalg.inv(H)
+    nrm = 1.0 / (2 * math.pi * math.sqrt(np.linalg.det(H)))
+
+    def dens(x, pts):
+        u = x[:, None, :] - pts[None, :, :]
+        return nrm * np.exp(-0.5 * np.einsum("pqi,ij,pqj->pq", u, Hi, u))
+
+    h = 0.05
+    axes = [np.arange(X[:, k].min() - 3.0, X[:, k].max() + 3.0, h) for k in range(2)]
+    g = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 2)
+    u = g[:, None, :] - X[None, :, :]
+    grad = -np.einsum("ij,pqj->pi", Hi, u * dens(g, X)[:, :, None]) / n
+    quad = float(np.sum(grad * grad)) * h * h
+    e = 1e-3
+    lap = 0.0
+    for i in range(n):
+        rest = np.delete(X, i, axis=0)
+        f = lambda x: float(np.sum(dens(x[None, :], rest))) / (n - 1)
+        for k in range(2):
+            ek = np.eye(2)[k] * e
+            lap += (f(X[i] + ek) - 2 * f(X[i]) + f(X[i] - ek)) / (e * e)
+    want = quad + 2.0 * lap / n
+    ev = lambda t: F.direct_sum(X, t)
+    got = S.lscv_r(ev, H, n, 1, exact_loo=True)
+    assert got == pytest.approx(want, rel=1e-6, abs=1e-6 * (abs(quad) + abs(2.0 * lap / n)))
+    # r = 2, d = 1
+    n = 25
+    x1 = rng.standard_normal(n) * 0.8
+    s2 = 0.1
+    phi = lambda x: np.exp(-0.5 * x * x / s2) / math.sqrt(2 * math.pi * s2)
+    xs = np.arange(x1.min() - 3.0, x1.max() + 3.0, 0.005)
+    u = xs[:, None] - x1[None, :]
+    f2 = np.sum((u * u / (s2 * s2) - 1.0 / s2) * phi(u), axis=1) / n
+    quad = float(np.sum(f2 * f2)) * 0.005
+    e = 5e-3
+    d4 = 0.0
+    for i in range(n):
+        rest = np.delete(x1, i)
+        f = lambda x: float(np.sum(phi(x - rest))) / (n - 1)
+        xi = x1[i]
+        d4 += (f(xi + 2 * e) - 4 * f(xi + e) + 6 * f(xi) - 4 * f(xi - e) + f(xi - 2 * e)) / e ** 4
+    want = quad - 2.0 * d4 / n
+    got = S.lscv_r(lambda t: F.direct_sum(x1[:, None], t), np.array([[s2]]), n, 2, exact_loo=True)
+    assert got == pytest.approx(want, abs=1e-3 * (abs(quad) + abs(2.0 * d4 / n)))

@@ -7,7 +7,7 @@ the grid is refined (second-order binning error)."""
 import numpy as np
 import pytest
 
-from oracle import binning, kde, rules
+from oracle import binning, functionals as F, kde, rules
 
 
 def _mixture():
@@ -44,6 +44,13 @@ def test_grid_estimate_integrates_to_one_and_single_point():
     x = (g - np.array([30, 31])) * delta
     assert f1[33, 29] == pytest.approx(float(gauss_density(x[None, :], H)[0]), rel=1e-12)
     assert f1[30 + L[0] + 1, 31] == 0.0      # outside the truncated stencil
+    # the stencil reaches |l_k| = L_k inclusive (Eq. 26's support)
+    xL = np.array([L[0], -L[1]]) * delta
+    assert f1[30 + L[0], 31 - L[1]] == pytest.approx(float(gauss_density(xL[None, :], H)[0]), rel=1e-12)
+    # n^-1 sum_g c_g f_hat(g) is Eq. 25's binned double sum of K_H
+    got = float(np.sum(c * f)) / X.shape[0]
+    want = F.binned_direct(c, X.shape[0], [(1.0, H, (0, 0))], delta, L)
+    assert got == pytest.approx(want, rel=1e-12)
 
 
 def test_mixture_square_integral_matches_quadrature():

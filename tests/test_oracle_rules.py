@@ -78,6 +78,14 @@ def test_P_rules_small_values():
     assert rules.P_minimal([100], [20]) == [120]
     assert rules.P_minimal([256], [21]) == [288]
     assert rules.P_minimal([48], [47]) == [96]
+    # bounds that are themselves powers of two or 5-smooth: Eqs. 21 and 27
+    # round up only strictly above them, and the minimal rule stops at the
+    # first smooth size at or above M + L (120 = M + L - 1 is one short)
+    assert rules.P_paper([5], [2]) == [8]              # 5 + 4 - 1 = 8
+    assert rules.P_paper([9], [12]) == [32]            # 9 + 24 - 1 = 32
+    assert rules.P_paper_full([3]) == [8]              # 3*3-1 = 8
+    assert rules.P_paper_full([11]) == [32]            # 3*11-1 = 32
+    assert rules.P_minimal([100], [21]) == [125]       # 121..124 are not 5-smooth
     assert rules.support_L(1.0, [0.1], [10], 3.7) == [9]   # capped at M-1
     assert rules.support_L(0.04, [0.1], [100], 3.7) == [8]  # ceil(7.4)
 
