@@ -113,7 +113,6 @@ class Clocks:
         self.t1 = datetime.datetime.now()
 
     def stop(self):
-        import datetime
         if self.p is None:
             return None
         time.sleep(0.12)   # let a sample land after the region
@@ -124,28 +123,39 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        rows = []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f:
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 10:
-                continue
-            try:
-                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
-                rows.append((ts, float(parts[2]), float(parts[3]),
-                             [nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")]))
-            except ValueError:
-                continue
+        lines = self.f.readlines()
         os.unlink(self.f.name)
-        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
-        if not inside:
-            after = [r for r in rows if self.t0 and r[0] >= self.t0]
-            inside = after[:1]
-        if not inside:
-            return None
-        reasons = sorted({nm for r in inside for nm in r[3]})
-        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[-1][2], "reasons": reasons,
-                "samples": len(inside), "interval_ms": 50}
+        return parse_clock_samples(lines, self.t0, self.t1)
+
+
+def parse_clock_samples(lines, t0, t1, interval_ms=50):
+    """nvidia-smi CSV rows (timestamp, index, clocks.sm, clocks.max.sm,
+    power.draw, reasons.active, hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap) -> the clocks object of the bench
+    line: median SM clock of the samples stamped inside [t0, t1] and every
+    throttle reason active in any of them.  A region shorter than the
+    sampling interval keeps the first sample after t0; no sample gives None."""
+    import datetime
+    rows = []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            rows.append((ts, float(parts[2]), float(parts[3]),
+                         [nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")]))
+        except ValueError:
+            continue
+    inside = [r for r in rows if t0 and t1 and t0 <= r[0] <= t1]
+    if not inside:
+        inside = [r for r in rows if t0 and r[0] >= t0][:1]
+    if not inside:
+        return None
+    reasons = sorted({nm for r in inside for nm in r[3]})
+    return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[-1][2], "reasons": reasons,
+            "samples": len(inside), "interval_ms": interval_ms}
 
 
 def kernel_hash():
@@ -450,13 +460,19 @@ def oracle_evals(w, Hs, G):
     return 2 * len(Hs), res
 
 
+def cores_used(cpu_s: float, wall_s: float) -> int:
+    """Threads the oracle kept busy: its process CPU time over the wall time
+    of the same region, rounded (the oracle's numpy FFTs run on one)."""
+    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
+
+
 def cpu_baseline(w, args, gpu_res):
     """The oracle, as it stands, on a bounded sample: binning of the full
     sample plus LSCV+grad and SCV+grad at the GPU-selected LSCV bandwidth and
     one more candidate; also the relative error of the GPU objective values
     at those bandwidths."""
     H1, f1, H2, f2 = gpu_res
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     n_ev, res = oracle_evals(w, [H1], w.G)
     # accuracy of the FP32 path at the selected H: compare with the oracle value
     ref_lscv = res[0][1][0]
@@ -467,7 +483,7 @@ def cpu_baseline(w, args, gpu_res):
         n_ev += k
         i += 1
     dt = time.perf_counter() - t0
-    return {"value": n_ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n_ev / dt, "unit": UNIT, "cores": cores_used(time.process_time() - c0, dt), "kind": "oracle",
             "sample": f"{w.name}: {1 + i} oracle binnings of all n, each followed by LSCV+gradient and "
                       f"SCV+gradient in FP64 (numpy FFT) at one bandwidth ({n_ev} evaluations, {dt:.1f} s)",
             "rel_err_lscv_at_selected_H": rel}
@@ -482,11 +498,12 @@ def run_reference(args):
     Hs = list(w.H[:4])
     for _ in range(args.warmup):
         oracle_evals(w, Hs, w.G)
-    t, ev = 0.0, 0
+    t, cpu, ev = 0.0, 0.0, 0
     for _ in range(args.steps):
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         n_ev, _ = oracle_evals(w, Hs, w.G)
         t += time.perf_counter() - t0
+        cpu += time.process_time() - c0
         ev += n_ev
     value = ev / t
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -494,7 +511,7 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name + ": bin + LSCV and SCV objective+gradient evaluations (oracle)",
                       "n": w.n, "d": w.d, "grid": w.M},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(cpu, t), "kind": "oracle",
                             "sample": f"per step: oracle binning of all n plus {2 * len(Hs)} FP64 "
                                       f"objective+gradient evaluations"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

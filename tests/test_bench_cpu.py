@@ -1,0 +1,100 @@
+"""Host logic of bench.py that needs no GPU: the oracle arm's JSON line, its
+rank-0-only rule under a multi-rank launch, the loud failure of our arm
+without a GPU (no CPU fallback), the clock-sample filter, and the traffic
+record's tie to the kernel source."""
+import datetime
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _run(args, env_extra=None, timeout=600):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True,
+                          text=True, cwd=ROOT, env=env, timeout=timeout)
+
+
+def test_reference_arm_prints_one_json_line():
+    r = _run(["--impl", "reference", "--steps", "2", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference"
+    assert out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
+    assert out["higher_is_better"] is True and out["steps"] == 2 and out["warmup"] == 3
+    assert out["value"] > 0 and out["ms_per_step"] > 0
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+    assert out["config"]["n"] == 100000 and out["config"]["grid"] == [256, 256]
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    r = _run(["--impl", "reference", "--steps", "1", "--warmup", "3"],
+             {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_our_arm_fails_loudly_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = _run(["--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--no-batch-compare"])
+    assert r.returncode != 0
+    assert not any(l.lstrip().startswith("{") for l in r.stdout.splitlines())
+
+
+def _row(ts, sm, reasons=()):
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    flags = ["Active" if n in reasons else "Not Active" for n in names]
+    return ", ".join([ts.strftime("%Y/%m/%d %H:%M:%S.%f")[:-3], "0", str(sm), "2070", "900.5",
+                      "0x0000000000000000"] + flags) + "\n"
+
+
+def test_clock_samples_inside_the_region_only():
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0)
+    ms = lambda k: t0 + datetime.timedelta(milliseconds=k)
+    lines = [_row(ms(-100), 900, ("hw_slowdown",)),          # before the region: ignored
+             _row(ms(10), 1950), _row(ms(60), 1965, ("sw_power_cap",)), _row(ms(110), 1980),
+             "garbage line\n",
+             _row(ms(400), 700, ("hw_thermal_slowdown",))]    # after the region: ignored
+    c = bench.parse_clock_samples(lines, t0, ms(200))
+    assert c["samples"] == 3 and c["sm_mhz"] == 1965 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["sw_power_cap"]
+    # a region shorter than the interval keeps the first sample after its start
+    c = bench.parse_clock_samples(lines, ms(20), ms(30))
+    assert c["samples"] == 1 and c["sm_mhz"] == 1965
+    # a throttle reason inside the region is reported
+    c = bench.parse_clock_samples(lines, ms(300), ms(500))
+    assert c["reasons"] == ["hw_thermal_slowdown"] and c["sm_mhz"] == 700
+    assert bench.parse_clock_samples(lines, ms(1000), ms(2000)) is None
+
+
+def test_traffic_record_is_tied_to_the_kernel_source(tmp_path, monkeypatch):
+    rec = {"kernel_source_hash": bench.kernel_hash(),
+           "kernels": {"select2d_lag_f32": {"dram_bytes_per_algorithmic_byte": 0.25}}}
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "PROFILE_FILE", str(p))
+    assert bench.ncu_traffic("select2d_lag_f32", 1000.0) == pytest.approx(250.0)
+    assert bench.ncu_traffic("another_kernel", 1000.0) is None
+    rec["kernel_source_hash"] = "0" * 16      # the kernels changed since the capture
+    p.write_text(json.dumps(rec))
+    assert bench.ncu_traffic("select2d_lag_f32", 1000.0) is None
+
+
+def test_cores_used_and_rank_seeds():
+    assert bench.cores_used(1.0, 1.0) == 1 and bench.cores_used(0.2, 1.0) == 1
+    assert bench.cores_used(3.9, 1.0) == 4 and bench.cores_used(1.0, 0.0) == 1
+    seeds = {bench.rank_seed(2, r) for r in range(8)}
+    assert len(seeds) == 8 and bench.rank_seed(2, 0) == 2
