@@ -126,18 +126,44 @@ def _host_f64(a):
     return a, a.ctypes.data_as(C.c_void_p)
 
 
+def _mat(a, d, what):
+    """A d x d FP64 matrix argument: (host copy, pointer).  The library reads
+    exactly d*d values through the pointer, so the size is checked here."""
+    arr, p = _host_f64(a)
+    if arr.size != d * d:
+        raise ValueError(f"{what} must hold {d} x {d} values, got shape {arr.shape}")
+    return arr, p
+
+
+def _opt_mat(a, d, what):
+    return _mat(a, d, what) if a is not None else (None, None)
+
+
+def _vec(a, d, what, dtype=np.float64):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype).ravel())
+    if arr.size != d:
+        raise ValueError(f"{what} must hold {d} values, got {arr.size}")
+    return arr
+
+
 def _ptr_of(x):
-    """(keepalive, pointer) for a numpy array or a torch tensor (host or CUDA)."""
+    """(keepalive, pointer) for an n x d sample: a numpy array or a torch
+    tensor (host or CUDA)."""
     try:
         import torch
         if isinstance(x, torch.Tensor):
             if x.dtype != torch.float64:
                 raise TypeError("expected a float64 tensor")
+            if x.dim() != 2:
+                raise ValueError(f"the sample must be n x d, got shape {tuple(x.shape)}")
             x = x.contiguous()
             return x, C.c_void_p(x.data_ptr())
     except ImportError:
         pass
-    return _host_f64(x)
+    arr, p = _host_f64(x)
+    if arr.ndim != 2:
+        raise ValueError(f"the sample must be n x d, got shape {arr.shape}")
+    return arr, p
 
 
 def lscv_noalloc(M, delta, n, counts, H, out, tau=3.7, stream=None):
@@ -147,13 +173,18 @@ def lscv_noalloc(M, delta, n, counts, H, out, tau=3.7, stream=None):
     stream); the caller synchronises."""
     import torch
     d = len(M)
-    M_a = np.ascontiguousarray(np.asarray(M, dtype=np.int64))
-    dl, pdl = _host_f64(delta)
-    Ha, pH = _host_f64(H)
+    M_a = _vec(M, d, "M", np.int64)
+    dl = _vec(delta, d, "delta")
+    pdl = dl.ctypes.data_as(C.c_void_p)
+    Ha, pH = _mat(H, d, "H")
     if not (isinstance(counts, torch.Tensor) and counts.is_cuda and counts.dtype == torch.float32):
         raise TypeError("counts must be a CUDA float32 tensor")
     if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64):
         raise TypeError("out must be a CUDA float64 tensor")
+    if not counts.is_contiguous() or counts.numel() != int(np.prod(M_a)):
+        raise ValueError("counts must be a contiguous tensor of prod(M) values")
+    if not out.is_contiguous() or out.numel() < 1 + d * d:
+        raise ValueError(f"out must be a contiguous tensor of at least {1 + d * d} values")
     if stream is None:
         stream = torch.cuda.current_stream(out.device).cuda_stream
     _check(load().kdefft_lscv_noalloc(d, M_a.ctypes.data_as(C.c_void_p), pdl, int(n),
@@ -261,9 +292,10 @@ class Context:
         """Sec. 4 step 1: bin the n x d FP64 sample onto the grid."""
         keep, px = _ptr_of(X)
         n, d = int(keep.shape[0]), int(keep.shape[1])
-        lo_a, plo = _host_f64(lo)
-        hi_a, phi = _host_f64(hi)
-        M_a = np.ascontiguousarray(np.asarray(M, dtype=np.int64))
+        lo_a = _vec(lo, d, "lo")
+        hi_a = _vec(hi, d, "hi")
+        plo, phi = lo_a.ctypes.data_as(C.c_void_p), hi_a.ctypes.data_as(C.c_void_p)
+        M_a = _vec(M, d, "M", np.int64)
         o = default_opts(**opts)
         h = C.c_void_p()
         _check(load().kdefft_bin(self.h, px, n, d, plo, phi, M_a.ctypes.data_as(C.c_void_p), C.byref(o),
@@ -278,6 +310,8 @@ class Context:
         nds = len(Xs)
         keep = [_ptr_of(X) for X in Xs]
         d = int(keep[0][0].shape[1])
+        if any(int(k.shape[1]) != d for k, _ in keep):
+            raise ValueError("every sample of a batch must have the same dimension d")
         ptrs = (C.c_void_p * nds)(*[p for _, p in keep])
         n = np.ascontiguousarray(np.array([int(k.shape[0]) for k, _ in keep], dtype=np.int64))
         lo = np.ascontiguousarray(np.asarray(los, dtype=np.float64).reshape(nds, d))
@@ -343,8 +377,8 @@ class Dataset:
         return out
 
     def plan(self, method, H, G=None):
-        Ha, pH = _host_f64(H)
-        Ga, pG = _host_f64(G) if G is not None else (None, None)
+        Ha, pH = _mat(H, self.d, "H")
+        Ga, pG = _opt_mat(G, self.d, "G")
         L = np.zeros(self.d, dtype=np.int32)
         P = np.zeros(self.d, dtype=np.int32)
         _check(load().kdefft_plan(self.h, method, pH, pG, L.ctypes.data_as(C.c_void_p),
@@ -372,7 +406,7 @@ class Dataset:
 
     def scv(self, H, G, grad=False):
         H, nH = self._Hs(H)
-        Ga, pG = _host_f64(G)
+        Ga, pG = _mat(G, self.d, "G")
         val = np.zeros(nH)
         g = np.zeros((nH, self.d, self.d)) if grad else None
         _check(load().kdefft_scv(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
@@ -381,7 +415,7 @@ class Dataset:
 
     def pi(self, H, G, grad=False):
         H, nH = self._Hs(H)
-        Ga, pG = _host_f64(G)
+        Ga, pG = _mat(G, self.d, "G")
         val = np.zeros(nH)
         g = np.zeros((nH, self.d, self.d)) if grad else None
         _check(load().kdefft_pi(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
@@ -410,8 +444,8 @@ class Dataset:
         """n^-2 sum_ij eta_{r,s}(X_i - X_j; A, B, Sigma) (Eqs. 29-30) for each
         Sigma; A, B default to the identity."""
         S, nS = self._Hs(Sigma)
-        Aa, pA = _host_f64(A) if A is not None else (None, None)
-        Ba, pB = _host_f64(B) if B is not None else (None, None)
+        Aa, pA = _opt_mat(A, self.d, "A")
+        Ba, pB = _opt_mat(B, self.d, "B")
         out = np.zeros(nS)
         _check(load().kdefft_eta_rs(self.h, pA, pB, S.ctypes.data_as(C.c_void_p), nS, int(r), int(s),
                                     out.ctypes.data_as(C.c_void_p)))
@@ -419,7 +453,7 @@ class Dataset:
 
     def kde_grid(self, H):
         """The binned kernel density estimate at every grid node (shape M)."""
-        Ha, pH = _host_f64(H)
+        Ha, pH = _mat(H, self.d, "H")
         out = np.zeros(self.M)
         _check(load().kdefft_kde_grid(self.h, pH, out.ctypes.data_as(C.c_void_p)))
         return out
@@ -447,7 +481,7 @@ class Dataset:
 
     def eta02(self, H, G):
         H, nH = self._Hs(H)
-        Ga, pG = _host_f64(G)
+        Ga, pG = _mat(G, self.d, "G")
         val = np.zeros(nH)
         _check(load().kdefft_eta02(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p)))
         return val
@@ -463,8 +497,8 @@ class Dataset:
         classes = {"full": 0, "diag": 1, "scalar": 2}
         if hclass not in classes:
             raise ValueError("hclass must be 'full', 'diag' or 'scalar'")
-        Ha, pH = _host_f64(H0) if H0 is not None else (None, None)
-        Ga, pG = _host_f64(G) if G is not None else (None, None)
+        Ha, pH = _opt_mat(H0, self.d, "H0")
+        Ga, pG = _opt_mat(G, self.d, "G")
         Hout = np.zeros((self.d, self.d))
         f = C.c_double()
         ne = C.c_int64()
@@ -485,8 +519,8 @@ class Dataset:
         Returns [(H, f, evals)] in the order of `methods`."""
         ms = np.ascontiguousarray(np.asarray(methods, dtype=np.int32))
         k = int(ms.size)
-        Ha, pH = _host_f64(H0) if H0 is not None else (None, None)
-        Ga, pG = _host_f64(G) if G is not None else (None, None)
+        Ha, pH = _opt_mat(H0, self.d, "H0")
+        Ga, pG = _opt_mat(G, self.d, "G")
         Hout = np.zeros((k, self.d, self.d))
         f = np.zeros(k)
         ne = np.zeros(k, dtype=np.int64)
