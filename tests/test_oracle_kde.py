@@ -80,3 +80,20 @@ def test_ise_nonnegative_and_binning_converges():
         assert b > 0.0
         errs.append(abs(b - exact))
     assert errs[1] < errs[0] / 2.5 and errs[2] < errs[1] / 2.5   # about 4x per halving of delta
+
+
+def test_exact_ise_matches_quadrature_of_the_squared_error():
+    """Eq. 37 straight from its definition: int (f_hat - f)^2 by a Riemann
+    sum on a fine grid, with f_hat and f evaluated pointwise (no Gaussian
+    convolution identities)."""
+    X = _sample(20, 5)
+    w, mu, S = _mixture()
+    H = np.array([[0.08, 0.02], [0.02, 0.06]])
+    from oracle.gauss import gauss_density
+    h = 0.02
+    xs = np.arange(-4.5, 4.5, h)
+    G = np.stack(np.meshgrid(xs, xs, indexing="ij"), axis=-1).reshape(-1, 2)
+    fhat = sum(gauss_density(G - x[None, :], H) for x in X) / X.shape[0]
+    f = sum(wm * gauss_density(G - m[None, :], Sm) for wm, m, Sm in zip(w, mu, S))
+    quad = float(np.sum((fhat - f) ** 2)) * h * h
+    assert kde.ise_mixture_exact(X, H, w, mu, S) == pytest.approx(quad, rel=1e-6)

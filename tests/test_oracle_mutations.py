@@ -239,6 +239,13 @@ def _lag_kernel_axes_swapped(terms, delta, L):
     return F.kernel_eval(x, terms)
 
 
+def _lag_kernel_uncentred(terms, delta, L):
+    delta = np.asarray(delta, dtype=np.float64)
+    axes = [delta[k] * np.arange(0, 2 * L[k] + 1, dtype=np.float64) for k in range(len(L))]
+    x = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1)
+    return F.kernel_eval(x, terms)
+
+
 def _binned_direct(norm_pow=2, inclusive=True):
     def binned_direct(c, n, terms, delta, L):
         c = np.asarray(c, dtype=np.float64)
@@ -355,6 +362,24 @@ def _scv_grad_sign(H, G, a, b):
     return [(s, 2.0 * H + 2.0 * G, al), (s, H + 2.0 * G, al)]
 
 
+def _scv_grad_rk_sign(ev, H, G, n, grad=False):
+    H = np.asarray(H, dtype=np.float64)
+    d = H.shape[0]
+    r0 = S.RK(H)
+    val = r0 / n + ev(S.scv_terms(H, G))
+    if not grad:
+        return val
+    Hinv = np.linalg.inv(H)
+    g = np.zeros((d, d))
+    for a, b in S.vech_pairs(d):
+        g[a, b] = g[b, a] = ev(S.scv_grad_terms(H, G, a, b)) + S._tie(a, b) * (0.5 * r0 * Hinv[a, b]) / n
+    return val, g
+
+
+def _pi_eta_half(ev, H, G, n):
+    return S.RK(H) / n + 0.5 * ev(S.eta02_terms(H, G))
+
+
 def _pi_from_psi4(quarter=0.25, half=0.5):
     def pi(psi4_kron, H, n, grad=False):
         H = np.asarray(H, dtype=np.float64)
@@ -439,18 +464,18 @@ def _ise_binned(cross_w=2.0, smooth_H=True):
     return ise
 
 
-def _ise_exact(pair_scale=2.0):
+def _ise_exact(pair_scale=2.0, cross_H=1.0):
     def ise(X, H, w, mu, S_):
-        return _ise_exact_scaled(X, H, w, mu, S_, pair_scale)
+        return _ise_exact_scaled(X, H, w, mu, S_, pair_scale, cross_H)
     return ise
 
 
-def _ise_exact_scaled(X, H, w, mu, S_, pair_scale):
+def _ise_exact_scaled(X, H, w, mu, S_, pair_scale, cross_H):
     X = np.asarray(X, dtype=np.float64)
     H = np.asarray(H, dtype=np.float64)
     n = X.shape[0]
     a = sum(float(np.sum(gauss.gauss_density(X - X[i][None, :], pair_scale * H))) for i in range(n))
-    b = sum(wm * float(np.sum(gauss.gauss_density(X - np.asarray(m)[None, :], H + np.asarray(Sm))))
+    b = sum(wm * float(np.sum(gauss.gauss_density(X - np.asarray(m)[None, :], cross_H * H + np.asarray(Sm))))
             for wm, m, Sm in zip(w, mu, S_))
     return a / n ** 2 - 2.0 * b / n + kde.mixture_sq_integral(w, mu, S_)
 
@@ -481,6 +506,7 @@ MUTANTS = {
     # binned double sums (Eqs. 18-25) and the lag-domain form
     "Eq. 12: i = j terms left out": lambda mp: _patch(mp, _direct_sum_offdiag, (F, "direct_sum")),
     "Eq. 25: a slice times itself": lambda mp: _patch(mp, _overlap_self, (F, "_overlap")),
+    "Eq. 18: lag box not centred on 0": lambda mp: _patch(mp, _lag_kernel_uncentred, (F, "lag_kernel")),
     "Eq. 18: axis spacings swapped": lambda mp: _patch(mp, _lag_kernel_axes_swapped, (F, "lag_kernel")),
     "Eq. 25: n^-1 for n^-2": lambda mp: _patch(mp, _binned_direct(norm_pow=1), (F, "binned_direct")),
     "Eq. 25: lag +L_k left out": lambda mp: _patch(mp, _binned_direct(inclusive=False), (F, "binned_direct")),
@@ -499,6 +525,8 @@ MUTANTS = {
     "SCV: middle weight -1": lambda mp: _patch(mp, _scv_terms(mid=-1.0), (S, "scv_terms")),
     "SCV: phi_G for phi_2G": lambda mp: _patch(mp, _scv_terms(last_G=1.0), (S, "scv_terms")),
     "SCV gradient: middle sign flipped": lambda mp: _patch(mp, _scv_grad_sign, (S, "scv_grad_terms")),
+    "SCV gradient: sign of the R(K) term": lambda mp: _patch(mp, _scv_grad_rk_sign, (S, "scv")),
+    "PI by eta_02: 1/2 for 1/4": lambda mp: _patch(mp, _pi_eta_half, (S, "pi_eta")),
     "R(K) with (2 pi)^-d/2": lambda mp: _patch(mp, _const_pi(2.0), (S, "RK")),
     "PI: 1/2 for 1/4": lambda mp: _patch(mp, _pi_from_psi4(quarter=0.5), (S, "pi_from_psi4")),
     "PI gradient: factor 1/2 dropped": lambda mp: _patch(mp, _pi_from_psi4(half=1.0), (S, "pi_from_psi4")),
@@ -513,6 +541,7 @@ MUTANTS = {
     "binned ISE: cross term weight 1": lambda mp: _patch(mp, _ise_binned(cross_w=1.0), (kde, "ise_mixture_binned")),
     "binned ISE: mixture not smoothed by H": lambda mp: _patch(mp, _ise_binned(smooth_H=False), (kde, "ise_mixture_binned")),
     "exact ISE: phi_H for phi_2H": lambda mp: _patch(mp, _ise_exact(pair_scale=1.0), (kde, "ise_mixture_exact")),
+    "exact ISE: mixture not smoothed by H": lambda mp: _patch(mp, _ise_exact(cross_H=0.0), (kde, "ise_mixture_exact")),
 }
 
 
