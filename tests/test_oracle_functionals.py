@@ -190,6 +190,22 @@ def test_fft_steps_equal_binned_double_sum(d, M, L):
             assert got == pytest.approx(ref, rel=1e-11, abs=1e-15)
 
 
+def test_untruncated_layout_of_eqs_19_to_23():
+    """With no truncation (L_k = M_k - 1, Eq. 17) and the padded size of
+    Eq. 21 (2^ceil(log2(3 M_k - 1))), the printed layout holds as it stands:
+    Eq. 23's extraction of M_k outputs from index 2 M_k - 2 (0-based)
+    reproduces the binned double sum."""
+    X, c, delta = _binned_case(2, [12, 10])
+    H = _spd(np.random.default_rng(3), 2, 0.4)
+    M = [12, 10]
+    L = [m - 1 for m in M]
+    assert rules.P_paper_full(M) == [64, 32]
+    for terms in (S.lscv_T_terms(H), [(1.0, H, (1, 1))]):
+        ref = F.binned_direct(c, 300, terms, delta, L)
+        for P in (rules.P_paper_full(M), rules.P_paper(M, L), rules.P_minimal(M, L)):
+            assert F.binned_fft(c, 300, terms, delta, L, P) == pytest.approx(ref, rel=1e-11, abs=1e-15)
+
+
 def _parseval(c, n, terms, delta, L, P):
     """n^-2 P_tot^-1 sum_w |C_w|^2 K_w with k wrapped to j mod P: the
     frequency-domain form of Eq. 25 (discrete Parseval)."""
