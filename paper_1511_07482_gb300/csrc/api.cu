@@ -550,7 +550,7 @@ struct kdefft_ctx_s {
     std::map<std::vector<long long>, GraphEntry> gcache;
     // A captured graph holds the context buffers it copied to and from: when
     // one of them is reallocated (even at the same address) every graph is
-    // dropped, since the driver may keep the old allocation's mapping in a
+    // dropped, since the CUDA driver may keep the old allocation's mapping in a
     // copy node.
     int64_t buf_gen = 0, graph_gen = 0;
     int64_t graphs_captured = 0, graph_replays = 0;
