@@ -158,6 +158,40 @@ def parse_clock_samples(lines, t0, t1, interval_ms=50):
             "samples": len(inside), "interval_ms": interval_ms}
 
 
+def roofline_of(kstats, hbm, smmax, src):
+    """The roofline object of the bench line for the kernel with the largest
+    summed CUDA-event time: algorithmic flops and bytes per launch over the
+    average launch time, against the FP32 ALU peak (152 SMs x 128 lanes x 2
+    flop x the maximum SM clock) or the measured HBM copy bandwidth, whichever
+    the kernel is closer to.  kstats: name -> {launches, ms, bytes, flops};
+    names starting with "host:" are host phases, not kernels."""
+    kernels = {k: v for k, v in kstats.items() if not k.startswith("host:")}
+    if not kernels:
+        return None
+    kname = max(kernels, key=lambda k: kernels[k]["ms"])
+    k = kernels[kname]
+    avg_s = k["ms"] / 1000.0 / max(k["launches"], 1)
+    fl = k["flops"] / max(k["launches"], 1)
+    by = k["bytes"] / max(k["launches"], 1)
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smmax * 1e6 / 1e12        # TFLOP/s
+    a_tf = fl / avg_s / 1e12
+    a_gb = by / avg_s / 1e9
+    if a_gb / hbm >= a_tf / alu_peak:
+        roof = {"bound": "hbm", "achieved": a_gb, "peak": hbm, "unit": "GB/s", "frac": a_gb / hbm,
+                "peak_source": f"{src} copy bandwidth"}
+    else:
+        roof = {"bound": "alu", "achieved": a_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": a_tf / alu_peak,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                               f"{smmax:.0f} MHz ({src} maximum SM clock)"}
+    roof.update({"kernel": kname, "launches": k["launches"],
+                 "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": by,
+                 "algorithmic_flops_per_launch": fl, "traffic": ncu_traffic(kname, by),
+                 "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kernels.values()),
+                 "timing": "CUDA events around every launch on the library stream, over min(steps, 20) "
+                           "identical steps run right after the timed region"})
+    return roof
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("engine.cu", "engine.cuh", "lag.cu", "devutil.cuh"):
@@ -359,29 +393,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    hbm, smmax, src = peaks()
-    # dominant kernel
-    kernels = {k: v for k, v in kstats.items() if not k.startswith("host:")}
-    kname = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
-    roof = None
-    if kname:
-        k = kstats[kname]
-        avg_s = k["ms"] / 1000.0 / max(k["launches"], 1)
-        fl = k["flops"] / max(k["launches"], 1)
-        by = k["bytes"] / max(k["launches"], 1)
-        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smmax * 1e6 / 1e12        # TFLOP/s
-        a_tf = fl / avg_s / 1e12
-        a_gb = by / avg_s / 1e9
-        if a_gb / hbm >= a_tf / alu_peak:
-            roof = {"bound": "hbm", "achieved": a_gb, "peak": hbm, "unit": "GB/s", "frac": a_gb / hbm}
-        else:
-            roof = {"bound": "alu", "achieved": a_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": a_tf / alu_peak}
-        roof.update({"kernel": kname, "peak_source": src, "launches": k["launches"],
-                     "avg_launch_us": avg_s * 1e6, "algorithmic_bytes_per_launch": by,
-                     "algorithmic_flops_per_launch": fl, "traffic": ncu_traffic(kname, by),
-                     "share_of_kernel_time": k["ms"] / sum(v["ms"] for v in kernels.values()),
-                     "timing": "CUDA events around every launch on the library stream, over min(steps, 20) "
-                               "identical steps run right after the timed region"})
+    roof = roofline_of(kstats, *peaks())
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot[0].item() / args.steps, "higher_is_better": True,

@@ -1,7 +1,7 @@
 """Host logic of bench.py that needs no GPU: the oracle arm's JSON line, its
 rank-0-only rule under a multi-rank launch, the loud failure of our arm
-without a GPU (no CPU fallback), the clock-sample filter, and the traffic
-record's tie to the kernel source."""
+without a GPU (no CPU fallback), the clock-sample filter, the roofline of
+the dominant kernel, and the traffic record's tie to the kernel source."""
 import datetime
 import json
 import os
@@ -98,3 +98,26 @@ def test_cores_used_and_rank_seeds():
     assert bench.cores_used(3.9, 1.0) == 4 and bench.cores_used(1.0, 0.0) == 1
     seeds = {bench.rank_seed(2, r) for r in range(8)}
     assert len(seeds) == 8 and bench.rank_seed(2, 0) == 2
+
+
+def test_roofline_of_the_dominant_kernel(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "PROFILE_FILE", str(tmp_path / "none.json"))   # no traffic record
+    kstats = {
+        "select2d_lag_f32": {"launches": 20, "ms": 7.3, "bytes": 282876800.0, "flops": 10326965600.0},
+        "bin": {"launches": 20, "ms": 0.445, "bytes": 37242880.0, "flops": 16000000.0},
+        "host:run": {"launches": 20, "ms": 99.0, "bytes": 0.0, "flops": 0.0},    # host phase: never the kernel
+    }
+    r = bench.roofline_of(kstats, 6800.7, 2070.0, "measured")
+    assert r["kernel"] == "select2d_lag_f32" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    assert r["peak"] == pytest.approx(peak) and "derived" in r["peak_source"]
+    assert r["avg_launch_us"] == pytest.approx(365.0)
+    assert r["achieved"] == pytest.approx(10326965600.0 / 20 / 365e-6 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["share_of_kernel_time"] == pytest.approx(7.3 / 7.745)
+    assert r["traffic"] is None
+    # a kernel that moves many bytes per flop is reported against the HBM copy bandwidth
+    r = bench.roofline_of({"copy": {"launches": 1, "ms": 1.0, "bytes": 5e9, "flops": 1e6}}, 6800.7, 2070.0,
+                          "measured")
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(5000.0) and r["frac"] == pytest.approx(5000 / 6800.7)
+    assert bench.roofline_of({"host:run": kstats["host:run"]}, 6800.7, 2070.0, "measured") is None
