@@ -193,6 +193,31 @@ def _support_L(rounding=math.ceil, root=True):
     return support_L
 
 
+def _lambda_min(S_):
+    return float(np.linalg.eigvalsh(np.asarray(S_, dtype=np.float64))[0])
+
+
+def _next_pow2_strict(x):
+    p = 1
+    while p <= x:
+        p *= 2
+    return p
+
+
+def _is_7_smooth(x):
+    for p in (2, 3, 5, 7):
+        while x % p == 0:
+            x //= p
+    return x == 1
+
+
+def _coords_unclamped(X, lo, hi, M):
+    X = np.asarray(X, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.float64)
+    delta = rules.bin_width(lo, hi, M)
+    return (X - lo) / delta, delta
+
+
 def _P_paper_no_minus_one(M, L):
     return [rules._next_pow2(int(m) + 2 * int(l)) for m, l in zip(M, L)]
 
@@ -302,6 +327,19 @@ def _half_box_weights(pos=2.0, first=True):
 
 
 # ---------------------------------------------------------------- selectors
+
+def _vech_pairs_offdiag(d):
+    return [(a, b) for a in range(d) for b in range(a + 1, d)] + [(a, a) for a in range(d)][:-1]
+
+
+def _tie_swapped(a, b):
+    return 2.0 if a == b else 1.0
+
+
+def _psi_unique_2H(ev, H, r):
+    return {a: ev([(1.0, 2.0 * np.asarray(H, dtype=np.float64), a)])
+            for a in gauss.multi_indices(np.asarray(H).shape[0], r)}
+
 
 def _T_terms(conv_scale=2.0, cross=-2.0):
     def terms(H):
@@ -500,6 +538,10 @@ MUTANTS = {
     "Eq. 16: range / M": lambda mp: _patch(mp, _bin_width_over_M, (rules, "bin_width"), (binning, "bin_width")),
     "Eq. 26: floor for ceil": lambda mp: _patch(mp, _support_L(rounding=math.floor), (rules, "support_L")),
     "Eq. 26: lambda for sqrt(lambda)": lambda mp: _patch(mp, _support_L(root=False), (rules, "support_L")),
+    "Eq. 26: smallest eigenvalue for the largest": lambda mp: _patch(mp, _lambda_min, (rules, "lambda_max")),
+    "powers of two: next strictly above": lambda mp: _patch(mp, _next_pow2_strict, (rules, "_next_pow2")),
+    "minimal P: 7 counted as a small prime": lambda mp: _patch(mp, _is_7_smooth, (rules, "_is_smooth")),
+    "binning: upper-edge clamp left out": lambda mp: _patch(mp, _coords_unclamped, (binning, "_coords")),
     "Eq. 27: M + 2L for M + 2L - 1": lambda mp: _patch(mp, _P_paper_no_minus_one, (rules, "P_paper")),
     "Eq. 21: 3M for 3M - 1": lambda mp: _patch(mp, _P_paper_full_3M, (rules, "P_paper_full")),
     "minimal P: M + L - 1": lambda mp: _patch(mp, _P_minimal_short, (rules, "P_minimal")),
@@ -516,6 +558,9 @@ MUTANTS = {
     "half box: weight 1 on the positive half": lambda mp: _patch(mp, _half_box_weights(pos=1.0), (F, "half_box_weights")),
     "half box: sign of the last nonzero lag": lambda mp: _patch(mp, _half_box_weights(first=False), (F, "half_box_weights")),
     # selectors (Eqs. 8, 10-11, 29-36; SCV and PI readings)
+    "gradients: one diagonal entry left out": lambda mp: _patch(mp, _vech_pairs_offdiag, (S, "vech_pairs")),
+    "gradients: factor 2 on the diagonal, not off it": lambda mp: _patch(mp, _tie_swapped, (S, "_tie")),
+    "Eq. 13: psi at 2H": lambda mp: _patch(mp, _psi_unique_2H, (S, "psi_unique")),
     "Eq. 11: K_H * K_H as phi_H": lambda mp: _patch(mp, _T_terms(conv_scale=1.0), (S, "lscv_T_terms")),
     "Eq. 11: factor 2 on K_H dropped": lambda mp: _patch(mp, _T_terms(cross=-1.0), (S, "lscv_T_terms")),
     "LSCV gradient: off-diagonal factor 2 dropped": lambda mp: _patch(mp, _lscv_grad_untied, (S, "lscv_grad_terms")),

@@ -92,3 +92,23 @@ def test_P_rules_small_values():
 
 def test_bin_width_eq16():
     np.testing.assert_allclose(rules.bin_width([0.0, -1.0], [1.0, 1.0], [11, 5]), [0.1, 0.5])
+
+
+def test_lambda_max_closed_form_and_rayleigh_bound():
+    """2 x 2: (tr + sqrt(tr^2 - 4 det)) / 2.  3 x 3: no Rayleigh quotient
+    exceeds it, and the power iteration reaches it."""
+    S2 = np.array([[0.3, 0.12], [0.12, 0.2]])
+    tr, det = np.trace(S2), np.linalg.det(S2)
+    assert rules.lambda_max(S2) == pytest.approx((tr + math.sqrt(tr * tr - 4 * det)) / 2, rel=1e-14)
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((3, 3))
+    S3 = A @ A.T + 0.2 * np.eye(3)
+    lam = rules.lambda_max(S3)
+    x = rng.standard_normal((1000, 3))
+    q = np.einsum("pi,ij,pj->p", x, S3, x) / np.einsum("pi,pi->p", x, x)
+    assert np.all(q <= lam * (1 + 1e-12))
+    v = np.ones(3)
+    for _ in range(500):
+        v = S3 @ v
+        v /= np.linalg.norm(v)
+    assert float(v @ S3 @ v) == pytest.approx(lam, rel=1e-10)
