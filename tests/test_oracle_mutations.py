@@ -4,7 +4,8 @@ Each mutant below replaces one oracle function with a copy that carries one
 plausible mistake: a dropped term or factor, a flipped sign, a wrong index,
 a swapped operand or a wrong constant.  The whole battery of oracle pins
 (every test in test_oracle_*.py) then runs against the mutated oracle, and
-at least one pin must fail on a wrong value (an AssertionError).  A mutant
+at least one pin must fail on a wrong value (an AssertionError, or the
+oracle's OutsideGrid for a sample on its grid).  A mutant
 that no pin catches marks a part of the oracle whose pins only restate it.
 
 The mistakes are planted in this process only, with monkeypatch, and only in
@@ -44,13 +45,14 @@ def _battery():
 
 def _first_failing_pin():
     """Runs the pins in order; returns the id of the first one that fails on a
-    value, or None.  A pin that raises anything else is reported as such, so
-    that a mutant which merely breaks the oracle's structure does not pass
-    for one the pins catch by value."""
+    value (or on the oracle refusing a sample that lies on its grid), or
+    None.  A pin that raises anything else is reported as such, so that a
+    mutant which merely breaks the oracle's structure does not pass for one
+    the pins catch."""
     for pid, fn, kw in _battery():
         try:
             fn(**kw)
-        except AssertionError:
+        except (AssertionError, binning.OutsideGrid):
             return pid
         except pytest.skip.Exception:
             continue
@@ -168,6 +170,15 @@ def _bin_linear(swap=False, axis_flip=False):
     return bin_linear
 
 
+def _inside_lower_open(X, lo, hi, policy):
+    """lo < x instead of lo <= x: a point on the lower edge counts as outside."""
+    X = np.asarray(X, dtype=np.float64)
+    ok = np.all((X > np.asarray(lo, dtype=np.float64)) & (X <= np.asarray(hi, dtype=np.float64)), axis=1)
+    if not np.all(ok) and policy == "error":
+        raise binning.OutsideGrid("outside")
+    return ok
+
+
 def _bin_simple_floor(X, lo, hi, M, policy="error"):
     M = [int(m) for m in M]
     t, _ = binning._coords(X, lo, hi, M)
@@ -245,6 +256,17 @@ def _direct_sum_offdiag(X, terms, block=256):
     diff = X[:, None, :] - X[None, :, :]
     v = F.kernel_eval(diff, terms)
     return float(np.sum(v) - np.trace(v)) / float(n) ** 2
+
+
+def _direct_sum_short_blocks(X, terms, block=256):
+    """Block rows [s, s + block - 1): the last row of every block left out."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    parts = []
+    for s0 in range(0, n, block):
+        diff = X[s0:s0 + block - 1, None, :] - X[None, :, :]
+        parts.append(float(np.sum(F.kernel_eval(diff, terms))))
+    return math.fsum(parts) / float(n) ** 2
 
 
 def _overlap_self(c, j):
@@ -534,6 +556,7 @@ MUTANTS = {
     # binning (Sec. 4) and the grid rules (Eqs. 16, 21, 26, 27)
     "linear binning: f and 1 - f swapped": lambda mp: _patch(mp, _bin_linear(swap=True), (binning, "bin_linear")),
     "linear binning: corner offsets on the reversed axis": lambda mp: _patch(mp, _bin_linear(axis_flip=True), (binning, "bin_linear")),
+    "grid: a point on the lower edge is outside": lambda mp: _patch(mp, _inside_lower_open, (binning, "_inside")),
     "simple binning: floor, not nearest": lambda mp: _patch(mp, _bin_simple_floor, (binning, "bin_simple")),
     "Eq. 16: range / M": lambda mp: _patch(mp, _bin_width_over_M, (rules, "bin_width"), (binning, "bin_width")),
     "Eq. 26: floor for ceil": lambda mp: _patch(mp, _support_L(rounding=math.floor), (rules, "support_L")),
@@ -546,6 +569,7 @@ MUTANTS = {
     "Eq. 21: 3M for 3M - 1": lambda mp: _patch(mp, _P_paper_full_3M, (rules, "P_paper_full")),
     "minimal P: M + L - 1": lambda mp: _patch(mp, _P_minimal_short, (rules, "P_minimal")),
     # binned double sums (Eqs. 18-25) and the lag-domain form
+    "direct sum: last row of each block left out": lambda mp: _patch(mp, _direct_sum_short_blocks, (F, "direct_sum")),
     "Eq. 12: i = j terms left out": lambda mp: _patch(mp, _direct_sum_offdiag, (F, "direct_sum")),
     "Eq. 25: a slice times itself": lambda mp: _patch(mp, _overlap_self, (F, "_overlap")),
     "Eq. 18: lag box not centred on 0": lambda mp: _patch(mp, _lag_kernel_uncentred, (F, "lag_kernel")),
