@@ -35,6 +35,8 @@ class OutsideGrid(ValueError):
 
 
 def _coords(X, lo, hi, M):
+    """t_k = (x_k - g_k1) / delta_k with delta_k of Eq. 16, clamped to M_k - 1
+    (Sec. 4, first step; reading in the module header)."""
     X = np.asarray(X, dtype=np.float64)
     lo = np.asarray(lo, dtype=np.float64)
     delta = bin_width(lo, hi, M)
@@ -44,6 +46,8 @@ def _coords(X, lo, hi, M):
 
 
 def _inside(X, lo, hi, policy):
+    """g_k1 <= x_k <= g_kM_k on every axis (the grid range holds the data,
+    Sec. 4); outside points raise under "error" and are skipped under "drop"."""
     X = np.asarray(X, dtype=np.float64)
     ok = np.all((X >= np.asarray(lo, dtype=np.float64)) & (X <= np.asarray(hi, dtype=np.float64)), axis=1)
     if not np.all(ok):
@@ -53,7 +57,8 @@ def _inside(X, lo, hi, policy):
 
 
 def bin_linear(X, lo, hi, M, policy: str = "error"):
-    """Linear binning; returns FP64 counts of shape M."""
+    """Linear binning (Sec. 4, first step; multilinear weights as in the
+    module header); returns FP64 counts of shape M."""
     M = [int(m) for m in M]
     t, _ = _coords(X, lo, hi, M)
     ok = _inside(X, lo, hi, policy)
@@ -75,7 +80,8 @@ def bin_linear(X, lo, hi, M, policy: str = "error"):
 
 
 def bin_simple(X, lo, hi, M, policy: str = "error"):
-    """Simple (nearest-node) binning; returns int64 counts of shape M."""
+    """Simple (nearest-node) binning (Sec. 4, first step); returns int64
+    counts of shape M."""
     M = [int(m) for m in M]
     t, _ = _coords(X, lo, hi, M)
     ok = _inside(X, lo, hi, policy)

@@ -56,7 +56,8 @@ def lag_kernel(terms, delta, L) -> np.ndarray:
 
 
 def _overlap(c: np.ndarray, j) -> float:
-    """sum_i c_i c_{i-j} over the grid (c = 0 outside)."""
+    """sum_i c_i c_{i-j} over the grid (c = 0 outside): the factor of k_j in
+    Eq. 25's double sum."""
     sl_a, sl_b = [], []
     for k, jk in enumerate(j):
         Mk = c.shape[k]
@@ -102,7 +103,7 @@ def autocorr(c, A) -> np.ndarray:
 
 
 def half_box_weights(A) -> np.ndarray:
-    """w_j on the half box of `autocorr`: 2 where the first nonzero of
+    """w_j on the half box of `autocorr` (Eq. 25 summed over the lag): 2 where the first nonzero of
     (j_0, .., j_{d-1}) is positive, 1 at j = 0, 0 where it is negative, so
     that sum_half w_j f_j = sum_full f_j for every even f."""
     d = len(A)

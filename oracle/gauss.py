@@ -31,7 +31,8 @@ import numpy as np
 
 
 def multi_indices(d: int, r: int):
-    """All alpha in N^d with |alpha| = r, lexicographically descending."""
+    """All alpha in N^d with |alpha| = r, lexicographically descending: the
+    unique entries of D^{(x)r} (Sec. 5)."""
     out = []
     for combo in itertools.combinations_with_replacement(range(d), r):
         a = [0] * d
@@ -42,7 +43,8 @@ def multi_indices(d: int, r: int):
 
 
 def kron_alphas(d: int, r: int):
-    """alpha(i) for every Kronecker position i of D^{(x)r}, i_1 slowest."""
+    """alpha(i) for every Kronecker position i of D^{(x)r}, i_1 slowest
+    (Sec. 5's vec / Kronecker-power layout)."""
     out = []
     for idx in itertools.product(range(d), repeat=r):
         a = [0] * d
@@ -67,7 +69,8 @@ def gauss_density(x: np.ndarray, Sigma: np.ndarray) -> np.ndarray:
 
 
 def hermite_table(z: np.ndarray, Lam: np.ndarray, R: int) -> dict:
-    """He_alpha(z; Lambda) for every |alpha| <= R by the recurrence above.
+    """He_alpha(z; Lambda) for every |alpha| <= R by the recurrence above,
+    which gives the partials that Sec. 5 needs.
 
     z has shape (..., d).  Returns {alpha: array of shape z.shape[:-1]}."""
     d = Lam.shape[0]
@@ -90,7 +93,8 @@ def hermite_table(z: np.ndarray, Lam: np.ndarray, R: int) -> dict:
 
 
 def gauss_derivs(x: np.ndarray, Sigma: np.ndarray, alphas) -> dict:
-    """{alpha: d^alpha phi_Sigma(x)} for the requested multi-indices."""
+    """{alpha: d^alpha phi_Sigma(x)} for the requested multi-indices: the
+    entries of D^{(x)r} phi_Sigma (Sec. 5)."""
     x = np.asarray(x, dtype=np.float64)
     Sigma = np.asarray(Sigma, dtype=np.float64)
     Lam = np.linalg.inv(Sigma)
@@ -103,7 +107,7 @@ def gauss_derivs(x: np.ndarray, Sigma: np.ndarray, alphas) -> dict:
 
 
 def gauss_deriv(x: np.ndarray, Sigma: np.ndarray, alpha) -> np.ndarray:
-    """d^alpha phi_Sigma(x) for one multi-index."""
+    """d^alpha phi_Sigma(x) for one multi-index (Sec. 5)."""
     return gauss_derivs(x, Sigma, [alpha])[tuple(alpha)]
 
 
@@ -130,7 +134,8 @@ def kernel_eval(x: np.ndarray, terms) -> np.ndarray:
 
 
 def pairings_value_at_zero(Sigma: np.ndarray, alpha) -> float:
-    """Isserlis closed form of d^alpha phi_Sigma(0), independent of the
+    """Isserlis closed form of d^alpha phi_Sigma(0) (the value at the origin
+    that the n = 1 case of Eq. 13 reduces to), independent of the
     recurrence: (-1)^{|alpha|/2} phi_Sigma(0) sum over perfect matchings of the
     multiset alpha of prod Lambda_ab; zero for odd |alpha|."""
     Sigma = np.asarray(Sigma, dtype=np.float64)

@@ -13,7 +13,8 @@ from .gauss import gauss_density
 
 
 def kde_grid(c, n, H, delta, L):
-    """f_hat(g) = n^-1 sum_{|l_k| <= L_k} c_{g - l} K_H(delta (.) l) at every
+    """Eq. 1 with the sample replaced by its bin counts:
+    f_hat(g) = n^-1 sum_{|l_k| <= L_k} c_{g - l} K_H(delta (.) l) at every
     grid node g (c = 0 off the grid): shifted copies of the counts weighted
     by the Gaussian at each lag."""
     c = np.asarray(c, dtype=np.float64)
@@ -30,7 +31,8 @@ def kde_grid(c, n, H, delta, L):
 
 
 def mixture_sq_integral(w, mu, S):
-    """int f^2 = sum_lm w_l w_m phi_{S_l + S_m}(mu_l - mu_m) for
+    """The int f^2 term of Eq. 37:
+    int f^2 = sum_lm w_l w_m phi_{S_l + S_m}(mu_l - mu_m) for
     f = sum_m w_m phi_{S_m}(. - mu_m) (Gaussian convolution identity)."""
     K = len(w)
     tot = 0.0

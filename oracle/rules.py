@@ -32,7 +32,8 @@ def bin_width(lo, hi, M):
 
 
 def lambda_max(S) -> float:
-    """Largest eigenvalue of a symmetric matrix (LAPACK via numpy)."""
+    """Largest eigenvalue of a symmetric matrix (LAPACK via numpy): the
+    lambda of Eq. 26."""
     return float(np.linalg.eigvalsh(np.asarray(S, dtype=np.float64))[-1])
 
 
@@ -46,6 +47,7 @@ def support_L(lam: float, delta, M, tau: float = 3.7):
 
 
 def _next_pow2(x: int) -> int:
+    """2^ceil(log2 x), the rounding of Eqs. 21 and 27."""
     p = 1
     while p < x:
         p *= 2
@@ -63,6 +65,8 @@ def P_paper_full(M):
 
 
 def _is_smooth(x: int) -> bool:
+    """x = 2^a 3^b 5^c: the lengths P_minimal allows (a reading of the
+    zero-padding layout of Eqs. 19-20)."""
     for p in (2, 3, 5):
         while x % p == 0:
             x //= p
@@ -70,7 +74,9 @@ def _is_smooth(x: int) -> bool:
 
 
 def P_minimal(M, L):
-    """Smallest 2^a 3^b 5^c >= M_k + L_k on each axis."""
+    """Smallest 2^a 3^b 5^c >= M_k + L_k on each axis: the least padded size
+    for which the layout of Eqs. 19-20 has no wrapped term at the outputs
+    Eq. 23 extracts."""
     out = []
     for m, l in zip(M, L):
         x = int(m) + int(l)

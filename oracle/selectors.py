@@ -30,6 +30,7 @@ from .gauss import kron_alphas, multi_indices
 
 
 def _e(d, *idx):
+    """The multi-index with one count per listed axis (d_a d_b ... of Sec. 5)."""
     a = [0] * d
     for i in idx:
         a[i] += 1
@@ -37,15 +38,20 @@ def _e(d, *idx):
 
 
 def _tie(a, b):
+    """1 on the diagonal, 2 off it: the tied-entry gradient convention of the
+    module header, one free parameter per entry pair of the unconstrained H
+    (Sec. 3)."""
     return 1.0 if a == b else 2.0
 
 
 def _det(S):
+    """|S| (LAPACK via numpy), as in K_H(0) of Eq. 11."""
     return float(np.linalg.det(np.asarray(S, dtype=np.float64)))
 
 
 def vech_pairs(d):
-    """(a, b) with a <= b in row-major order: the free entries of H."""
+    """(a, b) with a <= b in row-major order: the free entries of the
+    unconstrained H (Sec. 3)."""
     return [(a, b) for a in range(d) for b in range(a, d)]
 
 
@@ -111,6 +117,8 @@ def lscv(ev, H, n: int, exact_loo: bool = False, grad: bool = False):
 #            + n^-2 sum sum [phi_{2H+2G} - 2 phi_{H+2G} + phi_{2G}](X_i - X_j)
 
 def scv_terms(H, G):
+    """The kernel of the SCV double sum (reading in the comment above; SCV is
+    named in Sec. 3): phi_{2H+2G} - 2 phi_{H+2G} + phi_{2G}."""
     H = np.asarray(H, dtype=np.float64)
     G = np.asarray(G, dtype=np.float64)
     z = _e(H.shape[0])
@@ -118,6 +126,8 @@ def scv_terms(H, G):
 
 
 def scv_grad_terms(H, G, a, b):
+    """d/dh_ab of the SCV kernel (SCV named in Sec. 3) by the heat equation:
+    s_ab (d_a d_b phi_{2H+2G} - d_a d_b phi_{H+2G})."""
     H = np.asarray(H, dtype=np.float64)
     G = np.asarray(G, dtype=np.float64)
     s = _tie(a, b)
@@ -126,12 +136,15 @@ def scv_grad_terms(H, G, a, b):
 
 
 def RK(H) -> float:
-    """n-free roughness term (4 pi)^{-d/2} |H|^{-1/2} = int K_H^2."""
+    """n-free roughness term (4 pi)^{-d/2} |H|^{-1/2} = int K_H^2, the K_H * K_H
+    of Eq. 11 at 0."""
     d = np.asarray(H).shape[0]
     return (4.0 * math.pi) ** (-d / 2.0) / math.sqrt(_det(H))
 
 
 def scv(ev, H, G, n: int, grad: bool = False):
+    """SCV(H) (Sec. 3; the reading above) and, with grad, its gradient in the
+    tied convention."""
     H = np.asarray(H, dtype=np.float64)
     d = H.shape[0]
     r0 = RK(H)
@@ -150,7 +163,8 @@ def scv(ev, H, G, n: int, grad: bool = False):
 # psi_r (Eq. 13) and the eta functionals of Sec. 5 (Eqs. 29-32)
 
 def psi_unique(ev, H, r):
-    """{alpha: n^-2 sum sum d^alpha phi_H(X_i - X_j)} for |alpha| = r."""
+    """{alpha: n^-2 sum sum d^alpha phi_H(X_i - X_j)} for |alpha| = r: the
+    unique entries of psi_r of Eq. 13."""
     return {a: ev([(1.0, np.asarray(H, dtype=np.float64), a)])
             for a in multi_indices(np.asarray(H).shape[0], r)}
 
@@ -222,6 +236,8 @@ def eta_r_terms(Sigma, r):
 #   PI(H) = n^-1 (4 pi)^{-d/2} |H|^{-1/2} + 1/4 (vec^T H)^{(x)2} psi_4(G)
 
 def pi_from_psi4(psi4_kron, H, n: int, grad: bool = False):
+    """PI(H) from psi_4(G) in Kronecker order (plug-in reading above; psi_4 of
+    Eq. 13) and, with grad, its gradient in the tied convention."""
     H = np.asarray(H, dtype=np.float64)
     d = H.shape[0]
     T = np.asarray(psi4_kron, dtype=np.float64).reshape((d, d, d, d))
