@@ -61,3 +61,46 @@ def test_opts_struct_size_matches_header(lib_path):
     import paper_1511_07482_gb300 as pkg
     # double + 2 int + 4 int + 4 int = 8 + 40 = 48 bytes
     assert ctypes.sizeof(pkg._lib.Opts) == 48
+
+
+def _prototypes():
+    """name -> (return type, [parameter declarations]) of every function the
+    header declares (comments removed, declarations joined across lines)."""
+    import re as _re
+    src = open(os.path.join(ROOT, "include", "kdefft.h")).read()
+    src = _re.sub(r"/\*.*?\*/", "", src, flags=_re.S)
+    out = {}
+    for m in _re.finditer(r"(int|const char\*)\s+(kdefft_\w+)\s*\(([^)]*)\)\s*;", src):
+        params = [p.strip() for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(2)] = (m.group(1), params)
+    return out
+
+
+def _kind_of_decl(p):
+    if "*" in p or p.split()[0] in ("kdefft_ctx", "kdefft_ds"):
+        return "ptr"
+    t = p.replace("const ", "").split()[0]
+    return {"int": "int", "int64_t": "int64", "double": "double"}[t]
+
+
+def _kind_of_ctype(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and t.__name__.startswith("LP_"):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_int64: "int64", ctypes.c_double: "double"}[t]
+
+
+def test_binding_signatures_match_the_header(lib_path):
+    """Every ctypes prototype the binding sets has the header's number of
+    parameters, and each parameter the header's kind (pointer, int, int64,
+    double): a mismatch would pass the wrong bytes through the C ABI."""
+    import paper_1511_07482_gb300 as pkg
+    lib = pkg.load()
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    for name, (ret, params) in protos.items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == len(params), (name, len(f.argtypes), params)
+        for i, (t, p) in enumerate(zip(f.argtypes, params)):
+            assert _kind_of_ctype(t) == _kind_of_decl(p), (name, i, p, t)
+        assert (f.restype is ctypes.c_char_p) == (ret == "const char*"), name
