@@ -104,3 +104,24 @@ def test_binding_signatures_match_the_header(lib_path):
         for i, (t, p) in enumerate(zip(f.argtypes, params)):
             assert _kind_of_ctype(t) == _kind_of_decl(p), (name, i, p, t)
         assert (f.restype is ctypes.c_char_p) == (ret == "const char*"), name
+
+
+def test_binding_constants_match_the_header():
+    """The status codes and option enums of the binding carry the header's
+    values (KDEFFT_X in the header is X in the binding)."""
+    import re as _re
+    from paper_1511_07482_gb300 import _lib
+    src = _re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "kdefft.h")).read(), flags=_re.S)
+    consts = {m.group(1): int(m.group(2)) for m in _re.finditer(r"#define KDEFFT_(\w+)\s+(\d+)\s*$", src, _re.M)}
+    for body in _re.findall(r"enum\s*\{([^}]*)\}", src):
+        for m in _re.finditer(r"KDEFFT_(\w+)\s*=\s*(\d+)", body):
+            consts[m.group(1)] = int(m.group(2))
+    checked = 0
+    for name, value in consts.items():
+        if hasattr(_lib, name):
+            assert getattr(_lib, name) == value, name
+            checked += 1
+    assert checked >= 25
+    for name in ("OK", "ERR_ARG", "ERR_NOT_SPD", "ERR_OUTSIDE_GRID", "ERR_CUDA", "ERR_TIMEOUT", "P_MINIMAL",
+                 "FP32", "FP64", "BIN_SIMPLE", "LSCV", "SCV", "PI", "DT_I32"):
+        assert hasattr(_lib, name) and consts[name] == getattr(_lib, name), name
