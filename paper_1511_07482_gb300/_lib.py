@@ -3,7 +3,9 @@
 Every computation runs in libkdefft.so on the GPU; if the library is missing
 or no CUDA device is usable the calls raise: there is no CPU fallback.
 Arrays may be numpy arrays (host) or torch tensors (host or CUDA); outputs
-are returned as numpy arrays.
+are returned as numpy arrays.  Every array's size is checked against d before
+the library reads through its pointer; an empty batch (no bandwidths, no
+datasets) returns empty results without a library call.
 """
 from __future__ import annotations
 
@@ -308,6 +310,8 @@ class Context:
         """Bin many datasets of the same dimension in one call (a few
         batched launches): one Dataset per sample."""
         nds = len(Xs)
+        if nds == 0:
+            return []
         keep = [_ptr_of(X) for X in Xs]
         d = int(keep[0][0].shape[1])
         if any(int(k.shape[1]) != d for k, _ in keep):
@@ -331,6 +335,8 @@ class Context:
 
     def batch_lscv(self, datasets, H_per_ds, grad=True):
         """LSCV (+ gradient) for many datasets in one batched launch sequence."""
+        if len(datasets) == 0:
+            return (np.zeros(0), np.zeros((0, 0, 0))) if grad else np.zeros(0)
         lib = load()
         d = datasets[0].d
         nh = np.array([len(h) for h in H_per_ds], dtype=np.int32)
@@ -393,6 +399,8 @@ class Dataset:
         """psi_r(H) (Eq. 13) as nH x d^r, Kronecker order."""
         H, nH = self._Hs(H)
         out = np.zeros((nH, self.d ** r))
+        if nH == 0:
+            return out
         _check(load().kdefft_psi(self.h, H.ctypes.data_as(C.c_void_p), nH, r, out.ctypes.data_as(C.c_void_p)))
         return out
 
@@ -400,6 +408,8 @@ class Dataset:
         H, nH = self._Hs(H)
         val = np.zeros(nH)
         g = np.zeros((nH, self.d, self.d)) if grad else None
+        if nH == 0:
+            return (val, g) if grad else val
         _check(load().kdefft_lscv(self.h, H.ctypes.data_as(C.c_void_p), nH, val.ctypes.data_as(C.c_void_p),
                                   g.ctypes.data_as(C.c_void_p) if grad else None))
         return (val, g) if grad else val
@@ -409,6 +419,8 @@ class Dataset:
         Ga, pG = _mat(G, self.d, "G")
         val = np.zeros(nH)
         g = np.zeros((nH, self.d, self.d)) if grad else None
+        if nH == 0:
+            return (val, g) if grad else val
         _check(load().kdefft_scv(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
                                  g.ctypes.data_as(C.c_void_p) if grad else None))
         return (val, g) if grad else val
@@ -418,6 +430,8 @@ class Dataset:
         Ga, pG = _mat(G, self.d, "G")
         val = np.zeros(nH)
         g = np.zeros((nH, self.d, self.d)) if grad else None
+        if nH == 0:
+            return (val, g) if grad else val
         _check(load().kdefft_pi(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
                                 g.ctypes.data_as(C.c_void_p) if grad else None))
         return (val, g) if grad else val
@@ -437,6 +451,8 @@ class Dataset:
         derivative order (even).  One value per Sigma."""
         S, nS = self._Hs(Sigma)
         out = np.zeros(nS)
+        if nS == 0:
+            return out
         _check(load().kdefft_qr(self.h, S.ctypes.data_as(C.c_void_p), nS, int(r), out.ctypes.data_as(C.c_void_p)))
         return out
 
@@ -447,6 +463,8 @@ class Dataset:
         Aa, pA = _opt_mat(A, self.d, "A")
         Ba, pB = _opt_mat(B, self.d, "B")
         out = np.zeros(nS)
+        if nS == 0:
+            return out
         _check(load().kdefft_eta_rs(self.h, pA, pB, S.ctypes.data_as(C.c_void_p), nS, int(r), int(s),
                                     out.ctypes.data_as(C.c_void_p)))
         return out
@@ -466,6 +484,8 @@ class Dataset:
         mu = np.ascontiguousarray(np.asarray(means, dtype=np.float64).reshape(len(w), self.d))
         S = np.ascontiguousarray(np.asarray(covs, dtype=np.float64).reshape(len(w), self.d, self.d))
         out = np.zeros(nH)
+        if nH == 0:
+            return out
         _check(load().kdefft_ise_mixture(self.h, H.ctypes.data_as(C.c_void_p), nH, len(w),
                                          w.ctypes.data_as(C.c_void_p), mu.ctypes.data_as(C.c_void_p),
                                          S.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
@@ -476,6 +496,8 @@ class Dataset:
         derivative; values."""
         H, nH = self._Hs(H)
         out = np.zeros(nH)
+        if nH == 0:
+            return out
         _check(load().kdefft_lscv_r(self.h, H.ctypes.data_as(C.c_void_p), nH, int(r), out.ctypes.data_as(C.c_void_p)))
         return out
 
@@ -483,6 +505,8 @@ class Dataset:
         H, nH = self._Hs(H)
         Ga, pG = _mat(G, self.d, "G")
         val = np.zeros(nH)
+        if nH == 0:
+            return val
         _check(load().kdefft_eta02(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p)))
         return val
 

@@ -61,3 +61,28 @@ def test_well_shaped_arguments_pass_the_checks():
     assert v.dtype == np.int64 and v.shape == (3,)
     keep, p = _lib._ptr_of(np.zeros((4, 3)))
     assert keep.shape == (4, 3) and p.value
+
+
+def test_empty_batches_give_empty_results():
+    """No bandwidths, no datasets: empty results of the documented shapes,
+    without a library call (the C ABI itself refuses empty batches)."""
+    ds = _ds(d=2)
+    H0 = np.zeros((0, 2, 2))
+    G = np.eye(2)
+    assert ds.psi(H0, 4).shape == (0, 16)
+    v, g = ds.lscv(H0, grad=True)
+    assert v.shape == (0,) and g.shape == (0, 2, 2)
+    assert ds.lscv(H0).shape == (0,)
+    assert ds.scv(H0, G, grad=True)[1].shape == (0, 2, 2)
+    assert ds.pi(H0, G).shape == (0,)
+    assert ds.eta02(H0, G).shape == (0,)
+    assert ds.qr(H0, 2).shape == (0,)
+    assert ds.eta_rs(H0, 1, 1).shape == (0,)
+    assert ds.lscv_r(H0, 1).shape == (0,)
+    assert ds.ise_mixture(H0, [1.0], [[0.0, 0.0]], [np.eye(2)]).shape == (0,)
+    c = _ctx()
+    assert c.bin_many([], [], [], []) == []
+    assert c.batch_lscv([], [], grad=False).shape == (0,)
+    # the G check still runs on an empty batch
+    with pytest.raises(ValueError):
+        ds.scv(H0, np.eye(3))
