@@ -411,6 +411,118 @@ def test_pi_eta02_route_equals_psi4_contraction():
     assert a == pytest.approx(b, rel=1e-11)
 
 
+# ---------------------------------------------------------------- SCV and PI by quadrature
+#
+# Both readings (SCV and PI are named in Sec. 3; Sec. 5 defers their formulas)
+# are pinned here to integrals of plain kernel estimates, evaluated by a
+# Riemann sum on a uniform box.  For Gaussian integrands the uniform sum
+# converges faster than any power of the step (its aliasing error is about
+# exp(-2 pi^2 sd^2 / h^2)), so a step of a quarter of the narrowest standard
+# deviation and a box reaching ten of the widest ones beyond the sample give
+# the integral to rounding.  The densities and the Hessian below are written
+# out from the normal density, without the oracle's Hermite recurrence.
+
+def _normal_pdf_2d(P, mu, Sg):
+    """phi_Sigma(P - mu) for an array of points P (..., 2)."""
+    Sg = np.asarray(Sg, dtype=np.float64)
+    Li = np.linalg.inv(Sg)
+    y = P - mu
+    q = np.einsum("...a,ab,...b->...", y, Li, y)
+    return np.exp(-0.5 * q) / (2.0 * math.pi * math.sqrt(np.linalg.det(Sg)))
+
+
+def _plain_kde(P, X, Sg):
+    """f_hat_Sigma(P) = n^-1 sum_i phi_Sigma(P - X_i) (Eq. 1 with a Gaussian K_Sigma)."""
+    return sum(_normal_pdf_2d(P, x, Sg) for x in X) / len(X)
+
+
+def _quad_box(X, covs, pad=10.0, per_sd=4.0):
+    """Nodes of a uniform box holding every kernel's mass around the sample,
+    and the area of one cell."""
+    sd_max = max(math.sqrt(np.linalg.eigvalsh(C).max()) for C in covs)
+    sd_min = min(math.sqrt(np.linalg.eigvalsh(C).min()) for C in covs)
+    lo, hi = X.min(0) - pad * sd_max, X.max(0) + pad * sd_max
+    h = sd_min / per_sd
+    axes = [np.arange(lo[k], hi[k] + h, h) for k in range(2)]
+    return np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1), h * h
+
+
+def _scv_pi_case():
+    rng = np.random.default_rng(21)
+    n = 30
+    X = rng.standard_normal((n, 2))
+    X[: n // 2] += [1.2, -0.4]
+    H = np.array([[0.30, -0.09], [-0.09, 0.22]])
+    G = np.array([[0.18, 0.05], [0.05, 0.26]])
+    return X, H, G
+
+
+def test_scv_is_integrated_squared_difference_of_estimates():
+    """SCV(H) - n^-1 R(K_H) = int (f_hat_{H+G} - f_hat_G)^2: the smoothed
+    bootstrap's integrated squared bias, K_H * f_hat_G - f_hat_G with the
+    pilot estimate f_hat_G; K_H * f_hat_G = f_hat_{H+G} for Gaussians.  The
+    double-sum reading convolves the Gaussians pairwise (2H + 2G, H + 2G,
+    2G); here the integral is taken numerically."""
+    X, H, G = _scv_pi_case()
+    n = len(X)
+    P, dA = _quad_box(X, [H + G, G])
+    quad = float(np.sum((_plain_kde(P, X, H + G) - _plain_kde(P, X, G)) ** 2) * dA)
+    got = S.scv(lambda t: F.direct_sum(X, t), H, G, n) - S.RK(H) / n
+    assert got == pytest.approx(quad, rel=1e-10)
+    # the n^-1 R(K_H) term is int K_H^2, also by quadrature
+    Pk, dAk = _quad_box(np.zeros((1, 2)), [H])
+    assert S.RK(H) == pytest.approx(float(np.sum(_normal_pdf_2d(Pk, 0.0, H) ** 2) * dAk), rel=1e-10)
+
+
+def _trace_H_hessian_of_kde(P, X, H, Sg):
+    """tr(H grad grad^T f_hat_Sigma)(P), with grad grad^T phi_Sigma(y) =
+    (Lambda y y^T Lambda - Lambda) phi_Sigma(y), Lambda = Sigma^-1."""
+    Li = np.linalg.inv(Sg)
+    out = 0.0
+    for x in X:
+        z = (P - x) @ Li.T
+        quad = np.einsum("...a,ab,...b->...", z, H, z)
+        out = out + (quad - np.trace(H @ Li)) * _normal_pdf_2d(P, x, Sg)
+    return out / len(X)
+
+
+def test_pi_contraction_is_integrated_squared_hessian_trace():
+    """(vec^T H)^{(x)2} psi_4(G) = int (tr(H grad grad^T f_hat_{G/2}))^2
+    (integration by parts twice, and phi_{G/2} * phi_{G/2} = phi_G): the
+    contraction the plug-in reading uses, from psi_4 of Eq. 13 and from the
+    eta_{0,2} kernel of Eq. 30, against a numerical integral."""
+    X, H, G = _scv_pi_case()
+    n = len(X)
+    P, dA = _quad_box(X, [G / 2.0])
+    quad = float(np.sum(_trace_H_hessian_of_kde(P, X, H, G / 2.0) ** 2) * dA)
+    ev = lambda t: F.direct_sum(X, t)
+    T = S.psi_vector(ev, G, 4).reshape((2, 2, 2, 2))
+    assert float(np.einsum("ab,ce,abce->", H, H, T)) == pytest.approx(quad, rel=1e-10)
+    assert ev(S.eta02_terms(H, G)) == pytest.approx(quad, rel=1e-10)
+
+
+def test_pi_is_the_small_bandwidth_limit_of_the_exact_bias():
+    """The plug-in term is the leading order of the exact integrated squared
+    bias: int (f_hat_{G/2 + tH} - f_hat_{G/2})^2 = t^2 (PI(H) - n^-1 R(K_H))
+    + O(t^3) as t -> 0 (heat equation: phi_{S + tH} = exp(t/2 tr(H grad
+    grad^T)) phi_S, whose second-order term squared carries 1/4).  This fixes
+    the reading's factor 1/4, on both routes, without restating it: the
+    bias is integrated numerically at t, t/2, t/4 and extrapolated to t = 0."""
+    X, H, G = _scv_pi_case()
+    n = len(X)
+    Gh = G / 2.0
+    P, dA = _quad_box(X, [Gh])
+    f0 = _plain_kde(P, X, Gh)
+    r = lambda t: float(np.sum((_plain_kde(P, X, Gh + t * H) - f0) ** 2) * dA) / t ** 2
+    t = 0.01
+    lim = (8.0 * r(t / 4) - 6.0 * r(t / 2) + r(t)) / 3.0   # removes the O(t) and O(t^2) terms
+    ev = lambda tt: F.direct_sum(X, tt)
+    want_psi4 = S.pi_from_psi4(S.psi_vector(ev, G, 4), H, n) - S.RK(H) / n
+    want_eta = S.pi_eta(ev, H, G, n) - S.RK(H) / n
+    assert want_psi4 == pytest.approx(lim, rel=1e-3)
+    assert want_eta == pytest.approx(lim, rel=1e-3)
+
+
 def test_scv_single_point_closed_form():
     H = np.array([[0.3, 0.1], [0.1, 0.2]])
     G = np.array([[0.15, 0.0], [0.0, 0.1]])

@@ -440,6 +440,21 @@ def _pi_eta_half(ev, H, G, n):
     return S.RK(H) / n + 0.5 * ev(S.eta02_terms(H, G))
 
 
+def _scv_pilot_at_G_terms(H, G):
+    H = np.asarray(H, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    z = S._e(H.shape[0])
+    return [(1.0, 2.0 * H + G, z), (-2.0, H + G, z), (1.0, G, z)]
+
+
+def _scv_pilot_at_G_grad(H, G, a, b):
+    H = np.asarray(H, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    s = S._tie(a, b)
+    al = S._e(H.shape[0], a, b)
+    return [(s, 2.0 * H + G, al), (-s, H + G, al)]
+
+
 def _pi_from_psi4(quarter=0.25, half=0.5):
     def pi(psi4_kron, H, n, grad=False):
         H = np.asarray(H, dtype=np.float64)
@@ -599,6 +614,13 @@ MUTANTS = {
     "R(K) with (2 pi)^-d/2": lambda mp: _patch(mp, _const_pi(2.0), (S, "RK")),
     "PI: 1/2 for 1/4": lambda mp: _patch(mp, _pi_from_psi4(quarter=0.5), (S, "pi_from_psi4")),
     "PI gradient: factor 1/2 dropped": lambda mp: _patch(mp, _pi_from_psi4(half=1.0), (S, "pi_from_psi4")),
+    # consistent misreadings: value and gradient (or both routes) carry the same slip
+    "SCV: pilot convolutions at G, value and gradient together": lambda mp: (
+        _patch(mp, _scv_pilot_at_G_terms, (S, "scv_terms")),
+        _patch(mp, _scv_pilot_at_G_grad, (S, "scv_grad_terms"))),
+    "PI: 1/2 for 1/4 on both routes (value and gradient)": lambda mp: (
+        _patch(mp, _pi_from_psi4(quarter=0.5, half=1.0), (S, "pi_from_psi4")),
+        _patch(mp, _pi_eta_half, (S, "pi_eta"))),
     "Eq. 30: B_ab B_ae for B_ab B_ce": lambda mp: _patch(mp, _eta02_index_typo, (S, "eta02_terms")),
     "Eq. 31: multinomial weights dropped": lambda mp: _patch(mp, _eta_r_no_multinomial, (S, "eta_r_terms")),
     "Eq. 30: A in place of B": lambda mp: _patch(mp, _eta_rs_A_only, (S, "eta_rs_terms")),
