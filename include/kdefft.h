@@ -350,6 +350,25 @@ int kdefft_autocorr(kdefft_ds ds, const int* A, double* out);
  * events. */
 int kdefft_set_graphs(kdefft_ctx ctx, int on);
 
+/* Record of the device-resident searches' own evaluations (Eq. 9's
+ * minimiser on the d = 2 FP32 path of kdefft_select_H and
+ * kdefft_select_H_multi), so that each value and gradient the search compares
+ * can be checked against an FP64 evaluation at the same bandwidth.  rec: a
+ * device buffer on the context's GPU of rec_len doubles, or NULL to turn
+ * recording off (the default; the search kernels then write nothing).  While
+ * on, the s-th start of a search launch (criteria in the order given to
+ * kdefft_select_H_multi, each criterion's starts in order) writes its e-th
+ * evaluation, for e < cap, to rec[(s cap + e) 12 ..] as 12 doubles: s, e,
+ * criterion (0 LSCV of Eq. 10, 1 SCV), H_00, H_01, H_11 (the FP32 values the
+ * search evaluated), L_0, L_1 (Eq. 26, as the search computed them), the
+ * objective value, and its gradient dF/dH_00, dF/dH_01 (tied convention),
+ * dF/dH_11.  Slots of evaluations that did not happen are left untouched.
+ * The caller keeps the buffer alive while recording is on; a search with
+ * more than rec_len / (12 cap) starts fails with KDEFFT_ERR_ARG before its
+ * launch.  Errors: KDEFFT_ERR_ARG (cap < 1, rec_len < 12 cap, rec not device
+ * memory of the context's GPU). */
+int kdefft_set_search_record(kdefft_ctx ctx, double* rec, int64_t rec_len, int cap);
+
 /* Counters of the two above since the context was created: shapes tuned,
  * graphs captured, graph replays.  Any pointer may be NULL. */
 int kdefft_runtime_stats(kdefft_ctx ctx, int64_t* shapes_tuned,
@@ -382,17 +401,23 @@ int kdefft_trim(kdefft_ctx ctx);
  *   kdefft_counts); H: d x d host array; tau: Eq. 26 multiplier (L_k from
  *   lambda_max(H)); P_k: the minimal no-alias padding; stream: cudaStream_t;
  *   out: device pointer to 1 + d*d FP64 values, LSCV(H) of Eq. 10 followed by
- *   the d x d gradient (convention above).
- * Runs on the calling thread's current device and returns without waiting
- * for the GPU.  The first call on a device takes the scratch array's device
- * address (cudaGetSymbolAddress) and uploads small constant tables; make that
- * first call before any stream capture.  All calls share the one scratch
+ *   the d x d gradient (convention above).  counts and out must be device
+ *   memory of the calling thread's current device.
+ * Runs on the current device and is ordered on `stream`; the host does not
+ * wait for the kernels, but its small tables go up by copies from pageable
+ * host memory, so a call may wait for earlier work on its stream.  The first
+ * call on a device takes the scratch array's device address
+ * (cudaGetSymbolAddress), uploads small constant tables and sets the
+ * kernels' shared-memory limits.  While `stream` is being captured the call
+ * does nothing and returns KDEFFT_ERR_UNSUPPORTED: those uploads read host
+ * staging that the next call overwrites.  All calls share the one scratch
  * array, which keeps the previous call's contents (everything that must
  * start at zero is written before it is read), so calls that overlap on the
  * GPU -- on different streams, unordered -- race; order them on one stream.
- * Errors: KDEFFT_ERR_ARG (bad sizes, out/counts not device memory, H not
- * symmetric), KDEFFT_ERR_NOT_SPD, KDEFFT_ERR_UNSUPPORTED (the problem needs
- * more than the scratch array holds, or P_k > 4096), KDEFFT_ERR_CUDA. */
+ * Errors: KDEFFT_ERR_ARG (bad sizes, out/counts not device memory of the
+ * current device, H not symmetric), KDEFFT_ERR_NOT_SPD,
+ * KDEFFT_ERR_UNSUPPORTED (the problem needs more than the scratch array
+ * holds, P_k > 4096, or the stream is being captured), KDEFFT_ERR_CUDA. */
 #define KDEFFT_NOALLOC_SCRATCH_BYTES (32u << 20)
 int kdefft_lscv_noalloc(int d, const int64_t* M, const double* delta, int64_t n,
                         const float* counts, const double* H, double tau,

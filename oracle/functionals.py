@@ -102,6 +102,32 @@ def autocorr(c, A) -> np.ndarray:
     return out
 
 
+def autocorr_fft(c):
+    """a_j = sum_i c_i c_{i+j} for every lag |j_k| <= M_k - 1, by one FFT pair
+    at P_k = 2 M_k (no wrapped term, since P_k >= 2 M_k - 1), FP64 on every
+    host core (pocketfft through scipy.fft).  Lag j sits at index j mod P.
+    The same numbers as `autocorr`; this is the route that reaches the
+    full-size grids."""
+    import scipy.fft as sf
+    c = np.asarray(c, dtype=np.float64)
+    P = [2 * m for m in c.shape]
+    czp = np.zeros(P)
+    czp[tuple(slice(0, m) for m in c.shape)] = c
+    return sf.irfftn(np.abs(sf.rfftn(czp, workers=-1)) ** 2, s=P, workers=-1)
+
+
+def lag_sums(a, n, terms, delta, L):
+    """(n^-2 sum_{|j_k| <= L_k} k_j a_j, n^-2 sum |k_j| a_j) with a from
+    `autocorr_fft`: Eq. 25 with the sum over the grid taken first, and the
+    absolute functional of the same kernel (the magnitude of the summed
+    terms)."""
+    k = lag_kernel(terms, delta, L)
+    idx = np.ix_(*[np.arange(-L[i], L[i] + 1) % a.shape[i] for i in range(len(L))])
+    aj = a[idx]
+    n2 = float(n) ** 2
+    return float(np.sum(k * aj)) / n2, float(np.sum(np.abs(k) * aj)) / n2
+
+
 def half_box_weights(A) -> np.ndarray:
     """w_j on the half box of `autocorr` (Eq. 25 summed over the lag): 2 where the first nonzero of
     (j_0, .., j_{d-1}) is positive, 1 at j = 0, 0 where it is negative, so

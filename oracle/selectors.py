@@ -159,6 +159,32 @@ def scv(ev, H, G, n: int, grad: bool = False):
     return val, g
 
 
+def abs_scales(ev_abs, method, H, n: int, G=None):
+    """Magnitudes of the summed terms of an objective and of each gradient
+    entry: the absolute functional n^-2 sum |k|(X_i - X_j) of its kernel
+    (ev_abs) plus the magnitude of its closed-form term.  method: "lscv"
+    (Eq. 10) or "scv" (the reading above).  A value much smaller than its
+    scale is a difference of large terms, and its rounding error is bounded
+    relative to the scale, not to the value."""
+    H = np.asarray(H, dtype=np.float64)
+    d = H.shape[0]
+    Hinv = np.linalg.inv(H)
+    if method == "lscv":
+        c0 = K0(H)
+        sv = ev_abs(lscv_T_terms(H)) + 2.0 * c0 / n
+        grad_terms = lambda a, b: lscv_grad_terms(H, a, b)
+        closed = lambda a, b: 2.0 / n * _tie(a, b) * 0.5 * c0 * abs(Hinv[a, b])
+    else:
+        r0 = RK(H)
+        sv = ev_abs(scv_terms(H, G)) + r0 / n
+        grad_terms = lambda a, b: scv_grad_terms(H, G, a, b)
+        closed = lambda a, b: _tie(a, b) * 0.5 * r0 * abs(Hinv[a, b]) / n
+    sg = np.zeros((d, d))
+    for a, b in vech_pairs(d):
+        sg[a, b] = sg[b, a] = ev_abs(grad_terms(a, b)) + closed(a, b)
+    return sv, sg
+
+
 # ---------------------------------------------------------------------------
 # psi_r (Eq. 13) and the eta functionals of Sec. 5 (Eqs. 29-32)
 

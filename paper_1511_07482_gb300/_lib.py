@@ -35,7 +35,7 @@ EXPORTS = [
     "kdefft_lscv_noalloc", "kdefft_set_engine", "kdefft_set_autotune", "kdefft_set_graphs",
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
     "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class", "kdefft_bin_many",
-    "kdefft_select_H_multi", "kdefft_memory_stats", "kdefft_trim",
+    "kdefft_select_H_multi", "kdefft_memory_stats", "kdefft_trim", "kdefft_set_search_record",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         "kdefft_memory_stats": (I, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "kdefft_trim": (I, [P]),
         "kdefft_select_H_multi": (I, [P, I, P, P, P, I, I, P, P, P]),
+        "kdefft_set_search_record": (I, [P, P, I64, I]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -254,6 +255,21 @@ class Context:
     def set_graphs(self, on: bool = True):
         """Replay repeated batch launch sequences from CUDA graphs (default on)."""
         _check(load().kdefft_set_graphs(self.h, int(bool(on))))
+
+    def set_search_record(self, rec=None, cap: int = 0):
+        """Record the device-resident searches' own evaluations into `rec`, a
+        CUDA float64 tensor of starts x cap x 12 values (None: stop
+        recording).  The tensor is kept alive here while recording is on."""
+        if rec is None:
+            _check(load().kdefft_set_search_record(self.h, None, 0, 0))
+            self._rec = None
+            return
+        import torch
+        if not (isinstance(rec, torch.Tensor) and rec.is_cuda and rec.dtype == torch.float64
+                and rec.is_contiguous()):
+            raise TypeError("rec must be a contiguous CUDA float64 tensor")
+        _check(load().kdefft_set_search_record(self.h, C.c_void_p(rec.data_ptr()), int(rec.numel()), int(cap)))
+        self._rec = rec
 
     def runtime_stats(self):
         """{"shapes_tuned", "graphs_captured", "graph_replays"} since creation."""

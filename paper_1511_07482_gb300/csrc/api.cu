@@ -364,19 +364,19 @@ struct HermiteIndex {
     }
 };
 
+// built once, on first use (a function-local static: thread-safe initialisation)
 static HermiteIndex& hindex() {
-    static HermiteIndex h;
-    static bool init = false;
-    if (!init) {
+    static HermiteIndex h = [] {
+        HermiteIndex x;
         for (int d = 1; d <= 4; ++d) {
-            enumerate(d, kRmax[d], h.list[d]);
+            enumerate(d, kRmax[d], x.list[d]);
             int n = 1;
             for (int i = 0; i < d; ++i) n *= 9;
-            h.code[d].assign(n, -1);
-            for (size_t t = 0; t < h.list[d].size(); ++t) h.code[d][HermiteIndex::key(d, h.list[d][t].a)] = (int)t;
+            x.code[d].assign(n, -1);
+            for (size_t t = 0; t < x.list[d].size(); ++t) x.code[d][HermiteIndex::key(d, x.list[d][t].a)] = (int)t;
         }
-        init = true;
-    }
+        return x;
+    }();
     return h;
 }
 
@@ -426,18 +426,26 @@ static const int kRadices[] = {32, 30, 27, 25, 24, 20, 18, 16, 15, 12, 10, 9, 8,
 // fewest stages factoring P into allowed radices (cached per (P, max radix))
 static bool radix_plan_uncached(int P, AxisPlan& ap, int max_radix);
 static bool radix_plan(int P, AxisPlan& ap, int max_radix) {
+    // shared by every context of the process, so guarded for contexts used
+    // from several host threads
+    static std::mutex mu;
     static std::map<std::pair<int, int>, std::pair<bool, AxisPlan>> cache;
     const auto key = std::make_pair(P, max_radix);
-    auto it = cache.find(key);
-    if (it == cache.end()) {
-        AxisPlan a{};
-        const bool ok = radix_plan_uncached(P, a, max_radix);
-        it = cache.emplace(key, std::make_pair(ok, a)).first;
+    std::pair<bool, AxisPlan> hit;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            AxisPlan a{};
+            const bool ok = radix_plan_uncached(P, a, max_radix);
+            it = cache.emplace(key, std::make_pair(ok, a)).first;
+        }
+        hit = it->second;
     }
     const int tw_off = ap.tw_off;
-    ap = it->second.second;
+    ap = hit.second;
     ap.tw_off = tw_off;
-    return it->second.first;
+    return hit.first;
 }
 
 static bool radix_plan_uncached(int P, AxisPlan& ap, int max_radix) {
@@ -561,6 +569,10 @@ struct kdefft_ctx_s {
     bool autotune = false;
     std::map<std::array<long long, 5>, Knobs> tuned;
     int64_t keys_tuned = 0;
+    // caller's record of the device-resident searches' own evaluations
+    double* rec = nullptr;
+    int64_t rec_len = 0;
+    int rec_cap = 0;
 };
 
 #include <chrono>
@@ -2571,6 +2583,7 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
     }
     int r = upload_tables();
     if (r == KDEFFT_OK && prepare_binning() != cudaSuccess) r = fail(KDEFFT_ERR_CUDA, "binning kernel attributes");
+    if (r == KDEFFT_OK && prepare_kernels() != cudaSuccess) r = fail(KDEFFT_ERR_CUDA, "kernel shared-memory attributes");
     if (r != KDEFFT_OK) {
         delete c;
         return r;
@@ -2637,6 +2650,28 @@ int kdefft_set_autotune(kdefft_ctx c, int on) {
 int kdefft_set_graphs(kdefft_ctx c, int on) {
     if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
     c->graphs = (on != 0);
+    return KDEFFT_OK;
+}
+
+int kdefft_set_search_record(kdefft_ctx c, double* rec, int64_t rec_len, int cap) {
+    if (!c) return fail(KDEFFT_ERR_ARG, "NULL context");
+    if (!rec) {
+        c->rec = nullptr;
+        c->rec_len = 0;
+        c->rec_cap = 0;
+        return KDEFFT_OK;
+    }
+    if (cap < 1 || rec_len < (int64_t)cap * SEL_REC) return fail(KDEFFT_ERR_ARG, "record buffer too small for one start");
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, rec) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KDEFFT_ERR_ARG, "record buffer is not device memory");
+    }
+    if (a.type != cudaMemoryTypeDevice || a.device != c->device)
+        return fail(KDEFFT_ERR_ARG, "record buffer is not device memory of the context's GPU");
+    c->rec = rec;
+    c->rec_len = rec_len;
+    c->rec_cap = cap;
     return KDEFFT_OK;
 }
 
@@ -3836,8 +3871,12 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
         q.acorr = (const float*)ds->ac32.p;
         q.A0 = ds->acA[0];
         q.A1 = ds->acA[1];
+        q.rec = c->rec;
+        q.rec_cap = c->rec_cap;
     }
     if (nm == 1) prm[1] = prm[0];
+    if (c->rec && (int64_t)nst * c->rec_cap * SEL_REC > c->rec_len)
+        return fail(KDEFFT_ERR_ARG, "search record buffer smaller than starts x cap x fields");
     cudaEvent_t ev = prof_start(c);
     KCU(launch_select2d_lag(prm[0], prm[1], first[1], dst, nst, c->stream));
     prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
@@ -4041,6 +4080,10 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     prm.ptab1 = (const int*)(db + oP) + (Lcap + 1);
     prm.specs = (const SelSpec*)db;
     prm.errflag = c->errflag;
+    prm.rec = c->rec;
+    prm.rec_cap = c->rec_cap;
+    if (c->rec && (int64_t)nst * c->rec_cap * SEL_REC > c->rec_len)
+        return fail(KDEFFT_ERR_ARG, "search record buffer smaller than starts x cap x fields");
     cudaEvent_t ev = prof_start(c);
     cudaError_t le = launch_select2d(prm, (SelStart*)(db + oT), nst, (const float2*)c->tw32.p, c->stream);
     if (le == cudaErrorNotSupported) return KDEFFT_ERR_UNSUPPORTED;

@@ -719,12 +719,6 @@ cudaError_t acorr_plan(AcorrJob* jobs_h, int n, long long* blocks_out, size_t* s
 cudaError_t launch_acorr(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const double2* twpool,
                          cudaStream_t st) {
     if (n <= 0 || blocks <= 0) return cudaSuccess;
-    static size_t set = 48 * 1024;
-    if (sm > set) {
-        cudaError_t e = cudaFuncSetAttribute(k_acorr_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        set = sm;
-    }
     k_acorr_fft<<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, twpool);
     return cudaGetLastError();
 }
@@ -1284,7 +1278,7 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
 // (FP32 algebra; the value is the FP32 pair sum of the device sum r[0] and
 // the closed-form term; r[1..3]: the sums of the three derivative grids)
 __device__ void sel_assemble(const SelectParams& p, const float* H, const float* Rm, const DFloat* r, float det,
-                             DFloat* f, float* gt) {
+                             DFloat* f, float* gt, float* gH = nullptr) {
     const float rdet = __frcp_rn(det);
     const float rsd = rsqrtf(det);   // |H|^-1/2
     const float rn = p.inv_nf;
@@ -1304,6 +1298,11 @@ __device__ void sel_assemble(const SelectParams& p, const float* H, const float*
         g00 = r1 + (-0.5f * rk * hi00) * rn;
         g01 = r2 + 2.f * (-0.5f * rk * hi01) * rn;
         g11 = r3 + (-0.5f * rk * hi11) * rn;
+    }
+    if (gH) {
+        gH[0] = g00;
+        gH[1] = g01;
+        gH[2] = g11;
     }
     // dF/dR = 2 G_ind R (G_ind off-diagonal = g01 / 2), chain rule to theta
     const float G00 = g00, G01 = 0.5f * g01, G11 = g11;
@@ -1436,6 +1435,26 @@ __device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) 
     }
 }
 
+// One evaluation of the search into the caller's record (thread 0; only
+// when recording is on and the start has slots left).
+__device__ __forceinline__ void sel_record(const SelectParams& p, int start, int e, const float* H, int L0, int L1,
+                                          DFloat f, const float* gH) {
+    if (!p.rec || e >= p.rec_cap) return;
+    double* r = p.rec + ((size_t)start * p.rec_cap + e) * SEL_REC;
+    r[0] = start;
+    r[1] = e;
+    r[2] = p.method;
+    r[3] = H[0];
+    r[4] = H[1];
+    r[5] = H[3];
+    r[6] = L0;
+    r[7] = L1;
+    r[8] = (double)f.h + (double)f.l;
+    r[9] = gH[0];
+    r[10] = gH[1];
+    r[11] = gH[2];
+}
+
 __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __restrict__ starts,
                                                   const float2* __restrict__ twpool) {
     using C = float2;
@@ -1499,7 +1518,9 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
                     const float h = (float)rv[e];
                     r[e] = DFloat{h, (float)(rv[e] - (double)h)};
                 }
-                sel_assemble(p, Hs, Rs, r, aux[0], &fn, gt);
+                float gH[3];
+                sel_assemble(p, Hs, Rs, r, aux[0], &fn, gt, gH);
+                if (rank == 0) sel_record(p, start, opt.evals, Hs, items[0].off0, items[0].off1, fn, gH);
                 opt.evals++;
                 opt.flops += (double)aux[1];
                 opt.bytes += (double)aux[2];
@@ -1667,7 +1688,9 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
             DFloat fn{INFINITY, 0.f};
             float gt[3] = {0.f, 0.f, 0.f};
             if (valid) {
-                sel_assemble(p, Hs, Rs, res, aux[0], &fn, gt);
+                float gH[3];
+                sel_assemble(p, Hs, Rs, res, aux[0], &fn, gt, gH);
+                sel_record(p, start, opt.evals, Hs, items[0].off0, items[0].off1, fn, gH);
                 opt.evals++;
                 opt.pts += (long long)aux[1];
             }
@@ -1719,18 +1742,11 @@ __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelectPar
 cudaError_t launch_select2d_lag(const SelectParams& prm, const SelectParams& prm2, int nfirst, SelStart* starts,
                                 int nstarts, cudaStream_t st) {
     // dynamic shared memory for the staged box: up to `limit` on top of the
-    // kernel's static shared memory (the attribute is set once, before any
-    // launch, so that no box size falls between the default limit and it)
+    // kernel's static shared memory (within the limit prepare_kernels set)
     const size_t box = sizeof(float) * (size_t)(prm.A0 + 1) * (size_t)(2 * prm.A1 + 1);
     const size_t limit = 200 * 1024;
     const int stage = box <= limit ? 1 : 0;
     const size_t sm = stage ? box : 0;
-    static bool set = false;
-    if (!set) {
-        cudaError_t e = cudaFuncSetAttribute(k_select2d_lag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
-        if (e != cudaSuccess) return e;
-        set = true;
-    }
     k_select2d_lag<<<nstarts, 1024, sm, st>>>(prm, prm2, nfirst, starts, stage);
     return cudaGetLastError();
 }
@@ -1743,14 +1759,6 @@ static size_t select2d_smem(const SelectParams& prm) {
 static cudaError_t select2d_config(const SelectParams& prm, int nstarts, cudaStream_t st, cudaLaunchConfig_t& cfg,
                                    cudaLaunchAttribute* attr) {
     const size_t sm = select2d_smem(prm);
-    static size_t set_bytes = 0;
-    if (sm > set_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_select2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_select2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        set_bytes = sm;
-    }
     cfg = cudaLaunchConfig_t{};
     cfg.gridDim = dim3((unsigned)(nstarts * prm.cs), 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -1790,8 +1798,6 @@ cudaError_t launch_stage_a(const Item<real>* items, const Tile* tiles, int ntile
                            typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, double* partial,
                            int grid, cudaStream_t st) {
     const size_t sm = smem_bytes<real>(cap, pmax);
-    cudaError_t e = cudaFuncSetAttribute(k_stage_a<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     k_stage_a<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, cap, scratch, twpool, partial);
     return cudaGetLastError();
 }
@@ -1801,8 +1807,6 @@ cudaError_t launch_mid(const Item<real>* items, const Tile* tiles, int ntiles, i
                        typename Cpx<real>::T* scratch, const typename Cpx<real>::T* twpool, int grid,
                        cudaStream_t st) {
     const size_t sm = smem_bytes<real>(cap, pmax);
-    cudaError_t e = cudaFuncSetAttribute(k_mid<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     k_mid<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, axis, cap, scratch, twpool);
     return cudaGetLastError();
 }
@@ -1813,8 +1817,6 @@ cudaError_t launch_final(const Item<real>* items, const Tile* tiles, int ntiles,
                          int grid, cudaStream_t st) {
     // ping-pong buffers, twiddles, then the staged spectrum rows (cap reals)
     const size_t sm = smem_bytes<real>(cap, pmax) + sizeof(real) * (size_t)cap;
-    cudaError_t e = cudaFuncSetAttribute(k_final<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     k_final<real><<<grid, 256, sm, st>>>(items, tiles, ntiles, cap, scratch, twpool, partial);
     return cudaGetLastError();
 }
@@ -1835,14 +1837,6 @@ static cudaError_t launch_fused2d_r(const FusedItem<real>* items, int nitems, in
     // spectrum rows are real; keep the complex buffers after them 16-byte aligned
     const int spc_pad = (spc_elems + 3) & ~3;
     const size_t sm = sizeof(C) * (size_t)(gat_elems + 2 * pmax + 2 * padded_cap(cap)) + sizeof(real) * (size_t)spc_pad;
-    static size_t set_bytes = 0;
-    if (sm > set_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused2d<real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_fused2d<real, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        set_bytes = sm;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nitems * cs), 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -1883,6 +1877,39 @@ cudaError_t launch_fused2d(const FusedItem<real>* items, int nitems, int rmax, i
     if (rmax <= 4 && sizeof(real) == 4)
         return launch_fused2d_r<real, 4>(items, nitems, cs, gat_elems, spc_elems, cap, pmax, twpool, out, errflag, st);
     return cudaErrorNotSupported;
+}
+
+// Every kernel that may take more than the default 48 KB of dynamic shared
+// memory gets the device's opt-in maximum (less its static shared memory),
+// and the cluster kernels may use non-portable cluster sizes.  Set once per
+// device before any launch -- at context creation and by the first
+// allocation-free call -- so that no launch sets (or could lower) a limit
+// another thread's launch relies on.  Idempotent.
+cudaError_t prepare_kernels() {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    auto raise = [&](const void* f) -> cudaError_t {
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, f);
+        if (r != cudaSuccess) return r;
+        return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    };
+    const void* dyn[] = {(const void*)k_stage_a<float>,    (const void*)k_stage_a<double>,
+                         (const void*)k_mid<float>,        (const void*)k_mid<double>,
+                         (const void*)k_final<float>,      (const void*)k_final<double>,
+                         (const void*)k_acorr_fft,         (const void*)k_select2d_lag,
+                         (const void*)k_select2d,          (const void*)k_fused2d<float, 2>,
+                         (const void*)k_fused2d<float, 4>, (const void*)k_fused2d<double, 2>};
+    for (const void* f : dyn)
+        if ((e = raise(f)) != cudaSuccess) return e;
+    const void* clu[] = {(const void*)k_select2d, (const void*)k_fused2d<float, 2>, (const void*)k_fused2d<float, 4>,
+                         (const void*)k_fused2d<double, 2>};
+    for (const void* f : clu)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 #define KDEFFT_INST(real)                                                                                       \

@@ -182,7 +182,15 @@ struct SelectParams {
     // box [j_1 + A1][j_0], j_0 in [0, A0]; null for the FFT route
     const float* acorr;
     int A0, A1;
+    // optional record of the search's own evaluations (null: off): for CTA
+    // (start) s, evaluation e < rec_cap goes to rec + (s rec_cap + e) SEL_REC
+    double* rec;
+    int rec_cap;
 };
+// fields of one recorded evaluation: start, evaluation index, method, H_00,
+// H_01, H_11 (the FP32 values evaluated), L_0, L_1, value, dF/dH_00,
+// dF/dH_01 (tied), dF/dH_11
+constexpr int SEL_REC = 12;
 cudaError_t launch_select2d(const SelectParams& prm, SelStart* starts, int nstarts,
                             const float2* twpool, cudaStream_t st);
 // the same search in the lag domain: one CTA per start (prm.acorr set).
@@ -192,6 +200,9 @@ cudaError_t launch_select2d_lag(const SelectParams& prm, const SelectParams& prm
                                 int nstarts, cudaStream_t st);
 
 cudaError_t upload_hermite_tables(const HEnt* tab, const int* offsets, int total);
+// raise the dynamic shared-memory limits (and cluster permissions) of the
+// engine's kernels on the current device; once per device, before launches
+cudaError_t prepare_kernels();
 
 // ---- lag-domain engine (lag.cu)
 // Eq. 25 summed over the lag first: n^-2 sum_i sum_j c_i c_j k(i - j) =

@@ -250,8 +250,9 @@ __global__ void k_na_epilogue(const double* __restrict__ raw, int ngrid, double 
     (void)ngrid;
 }
 
-// one-time set-up for the current device: the scratch address and the
-// Hermite tables in constant memory
+// one-time set-up for the current device: the scratch address, the
+// Hermite tables in constant memory and the kernels' shared-memory limits
+// (raised once, so that no call sets them)
 int na_setup(int dev, unsigned char** base) {
     if (dev < 0 || dev >= kNaMaxDevices) return na_fail(KDEFFT_ERR_UNSUPPORTED, "device index too large");
     if (!g_na_ptr[dev]) {
@@ -262,6 +263,7 @@ int na_setup(int dev, unsigned char** base) {
         const int n = build_table(h_htab, offs);
         if (upload_hermite_tables(h_htab, offs, n) != cudaSuccess)
             return na_fail(KDEFFT_ERR_CUDA, "Hermite table upload failed");
+        if (prepare_kernels() != cudaSuccess) return na_fail(KDEFFT_ERR_CUDA, "kernel attributes failed");
         g_na_ptr[dev] = (unsigned char*)p;
     }
     *base = g_na_ptr[dev];
@@ -279,17 +281,28 @@ extern "C" int kdefft_lscv_noalloc(int d, const int64_t* M, const double* delta,
     if (d < 1 || d > 3 || !M || !delta || !counts || !H || !out || n < 2 || !(tau > 0.0))
         return na_fail(KDEFFT_ERR_ARG, "bad argument (d must be 1..3, n >= 2, tau > 0, non-null arrays)");
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        // The small tables go up from host staging that the next call
+        // overwrites; a captured copy would replay whatever a later call left
+        // there.  So the call does nothing while its stream is being captured.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return na_fail(KDEFFT_ERR_UNSUPPORTED, "the stream is being captured");
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(KDEFFT_ERR_CUDA, "no current CUDA device");
     {
+        // both buffers must be device memory of the current device: a peer
+        // device's buffer would be read without peer access
         cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+        if (cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeDevice || a.device != dev) {
             cudaGetLastError();
-            return na_fail(KDEFFT_ERR_ARG, "out must be device memory");
+            return na_fail(KDEFFT_ERR_ARG, "out must be device memory of the current device");
         }
-        if (cudaPointerGetAttributes(&a, counts) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+        if (cudaPointerGetAttributes(&a, counts) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
+            a.device != dev) {
             cudaGetLastError();
-            return na_fail(KDEFFT_ERR_ARG, "counts must be device memory");
+            return na_fail(KDEFFT_ERR_ARG, "counts must be device memory of the current device");
         }
     }
     unsigned char* base = nullptr;

@@ -1,6 +1,6 @@
 """The oracle and the CUDA path stay independent (CPU, by reading the code):
 no module of the package imports the oracle, the oracle imports neither the
-package nor torch nor ctypes, bench.py and the smoke check reach the oracle
+package nor torch nor ctypes (only numpy, scipy's FFT and the standard library), bench.py and the smoke check reach the oracle
 only inside the functions allowed to run it, and the binding refuses to run
 without the compiled library (no CPU fallback)."""
 import ast
@@ -51,7 +51,8 @@ def test_package_never_imports_the_oracle():
 
 
 def test_oracle_imports_only_the_standard_library_and_numpy():
-    allowed = {"numpy", "math", "itertools", "__future__", "functools", "typing"}
+    # scipy for its FFT only (pocketfft on every host core, the FP64 FFT tier of the oracle)
+    allowed = {"numpy", "scipy", "math", "itertools", "__future__", "functools", "typing"}
     for p in _py_files(ORACLE):
         for mod, _ in _imports(p):
             if mod.startswith("."):

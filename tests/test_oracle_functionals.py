@@ -273,6 +273,32 @@ def test_autocorrelation_pins(d, M):
     assert tot / 300.0 ** 2 == pytest.approx(F.binned_direct(c, 300, terms, delta, L), rel=1e-12)
 
 
+@pytest.mark.parametrize("d,M", [(1, [13]), (2, [9, 12]), (3, [5, 6, 4])])
+def test_fft_autocorrelation_and_lag_sums(d, M):
+    """The FFT autocorrelation equals the direct lag overlaps on every lag of
+    the half box, and the lag-first sum equals Eq. 25's double sum; the
+    absolute functional equals the double sum of |k|."""
+    X, c, delta = _binned_case(d, M, n=250, seed=40 + d)
+    a = F.autocorr_fft(c)
+    A = [m - 1 for m in M]
+    ref = F.autocorr(c, A)
+    for idx in np.ndindex(*ref.shape):
+        j = [idx[-1]] + [idx[d - 1 - k] - A[k] for k in range(1, d)]
+        got = a[tuple(jj % a.shape[k] for k, jj in enumerate(j))]
+        assert got == pytest.approx(ref[idx], rel=1e-12, abs=1e-9 * ref.max())
+    rng = np.random.default_rng(d)
+    H = _spd(rng, d, 0.5)
+    L = [min(m - 1, 3 + k) for k, m in enumerate(M)]
+    terms = [(1.0, H, (0,) * d), (-0.7, 2.0 * H, tuple([2] + [0] * (d - 1)))]
+    v, s_abs = F.lag_sums(a, 250, terms, delta, L)
+    assert v == pytest.approx(F.binned_direct(c, 250, terms, delta, L), rel=1e-11)
+    k = F.lag_kernel(terms, delta, L)
+    want = 0.0
+    for j in itertools.product(*[range(-l, l + 1) for l in L]):
+        want += abs(k[tuple(jj + l for jj, l in zip(j, L))]) * F._overlap(c, j)
+    assert s_abs == pytest.approx(want / 250.0 ** 2, rel=1e-11)
+
+
 def test_binned_equals_direct_on_nodes():
     """All points on nodes and L = M - 1: binned sum = direct sum."""
     rng = np.random.default_rng(2)
