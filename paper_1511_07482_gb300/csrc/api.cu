@@ -3773,6 +3773,25 @@ static void params_f32(SelectParams& q) {
     q.d0f = (float)q.delta0;
     q.d1f = (float)q.delta1;
     for (int e = 0; e < 4; ++e) q.Gf[e] = (float)q.G[e];
+    // the pilot's Gaussian phi_{2G}, the base of the SCV kernel's
+    // cancellation-free form (zero for LSCV, whose G is zero)
+    const double g00 = 2.0 * q.G[0], g01 = 2.0 * 0.5 * (q.G[1] + q.G[2]), g11 = 2.0 * q.G[3];
+    const double det = g00 * g11 - g01 * g01;
+    const double d0 = q.delta0, d1 = q.delta1;
+    auto pair = [](double v, float& h, float& l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    const double L[3] = {det > 0.0 ? g11 / det : 0.0, det > 0.0 ? -g01 / det : 0.0, det > 0.0 ? g00 / det : 0.0};
+    const double dd[3] = {d0 * d0, d0 * d1, d1 * d1};
+    for (int e = 0; e < 3; ++e) {
+        pair(L[e], q.l2gh[e], q.l2gl[e]);
+        pair(dd[e], q.ddh[e], q.ddl[e]);
+        q.l2gj[e] = (float)(dd[e] * L[e]);
+        q.gsc[e] = (float)(1.0 / dd[e]);
+    }
+    pair(det > 0.0 ? 1.0 / det : 0.0, q.dl2gh, q.dl2gl);
+    q.n2g = det > 0.0 ? (float)(1.0 / (2.0 * M_PI * std::sqrt(det))) : 0.f;
 }
 
 // Whether the device-resident search covers a criterion on this dataset:

@@ -24,6 +24,26 @@ __device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
     const float h = s.h + e;
     return {h, e - (h - s.h)};
 }
+// a b for FP32 a, b as an unevaluated pair: exact (the fused multiply-add
+// gives the product's rounding error)
+__device__ __forceinline__ DFloat df_prod(float a, float b) {
+    const float p = a * b;
+    return DFloat{p, fmaf(a, b, -p)};
+}
+// (a.h + a.l)(b.h + b.l) to a few units of 2^-44 relative
+__device__ __forceinline__ DFloat df_mul(DFloat a, DFloat b) {
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+    const float s = p + e;
+    return DFloat{s, e - (s - p)};
+}
+// (a.h + a.l) b for an FP32 b
+__device__ __forceinline__ DFloat df_mulf(DFloat a, float b) {
+    const float p = a.h * b;
+    const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+    const float s = p + e;
+    return DFloat{s, e - (s - p)};
+}
 __device__ __forceinline__ void df_acc(DFloat& a, float x) {
     const DFloat s = df_two_sum(a.h, x);
     const float e = s.l + a.l;

@@ -949,57 +949,81 @@ __global__ void __launch_bounds__(256) k_fused2d(const FusedItem<real>* __restri
 // and gradient and applies the line search / BFGS update that the host
 // optimiser uses.  Every loop is bounded.
 
-// the four grids of both packed pairs at lag (j0, j1): item 1 carries only
-// its weights (covariances are those of item 0)
-__device__ __forceinline__ void kernel_quad_2d(const FusedItem<float>& f, const FusedItem<float>& g, int j0, int j1,
-                                               float* v) {
-    constexpr HTab<2, 2> ht{};
-    constexpr int N = HTab<2, 2>::N;
-    const float x0 = (float)f.delta0 * (float)j0, x1 = (float)f.delta1 * (float)j1;
-    float a0 = 0, b0 = 0, a1 = 0, b1 = 0;
+// The four grids of the search at lag x = (delta_0 j_0, delta_1 j_1): the
+// objective's kernel and its derivatives in H_00, H_01 (tied), H_11, from
+// the Gaussians of the covariances Sigma_s (LSCV: 2H, H; SCV: 2H + 2G,
+// H + 2G, 2G) and the order-2 Hermite terms He_(2,0) = z_0^2 - L_00,
+// He_(1,1) = z_0 z_1 - L_01, He_(0,2) = z_1^2 - L_11, z = L x (heat
+// equation: d phi_S / dS_ab = 1/2 d_a d_b phi_S).  For LSCV, Sigma_1 =
+// Sigma_0 / 2, so L_1 = 2 L_0, z_1 = 2 z_0 and phi_H's exponent is twice
+// phi_2H's: one exponential serves both.
+//
+// The SCV kernel phi_{2H+2G} - 2 phi_{H+2G} + phi_{2G} integrates to zero
+// and is far smaller than its terms (the pilot smooths all three alike), so
+// rounding each Gaussian on its own would leave errors of the terms' size.
+// It is evaluated as phi_{2G} (m_0 - 2 m_1), where
+//   m_s = phi_{Sigma_s} / phi_{2G} - 1 = rho_s expm1(-q_s / 2) + (rho_s - 1)
+// and q_s = j^T D_s j is the exponent difference in lag-index coordinates:
+// the products of j are exact, and D_s, rho_s and rho_s - 1 carry FP32
+// remainders (sel_prepare), so the per-bandwidth constants add no
+// systematic error, and m_0, 2 m_1 share only their first-order parts.  The
+// gradient grids are formed in the same coordinates (Hermite terms
+// Z_a Z_b - L~_ab with Z = L~ j, L~ = Delta Sigma^-1 Delta), which is
+// delta_a delta_b times their value; the assembly divides it out.
+template <int METHOD>
+__device__ __forceinline__ void sel_grids(const FusedItem<float>& f, int j0i, int j1i, float d0, float d1, float* v) {
+    if constexpr (METHOD == 0) {
+        const float x0 = d0 * (float)j0i, x1 = d1 * (float)j1i;
+        const float a00 = f.laml[0][0], a01 = f.laml[0][1], a11 = f.laml[0][3];
+        const float z0 = fmaf(a00, x0, a01 * x1), z1 = fmaf(a01, x0, a11 * x1);
+        const float q0 = fmaf(x0, z0, x1 * z1);
+        const float u = expf(-0.5f * q0);
+        const float e0 = f.nrm[0] * u;
+        const float h3 = fmaf(z0, z0, -a00), h4 = fmaf(z0, z1, -a01), h5 = fmaf(z1, z1, -a11);
+        const float e1 = f.nrm[1] * (u * u);
+        const float g3 = fmaf(4.f * z0, z0, -2.f * a00), g4 = fmaf(4.f * z0, z1, -2.f * a01),
+                    g5 = fmaf(4.f * z1, z1, -2.f * a11);
+        v[0] = fmaf(-2.f, e1, e0);
+        v[1] = fmaf(e0, h3, -e1 * g3);
+        v[2] = 2.f * fmaf(e0, h4, -e1 * g4);
+        v[3] = fmaf(e0, h5, -e1 * g5);
+    } else {
+        const float j0 = (float)j0i, j1 = (float)j1i;
+        const float c00 = f.laml[2][0], c01 = f.laml[2][1], c11 = f.laml[2][3];
+        const float w0 = fmaf(c00, j0, c01 * j1), w1 = fmaf(c01, j0, c11 * j1);
+        const float e2 = f.nrm[2] * expf(-0.5f * fmaf(j0, w0, j1 * w1));
+        float m[2], Z[2][2];
 #pragma unroll
-    for (int s = 0; s < MAXSIG; ++s) {
-        if (s < f.nsig) {
-            const float z0 = f.laml[s][0] * x0 + f.laml[s][1] * x1;
-            const float z1 = f.laml[s][2] * x0 + f.laml[s][3] * x1;
-            const float e = f.nrm[s] * expf(-0.5f * (x0 * z0 + x1 * z1));
-            float He[N];
-            He[0] = 1.f;
-#pragma unroll
-            for (int t = 1; t < N; ++t) {
-                float w = (ht.piv[t] == 0 ? z0 : z1) * He[ht.par[t]];
-#pragma unroll
-                for (int r = 0; r < 2; ++r)
-                    if (r < ht.nred[t]) w -= float(ht.rc[t][r]) * f.laml[s][ht.piv[t] * 2 + ht.rj[t][r]] * He[ht.ridx[t][r]];
-                He[t] = w;
-            }
-            float pa0 = 0, pb0 = 0, pa1 = 0, pb1 = 0;
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                pa0 += f.W[0][s][t] * He[t];
-                pb0 += f.W[1][s][t] * He[t];
-                pa1 += g.W[0][s][t] * He[t];
-                pb1 += g.W[1][s][t] * He[t];
-            }
-            a0 += e * pa0;
-            b0 += e * pb0;
-            a1 += e * pa1;
-            b1 += e * pb1;
+        for (int q = 0; q < 2; ++q) {
+            const float* D = f.xd[q];
+            const float p0 = fmaf(D[0], j0, D[1] * j1), p1 = fmaf(D[1], j0, D[2] * j1);
+            const float r0 = fmaf(D[3], j0, D[4] * j1), r1 = fmaf(D[4], j0, D[5] * j1);
+            const float qh = fmaf(j0, p0, j1 * p1), ql = fmaf(j0, r0, j1 * r1);
+            const float em = expm1f(-0.5f * qh);
+            const float em2 = fmaf(-0.5f * ql, 1.f + em, em);   // expm1(-(qh + ql) / 2)
+            m[q] = fmaf(D[6], em2, D[8]) + fmaf(D[7], em2, D[9]);
+            Z[q][0] = w0 + p0;
+            Z[q][1] = w1 + p1;
         }
+        v[0] = e2 * fmaf(-2.f, m[1], m[0]);
+        const float e0 = fmaf(e2, m[0], e2), e1 = fmaf(e2, m[1], e2);
+        const float a00 = f.laml[0][0], a01 = f.laml[0][1], a11 = f.laml[0][3];
+        const float b00 = f.laml[1][0], b01 = f.laml[1][1], b11 = f.laml[1][3];
+        v[1] = fmaf(e0, fmaf(Z[0][0], Z[0][0], -a00), -e1 * fmaf(Z[1][0], Z[1][0], -b00));
+        v[2] = 2.f * fmaf(e0, fmaf(Z[0][0], Z[0][1], -a01), -e1 * fmaf(Z[1][0], Z[1][1], -b01));
+        v[3] = fmaf(e0, fmaf(Z[0][1], Z[0][1], -a11), -e1 * fmaf(Z[1][1], Z[1][1], -b11));
     }
-    v[0] = a0;
-    v[1] = b0;
-    v[2] = a1;
-    v[3] = b1;
 }
 
-// Both packed pairs of one bandwidth (same H, L, P and spectrum, different
-// weights) evaluated together by the cluster: lines and columns of the two
-// pairs share every barrier, the twiddles, the staged spectrum rows and the
-// reduction.  gat holds 2 x S_0 x cpc values (pair-major).  res4 (rank 0):
-// the four scaled sums (pair 0 grids A, B; pair 1 grids A, B).
-__device__ __forceinline__ void sel_eval2(cg::cluster_group& cluster, const FusedItem<float>& f,
-                                          const FusedItem<float>& g2, int cs, int rank, int chunk, float2* gat,
+// The four grids of one bandwidth (sel_grids: value and the three
+// derivative grids, packed as two complex pairs) evaluated together by the
+// cluster: lines and columns of the two pairs share every barrier, the
+// twiddles, the staged spectrum rows and the reduction.  gat holds
+// 2 x S_0 x cpc values (pair-major).  res4 (rank 0): the four scaled sums
+// (pair 0 grids A, B; pair 1 grids A, B).
+template <int METHOD>
+__device__ __forceinline__ void sel_eval2(cg::cluster_group& cluster, const FusedItem<float>& f, int cs, int rank,
+                                          int chunk, float2* gat,
                                           float* spc, float2* tw1, float2* tw0, float2* bufa, float2* bufb,
                                           const float2* twpool, double* cl_red, double* res4) {
     using C = float2;
@@ -1029,7 +1053,7 @@ __device__ __forceinline__ void sel_eval2(cg::cluster_group& cluster, const Fuse
             int idx = p + off1;
             if (idx >= P1) idx -= P1;
             float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (idx < S1) kernel_quad_2d(f, g2, l0 + c0 + c - off0, idx - off1, v);
+            if (idx < S1) sel_grids<METHOD>(f, l0 + c0 + c - off0, idx - off1, (float)f.delta0, (float)f.delta1, v);
             bufa[pad(t)] = C{v[0], v[1]};
             bufa[pad(t + nc * P1)] = C{v[2], v[3]};
         }
@@ -1168,13 +1192,74 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
     const float G[4] = {p.Gf[0], p.Gf[1], p.Gf[2], p.Gf[3]};
     const int sl = lane < nsig ? lane : 0;
     const float hco = (sl == 0) ? 2.f : (sl == 1 ? 1.f : 0.f);
-    float Ss[4];
+    float iv0, iv1, iv3, nr;
+    float xdv[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (p.method == 0) {
+        float Ss[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) Ss[e] = fmaf(hco, H[e], gco * G[e]);
-    const float dts = det2(Ss[0], Ss[1], Ss[3]);
-    const float rdt = __frcp_rn(dts);
-    const float iv0 = Ss[3] * rdt, iv1 = -Ss[1] * rdt, iv3 = Ss[0] * rdt;
-    const float nr = 0.15915494f * rsqrtf(dts);   // 1 / (2 pi sqrt(det))
+        for (int e = 0; e < 4; ++e) Ss[e] = hco * H[e];
+        const float dts = det2(Ss[0], Ss[1], Ss[3]);
+        const float rdt = __frcp_rn(dts);
+        iv0 = Ss[3] * rdt;
+        iv1 = -Ss[1] * rdt;
+        iv3 = Ss[0] * rdt;
+        nr = 0.15915494f * rsqrtf(dts);   // 1 / (2 pi sqrt(det))
+    } else {
+        // SCV: the kernel is evaluated relative to phi_{2G} (sel_grids), from
+        // the exponent difference D_s and normaliser ratio rho_s of each
+        // H-dependent Gaussian, which must be accurate well beyond FP32
+        // because the kernel is much smaller than its terms.  With
+        // Sigma_s = 2G + h_s H = 2G (I + h_s B), B = (2G)^-1 H, and the 2 x 2
+        // identities det(I + h B) = 1 + h tr B + h^2 det B and
+        // (I + h B)^-1 h B = (h B + h^2 det B I) / det(I + h B):
+        //   Sigma_s^-1 - (2G)^-1 = -(h_s P + h_s^2 det(B) (2G)^-1) rho_s^2,
+        //   rho_s = |Sigma_s|^-1/2 |2G|^1/2 = (1 + h_s tr B + h_s^2 det B)^-1/2,
+        // P = (2G)^-1 H (2G)^-1: no difference of nearby values.  Lanes 0 and 1
+        // (s = 0, 1) take it in FP32-pair arithmetic (about 44 bits) from the
+        // FP32 trial H, which is exact there, with rho from an FP32 rsqrt and
+        // one Newton step; lane 2 holds phi_{2G}.  No FP64 instruction: that
+        // pipe is narrow on this part.  Entries in lag-index coordinates.
+        iv0 = p.l2gj[0];
+        iv1 = p.l2gj[1];
+        iv3 = p.l2gj[2];
+        nr = p.n2g;
+        if (lane < 2) {
+            const float hs = (lane == 0) ? 2.f : 1.f;
+            const float h00 = H[0], h01 = H[1], h11 = H[3];
+            const DFloat L00{p.l2gh[0], p.l2gl[0]}, L01{p.l2gh[1], p.l2gl[1]}, L11{p.l2gh[2], p.l2gl[2]};
+            const DFloat m00 = df_add(df_mulf(L00, h00), df_mulf(L01, h01));
+            const DFloat m01 = df_add(df_mulf(L00, h01), df_mulf(L01, h11));
+            const DFloat m10 = df_add(df_mulf(L01, h00), df_mulf(L11, h01));
+            const DFloat m11 = df_add(df_mulf(L01, h01), df_mulf(L11, h11));
+            const DFloat P[3] = {df_add(df_mul(m00, L00), df_mul(m01, L01)), df_add(df_mul(m00, L01), df_mul(m01, L11)),
+                                 df_add(df_mul(m10, L01), df_mul(m11, L11))};
+            const DFloat q01 = df_prod(h01, h01);
+            const DFloat detH = df_add(df_prod(h00, h11), DFloat{-q01.h, -q01.l});
+            const DFloat hh = df_mulf(df_mul(DFloat{p.dl2gh, p.dl2gl}, detH), hs * hs);   // h_s^2 det B
+            const DFloat xg = df_add(df_add(df_mulf(df_add(m00, m11), hs), hh), DFloat{1.f, 0.f});
+            // rho = xg^-1/2: y + y (1 - xg y^2) / 2 from the FP32 estimate y
+            const float y = rsqrtf(xg.h);
+            const DFloat xy2 = df_mul(xg, df_prod(y, y));
+            const DFloat rho = df_two_sum(y, 0.5f * y * ((1.f - xy2.h) - xy2.l));
+            const DFloat r2 = df_mul(rho, rho);
+            const DFloat Ls[3] = {L00, L01, L11};
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const DFloat num = df_add(df_mulf(P[e], hs), df_mul(hh, Ls[e]));
+                const DFloat De = df_mul(df_mul(num, r2), DFloat{p.ddh[e], p.ddl[e]});
+                xdv[e] = -De.h;
+                xdv[3 + e] = -De.l;
+            }
+            const DFloat rm1 = df_add(rho, DFloat{-1.f, 0.f});
+            xdv[6] = rho.h;
+            xdv[7] = rho.l;
+            xdv[8] = rm1.h;
+            xdv[9] = rm1.l;
+            iv0 += xdv[0];
+            iv1 += xdv[1];
+            iv3 += xdv[2];
+        }
+    }
     // supports from lambda_max of H (LSCV, paper rule), 2H (LSCV widest) or 2H + 2G (SCV)
     const float bs = (p.method == 1 || p.widest) ? 2.f : 1.f;
     float B[4];
@@ -1214,6 +1299,9 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
 #pragma unroll
             for (int e = 0; e < 4; ++e) it[q].laml[lane][e] = iv[e];
             it[q].nrm[lane] = on ? nr : 0.f;
+            if (lane < 2)
+#pragma unroll
+                for (int e = 0; e < 12; ++e) it[q].xd[lane][e] = xdv[e];
         }
     }
     if (lane < 2) {
@@ -1237,25 +1325,8 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
             f.scale = sp.scale;
         }
     }
-    constexpr int NW = 2 * MAXSIG * WDENSE;
-    if (!p.acorr)   // the FFT route's generic evaluator reads dense weights; the lag route has them built in
-        for (int t = lane; t < 2 * NW; t += 32) {
-            const int q = t / NW, r = t - q * NW;
-            (&it[q].W[0][0][0])[r] = 0.f;
-        }
+    // (both routes evaluate the four grids with sel_grids: no dense weights)
     __syncwarp();
-    if (lane == 0 && !p.acorr) {
-        // Hermite indices (d = 2, graded): 0 -> (0,0), 3 -> (2,0), 4 -> (1,1), 5 -> (0,2)
-        it[0].W[0][0][0] = 1.f;
-        it[0].W[0][1][0] = -2.f;
-        if (p.method != 0) it[0].W[0][2][0] = 1.f;
-        it[0].W[1][0][3] = 1.f;   // d^2/dH00: s_00 = 1
-        it[0].W[1][1][3] = -1.f;
-        it[1].W[0][0][4] = 2.f;   // tied off-diagonal: s_01 = 2
-        it[1].W[0][1][4] = -2.f;
-        it[1].W[1][0][5] = 1.f;
-        it[1].W[1][1][5] = -1.f;
-    }
     if (lane == 0) {
         for (int e = 0; e < 4; ++e) Hs[e] = H[e];
         Rs[0] = r00;
@@ -1293,11 +1364,12 @@ __device__ void sel_assemble(const SelectParams& p, const float* H, const float*
         g01 = r2 + c0 * 2.f * (-0.5f * k0 * hi01);
         g11 = r3 + c0 * (-0.5f * k0 * hi11);
     } else {
+        // the derivative grids were summed in lag-index coordinates
         const float rk = 0.07957747f * rsd;   // (4 pi)^-1 |H|^-1/2
         *f = df_add(r[0], DFloat{rk * rn, 0.f});
-        g00 = r1 + (-0.5f * rk * hi00) * rn;
-        g01 = r2 + 2.f * (-0.5f * rk * hi01) * rn;
-        g11 = r3 + (-0.5f * rk * hi11) * rn;
+        g00 = fmaf(r1, p.gsc[0], (-0.5f * rk * hi00) * rn);
+        g01 = fmaf(r2, p.gsc[1], 2.f * (-0.5f * rk * hi01) * rn);
+        g11 = fmaf(r3, p.gsc[2], (-0.5f * rk * hi11) * rn);
     }
     if (gH) {
         gH[0] = g00;
@@ -1503,8 +1575,12 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
         const int valid = ctl[0], done = ctl[1];
         if (done) break;
         if (valid) {
-            sel_eval2(cluster, items[0], items[1], p.cs, rank, p.chunk, gat, spc, tw1, tw0, bufa, bufb, twpool, cl_red,
-                      &res[0][0]);
+            if (p.method == 0)
+                sel_eval2<0>(cluster, items[0], p.cs, rank, p.chunk, gat, spc, tw1, tw0, bufa, bufb, twpool,
+                             cl_red, &res[0][0]);
+            else
+                sel_eval2<1>(cluster, items[0], p.cs, rank, p.chunk, gat, spc, tw1, tw0, bufa, bufb, twpool,
+                             cl_red, &res[0][0]);
             __syncthreads();
         }
         if (threadIdx.x == 0) {
@@ -1541,44 +1617,6 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     }
 }
 
-// The four grids of the search at lag x = (delta_0 j_0, delta_1 j_1): the
-// objective's kernel and its derivatives in H_00, H_01 (tied), H_11, from
-// the Gaussians of the covariances Sigma_s (LSCV: 2H, H; SCV: 2H + 2G,
-// H + 2G, 2G) and the order-2 Hermite terms He_(2,0) = z_0^2 - L_00,
-// He_(1,1) = z_0 z_1 - L_01, He_(0,2) = z_1^2 - L_11, z = L x (heat
-// equation: d phi_S / dS_ab = 1/2 d_a d_b phi_S).  For LSCV, Sigma_1 =
-// Sigma_0 / 2, so L_1 = 2 L_0, z_1 = 2 z_0 and phi_H's exponent is twice
-// phi_2H's: one exponential serves both.
-template <int METHOD>
-__device__ __forceinline__ void sel_grids(const FusedItem<float>& f, float x0, float x1, float* v) {
-    const float a00 = f.laml[0][0], a01 = f.laml[0][1], a11 = f.laml[0][3];
-    const float z0 = fmaf(a00, x0, a01 * x1), z1 = fmaf(a01, x0, a11 * x1);
-    const float q0 = fmaf(x0, z0, x1 * z1);
-    const float u = expf(-0.5f * q0);
-    const float e0 = f.nrm[0] * u;
-    const float h3 = fmaf(z0, z0, -a00), h4 = fmaf(z0, z1, -a01), h5 = fmaf(z1, z1, -a11);
-    if constexpr (METHOD == 0) {
-        const float e1 = f.nrm[1] * (u * u);
-        const float g3 = fmaf(4.f * z0, z0, -2.f * a00), g4 = fmaf(4.f * z0, z1, -2.f * a01),
-                    g5 = fmaf(4.f * z1, z1, -2.f * a11);
-        v[0] = fmaf(-2.f, e1, e0);
-        v[1] = fmaf(e0, h3, -e1 * g3);
-        v[2] = 2.f * fmaf(e0, h4, -e1 * g4);
-        v[3] = fmaf(e0, h5, -e1 * g5);
-    } else {
-        const float b00 = f.laml[1][0], b01 = f.laml[1][1], b11 = f.laml[1][3];
-        const float y0 = fmaf(b00, x0, b01 * x1), y1 = fmaf(b01, x0, b11 * x1);
-        const float e1 = f.nrm[1] * expf(-0.5f * fmaf(x0, y0, x1 * y1));
-        const float c00 = f.laml[2][0], c01 = f.laml[2][1], c11 = f.laml[2][3];
-        const float w0 = fmaf(c00, x0, c01 * x1), w1 = fmaf(c01, x0, c11 * x1);
-        const float e2 = f.nrm[2] * expf(-0.5f * fmaf(x0, w0, x1 * w1));
-        v[0] = fmaf(-2.f, e1, e0 + e2);
-        v[1] = fmaf(e0, h3, -e1 * fmaf(y0, y0, -b00));
-        v[2] = 2.f * fmaf(e0, h4, -e1 * fmaf(y0, y1, -b01));
-        v[3] = fmaf(e0, h5, -e1 * fmaf(y1, y1, -b11));
-    }
-}
-
 // One bandwidth of the search in the lag domain by one CTA: the half box
 // j_0 in [0, L_0], |j_1| <= L_1 (j_0 fastest, so that neighbouring threads
 // read neighbouring a_j), weights 2 / 1 / 0, four compensated sums; thread 0
@@ -1603,7 +1641,7 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
         if (!wt) continue;
         const float av = acorr[(j1 + A1) * (A0 + 1) + j0];
         float v[4];
-        sel_grids<METHOD>(f, d0 * (float)j0, d1 * (float)j1, v);
+        sel_grids<METHOD>(f, j0, j1, d0, d1, v);
         const float wa = (float)wt * av;
 #pragma unroll
         for (int e = 0; e < 4; ++e) s4[e] = fmaf(wa, v[e], s4[e]);

@@ -123,6 +123,13 @@ struct FusedItem {
     real laml[MAXSIG][4];    // the same in the working type, for the Hermite recurrence
     real nrm[MAXSIG];
     real W[2][MAXSIG][WDENSE];
+    // device search, SCV only: for s = 0 (2H + 2G) and 1 (H + 2G), in
+    // lag-index coordinates (x = delta (.) j): the exponent difference
+    // x^T (Sigma_s^-1 - (2G)^-1) x = j^T D_s j, entries 00, 01, 11 as FP32
+    // leading parts [0..2] and remainders [3..5]; the normaliser ratio
+    // rho_s = phi_{Sigma_s}(0) / phi_{2G}(0) [6, 7] and rho_s - 1 [8, 9],
+    // each as an FP32 pair
+    real xd[2][12];
     AxisPlan a0, a1;
     const real* spec;
     double scale;
@@ -172,6 +179,13 @@ struct SelectParams {
     float inv_n2h, inv_n2l; // 1/n^2 as an FP32 pair (h + l)
     float tauf, d0f, d1f;   // tau, delta_0, delta_1 rounded to FP32
     float Gf[4];            // G rounded to FP32
+    // SCV, each from FP64 on the host: (2G)^-1 (entries 00, 01, 11), its
+    // determinant and delta_0^2, delta_0 delta_1, delta_1^2 as FP32 pairs
+    // (h, l); (2G)^-1 in lag-index coordinates, delta_a delta_b (2G)^-1_ab,
+    // and phi_{2G}(0) rounded to FP32; the lag-index to H-gradient factors
+    // 1 / (delta_0^2), 1 / (delta_0 delta_1), 1 / (delta_1^2)
+    float l2gh[3], l2gl[3], dl2gh, dl2gl, ddh[3], ddl[3];
+    float l2gj[3], n2g, gsc[3];
     double delta0, delta1;
     double G[4];            // SCV pilot, row-major
     const int* ptab0;       // P_0 for support L_0 (index L_0 <= Lcap)
