@@ -4137,12 +4137,17 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
     return KDEFFT_OK;
 }
 
-// The line search gives up after this many halvings (the step then moves
-// theta by under 2.5e-4 of the quasi-Newton step): the binned objective
-// steps where a support L_k changes with H (Eq. 26), and a sufficient-
-// decrease test at smaller steps only measures those steps.  The
-// device-resident search uses the same limit.
-static constexpr int kMaxHalvings = 12;
+// Backtracking, as in the device-resident search: a rejected trial step is
+// replaced by the minimiser of the quadratic through f(0), the slope and
+// f(step), kept within [0.1, 0.5] of the step (a point outside the domain
+// halves it).  The line search gives up after kMaxBacktracks rejections, or
+// once the next trial point would move theta by less than kStepFloor in every
+// coordinate (about 2e-5 relative in H), which the FP32 objective cannot
+// resolve: the binned objective steps where a support L_k changes with H
+// (Eq. 26), and a sufficient-decrease test at smaller steps only measures
+// those steps.
+static constexpr int kMaxBacktracks = 12;
+static constexpr double kStepFloor = 1e-5;
 
 // Start points of the multi-start search: Hstart, then dilations (factors
 // 2^{-1}..2^{1} in half powers of two) and plane rotations of it.
@@ -4317,6 +4322,7 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
     struct State {
         std::vector<double> th, g, dir, Binv, th_try;
         double f = 0.0, step = 1.0, slope = 0.0;
+        double dfp = 0.0;   // decrease of the last accepted step (0: none since the last reset)
         int iter = 0, ls = 0;
         bool done = false;
         bool fresh = true;   // the current direction comes from a reset (scaled steepest descent)
@@ -4535,7 +4541,14 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
             for (double& v : s.dir) v /= dm;
             s.slope /= dm;
         }
+        // first trial step: the minimiser of the quadratic that repeats the
+        // last accepted decrease along the new direction (Nocedal & Wright),
+        // 1.01 x 2 (f_k - f_{k-1}) / slope, at most the unit quasi-Newton step
         s.step = 1.0;
+        if (s.dfp < 0.0) {
+            const double q = 2.02 * s.dfp / s.slope;
+            if (q > 0.0) s.step = std::min(1.0, q);
+        }
         s.ls = 0;
         s.th_try.resize(p);
         for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
@@ -4585,6 +4598,7 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
                 const double fold = s.f;
                 s.th = s.th_try;
                 s.f = fn;
+                s.dfp = fn - fold;
                 s.g = g[k];
                 s.iter++;
                 double gn = 0.0, tn = 0.0;
@@ -4600,9 +4614,17 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
                     new_direction(s);
                 }
             } else {
-                s.step *= 0.5;
+                double nstep = 0.5 * s.step;
+                if (std::isfinite(fn)) {
+                    const double pred = s.step * s.slope, den = (fn - s.f) - pred;
+                    if (den > 0.0) nstep = std::min(std::max(-0.5 * pred * s.step / den, 0.1 * s.step), 0.5 * s.step);
+                }
+                s.step = nstep;
                 s.ls++;
-                if (s.ls > kMaxHalvings && !s.fresh) {
+                double dm = 0.0;
+                for (double v : s.dir) dm = std::max(dm, std::fabs(v));
+                const bool give_up = s.ls > kMaxBacktracks || s.step * dm < kStepFloor;
+                if (give_up && !s.fresh) {
                     // restart: the quasi-Newton model failed here; scaled steepest descent once
                     double gm = 0.0;
                     for (double v : s.g) gm = std::max(gm, std::fabs(v));
@@ -4610,8 +4632,9 @@ static int select_H_impl(kdefft_ds ds, int method, const double* H0, const doubl
                     std::fill(s.Binv.begin(), s.Binv.end(), 0.0);
                     for (int i = 0; i < p; ++i) s.Binv[i * p + i] = sc;
                     s.fresh = true;
+                    s.dfp = 0.0;
                     new_direction(s);
-                } else if (s.ls > kMaxHalvings) {
+                } else if (give_up) {
                     s.done = true;
                 } else {
                     for (int i = 0; i < p; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];

@@ -1155,6 +1155,7 @@ struct SelOpt {
     float g[3], dir[3], Binv[9];
     DFloat f;                 // objective at th, an unevaluated FP32 pair
     float step, slope;
+    float dfp;                // decrease of the last accepted step (0: none since the last reset)
     long long pts;            // lag route: half-box points evaluated
     double flops, bytes;      // FFT route: algorithmic work of the evaluations
     int iter, ls, done, evals, status, first;
@@ -1410,16 +1411,30 @@ __device__ void sel_new_direction(SelOpt& s) {
         for (int i = 0; i < 3; ++i) s.dir[i] *= r;
         s.slope *= r;
     }
-    s.step = 1.f;
+    // first trial step: the minimiser of the quadratic that repeats the last
+    // accepted decrease along the new direction, 1.01 x 2 (f_k - f_{k-1}) /
+    // slope, at most 1 (the unit quasi-Newton step)
+    float a0 = 1.f;
+    if (s.dfp < 0.f) {
+        const float q = 2.02f * s.dfp * __frcp_rn(s.slope);
+        if (q > 0.f) a0 = fminf(1.f, q);
+    }
+    s.step = a0;
     s.ls = 0;
     for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
 }
 
-// The line search gives up after this many halvings (the step then moves
-// theta by under 2.5e-4 of the quasi-Newton step): the binned objective
-// steps where a support L_k changes with H (Eq. 26), and a sufficient-
-// decrease test at smaller steps only measures those steps.
-constexpr int kMaxHalvings = 12;
+// Backtracking: a rejected trial step is replaced by the minimiser of the
+// quadratic through f(0), the slope f'(0) and f(step), kept within
+// [0.1, 0.5] of the step (safeguarded interpolation); a trial point outside
+// the search domain halves the step.  The line search gives up after
+// kMaxBacktracks rejections, or as soon as the next trial point would move
+// theta by less than kStepFloor in every coordinate (a relative change of
+// about 2e-5 in H), which the FP32 objective cannot resolve: the binned
+// objective also steps where a support L_k changes with H (Eq. 26), and a
+// sufficient-decrease test at smaller steps only measures those steps.
+constexpr int kMaxBacktracks = 12;
+constexpr float kStepFloor = 1e-5f;
 
 // consume the evaluation (fn, gn) of the trial point th_try.  The value is
 // an FP32 pair: the difference of two nearby values (Sterbenz: the leading
@@ -1446,6 +1461,7 @@ __device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) 
             return;
         }
         s.fresh = 1;
+        s.dfp = 0.f;
         sel_new_direction(s);
         return;
     }
@@ -1478,6 +1494,7 @@ __device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) 
             tn = fmaxf(tn, fabsf(sv[i]));
         }
         s.f = fn;
+        s.dfp = df;
         s.iter++;
         if (s.iter >= max_iter) {
             s.done = 1;
@@ -1489,17 +1506,26 @@ __device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) 
             sel_new_direction(s);
         }
     } else {
-        s.step *= 0.5f;
+        float nstep = 0.5f * s.step;
+        if (isfinite(fn.h)) {
+            const float pred = s.step * s.slope;   // < 0
+            const float den = df - pred;           // > 0 after a failed sufficient-decrease test
+            if (den > 0.f) nstep = fminf(fmaxf(-0.5f * pred * s.step * __frcp_rn(den), 0.1f * s.step), 0.5f * s.step);
+        }
+        s.step = nstep;
         s.ls++;
-        if (s.ls > kMaxHalvings && !s.fresh) {
+        const float dm = fmaxf(fabsf(s.dir[0]), fmaxf(fabsf(s.dir[1]), fabsf(s.dir[2])));
+        const bool give_up = s.ls > kMaxBacktracks || s.step * dm < kStepFloor;
+        if (give_up && !s.fresh) {
             // restart: the quasi-Newton model failed here; scaled steepest descent once
             const float gm = fmaxf(fabsf(s.g[0]), fmaxf(fabsf(s.g[1]), fabsf(s.g[2])));
             const float sc = (gm > 0.f) ? 0.1f * __frcp_rn(gm) : 1.f;
             for (int i = 0; i < 9; ++i) s.Binv[i] = 0.f;
             for (int i = 0; i < 3; ++i) s.Binv[i * 4] = sc;
             s.fresh = 1;
+            s.dfp = 0.f;
             sel_new_direction(s);
-        } else if (s.ls > kMaxHalvings) {
+        } else if (give_up) {
             s.done = 1;
         } else {
             for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
@@ -1559,6 +1585,7 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
         opt.flops = 0.0;
         opt.bytes = 0.0;
         opt.fresh = 0;
+        opt.dfp = 0.f;
     }
     __syncthreads();
     const int max_rounds = 40 * p.max_iter + 2;
@@ -1699,6 +1726,7 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
         opt.flops = 0.0;
         opt.bytes = 0.0;
         opt.fresh = 0;
+        opt.dfp = 0.f;
     }
     __syncthreads();
     const int max_rounds = 40 * p.max_iter + 2;
