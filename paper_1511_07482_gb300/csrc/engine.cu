@@ -19,6 +19,9 @@
 #include <algorithm>
 
 #include <cooperative_groups.h>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "engine.cuh"
 #include "devutil.cuh"
@@ -1156,6 +1159,7 @@ struct SelOpt {
     DFloat f;                 // objective at th, an unevaluated FP32 pair
     float step, slope;
     float dfp;                // decrease of the last accepted step (0: none since the last reset)
+    float noise;              // resolution of the FP32 objective at th (0: not known)
     long long pts;            // lag route: half-box points evaluated
     double flops, bytes;      // FFT route: algorithmic work of the evaluations
     int iter, ls, done, evals, status, first;
@@ -1350,7 +1354,7 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
 // (FP32 algebra; the value is the FP32 pair sum of the device sum r[0] and
 // the closed-form term; r[1..3]: the sums of the three derivative grids)
 __device__ void sel_assemble(const SelectParams& p, const float* H, const float* Rm, const DFloat* r, float det,
-                             DFloat* f, float* gt, float* gH = nullptr) {
+                             DFloat* f, float* gt, float* gH = nullptr, float* fsc = nullptr) {
     const float rdet = __frcp_rn(det);
     const float rsd = rsqrtf(det);   // |H|^-1/2
     const float rn = p.inv_nf;
@@ -1361,6 +1365,7 @@ __device__ void sel_assemble(const SelectParams& p, const float* H, const float*
         const float k0 = 0.15915494f * rsd;   // K_H(0) = (2 pi)^-1 |H|^-1/2, Eq. 11
         const float c0 = 2.f * rn;
         *f = df_add(r[0], DFloat{c0 * k0, 0.f});
+        if (fsc) *fsc = r[4].h + c0 * k0;   // magnitude of the summed terms
         g00 = r1 + c0 * (-0.5f * k0 * hi00);
         g01 = r2 + c0 * 2.f * (-0.5f * k0 * hi01);
         g11 = r3 + c0 * (-0.5f * k0 * hi11);
@@ -1368,6 +1373,7 @@ __device__ void sel_assemble(const SelectParams& p, const float* H, const float*
         // the derivative grids were summed in lag-index coordinates
         const float rk = 0.07957747f * rsd;   // (4 pi)^-1 |H|^-1/2
         *f = df_add(r[0], DFloat{rk * rn, 0.f});
+        if (fsc) *fsc = r[4].h + rk * rn;
         g00 = fmaf(r1, p.gsc[0], (-0.5f * rk * hi00) * rn);
         g01 = fmaf(r2, p.gsc[1], 2.f * (-0.5f * rk * hi01) * rn);
         g11 = fmaf(r3, p.gsc[2], (-0.5f * rk * hi11) * rn);
@@ -1422,7 +1428,12 @@ __device__ void sel_new_direction(SelOpt& s) {
     s.step = a0;
     s.ls = 0;
     for (int i = 0; i < 3; ++i) s.th_try[i] = s.th[i] + s.step * s.dir[i];
+    if (-a0 * s.slope <= s.noise) s.done = 1;   // nothing left to resolve along this direction
 }
+
+// sums of one lag-domain evaluation: the four grids and the magnitude of the
+// objective's terms
+constexpr int SEL_NSUM = 5;
 
 // Backtracking: a rejected trial step is replaced by the minimiser of the
 // quadratic through f(0), the slope f'(0) and f(step), kept within
@@ -1435,14 +1446,21 @@ __device__ void sel_new_direction(SelOpt& s) {
 // sufficient-decrease test at smaller steps only measures those steps.
 constexpr int kMaxBacktracks = 12;
 constexpr float kStepFloor = 1e-5f;
+// Resolution of an FP32 objective value relative to the magnitude S of its
+// summed terms (measured against the FP64 oracle: errors up to about
+// 6e-7 S).  Where S is known (lag route), a search also stops when an accepted
+// step, or the first-order decrease predicted for the next trial step, is
+// below kResolution S: such differences are rounding, not descent.
+constexpr float kResolution = 2e-7f;
 
 // consume the evaluation (fn, gn) of the trial point th_try.  The value is
 // an FP32 pair: the difference of two nearby values (Sterbenz: the leading
 // parts subtract exactly) keeps about 14 digits.
-__device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) {
+__device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter, float fscale = 0.f) {
     if (s.first) {
         s.first = 0;
         s.f = fn;
+        s.noise = kResolution * fscale;
         for (int i = 0; i < 3; ++i) {
             s.th[i] = s.th_try[i];
             s.g[i] = gn[i];
@@ -1495,11 +1513,13 @@ __device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) 
         }
         s.f = fn;
         s.dfp = df;
+        s.noise = kResolution * fscale;
         s.iter++;
         if (s.iter >= max_iter) {
             s.done = 1;
             s.status = 1;
-        } else if (fabsf(df) <= 1e-12f * fabsf(fn.h) + 1e-30f || tn < 1e-10f || gm < 1e-12f * (fabsf(fn.h) + 1e-30f)) {
+        } else if (fabsf(df) <= 1e-12f * fabsf(fn.h) + 1e-30f || -df <= s.noise || tn < 1e-10f ||
+                   gm < 1e-12f * (fabsf(fn.h) + 1e-30f)) {
             s.done = 1;
         } else {
             s.fresh = 0;
@@ -1515,7 +1535,7 @@ __device__ void sel_update(SelOpt& s, DFloat fn, const float* gn, int max_iter) 
         s.step = nstep;
         s.ls++;
         const float dm = fmaxf(fabsf(s.dir[0]), fmaxf(fabsf(s.dir[1]), fabsf(s.dir[2])));
-        const bool give_up = s.ls > kMaxBacktracks || s.step * dm < kStepFloor;
+        const bool give_up = s.ls > kMaxBacktracks || s.step * dm < kStepFloor || -s.step * s.slope <= s.noise;
         if (give_up && !s.fresh) {
             // restart: the quasi-Newton model failed here; scaled steepest descent once
             const float gm = fmaxf(fabsf(s.g[0]), fmaxf(fabsf(s.g[1]), fabsf(s.g[2])));
@@ -1586,6 +1606,7 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
         opt.bytes = 0.0;
         opt.fresh = 0;
         opt.dfp = 0.f;
+        opt.noise = 0.f;
     }
     __syncthreads();
     const int max_rounds = 40 * p.max_iter + 2;
@@ -1644,13 +1665,20 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     }
 }
 
-// One bandwidth of the search in the lag domain by one CTA: the half box
-// j_0 in [0, L_0], |j_1| <= L_1 (j_0 fastest, so that neighbouring threads
-// read neighbouring a_j), weights 2 / 1 / 0, four compensated sums; thread 0
-// receives the four scaled totals in res4.
-template <int METHOD>
+// One bandwidth of the search in the lag domain by the CS CTAs of a cluster
+// (CS = 1: one CTA): the half box j_0 in [0, L_0], |j_1| <= L_1 (j_0
+// fastest, so that neighbouring threads read neighbouring a_j), weights
+// 2 / 1 / 0, compensated sums of the four grids and of |grid 0| (the
+// magnitude of the objective's summed terms: its FP32 resolution scale).
+// With CS > 1 the points are dealt out over the cluster's threads; every
+// CTA sends its partial sums to all CTAs (distributed shared memory, clp =
+// this round's buffer, [CS][NSUM]), and after one cluster barrier each sums
+// them in rank order, so that every CTA holds the same totals.  Thread 0
+// receives the NSUM scaled totals in res4.
+template <int METHOD, int CS>
 __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const float* __restrict__ acorr, int A0,
-                                             int A1, float d0f, float d1f, DFloat scale, DFloat* res4) {
+                                             int A1, float d0f, float d1f, DFloat scale, DFloat* res4, DFloat* clp,
+                                             int rank) {
     const int L0 = f.off0, L1 = f.off1;
     const int n0 = L0 + 1;
     const int total = n0 * (2 * L1 + 1);
@@ -1659,8 +1687,9 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
     // a thread holds a few points: plain FP32 sums there and across its warp
     // (the search compares values to FP32 accuracy; the reported value is
     // recomputed), compensated sums across the warps
-    float s4[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    constexpr int NS = SEL_NSUM;
+    float s4[NS] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int t = rank * (int)blockDim.x + (int)threadIdx.x; t < total; t += CS * (int)blockDim.x) {
         const int q = (n0 == 1) ? t : (int)qdiv((uint32_t)t, mn0);
         const int j0 = t - q * n0;
         const int j1 = q - L1;
@@ -1672,47 +1701,74 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
         const float wa = (float)wt * av;
 #pragma unroll
         for (int e = 0; e < 4; ++e) s4[e] = fmaf(wa, v[e], s4[e]);
+        s4[4] = fmaf(wa, fabsf(v[0]), s4[4]);
     }
-    __shared__ float red4[4][32];
+    __shared__ float red4[NS][32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) s4[e] += __shfl_down_sync(0xffffffffu, s4[e], o);
+        for (int e = 0; e < NS; ++e) s4[e] += __shfl_down_sync(0xffffffffu, s4[e], o);
     const int wi = threadIdx.x >> 5, li = threadIdx.x & 31;
     if (li == 0)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) red4[e][wi] = s4[e];
+        for (int e = 0; e < NS; ++e) red4[e][wi] = s4[e];
     __syncthreads();
+    DFloat v4[NS];
     if (wi == 0) {
         const int nw = (blockDim.x + 31) >> 5;
-        DFloat v4[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v4[e] = DFloat{(li < nw) ? red4[e][li] : 0.f, 0.f};
+        for (int e = 0; e < NS; ++e) v4[e] = DFloat{(li < nw) ? red4[e][li] : 0.f, 0.f};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < NS; ++e) {
                 const DFloat t{__shfl_down_sync(0xffffffffu, v4[e].h, o), __shfl_down_sync(0xffffffffu, v4[e].l, o)};
                 v4[e] = df_add(v4[e], t);
             }
-        if (li == 0)
+        if constexpr (CS > 1) {
+            // lane r < CS sends this CTA's totals (held by lane 0) to CTA r
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {   // times n^-2 as FP32 pairs
-                const float ph = v4[e].h * scale.h;
-                const float pl = fmaf(v4[e].h, scale.h, -ph) + fmaf(v4[e].h, scale.l, v4[e].l * scale.h);
-                const float h = ph + pl;
-                res4[e] = DFloat{h, pl - (h - ph)};
+            for (int e = 0; e < NS; ++e)
+                v4[e] = DFloat{__shfl_sync(0xffffffffu, v4[e].h, 0), __shfl_sync(0xffffffffu, v4[e].l, 0)};
+            if (li < CS) {
+                DFloat* dst = cg::this_cluster().map_shared_rank(clp, li);
+#pragma unroll
+                for (int e = 0; e < NS; ++e) dst[rank * NS + e] = v4[e];
             }
+        }
     }
+    if constexpr (CS > 1) {
+        cg::this_cluster().sync();
+        if (wi == 0 && li == 0) {
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+                v4[e] = clp[e];
+#pragma unroll
+                for (int r = 1; r < CS; ++r) v4[e] = df_add(v4[e], clp[r * NS + e]);
+            }
+        }
+    }
+    if (wi == 0 && li == 0)
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {   // times n^-2 as FP32 pairs
+            const float ph = v4[e].h * scale.h;
+            const float pl = fmaf(v4[e].h, scale.h, -ph) + fmaf(v4[e].h, scale.l, v4[e].l * scale.h);
+            const float h = ph + pl;
+            res4[e] = DFloat{h, pl - (h - ph)};
+        }
 }
 
-// One CTA per start runs the whole quasi-Newton search with lag-domain
-// evaluations against the count autocorrelation (staged in shared memory, or
-// read from the L2-resident FP32 copy).  The search state lives in the
-// caller's shared memory; `start` indexes the start table.
+// One start's whole quasi-Newton search with lag-domain evaluations against
+// the count autocorrelation (staged in shared memory, or read from the
+// L2-resident FP32 copy), by one CTA or a cluster of CS CTAs.  Every CTA of
+// a cluster runs its own copy of the optimiser state (in the caller's
+// shared memory) on the same totals, so all take the same branches and meet
+// at the same cluster barriers; rank 0 writes the record and the result.
+template <int CS>
 __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* __restrict__ starts, int start,
                                                const float* acorr, DFloat* res, FusedItem<float>* items,
-                                               SelOpt& opt, int* ctl, float* Hs, float* Rs, float* aux) {
+                                               SelOpt& opt, int* ctl, float* Hs, float* Rs, float* aux,
+                                               DFloat* clp /* [2][CS][SEL_NSUM] */, int rank) {
     if (threadIdx.x == 0) {
         const SelStart& st = starts[start];
         for (int i = 0; i < 3; ++i) opt.th_try[i] = (float)st.th[i];
@@ -1727,6 +1783,7 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
         opt.bytes = 0.0;
         opt.fresh = 0;
         opt.dfp = 0.f;
+        opt.noise = 0.f;
     }
     __syncthreads();
     const int max_rounds = 40 * p.max_iter + 2;
@@ -1743,28 +1800,32 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
         const int valid = ctl[0], done = ctl[1];
         if (done) break;
         if (valid) {
+            // partial sums alternate between two buffers, so that a CTA ahead
+            // by a round never overwrites totals another CTA is still reading
+            DFloat* cb = clp + (round & 1) * (CS * SEL_NSUM);
             const DFloat sc{p.inv_n2h, p.inv_n2l};
             if (p.method == 0)
-                sel_eval_lag<0>(items[0], acorr, p.A0, p.A1, p.d0f, p.d1f, sc, res);
+                sel_eval_lag<0, CS>(items[0], acorr, p.A0, p.A1, p.d0f, p.d1f, sc, res, cb, rank);
             else
-                sel_eval_lag<1>(items[0], acorr, p.A0, p.A1, p.d0f, p.d1f, sc, res);
+                sel_eval_lag<1, CS>(items[0], acorr, p.A0, p.A1, p.d0f, p.d1f, sc, res, cb, rank);
             __syncthreads();
         }
         if (threadIdx.x == 0) {
             DFloat fn{INFINITY, 0.f};
             float gt[3] = {0.f, 0.f, 0.f};
+            float fsc = 0.f;
             if (valid) {
                 float gH[3];
-                sel_assemble(p, Hs, Rs, res, aux[0], &fn, gt, gH);
-                sel_record(p, start, opt.evals, Hs, items[0].off0, items[0].off1, fn, gH);
+                sel_assemble(p, Hs, Rs, res, aux[0], &fn, gt, gH, &fsc);
+                if (rank == 0) sel_record(p, start, opt.evals, Hs, items[0].off0, items[0].off1, fn, gH);
                 opt.evals++;
                 opt.pts += (long long)aux[1];
             }
-            sel_update(opt, fn, gt, p.max_iter);
+            sel_update(opt, fn, gt, p.max_iter, fsc);
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && rank == 0) {
         // per half-box point and covariance: a quadratic form (8 flops) and
         // four six-term weighted sums (48); 4 bytes of autocorrelation
         const double nsig = (p.method == 0) ? 2.0 : 3.0;
@@ -1779,17 +1840,22 @@ __device__ __forceinline__ void sel_search_lag(const SelectParams& p, SelStart* 
     }
 }
 
-// Two searches on one dataset in one launch: CTAs [0, nfirst) run criterion
-// p, the rest criterion q (the same autocorrelation box).  A single search
-// passes q = p.
+// Two searches on one dataset in one launch: starts [0, nfirst) run
+// criterion p, the rest criterion q (the same autocorrelation box).  A
+// single search passes q = p.  Start s runs on CTAs [s CS, (s + 1) CS), one
+// cluster.
+template <int CS>
 __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelectParams q, int nfirst,
                                                        SelStart* __restrict__ starts, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ DFloat res[4];
+    __shared__ DFloat res[SEL_NSUM];
     __shared__ FusedItem<float> items[2];
     __shared__ SelOpt opt;
     __shared__ int ctl[2];
     __shared__ float Hs[4], Rs[3], aux[3];
+    __shared__ DFloat clp[2 * CS * SEL_NSUM];
+    const int start = (int)blockIdx.x / CS;
+    const int rank = (CS > 1) ? (int)cg::this_cluster().block_rank() : 0;
     // the autocorrelation box is fixed for the whole search: staged once in
     // shared memory when it fits (stage != 0)
     const float* acorr = p.acorr;
@@ -1799,10 +1865,67 @@ __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelectPar
         for (int t = threadIdx.x; t < nbox; t += blockDim.x) sa[t] = p.acorr[t];
         acorr = sa;
     }
-    if ((int)blockIdx.x < nfirst)
-        sel_search_lag(p, starts, blockIdx.x, acorr, res, items, opt, ctl, Hs, Rs, aux);
+    if (start < nfirst)
+        sel_search_lag<CS>(p, starts, start, acorr, res, items, opt, ctl, Hs, Rs, aux, clp, rank);
     else
-        sel_search_lag(q, starts, blockIdx.x, acorr, res, items, opt, ctl, Hs, Rs, aux);
+        sel_search_lag<CS>(q, starts, start, acorr, res, items, opt, ctl, Hs, Rs, aux, clp, rank);
+    // no CTA leaves while another may still write into its shared memory
+    if constexpr (CS > 1) cg::this_cluster().sync();
+}
+
+// Cluster size for a launch: the largest of 4, 2 whose clusters are all
+// co-resident (one wave), else one CTA per start.  Queried once per device
+// and shared-memory size.
+static int select2d_lag_cs(int nstarts, size_t sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, size_t, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int cs : {4, 2}) {
+        const auto key = std::make_tuple(dev, sm, cs);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            cfg.gridDim = dim3((unsigned)cs, 1, 1);
+            cfg.blockDim = dim3(1024, 1, 1);
+            cfg.dynamicSmemBytes = sm;
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)cs;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            const void* f = (cs == 4) ? (const void*)k_select2d_lag<4> : (const void*)k_select2d_lag<2>;
+            if (cudaOccupancyMaxActiveClusters(&n, f, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                n = 0;
+            }
+            it = cache.emplace(key, n).first;
+        }
+        if (it->second >= nstarts) return cs;
+    }
+    return 1;
+}
+
+template <int CS>
+static cudaError_t launch_select2d_lag_cs(const SelectParams& prm, const SelectParams& prm2, int nfirst,
+                                          SelStart* starts, int nstarts, size_t sm, int stage, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)(nstarts * CS), 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_select2d_lag<CS>, prm, prm2, nfirst, starts, stage);
 }
 
 cudaError_t launch_select2d_lag(const SelectParams& prm, const SelectParams& prm2, int nfirst, SelStart* starts,
@@ -1813,7 +1936,10 @@ cudaError_t launch_select2d_lag(const SelectParams& prm, const SelectParams& prm
     const size_t limit = 200 * 1024;
     const int stage = box <= limit ? 1 : 0;
     const size_t sm = stage ? box : 0;
-    k_select2d_lag<<<nstarts, 1024, sm, st>>>(prm, prm2, nfirst, starts, stage);
+    const int cs = select2d_lag_cs(nstarts, sm);
+    if (cs == 4) return launch_select2d_lag_cs<4>(prm, prm2, nfirst, starts, nstarts, sm, stage, st);
+    if (cs == 2) return launch_select2d_lag_cs<2>(prm, prm2, nfirst, starts, nstarts, sm, stage, st);
+    k_select2d_lag<1><<<nstarts, 1024, sm, st>>>(prm, prm2, nfirst, starts, stage);
     return cudaGetLastError();
 }
 
@@ -1966,7 +2092,8 @@ cudaError_t prepare_kernels() {
     const void* dyn[] = {(const void*)k_stage_a<float>,    (const void*)k_stage_a<double>,
                          (const void*)k_mid<float>,        (const void*)k_mid<double>,
                          (const void*)k_final<float>,      (const void*)k_final<double>,
-                         (const void*)k_acorr_fft,         (const void*)k_select2d_lag,
+                         (const void*)k_acorr_fft,         (const void*)k_select2d_lag<1>,
+                         (const void*)k_select2d_lag<2>,   (const void*)k_select2d_lag<4>,
                          (const void*)k_select2d,          (const void*)k_fused2d<float, 2>,
                          (const void*)k_fused2d<float, 4>, (const void*)k_fused2d<double, 2>};
     for (const void* f : dyn)
