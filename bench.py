@@ -413,14 +413,78 @@ def run_ours(args):
         "profiled_ms_per_step": sum(prof_times) / prof_steps,
         "clocks": clk,
     }
+    if args.workload == "select2d":
+        # one step is one LSCV and one SCV selection
+        out["ms_per_selection"] = {"lscv_and_scv": out["ms_per_step"],
+                                   "note": "one step selects H for both criteria (16 starts each)"}
+    if world == 1 and args.workload == "select2d" and not args.no_fp64:
+        out["fp64_path"], fp64_res = fp64_selection(ctx, w, dev, args)
+    else:
+        fp64_res = None
     if not args.no_cpu_baseline and world == 1 and args.workload == "select2d":
-        out["cpu_baseline"] = cpu_baseline(w, args, res)
+        rec = search_records(ctx, w, dev, args)
+        out["cpu_baseline"] = cpu_baseline(w, args, res, fp64_res, rec)
+        for k in ("rel_err_max_search_lscv", "rel_err_max_search_scv"):
+            out[k] = out["cpu_baseline"]["search_parity"][k]
+        if fp64_res is not None:
+            out["fp64_path"].update(out["cpu_baseline"].pop("fp64_parity"))
     if world == 1 and args.workload == "select2d" and not args.no_batch_compare:
         out["batched_vs_single_h"] = batched_vs_single(ctx, w, dev)
     print(json.dumps(out))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def fp64_selection(ctx, w, dev, args, steps=3):
+    """The same step (binning + LSCV and SCV selection, same starts) on an FP64
+    dataset: FP64 arithmetic on the GPU, searched from the host with one
+    batched evaluation per round.  Device-timed with CUDA events like the FP32
+    line; returns (its line, the selected bandwidths and values)."""
+    import torch
+    from paper_1511_07482_gb300 import FP64, LSCV, SCV
+    X = torch.from_numpy(w.X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ds = ctx.bin(X, w.lo, w.hi, w.M, precision=FP64)
+        (H1, f1, e1), (H2, f2, e2) = ds.select_H_many([LSCV, SCV], G=w.G, n_starts=args.n_starts,
+                                                      max_iter=args.max_iter)
+        ds.close()
+        return e1 + e2, (H1, f1, H2, f2)
+    step()
+    t, ev = 0.0, 0
+    for _ in range(steps):
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e, res = step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t += a.elapsed_time(b)
+        ev += e
+    line = {"value": ev / (t / 1000.0), "unit": UNIT, "ms_per_step": t / steps, "evals_per_step": ev / steps,
+            "precision": "fp64 (every kernel value, transform and sum)", "search": "host-driven, one batched "
+            "evaluation per round", "steps": steps}
+    return line, res
+
+
+def search_records(ctx, w, dev, args):
+    """One more step of the FP32 selection with the search kernel recording
+    every evaluation it makes (bandwidth, support, value, gradient): rows of
+    12 values, outside every timed region."""
+    import torch
+    from paper_1511_07482_gb300 import LSCV, SCV
+    cap = 400
+    rec = torch.full((2 * args.n_starts * cap * 12,), float("nan"), dtype=torch.float64, device=dev)
+    ds = ctx.bin(torch.from_numpy(w.X).to(dev), w.lo, w.hi, w.M)
+    ctx.set_search_record(rec, cap)
+    ds.select_H_many([LSCV, SCV], G=w.G, n_starts=args.n_starts, max_iter=args.max_iter)
+    ctx.set_search_record(None)
+    ds.close()
+    R = rec.view(-1, 12).cpu().numpy()
+    return R[np.isfinite(R[:, 0])]
 
 
 def batched_vs_single(ctx, w, dev, reps=5):
@@ -472,33 +536,113 @@ def oracle_evals(w, Hs, G):
     return 2 * len(Hs), res
 
 
-def cores_used(cpu_s: float, wall_s: float) -> int:
-    """Threads the oracle kept busy: its process CPU time over the wall time
-    of the same region, rounded (the oracle's numpy FFTs run on one)."""
-    return max(1, int(round(cpu_s / wall_s))) if wall_s > 0 else 1
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
-def cpu_baseline(w, args, gpu_res):
-    """The oracle, as it stands, on a bounded sample: binning of the full
-    sample plus LSCV+grad and SCV+grad at the GPU-selected LSCV bandwidth and
-    one more candidate; also the relative error of the GPU objective values
-    at those bandwidths."""
-    H1, f1, H2, f2 = gpu_res
-    t0, c0 = time.perf_counter(), time.process_time()
-    n_ev, res = oracle_evals(w, [H1], w.G)
-    # accuracy of the FP32 path at the selected H: compare with the oracle value
-    ref_lscv = res[0][1][0]
-    rel = abs(f1 - ref_lscv) / abs(ref_lscv)
-    i = 0
-    while time.perf_counter() - t0 < args.cpu_seconds:
-        k, _ = oracle_evals(w, [w.H[i % len(w.H)]], w.G)
+def _oracle_worker(job):
+    """One oracle process of the all-core baseline: repeats the bounded
+    sample (binning of all n, then LSCV+gradient and SCV+gradient at one
+    bandwidth) until `seconds` have passed; returns its evaluation count and
+    wall time.  Started by spawn, it imports only the oracle and numpy."""
+    import types
+    X, lo, hi, M, Hs, G, name, seconds = job
+    sys.path.insert(0, ROOT)
+    wk = types.SimpleNamespace(X=X, lo=lo, hi=hi, M=M, n=X.shape[0], name=name)
+    t0, n_ev, i = time.perf_counter(), 0, 0
+    while time.perf_counter() - t0 < seconds:
+        k, _ = oracle_evals(wk, [Hs[i % len(Hs)]], G)
         n_ev += k
         i += 1
-    dt = time.perf_counter() - t0
-    return {"value": n_ev / dt, "unit": UNIT, "cores": cores_used(time.process_time() - c0, dt), "kind": "oracle",
-            "sample": f"{w.name}: {1 + i} oracle binnings of all n, each followed by LSCV+gradient and "
-                      f"SCV+gradient in FP64 (numpy FFT) at one bandwidth ({n_ev} evaluations, {dt:.1f} s)",
-            "rel_err_lscv_at_selected_H": rel}
+    return n_ev, time.perf_counter() - t0
+
+
+def oracle_throughput(w, seconds: float, procs: int):
+    """Evaluations per second of `procs` concurrent oracle processes (spawned:
+    no process inherits CUDA state), each running the bounded sample for
+    `seconds`; the job's rate is the summed count over the slowest wall time."""
+    import multiprocessing as mp
+    job = (w.X, w.lo, w.hi, list(w.M), list(w.H), w.G, w.name, seconds)
+    if procs == 1:
+        n_ev, dt = _oracle_worker(job)
+        return n_ev / dt, n_ev, dt
+    with mp.get_context("spawn").Pool(procs) as pool:
+        out = pool.map(_oracle_worker, [job] * procs)
+    n_ev = sum(o[0] for o in out)
+    dt = max(o[1] for o in out)
+    return n_ev / dt, n_ev, dt
+
+
+def search_parity(w, rec):
+    """Max error of the search kernel's own evaluations (value and the three
+    gradient entries of every recorded LSCV and SCV evaluation) against the
+    FP64 oracle at the same FP32 bandwidth and support, each relative to
+    max(|ref|, S/10), S the magnitude of the summed terms (the FP32
+    tolerance's normalisation)."""
+    from oracle import binning, functionals as F, rules, selectors as S
+    c = binning.bin_linear(w.X, w.lo, w.hi, w.M)
+    delta = rules.bin_width(w.lo, w.hi, w.M)
+    a = F.autocorr_fft(c)
+    err = {0: [0.0, 0.0, 0], 1: [0.0, 0.0, 0]}
+    for r in rec:
+        m = int(r[2])
+        H = np.array([[r[3], r[4]], [r[4], r[5]]])
+        L = [int(r[6]), int(r[7])]
+        ev = lambda t: F.lag_sums(a, w.n, t, delta, L)[0]
+        ea = lambda t: F.lag_sums(a, w.n, t, delta, L)[1]
+        if m == 0:
+            val, g = S.lscv(ev, H, w.n, grad=True)
+            sv, sg = S.abs_scales(ea, "lscv", H, w.n)
+        else:
+            val, g = S.scv(ev, H, w.G, w.n, grad=True)
+            sv, sg = S.abs_scales(ea, "scv", H, w.n, w.G)
+        gg = np.array([[r[9], r[10]], [r[10], r[11]]])
+        e = err[m]
+        e[0] = max(e[0], abs(r[8] - val) / max(abs(val), 0.1 * sv))
+        e[1] = max(e[1], float(np.max(np.abs(gg - g) / np.maximum(np.abs(g), 0.1 * sg))))
+        e[2] += 1
+    return {"rel_err_max_search_lscv": max(err[0][0], err[0][1]), "rel_err_max_search_scv": max(err[1][0], err[1][1]),
+            "lscv": {"evaluations": err[0][2], "value": err[0][0], "gradient": err[0][1]},
+            "scv": {"evaluations": err[1][2], "value": err[1][0], "gradient": err[1][1]},
+            "normalisation": "|got - ref| / max(|ref|, S/10), S = magnitude of the summed terms; tolerance 1e-5"}
+
+
+def cpu_baseline(w, args, gpu_res, fp64_res=None, rec=None):
+    """The oracle, as it stands, on a bounded sample: binning of the full
+    sample plus LSCV+grad and SCV+grad at one bandwidth per repetition, on one
+    host core and on every host core (one oracle process per core); also the
+    oracle's check of the GPU's results: the objective values at the selected
+    bandwidths (FP32 and FP64 paths) and every evaluation the search kernel
+    recorded."""
+    H1, f1, H2, f2 = gpu_res
+    _, res = oracle_evals(w, [H1], w.G)
+    _, res2 = oracle_evals(w, [H2], w.G)
+    rel_l = abs(f1 - res[0][1][0]) / abs(res[0][1][0])
+    rel_s = abs(f2 - res2[1][1][0]) / abs(res2[1][1][0])
+    ncore = host_cores()
+    half = args.cpu_seconds / 2.0
+    v1, n1, d1 = oracle_throughput(w, half, 1)
+    vall, nall, dall = oracle_throughput(w, half, ncore)
+    out = {"value": vall, "unit": UNIT, "cores": ncore, "kind": "oracle", "host_cores": ncore,
+           "sample": f"{w.name}: repetitions of oracle binning of all n followed by LSCV+gradient and SCV+gradient "
+                     f"in FP64 (numpy FFT) at one bandwidth; {ncore} processes x {half:.0f} s ({nall} evaluations) "
+                     f"for the all-core value, one process x {half:.0f} s ({n1} evaluations) for one core",
+           "one_core": {"value": v1, "unit": UNIT, "cores": 1, "evaluations": n1, "seconds": d1},
+           "all_cores": {"value": vall, "unit": UNIT, "cores": ncore, "evaluations": nall, "seconds": dall},
+           "rel_err_lscv_at_selected_H": rel_l, "rel_err_scv_at_selected_H": rel_s}
+    if rec is not None:
+        out["search_parity"] = search_parity(w, rec)
+    if fp64_res is not None:
+        G1, g1, G2, g2 = fp64_res
+        _, r1 = oracle_evals(w, [G1], w.G)
+        _, r2 = oracle_evals(w, [G2], w.G)
+        out["fp64_parity"] = {"rel_err_lscv_at_selected_H": abs(g1 - r1[0][1][0]) / abs(r1[0][1][0]),
+                              "rel_err_scv_at_selected_H": abs(g2 - r2[1][1][0]) / abs(r2[1][1][0])}
+    return out
 
 
 def run_reference(args):
@@ -510,12 +654,11 @@ def run_reference(args):
     Hs = list(w.H[:4])
     for _ in range(args.warmup):
         oracle_evals(w, Hs, w.G)
-    t, cpu, ev = 0.0, 0.0, 0
+    t, ev = 0.0, 0
     for _ in range(args.steps):
-        t0, c0 = time.perf_counter(), time.process_time()
+        t0 = time.perf_counter()
         n_ev, _ = oracle_evals(w, Hs, w.G)
         t += time.perf_counter() - t0
-        cpu += time.process_time() - c0
         ev += n_ev
     value = ev / t
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -523,9 +666,9 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name + ": bin + LSCV and SCV objective+gradient evaluations (oracle)",
                       "n": w.n, "d": w.d, "grid": w.M},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(cpu, t), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cores": host_cores(),
                             "sample": f"per step: oracle binning of all n plus {2 * len(Hs)} FP64 "
-                                      f"objective+gradient evaluations"},
+                                      f"objective+gradient evaluations, one process"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -547,7 +690,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="skip the batched-vs-single-H LSCV comparison of the select2d workload")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="oracle baseline budget: half on one core, half on every host core")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path line of the select2d workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -155,6 +155,19 @@ int kdefft_plan(kdefft_ds ds, int method, const double* H, const double* G,
  * alpha_k = #{m : i_m = k}).  r even, 0 <= r <= 8.  out: host or device. */
 int kdefft_psi(kdefft_ds ds, const double* H, int nH, int r, double* out);
 
+/* Adjoint of psi_r (Eq. 13) for reverse-mode differentiation: for each of
+ * the nH bandwidths H_k, out_k = sum_i w_{k,i} d psi_{r,i}(H_k) / d H, a d x d
+ * matrix whose entry (a, b) is the derivative in H_ab with the d^2 entries of
+ * H taken as independent (evaluated at the symmetric H; each off-diagonal
+ * entry gets half the tied derivative of the other calls).  By the Gaussian's
+ * heat equation d phi_H / dH = 1/2 grad grad^T phi_H (Sec. 5's derivative
+ * functionals), d psi_alpha / d H_ab = 1/2 psi_{alpha + e_a + e_b}, so this
+ * evaluates psi_{r+2} at each H (binned, the same FFT steps as kdefft_psi)
+ * and contracts it with w.  w: nH x d^r (Kronecker order, as kdefft_psi's
+ * output), host or device; out: nH x d x d FP64, host or device.  Errors:
+ * KDEFFT_ERR_UNSUPPORTED when r + 2 exceeds the order limit for d. */
+int kdefft_psi_grad(kdefft_ds ds, const double* H, int nH, int r, const double* w, double* out);
+
 /* LSCV(H) for nH bandwidths: Eq. 10 (psi of Eq. 12 with T_H of Eq. 11, plus
  * 2 n^-1 K_H(0)) or, with opts.exact_loo, Eq. 8.  val: nH FP64; grad: NULL
  * or nH d x d gradients (heat-equation kernels through the same FFT, L held

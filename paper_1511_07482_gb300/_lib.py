@@ -36,6 +36,7 @@ EXPORTS = [
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
     "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class", "kdefft_bin_many",
     "kdefft_select_H_multi", "kdefft_memory_stats", "kdefft_trim", "kdefft_set_search_record",
+    "kdefft_psi_grad",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         "kdefft_trim": (I, [P]),
         "kdefft_select_H_multi": (I, [P, I, P, P, P, I, I, P, P, P]),
         "kdefft_set_search_record": (I, [P, P, I64, I]),
+        "kdefft_psi_grad": (I, [P, P, I, I, P, P]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -418,6 +420,20 @@ class Dataset:
         if nH == 0:
             return out
         _check(load().kdefft_psi(self.h, H.ctypes.data_as(C.c_void_p), nH, r, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def psi_grad(self, H, r, w):
+        """sum_i w_i d psi_{r,i}(H) / dH per bandwidth (entries of H
+        independent): nH x d x d, from psi_{r+2} through the library."""
+        H, nH = self._Hs(H)
+        wa = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+        if wa.size != nH * self.d ** r:
+            raise ValueError(f"w must hold {nH} x {self.d ** r} values, got {wa.size}")
+        out = np.zeros((nH, self.d, self.d))
+        if nH == 0:
+            return out
+        _check(load().kdefft_psi_grad(self.h, H.ctypes.data_as(C.c_void_p), nH, int(r),
+                                      wa.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
         return out
 
     def lscv(self, H, grad=False):

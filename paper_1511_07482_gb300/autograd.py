@@ -1,18 +1,13 @@
 """psi_r, LSCV, SCV and PI of a binned dataset as differentiable functions
 of H for torch.autograd.
 
-H is a float tensor of shape (d, d) or (nH, d, d) on any device; the
-functions see its symmetric part (H + H^T)/2, so the gradient of an output
-with respect to the full matrix is, entry by entry,
-
-    d f / d H_ab = 1/2 (d f / d H_ab + d f / d H_ba)   of the symmetric form,
-
-which for the Gaussian kernel follows from its heat equation
-d phi_H / dH = 1/2 grad grad^T phi_H:
-    d psi_alpha(H) / d H_ab = 1/2 psi_{alpha + e_a + e_b}(H),
-so psi_r's backward evaluates psi_{r+2} at the same H (r <= 6), and the
-objectives' backward takes the exact gradients the library returns with
-their values (tied off-diagonal convention, halved off the diagonal here).
+H is a float tensor of shape (d, d) or (nH, d, d) on any device, symmetric
+(the library checks it to 1e-12 relative).  Gradients are with respect to the
+d^2 entries of H taken as independent.  psi_r's backward is the library's
+adjoint (kdefft_psi_grad: psi_{r+2} by the Gaussian's heat equation, for
+r + 2 within the order limit); the objectives' backward takes the exact
+gradients the library returns with their values, whose off-diagonal entries
+(derivatives along E_ab + E_ba) split evenly between H_ab and H_ba.
 
 Every evaluation runs in the CUDA library through the C ABI; this module only
 marshals tensors.
@@ -26,15 +21,14 @@ __all__ = ["psi", "lscv", "scv", "pi"]
 def _batch(H):
     Hn = H.detach().to("cpu", torch.float64).numpy()
     single = Hn.ndim == 2
-    Hb = Hn.reshape((-1,) + Hn.shape[-2:])
-    return 0.5 * (Hb + np.swapaxes(Hb, 1, 2)), single
+    return np.ascontiguousarray(Hn.reshape((-1,) + Hn.shape[-2:])), single
 
 
-def _full_from_tied(g):
-    g = np.array(g, dtype=np.float64, copy=True)
-    d = g.shape[-1]
-    g[..., ~np.eye(d, dtype=bool)] *= 0.5
-    return g
+def _tied_share(d, device):
+    """The library's off-diagonal gradient entries are derivatives along
+    E_ab + E_ba; each of the two independent entries H_ab, H_ba carries half
+    of it (1 on the diagonal, 1/2 off it)."""
+    return torch.full((d, d), 0.5, dtype=torch.float64, device=device).fill_diagonal_(1.0)
 
 
 class _Objective(torch.autograd.Function):
@@ -48,14 +42,14 @@ class _Objective(torch.autograd.Function):
         else:
             v, g = ds.pi(Hs, G, grad=True)
         ctx.single = single
-        ctx.save_for_backward(torch.from_numpy(_full_from_tied(g)).to(H.device))
+        ctx.save_for_backward(torch.from_numpy(g).to(H.device))
         out = torch.from_numpy(np.ascontiguousarray(v)).to(device=H.device, dtype=H.dtype)
         return out[0] if single else out
 
     @staticmethod
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
-        gH = grad_out.to(g.dtype).reshape(-1, 1, 1) * g
+        gH = grad_out.to(g.dtype).reshape(-1, 1, 1) * (g * _tied_share(g.shape[-1], g.device))
         if ctx.single:
             gH = gH[0]
         return gH.to(grad_out.dtype), None, None, None
@@ -74,14 +68,9 @@ class _Psi(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (H,) = ctx.saved_tensors
-        ds, r, d = ctx.ds, ctx.r, H.shape[-1]
-        if r + 2 > 8:
-            raise NotImplementedError("the gradient of psi_r needs psi_{r+2}, available for r <= 6")
         Hs, _ = _batch(H)
-        p2 = ds.psi(Hs, r + 2).reshape(len(Hs), d ** r, d, d)
-        go = grad_out.detach().to("cpu", torch.float64).numpy().reshape(len(Hs), d ** r)
-        gH = 0.5 * np.einsum("ki,kiab->kab", go, p2)
-        gH = torch.from_numpy(gH).to(device=H.device, dtype=grad_out.dtype)
+        go = grad_out.detach().to("cpu", torch.float64).numpy()
+        gH = torch.from_numpy(ctx.ds.psi_grad(Hs, ctx.r, go)).to(device=H.device, dtype=grad_out.dtype)
         return (gH[0] if ctx.single else gH), None, None
 
 

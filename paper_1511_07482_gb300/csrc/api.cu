@@ -3197,6 +3197,40 @@ int kdefft_psi(kdefft_ds ds, const double* H, int nH, int r, double* out) {
     return write_out(ds->ctx, out, res.data(), res.size());
 }
 
+int kdefft_psi_grad(kdefft_ds ds, const double* H, int nH, int r, const double* w, double* out) {
+    KCHK(check_common(ds, H, nH));
+    if (!out || !w) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    const int d = ds->d;
+    if (r < 0 || (r & 1)) return fail(KDEFFT_ERR_ARG, "r must be even");
+    if (r + 2 > kRmax[d]) return fail(KDEFFT_ERR_UNSUPPORTED, "the adjoint of psi_r needs psi_{r+2} within the order limit");
+    size_t len = 1;
+    for (int i = 0; i < r; ++i) len *= (size_t)d;
+    // psi_{r+2} at every bandwidth (Kronecker order: position i d^2 + a d + b
+    // holds d^{alpha(i) + e_a + e_b} phi), then the contraction with w: the
+    // heat equation gives d psi_alpha / d H_ab = 1/2 psi_{alpha + e_a + e_b}
+    // for the entries of H taken as independent
+    std::vector<double> p2(len * d * d * (size_t)nH);
+    KCHK(kdefft_psi(ds, H, nH, r + 2, p2.data()));
+    std::vector<double> wh(len * (size_t)nH);
+    if (is_device_ptr(w)) {
+        KCU(cudaMemcpyAsync(wh.data(), w, sizeof(double) * wh.size(), cudaMemcpyDeviceToHost, ds->ctx->stream));
+        KCU(cudaStreamSynchronize(ds->ctx->stream));
+        ds->ctx->d2h += (int64_t)(sizeof(double) * wh.size());
+    } else {
+        std::memcpy(wh.data(), w, sizeof(double) * wh.size());
+    }
+    std::vector<double> g((size_t)nH * d * d, 0.0);
+    for (int h = 0; h < nH; ++h)
+        for (size_t i = 0; i < len; ++i) {
+            const double wi = 0.5 * wh[(size_t)h * len + i];
+            if (wi == 0.0) continue;
+            const double* q = &p2[((size_t)h * len + i) * d * d];
+            double* gh = &g[(size_t)h * d * d];
+            for (int e = 0; e < d * d; ++e) gh[e] += wi * q[e];
+        }
+    return write_out(ds->ctx, out, g.data(), g.size());
+}
+
 // LSCV at nH bandwidths in two halves around run(): the requests, then the
 // assembly, so that several criteria can share one run()
 struct LscvJob {

@@ -93,11 +93,48 @@ def test_traffic_record_is_tied_to_the_kernel_source(tmp_path, monkeypatch):
     assert bench.ncu_traffic("select2d_lag_f32", 1000.0) is None
 
 
-def test_cores_used_and_rank_seeds():
-    assert bench.cores_used(1.0, 1.0) == 1 and bench.cores_used(0.2, 1.0) == 1
-    assert bench.cores_used(3.9, 1.0) == 4 and bench.cores_used(1.0, 0.0) == 1
+def test_host_cores_and_rank_seeds():
+    assert 1 <= bench.host_cores() <= (os.cpu_count() or 1)
     seeds = {bench.rank_seed(2, r) for r in range(8)}
     assert len(seeds) == 8 and bench.rank_seed(2, 0) == 2
+
+
+def test_all_core_oracle_baseline_runs_one_spawned_process_per_core():
+    """The all-core baseline: `procs` spawned oracle processes each repeat the
+    bounded sample; the job's rate sums their counts over the slowest wall
+    time (here two processes on a small sample)."""
+    from paper_1511_07482_gb300 import synthetic
+    w = synthetic.small_case(n=300, d=2, M=[24, 20], seed=3, n_candidates=2)
+    v1, n1, d1 = bench.oracle_throughput(w, 0.3, 1)
+    v2, n2, d2 = bench.oracle_throughput(w, 0.3, 2)
+    assert n1 >= 2 and n2 >= 4 and d1 >= 0.3 and d2 >= 0.3
+    assert v1 == pytest.approx(n1 / d1) and v2 == pytest.approx(n2 / d2)
+
+
+def test_search_parity_checker_sees_a_wrong_evaluation():
+    """The check of the search kernel's records against the oracle: rows
+    holding the oracle's own LSCV and SCV values and gradients give errors at
+    rounding level, and one corrupted value is reported."""
+    import numpy as np
+    from oracle import binning, functionals as F, rules, selectors as S
+    from paper_1511_07482_gb300 import synthetic
+    w = synthetic.small_case(n=400, d=2, M=[30, 28], seed=5, n_candidates=2)
+    c = binning.bin_linear(w.X, w.lo, w.hi, w.M)
+    delta = rules.bin_width(w.lo, w.hi, w.M)
+    a = F.autocorr_fft(c)
+    rows = []
+    for m, H in [(0, w.H[0]), (1, w.H[1]), (0, w.H[1])]:
+        B = H if m == 0 else 2 * H + 2 * w.G
+        L = rules.support_L(rules.lambda_max(B), delta, w.M)
+        ev = lambda t: F.binned_direct(c, w.n, t, delta, L)
+        f, g = S.lscv(ev, H, w.n, grad=True) if m == 0 else S.scv(ev, H, w.G, w.n, grad=True)
+        rows.append([0, len(rows), m, H[0, 0], H[0, 1], H[1, 1], L[0], L[1], f, g[0, 0], g[0, 1], g[1, 1]])
+    R = np.array(rows)
+    out = bench.search_parity(w, R)
+    assert out["lscv"]["evaluations"] == 2 and out["scv"]["evaluations"] == 1
+    assert out["rel_err_max_search_lscv"] < 1e-10 and out["rel_err_max_search_scv"] < 1e-10
+    R[2, 9] *= 1.001
+    assert bench.search_parity(w, R)["rel_err_max_search_lscv"] > 1e-4
 
 
 def test_roofline_of_the_dominant_kernel(monkeypatch, tmp_path):

@@ -61,7 +61,9 @@ def test_oracle_imports_only_the_standard_library_and_numpy():
 
 
 def test_oracle_reached_only_where_allowed():
-    allowed = {os.path.join(ROOT, "bench.py"): {"oracle_evals"},
+    # bench.py: the oracle arm and the cpu_baseline leg's checks (oracle_evals,
+    # search_parity), reached from cpu_baseline and run_reference only
+    allowed = {os.path.join(ROOT, "bench.py"): {"oracle_evals", "search_parity"},
                os.path.join(ROOT, "__graft_entry__.py"): {"smoke"}}
     for path, fns in allowed.items():
         for mod, fn in _imports(path):
