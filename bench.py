@@ -233,6 +233,8 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx = Context(local)
     ctx.set_graphs(args.graphs == "on")
+    from paper_1511_07482_gb300 import ENGINE_AUTO, ENGINE_FFT, ENGINE_MULTIPASS
+    ctx.set_engine({"auto": ENGINE_AUTO, "fft": ENGINE_FFT, "multipass": ENGINE_MULTIPASS}[args.engine])
     stream = torch.cuda.current_stream(dev)
     if args.workload == "select2d":
         w = synthetic.mixture_2d_large(seed=rank_seed(2, rank))
@@ -248,7 +250,7 @@ def run_ours(args):
         workload_desc = (w.name + ": bin + full LSCV and SCV minimisation (3 free entries of H, adjoint "
                          "gradients)")
     elif args.workload == "psi4_3d":
-        w = synthetic.mixture_3d(seed=rank_seed(3, rank))
+        w = synthetic.mixture_3d(seed=rank_seed(3, rank), **({"n_candidates": args.candidates} if args.candidates else {}))
         X_dev = torch.from_numpy(w.X).to(dev)
         X_pin = torch.from_numpy(w.X).pin_memory()
 
@@ -303,7 +305,7 @@ def run_ours(args):
             return 5, None
         workload_desc = "normal-2d-n10000-M100: bin + Q_r (Eq. 32) for total derivative orders 0, 2, 4, 6, 8"
     else:  # plugin4d
-        w = synthetic.mixture_4d(seed=rank_seed(5, rank), n_candidates=16)
+        w = synthetic.mixture_4d(seed=rank_seed(5, rank), n_candidates=args.candidates or 16)
         X_dev = torch.from_numpy(w.X).to(dev)
         X_pin = torch.from_numpy(w.X).pin_memory()
         from paper_1511_07482_gb300 import P_FIXED
@@ -485,6 +487,66 @@ def search_records(ctx, w, dev, args):
     ds.close()
     R = rec.view(-1, 12).cpu().numpy()
     return R[np.isfinite(R[:, 0])]
+
+
+def crossover(args):
+    """Per-bandwidth device time of the lag-domain engine against the FFT
+    route (the transforms of Eqs. 19-24) as the support L grows, on the
+    benchmark datasets' shapes: LSCV with its gradient for 32 bandwidths per
+    call, the bandwidth set to a multiple of the identity chosen so that Eq. 26
+    gives the listed L on the first axis (the last rung is the untruncated
+    support L = M - 1).  Times are the library's CUDA events around every
+    kernel of a second, identical call (the count spectrum and
+    autocorrelation are cached by the first); one JSON object per rung."""
+    import torch
+    from paper_1511_07482_gb300 import ENGINE_AUTO, ENGINE_FFT, L_FULL, P_FIXED, Context, synthetic
+    torch.cuda.set_device(0)
+    cases = [("mixture-2d-n100000-M256", synthetic.mixture_2d_large(), {}, [8, 16, 32, 64, 128, 255]),
+             ("mixture-3d-n1000000-M128", synthetic.mixture_3d(n_candidates=4), {}, [4, 8, 16, 32, 64, 127]),
+             ("mixture-4d-n1000000-M48", synthetic.mixture_4d(n_candidates=4), {"P_rule": P_FIXED}, [4, 8, 16, 24, 47])]
+    per_dataset = ("acorr_f64", "stage_a_f64", "mid_f64", "final_f64", "bin")
+    rows = []
+    for name, w, extra, Ls in cases:
+        delta = (np.asarray(w.hi) - np.asarray(w.lo)) / (np.asarray(w.M) - 1)
+        for L in Ls:
+            full = L == w.M[0] - 1
+            lam = (L * delta[0] / 3.7) ** 2 * (0.999 if not full else 1.0)
+            Hs = np.stack([lam * np.eye(w.d)] * 32)
+            row = {"workload": name, "d": w.d, "M": list(w.M), "L_target": L}
+            for eng_name, eng in (("lag", ENGINE_AUTO), ("fft", ENGINE_FFT)):
+                ctx = Context(0)
+                ctx.set_engine(eng)
+                opts = dict(extra)
+                if "P_rule" in opts:
+                    opts["P_fixed"] = w.P
+                if full:
+                    opts["L_basis"] = L_FULL
+                ds = ctx.bin(w.X, w.lo, w.hi, w.M, **opts)
+                try:
+                    Lp, Pp = ds.plan(0, Hs[0])
+                    if extra.get("P_rule") is not None and any(p < m + l for p, m, l in zip(Pp, w.M, Lp)):
+                        row[eng_name] = None          # the fixed padding aliases at this support
+                        continue
+                    ds.lscv(Hs, grad=True)
+                    torch.cuda.synchronize()
+                    ctx.profile(1)
+                    ds.lscv(Hs, grad=True)
+                    torch.cuda.synchronize()
+                    ks, _, _, _ = ctx.profile_read()
+                    ctx.profile(0)
+                except Exception as e:       # noqa: BLE001 - reported in the row
+                    row[eng_name] = {"error": str(e)[:200]}
+                    continue
+                finally:
+                    ds.close()
+                    ctx.close()
+                ker = {k: v for k, v in ks.items() if not k.startswith("host:") and k not in per_dataset}
+                row.update({"L": Lp, "P": Pp})
+                row[eng_name] = {"us_per_bandwidth": 1000.0 * sum(v["ms"] for v in ker.values()) / len(Hs),
+                                 "kernels": sorted(ker)}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    return rows
 
 
 def batched_vs_single(ctx, w, dev, reps=5):
@@ -693,8 +755,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="oracle baseline budget: half on one core, half on every host core")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path line of the select2d workload")
+    ap.add_argument("--engine", choices=["auto", "fft", "multipass"], default="auto",
+                    help="evaluation engine of the library (auto: lag domain wherever the padding has no aliasing)")
+    ap.add_argument("--candidates", type=int, default=0,
+                    help="psi4_3d / plugin4d: number of candidate bandwidths (0: the configuration's)")
+    ap.add_argument("--crossover", action="store_true",
+                    help="print the lag-domain against FFT-route cost per bandwidth over the support L "
+                         "(one JSON object per rung) instead of the benchmark line")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.crossover:
+        crossover(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
