@@ -436,6 +436,15 @@ int kdefft_lscv_noalloc(int d, const int64_t* M, const double* delta, int64_t n,
                         const float* counts, const double* H, double tau,
                         void* stream, double* out);
 
+/* The radix schedule of the library's 1-D transforms of length P (Eqs.
+ * 19-22 on each axis): the fewest Stockham stages whose radices (at most
+ * max_radix; 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32)
+ * multiply to P, in the order the passes apply them.  radices: room for 16
+ * ints; *nstages receives their count.  Needs no GPU; shared by every
+ * context (the schedule cache is thread-safe).  Errors: KDEFFT_ERR_UNSUPPORTED
+ * for P outside [2, 4096] or not of the form 2^a 3^b 5^c. */
+int kdefft_radix_plan(int P, int max_radix, int* radices, int* nstages);
+
 /* Instrumentation (no paper counterpart).  kdefft_profile(ctx, mode):
  * mode 1 resets the counters and turns per-kernel timing on, 2 turns it on
  * without a reset, 0 resets and turns it off.  With timing on, every kernel

@@ -36,7 +36,7 @@ EXPORTS = [
     "kdefft_runtime_stats", "kdefft_autocorr", "kdefft_qr", "kdefft_lscv_r", "kdefft_eta_rs",
     "kdefft_kde_grid", "kdefft_ise_mixture", "kdefft_select_H_class", "kdefft_bin_many",
     "kdefft_select_H_multi", "kdefft_memory_stats", "kdefft_trim", "kdefft_set_search_record",
-    "kdefft_psi_grad",
+    "kdefft_psi_grad", "kdefft_radix_plan",
 ]
 ENGINE_AUTO, ENGINE_MULTIPASS, ENGINE_HOST_SELECT, ENGINE_FFT = 0, 1, 2, 3
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "kdefft_select_H_multi": (I, [P, I, P, P, P, I, I, P, P, P]),
         "kdefft_set_search_record": (I, [P, P, I64, I]),
         "kdefft_psi_grad": (I, [P, P, I, I, P, P]),
+        "kdefft_radix_plan": (I, [I, I, P, C.POINTER(C.c_int)]),
         "kdefft_strerror": (C.c_char_p, [I]),
         "kdefft_last_error": (C.c_char_p, []),
     }
@@ -195,6 +196,15 @@ def lscv_noalloc(M, delta, n, counts, H, out, tau=3.7, stream=None):
     _check(load().kdefft_lscv_noalloc(d, M_a.ctypes.data_as(C.c_void_p), pdl, int(n),
                                       C.c_void_p(counts.data_ptr()), pH, float(tau), C.c_void_p(stream),
                                       C.c_void_p(out.data_ptr())))
+
+
+def radix_plan(P: int, max_radix: int = 32):
+    """The radix schedule of the library's transforms of length P (no GPU
+    needed)."""
+    r = (C.c_int * 16)()
+    n = C.c_int()
+    _check(load().kdefft_radix_plan(int(P), int(max_radix), C.cast(r, C.c_void_p), C.byref(n)))
+    return [int(r[i]) for i in range(n.value)]
 
 
 def default_opts(**kw) -> Opts:

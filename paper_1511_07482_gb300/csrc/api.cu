@@ -481,6 +481,15 @@ static bool radix_plan_uncached(int P, AxisPlan& ap, int max_radix) {
     return true;
 }
 
+extern "C" int kdefft_radix_plan(int P, int max_radix, int* radices, int* nstages) {
+    if (!radices || !nstages) return fail(KDEFFT_ERR_ARG, "NULL argument");
+    AxisPlan ap{};
+    if (!radix_plan(P, ap, max_radix)) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix schedule for this length");
+    *nstages = ap.nst;
+    for (int i = 0; i < ap.nst; ++i) radices[i] = ap.radix[i];
+    return KDEFFT_OK;
+}
+
 static bool is_smooth(long long x) {
     if (x < 1) return false;
     for (int p : {2, 3, 5})

@@ -2043,18 +2043,22 @@ static cudaError_t launch_fused2d_r(const FusedItem<real>* items, int nitems, in
     cfg.numAttrs = 1;
     if (cs > 8) {
         // clusters above the portable size must be schedulable with this
-        // shared-memory footprint (checked once per footprint)
-        static size_t ok_bytes = 0, bad_bytes = ~(size_t)0;
-        if (sm > ok_bytes) {
-            if (sm >= bad_bytes) return cudaErrorNotSupported;
+        // shared-memory footprint (checked once per device, cluster size and
+        // footprint; the cache is shared by every context of the process)
+        static std::mutex mu;
+        static std::map<std::tuple<int, int, size_t>, bool> fits;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorNotSupported;
+        std::lock_guard<std::mutex> lk(mu);
+        const auto key = std::make_tuple(dev, cs, sm);
+        auto it = fits.find(key);
+        if (it == fits.end()) {
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, k_fused2d<real, R>, &cfg) != cudaSuccess || nclusters < 1) {
-                cudaGetLastError();
-                bad_bytes = std::min(bad_bytes, sm);
-                return cudaErrorNotSupported;
-            }
-            ok_bytes = sm;
+            bool ok = cudaOccupancyMaxActiveClusters(&nclusters, k_fused2d<real, R>, &cfg) == cudaSuccess && nclusters >= 1;
+            if (!ok) cudaGetLastError();
+            it = fits.emplace(key, ok).first;
         }
+        if (!it->second) return cudaErrorNotSupported;
     }
     return cudaLaunchKernelEx(&cfg, k_fused2d<real, R>, items, cs, gat_elems, spc_pad, cap, pmax, twpool, out,
                               errflag);
