@@ -504,7 +504,7 @@ def crossover(args):
     cases = [("mixture-2d-n100000-M256", synthetic.mixture_2d_large(), {}, [8, 16, 32, 64, 128, 255]),
              ("mixture-3d-n1000000-M128", synthetic.mixture_3d(n_candidates=4), {}, [4, 8, 16, 32, 64, 127]),
              ("mixture-4d-n1000000-M48", synthetic.mixture_4d(n_candidates=4), {"P_rule": P_FIXED}, [4, 8, 16, 24, 47])]
-    per_dataset = ("acorr_f64", "stage_a_f64", "mid_f64", "final_f64", "bin")
+    per_dataset = ("acorr", "spec_df", "stage_a_f64", "mid_f64", "final_f64", "bin")
     rows = []
     for name, w, extra, Ls in cases:
         delta = (np.asarray(w.hi) - np.asarray(w.lo)) / (np.asarray(w.M) - 1)

@@ -507,7 +507,7 @@ struct kdefft_ctx_s {
     int nsm = 1;
     std::map<int, int> tw_off;
     std::vector<double> tw_host;      // interleaved re, im
-    DevBuf tw32, tw64;
+    DevBuf tw32, tw64, twdf;          // twiddles in FP32, FP64 and FP32 pairs
     size_t tw_dev_n = 0;              // twiddles resident on the device
     DevBuf scratch, partial, items, tiles, out;
     HostBuf h_items, h_out;
@@ -545,6 +545,10 @@ struct kdefft_ctx_s {
     HostBuf h_binres;         // pinned outside count and moment partials of a binning
     cudaEvent_t acjobs_ev = nullptr;
     bool acjobs_free = true;
+    DevBuf specjobs;          // job table of the FP32-pair count-spectrum passes
+    HostBuf h_specjobs;       // its pinned staging copy, free once specjobs_ev has passed
+    cudaEvent_t specjobs_ev = nullptr;
+    bool specjobs_free = true;
     DevBuf binjobs;           // job tables of the batched binning
     DevBuf kdebuf;            // stencil table / outputs of the grid estimate and the mixture term
     std::map<std::string, KStat> kstat;
@@ -774,10 +778,17 @@ static int sync_twiddles(kdefft_ctx c) {
     KCU(cudaStreamSynchronize(c->stream));
     KCHK(c->tw64.ensure(n * sizeof(double2)));
     KCHK(c->tw32.ensure(n * sizeof(float2)));
-    std::vector<float> f(2 * n);
-    for (size_t i = 0; i < 2 * n; ++i) f[i] = (float)c->tw_host[i];
+    KCHK(c->twdf.ensure(n * sizeof(double2)));
+    std::vector<float> f(2 * n), fp(4 * n);
+    for (size_t i = 0; i < 2 * n; ++i) {
+        const double v = c->tw_host[i];
+        f[i] = (float)v;
+        fp[2 * i] = (float)v;                          // FP32 pair: leading part
+        fp[2 * i + 1] = (float)(v - (double)(float)v);  // and its remainder
+    }
     KCU(cudaMemcpy(c->tw64.p, c->tw_host.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
     KCU(cudaMemcpy(c->tw32.p, f.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    KCU(cudaMemcpy(c->twdf.p, fp.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
     c->tw_dev_n = n;
     return KDEFFT_OK;
 }
@@ -1778,6 +1789,137 @@ static int acorr_lines(int P, long long lines, int nsm) {
     return (int)std::min<long long>(nl, spread);
 }
 
+// Cache key of a count spectrum held as FP32 pairs (the autocorrelation input
+// of FP32 datasets): element size 8 as for FP64, told apart by this tag.
+static constexpr size_t kPairTag = 9;
+// Largest radix of the FP32-pair transforms.  A pair butterfly is a long
+// chain of dependent FP32 operations, so small radices (more threads busy
+// per stage, shorter chains) win: measured for the count spectrum and
+// autocorrelation of a 256^2 grid at P = 384 (n = 1e5), 42 µs with radices up
+// to 5, 55 µs up to 8, 84 µs up to 16 (the FP64 passes: 81 µs); 128^3 at
+// P = 180 (n = 1e6): 405, 406, 494 µs (FP64: 921 µs).
+static constexpr int kPairRadix = 5;
+
+// |F(c_zp)|^2 at padded P for FP32 datasets, in FP32-pair arithmetic: d
+// forward passes of k_spec_df per dataset, one launch per pass level for
+// every dataset of a dimension.  The first level transforms the last axis
+// of the FP32 counts (half spectrum), the middle levels the interior axes,
+// the last level axis 0 and writes |X|^2 in the spectrum layout
+// [w_{d-1}]..[w_1][w_0] that the autocorrelation passes read.  Intermediate
+// lines go through the context's two pass buffers (stream-ordered reuse).
+static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& need) {
+    struct Sj {
+        kdefft_ds ds;
+        std::array<int, 4> P;
+        std::vector<int> key;
+        std::shared_ptr<DevBuf> buf;
+        long long E[MAXD];   // frequencies kept per axis: P_k, the half spectrum on the last axis
+        size_t off, most;
+    };
+    std::vector<Sj> todo;
+    std::set<std::pair<kdefft_ds, std::vector<int>>> queued;
+    for (const auto& np : need) {
+        kdefft_ds ds = np.first;
+        std::vector<int> key = spectrum_key(ds, np.second.data(), kPairTag);
+        if (ds->spectra.count(key) || queued.count({ds, key})) continue;
+        queued.insert({ds, key});
+        Sj j{ds, np.second, key, std::make_shared<DevBuf>(&c->cache), {0, 0, 0, 0}, 0, 0};
+        KCHK(j.buf->ensure(sizeof(double) * spec_elems(ds->d, np.second.data())));
+        todo.push_back(std::move(j));
+    }
+    if (todo.empty()) return KDEFFT_OK;
+    size_t pool = 0;
+    for (Sj& j : todo) {
+        const int d = j.ds->d;
+        for (int k = 0; k < d; ++k) {
+            j.E[k] = (k == d - 1) ? j.P[k] / 2 + 1 : j.P[k];
+            twiddle_offset(c, j.P[k]);
+        }
+        // the largest intermediate: after the pass on axis k (k >= 1), the
+        // untransformed axes m < k hold M_m values and the others E_m
+        j.most = 0;
+        for (int k = d - 1; k >= 1; --k) {
+            long long e = 1;
+            for (int m = 0; m < d; ++m) e *= (m < k) ? j.ds->M[m] : j.E[m];
+            j.most = std::max(j.most, (size_t)e);
+        }
+        j.off = pool;
+        pool += (j.most + 1) & ~(size_t)1;
+    }
+    KCHK(sync_twiddles(c));
+    KCHK(c->acbuf[0].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
+    KCHK(c->acbuf[1].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
+    double2* pools[2] = {(double2*)c->acbuf[0].p, (double2*)c->acbuf[1].p};
+    std::vector<SpecJob> all;
+    struct Launch {
+        size_t slot;
+        int n;
+        long long blocks;
+        size_t sm;
+    };
+    std::vector<Launch> lv;
+    double fl = 0.0, by = 0.0;
+    for (int dim = 1; dim <= MAXD; ++dim) {
+        std::vector<size_t> sel;
+        for (size_t u = 0; u < todo.size(); ++u)
+            if (todo[u].ds->d == dim) sel.push_back(u);
+        if (sel.empty()) continue;
+        for (int lev = 0; lev < dim; ++lev) {
+            const int k = dim - 1 - lev;   // the axis of this level
+            const size_t slot = all.size();
+            all.resize(slot + sel.size());
+            for (size_t v = 0; v < sel.size(); ++v) {
+                const Sj& j = todo[sel[v]];
+                kdefft_ds ds = j.ds;
+                SpecJob& a = all[slot + v];
+                std::memset(&a, 0, sizeof(a));
+                a.d = dim;
+                a.in_f = (lev == 0) ? (const float*)ds->counts.p : nullptr;
+                a.in_c = (lev == 0) ? nullptr : (const void*)(pools[(lev - 1) & 1] + j.off);
+                long long O = 1, I = 1;
+                for (int m = 0; m < k; ++m) O *= ds->M[m];
+                for (int m = k + 1; m < dim; ++m) I *= j.E[m];
+                a.O = O;
+                a.I = I;
+                a.X = (int)ds->M[k];
+                a.Y = (int)j.E[k];
+                if (k == 0) {
+                    a.out_s = j.buf->p;
+                    for (int m = 1; m < dim; ++m) a.ext[m] = (int)j.E[m];
+                } else {
+                    a.out_c = (void*)(pools[lev & 1] + j.off);
+                }
+                a.ap.tw_off = twiddle_offset(c, j.P[k]);
+                if (!radix_plan(j.P[k], a.ap, kPairRadix)) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
+                a.nl = acorr_lines(j.P[k], O * I, c->nsm);
+                fl += 5.0 * j.P[k] * std::log2((double)j.P[k]) * (double)(O * I);
+                by += (lev == 0 ? 4.0 : 16.0) * (double)(O * I) * a.X + (k == 0 ? 8.0 : 16.0) * (double)(O * I) * a.Y;
+            }
+            Launch L{slot, (int)sel.size(), 0, 0};
+            KCU(spec_plan(all.data() + slot, L.n, &L.blocks, &L.sm));
+            lv.push_back(L);
+        }
+    }
+    KCHK(c->specjobs.ensure(sizeof(SpecJob) * all.size()));
+    if (!c->specjobs_free) KCU(cudaEventSynchronize(c->specjobs_ev));
+    KCHK(c->h_specjobs.ensure(sizeof(SpecJob) * all.size()));
+    std::memcpy(c->h_specjobs.p, all.data(), sizeof(SpecJob) * all.size());
+    SpecJob* jd = (SpecJob*)c->specjobs.p;
+    KCU(cudaMemcpyAsync(jd, c->h_specjobs.p, sizeof(SpecJob) * all.size(), cudaMemcpyHostToDevice, c->stream));
+    KCU(cudaEventRecord(c->specjobs_ev, c->stream));
+    c->specjobs_free = false;
+    c->h2d += (int64_t)(sizeof(SpecJob) * all.size());
+    cudaEvent_t ev = prof_start(c);
+    c->launches--;   // counted per launch below
+    for (const Launch& L : lv) {
+        c->launches++;
+        KCU(launch_spec_df(jd + L.slot, L.n, L.blocks, L.sm, c->twdf.p, c->stream));
+    }
+    prof_stop(c, ev, "spec_df", by, fl);
+    for (Sj& j : todo) j.ds->spectra[j.key] = j.buf;
+    return KDEFFT_OK;
+}
+
 static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& req) {
     HostTimer ht(c, "host:acorr");
     struct Job {
@@ -1785,7 +1927,7 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
         int A[4], P[4];
     };
     std::vector<Job> jobs;
-    std::vector<std::pair<kdefft_ds, std::array<int, 4>>> specs;
+    std::vector<std::pair<kdefft_ds, std::array<int, 4>>> specs, specs_df;
     for (const auto& rq : req) {
         kdefft_ds ds = rq.first;
         const int d = ds->d;
@@ -1800,9 +1942,12 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
             if (jb.P[k] > MAXP) return KDEFFT_ERR_UNSUPPORTED;
         }
         jobs.push_back(jb);
-        specs.push_back({ds, {jb.P[0], jb.P[1], jb.P[2], jb.P[3]}});
+        (ds->opts.precision == KDEFFT_FP64 ? specs : specs_df).push_back({ds, {jb.P[0], jb.P[1], jb.P[2], jb.P[3]}});
     }
-    if (!jobs.empty()) KCHK(ensure_spectra<double>(c, specs));
+    // FP64 datasets: the FP64 transforms; FP32 datasets: FP32 pairs (about 44
+    // bits, on the FP32 pipes), far beyond their FP32 counts' own rounding
+    if (!specs.empty()) KCHK(ensure_spectra<double>(c, specs));
+    if (!specs_df.empty()) KCHK(ensure_spectra_df(c, specs_df));
     for (const Job& jb : jobs)
         for (int k = 0; k < jb.ds->d; ++k) twiddle_offset(c, jb.P[k]);
     KCHK(sync_twiddles(c));
@@ -1829,7 +1974,8 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
         const int d = ds->d;
         const int* A = jb.A;
         const int* P = jb.P;
-        auto sit = ds->spectra.find(spectrum_key(ds, P, sizeof(double)));
+        const bool pairs = ds->opts.precision != KDEFFT_FP64;
+        auto sit = ds->spectra.find(spectrum_key(ds, P, pairs ? kPairTag : sizeof(double)));
         if (sit == ds->spectra.end()) return fail(KDEFFT_ERR_CUDA, "count spectrum missing");
         Plan& pl = plan[u];
         pl.S = (const double*)sit->second->p;
@@ -1879,12 +2025,14 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
             int n;
             long long blocks;
             size_t sm;
+            bool pairs;   // FP32-pair passes (FP32 datasets)
         };
         std::vector<Launch> lv;
+        for (int pr = 0; pr < 2; ++pr)
         for (int dim = 1; dim <= MAXD; ++dim) {
             std::vector<size_t> sel;
             for (size_t u = 0; u < jobs.size(); ++u)
-                if (jobs[u].ds->d == dim) sel.push_back(u);
+                if (jobs[u].ds->d == dim && (jobs[u].ds->opts.precision != KDEFFT_FP64) == (pr == 1)) sel.push_back(u);
             if (sel.empty()) continue;
             // level k of every selected dataset
             std::vector<long long> O(sel.size()), I(sel.size(), 1);
@@ -1909,7 +2057,8 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                     a.J = (k == 0) ? jb.A[0] + 1 : 2 * jb.A[k] + 1;
                     a.jlo = (k == 0) ? 0 : -jb.A[k];
                     a.ap.tw_off = twiddle_offset(c, jb.P[k]);
-                    if (!radix_plan(jb.P[k], a.ap, 16)) return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
+                    if (!radix_plan(jb.P[k], a.ap, pr == 1 ? kPairRadix : 16))
+                        return fail(KDEFFT_ERR_UNSUPPORTED, "no radix plan for P");
                     a.nl = acorr_lines(jb.P[k], a.O * a.I, c->nsm);
                     a.half = last ? 1 : 0;
                     a.scale = last ? 1.0 / pl.ptot : 1.0;
@@ -1920,7 +2069,7 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                         a.out_c = wr;
                     }
                 }
-                Launch L{slot, (int)sel.size(), 0, 0};
+                Launch L{slot, (int)sel.size(), 0, 0, pr == 1};
                 KCU(acorr_plan(all.data() + slot, L.n, &L.blocks, &L.sm));
                 lv.push_back(L);
                 for (size_t v = 0; v < sel.size(); ++v) {
@@ -1941,9 +2090,12 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
         c->launches--;   // counted per launch below
         for (const Launch& L : lv) {
             c->launches++;
-            KCU(launch_acorr(jd + L.slot, L.n, L.blocks, L.sm, tw, c->stream));
+            if (L.pairs)
+                KCU(launch_acorr_df(jd + L.slot, L.n, L.blocks, L.sm, c->twdf.p, c->stream));
+            else
+                KCU(launch_acorr(jd + L.slot, L.n, L.blocks, L.sm, tw, c->stream));
         }
-        prof_stop(c, ev, "acorr_f64", by, fl);
+        prof_stop(c, ev, "acorr", by, fl);
     }
     for (const Job& jb : jobs)
         for (int k = 0; k < 4; ++k) jb.ds->acA[k] = (k < jb.ds->d) ? jb.A[k] : 0;
@@ -2575,14 +2727,16 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
         return fail(KDEFFT_ERR_CUDA, "cudaGetDeviceProperties failed");
     }
     c->nsm = prop.multiProcessorCount;
-    for (DevBuf* b : {&c->tw32, &c->tw64, &c->scratch, &c->partial, &c->items, &c->tiles, &c->out, &c->sel_buf,
-                      &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf})
+    for (DevBuf* b : {&c->tw32, &c->tw64, &c->twdf, &c->scratch, &c->partial, &c->items, &c->tiles, &c->out,
+                      &c->sel_buf, &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf,
+                      &c->specjobs})
         b->gen = &c->buf_gen;
     c->h_items.gen = &c->buf_gen;
     c->h_out.gen = &c->buf_gen;
     c->h_binres.gen = &c->buf_gen;
     if (cudaEventCreateWithFlags(&c->staging_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->acjobs_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->acjobs_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->specjobs_ev, cudaEventDisableTiming) != cudaSuccess) {
         delete c;
         return fail(KDEFFT_ERR_CUDA, "event creation failed");
     }
@@ -2777,7 +2931,9 @@ int kdefft_destroy(kdefft_ctx c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->staging_ev) cudaEventDestroy(c->staging_ev);
     if (c->acjobs_ev) cudaEventDestroy(c->acjobs_ev);
+    if (c->specjobs_ev) cudaEventDestroy(c->specjobs_ev);
     c->h_acjobs.release();
+    c->h_specjobs.release();
     c->h_sel.release();
     c->h_binres.release();
     if (c->errflag) cudaFree(c->errflag);

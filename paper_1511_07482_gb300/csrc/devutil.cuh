@@ -51,6 +51,41 @@ __device__ __forceinline__ void df_acc(DFloat& a, float x) {
     a.l = e - (a.h - s.h);
 }
 
+// ---- an FP32 pair x = h + l with |l| <= ulp(h) / 2 as an arithmetic type
+// (about 44 significant bits), so that templated transforms can run on the
+// FP32 pipes where FP64 would be slow.  Sums renormalise through two-sum,
+// products through the fused multiply-add's exact rounding error; both keep
+// the error a few units of 2^-44 of the operands' magnitudes, which is what
+// a transform's error bound needs.  Constants come from double literals,
+// split at compile time.
+struct dflt {
+    float h, l;
+    __host__ __device__ constexpr dflt() : h(0.f), l(0.f) {}
+    __host__ __device__ constexpr dflt(float a, float b) : h(a), l(b) {}
+    __host__ __device__ constexpr explicit dflt(double v) : h((float)v), l((float)(v - (double)(float)v)) {}
+};
+__device__ __forceinline__ dflt operator+(dflt a, dflt b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
+    const float h = s + e;
+    return dflt(h, e - (h - s));
+}
+__device__ __forceinline__ dflt operator-(dflt a) { return dflt(-a.h, -a.l); }
+__device__ __forceinline__ dflt operator-(dflt a, dflt b) { return a + (-b); }
+__device__ __forceinline__ dflt operator*(dflt a, dflt b) {
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+    const float h = p + e;
+    return dflt(h, e - (h - p));
+}
+__device__ __forceinline__ double to_double(dflt a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double to_double(double a) { return a; }
+// complex FP32 pair: the layout and size of double2
+struct dcplx {
+    dflt x, y;
+};
+
 // per-thread accumulator of the spectral sums: DFloat in FP32 mode, double in FP64 mode
 template <typename real>
 struct SumAcc;

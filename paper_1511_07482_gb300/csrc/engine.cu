@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include <cooperative_groups.h>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -198,6 +199,22 @@ struct CxTw {
     }
 };
 
+// the same twiddles as FP32 pairs, split at compile time (no FP64
+// conversion at run time when the table is indexed)
+template <int R>
+struct CxTwPair {
+    float ch[R], cl[R], sh[R], sl[R];
+    constexpr CxTwPair() : ch(), cl(), sh(), sl() {
+        for (int m = 0; m < R; ++m) {
+            const CxCis z = cx_cis(m, R);
+            ch[m] = (float)z.c;
+            cl[m] = (float)(z.c - (double)(float)z.c);
+            sh[m] = (float)z.s;
+            sl[m] = (float)(z.s - (double)(float)z.s);
+        }
+    }
+};
+
 template <typename C, int R>
 struct Dft {
     __device__ __forceinline__ static void run(C* v) {
@@ -205,6 +222,7 @@ struct Dft {
         constexpr int A = cx_small_factor(R);
         constexpr int B = R / A;
         constexpr CxTw<R> tw{};
+        constexpr CxTwPair<R> tp{};
         C u[R];
         // A-point DFTs over b-strided subsequences: u[b * A + k1]
 #pragma unroll
@@ -220,7 +238,14 @@ struct Dft {
                     u[b * A + k1] = t[k1];
                 } else {
                     // t * exp(-2 pi i m / R) = t * (cos - i sin)
-                    const R_ cw = R_(tw.c[m]), sw = R_(tw.s[m]);
+                    R_ cw, sw;
+                    if constexpr (sizeof(R_) == 8 && !std::is_same<R_, double>::value) {   // FP32 pairs
+                        cw = R_(tp.ch[m], tp.cl[m]);
+                        sw = R_(tp.sh[m], tp.sl[m]);
+                    } else {
+                        cw = R_(tw.c[m]);
+                        sw = R_(tw.s[m]);
+                    }
                     u[b * A + k1] = C{t[k1].x * cw + t[k1].y * sw, t[k1].y * cw - t[k1].x * sw};
                 }
             }
@@ -629,7 +654,8 @@ __global__ void __launch_bounds__(256) k_final(const Item<real>* __restrict__ it
 //   sum_w x_w e^{+2 pi i w j / P} = conj(sum_w conj(x_w) e^{-2 pi i w j / P}).
 // Line l = o I + i of a pass reads (o, w, i) at (o W + w) I + i and writes
 // lag jj to (o J + jj) I + i; the real spectrum of the first pass has I = 1.
-__device__ __forceinline__ int acorr_job_of(const AcorrJob* __restrict__ jobs, int n, long long b) {
+template <typename J>
+__device__ __forceinline__ int job_of(const J* __restrict__ jobs, int n, long long b) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -641,44 +667,50 @@ __device__ __forceinline__ int acorr_job_of(const AcorrJob* __restrict__ jobs, i
     return lo;
 }
 
+// C: double2 (FP64) or dcplx (FP32 pairs, the same layout and size)
+template <typename C>
 __global__ void __launch_bounds__(256) k_acorr_fft(const AcorrJob* __restrict__ jobs, int njobs,
-                                                   const double2* __restrict__ twpool) {
+                                                   const C* __restrict__ twpool) {
+    using R = decltype(C{}.x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const AcorrJob& jb = jobs[acorr_job_of(jobs, njobs, blockIdx.x)];
+    const AcorrJob& jb = jobs[job_of(jobs, njobs, blockIdx.x)];
     const int P = jb.ap.P, W = jb.W, J = jb.J, cap = jb.nl;
     const long long I = jb.I;
-    double2* bufa = reinterpret_cast<double2*>(smem_raw);
-    double2* bufb = bufa + padded_cap(cap * P);
-    double2* tw = bufb + padded_cap(cap * P);
+    const R* in_r = reinterpret_cast<const R*>(jb.in_r);
+    const C* in_c = reinterpret_cast<const C*>(jb.in_c);
+    C* out_c = reinterpret_cast<C*>(jb.out_c);
+    C* bufa = reinterpret_cast<C*>(smem_raw);
+    C* bufb = bufa + padded_cap(cap * P);
+    C* tw = bufb + padded_cap(cap * P);
     const long long l0 = ((long long)blockIdx.x - jb.blk0) * cap;
     const int nl = (int)min((long long)cap, jb.O * I - l0);
     load_twiddles(tw, twpool, jb.ap);
-    auto hw = [&](int w) { return (jb.half && w != 0 && 2 * w != P) ? 2.0 : 1.0; };
+    auto hw = [&](int w) { return (jb.half && w != 0 && 2 * w != P) ? R(2.0) : R(1.0); };
     if (I == 1) {   // consecutive lines are rows: w fastest
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int c = t / P, w = t - c * P;
-            double2 x = make_double2(0.0, 0.0);
+            C x{R(0.0), R(0.0)};
             if (w < W) {
                 const long long at = (l0 + c) * W + w;
-                const double h = hw(w);
-                x = jb.in_r ? make_double2(h * jb.in_r[at], 0.0) : make_double2(h * jb.in_c[at].x, -h * jb.in_c[at].y);
+                const R h = hw(w);
+                x = in_r ? C{h * in_r[at], R(0.0)} : C{h * in_c[at].x, -(h * in_c[at].y)};
             }
             bufa[pad(t)] = x;
         }
     } else {        // consecutive lines are consecutive i: line fastest
         for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
             const int w = t / nl, c = t - w * nl;
-            double2 x = make_double2(0.0, 0.0);
+            C x{R(0.0), R(0.0)};
             if (w < W) {
                 const long long l = l0 + c, o = l / I, i = l - o * I;
-                const double2 v = jb.in_c[(o * W + w) * I + i];
-                const double h = hw(w);
-                x = make_double2(h * v.x, -h * v.y);
+                const C v = in_c[(o * W + w) * I + i];
+                const R h = hw(w);
+                x = C{h * v.x, -(h * v.y)};
             }
             bufa[pad(c * P + w)] = x;
         }
     }
-    const double2* Y = smem_fft(bufa, bufb, nl, jb.ap, tw);
+    const C* Y = smem_fft(bufa, bufb, nl, jb.ap, tw);
     for (int t = threadIdx.x; t < nl * J; t += blockDim.x) {
         int c, jj;
         if (I == 1) {
@@ -690,14 +722,83 @@ __global__ void __launch_bounds__(256) k_acorr_fft(const AcorrJob* __restrict__ 
         }
         int j = (jb.jlo + jj) % P;
         if (j < 0) j += P;
-        const double2 y = Y[pad(c * P + j)];
+        const C y = Y[pad(c * P + j)];
         const long long l = l0 + c, o = l / I, i = l - o * I;
         const long long at = (o * J + jj) * I + i;
         if (jb.out_r) {
-            jb.out_r[at] = y.x * jb.scale;
-            if (jb.out_r32) jb.out_r32[at] = (float)(y.x * jb.scale);
+            const double v = to_double(y.x) * jb.scale;
+            jb.out_r[at] = v;
+            if (jb.out_r32) jb.out_r32[at] = (float)v;
         } else {
-            jb.out_c[at] = make_double2(y.x, -y.y);
+            out_c[at] = C{y.x, -y.y};
+        }
+    }
+}
+
+// Forward passes of the count spectrum in FP32 pairs (SpecJob).
+__global__ void __launch_bounds__(256) k_spec_df(const SpecJob* __restrict__ jobs, int njobs,
+                                                 const dcplx* __restrict__ twpool) {
+    using C = dcplx;
+    using R = dflt;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SpecJob& jb = jobs[job_of(jobs, njobs, blockIdx.x)];
+    const int P = jb.ap.P, X = jb.X, Yn = jb.Y, cap = jb.nl;
+    const long long I = jb.I;
+    const C* in_c = reinterpret_cast<const C*>(jb.in_c);
+    C* bufa = reinterpret_cast<C*>(smem_raw);
+    C* bufb = bufa + padded_cap(cap * P);
+    C* tw = bufb + padded_cap(cap * P);
+    const long long l0 = ((long long)blockIdx.x - jb.blk0) * cap;
+    const int nl = (int)min((long long)cap, jb.O * I - l0);
+    load_twiddles(tw, twpool, jb.ap);
+    if (I == 1) {   // rows: x fastest
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int c = t / P, x = t - c * P;
+            C v{R(0.0), R(0.0)};
+            if (x < X) {
+                const long long at = (l0 + c) * X + x;
+                v = jb.in_f ? C{R(jb.in_f[at], 0.f), R(0.0)} : in_c[at];
+            }
+            bufa[pad(t)] = v;
+        }
+    } else {        // line fastest
+        for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
+            const int x = t / nl, c = t - x * nl;
+            C v{R(0.0), R(0.0)};
+            if (x < X) {
+                const long long l = l0 + c, o = l / I, i = l - o * I;
+                const long long at = (o * X + x) * I + i;
+                v = jb.in_f ? C{R(jb.in_f[at], 0.f), R(0.0)} : in_c[at];
+            }
+            bufa[pad(c * P + x)] = v;
+        }
+    }
+    const C* Yb = smem_fft(bufa, bufb, nl, jb.ap, tw);
+    C* out_c = reinterpret_cast<C*>(jb.out_c);
+    R* out_s = reinterpret_cast<R*>(jb.out_s);
+    for (int t = threadIdx.x; t < nl * Yn; t += blockDim.x) {
+        int c, y;
+        if (I == 1) {
+            c = t / Yn;
+            y = t - c * Yn;
+        } else {
+            y = t / nl;
+            c = t - y * nl;
+        }
+        const C v = Yb[pad(c * P + y)];
+        const long long l = l0 + c, o = l / I, i = l - o * I;
+        if (out_c) {
+            out_c[(o * Yn + y) * I + i] = v;
+        } else {
+            // |X|^2 at the inner index reordered with w_{d-1} slowest
+            long long r = i, q = 0;
+            int wv[MAXD];
+            for (int m = jb.d - 1; m >= 1; --m) {
+                wv[m] = (int)(r % jb.ext[m]);
+                r /= jb.ext[m];
+            }
+            for (int m = jb.d - 1; m >= 1; --m) q = q * jb.ext[m] + wv[m];
+            out_s[q * P + y] = v.x * v.x + v.y * v.y;
         }
     }
 }
@@ -719,10 +820,42 @@ cudaError_t acorr_plan(AcorrJob* jobs_h, int n, long long* blocks_out, size_t* s
     return cudaSuccess;
 }
 
+cudaError_t spec_plan(SpecJob* jobs_h, int n, long long* blocks_out, size_t* sm_out) {
+    long long blocks = 0;
+    size_t sm = 0;
+    for (int k = 0; k < n; ++k) {
+        SpecJob& jb = jobs_h[k];
+        if (jb.nl < 1 || jb.ap.P < 2 || jb.X > jb.ap.P || jb.Y > jb.ap.P || (!jb.in_f && !jb.in_c) ||
+            (!jb.out_c && !jb.out_s) || (jb.out_s && jb.O != 1) || jb.d < 1 || jb.d > MAXD)
+            return cudaErrorInvalidValue;
+        jb.blk0 = blocks;
+        blocks += (jb.O * jb.I + jb.nl - 1) / jb.nl;
+        sm = std::max(sm, acorr_smem_bytes(jb.ap.P, jb.nl));
+    }
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    *blocks_out = blocks;
+    *sm_out = sm;
+    return cudaSuccess;
+}
+
 cudaError_t launch_acorr(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const double2* twpool,
                          cudaStream_t st) {
     if (n <= 0 || blocks <= 0) return cudaSuccess;
-    k_acorr_fft<<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, twpool);
+    k_acorr_fft<double2><<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, twpool);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acorr_df(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const void* twpool,
+                            cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    k_acorr_fft<dcplx><<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, (const dcplx*)twpool);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_df(const SpecJob* jobs_d, int n, long long blocks, size_t sm, const void* twpool,
+                           cudaStream_t st) {
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    k_spec_df<<<(unsigned)blocks, 256, sm, st>>>(jobs_d, n, (const dcplx*)twpool);
     return cudaGetLastError();
 }
 
@@ -2096,7 +2229,8 @@ cudaError_t prepare_kernels() {
     const void* dyn[] = {(const void*)k_stage_a<float>,    (const void*)k_stage_a<double>,
                          (const void*)k_mid<float>,        (const void*)k_mid<double>,
                          (const void*)k_final<float>,      (const void*)k_final<double>,
-                         (const void*)k_acorr_fft,         (const void*)k_select2d_lag<1>,
+                         (const void*)k_acorr_fft<double2>, (const void*)k_acorr_fft<dcplx>,
+                         (const void*)k_spec_df,           (const void*)k_select2d_lag<1>,
                          (const void*)k_select2d_lag<2>,   (const void*)k_select2d_lag<4>,
                          (const void*)k_select2d,          (const void*)k_fused2d<float, 2>,
                          (const void*)k_fused2d<float, 4>, (const void*)k_fused2d<double, 2>};

@@ -285,6 +285,37 @@ __host__ __device__ constexpr size_t acorr_smem_bytes(int P, int nl) {
 cudaError_t acorr_plan(AcorrJob* jobs_h, int n, long long* blocks, size_t* sm);
 cudaError_t launch_acorr(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const double2* twpool,
                          cudaStream_t st);
+// The same passes in FP32-pair arithmetic (FP32 datasets): the pointers of
+// the jobs then hold FP32 pairs of the same sizes (in_r: the spectrum as
+// pairs; in_c / out_c: complex pairs); out_r / out_r32 stay FP64 / FP32.
+// twpool: the twiddles as complex FP32 pairs.
+cudaError_t launch_acorr_df(const AcorrJob* jobs_d, int n, long long blocks, size_t sm, const void* twpool,
+                            cudaStream_t st);
+
+// One forward pass of the count spectrum |F(c_zp)|^2 in FP32-pair arithmetic
+// (FP32 datasets), for one dataset: lines O I, element (o, x, i) at
+// (o X + x) I + i for x < X (the grid's M_k values along the axis, zero-
+// extended to P), its forward DFT of length P, the first Y frequencies kept.
+// The first pass reads the FP32 counts (in_f, rows: I = 1) and keeps the
+// half spectrum; the others read complex pairs (in_c).  A pass before the
+// last writes (o, y, i) at (o Y + y) I + i (out_c); the last (axis 0, O = 1)
+// writes |X_y|^2 as an FP32 pair to out_s at q P + y, q the inner index
+// (w_1 .. w_{d-1}, extents ext[1..d-1], w_{d-1} fastest) reordered with
+// w_{d-1} slowest: the layout the autocorrelation passes read.
+struct SpecJob {
+    const float* in_f;
+    const void* in_c;
+    void* out_c;
+    void* out_s;
+    long long O, I;
+    int X, Y, nl, d;
+    int ext[MAXD];
+    AxisPlan ap;
+    long long blk0;
+};
+cudaError_t spec_plan(SpecJob* jobs_h, int n, long long* blocks, size_t* sm);
+cudaError_t launch_spec_df(const SpecJob* jobs_d, int n, long long blocks, size_t sm, const void* twpool,
+                           cudaStream_t st);
 
 // ---- kernel density estimate on the grid and mixture cross term (kde.cu)
 struct KdeDesc {
