@@ -128,8 +128,10 @@ def _check(code):
 
 
 def _host_f64(a):
+    """(contiguous FP64 copy or view, its address as an int: what a
+    c_void_p argument takes, without building a ctypes object per call)."""
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
-    return a, a.ctypes.data_as(C.c_void_p)
+    return a, a.ctypes.data
 
 
 def _mat(a, d, what):
@@ -153,7 +155,7 @@ def _vec(a, d, what, dtype=np.float64):
 
 
 def _ptr_of(x):
-    """(keepalive, pointer) for an n x d sample: a numpy array or a torch
+    """(keepalive, address) for an n x d sample: a numpy array or a torch
     tensor (host or CUDA)."""
     try:
         import torch
@@ -163,7 +165,7 @@ def _ptr_of(x):
             if x.dim() != 2:
                 raise ValueError(f"the sample must be n x d, got shape {tuple(x.shape)}")
             x = x.contiguous()
-            return x, C.c_void_p(x.data_ptr())
+            return x, x.data_ptr()
     except ImportError:
         pass
     arr, p = _host_f64(x)
@@ -181,7 +183,7 @@ def lscv_noalloc(M, delta, n, counts, H, out, tau=3.7, stream=None):
     d = len(M)
     M_a = _vec(M, d, "M", np.int64)
     dl = _vec(delta, d, "delta")
-    pdl = dl.ctypes.data_as(C.c_void_p)
+    pdl = dl.ctypes.data
     Ha, pH = _mat(H, d, "H")
     if not (isinstance(counts, torch.Tensor) and counts.is_cuda and counts.dtype == torch.float32):
         raise TypeError("counts must be a CUDA float32 tensor")
@@ -193,7 +195,7 @@ def lscv_noalloc(M, delta, n, counts, H, out, tau=3.7, stream=None):
         raise ValueError(f"out must be a contiguous tensor of at least {1 + d * d} values")
     if stream is None:
         stream = torch.cuda.current_stream(out.device).cuda_stream
-    _check(load().kdefft_lscv_noalloc(d, M_a.ctypes.data_as(C.c_void_p), pdl, int(n),
+    _check(load().kdefft_lscv_noalloc(d, M_a.ctypes.data, pdl, int(n),
                                       C.c_void_p(counts.data_ptr()), pH, float(tau), C.c_void_p(stream),
                                       C.c_void_p(out.data_ptr())))
 
@@ -205,6 +207,21 @@ def radix_plan(P: int, max_radix: int = 32):
     n = C.c_int()
     _check(load().kdefft_radix_plan(int(P), int(max_radix), C.cast(r, C.c_void_p), C.byref(n)))
     return [int(r[i]) for i in range(n.value)]
+
+
+_DEFAULT_OPTS = None
+
+
+def _opts(**kw) -> Opts:
+    """Options for a call: without fields one shared, never-modified
+    instance of the defaults (the library only reads the options it is
+    given), else a fresh default_opts(**kw)."""
+    global _DEFAULT_OPTS
+    if kw:
+        return default_opts(**kw)
+    if _DEFAULT_OPTS is None:
+        _DEFAULT_OPTS = default_opts()
+    return _DEFAULT_OPTS
 
 
 def default_opts(**kw) -> Opts:
@@ -324,11 +341,11 @@ class Context:
         n, d = int(keep.shape[0]), int(keep.shape[1])
         lo_a = _vec(lo, d, "lo")
         hi_a = _vec(hi, d, "hi")
-        plo, phi = lo_a.ctypes.data_as(C.c_void_p), hi_a.ctypes.data_as(C.c_void_p)
+        plo, phi = lo_a.ctypes.data, hi_a.ctypes.data
         M_a = _vec(M, d, "M", np.int64)
-        o = default_opts(**opts)
+        o = _opts(**opts)
         h = C.c_void_p()
-        _check(load().kdefft_bin(self.h, px, n, d, plo, phi, M_a.ctypes.data_as(C.c_void_p), C.byref(o),
+        _check(load().kdefft_bin(self.h, px, n, d, plo, phi, M_a.ctypes.data, C.byref(o),
                                  C.byref(h)))
         ds = Dataset(self, h, d, [int(m) for m in M_a])
         self._datasets.add(ds)
@@ -349,11 +366,11 @@ class Context:
         lo = np.ascontiguousarray(np.asarray(los, dtype=np.float64).reshape(nds, d))
         hi = np.ascontiguousarray(np.asarray(his, dtype=np.float64).reshape(nds, d))
         M = np.ascontiguousarray(np.asarray(Ms, dtype=np.int64).reshape(nds, d))
-        o = default_opts(**opts)
+        o = _opts(**opts)
         hs = (C.c_void_p * nds)()
-        _check(load().kdefft_bin_many(self.h, nds, C.cast(ptrs, C.c_void_p), n.ctypes.data_as(C.c_void_p), d,
-                                      lo.ctypes.data_as(C.c_void_p), hi.ctypes.data_as(C.c_void_p),
-                                      M.ctypes.data_as(C.c_void_p), C.byref(o), C.cast(hs, C.c_void_p)))
+        _check(load().kdefft_bin_many(self.h, nds, C.cast(ptrs, C.c_void_p), n.ctypes.data, d,
+                                      lo.ctypes.data, hi.ctypes.data,
+                                      M.ctypes.data, C.byref(o), C.cast(hs, C.c_void_p)))
         out = []
         for i in range(nds):
             ds = Dataset(self, C.c_void_p(hs[i]), d, [int(m) for m in M[i]])
@@ -374,9 +391,9 @@ class Context:
         val = np.zeros(tot)
         g = np.zeros((tot, d, d)) if grad else None
         arr = (C.c_void_p * len(datasets))(*[ds.h for ds in datasets])
-        _check(lib.kdefft_batch_lscv(self.h, len(datasets), arr, nh.ctypes.data_as(C.c_void_p),
-                                     H.ctypes.data_as(C.c_void_p), val.ctypes.data_as(C.c_void_p),
-                                     g.ctypes.data_as(C.c_void_p) if grad else None))
+        _check(lib.kdefft_batch_lscv(self.h, len(datasets), arr, nh.ctypes.data,
+                                     H.ctypes.data, val.ctypes.data,
+                                     g.ctypes.data if grad else None))
         return (val, g) if grad else val
 
 
@@ -396,7 +413,7 @@ class Dataset:
             pass
 
     def set_opts(self, **opts):
-        o = default_opts(**opts)
+        o = _opts(**opts)
         _check(load().kdefft_ds_set_opts(self.h, C.byref(o)))
 
     def info(self):
@@ -407,7 +424,7 @@ class Dataset:
     def counts(self, dtype=DT_F64):
         np_t = {DT_F32: np.float32, DT_F64: np.float64, DT_I32: np.int32}[dtype]
         out = np.zeros(self.M, dtype=np_t)
-        _check(load().kdefft_counts(self.h, out.ctypes.data_as(C.c_void_p), dtype))
+        _check(load().kdefft_counts(self.h, out.ctypes.data, dtype))
         return out
 
     def plan(self, method, H, G=None):
@@ -415,8 +432,8 @@ class Dataset:
         Ga, pG = _opt_mat(G, self.d, "G")
         L = np.zeros(self.d, dtype=np.int32)
         P = np.zeros(self.d, dtype=np.int32)
-        _check(load().kdefft_plan(self.h, method, pH, pG, L.ctypes.data_as(C.c_void_p),
-                                  P.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_plan(self.h, method, pH, pG, L.ctypes.data,
+                                  P.ctypes.data))
         return [int(v) for v in L], [int(v) for v in P]
 
     def _Hs(self, H):
@@ -429,7 +446,7 @@ class Dataset:
         out = np.zeros((nH, self.d ** r))
         if nH == 0:
             return out
-        _check(load().kdefft_psi(self.h, H.ctypes.data_as(C.c_void_p), nH, r, out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_psi(self.h, H.ctypes.data, nH, r, out.ctypes.data))
         return out
 
     def psi_grad(self, H, r, w):
@@ -442,8 +459,8 @@ class Dataset:
         out = np.zeros((nH, self.d, self.d))
         if nH == 0:
             return out
-        _check(load().kdefft_psi_grad(self.h, H.ctypes.data_as(C.c_void_p), nH, int(r),
-                                      wa.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_psi_grad(self.h, H.ctypes.data, nH, int(r),
+                                      wa.ctypes.data, out.ctypes.data))
         return out
 
     def lscv(self, H, grad=False):
@@ -452,8 +469,8 @@ class Dataset:
         g = np.zeros((nH, self.d, self.d)) if grad else None
         if nH == 0:
             return (val, g) if grad else val
-        _check(load().kdefft_lscv(self.h, H.ctypes.data_as(C.c_void_p), nH, val.ctypes.data_as(C.c_void_p),
-                                  g.ctypes.data_as(C.c_void_p) if grad else None))
+        _check(load().kdefft_lscv(self.h, H.ctypes.data, nH, val.ctypes.data,
+                                  g.ctypes.data if grad else None))
         return (val, g) if grad else val
 
     def scv(self, H, G, grad=False):
@@ -463,8 +480,8 @@ class Dataset:
         g = np.zeros((nH, self.d, self.d)) if grad else None
         if nH == 0:
             return (val, g) if grad else val
-        _check(load().kdefft_scv(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
-                                 g.ctypes.data_as(C.c_void_p) if grad else None))
+        _check(load().kdefft_scv(self.h, H.ctypes.data, nH, pG, val.ctypes.data,
+                                 g.ctypes.data if grad else None))
         return (val, g) if grad else val
 
     def pi(self, H, G, grad=False):
@@ -474,8 +491,8 @@ class Dataset:
         g = np.zeros((nH, self.d, self.d)) if grad else None
         if nH == 0:
             return (val, g) if grad else val
-        _check(load().kdefft_pi(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p),
-                                g.ctypes.data_as(C.c_void_p) if grad else None))
+        _check(load().kdefft_pi(self.h, H.ctypes.data, nH, pG, val.ctypes.data,
+                                g.ctypes.data if grad else None))
         return (val, g) if grad else val
 
     def autocorr(self, A):
@@ -485,7 +502,7 @@ class Dataset:
         A_a = np.ascontiguousarray(np.asarray(A, dtype=np.int32).reshape(self.d))
         shape = tuple(2 * int(a) + 1 for a in A_a[1:][::-1]) + (int(A_a[0]) + 1,)
         out = np.zeros(shape)
-        _check(load().kdefft_autocorr(self.h, A_a.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_autocorr(self.h, A_a.ctypes.data, out.ctypes.data))
         return out
 
     def qr(self, Sigma, r):
@@ -495,7 +512,7 @@ class Dataset:
         out = np.zeros(nS)
         if nS == 0:
             return out
-        _check(load().kdefft_qr(self.h, S.ctypes.data_as(C.c_void_p), nS, int(r), out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_qr(self.h, S.ctypes.data, nS, int(r), out.ctypes.data))
         return out
 
     def eta_rs(self, Sigma, r, s, A=None, B=None):
@@ -507,15 +524,15 @@ class Dataset:
         out = np.zeros(nS)
         if nS == 0:
             return out
-        _check(load().kdefft_eta_rs(self.h, pA, pB, S.ctypes.data_as(C.c_void_p), nS, int(r), int(s),
-                                    out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_eta_rs(self.h, pA, pB, S.ctypes.data, nS, int(r), int(s),
+                                    out.ctypes.data))
         return out
 
     def kde_grid(self, H):
         """The binned kernel density estimate at every grid node (shape M)."""
         Ha, pH = _mat(H, self.d, "H")
         out = np.zeros(self.M)
-        _check(load().kdefft_kde_grid(self.h, pH, out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_kde_grid(self.h, pH, out.ctypes.data))
         return out
 
     def ise_mixture(self, H, weights, means, covs):
@@ -528,9 +545,9 @@ class Dataset:
         out = np.zeros(nH)
         if nH == 0:
             return out
-        _check(load().kdefft_ise_mixture(self.h, H.ctypes.data_as(C.c_void_p), nH, len(w),
-                                         w.ctypes.data_as(C.c_void_p), mu.ctypes.data_as(C.c_void_p),
-                                         S.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_ise_mixture(self.h, H.ctypes.data, nH, len(w),
+                                         w.ctypes.data, mu.ctypes.data,
+                                         S.ctypes.data, out.ctypes.data))
         return out
 
     def lscv_r(self, H, r):
@@ -540,7 +557,7 @@ class Dataset:
         out = np.zeros(nH)
         if nH == 0:
             return out
-        _check(load().kdefft_lscv_r(self.h, H.ctypes.data_as(C.c_void_p), nH, int(r), out.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_lscv_r(self.h, H.ctypes.data, nH, int(r), out.ctypes.data))
         return out
 
     def eta02(self, H, G):
@@ -549,7 +566,7 @@ class Dataset:
         val = np.zeros(nH)
         if nH == 0:
             return val
-        _check(load().kdefft_eta02(self.h, H.ctypes.data_as(C.c_void_p), nH, pG, val.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_eta02(self.h, H.ctypes.data, nH, pG, val.ctypes.data))
         return val
 
     def select_H(self, method=LSCV, H0=None, G=None, n_starts=1, max_iter=None, optimizer="bfgs", hclass="full"):
@@ -572,11 +589,11 @@ class Dataset:
         if hclass == "full":
             fn = lib.kdefft_select_H if optimizer == "bfgs" else lib.kdefft_select_H_nm
             _check(fn(self.h, method, pH, pG, int(n_starts), int(max_iter or 0),
-                      Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
+                      Hout.ctypes.data, C.byref(f), C.byref(ne)))
         else:
             _check(lib.kdefft_select_H_class(self.h, method, classes[hclass], 0 if optimizer == "bfgs" else 1, pH,
                                              pG, int(n_starts), int(max_iter or 0),
-                                             Hout.ctypes.data_as(C.c_void_p), C.byref(f), C.byref(ne)))
+                                             Hout.ctypes.data, C.byref(f), C.byref(ne)))
         return Hout, f.value, ne.value
 
     def select_H_many(self, methods, H0=None, G=None, n_starts=1, max_iter=None):
@@ -590,7 +607,7 @@ class Dataset:
         Hout = np.zeros((k, self.d, self.d))
         f = np.zeros(k)
         ne = np.zeros(k, dtype=np.int64)
-        _check(load().kdefft_select_H_multi(self.h, k, ms.ctypes.data_as(C.c_void_p), pH, pG, int(n_starts),
-                                            int(max_iter or 0), Hout.ctypes.data_as(C.c_void_p),
-                                            f.ctypes.data_as(C.c_void_p), ne.ctypes.data_as(C.c_void_p)))
+        _check(load().kdefft_select_H_multi(self.h, k, ms.ctypes.data, pH, pG, int(n_starts),
+                                            int(max_iter or 0), Hout.ctypes.data,
+                                            f.ctypes.data, ne.ctypes.data))
         return [(Hout[m], float(f[m]), int(ne[m])) for m in range(k)]

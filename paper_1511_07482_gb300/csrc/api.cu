@@ -510,6 +510,7 @@ struct kdefft_ctx_s {
     DevBuf tw32, tw64, twdf;          // twiddles in FP32, FP64 and FP32 pairs
     size_t tw_dev_n = 0;              // twiddles resident on the device
     DevBuf scratch, partial, items, tiles, out;
+    DevBuf lagcnt;                    // per-item tile counters of the lag launches
     HostBuf h_items, h_out;
     // lag-domain results on their way to h_out, not yet read: run_lag returns
     // without waiting, and flush_reads (at the end of run()) waits once for
@@ -1807,7 +1808,23 @@ static constexpr int kPairRadix = 5;
 // the last level axis 0 and writes |X|^2 in the spectrum layout
 // [w_{d-1}]..[w_1][w_0] that the autocorrelation passes read.  Intermediate
 // lines go through the context's two pass buffers (stream-ordered reuse).
-static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& need) {
+// The launches of a batch of FP32-pair count-spectrum passes, whose job table
+// is already on its way to the device: issued by the caller (in one graph
+// with the autocorrelation passes that read the spectra).
+struct SpecLaunches {
+    const SpecJob* jd = nullptr;
+    struct L {
+        size_t slot;
+        int n;
+        long long blocks;
+        size_t sm;
+    };
+    std::vector<L> lv;
+    double by = 0.0, fl = 0.0;
+};
+
+static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& need,
+                             SpecLaunches& sl) {
     struct Sj {
         kdefft_ds ds;
         std::array<int, 4> P;
@@ -1851,14 +1868,9 @@ static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds
     KCHK(c->acbuf[1].ensure(sizeof(double2) * std::max<size_t>(pool, 1)));
     double2* pools[2] = {(double2*)c->acbuf[0].p, (double2*)c->acbuf[1].p};
     std::vector<SpecJob> all;
-    struct Launch {
-        size_t slot;
-        int n;
-        long long blocks;
-        size_t sm;
-    };
-    std::vector<Launch> lv;
-    double fl = 0.0, by = 0.0;
+    std::vector<SpecLaunches::L>& lv = sl.lv;
+    double& fl = sl.fl;
+    double& by = sl.by;
     for (int dim = 1; dim <= MAXD; ++dim) {
         std::vector<size_t> sel;
         for (size_t u = 0; u < todo.size(); ++u)
@@ -1895,7 +1907,7 @@ static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds
                 fl += 5.0 * j.P[k] * std::log2((double)j.P[k]) * (double)(O * I);
                 by += (lev == 0 ? 4.0 : 16.0) * (double)(O * I) * a.X + (k == 0 ? 8.0 : 16.0) * (double)(O * I) * a.Y;
             }
-            Launch L{slot, (int)sel.size(), 0, 0};
+            SpecLaunches::L L{slot, (int)sel.size(), 0, 0};
             KCU(spec_plan(all.data() + slot, L.n, &L.blocks, &L.sm));
             lv.push_back(L);
         }
@@ -1909,13 +1921,9 @@ static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds
     KCU(cudaEventRecord(c->specjobs_ev, c->stream));
     c->specjobs_free = false;
     c->h2d += (int64_t)(sizeof(SpecJob) * all.size());
-    cudaEvent_t ev = prof_start(c);
-    c->launches--;   // counted per launch below
-    for (const Launch& L : lv) {
-        c->launches++;
-        KCU(launch_spec_df(jd + L.slot, L.n, L.blocks, L.sm, c->twdf.p, c->stream));
-    }
-    prof_stop(c, ev, "spec_df", by, fl);
+    sl.jd = jd;
+    // the spectra are registered now; the caller issues their passes before
+    // any launch that reads them
     for (Sj& j : todo) j.ds->spectra[j.key] = j.buf;
     return KDEFFT_OK;
 }
@@ -1947,7 +1955,8 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
     // FP64 datasets: the FP64 transforms; FP32 datasets: FP32 pairs (about 44
     // bits, on the FP32 pipes), far beyond their FP32 counts' own rounding
     if (!specs.empty()) KCHK(ensure_spectra<double>(c, specs));
-    if (!specs_df.empty()) KCHK(ensure_spectra_df(c, specs_df));
+    SpecLaunches sl;
+    if (!specs_df.empty()) KCHK(ensure_spectra_df(c, specs_df, sl));
     for (const Job& jb : jobs)
         for (int k = 0; k < jb.ds->d; ++k) twiddle_offset(c, jb.P[k]);
     KCHK(sync_twiddles(c));
@@ -2086,16 +2095,38 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
         KCU(cudaMemcpyAsync(jd, c->h_acjobs.p, sizeof(AcorrJob) * all.size(), cudaMemcpyHostToDevice, c->stream));
         KCU(cudaEventRecord(c->acjobs_ev, c->stream));
         c->acjobs_free = false;
-        cudaEvent_t ev = prof_start(c);
-        c->launches--;   // counted per launch below
-        for (const Launch& L : lv) {
-            c->launches++;
-            if (L.pairs)
-                KCU(launch_acorr_df(jd + L.slot, L.n, L.blocks, L.sm, c->twdf.p, c->stream));
-            else
-                KCU(launch_acorr(jd + L.slot, L.n, L.blocks, L.sm, tw, c->stream));
-        }
-        prof_stop(c, ev, "acorr", by, fl);
+        // the count-spectrum passes (FP32 datasets) and the autocorrelation
+        // passes in one launch sequence, replayed as a CUDA graph when its
+        // tables, sizes and launch shapes repeat
+        std::vector<long long> sig = {7, (long long)(uintptr_t)sl.jd, (long long)(uintptr_t)jd,
+                                      (long long)(uintptr_t)c->twdf.p, (long long)(uintptr_t)tw,
+                                      (long long)sl.lv.size()};
+        for (const auto& L : sl.lv) sig.insert(sig.end(), {(long long)L.slot, L.n, L.blocks, (long long)L.sm});
+        for (const Launch& L : lv)
+            sig.insert(sig.end(), {(long long)L.slot, L.n, L.blocks, (long long)L.sm, L.pairs ? 1 : 0});
+        auto issue = [&]() -> int {
+            if (!sl.lv.empty()) {
+                cudaEvent_t es = prof_start(c);
+                c->launches--;   // counted per launch below
+                for (const auto& L : sl.lv) {
+                    c->launches++;
+                    KCU(launch_spec_df(sl.jd + L.slot, L.n, L.blocks, L.sm, c->twdf.p, c->stream));
+                }
+                prof_stop(c, es, "spec_df", sl.by, sl.fl);
+            }
+            cudaEvent_t ev = prof_start(c);
+            c->launches--;   // counted per launch below
+            for (const Launch& L : lv) {
+                c->launches++;
+                if (L.pairs)
+                    KCU(launch_acorr_df(jd + L.slot, L.n, L.blocks, L.sm, c->twdf.p, c->stream));
+                else
+                    KCU(launch_acorr(jd + L.slot, L.n, L.blocks, L.sm, tw, c->stream));
+            }
+            prof_stop(c, ev, "acorr", by, fl);
+            return KDEFFT_OK;
+        };
+        KCHK(run_graph(c, sig, issue));
     }
     for (const Job& jb : jobs)
         for (int k = 0; k < 4; ++k) jb.ds->acA[k] = (k < jb.ds->d) ? jb.A[k] : 0;
@@ -2128,10 +2159,27 @@ static bool lag_eligible(kdefft_ctx c, const ReqSet& rs, const std::pair<int, in
     return lag_table_size(d, pair_order(rs, pr, d), sizeof(real) == 8) > 0;
 }
 
-// Values of the grid pairs through the lag-domain engine: one tiled launch
-// per derivative-order class, a fixed-order reduction, one copy back.
+// The lag-domain work of one precision in a run, built on the host: the
+// items (LagItem<real>), their tiles and dense weights, the derivative-order
+// classes (R, first tile, tiles; one launch each) and the grid pairs in item
+// order.  run_lag builds it; issue_lag uploads and launches the batches of
+// both precisions of a run together.
+struct LagBatch {
+    bool dbl = false;
+    int d = 0;
+    int nitems = 0;
+    std::vector<unsigned char> items;
+    std::vector<LagTile> tiles;
+    std::vector<unsigned char> wpool;
+    std::vector<std::array<int, 3>> classes;
+    std::vector<std::pair<int, int>> pairs;
+    double fl = 0.0, by = 0.0;   // algorithmic flops and bytes of the batch
+};
+
+// Build the lag-domain batch for the grid pairs (the count autocorrelation
+// box they need is grown first).
 template <typename real>
-static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pairs) {
+static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pairs, std::vector<LagBatch>& out) {
     if (pairs.empty()) return KDEFFT_OK;
     const bool dbl = sizeof(real) == 8;
     const int d = rs.grids[pairs[0].first].ds->d;
@@ -2155,10 +2203,11 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     HermiteIndex& hx = hindex();
     std::vector<LagItem<real>> items;
     std::vector<real> wpool;
-    std::vector<LagTile> tiles;
-    std::vector<std::array<int, 3>> classes;   // (R, first tile, tiles)
+    LagBatch bt;
+    bt.dbl = dbl;
+    bt.d = d;
     items.reserve(pairs.size());
-    tiles.reserve(pairs.size() * 4);
+    bt.tiles.reserve(pairs.size() * 4);
     // inverse covariances and normalisations once per kernel spec (the
     // pairs of one bandwidth share them)
     struct SpecInv {
@@ -2167,10 +2216,17 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         double nrm[MAXSIG];
     };
     std::vector<SpecInv> sinv(rs.specs.size());
-    // fixed tiles (4096 points in FP32, 512 in FP64, whose slower points need
-    // more CTAs in flight): an item's sum depends on the item alone, not on
-    // the batch it came in
-    const long long T = dbl ? 512 : 4096;
+    // tiles sized from the item's own point count, so that an item's sum
+    // depends on the item alone, not on the batch it came in: the smallest
+    // power of two from 64 points that cuts the item into at most 128 tiles
+    // (a small item spreads over the SMs instead of queueing its points on a
+    // few), at most 4096 points in FP32 and 512 in FP64 (whose slower points
+    // need more CTAs in flight)
+    auto tile_of = [dbl](long long pts) {
+        long long t = 64;
+        while (t < (dbl ? 512 : 4096) && t * 128 < pts) t *= 2;
+        return t;
+    };
     for (size_t u : ord) {
         const auto& pr = pairs[u];
         const GridReq& g = rs.grids[pr.first];
@@ -2223,80 +2279,124 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         it.scale = 1.0 / (nn * nn);
         long long pts = g.L[0] + 1;
         for (int k = 1; k < d; ++k) pts *= 2 * g.L[k] + 1;
-        it.tile0 = (int)tiles.size();
-        for (long long f = 0; f < pts; f += T) tiles.push_back(LagTile{(int)items.size(), (int)std::min(T, pts - f), f});
-        it.ntile = (int)tiles.size() - it.tile0;
-        if (classes.empty() || classes.back()[0] != it.R) classes.push_back({it.R, it.tile0, 0});
-        classes.back()[2] += it.ntile;
+        it.tile0 = (int)bt.tiles.size();
+        const long long T = tile_of(pts);
+        for (long long f = 0; f < pts; f += T)
+            bt.tiles.push_back(LagTile{(int)items.size(), (int)std::min(T, pts - f), f});
+        it.ntile = (int)bt.tiles.size() - it.tile0;
+        if (bt.classes.empty() || bt.classes.back()[0] != it.R) bt.classes.push_back({it.R, it.tile0, 0});
+        bt.classes.back()[2] += it.ntile;
+        // algorithmic work: per point nsig exponentials and Hermite tables; bytes: a_j once per point
+        bt.fl += (double)pts * it.nsig * (2.0 * d * d + 8.0 * N);
+        bt.by += (double)pts * sizeof(real);
         items.push_back(it);
+        bt.pairs.push_back(pr);
     }
-    const int nitems = (int)items.size();
+    bt.nitems = (int)items.size();
+    bt.items.resize(sizeof(LagItem<real>) * items.size());
+    std::memcpy(bt.items.data(), items.data(), bt.items.size());
+    bt.wpool.resize(sizeof(real) * wpool.size());
+    if (!wpool.empty()) std::memcpy(bt.wpool.data(), wpool.data(), bt.wpool.size());
+    out.push_back(std::move(bt));
+    return KDEFFT_OK;
+}
+
+// Upload the lag batches of a run in one copy and launch them (one tiled
+// launch per batch and derivative-order class, each item's fixed-order sum
+// in the launch that finishes it), then one copy of all values back; the
+// values are read by flush_reads.
+static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
+    if (bts.empty()) return KDEFFT_OK;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t bI = sizeof(LagItem<real>) * nitems, bT = sizeof(LagTile) * tiles.size(), bW = sizeof(real) * wpool.size();
-    const size_t oT = al(bI), oW = oT + al(bT), bytes = oW + std::max<size_t>(bW, 16);
+    struct Lay {
+        size_t oI, oT, oW;
+        int item0, tile0;
+    };
+    std::vector<Lay> lay(bts.size());
+    size_t bytes = 0;
+    int nit = 0, ntl = 0;
+    for (size_t b = 0; b < bts.size(); ++b) {
+        const LagBatch& bt = bts[b];
+        lay[b].oI = bytes;
+        bytes += al(bt.items.size());
+        lay[b].oT = bytes;
+        bytes += al(sizeof(LagTile) * bt.tiles.size());
+        lay[b].oW = bytes;
+        bytes += al(std::max<size_t>(bt.wpool.size(), 16));
+        lay[b].item0 = nit;
+        lay[b].tile0 = ntl;
+        nit += bt.nitems;
+        ntl += (int)bt.tiles.size();
+    }
     KCHK(staging_wait(c));
     KCHK(c->h_items.ensure(bytes));
     KCHK(c->items.ensure(bytes));
-    KCHK(c->partial.ensure(sizeof(double) * 2 * tiles.size()));
-    KCHK(c->out.ensure(sizeof(double) * 2 * nitems));
+    KCHK(c->partial.ensure(sizeof(double) * 2 * (size_t)ntl));
+    KCHK(c->out.ensure(sizeof(double) * 2 * (size_t)nit));
+    // per-item tile counters: zero on allocation, left zero by every launch
+    void* const cnt0 = c->lagcnt.p;
+    KCHK(c->lagcnt.ensure(sizeof(unsigned int) * (size_t)nit));
+    if (c->lagcnt.p != cnt0) KCU(cudaMemsetAsync(c->lagcnt.p, 0, c->lagcnt.cap, c->stream));
     // results go behind those of earlier lag launches still on their way
-    const size_t need = 2 * (size_t)nitems;
+    const size_t need = 2 * (size_t)nit;
     if (c->h_out.cap < sizeof(double) * (c->hout_used + need)) {
         KCHK(flush_reads(c));
         KCHK(c->h_out.ensure(sizeof(double) * need));
     }
     const size_t off = c->hout_used;
     unsigned char* h = (unsigned char*)c->h_items.p;
-    std::memcpy(h, items.data(), bI);
-    std::memcpy(h + oT, tiles.data(), bT);
-    if (bW) std::memcpy(h + oW, wpool.data(), bW);
     unsigned char* dbase = (unsigned char*)c->items.p;
-    const LagItem<real>* dI = (const LagItem<real>*)dbase;
-    const LagTile* dT = (const LagTile*)(dbase + oT);
-    const real* dW = (const real*)(dbase + oW);
     double* part = (double*)c->partial.p;
-    // algorithmic work: per point nsig exponentials and Hermite tables; bytes: a_j once per point
-    double fl = 0.0, by = 0.0;
-    for (const LagItem<real>& it : items) {
-        long long pts = it.L[0] + 1;
-        for (int k = 1; k < d; ++k) pts *= 2 * it.L[k] + 1;
-        const int N = lag_table_size(d, it.R, dbl);
-        fl += (double)pts * it.nsig * (2.0 * d * d + 8.0 * N);
-        by += (double)pts * sizeof(real);
-    }
-    std::vector<long long> sig = {3, (long long)sizeof(real), d, nitems, (long long)tiles.size(),
-                                  (long long)(uintptr_t)dbase, (long long)(uintptr_t)h, (long long)bytes,
-                                  (long long)(uintptr_t)part, (long long)(uintptr_t)c->out.p,
+    double* dout = (double*)c->out.p;
+    unsigned int* cnt = (unsigned int*)c->lagcnt.p;
+    std::vector<long long> sig = {3, (long long)(uintptr_t)dbase, (long long)(uintptr_t)h, (long long)bytes,
+                                  (long long)(uintptr_t)part, (long long)(uintptr_t)dout, (long long)(uintptr_t)cnt,
                                   (long long)(uintptr_t)c->h_out.p, (long long)off};
-    for (const auto& cl : classes) {
-        sig.push_back(cl[0]);
-        sig.push_back(cl[1]);
-        sig.push_back(cl[2]);
+    for (size_t b = 0; b < bts.size(); ++b) {
+        const LagBatch& bt = bts[b];
+        std::memcpy(h + lay[b].oI, bt.items.data(), bt.items.size());
+        std::memcpy(h + lay[b].oT, bt.tiles.data(), sizeof(LagTile) * bt.tiles.size());
+        if (!bt.wpool.empty()) std::memcpy(h + lay[b].oW, bt.wpool.data(), bt.wpool.size());
+        sig.insert(sig.end(), {bt.dbl ? 8 : 4, bt.d, bt.nitems, (long long)bt.tiles.size(), (long long)lay[b].oI,
+                               (long long)lay[b].oT, (long long)lay[b].oW, lay[b].item0, lay[b].tile0});
+        for (const auto& cl : bt.classes) sig.insert(sig.end(), {cl[0], cl[1], cl[2]});
     }
     auto issue = [&]() -> int {
-        for (const auto& cl : classes) {
-            cudaEvent_t ev = prof_start(c);
-            const int grid = std::min(cl[2], c->nsm * 8);
-            KCU(launch_lag<real>(d, cl[0], dI, dT + cl[1], cl[2], dW, part + 2 * (size_t)cl[1], grid, c->stream));
-            prof_stop(c, ev, dbl ? "lag_f64" : "lag_f32", by * cl[2] / std::max<size_t>(tiles.size(), 1),
-                      fl * cl[2] / std::max<size_t>(tiles.size(), 1));
+        for (size_t b = 0; b < bts.size(); ++b) {
+            const LagBatch& bt = bts[b];
+            const size_t nt = std::max<size_t>(bt.tiles.size(), 1);
+            for (const auto& cl : bt.classes) {
+                cudaEvent_t ev = prof_start(c);
+                const int grid = std::min(cl[2], c->nsm * 8);
+                if (bt.dbl) {
+                    const LagJob<double> j{(const LagItem<double>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
+                                           cl[1], cl[2], grid, (const double*)(dbase + lay[b].oW),
+                                           part + 2 * (size_t)lay[b].tile0, dout + 2 * (size_t)lay[b].item0,
+                                           cnt + lay[b].item0};
+                    KCU(launch_lag<double>(bt.d, cl[0], j, c->stream));
+                } else {
+                    const LagJob<float> j{(const LagItem<float>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
+                                          cl[1], cl[2], grid, (const float*)(dbase + lay[b].oW),
+                                          part + 2 * (size_t)lay[b].tile0, dout + 2 * (size_t)lay[b].item0,
+                                          cnt + lay[b].item0};
+                    KCU(launch_lag<float>(bt.d, cl[0], j, c->stream));
+                }
+                prof_stop(c, ev, bt.dbl ? "lag_f64" : "lag_f32", bt.by * cl[2] / nt, bt.fl * cl[2] / nt);
+            }
         }
-        cudaEvent_t ev = prof_start(c);
-        KCU(launch_lag_reduce<real>(dI, nitems, part, (double*)c->out.p, c->stream));
-        prof_stop(c, ev, "reduce", 16.0 * tiles.size(), 2.0 * tiles.size());
-        KCU(cudaMemcpyAsync((double*)c->h_out.p + off, c->out.p, sizeof(double) * need, cudaMemcpyDeviceToHost,
-                            c->stream));
+        KCU(cudaMemcpyAsync((double*)c->h_out.p + off, dout, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream));
         return KDEFFT_OK;
     };
     KCHK(staging_upload(c, dbase, bytes));
     KCHK(run_graph(c, sig, issue));
     c->h2d += (int64_t)bytes;
     c->d2h += (int64_t)(sizeof(double) * need);
-    kdefft_ctx_s::PendingRead pr{&rs, {}, off};
-    pr.pairs.reserve(ord.size());
-    for (size_t i = 0; i < ord.size(); ++i) pr.pairs.push_back(pairs[ord[i]]);
-    c->pend_reads.push_back(std::move(pr));
+    for (size_t b = 0; b < bts.size(); ++b) {
+        kdefft_ctx_s::PendingRead pr{&rs, std::move(bts[b].pairs), off + 2 * (size_t)lay[b].item0};
+        c->pend_reads.push_back(std::move(pr));
+    }
     c->hout_used += need;
+    bts.clear();
     prof_flush(c);
     return KDEFFT_OK;
 }
@@ -2389,8 +2489,11 @@ static int dispatch_batch(kdefft_ctx c, std::vector<Item<real>>& items, int d, i
     return KDEFFT_OK;
 }
 
+// The selected grids of one precision: lag-domain pairs are built into lagq
+// (issued by the caller with the other precision's), the rest run the FFT
+// route here.
 template <typename real>
-static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
+static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel, std::vector<LagBatch>& lagq) {
     if (sel.empty()) return KDEFFT_OK;
     const int d = rs.grids[sel[0]].ds->d;
     HermiteIndex& hx = hindex();
@@ -2416,7 +2519,7 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel) {
         std::vector<std::pair<int, int>> lagp, fftp;
         for (const auto& pr : pairs) (lag_eligible<real>(c, rs, pr) ? lagp : fftp).push_back(pr);
         if (!lagp.empty()) {
-            const int lr = run_lag<real>(c, rs, lagp);
+            const int lr = run_lag<real>(c, rs, lagp, lagq);
             if (lr == KDEFFT_ERR_UNSUPPORTED)
                 fftp.insert(fftp.end(), lagp.begin(), lagp.end());   // autocorrelation box beyond MAXP
             else
@@ -2528,10 +2631,13 @@ static int run(kdefft_ctx c, ReqSet& rs) {
         const GridReq& g = rs.grids[i];
         ((g.fp64 || g.ds->opts.precision == KDEFFT_FP64) ? s64 : s32).push_back((int)i);
     }
-    int r = run_requests<double>(c, rs, s64);
-    if (r == KDEFFT_OK) r = run_requests<float>(c, rs, s32);
-    // the lag launches of both precisions are in flight: one wait for all
-    // (also on an error, as the pending reads point into rs)
+    std::vector<LagBatch> lagq;
+    int r = run_requests<double>(c, rs, s64, lagq);
+    if (r == KDEFFT_OK) r = run_requests<float>(c, rs, s32, lagq);
+    // the lag batches of both precisions: one upload, one launch sequence,
+    // one copy back, one wait (also on an error, as the pending reads point
+    // into rs)
+    if (r == KDEFFT_OK) r = issue_lag(c, rs, lagq);
     const int f = flush_reads(c);
     return r != KDEFFT_OK ? r : f;
 }
@@ -2728,7 +2834,7 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
     }
     c->nsm = prop.multiProcessorCount;
     for (DevBuf* b : {&c->tw32, &c->tw64, &c->twdf, &c->scratch, &c->partial, &c->items, &c->tiles, &c->out,
-                      &c->sel_buf, &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf,
+                      &c->lagcnt, &c->sel_buf, &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf,
                       &c->specjobs})
         b->gen = &c->buf_gen;
     c->h_items.gen = &c->buf_gen;

@@ -247,12 +247,22 @@ struct LagTile {
 // Number of Hermite entries C(d + R, d) of the compile-time tables, or 0 when
 // no lag kernel is instantiated for (d, R, real) (the caller uses the FFT path).
 int lag_table_size(int d, int R, bool dbl);
+// One launch of the lag kernel over tiles [t0, t0 + ntiles) of a batch (one
+// derivative-order class): items, tiles and weights of the batch; partial
+// (2 per tile of the batch), out (2 per item) and cnt (1 per item, zero
+// between launches, left zero) of the batch.
 template <typename real>
-cudaError_t launch_lag(int d, int R, const LagItem<real>* items, const LagTile* tiles, int ntiles, const real* wpool,
-                       double* partial, int grid, cudaStream_t st);
+struct LagJob {
+    const LagItem<real>* items;
+    const LagTile* tiles;
+    int t0, ntiles, grid;
+    const real* wpool;
+    double* partial;
+    double* out;
+    unsigned int* cnt;
+};
 template <typename real>
-cudaError_t launch_lag_reduce(const LagItem<real>* items, int nitems, const double* partial, double* out,
-                              cudaStream_t st);
+cudaError_t launch_lag(int d, int R, const LagJob<real>& j, cudaStream_t st);
 // One separable pass of the inverse DFT that turns the FP64 count spectrum
 // into the autocorrelation, for one dataset: out[o][jj][i] = sum_{w < W} h(w)
 // in[o][w][i] e^{+2 pi i w (jlo + jj) / P}, h(w) = 1, or for the

@@ -2,12 +2,13 @@
 // the lag done first) against the count autocorrelation (whose passes run
 // in engine.cu with the other transforms).
 //
-//   lag         per work item (two kernels of the same covariances and
-//               support, as in the FFT path), sum over the half lag box of
-//               w_j k_j a_j, w_j in {0, 1, 2}; kernels from the
-//               compile-time Hermite recurrence; compensated FP32 (or FP64)
-//               sums, one FP64 partial per tile.
-//   lag_reduce  fixed-order sum of an item's tile partials, times n^-2.
+//   lag   per work item (two kernels of the same covariances and support,
+//         as in the FFT path), sum over the half lag box of w_j k_j a_j,
+//         w_j in {0, 1, 2}; kernels from the compile-time Hermite
+//         recurrence; compensated FP32 (or FP64) sums, one FP64 partial per
+//         tile.  The CTA that finishes an item's last tile sums the item's
+//         partials in a fixed order (whichever CTA that is) and writes the
+//         item's two values times n^-2.
 #include <algorithm>
 
 #include "devutil.cuh"
@@ -16,15 +17,20 @@
 namespace kdefft {
 
 // ------------------------------------------------------------ lag evaluation
+// tiles [t0, t0 + ntiles) of the batch's tile list; partial holds one pair
+// per tile of the batch, out one pair per item; cnt (one per item, zero
+// between launches) counts an item's finished tiles.
 template <typename real, int D, int R>
 __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ items,
-                                             const LagTile* __restrict__ tiles, int ntiles,
-                                             const real* __restrict__ wpool, double* __restrict__ partial) {
+                                             const LagTile* __restrict__ tiles, int t0, int ntiles,
+                                             const real* __restrict__ wpool, double* partial, double* __restrict__ out,
+                                             unsigned int* __restrict__ cnt) {
     constexpr HTab<D, R> ht{};
     constexpr int N = HTab<D, R>::N;
     __shared__ real Ws[2][MAXSIG][N];
     __shared__ LagItem<real> it;
-    for (int tix = blockIdx.x; tix < ntiles; tix += gridDim.x) {
+    __shared__ int last;
+    for (int tix = t0 + blockIdx.x; tix < t0 + ntiles; tix += gridDim.x) {
         const LagTile tl = tiles[tix];
         __syncthreads();   // the previous tile's readers of it / Ws are done
         if (threadIdx.x == 0) it = items[tl.item];
@@ -112,23 +118,31 @@ __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ i
         if (threadIdx.x == 0) {
             partial[2 * (long long)tix] = out2[0];
             partial[2 * (long long)tix + 1] = out2[1];
+            __threadfence();   // the partial is visible before the count says so
+            last = (atomicAdd(&cnt[tl.item], 1u) + 1u == (unsigned)it.ntile) ? 1 : 0;
+        }
+        __syncthreads();
+        if (last && threadIdx.x < 32) {
+            // the item's last tile: lane l sums tiles l, l + 32, ... in order,
+            // then a fixed shuffle tree (the same order whichever CTA is last)
+            __threadfence();
+            double a = 0.0, b = 0.0;
+            for (int t = threadIdx.x; t < it.ntile; t += 32) {
+                a += __ldcg(&partial[2 * (long long)(it.tile0 + t)]);
+                b += __ldcg(&partial[2 * (long long)(it.tile0 + t) + 1]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                b += __shfl_xor_sync(0xffffffffu, b, o);
+            }
+            if (threadIdx.x == 0) {
+                out[2 * (long long)tl.item] = a * it.scale;
+                out[2 * (long long)tl.item + 1] = b * it.scale;
+                cnt[tl.item] = 0u;   // ready for the next launch
+            }
         }
     }
-}
-
-template <typename real>
-__global__ void k_lag_reduce(const LagItem<real>* __restrict__ items, int nitems, const double* __restrict__ partial,
-                             double* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nitems) return;
-    const LagItem<real>& it = items[i];
-    double a = 0.0, b = 0.0;
-    for (int t = 0; t < it.ntile; ++t) {
-        a += partial[2 * (long long)(it.tile0 + t)];
-        b += partial[2 * (long long)(it.tile0 + t) + 1];
-    }
-    out[2 * i] = a * it.scale;
-    out[2 * i + 1] = b * it.scale;
 }
 
 // instantiated (d, R): FP32 d <= 2 up to R = 8, d = 3 up to 6, d = 4 up to 4;
@@ -152,58 +166,44 @@ int lag_table_size(int d, int R, bool dbl) {
 }
 
 template <typename real, int D, int R>
-static cudaError_t lag_go(const LagItem<real>* items, const LagTile* tiles, int ntiles, const real* wpool,
-                          double* partial, int grid, cudaStream_t st) {
-    k_lag<real, D, R><<<grid, 256, 0, st>>>(items, tiles, ntiles, wpool, partial);
+static cudaError_t lag_go(const LagJob<real>& j, cudaStream_t st) {
+    k_lag<real, D, R><<<j.grid, 256, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial, j.out, j.cnt);
     return cudaGetLastError();
 }
 
 template <typename real, int D>
-static cudaError_t lag_d(int R, const LagItem<real>* items, const LagTile* tiles, int ntiles, const real* wpool,
-                         double* partial, int grid, cudaStream_t st) {
+static cudaError_t lag_d(int R, const LagJob<real>& j, cudaStream_t st) {
     constexpr bool dbl = sizeof(real) == 8;
     const int Re = (R + 1) & ~1;
     if (Re > lag_rmax(D, dbl)) return cudaErrorNotSupported;
     switch (Re) {
-        case 0: return lag_go<real, D, 0>(items, tiles, ntiles, wpool, partial, grid, st);
-        case 2: return lag_go<real, D, 2>(items, tiles, ntiles, wpool, partial, grid, st);
-        case 4: return lag_go<real, D, 4>(items, tiles, ntiles, wpool, partial, grid, st);
+        case 0: return lag_go<real, D, 0>(j, st);
+        case 2: return lag_go<real, D, 2>(j, st);
+        case 4: return lag_go<real, D, 4>(j, st);
         case 6:
-            if constexpr (D <= 2 || (D == 3 && !dbl)) return lag_go<real, D, 6>(items, tiles, ntiles, wpool, partial, grid, st);
+            if constexpr (D <= 2 || (D == 3 && !dbl)) return lag_go<real, D, 6>(j, st);
             return cudaErrorNotSupported;
         case 8:
-            if constexpr (D <= 2) return lag_go<real, D, 8>(items, tiles, ntiles, wpool, partial, grid, st);
+            if constexpr (D <= 2) return lag_go<real, D, 8>(j, st);
             return cudaErrorNotSupported;
         default: return cudaErrorNotSupported;
     }
 }
 
 template <typename real>
-cudaError_t launch_lag(int d, int R, const LagItem<real>* items, const LagTile* tiles, int ntiles, const real* wpool,
-                       double* partial, int grid, cudaStream_t st) {
-    if (ntiles <= 0) return cudaSuccess;
+cudaError_t launch_lag(int d, int R, const LagJob<real>& j, cudaStream_t st) {
+    if (j.ntiles <= 0) return cudaSuccess;
+    if (j.grid < 1) return cudaErrorInvalidValue;
     switch (d) {
-        case 1: return lag_d<real, 1>(R, items, tiles, ntiles, wpool, partial, grid, st);
-        case 2: return lag_d<real, 2>(R, items, tiles, ntiles, wpool, partial, grid, st);
-        case 3: return lag_d<real, 3>(R, items, tiles, ntiles, wpool, partial, grid, st);
-        case 4: return lag_d<real, 4>(R, items, tiles, ntiles, wpool, partial, grid, st);
+        case 1: return lag_d<real, 1>(R, j, st);
+        case 2: return lag_d<real, 2>(R, j, st);
+        case 3: return lag_d<real, 3>(R, j, st);
+        case 4: return lag_d<real, 4>(R, j, st);
         default: return cudaErrorNotSupported;
     }
 }
 
-template <typename real>
-cudaError_t launch_lag_reduce(const LagItem<real>* items, int nitems, const double* partial, double* out,
-                              cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    k_lag_reduce<real><<<(nitems + 127) / 128, 128, 0, st>>>(items, nitems, partial, out);
-    return cudaGetLastError();
-}
-
-template cudaError_t launch_lag<float>(int, int, const LagItem<float>*, const LagTile*, int, const float*, double*, int,
-                                       cudaStream_t);
-template cudaError_t launch_lag<double>(int, int, const LagItem<double>*, const LagTile*, int, const double*, double*,
-                                        int, cudaStream_t);
-template cudaError_t launch_lag_reduce<float>(const LagItem<float>*, int, const double*, double*, cudaStream_t);
-template cudaError_t launch_lag_reduce<double>(const LagItem<double>*, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_lag<float>(int, int, const LagJob<float>&, cudaStream_t);
+template cudaError_t launch_lag<double>(int, int, const LagJob<double>&, cudaStream_t);
 
 }  // namespace kdefft

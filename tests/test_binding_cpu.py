@@ -60,7 +60,7 @@ def test_well_shaped_arguments_pass_the_checks():
     v = _lib._vec([[1, 2, 3]], 3, "M", np.int64)
     assert v.dtype == np.int64 and v.shape == (3,)
     keep, p = _lib._ptr_of(np.zeros((4, 3)))
-    assert keep.shape == (4, 3) and p.value
+    assert keep.shape == (4, 3) and p == keep.ctypes.data != 0
 
 
 def test_empty_batches_give_empty_results():

@@ -76,7 +76,7 @@ def test_graphs_are_bypassed_while_profiling():
     stats, launches, _, _ = c.profile_read()
     c.profile(0)
     assert c.runtime_stats() == before
-    assert launches >= 2 and any(k.startswith(("lag", "final")) for k in stats)
+    assert launches >= 1 and any(k.startswith(("lag", "final")) for k in stats)
     assert np.array_equal(a, b)
     ds.close()
     c.close()
