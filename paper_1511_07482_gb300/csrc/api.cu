@@ -1812,7 +1812,8 @@ static constexpr int kPairRadix = 5;
 // is already on its way to the device: issued by the caller (in one graph
 // with the autocorrelation passes that read the spectra).
 struct SpecLaunches {
-    const SpecJob* jd = nullptr;
+    SpecJob* jd = nullptr;
+    size_t table_bytes = 0;   // the job table, in h_specjobs until the caller's copy
     struct L {
         size_t slot;
         int n;
@@ -1916,19 +1917,29 @@ static int ensure_spectra_df(kdefft_ctx c, const std::vector<std::pair<kdefft_ds
     if (!c->specjobs_free) KCU(cudaEventSynchronize(c->specjobs_ev));
     KCHK(c->h_specjobs.ensure(sizeof(SpecJob) * all.size()));
     std::memcpy(c->h_specjobs.p, all.data(), sizeof(SpecJob) * all.size());
-    SpecJob* jd = (SpecJob*)c->specjobs.p;
-    KCU(cudaMemcpyAsync(jd, c->h_specjobs.p, sizeof(SpecJob) * all.size(), cudaMemcpyHostToDevice, c->stream));
-    KCU(cudaEventRecord(c->specjobs_ev, c->stream));
-    c->specjobs_free = false;
-    c->h2d += (int64_t)(sizeof(SpecJob) * all.size());
-    sl.jd = jd;
-    // the spectra are registered now; the caller issues their passes before
-    // any launch that reads them
+    sl.jd = (SpecJob*)c->specjobs.p;
+    sl.table_bytes = sizeof(SpecJob) * all.size();
+    // the spectra are registered now; the caller copies the table up and
+    // issues the passes before any launch that reads them
     for (Sj& j : todo) j.ds->spectra[j.key] = j.buf;
     return KDEFFT_OK;
 }
 
-static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& req) {
+// Work that follows the autocorrelation passes on the stream (the device
+// search): its launch signature and its copies and launches.
+struct StreamTail {
+    // called once the autocorrelation boxes and buffers are final: sets up
+    // the work's parameters and appends its launch signature
+    std::function<int(std::vector<long long>&)> prepare;
+    std::function<int()> issue;
+};
+
+// Grow the count autocorrelation of each dataset to the half box it needs
+// (the FP32-pair or FP64 count spectrum first).  With a tail, the tail's work
+// joins the same launch sequence (one graph replay for all of it); it runs on
+// its own when there is nothing to grow.
+static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, std::array<int, 4>>>& req,
+                                StreamTail* tail = nullptr) {
     HostTimer ht(c, "host:acorr");
     struct Job {
         kdefft_ds ds;
@@ -2089,22 +2100,29 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                 }
             }
         }
+        for (const Job& jb : jobs)
+            for (int k = 0; k < 4; ++k) jb.ds->acA[k] = (k < jb.ds->d) ? jb.A[k] : 0;
         if (!c->acjobs_free) KCU(cudaEventSynchronize(c->acjobs_ev));
-        KCHK(c->h_acjobs.ensure(sizeof(AcorrJob) * all.size()));
-        std::memcpy(c->h_acjobs.p, all.data(), sizeof(AcorrJob) * all.size());
-        KCU(cudaMemcpyAsync(jd, c->h_acjobs.p, sizeof(AcorrJob) * all.size(), cudaMemcpyHostToDevice, c->stream));
-        KCU(cudaEventRecord(c->acjobs_ev, c->stream));
-        c->acjobs_free = false;
-        // the count-spectrum passes (FP32 datasets) and the autocorrelation
-        // passes in one launch sequence, replayed as a CUDA graph when its
-        // tables, sizes and launch shapes repeat
+        const size_t acb = sizeof(AcorrJob) * all.size();
+        KCHK(c->h_acjobs.ensure(acb));
+        std::memcpy(c->h_acjobs.p, all.data(), acb);
+        // the table copies, the count-spectrum passes (FP32 datasets), the
+        // autocorrelation passes and the tail in one launch sequence,
+        // replayed as a CUDA graph when its tables, sizes and launch shapes
+        // repeat (the copies read the pinned tables when the graph runs)
         std::vector<long long> sig = {7, (long long)(uintptr_t)sl.jd, (long long)(uintptr_t)jd,
+                                      (long long)(uintptr_t)c->h_specjobs.p, (long long)sl.table_bytes,
+                                      (long long)(uintptr_t)c->h_acjobs.p, (long long)acb,
                                       (long long)(uintptr_t)c->twdf.p, (long long)(uintptr_t)tw,
                                       (long long)sl.lv.size()};
         for (const auto& L : sl.lv) sig.insert(sig.end(), {(long long)L.slot, L.n, L.blocks, (long long)L.sm});
         for (const Launch& L : lv)
             sig.insert(sig.end(), {(long long)L.slot, L.n, L.blocks, (long long)L.sm, L.pairs ? 1 : 0});
+        if (tail) KCHK(tail->prepare(sig));
         auto issue = [&]() -> int {
+            if (sl.table_bytes)
+                KCU(cudaMemcpyAsync(sl.jd, c->h_specjobs.p, sl.table_bytes, cudaMemcpyHostToDevice, c->stream));
+            KCU(cudaMemcpyAsync(jd, c->h_acjobs.p, acb, cudaMemcpyHostToDevice, c->stream));
             if (!sl.lv.empty()) {
                 cudaEvent_t es = prof_start(c);
                 c->launches--;   // counted per launch below
@@ -2124,12 +2142,25 @@ static int ensure_autocorr_many(kdefft_ctx c, const std::vector<std::pair<kdefft
                     KCU(launch_acorr(jd + L.slot, L.n, L.blocks, L.sm, tw, c->stream));
             }
             prof_stop(c, ev, "acorr", by, fl);
+            if (tail) KCHK(tail->issue());
             return KDEFFT_OK;
         };
         KCHK(run_graph(c, sig, issue));
+        // the pinned tables are free again once this work has run
+        if (sl.table_bytes) {
+            KCU(cudaEventRecord(c->specjobs_ev, c->stream));
+            c->specjobs_free = false;
+        }
+        KCU(cudaEventRecord(c->acjobs_ev, c->stream));
+        c->acjobs_free = false;
+        c->h2d += (int64_t)(sl.table_bytes + acb);
+        tail = nullptr;
     }
-    for (const Job& jb : jobs)
-        for (int k = 0; k < 4; ++k) jb.ds->acA[k] = (k < jb.ds->d) ? jb.A[k] : 0;
+    if (tail) {
+        std::vector<long long> sig = {9};
+        KCHK(tail->prepare(sig));
+        KCHK(run_graph(c, sig, tail->issue));
+    }
     return KDEFFT_OK;
 }
 
@@ -2361,7 +2392,10 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
                                (long long)lay[b].oT, (long long)lay[b].oW, lay[b].item0, lay[b].tile0});
         for (const auto& cl : bt.classes) sig.insert(sig.end(), {cl[0], cl[1], cl[2]});
     }
+    // the upload from pinned staging, the launches and the copy back replay
+    // as one graph (the copy reads the staging buffer when the graph runs)
     auto issue = [&]() -> int {
+        KCU(cudaMemcpyAsync(dbase, h, bytes, cudaMemcpyHostToDevice, c->stream));
         for (size_t b = 0; b < bts.size(); ++b) {
             const LagBatch& bt = bts[b];
             const size_t nt = std::max<size_t>(bt.tiles.size(), 1);
@@ -2387,8 +2421,9 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
         KCU(cudaMemcpyAsync((double*)c->h_out.p + off, dout, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream));
         return KDEFFT_OK;
     };
-    KCHK(staging_upload(c, dbase, bytes));
     KCHK(run_graph(c, sig, issue));
+    KCU(cudaEventRecord(c->staging_ev, c->stream));   // staging free again once this has run
+    c->staging_free = false;
     c->h2d += (int64_t)bytes;
     c->d2h += (int64_t)(sizeof(double) * need);
     for (size_t b = 0; b < bts.size(); ++b) {
@@ -4146,17 +4181,14 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
     std::array<int, 4> need{0, 0, 0, 0};
     for (int k = 0; k < 2; ++k)
         need[k] = (int)std::min<long long>(ds->M[k] - 1, std::max(8, (int)std::ceil(2.5 * Lmax[k])));
-    const int ar = ensure_autocorr_many(c, {{ds, need}});
-    if (ar == KDEFFT_ERR_UNSUPPORTED) return KDEFFT_ERR_UNSUPPORTED;
-    KCHK(ar);
     std::vector<int> first(nm + 1, 0);
     for (int m = 0; m < nm; ++m) first[m + 1] = first[m] + (int)th0s[m].size();
     const int nst = first[nm];
     const size_t bT = sizeof(SelStart) * nst;
     KCHK(c->sel_buf.ensure(bT));
-    // pinned start table: the copy and the search launch queue behind the
-    // autocorrelation passes without the host waiting for them (the table is
-    // free again after the synchronisation at the end of every search)
+    // pinned start table: copied up when the launch sequence runs, and the
+    // results come back into it (free again after the synchronisation at
+    // the end of every search)
     KCHK(c->h_sel.ensure(bT));
     SelStart* st = (SelStart*)c->h_sel.p;
     for (int m = 0; m < nm; ++m)
@@ -4166,45 +4198,66 @@ static int device_select2d_lag(kdefft_ds ds, const std::vector<int>& methods, co
             for (int k = 0; k < 3; ++k) x.th[k] = th0s[m][i][k];
         }
     SelStart* dst = (SelStart*)c->sel_buf.p;
-    KCU(cudaMemcpyAsync(dst, st, bT, cudaMemcpyHostToDevice, c->stream));
-    c->h2d += (int64_t)bT;
-    SelectParams prm[2]{};
-    for (int m = 0; m < nm; ++m) {
-        SelectParams& q = prm[m];
-        const int method = methods[m];
-        q.method = (method == KDEFFT_LSCV) ? 0 : 1;
-        q.max_iter = max_iter;
-        q.widest = (method == KDEFFT_LSCV && ds->opts.L_basis == KDEFFT_L_WIDEST) ? 1 : 0;
-        q.M0 = (int)ds->M[0];
-        q.M1 = (int)ds->M[1];
-        q.Lcap = ds->acA[0];
-        q.Lcap1 = ds->acA[1];
-        q.n = (double)ds->n;
-        q.inv_n = 1.0 / q.n;
-        q.inv_n2 = 1.0 / (q.n * q.n);
-        q.inv_nf = (float)q.inv_n;
-        q.inv_n2h = (float)q.inv_n2;
-        q.inv_n2l = (float)(q.inv_n2 - (double)q.inv_n2h);
-        q.tau = ds->opts.tau;
-        q.delta0 = ds->delta[0];
-        q.delta1 = ds->delta[1];
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) q.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gms[m](a, b) : 0.0;
-        params_f32(q);
-        q.errflag = c->errflag;
-        q.acorr = (const float*)ds->ac32.p;
-        q.A0 = ds->acA[0];
-        q.A1 = ds->acA[1];
-        q.rec = c->rec;
-        q.rec_cap = c->rec_cap;
-    }
-    if (nm == 1) prm[1] = prm[0];
     if (c->rec && (int64_t)nst * c->rec_cap * SEL_REC > c->rec_len)
         return fail(KDEFFT_ERR_ARG, "search record buffer smaller than starts x cap x fields");
-    cudaEvent_t ev = prof_start(c);
-    KCU(launch_select2d_lag(prm[0], prm[1], first[1], dst, nst, c->stream));
-    prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
-    KCU(cudaMemcpyAsync(st, dst, bT, cudaMemcpyDeviceToHost, c->stream));
+    SelectParams prm[2]{};
+    cudaEvent_t ev = nullptr;
+    // the search's parameters need the final autocorrelation box: set up
+    // when the box is (the start table copy, the search and the copy back
+    // join the autocorrelation passes' launch sequence)
+    StreamTail tail;
+    tail.prepare = [&](std::vector<long long>& sig) -> int {
+        std::memset(prm, 0, sizeof(prm));   // padding too: the bytes are the signature
+        for (int m = 0; m < nm; ++m) {
+            SelectParams& q = prm[m];
+            const int method = methods[m];
+            q.method = (method == KDEFFT_LSCV) ? 0 : 1;
+            q.max_iter = max_iter;
+            q.widest = (method == KDEFFT_LSCV && ds->opts.L_basis == KDEFFT_L_WIDEST) ? 1 : 0;
+            q.M0 = (int)ds->M[0];
+            q.M1 = (int)ds->M[1];
+            q.Lcap = ds->acA[0];
+            q.Lcap1 = ds->acA[1];
+            q.n = (double)ds->n;
+            q.inv_n = 1.0 / q.n;
+            q.inv_n2 = 1.0 / (q.n * q.n);
+            q.inv_nf = (float)q.inv_n;
+            q.inv_n2h = (float)q.inv_n2;
+            q.inv_n2l = (float)(q.inv_n2 - (double)q.inv_n2h);
+            q.tau = ds->opts.tau;
+            q.delta0 = ds->delta[0];
+            q.delta1 = ds->delta[1];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) q.G[a * 2 + b] = (method == KDEFFT_SCV) ? Gms[m](a, b) : 0.0;
+            params_f32(q);
+            q.errflag = c->errflag;
+            q.acorr = (const float*)ds->ac32.p;
+            q.A0 = ds->acA[0];
+            q.A1 = ds->acA[1];
+            q.rec = c->rec;
+            q.rec_cap = c->rec_cap;
+        }
+        if (nm == 1) prm[1] = prm[0];
+        // the parameters by value, as the launch captures them
+        const size_t w = (sizeof(prm) + sizeof(long long) - 1) / sizeof(long long);
+        std::vector<long long> pb(w, 0);
+        std::memcpy(pb.data(), prm, sizeof(prm));
+        sig.insert(sig.end(), {8, (long long)(uintptr_t)dst, (long long)(uintptr_t)st, (long long)bT, nst, first[1]});
+        sig.insert(sig.end(), pb.begin(), pb.end());
+        return KDEFFT_OK;
+    };
+    tail.issue = [&]() -> int {
+        KCU(cudaMemcpyAsync(dst, st, bT, cudaMemcpyHostToDevice, c->stream));
+        ev = prof_start(c);
+        KCU(launch_select2d_lag(prm[0], prm[1], first[1], dst, nst, c->stream));
+        prof_stop(c, ev, "select2d_lag_f32", 0.0, 0.0);
+        KCU(cudaMemcpyAsync(st, dst, bT, cudaMemcpyDeviceToHost, c->stream));
+        return KDEFFT_OK;
+    };
+    const int ar = ensure_autocorr_many(c, {{ds, need}}, &tail);
+    if (ar == KDEFFT_ERR_UNSUPPORTED) return KDEFFT_ERR_UNSUPPORTED;
+    KCHK(ar);
+    c->h2d += (int64_t)bT;
     {
         HostTimer w(c, "host:wait");
         KCU(cudaStreamSynchronize(c->stream));
