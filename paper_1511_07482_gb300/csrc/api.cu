@@ -510,7 +510,6 @@ struct kdefft_ctx_s {
     DevBuf tw32, tw64, twdf;          // twiddles in FP32, FP64 and FP32 pairs
     size_t tw_dev_n = 0;              // twiddles resident on the device
     DevBuf scratch, partial, items, tiles, out;
-    DevBuf lagcnt;                    // per-item tile counters of the lag launches
     HostBuf h_items, h_out;
     // lag-domain results on their way to h_out, not yet read: run_lag returns
     // without waiting, and flush_reads (at the end of run()) waits once for
@@ -2247,17 +2246,12 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         double nrm[MAXSIG];
     };
     std::vector<SpecInv> sinv(rs.specs.size());
-    // tiles sized from the item's own point count, so that an item's sum
-    // depends on the item alone, not on the batch it came in: the smallest
-    // power of two from 64 points that cuts the item into at most 128 tiles
-    // (a small item spreads over the SMs instead of queueing its points on a
-    // few), at most 4096 points in FP32 and 512 in FP64 (whose slower points
-    // need more CTAs in flight)
-    auto tile_of = [dbl](long long pts) {
-        long long t = 64;
-        while (t < (dbl ? 512 : 4096) && t * 128 < pts) t *= 2;
-        return t;
-    };
+    // fixed tiles, so that an item's sum depends on the item alone, not on
+    // the batch it came in: 4096 points in FP32 (smaller tiles halved the
+    // throughput of batches: per-tile work is then too small for a CTA), 256
+    // in FP64 (the points are slow on the FP64 pipe: more CTAs in flight, one
+    // point per thread)
+    const long long T = dbl ? 256 : 4096;
     for (size_t u : ord) {
         const auto& pr = pairs[u];
         const GridReq& g = rs.grids[pr.first];
@@ -2311,7 +2305,6 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
         long long pts = g.L[0] + 1;
         for (int k = 1; k < d; ++k) pts *= 2 * g.L[k] + 1;
         it.tile0 = (int)bt.tiles.size();
-        const long long T = tile_of(pts);
         for (long long f = 0; f < pts; f += T)
             bt.tiles.push_back(LagTile{(int)items.size(), (int)std::min(T, pts - f), f});
         it.ntile = (int)bt.tiles.size() - it.tile0;
@@ -2333,9 +2326,9 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
 }
 
 // Upload the lag batches of a run in one copy and launch them (one tiled
-// launch per batch and derivative-order class, each item's fixed-order sum
-// in the launch that finishes it), then one copy of all values back; the
-// values are read by flush_reads.
+// launch per batch and derivative-order class, then one fixed-order sum of
+// every item's tile partials), then one copy of all values back; the values
+// are read by flush_reads.
 static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
     if (bts.empty()) return KDEFFT_OK;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -2346,6 +2339,7 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
     std::vector<Lay> lay(bts.size());
     size_t bytes = 0;
     int nit = 0, ntl = 0;
+    std::vector<LagSum> sums;
     for (size_t b = 0; b < bts.size(); ++b) {
         const LagBatch& bt = bts[b];
         lay[b].oI = bytes;
@@ -2356,18 +2350,30 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
         bytes += al(std::max<size_t>(bt.wpool.size(), 16));
         lay[b].item0 = nit;
         lay[b].tile0 = ntl;
+        for (int i = 0; i < bt.nitems; ++i) {
+            // the item's tile range and scale, wherever its precision keeps them
+            const unsigned char* ip = bt.items.data() + (size_t)i * (bt.items.size() / bt.nitems);
+            int t0i, nti;
+            double sc;
+            if (bt.dbl) {
+                const LagItem<double>* q = (const LagItem<double>*)ip;
+                t0i = q->tile0, nti = q->ntile, sc = q->scale;
+            } else {
+                const LagItem<float>* q = (const LagItem<float>*)ip;
+                t0i = q->tile0, nti = q->ntile, sc = q->scale;
+            }
+            sums.push_back(LagSum{(long long)ntl + t0i, nti, 0, sc});
+        }
         nit += bt.nitems;
         ntl += (int)bt.tiles.size();
     }
+    const size_t oS = bytes;
+    bytes += al(sizeof(LagSum) * sums.size());
     KCHK(staging_wait(c));
     KCHK(c->h_items.ensure(bytes));
     KCHK(c->items.ensure(bytes));
     KCHK(c->partial.ensure(sizeof(double) * 2 * (size_t)ntl));
     KCHK(c->out.ensure(sizeof(double) * 2 * (size_t)nit));
-    // per-item tile counters: zero on allocation, left zero by every launch
-    void* const cnt0 = c->lagcnt.p;
-    KCHK(c->lagcnt.ensure(sizeof(unsigned int) * (size_t)nit));
-    if (c->lagcnt.p != cnt0) KCU(cudaMemsetAsync(c->lagcnt.p, 0, c->lagcnt.cap, c->stream));
     // results go behind those of earlier lag launches still on their way
     const size_t need = 2 * (size_t)nit;
     if (c->h_out.cap < sizeof(double) * (c->hout_used + need)) {
@@ -2379,9 +2385,9 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
     unsigned char* dbase = (unsigned char*)c->items.p;
     double* part = (double*)c->partial.p;
     double* dout = (double*)c->out.p;
-    unsigned int* cnt = (unsigned int*)c->lagcnt.p;
+    std::memcpy(h + oS, sums.data(), sizeof(LagSum) * sums.size());
     std::vector<long long> sig = {3, (long long)(uintptr_t)dbase, (long long)(uintptr_t)h, (long long)bytes,
-                                  (long long)(uintptr_t)part, (long long)(uintptr_t)dout, (long long)(uintptr_t)cnt,
+                                  (long long)(uintptr_t)part, (long long)(uintptr_t)dout, (long long)oS, nit,
                                   (long long)(uintptr_t)c->h_out.p, (long long)off};
     for (size_t b = 0; b < bts.size(); ++b) {
         const LagBatch& bt = bts[b];
@@ -2405,19 +2411,20 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
                 if (bt.dbl) {
                     const LagJob<double> j{(const LagItem<double>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
                                            cl[1], cl[2], grid, (const double*)(dbase + lay[b].oW),
-                                           part + 2 * (size_t)lay[b].tile0, dout + 2 * (size_t)lay[b].item0,
-                                           cnt + lay[b].item0};
+                                           part + 2 * (size_t)lay[b].tile0};
                     KCU(launch_lag<double>(bt.d, cl[0], j, c->stream));
                 } else {
                     const LagJob<float> j{(const LagItem<float>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
                                           cl[1], cl[2], grid, (const float*)(dbase + lay[b].oW),
-                                          part + 2 * (size_t)lay[b].tile0, dout + 2 * (size_t)lay[b].item0,
-                                          cnt + lay[b].item0};
+                                          part + 2 * (size_t)lay[b].tile0};
                     KCU(launch_lag<float>(bt.d, cl[0], j, c->stream));
                 }
                 prof_stop(c, ev, bt.dbl ? "lag_f64" : "lag_f32", bt.by * cl[2] / nt, bt.fl * cl[2] / nt);
             }
         }
+        cudaEvent_t es = prof_start(c);
+        KCU(launch_lag_sum((const LagSum*)(dbase + oS), nit, part, dout, c->stream));
+        prof_stop(c, es, "lag_sum", 16.0 * ntl, 2.0 * ntl);
         KCU(cudaMemcpyAsync((double*)c->h_out.p + off, dout, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream));
         return KDEFFT_OK;
     };
@@ -2869,7 +2876,7 @@ int kdefft_create(kdefft_ctx* out, int device, void* stream) {
     }
     c->nsm = prop.multiProcessorCount;
     for (DevBuf* b : {&c->tw32, &c->tw64, &c->twdf, &c->scratch, &c->partial, &c->items, &c->tiles, &c->out,
-                      &c->lagcnt, &c->sel_buf, &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf,
+                      &c->sel_buf, &c->binfix, &c->acbuf[0], &c->acbuf[1], &c->acjobs, &c->binjobs, &c->kdebuf,
                       &c->specjobs})
         b->gen = &c->buf_gen;
     c->h_items.gen = &c->buf_gen;

@@ -248,9 +248,8 @@ struct LagTile {
 // no lag kernel is instantiated for (d, R, real) (the caller uses the FFT path).
 int lag_table_size(int d, int R, bool dbl);
 // One launch of the lag kernel over tiles [t0, t0 + ntiles) of a batch (one
-// derivative-order class): items, tiles and weights of the batch; partial
-// (2 per tile of the batch), out (2 per item) and cnt (1 per item, zero
-// between launches, left zero) of the batch.
+// derivative-order class): items, tiles and weights of the batch, partial
+// (2 per tile of the batch).
 template <typename real>
 struct LagJob {
     const LagItem<real>* items;
@@ -258,11 +257,17 @@ struct LagJob {
     int t0, ntiles, grid;
     const real* wpool;
     double* partial;
-    double* out;
-    unsigned int* cnt;
 };
 template <typename real>
 cudaError_t launch_lag(int d, int R, const LagJob<real>& j, cudaStream_t st);
+// An item's tile partials (tile0 indexes the run's whole partial buffer) and
+// its scale n^-2: the per-item sums of a run, whatever the batch's precision.
+struct LagSum {
+    long long tile0;
+    int ntile, pad_;
+    double scale;
+};
+cudaError_t launch_lag_sum(const LagSum* sums, int nitems, const double* partial, double* out, cudaStream_t st);
 // One separable pass of the inverse DFT that turns the FP64 count spectrum
 // into the autocorrelation, for one dataset: out[o][jj][i] = sum_{w < W} h(w)
 // in[o][w][i] e^{+2 pi i w (jlo + jj) / P}, h(w) = 1, or for the

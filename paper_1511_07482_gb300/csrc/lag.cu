@@ -2,13 +2,13 @@
 // the lag done first) against the count autocorrelation (whose passes run
 // in engine.cu with the other transforms).
 //
-//   lag   per work item (two kernels of the same covariances and support,
-//         as in the FFT path), sum over the half lag box of w_j k_j a_j,
-//         w_j in {0, 1, 2}; kernels from the compile-time Hermite
-//         recurrence; compensated FP32 (or FP64) sums, one FP64 partial per
-//         tile.  The CTA that finishes an item's last tile sums the item's
-//         partials in a fixed order (whichever CTA that is) and writes the
-//         item's two values times n^-2.
+//   lag      per work item (two kernels of the same covariances and
+//            support, as in the FFT path), sum over the half lag box of
+//            w_j k_j a_j, w_j in {0, 1, 2}; kernels from the compile-time
+//            Hermite recurrence; compensated FP32 (or FP64) sums, one FP64
+//            partial per tile.
+//   lag_sum  fixed-order sum of each item's tile partials, times n^-2, for
+//            the items of every batch of a run in one launch.
 #include <algorithm>
 
 #include "devutil.cuh"
@@ -18,18 +18,15 @@ namespace kdefft {
 
 // ------------------------------------------------------------ lag evaluation
 // tiles [t0, t0 + ntiles) of the batch's tile list; partial holds one pair
-// per tile of the batch, out one pair per item; cnt (one per item, zero
-// between launches) counts an item's finished tiles.
+// per tile of the batch.
 template <typename real, int D, int R>
 __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ items,
                                              const LagTile* __restrict__ tiles, int t0, int ntiles,
-                                             const real* __restrict__ wpool, double* partial, double* __restrict__ out,
-                                             unsigned int* __restrict__ cnt) {
+                                             const real* __restrict__ wpool, double* __restrict__ partial) {
     constexpr HTab<D, R> ht{};
     constexpr int N = HTab<D, R>::N;
     __shared__ real Ws[2][MAXSIG][N];
     __shared__ LagItem<real> it;
-    __shared__ int last;
     for (int tix = t0 + blockIdx.x; tix < t0 + ntiles; tix += gridDim.x) {
         const LagTile tl = tiles[tix];
         __syncthreads();   // the previous tile's readers of it / Ws are done
@@ -118,30 +115,31 @@ __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ i
         if (threadIdx.x == 0) {
             partial[2 * (long long)tix] = out2[0];
             partial[2 * (long long)tix + 1] = out2[1];
-            __threadfence();   // the partial is visible before the count says so
-            last = (atomicAdd(&cnt[tl.item], 1u) + 1u == (unsigned)it.ntile) ? 1 : 0;
         }
-        __syncthreads();
-        if (last && threadIdx.x < 32) {
-            // the item's last tile: lane l sums tiles l, l + 32, ... in order,
-            // then a fixed shuffle tree (the same order whichever CTA is last)
-            __threadfence();
-            double a = 0.0, b = 0.0;
-            for (int t = threadIdx.x; t < it.ntile; t += 32) {
-                a += __ldcg(&partial[2 * (long long)(it.tile0 + t)]);
-                b += __ldcg(&partial[2 * (long long)(it.tile0 + t) + 1]);
-            }
+    }
+}
+
+// One warp per item (of every batch of a run): lane l sums the item's tile
+// partials l, l + 32, ... in order, then a fixed shuffle tree; times n^-2.
+__global__ void __launch_bounds__(256) k_lag_sum(const LagSum* __restrict__ sums, int nitems,
+                                                 const double* __restrict__ partial, double* __restrict__ out) {
+    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= nitems) return;   // whole warps leave together
+    const LagSum sm = sums[i];
+    double a = 0.0, b = 0.0;
+    for (int t = lane; t < sm.ntile; t += 32) {
+        a += partial[2 * (sm.tile0 + (long long)t)];
+        b += partial[2 * (sm.tile0 + (long long)t) + 1];
+    }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                b += __shfl_xor_sync(0xffffffffu, b, o);
-            }
-            if (threadIdx.x == 0) {
-                out[2 * (long long)tl.item] = a * it.scale;
-                out[2 * (long long)tl.item + 1] = b * it.scale;
-                cnt[tl.item] = 0u;   // ready for the next launch
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        out[2 * (long long)i] = a * sm.scale;
+        out[2 * (long long)i + 1] = b * sm.scale;
     }
 }
 
@@ -167,7 +165,7 @@ int lag_table_size(int d, int R, bool dbl) {
 
 template <typename real, int D, int R>
 static cudaError_t lag_go(const LagJob<real>& j, cudaStream_t st) {
-    k_lag<real, D, R><<<j.grid, 256, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial, j.out, j.cnt);
+    k_lag<real, D, R><<<j.grid, 256, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial);
     return cudaGetLastError();
 }
 
@@ -201,6 +199,13 @@ cudaError_t launch_lag(int d, int R, const LagJob<real>& j, cudaStream_t st) {
         case 4: return lag_d<real, 4>(R, j, st);
         default: return cudaErrorNotSupported;
     }
+}
+
+cudaError_t launch_lag_sum(const LagSum* sums, int nitems, const double* partial, double* out, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const long long threads = 32LL * nitems;
+    k_lag_sum<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sums, nitems, partial, out);
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_lag<float>(int, int, const LagJob<float>&, cudaStream_t);
