@@ -2229,7 +2229,10 @@ struct LagBatch {
 };
 
 // Build the lag-domain batch for the grid pairs (the count autocorrelation
-// box they need is grown first).
+// box they need is grown first).  (Building a large set in chunks, each
+// issued while the next is built, was measured slower: each chunk's launch
+// leaves the GPU partly idle at its tail.)
+
 template <typename real>
 static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pairs, std::vector<LagBatch>& out) {
     if (pairs.empty()) return KDEFFT_OK;
@@ -2253,13 +2256,6 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
     std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return Re[a] < Re[b]; });
     HermiteIndex& hx = hindex();
-    LagBatch bt;
-    bt.dbl = dbl;
-    std::vector<LagItem<real>>& items = bt.items<real>();
-    std::vector<real>& wpool = bt.wpool<real>();
-    bt.d = d;
-    items.reserve(pairs.size());
-    bt.tiles.reserve(pairs.size() * 4);
     // inverse covariances and normalisations once per kernel spec (the
     // pairs of one bandwidth share them)
     struct SpecInv {
@@ -2274,6 +2270,13 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     // in FP64 (the points are slow on the FP64 pipe: more CTAs in flight, one
     // point per thread)
     const long long T = dbl ? 256 : 4096;
+    LagBatch bt;
+    bt.dbl = dbl;
+    bt.d = d;
+    std::vector<LagItem<real>>& items = bt.items<real>();
+    std::vector<real>& wpool = bt.wpool<real>();
+    items.reserve(ord.size());
+    bt.tiles.reserve(ord.size() * 4);
     for (size_t u : ord) {
         const auto& pr = pairs[u];
         const GridReq& g = rs.grids[pr.first];
@@ -2394,8 +2397,11 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
     // results go behind those of earlier lag launches still on their way
     const size_t need = 2 * (size_t)nit;
     if (c->h_out.cap < sizeof(double) * (c->hout_used + need)) {
+        // (the results still on their way point into h_out: read them first;
+        // grow by at least 4x, so that the next chunks of a large run fit)
+        const size_t grow = std::max(need, 4 * (c->h_out.cap / sizeof(double)));
         KCHK(flush_reads(c));
-        KCHK(c->h_out.ensure(sizeof(double) * need));
+        KCHK(c->h_out.ensure(sizeof(double) * grow));
     }
     const size_t off = c->hout_used;
     unsigned char* h = (unsigned char*)c->h_items.p;
@@ -2419,6 +2425,14 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
     // as one graph (the copy reads the staging buffer when the graph runs)
     auto issue = [&]() -> int {
         KCU(cudaMemcpyAsync(dbase, h, bytes, cudaMemcpyHostToDevice, c->stream));
+        // the staging buffer is free again once this copy is done (inside a
+        // graph: an event node that records when the replayed copy is done),
+        // so the host can stage the next chunk while these launches run
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        KCU(cudaStreamIsCapturing(c->stream, &cs));
+        KCU(cudaEventRecordWithFlags(c->staging_ev, c->stream,
+                                     cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                         : cudaEventRecordDefault));
         for (size_t b = 0; b < bts.size(); ++b) {
             const LagBatch& bt = bts[b];
             const size_t nt = std::max<size_t>(bt.tiles.size(), 1);
@@ -2446,7 +2460,6 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
         return KDEFFT_OK;
     };
     KCHK(run_graph(c, sig, issue));
-    KCU(cudaEventRecord(c->staging_ev, c->stream));   // staging free again once this has run
     c->staging_free = false;
     c->h2d += (int64_t)bytes;
     c->d2h += (int64_t)(sizeof(double) * need);
