@@ -505,6 +505,27 @@ static bool is_smooth(long long x) {
     return x == 1;
 }
 
+// smallest 2^a 3^b 5^c >= m: a table up to 8192 (built once, thread-safe
+// initialisation of a function-local static; the search loop cost about half
+// of the request building of a large batch of bandwidths), a search above
+static long long next_smooth(long long m) {
+    constexpr int kTab = 8192;
+    static const std::vector<int> tab = [] {
+        std::vector<int> t(kTab + 1);
+        int next = kTab + 1;
+        while (!is_smooth(next)) ++next;
+        for (int x = kTab; x >= 1; --x) {
+            if (is_smooth(x)) next = x;
+            t[x] = next;
+        }
+        t[0] = 1;
+        return t;
+    }();
+    if (m <= kTab) return tab[m < 0 ? 0 : m];
+    while (!is_smooth(m)) ++m;
+    return m;
+}
+
 // ============================================================ context & dataset
 struct kdefft_ds_s;
 struct ReqSet;
@@ -906,8 +927,7 @@ static int choose_P(const kdefft_ds ds, const int* L, int* P) {
                 p = ds->opts.P_fixed[k];
                 break;
             default: {
-                p = M + L[k];
-                while (!is_smooth(p)) ++p;
+                p = next_smooth(M + L[k]);
             }
         }
         if (p < M + L[k]) return fail(KDEFFT_ERR_ARG, "padded size P_k below M_k + L_k would alias");
@@ -1775,10 +1795,7 @@ static int ensure_spectra(kdefft_ctx c, const std::vector<std::pair<kdefft_ds, s
 
 // Evaluate every grid of rs (value = Eq. 25 for that lag kernel).
 // ============================================================ lag-domain engine
-static long long pmin_smooth(long long m) {
-    while (!is_smooth(m)) ++m;
-    return m;
-}
+static long long pmin_smooth(long long m) { return next_smooth(m); }
 
 // a_j = sum_i c_i c_{i+j} on the half box A (j_0 in [0, A_0], |j_k| <= A_k),
 // layout [j_{d-1}]..[j_0], from the FP64 count spectrum at P_k >= M_k + A_k
@@ -4349,11 +4366,7 @@ static int device_select2d(kdefft_ds ds, int method, const Mat& Gm, const std::v
         *evals_out = ev[0];
         return KDEFFT_OK;
     }
-    auto pmin = [](int m) {
-        int p = m;
-        while (!is_smooth(p)) ++p;
-        return p;
-    };
+    auto pmin = [](int m) { return (int)next_smooth(m); };
     // cluster size, batch size and support cap from the shared-memory budget
     // The two packed pairs are transformed together: the gather holds both
     // and a batch holds `chunk` lines of each.  For a cluster size and a

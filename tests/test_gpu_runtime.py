@@ -44,6 +44,34 @@ def test_graph_replay_gives_the_direct_bits(engine):
     assert st_off["graphs_captured"] == 0 and st_off["graph_replays"] == 0
 
 
+def test_selection_replay_gives_the_direct_bits():
+    """The selection's launch sequence (table copies, count spectrum and
+    autocorrelation passes, the device search and its copy back, then both
+    end-point values) replays as CUDA graphs from the second step on, each
+    step on a freshly binned dataset: the same bandwidths, values and
+    evaluation counts as direct launches, step after step."""
+    from paper_1511_07482_gb300 import LSCV, SCV
+    w = synthetic.small_case(n=20000, d=2, M=[96, 90], seed=74, n_candidates=1)
+    G = synthetic.normal_scale(w.X)
+    res = {}
+    for g in (True, False):
+        c = _ctx(graphs=g)
+        steps = []
+        for _ in range(3):
+            ds = c.bin(w.X, w.lo, w.hi, w.M)
+            steps.append(ds.select_H_many([LSCV, SCV], G=G, n_starts=4, max_iter=30))
+            ds.close()
+        for st in steps[1:]:
+            for (Ha, fa, ea), (Hb, fb, eb) in zip(st, steps[0]):
+                assert np.array_equal(Ha, Hb) and fa == fb and ea == eb
+        res[g] = (steps[0], c.runtime_stats())
+        c.close()
+    for (Ha, fa, ea), (Hb, fb, eb) in zip(res[True][0], res[False][0]):
+        assert np.array_equal(Ha, Hb) and fa == fb and ea == eb
+    assert res[True][1]["graph_replays"] >= 2
+    assert res[False][1]["graphs_captured"] == 0
+
+
 def test_graphs_are_recaptured_after_buffers_grow():
     """A captured graph copies through the context's staging buffers; once a
     larger batch has reallocated them, the small batch is captured again
