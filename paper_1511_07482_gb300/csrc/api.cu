@@ -3209,7 +3209,9 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
         DevBuf& fix = c->binfix;
         KCHK(fix.ensure(8 * (size_t)ds->ncells));
         KCHK(ds->counts.ensure(4 * (size_t)ds->ncells));
-        const size_t nres = 1 + (size_t)mblk * nv;
+        // the outside counter and the moment partials come back in one copy
+        // of the whole work buffer (counter at 0, partials from 16)
+        const size_t nres = 16 + (size_t)mblk * nv;
         KCHK(c->h_binres.ensure(sizeof(double) * nres));
         double* hres = (double*)c->h_binres.p;
         std::vector<long long> sig = {4, (long long)(uintptr_t)dX, n, d, K, (long long)(uintptr_t)fix.p,
@@ -3234,14 +3236,13 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
             prof_stop(c, evb, "bin", (double)n * d * 8.0 + (double)ds->ncells * 4.0, (double)n * (1 << d) * 2.0);
             c->launches += 1;
             KCU(launch_moments_shifted(dX, n, d, sh, dPart, c->nsm, c->stream));
-            KCU(cudaMemcpyAsync(hres, dOut, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-            KCU(cudaMemcpyAsync(hres + 1, dPart, sizeof(double) * mblk * nv, cudaMemcpyDeviceToHost, c->stream));
+            KCU(cudaMemcpyAsync(hres, misc.p, sizeof(double) * nres, cudaMemcpyDeviceToHost, c->stream));
             return KDEFFT_OK;
         };
         KCHK(run_graph(c, sig, issue));
         KCU(cudaStreamSynchronize(c->stream));
         std::memcpy(&nout, hres, sizeof(nout));
-        std::memcpy(part.data(), hres + 1, sizeof(double) * mblk * nv);
+        std::memcpy(part.data(), hres + 16, sizeof(double) * mblk * nv);
     } else {
         KCU(cudaMemsetAsync(misc.p, 0, sizeof(double) * 16, c->stream));
         KCHK(ds->counts.ensure((dbl ? 8 : 4) * (size_t)ds->ncells));

@@ -1806,8 +1806,9 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
 // With CS > 1 the points are dealt out over the cluster's threads; every
 // CTA sends its partial sums to all CTAs (distributed shared memory, clp =
 // this round's buffer, [CS][NSUM]), and after one cluster barrier each sums
-// them in rank order, so that every CTA holds the same totals.  Thread 0
-// receives the NSUM scaled totals in res4.
+// them in rank order, so that every CTA holds the same totals.  Lanes
+// 0..NSUM-1 of warp 0 write the NSUM scaled totals to res4 (shared; the
+// caller's barrier publishes them).  The CTA has at least NSUM warps.
 template <int METHOD, int CS>
 __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const float* __restrict__ acorr, int A0,
                                              int A1, float d0f, float d1f, DFloat scale, DFloat* res4, DFloat* clp,
@@ -1846,49 +1847,48 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
 #pragma unroll
         for (int e = 0; e < NS; ++e) red4[e][wi] = s4[e];
     __syncthreads();
-    DFloat v4[NS];
-    if (wi == 0) {
+    // warp e (e < NS; the CTA has at least NS warps) sums value e over the
+    // warps as FP32 pairs, in a fixed tree: the NS sums run on NS warps side
+    // by side instead of interleaved on one
+    __shared__ DFloat tot[NS];
+    if (wi < NS) {
+        const int e = wi;
         const int nw = (blockDim.x + 31) >> 5;
+        DFloat v{(li < nw) ? red4[e][li] : 0.f, 0.f};
 #pragma unroll
-        for (int e = 0; e < NS; ++e) v4[e] = DFloat{(li < nw) ? red4[e][li] : 0.f, 0.f};
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int e = 0; e < NS; ++e) {
-                const DFloat t{__shfl_down_sync(0xffffffffu, v4[e].h, o), __shfl_down_sync(0xffffffffu, v4[e].l, o)};
-                v4[e] = df_add(v4[e], t);
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const DFloat t{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+            v = df_add(v, t);
+        }
         if constexpr (CS > 1) {
-            // lane r < CS sends this CTA's totals (held by lane 0) to CTA r
-#pragma unroll
-            for (int e = 0; e < NS; ++e)
-                v4[e] = DFloat{__shfl_sync(0xffffffffu, v4[e].h, 0), __shfl_sync(0xffffffffu, v4[e].l, 0)};
-            if (li < CS) {
-                DFloat* dst = cg::this_cluster().map_shared_rank(clp, li);
-#pragma unroll
-                for (int e = 0; e < NS; ++e) dst[rank * NS + e] = v4[e];
-            }
+            // lane r < CS sends this CTA's total (held by lane 0) to CTA r
+            v = DFloat{__shfl_sync(0xffffffffu, v.h, 0), __shfl_sync(0xffffffffu, v.l, 0)};
+            if (li < CS) cg::this_cluster().map_shared_rank(clp, li)[rank * NS + e] = v;
+        } else {
+            if (li == 0) tot[e] = v;
         }
     }
-    if constexpr (CS > 1) {
+    if constexpr (CS > 1)
         cg::this_cluster().sync();
-        if (wi == 0 && li == 0) {
+    else
+        __syncthreads();
+    if (wi == 0 && li < NS) {
+        // lane e: value e summed over the CTAs in rank order, times n^-2 as
+        // FP32 pairs
+        const int e = li;
+        DFloat v;
+        if constexpr (CS > 1) {
+            v = clp[e];
 #pragma unroll
-            for (int e = 0; e < NS; ++e) {
-                v4[e] = clp[e];
-#pragma unroll
-                for (int r = 1; r < CS; ++r) v4[e] = df_add(v4[e], clp[r * NS + e]);
-            }
+            for (int r = 1; r < CS; ++r) v = df_add(v, clp[r * NS + e]);
+        } else {
+            v = tot[e];
         }
+        const float ph = v.h * scale.h;
+        const float pl = fmaf(v.h, scale.h, -ph) + fmaf(v.h, scale.l, v.l * scale.h);
+        const float h = ph + pl;
+        res4[e] = DFloat{h, pl - (h - ph)};
     }
-    if (wi == 0 && li == 0)
-#pragma unroll
-        for (int e = 0; e < NS; ++e) {   // times n^-2 as FP32 pairs
-            const float ph = v4[e].h * scale.h;
-            const float pl = fmaf(v4[e].h, scale.h, -ph) + fmaf(v4[e].h, scale.l, v4[e].l * scale.h);
-            const float h = ph + pl;
-            res4[e] = DFloat{h, pl - (h - ph)};
-        }
 }
 
 // One start's whole quasi-Newton search with lag-domain evaluations against
