@@ -1823,7 +1823,12 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
     // recomputed), compensated sums across the warps
     constexpr int NS = SEL_NSUM;
     float s4[NS] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t = rank * (int)blockDim.x + (int)threadIdx.x; t < total; t += CS * (int)blockDim.x) {
+    // warp w of CTA r takes the 32-point runs w CS + r (+ k CS warps): the
+    // CTAs of a cluster get equal shares, and a warp past the end of the box
+    // skips the shuffles below
+    const int wi = threadIdx.x >> 5, li = threadIdx.x & 31;
+    const bool wact = (wi * CS + rank) * 32 < total;
+    for (int t = (wi * CS + rank) * 32 + li; t < total; t += CS * (int)blockDim.x) {
         const int q = (n0 == 1) ? t : (int)qdiv((uint32_t)t, mn0);
         const int j0 = t - q * n0;
         const int j1 = q - L1;
@@ -1838,11 +1843,11 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
         s4[4] = fmaf(wa, fabsf(v[0]), s4[4]);
     }
     __shared__ float red4[NS][32];
+    if (wact)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int e = 0; e < NS; ++e) s4[e] += __shfl_down_sync(0xffffffffu, s4[e], o);
-    const int wi = threadIdx.x >> 5, li = threadIdx.x & 31;
+            for (int e = 0; e < NS; ++e) s4[e] += __shfl_down_sync(0xffffffffu, s4[e], o);
     if (li == 0)
 #pragma unroll
         for (int e = 0; e < NS; ++e) red4[e][wi] = s4[e];
