@@ -4167,6 +4167,8 @@ static void params_f32(SelectParams& q) {
     q.tauf = (float)q.tau;
     q.d0f = (float)q.delta0;
     q.d1f = (float)q.delta1;
+    q.rd0f = 1.0f / q.d0f;   // an IEEE FP32 division: the correctly rounded reciprocal
+    q.rd1f = 1.0f / q.d1f;
     for (int e = 0; e < 4; ++e) q.Gf[e] = (float)q.G[e];
     // the pilot's Gaussian phi_{2G}, the base of the SCV kernel's
     // cancellation-free form (zero for LSCV, whose G is zero)

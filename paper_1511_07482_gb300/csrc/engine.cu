@@ -1308,13 +1308,13 @@ __device__ __forceinline__ float det2(float a, float b, float c) {
 }
 
 // H = R R^T, R = [[e^t0, 0], [t1, e^t2]].
-// Warp 0 of a CTA: trial point theta -> H, R and the two work items; every
+// Warp 0 of a CTA: trial point theta -> H, R and the work item; every
 // lane returns false when H is outside the search domain (or needs a support
 // beyond the cap / a size with no spectrum).  All lanes run the same
 // straight-line FP32 code (lane s < nsig keeps covariance s), with the
 // determinants in the compensated form of det2, which keeps a strongly
 // correlated H's cancellation exact.  Every CTA of a cluster computes the
-// same items from the same theta.  aux: determinant of H, work of the
+// same item from the same theta.  aux: determinant of H, work of the
 // evaluation (lag route: half-box points; FFT route: flops), bytes.
 __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<float>* it, float* Hs, float* Rs,
                             float* aux) {
@@ -1406,8 +1406,8 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
     const float tr = 0.5f * (B[0] + B[3]), dd = 0.5f * (B[0] - B[3]);
     const float sq = sqrtf(fabsf(tr + sqrtf(fmaf(dd, dd, B[1] * B[1]))));
     const float tau = p.tauf;
-    float v0 = ceilf(tau * sq * __frcp_rn(p.d0f));
-    float v1 = ceilf(tau * sq * __frcp_rn(p.d1f));
+    float v0 = ceilf(tau * sq * p.rd0f);
+    float v1 = ceilf(tau * sq * p.rd1f);
     v0 = fminf(fmaxf(v0, 1.f), (float)(p.M0 - 1));
     v1 = fminf(fmaxf(v1, 1.f), (float)(p.M1 - 1));
     const int L0 = (int)v0, L1 = (int)v1;
@@ -1428,22 +1428,23 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
         if (lane == 0) atomicOr(p.errflag, 2);
         return false;
     }
-    // covariance rows of both items, then the headers, then the weights
+    // the work item (one: the four grids of a bandwidth are evaluated
+    // together), its stores spread over lanes: lanes 0..2 the covariance
+    // rows (lanes 0 and 1 also SCV's exponent differences), lane 3 the
+    // header, lane 4 the bandwidth and its factor (the caller's barrier
+    // publishes them)
     if (lane < MAXSIG) {
         const bool on = lane < nsig;
         const float iv[4] = {on ? iv0 : 0.f, on ? iv1 : 0.f, on ? iv1 : 0.f, on ? iv3 : 0.f};
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int e = 0; e < 4; ++e) it[0].laml[lane][e] = iv[e];
+        it[0].nrm[lane] = on ? nr : 0.f;
+        if (lane < 2 && p.method == 1)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) it[q].laml[lane][e] = iv[e];
-            it[q].nrm[lane] = on ? nr : 0.f;
-            if (lane < 2)
-#pragma unroll
-                for (int e = 0; e < 12; ++e) it[q].xd[lane][e] = xdv[e];
-        }
+            for (int e = 0; e < 12; ++e) it[0].xd[lane][e] = xdv[e];
     }
-    if (lane < 2) {
-        FusedItem<float>& f = it[lane];
+    if (lane == 3) {
+        FusedItem<float>& f = it[0];
         f.S0 = 2 * L0 + 1;
         f.S1 = 2 * L1 + 1;
         f.off0 = L0;
@@ -1464,8 +1465,7 @@ __device__ bool sel_prepare(const SelectParams& p, const float* th, FusedItem<fl
         }
     }
     // (both routes evaluate the four grids with sel_grids: no dense weights)
-    __syncwarp();
-    if (lane == 0) {
+    if (lane == 4) {
         for (int e = 0; e < 4; ++e) Hs[e] = H[e];
         Rs[0] = r00;
         Rs[1] = r10;
@@ -1713,7 +1713,7 @@ __global__ void __launch_bounds__(256) k_select2d(SelectParams p, SelStart* __re
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double cl_red[64];
     __shared__ double res[2][2];
-    __shared__ FusedItem<float> items[2];
+    __shared__ FusedItem<float> items[1];
     __shared__ SelOpt opt;
     __shared__ int ctl[2];              // [valid, done] of this round
     __shared__ float Hs[4], Rs[3], aux[3];
@@ -1987,7 +1987,7 @@ __global__ void __launch_bounds__(1024) k_select2d_lag(SelectParams p, SelectPar
                                                        SelStart* __restrict__ starts, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DFloat res[SEL_NSUM];
-    __shared__ FusedItem<float> items[2];
+    __shared__ FusedItem<float> items[1];
     __shared__ SelOpt opt;
     __shared__ int ctl[2];
     __shared__ float Hs[4], Rs[3], aux[3];

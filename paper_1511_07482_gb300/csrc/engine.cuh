@@ -178,6 +178,7 @@ struct SelectParams {
     float inv_nf;           // 1/n in FP32
     float inv_n2h, inv_n2l; // 1/n^2 as an FP32 pair (h + l)
     float tauf, d0f, d1f;   // tau, delta_0, delta_1 rounded to FP32
+    float rd0f, rd1f;       // 1 / d0f, 1 / d1f, correctly rounded (as __frcp_rn)
     float Gf[4];            // G rounded to FP32
     // SCV, each from FP64 on the host: (2G)^-1 (entries 00, 01, 11), its
     // determinant and delta_0^2, delta_0 delta_1, delta_1^2 as FP32 pairs
