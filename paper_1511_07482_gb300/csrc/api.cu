@@ -939,11 +939,48 @@ static int choose_P(const kdefft_ds ds, const int* L, int* P) {
 }
 
 // support and padding for a kernel whose basis matrix is B
+// lambda_max in closed form for d <= 3 (d = 2: the larger root of the
+// characteristic quadratic; d = 3: the trigonometric solution of the
+// characteristic cubic of a symmetric matrix), Jacobi otherwise
+static double lambda_max_closed(const Mat& S) {
+    const int d = S.d;
+    if (d == 1) return S(0, 0);
+    if (d == 2) {
+        const double h = 0.5 * (S(0, 0) - S(1, 1));
+        return 0.5 * (S(0, 0) + S(1, 1)) + std::sqrt(h * h + S(0, 1) * S(0, 1));
+    }
+    if (d == 3) {
+        const double p1 = S(0, 1) * S(0, 1) + S(0, 2) * S(0, 2) + S(1, 2) * S(1, 2);
+        if (p1 == 0.0) return std::max(S(0, 0), std::max(S(1, 1), S(2, 2)));
+        const double q = (S(0, 0) + S(1, 1) + S(2, 2)) / 3.0;
+        const double a = S(0, 0) - q, b = S(1, 1) - q, c = S(2, 2) - q;
+        const double p = std::sqrt((a * a + b * b + c * c + 2.0 * p1) / 6.0);
+        // det((S - q I) / p) / 2, clamped to the cosine's range
+        const double B01 = S(0, 1) / p, B02 = S(0, 2) / p, B12 = S(1, 2) / p, Ba = a / p, Bb = b / p, Bc = c / p;
+        double r = 0.5 * (Ba * (Bb * Bc - B12 * B12) - B01 * (B01 * Bc - B12 * B02) + B02 * (B01 * B12 - Bb * B02));
+        r = std::min(1.0, std::max(-1.0, r));
+        return q + 2.0 * p * std::cos(std::acos(r) / 3.0);
+    }
+    return lambda_max(S);
+}
+
+// The support of Eq. 26 from lambda_max of B: the closed form first; where
+// tau sqrt(lambda) / delta_k falls within 1e-7 (relative) of an integer, the
+// support could round the other way, so lambda comes from the Jacobi
+// rotations instead (machine precision).  The closed form costs a tenth of
+// the rotations: the supports of a batch of many bandwidths.
 static int plan_for(const kdefft_ds ds, const Mat& B, int* L, int* P) {
     if (ds->opts.L_basis == KDEFFT_L_FULL) {
         for (int k = 0; k < ds->d; ++k) L[k] = (int)(ds->M[k] - 1);
     } else {
-        KCHK(support_L(ds, lambda_max(B), L));
+        double lam = lambda_max_closed(B);
+        bool near = !std::isfinite(lam);
+        for (int k = 0; k < ds->d && !near; ++k) {
+            const double v = ds->opts.tau * std::sqrt(std::fabs(lam)) / ds->delta[k];
+            near = std::fabs(v - std::nearbyint(v)) <= 1e-7 * std::max(1.0, std::fabs(v));
+        }
+        if (near) lam = lambda_max(B);
+        KCHK(support_L(ds, lam, L));
     }
     return choose_P(ds, L, P);
 }
