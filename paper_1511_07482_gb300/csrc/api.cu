@@ -13,7 +13,9 @@
 //   - the quasi-Newton bandwidth optimiser of kdefft_select_H.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <functional>
+#include <thread>
 #include <set>
 #include <cmath>
 #include <cstdio>
@@ -31,6 +33,35 @@
 using namespace kdefft;
 
 // ============================================================ errors
+// Run fn(i0, i1) over [0, n) split into contiguous ranges: inline below two
+// grains, else on up to four host threads (the caller's among them).  Each
+// range's results go to entries of their own, so the outcome does not depend
+// on the split; fn reports failures through shared flags, never through
+// fail() (whose message is per thread).
+template <typename F>
+static void host_parallel_for(size_t n, size_t grain, F&& fn) {
+    if (n < 2 * std::max<size_t>(grain, 1)) {
+        if (n) fn((size_t)0, n);
+        return;
+    }
+    // (the core count is read once: the query reads a system file)
+    static const unsigned hc = std::max(1u, std::thread::hardware_concurrency());
+    const size_t parts = std::min<size_t>({(size_t)4, (size_t)hc, n / std::max<size_t>(grain, 1)});
+    if (parts < 2) {
+        fn((size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(parts - 1);
+    const size_t per = (n + parts - 1) / parts;
+    for (size_t k = 1; k < parts; ++k) {
+        const size_t a = k * per, b = std::min(n, a + per);
+        if (a < b) th.emplace_back([&fn, a, b] { fn(a, b); });
+    }
+    fn((size_t)0, std::min(n, per));
+    for (std::thread& t : th) t.join();
+}
+
 static thread_local std::string g_err;
 
 static int fail(int code, const std::string& msg) {
@@ -2310,91 +2341,125 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
     std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return Re[a] < Re[b]; });
     HermiteIndex& hx = hindex();
-    // inverse covariances and normalisations once per kernel spec (the
-    // pairs of one bandwidth share them)
-    struct SpecInv {
-        bool done = false;
-        double lam[MAXSIG][MAXD * MAXD];
-        double nrm[MAXSIG];
-    };
-    std::vector<SpecInv> sinv(rs.specs.size());
     // fixed tiles, so that an item's sum depends on the item alone, not on
     // the batch it came in: 4096 points in FP32 (smaller tiles halved the
     // throughput of batches: per-tile work is then too small for a CTA), 256
     // in FP64 (the points are slow on the FP64 pipe: more CTAs in flight, one
     // point per thread)
     const long long T = dbl ? 256 : 4096;
+    const size_t ni = ord.size();
     LagBatch bt;
     bt.dbl = dbl;
     bt.d = d;
     std::vector<LagItem<real>>& items = bt.items<real>();
     std::vector<real>& wpool = bt.wpool<real>();
-    items.reserve(ord.size());
-    bt.tiles.reserve(ord.size() * 4);
-    for (size_t u : ord) {
-        const auto& pr = pairs[u];
-        const GridReq& g = rs.grids[pr.first];
-        const KSpec& sp = rs.specs[g.spec];
-        kdefft_ds ds = g.ds;
-        items.emplace_back();
-        LagItem<real>& it = items.back();   // (reserved: no reallocation in the loop)
-        std::memset(&it, 0, sizeof(it));
-        it.d = d;
-        it.nsig = sp.nsig;
-        it.R = Re[u];
-        for (int k = 0; k < d; ++k) {
-            it.L[k] = g.L[k];
-            it.A[k] = ds->acA[k];
-            it.delta[k] = (real)ds->delta[k];
-        }
-        SpecInv& si = sinv[g.spec];
-        if (!si.done) {
+    // layout (serial): each item's tiles and weights at fixed offsets, the
+    // order classes, the algorithmic work
+    std::vector<long long> tile0(ni + 1), woff(ni + 1), npts(ni);
+    tile0[0] = 0;
+    woff[0] = 0;
+    for (size_t q = 0; q < ni; ++q) {
+        const size_t u = ord[q];
+        const GridReq& g = rs.grids[pairs[u].first];
+        const int nsig = rs.specs[g.spec].nsig;
+        long long pts = g.L[0] + 1;
+        for (int k = 1; k < d; ++k) pts *= 2 * g.L[k] + 1;
+        npts[q] = pts;
+        const int N = lag_table_size(d, Re[u], dbl);
+        tile0[q + 1] = tile0[q] + (pts + T - 1) / T;
+        woff[q + 1] = woff[q] + 2LL * nsig * N;
+        if (bt.classes.empty() || bt.classes.back()[0] != Re[u]) bt.classes.push_back({Re[u], (int)tile0[q], 0});
+        bt.classes.back()[2] += (int)(tile0[q + 1] - tile0[q]);
+        bt.fl += (double)pts * nsig * (2.0 * d * d + 8.0 * N);
+        bt.by += (double)pts * sizeof(real);
+        bt.pairs.push_back(pairs[u]);
+    }
+    if (tile0[ni] > 0x7fffffffLL || woff[ni] > 0x7fffffffLL)
+        return fail(KDEFFT_ERR_UNSUPPORTED, "lag batch too large");
+    items.resize(ni);
+    bt.tiles.resize((size_t)tile0[ni]);
+    wpool.assign((size_t)woff[ni], real(0));
+    // inverse covariances and normalisations once per kernel spec (the pairs
+    // of one bandwidth share them), then the items: both over index ranges
+    // that may run on several host threads (each writes its own entries;
+    // the result does not depend on the split)
+    struct SpecInv {
+        double lam[MAXSIG][MAXD * MAXD];
+        double nrm[MAXSIG];
+    };
+    std::vector<char> used(rs.specs.size(), 0);
+    for (size_t q = 0; q < ni; ++q) used[rs.grids[pairs[ord[q]].first].spec] = 1;
+    std::vector<SpecInv> sinv(rs.specs.size());
+    std::atomic<int> err{KDEFFT_OK};
+    host_parallel_for(rs.specs.size(), 2048, [&](size_t s0, size_t s1) {
+        for (size_t si = s0; si < s1; ++si) {
+            if (!used[si]) continue;
+            const KSpec& sp = rs.specs[si];
             for (int s = 0; s < sp.nsig; ++s) {
                 Mat inv;
                 double det;
-                if (!spd_inv_det(sp.sig[s], inv, det))
-                    return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
+                if (!spd_inv_det(sp.sig[s], inv, det)) {
+                    err = KDEFFT_ERR_NOT_SPD;
+                    return;
+                }
                 for (int a = 0; a < d; ++a)
-                    for (int b = 0; b < d; ++b) si.lam[s][a * MAXD + b] = inv(a, b);
-                si.nrm[s] = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
-            }
-            si.done = true;
-        }
-        for (int s = 0; s < sp.nsig; ++s) {
-            for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)si.lam[s][a * MAXD + b];
-            it.nrm[s] = (real)si.nrm[s];
-        }
-        it.acorr = dbl ? (const real*)ds->ac64.p : (const real*)ds->ac32.p;
-        const int N = lag_table_size(d, it.R, dbl);
-        it.w_off = (int)wpool.size();
-        wpool.resize(wpool.size() + 2 * (size_t)sp.nsig * N, real(0));
-        const int gi[2] = {pr.first, pr.second};
-        for (int h = 0; h < 2; ++h) {
-            if (gi[h] < 0) continue;
-            for (const Term& t : rs.grids[gi[h]].terms) {
-                int o = 0;
-                for (int k = 0; k < d; ++k) o += t.alpha[k];
-                const int hidx = hx.idx(d, t.alpha);
-                if (hidx < 0 || hidx >= N) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high");
-                wpool[it.w_off + (h * sp.nsig + t.sig) * N + hidx] += (real)(((o & 1) ? -1.0 : 1.0) * t.w);
+                    for (int b = 0; b < d; ++b) sinv[si].lam[s][a * MAXD + b] = inv(a, b);
+                sinv[si].nrm[s] = std::pow(2.0 * M_PI, -0.5 * d) / std::sqrt(det);
             }
         }
-        const double nn = (double)ds->n;
-        it.scale = 1.0 / (nn * nn);
-        long long pts = g.L[0] + 1;
-        for (int k = 1; k < d; ++k) pts *= 2 * g.L[k] + 1;
-        it.tile0 = (int)bt.tiles.size();
-        for (long long f = 0; f < pts; f += T)
-            bt.tiles.push_back(LagTile{(int)items.size() - 1, (int)std::min(T, pts - f), f});
-        it.ntile = (int)bt.tiles.size() - it.tile0;
-        if (bt.classes.empty() || bt.classes.back()[0] != it.R) bt.classes.push_back({it.R, it.tile0, 0});
-        bt.classes.back()[2] += it.ntile;
-        // algorithmic work: per point nsig exponentials and Hermite tables; bytes: a_j once per point
-        bt.fl += (double)pts * it.nsig * (2.0 * d * d + 8.0 * N);
-        bt.by += (double)pts * sizeof(real);
-        bt.pairs.push_back(pr);
-    }
+    });
+    if (err != KDEFFT_OK) return fail(KDEFFT_ERR_NOT_SPD, "a kernel covariance is not positive definite");
+    host_parallel_for(ni, 2048, [&](size_t q0, size_t q1) {
+        for (size_t q = q0; q < q1; ++q) {
+            const size_t u = ord[q];
+            const auto& pr = pairs[u];
+            const GridReq& g = rs.grids[pr.first];
+            const KSpec& sp = rs.specs[g.spec];
+            kdefft_ds ds = g.ds;
+            LagItem<real>& it = items[q];
+            std::memset(&it, 0, sizeof(it));
+            it.d = d;
+            it.nsig = sp.nsig;
+            it.R = Re[u];
+            for (int k = 0; k < d; ++k) {
+                it.L[k] = g.L[k];
+                it.A[k] = ds->acA[k];
+                it.delta[k] = (real)ds->delta[k];
+            }
+            const SpecInv& si = sinv[g.spec];
+            for (int s = 0; s < sp.nsig; ++s) {
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) it.lam[s][a * MAXD + b] = (real)si.lam[s][a * MAXD + b];
+                it.nrm[s] = (real)si.nrm[s];
+            }
+            it.acorr = dbl ? (const real*)ds->ac64.p : (const real*)ds->ac32.p;
+            const int N = lag_table_size(d, it.R, dbl);
+            it.w_off = (int)woff[q];
+            const int gi[2] = {pr.first, pr.second};
+            for (int h = 0; h < 2; ++h) {
+                if (gi[h] < 0) continue;
+                for (const Term& t : rs.grids[gi[h]].terms) {
+                    int o = 0;
+                    for (int k = 0; k < d; ++k) o += t.alpha[k];
+                    const int hidx = hx.idx(d, t.alpha);
+                    if (hidx < 0 || hidx >= N) {
+                        err = KDEFFT_ERR_UNSUPPORTED;
+                        return;
+                    }
+                    wpool[it.w_off + (h * sp.nsig + t.sig) * N + hidx] += (real)(((o & 1) ? -1.0 : 1.0) * t.w);
+                }
+            }
+            const double nn = (double)ds->n;
+            it.scale = 1.0 / (nn * nn);
+            it.tile0 = (int)tile0[q];
+            it.ntile = (int)(tile0[q + 1] - tile0[q]);
+            const long long pts = npts[q];
+            long long f = 0;
+            for (long long tq = tile0[q]; tq < tile0[q + 1]; ++tq, f += T)
+                bt.tiles[tq] = LagTile{(int)q, (int)std::min(T, pts - f), f};
+        }
+    });
+    if (err != KDEFFT_OK) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high");
     bt.nitems = (int)items.size();
     out.push_back(std::move(bt));
     return KDEFFT_OK;
