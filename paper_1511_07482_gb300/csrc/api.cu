@@ -1031,34 +1031,39 @@ static void alpha2(int d, int a, int b, int* out) {
 
 // ---- LSCV (Eqs. 8, 10-11) ------------------------------------------------
 // grids: [value grids..., gradient grids (a <= b)...]
-static int add_lscv(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int& first) {
+// grids of one LSCV bandwidth: the value grid(s), then the gradient grids
+static int lscv_grid_count(kdefft_ds ds, bool grad) {
+    const int d = ds->d;
+    return (ds->opts.exact_loo ? 2 : 1) + (grad ? d * (d + 1) / 2 : 0);
+}
+
+// The LSCV requests of one bandwidth written in place: its kernel spec at
+// rs.specs[si], its grids at rs.grids[g0 ..] (lscv_grid_count of them).
+static int add_lscv_at(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int si, int g0) {
     const int d = ds->d;
     KCHK(spd_or_fail(H, "H"));
-    KSpec sp;
+    KSpec& sp = rs.specs[si];
     sp.nsig = 2;
     sp.sig[0] = scaled(2.0, H);
     sp.sig[1] = H;
-    const int si = (int)rs.specs.size();
-    rs.specs.push_back(sp);
     int L[4], P[4];
     const Mat& basis = (ds->opts.L_basis == KDEFFT_L_WIDEST) ? sp.sig[0] : H;
     KCHK(plan_for(ds, basis, L, P));
-    first = (int)rs.grids.size();
-    auto push = [&](TermVec t) {
-        GridReq g;
+    int gi = g0;
+    auto put = [&](TermVec t) {
+        GridReq& g = rs.grids[gi++];
         g.ds = ds;
         g.spec = si;
         std::memcpy(g.L, L, sizeof(L));
         std::memcpy(g.P, P, sizeof(P));
         g.terms = std::move(t);
-        rs.grids.push_back(std::move(g));
     };
     const double n = (double)ds->n;
     if (!ds->opts.exact_loo) {
-        push({Term{0, {0, 0, 0, 0}, 1.0}, Term{1, {0, 0, 0, 0}, -2.0}});
+        put({Term{0, {0, 0, 0, 0}, 1.0}, Term{1, {0, 0, 0, 0}, -2.0}});
     } else {
-        push({Term{0, {0, 0, 0, 0}, 1.0}});
-        push({Term{1, {0, 0, 0, 0}, 1.0}});
+        put({Term{0, {0, 0, 0, 0}, 1.0}});
+        put({Term{1, {0, 0, 0, 0}, 1.0}});
     }
     if (grad) {
         const double f = ds->opts.exact_loo ? n / (n - 1.0) : 1.0;
@@ -1068,9 +1073,46 @@ static int add_lscv(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int& firs
                 Term t0{0, {0}, s}, t1{1, {0}, -s * f};
                 alpha2(d, a, b, t0.alpha);
                 alpha2(d, a, b, t1.alpha);
-                push({t0, t1});
+                put({t0, t1});
             }
     }
+    return KDEFFT_OK;
+}
+
+// grids: [value grids..., gradient grids (a <= b)...]
+static int add_lscv(ReqSet& rs, kdefft_ds ds, const Mat& H, bool grad, int& first) {
+    const int si = (int)rs.specs.size();
+    first = (int)rs.grids.size();
+    rs.specs.emplace_back();
+    rs.grids.resize(rs.grids.size() + lscv_grid_count(ds, grad));
+    return add_lscv_at(rs, ds, H, grad, si, first);
+}
+
+// The LSCV requests of many bandwidths (owner[h]: the dataset of H_h): the
+// layout first, then the bandwidths over index ranges that may run on
+// several host threads.  On a failure the set is rebuilt serially, which
+// reports it exactly.
+static int add_lscv_many(ReqSet& rs, const std::vector<kdefft_ds>& owner, const std::vector<Mat>& Hs, bool grad,
+                         std::vector<int>& first) {
+    const size_t nt = Hs.size();
+    const size_t s0 = rs.specs.size(), g00 = rs.grids.size();
+    first.assign(nt, 0);
+    size_t ng = g00;
+    for (size_t h = 0; h < nt; ++h) {
+        first[h] = (int)ng;
+        ng += lscv_grid_count(owner[h], grad);
+    }
+    rs.specs.resize(s0 + nt);
+    rs.grids.resize(ng);
+    std::atomic<int> err{KDEFFT_OK};
+    host_parallel_for(nt, 2048, [&](size_t h0, size_t h1) {
+        for (size_t h = h0; h < h1 && err == KDEFFT_OK; ++h)
+            if (add_lscv_at(rs, owner[h], Hs[h], grad, (int)(s0 + h), first[h]) != KDEFFT_OK) err = KDEFFT_ERR_ARG;
+    });
+    if (err == KDEFFT_OK) return KDEFFT_OK;
+    rs.specs.resize(s0);
+    rs.grids.resize(g00);
+    for (size_t h = 0; h < nt; ++h) KCHK(add_lscv(rs, owner[h], Hs[h], grad, first[h]));
     return KDEFFT_OK;
 }
 
@@ -3703,13 +3745,9 @@ struct LscvJob {
 
 static int lscv_requests(ReqSet& rs, kdefft_ds ds, const double* H, int nH, bool grad, LscvJob& j) {
     const int d = ds->d;
-    j.first.assign(nH, 0);
     j.Hs.assign(nH, Mat());
-    for (int h = 0; h < nH; ++h) {
-        KCHK(sym_check(H + (size_t)h * d * d, d, j.Hs[h], "H"));
-        KCHK(add_lscv(rs, ds, j.Hs[h], grad, j.first[h]));
-    }
-    return KDEFFT_OK;
+    for (int h = 0; h < nH; ++h) KCHK(sym_check(H + (size_t)h * d * d, d, j.Hs[h], "H"));
+    return add_lscv_many(rs, std::vector<kdefft_ds>((size_t)nH, ds), j.Hs, grad, j.first);
 }
 
 static void lscv_assemble(const ReqSet& rs, kdefft_ds ds, const LscvJob& j, std::vector<double>& val,
@@ -4147,19 +4185,19 @@ int kdefft_batch_lscv(kdefft_ctx c, int nds, const kdefft_ds* dss, const int* nH
         for (int h = 0; h < nH_per_ds[i]; ++h) {
             Mat Hm;
             KCHK(sym_check(H + (off + h) * d * d, d, Hm, "H"));
-            int f;
-            KCHK(add_lscv(rs, ds, Hm, grad != nullptr, f));
-            first.push_back(f);
             Hs.push_back(Hm);
             owner.push_back(ds);
         }
         off += nH_per_ds[i];
     }
+    KCHK(add_lscv_many(rs, owner, Hs, grad != nullptr, first));
     KCHK(run(c, rs));
     const size_t nt = Hs.size();
     std::vector<double> v(nt), g(grad ? nt * d * d : 0);
-    for (size_t h = 0; h < nt; ++h)
-        assemble_lscv(owner[h], Hs[h], &rs.grids[first[h]], &v[h], grad ? g.data() + h * d * d : nullptr);
+    host_parallel_for(nt, 2048, [&](size_t h0, size_t h1) {
+        for (size_t h = h0; h < h1; ++h)
+            assemble_lscv(owner[h], Hs[h], &rs.grids[first[h]], &v[h], grad ? g.data() + h * d * d : nullptr);
+    });
     std::memcpy(val, v.data(), sizeof(double) * nt);
     if (grad) std::memcpy(grad, g.data(), sizeof(double) * g.size());
     return KDEFFT_OK;
