@@ -34,6 +34,11 @@
  *     E_ab + E_ba (the single free off-diagonal parameter moving both entries).
  *   - Limits: 1 <= d <= 4, 2 <= M_k, padded sizes P_k <= 4096 and of the form
  *     2^a 3^b 5^c, derivative order r even and r <= 8 (r <= 6 when d = 4).
+ *   - Threads: a context serves one host thread at a time (contexts on
+ *     different threads are independent).  Inside a call with thousands of
+ *     bandwidths the library may build its requests on up to four host
+ *     threads of its own, joined before the call returns; results do not
+ *     depend on it.
  */
 #ifndef KDEFFT_H
 #define KDEFFT_H
