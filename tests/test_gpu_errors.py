@@ -135,3 +135,29 @@ def test_destroyed_handles_are_rejected():
     c.close()
     assert lib.kdefft_destroy(hc) == ERR_ARG
     assert lib.kdefft_destroy(None) == 0
+
+
+def test_large_batch_failure_is_reported_exactly(setup):
+    """A batch of thousands of bandwidths builds its requests on several host
+    threads; one non-positive-definite bandwidth among them still fails with
+    its code and message (the set is rebuilt serially to report it), before
+    any launch, and the same batch without it gives the values of the
+    smaller batches it is made of."""
+    from paper_1511_07482_gb300 import KdefftError
+    c, ds, X, Hns, lo, hi, ref = setup
+    rng = np.random.default_rng(91)
+    Hs = np.stack([Hns * s for s in rng.uniform(0.5, 2.0, 5000)])
+    bad = Hs.copy()
+    bad[3777] = np.array([[1.0, 2.0], [2.0, 1.0]]) * Hns[0, 0]
+    c.profile(1)
+    with pytest.raises(KdefftError) as e:
+        ds.lscv(bad, grad=True)
+    assert _code(e) == ERR_NOT_SPD
+    assert "positive definite" in str(e.value)
+    assert _launches(c) == 0
+    c.profile(0)
+    v, g = ds.lscv(Hs, grad=True)
+    v1, g1 = ds.lscv(Hs[:1000], grad=True)
+    v2, g2 = ds.lscv(Hs[4000:], grad=True)
+    assert np.array_equal(v[:1000], v1) and np.array_equal(g[:1000], g1)
+    assert np.array_equal(v[4000:], v2) and np.array_equal(g[4000:], g2)
