@@ -86,7 +86,8 @@ typedef struct {
     int    L_basis;      /* KDEFFT_L_*                                          */
     int    P_rule;       /* KDEFFT_P_*                                          */
     int    P_fixed[4];   /* used with KDEFFT_P_FIXED                            */
-    int    exact_loo;    /* LSCV: 0 = Eq. 10 (n ~ n-1), 1 = Eq. 8 (leave-one-out) */
+    int    exact_loo;    /* LSCV: 0 = Eq. 10 (n ~ n-1), 1 = Eq. 8 (leave-one- */
+                         /* out; needs n >= 2, else KDEFFT_ERR_ARG)           */
     int    precision;    /* KDEFFT_FP32 or KDEFFT_FP64 arithmetic on the GPU    */
     int    binning;      /* KDEFFT_BIN_*                                        */
     int    outside_policy; /* KDEFFT_OUTSIDE_*                                  */

@@ -3314,6 +3314,10 @@ int kdefft_destroy(kdefft_ctx c) {
     return KDEFFT_OK;
 }
 
+// Eq. 8's leave-one-out sum over j != i carries 1/(n (n - 1)): it has no
+// value for a single point
+static const char* const kLooNeedsTwo = "exact leave-one-out (Eq. 8) needs n >= 2";
+
 int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo, const double* hi,
                const int64_t* M, const kdefft_opts* opts, kdefft_ds* out) {
     if (!c || !out || !lo || !hi || !M) return fail(KDEFFT_ERR_ARG, "NULL argument");
@@ -3327,6 +3331,7 @@ int kdefft_bin(kdefft_ctx c, const double* X, int64_t n, int d, const double* lo
     else
         kdefft_opts_default(&o);
     if (!(o.tau > 0.0)) return fail(KDEFFT_ERR_ARG, "tau must be positive");
+    if (o.exact_loo && n < 2) return fail(KDEFFT_ERR_ARG, kLooNeedsTwo);
     KCU(cudaSetDevice(c->device));
     std::unique_ptr<kdefft_ds_s> ds(new kdefft_ds_s());
     ds->ctx = c;
@@ -3498,6 +3503,7 @@ int kdefft_bin_many(kdefft_ctx c, int nds, const double* const* X, const int64_t
     int K = 32;
     for (int i = 0; i < nds; ++i) {
         if (n[i] < 1 || !X[i]) return fail(KDEFFT_ERR_ARG, "need n >= 1 samples for every dataset");
+        if (o.exact_loo && n[i] < 2) return fail(KDEFFT_ERR_ARG, kLooNeedsTwo);
         dss[i].reset(new kdefft_ds_s());
         kdefft_ds_s& ds = *dss[i];
         ds.ctx = c;
@@ -3632,6 +3638,7 @@ int kdefft_ds_destroy(kdefft_ds ds) {
 int kdefft_ds_set_opts(kdefft_ds ds, const kdefft_opts* o) {
     if (!ds || !o) return fail(KDEFFT_ERR_ARG, "NULL argument");
     if (!(o->tau > 0.0)) return fail(KDEFFT_ERR_ARG, "tau must be positive");
+    if (o->exact_loo && ds->n < 2) return fail(KDEFFT_ERR_ARG, kLooNeedsTwo);
     ds->opts.tau = o->tau;
     ds->opts.L_basis = o->L_basis;
     ds->opts.P_rule = o->P_rule;
