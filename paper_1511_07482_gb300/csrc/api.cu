@@ -2422,7 +2422,7 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
     // throughput of batches: per-tile work is then too small for a CTA), 256
     // in FP64 (the points are slow on the FP64 pipe: more CTAs in flight, one
     // point per thread)
-    const long long T = dbl ? 256 : 4096;
+    const long long T = dbl ? 32 * kLagSlices : 4096;
     const size_t ni = ord.size();
     LagBatch bt;
     bt.dbl = dbl;
@@ -2550,11 +2550,13 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     struct Lay {
         size_t oI, oT, oW;
-        int item0, tile0;
+        int item0;
+        long long tile0;   // first partial pair of the batch
     };
     std::vector<Lay> lay(bts.size());
     size_t bytes = 0;
-    int nit = 0, ntl = 0;
+    int nit = 0;
+    long long ntl = 0;   // partial pairs of the run
     std::vector<LagSum> sums;
     for (size_t b = 0; b < bts.size(); ++b) {
         const LagBatch& bt = bts[b];
@@ -2566,6 +2568,7 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
         bytes += al(std::max<size_t>(bt.w_size(), 16));
         lay[b].item0 = nit;
         lay[b].tile0 = ntl;
+        const int ps = bt.dbl ? kLagSlices : 1;   // partial pairs per tile
         for (int i = 0; i < bt.nitems; ++i) {
             // the item's tile range and scale, wherever its precision keeps them
             int t0i, nti;
@@ -2577,10 +2580,10 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
                 const LagItem<float>& q = bt.it32[i];
                 t0i = q.tile0, nti = q.ntile, sc = q.scale;
             }
-            sums.push_back(LagSum{(long long)ntl + t0i, nti, 0, sc});
+            sums.push_back(LagSum{ntl + (long long)t0i * ps, nti, ps, sc});
         }
         nit += bt.nitems;
-        ntl += (int)bt.tiles.size();
+        ntl += (long long)bt.tiles.size() * ps;
     }
     const size_t oS = bytes;
     bytes += al(sizeof(LagSum) * sums.size());
@@ -2633,16 +2636,19 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
             const size_t nt = std::max<size_t>(bt.tiles.size(), 1);
             for (const auto& cl : bt.classes) {
                 cudaEvent_t ev = prof_start(c);
-                const int grid = std::min(cl[2], c->nsm * 8);
                 if (bt.dbl) {
+                    // fewer tiles than SMs: a warp slice per CTA, so that the
+                    // FP64 points spread over kLagSlices times as many SMs
+                    const bool sl = cl[2] < c->nsm;
                     const LagJob<double> j{(const LagItem<double>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
-                                           cl[1], cl[2], grid, (const double*)(dbase + lay[b].oW),
+                                           cl[1], cl[2], sl ? cl[2] * kLagSlices : std::min(cl[2], c->nsm * 8),
+                                           sl ? 32 : 256, (const double*)(dbase + lay[b].oW),
                                            part + 2 * (size_t)lay[b].tile0};
                     KCU(launch_lag<double>(bt.d, cl[0], j, c->stream));
                 } else {
                     const LagJob<float> j{(const LagItem<float>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
-                                          cl[1], cl[2], grid, (const float*)(dbase + lay[b].oW),
-                                          part + 2 * (size_t)lay[b].tile0};
+                                          cl[1], cl[2], std::min(cl[2], c->nsm * 8), 256,
+                                          (const float*)(dbase + lay[b].oW), part + 2 * (size_t)lay[b].tile0};
                     KCU(launch_lag<float>(bt.d, cl[0], j, c->stream));
                 }
                 prof_stop(c, ev, bt.dbl ? "lag_f64" : "lag_f32", bt.by * cl[2] / nt, bt.fl * cl[2] / nt);

@@ -251,21 +251,30 @@ int lag_table_size(int d, int R, bool dbl);
 // One launch of the lag kernel over tiles [t0, t0 + ntiles) of a batch (one
 // derivative-order class): items, tiles and weights of the batch, partial
 // (2 per tile of the batch).
+// FP64 lag tiles hold 32 * kLagSlices points, one per thread, in kLagSlices
+// warp slices; each slice writes its own partial pair (kLagSlices per tile),
+// which k_lag_sum combines in a fixed order.  So a launch may run one slice
+// per 32-thread CTA (few tiles: the slow FP64 points spread over the SMs) or
+// a whole tile per 256-thread CTA, with the same bits.  FP32 tiles write one
+// partial pair each.
+constexpr int kLagSlices = 8;
 template <typename real>
 struct LagJob {
     const LagItem<real>* items;
     const LagTile* tiles;
     int t0, ntiles, grid;
+    int block;                        // 256; FP64 also 32, 64 or 128 (slices per CTA = block / 32)
     const real* wpool;
-    double* partial;
+    double* partial;                  // per tile of the batch: 1 pair (FP32) or kLagSlices pairs (FP64)
 };
 template <typename real>
 cudaError_t launch_lag(int d, int R, const LagJob<real>& j, cudaStream_t st);
-// An item's tile partials (tile0 indexes the run's whole partial buffer) and
-// its scale n^-2: the per-item sums of a run, whatever the batch's precision.
+// An item's tile partials (tile0 indexes the run's whole partial buffer, in
+// pairs) and its scale n^-2: the per-item sums of a run, whatever the
+// batch's precision.
 struct LagSum {
-    long long tile0;
-    int ntile, pad_;
+    long long tile0;                  // first partial pair of the item's first tile
+    int ntile, nslice;                // tiles; partial pairs per tile (1 or kLagSlices)
     double scale;
 };
 cudaError_t launch_lag_sum(const LagSum* sums, int nitems, const double* partial, double* out, cudaStream_t st);

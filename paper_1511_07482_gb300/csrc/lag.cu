@@ -5,8 +5,9 @@
 //   lag      per work item (two kernels of the same covariances and
 //            support, as in the FFT path), sum over the half lag box of
 //            w_j k_j a_j, w_j in {0, 1, 2}; kernels from the compile-time
-//            Hermite recurrence; compensated FP32 (or FP64) sums, one FP64
-//            partial per tile.
+//            Hermite recurrence; compensated FP32 sums with one FP64
+//            partial per tile, or FP64 sums with one partial per warp slice
+//            of a tile.
 //   lag_sum  fixed-order sum of each item's tile partials, times n^-2, for
 //            the items of every batch of a run in one launch.
 #include <algorithm>
@@ -17,17 +18,28 @@
 namespace kdefft {
 
 // ------------------------------------------------------------ lag evaluation
-// tiles [t0, t0 + ntiles) of the batch's tile list; partial holds one pair
-// per tile of the batch.
+// tiles [t0, t0 + ntiles) of the batch's tile list.  FP32: a tile per CTA
+// (256 threads, thread t takes the tile's points t, t + 256, ...), one
+// partial pair per tile.  FP64: a tile's 256 points are 8 warp slices of one
+// point per thread; a CTA of blockDim threads takes blockDim / 32 slices of
+// a tile, and each warp writes its slice's pair (partial holds kLagSlices
+// pairs per tile).  A thread's points and a warp's shuffle tree are the same
+// for every block size, so the partials are too.
 template <typename real, int D, int R>
 __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ items,
                                              const LagTile* __restrict__ tiles, int t0, int ntiles,
                                              const real* __restrict__ wpool, double* __restrict__ partial) {
+    constexpr bool dbl = sizeof(real) == 8;
     constexpr HTab<D, R> ht{};
     constexpr int N = HTab<D, R>::N;
     __shared__ real Ws[2][MAXSIG][N];
     __shared__ LagItem<real> it;
-    for (int tix = t0 + blockIdx.x; tix < t0 + ntiles; tix += gridDim.x) {
+    const int wpc = (int)(blockDim.x >> 5);               // warps (FP64: slices) per CTA
+    const int per = dbl ? kLagSlices / wpc : 1;           // CTAs per tile
+    const long long nunits = (long long)ntiles * per;
+    for (long long u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int tix = t0 + (int)(u / per);
+        const int s0 = dbl ? (int)(u % per) * wpc : 0;   // first slice of this CTA
         const LagTile tl = tiles[tix];
         __syncthreads();   // the previous tile's readers of it / Ws are done
         if (threadIdx.x == 0) it = items[tl.item];
@@ -43,7 +55,8 @@ __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ i
         SumAcc<real> acc;
         const int n0 = it.L[0] + 1;
         const long long end = tl.first + tl.n;
-        for (long long f = tl.first + threadIdx.x; f < end; f += blockDim.x) {
+        const int vstride = dbl ? 32 * kLagSlices : (int)blockDim.x;
+        for (long long f = tl.first + s0 * 32 + threadIdx.x; f < end; f += vstride) {
             int j[D];
             long long g = f;
             j[0] = (int)(g % n0);
@@ -110,17 +123,40 @@ __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ i
             const real wa = real(wt) * av;
             acc.add(wa * va, wa * vb);
         }
-        double out2[2];
-        block_reduce_acc(acc, out2);
-        if (threadIdx.x == 0) {
-            partial[2 * (long long)tix] = out2[0];
-            partial[2 * (long long)tix + 1] = out2[1];
+        if constexpr (dbl) {
+            double a = acc.a, b = acc.b;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                b += __shfl_down_sync(0xffffffffu, b, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                const long long slot = (long long)tix * kLagSlices + s0 + (threadIdx.x >> 5);
+                partial[2 * slot] = a;
+                partial[2 * slot + 1] = b;
+            }
+        } else {
+            double out2[2];
+            block_reduce_acc(acc, out2);
+            if (threadIdx.x == 0) {
+                partial[2 * (long long)tix] = out2[0];
+                partial[2 * (long long)tix + 1] = out2[1];
+            }
         }
     }
 }
 
+// A FP64 tile's partial from its kLagSlices slice pairs (c = 0, 1): the
+// order of a shuffle-down tree over the eight values (the block reduction
+// these slices replace).
+static_assert(kLagSlices == 8, "the combining order below is written for eight slices");
+__device__ __forceinline__ double slices_sum(const double* __restrict__ p, int c) {
+    return ((p[0 + c] + p[8 + c]) + (p[4 + c] + p[12 + c])) + ((p[2 + c] + p[10 + c]) + (p[6 + c] + p[14 + c]));
+}
+
 // One warp per item (of every batch of a run): lane l sums the item's tile
-// partials l, l + 32, ... in order, then a fixed shuffle tree; times n^-2.
+// partials l, l + 32, ... in order (a FP64 tile's from its slices first),
+// then a fixed shuffle tree; times n^-2.
 __global__ void __launch_bounds__(256) k_lag_sum(const LagSum* __restrict__ sums, int nitems,
                                                  const double* __restrict__ partial, double* __restrict__ out) {
     const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
@@ -129,8 +165,14 @@ __global__ void __launch_bounds__(256) k_lag_sum(const LagSum* __restrict__ sums
     const LagSum sm = sums[i];
     double a = 0.0, b = 0.0;
     for (int t = lane; t < sm.ntile; t += 32) {
-        a += partial[2 * (sm.tile0 + (long long)t)];
-        b += partial[2 * (sm.tile0 + (long long)t) + 1];
+        const double* p = partial + 2 * (sm.tile0 + (long long)t * sm.nslice);
+        if (sm.nslice == kLagSlices) {
+            a += slices_sum(p, 0);
+            b += slices_sum(p, 1);
+        } else {
+            a += p[0];
+            b += p[1];
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -165,7 +207,7 @@ int lag_table_size(int d, int R, bool dbl) {
 
 template <typename real, int D, int R>
 static cudaError_t lag_go(const LagJob<real>& j, cudaStream_t st) {
-    k_lag<real, D, R><<<j.grid, 256, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial);
+    k_lag<real, D, R><<<j.grid, j.block, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial);
     return cudaGetLastError();
 }
 
@@ -192,6 +234,8 @@ template <typename real>
 cudaError_t launch_lag(int d, int R, const LagJob<real>& j, cudaStream_t st) {
     if (j.ntiles <= 0) return cudaSuccess;
     if (j.grid < 1) return cudaErrorInvalidValue;
+    const bool slices_ok = sizeof(real) == 8 && (j.block == 32 || j.block == 64 || j.block == 128);
+    if (j.block != 256 && !slices_ok) return cudaErrorInvalidValue;
     switch (d) {
         case 1: return lag_d<real, 1>(R, j, st);
         case 2: return lag_d<real, 2>(R, j, st);
