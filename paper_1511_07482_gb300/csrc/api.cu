@@ -2353,9 +2353,26 @@ static bool lag_eligible(kdefft_ctx c, const ReqSet& rs, const std::pair<int, in
     if (!c->lag) return false;
     const GridReq& g = rs.grids[pr.first];
     const int d = g.ds->d;
-    for (int k = 0; k < d; ++k)
+    long long pts = g.L[0] + 1;   // half-box points: the lag kernel indexes them in 32 bits
+    for (int k = 0; k < d; ++k) {
         if (g.P[k] < g.ds->M[k] + g.L[k]) return false;
+        if (k > 0) pts *= 2 * g.L[k] + 1;
+    }
+    if (pts > (1LL << 32)) return false;
     return lag_table_size(d, pair_order(rs, pr, d), sizeof(real) == 8) > 0;
+}
+
+// Granlund and Montgomery's unsigned division by an invariant integer
+// 1 <= v < 2^32 for 32-bit numerators ("Division by invariant integers
+// using multiplication", 1994): with l = ceil(log2 v), the multiplier
+// m = floor(2^32 (2^l - v) / v) + 1 and the shifts s1 = min(l, 1),
+// s2 = max(l - 1, 0) give floor(n / v) = (t + ((n - t) >> s1)) >> s2,
+// t = mulhi(m, n).  sh packs s1 | s2 << 8.
+static void invariant_div(uint32_t v, unsigned int& m, int& sh) {
+    int l = 0;
+    while ((1ULL << l) < v) ++l;
+    m = (unsigned int)(((((1ULL << l) - v) << 32) / v) + 1);
+    sh = std::min(l, 1) | (std::max(l - 1, 0) << 8);
 }
 
 // The lag-domain work of one precision in a run, built on the host: the
@@ -2501,6 +2518,7 @@ static int run_lag(kdefft_ctx c, ReqSet& rs, std::vector<std::pair<int, int>> pa
                 it.L[k] = g.L[k];
                 it.A[k] = ds->acA[k];
                 it.delta[k] = (real)ds->delta[k];
+                invariant_div((uint32_t)(k == 0 ? g.L[0] + 1 : 2 * g.L[k] + 1), it.qm[k], it.qs[k]);
             }
             const SpecInv& si = sinv[g.spec];
             for (int s = 0; s < sp.nsig; ++s) {

@@ -1817,6 +1817,9 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
     const int n0 = L0 + 1;
     const int total = n0 * (2 * L1 + 1);
     const uint32_t mn0 = magic_of((uint32_t)max(n0, 2));
+    // the multiply-high quotient is exact while t n0 < 2^32 for every t <
+    // total (large boxes on grids beyond ~1500 nodes divide plainly)
+    const bool fastq = (unsigned long long)total * (unsigned long long)n0 < (1ULL << 32);
     const float d0 = d0f, d1 = d1f;
     // a thread holds a few points: plain FP32 sums there and across its warp
     // (the search compares values to FP32 accuracy; the reported value is
@@ -1829,7 +1832,7 @@ __device__ __forceinline__ void sel_eval_lag(const FusedItem<float>& f, const fl
     const int wi = threadIdx.x >> 5, li = threadIdx.x & 31;
     const bool wact = (wi * CS + rank) * 32 < total;
     for (int t = (wi * CS + rank) * 32 + li; t < total; t += CS * (int)blockDim.x) {
-        const int q = (n0 == 1) ? t : (int)qdiv((uint32_t)t, mn0);
+        const int q = (n0 == 1) ? t : (fastq ? (int)qdiv((uint32_t)t, mn0) : t / n0);
         const int j0 = t - q * n0;
         const int j1 = q - L1;
         const int wt = (j0 > 0 || j1 > 0) ? 2 : (j1 == 0 ? 1 : 0);

@@ -232,6 +232,11 @@ struct LagItem {
     int d, nsig, R, pad_;
     int L[MAXD];                      // support of this item's kernels
     int A[MAXD];                      // box of the autocorrelation array
+    // division of a flat half-box index by the extents L_0 + 1, 2 L_k + 1
+    // (axes 0 .. d - 2) as a multiply-high: multiplier and shifts s1 | s2 << 8
+    // of Granlund and Montgomery's unsigned division by an invariant integer
+    unsigned int qm[MAXD];
+    int qs[MAXD];
     real lam[MAXSIG][MAXD * MAXD];    // Sigma^{-1}, row stride MAXD
     real nrm[MAXSIG];                 // (2 pi)^{-d/2} |Sigma|^{-1/2}
     real delta[MAXD];

@@ -17,6 +17,15 @@
 
 namespace kdefft {
 
+// floor(n / v) for a 32-bit n from the invariant divisor's multiplier m and
+// shifts (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, unsigned case): t = mulhi(m, n), then
+// (t + ((n - t) >> s1)) >> s2; exact for every 32-bit n.
+__device__ __forceinline__ uint32_t inv_div(uint32_t n, uint32_t m, int sh) {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> (sh & 0xff))) >> (sh >> 8);
+}
+
 // ------------------------------------------------------------ lag evaluation
 // tiles [t0, t0 + ntiles) of the batch's tile list.  FP32: a tile per CTA
 // (256 threads, thread t takes the tile's points t, t + 256, ...), one
@@ -26,9 +35,9 @@ namespace kdefft {
 // pairs per tile).  A thread's points and a warp's shuffle tree are the same
 // for every block size, so the partials are too.
 template <typename real, int D, int R>
-__global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ items,
-                                             const LagTile* __restrict__ tiles, int t0, int ntiles,
-                                             const real* __restrict__ wpool, double* __restrict__ partial) {
+__device__ __forceinline__ void lag_tiles(const LagItem<real>* __restrict__ items, const LagTile* __restrict__ tiles,
+                                          int t0, int ntiles, const real* __restrict__ wpool,
+                                          double* __restrict__ partial) {
     constexpr bool dbl = sizeof(real) == 8;
     constexpr HTab<D, R> ht{};
     constexpr int N = HTab<D, R>::N;
@@ -57,16 +66,18 @@ __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ i
         const long long end = tl.first + tl.n;
         const int vstride = dbl ? 32 * kLagSlices : (int)blockDim.x;
         for (long long f = tl.first + s0 * 32 + threadIdx.x; f < end; f += vstride) {
+            // the flat index splits into (j_0, .., j_{d-1}) by exact 32-bit
+            // divisions (the engine takes half boxes below 2^32 points)
             int j[D];
-            long long g = f;
-            j[0] = (int)(g % n0);
-            g /= n0;
+            uint32_t g = (uint32_t)f;
 #pragma unroll
-            for (int k = 1; k < D; ++k) {
-                const int w = 2 * it.L[k] + 1;
-                j[k] = (int)(g % w) - it.L[k];
-                g /= w;
+            for (int k = 0; k < D - 1; ++k) {
+                const uint32_t w = (k == 0) ? (uint32_t)n0 : (uint32_t)(2 * it.L[k] + 1);
+                const uint32_t qv = inv_div(g, it.qm[k], it.qs[k]);
+                j[k] = (int)(g - qv * w) - (k == 0 ? 0 : it.L[k]);
+                g = qv;
             }
+            j[D - 1] = (int)g - (D == 1 ? 0 : it.L[D - 1]);
             // half-space weight: 2 where the first nonzero coordinate is positive
             int wt = 1, decided = 0;
 #pragma unroll
@@ -146,6 +157,26 @@ __global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ i
     }
 }
 
+template <typename real, int D, int R>
+__global__ void __launch_bounds__(256) k_lag(const LagItem<real>* __restrict__ items, const LagTile* __restrict__ tiles,
+                                             int t0, int ntiles, const real* __restrict__ wpool,
+                                             double* __restrict__ partial) {
+    lag_tiles<real, D, R>(items, tiles, t0, ntiles, wpool, partial);
+}
+
+// The same, held to three CTAs per SM (taken for the 3-D fourth-order FP32
+// kernel: 80 registers and a 20-byte spill, where the compiler's own choice
+// of 98 registers leaves two CTAs per SM; psi_4 of 256 bandwidths on a 128^3
+// grid measured 192 against 221 us per launch.  The same cap on the 4-D
+// kernel spilled 268 bytes and measured 64 against 54 us, so the others keep
+// the compiler's choice.)
+template <typename real, int D, int R>
+__global__ void __launch_bounds__(256, 3) k_lag_occ3(const LagItem<real>* __restrict__ items,
+                                                     const LagTile* __restrict__ tiles, int t0, int ntiles,
+                                                     const real* __restrict__ wpool, double* __restrict__ partial) {
+    lag_tiles<real, D, R>(items, tiles, t0, ntiles, wpool, partial);
+}
+
 // A FP64 tile's partial from its kLagSlices slice pairs (c = 0, 1): the
 // order of a shuffle-down tree over the eight values (the block reduction
 // these slices replace).
@@ -207,7 +238,10 @@ int lag_table_size(int d, int R, bool dbl) {
 
 template <typename real, int D, int R>
 static cudaError_t lag_go(const LagJob<real>& j, cudaStream_t st) {
-    k_lag<real, D, R><<<j.grid, j.block, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial);
+    if constexpr (sizeof(real) == 4 && D == 3 && R == 4)
+        k_lag_occ3<real, D, R><<<j.grid, j.block, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial);
+    else
+        k_lag<real, D, R><<<j.grid, j.block, 0, st>>>(j.items, j.tiles, j.t0, j.ntiles, j.wpool, j.partial);
     return cudaGetLastError();
 }
 
