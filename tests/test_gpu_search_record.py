@@ -158,3 +158,45 @@ def test_search_evaluations_match_oracle_on_other_datasets(seed):
         ds.close()
     finally:
         ctx.close()
+
+
+def test_search_values_on_a_box_past_the_fast_quotient():
+    """Lag boxes where a multiply-high quotient by L_0 + 1 is not exact: a
+    1103 x 2048 grid whose support is the whole grid at every trial point
+    (a pilot G wider than the grid), so each evaluation sums 1103 x 4095
+    half-box points and index x 1103 reaches 2^32.  The search kernel takes
+    its plain-division branch there; the values of the first recorded
+    evaluations of two SCV starts against the oracle."""
+    import torch
+    from paper_1511_07482_gb300 import SCV, Context
+    rng = np.random.default_rng(501)
+    X = synthetic.random_mixture(rng, 40, 2, 2)
+    lo, hi, M = X.min(0), X.max(0), [1103, 2048]
+    G = (float(np.max(hi - lo)) / 3.7) ** 2 * np.eye(2)
+    delta = rules.bin_width(lo, hi, M)
+    ctx = Context(0)
+    try:
+        ds = ctx.bin(X, lo, hi, M)
+        n_starts, cap = 2, 2
+        rec = torch.full((n_starts * cap * FIELDS,), float("nan"), dtype=torch.float64, device="cuda:0")
+        ctx.set_search_record(rec, cap)
+        H, f, ne = ds.select_H(SCV, G=G, n_starts=n_starts, max_iter=20)
+        ctx.set_search_record(None)
+        assert np.isfinite(f) and ne > 1
+        R = rec.view(-1, FIELDS).cpu().numpy()
+        R = R[np.isfinite(R[:, 0])]
+        assert len(R) >= 2
+        a = F.autocorr_fft(binning.bin_linear(X, lo, hi, M))
+        for r in R:
+            L = [int(r[6]), int(r[7])]
+            assert L == [M[0] - 1, M[1] - 1]
+            n0, total = L[0] + 1, (L[0] + 1) * (2 * L[1] + 1)
+            assert total * n0 >= 2 ** 32   # past the multiply-high quotient's exactness bound
+            Hr = np.array([[r[3], r[4]], [r[4], r[5]]])
+            sums = F.lag_sums(a, len(X), S.scv_terms(Hr, G), delta, L)   # (value, magnitude) of the double sum
+            ref = S.scv(lambda t: sums[0], Hr, G, len(X))
+            sv = sums[1] + S.RK(Hr) / len(X)   # the value's scale, as abs_scales defines it
+            assert abs(r[8] - ref) / max(abs(ref), 0.1 * sv) <= TOL, (r[8], ref, sv)
+        ds.close()
+    finally:
+        ctx.close()
