@@ -627,6 +627,11 @@ struct kdefft_ctx_s {
     // CUDA graphs of repeated launch sequences, keyed by launch signature
     bool graphs = true;
     cudaStream_t cap_stream = nullptr;   // capture stream, created on first use
+    // second stream for launches that run beside the main stream's (the
+    // FP64 lag batch of a run beside its FP32 one), forked and joined by the
+    // two events; created on first use
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     struct GraphEntry {
         cudaGraphExec_t exec;
         int64_t launches;
@@ -2637,6 +2642,18 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
                                (long long)lay[b].oT, (long long)lay[b].oW, lay[b].item0, lay[b].tile0});
         for (const auto& cl : bt.classes) sig.insert(sig.end(), {cl[0], cl[1], cl[2]});
     }
+    // a run with batches of both precisions launches its FP64 batch on the
+    // side stream, beside the FP32 one (the two touch disjoint partials;
+    // k_lag_sum joins them); not while profiling, whose events time the
+    // launches one after another on the main stream
+    bool has32 = false, has64 = false;
+    for (const LagBatch& bt : bts) (bt.dbl ? has64 : has32) = true;
+    const bool fork = has32 && has64 && !c->prof;
+    if (fork) {
+        if (!c->side) KCU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        if (!c->fork_ev) KCU(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        if (!c->join_ev) KCU(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
     // the upload from pinned staging, the launches and the copy back replay
     // as one graph (the copy reads the staging buffer when the graph runs)
     auto issue = [&]() -> int {
@@ -2649,9 +2666,14 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
         KCU(cudaEventRecordWithFlags(c->staging_ev, c->stream,
                                      cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
                                                                          : cudaEventRecordDefault));
+        if (fork) {
+            KCU(cudaEventRecord(c->fork_ev, c->stream));
+            KCU(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+        }
         for (size_t b = 0; b < bts.size(); ++b) {
             const LagBatch& bt = bts[b];
             const size_t nt = std::max<size_t>(bt.tiles.size(), 1);
+            const cudaStream_t ls = (fork && bt.dbl) ? c->side : c->stream;
             for (const auto& cl : bt.classes) {
                 cudaEvent_t ev = prof_start(c);
                 if (bt.dbl) {
@@ -2662,15 +2684,19 @@ static int issue_lag(kdefft_ctx c, ReqSet& rs, std::vector<LagBatch>& bts) {
                                            cl[1], cl[2], sl ? cl[2] * kLagSlices : std::min(cl[2], c->nsm * 8),
                                            sl ? 32 : 256, (const double*)(dbase + lay[b].oW),
                                            part + 2 * (size_t)lay[b].tile0};
-                    KCU(launch_lag<double>(bt.d, cl[0], j, c->stream));
+                    KCU(launch_lag<double>(bt.d, cl[0], j, ls));
                 } else {
                     const LagJob<float> j{(const LagItem<float>*)(dbase + lay[b].oI), (const LagTile*)(dbase + lay[b].oT),
                                           cl[1], cl[2], std::min(cl[2], c->nsm * 8), 256,
                                           (const float*)(dbase + lay[b].oW), part + 2 * (size_t)lay[b].tile0};
-                    KCU(launch_lag<float>(bt.d, cl[0], j, c->stream));
+                    KCU(launch_lag<float>(bt.d, cl[0], j, ls));
                 }
                 prof_stop(c, ev, bt.dbl ? "lag_f64" : "lag_f32", bt.by * cl[2] / nt, bt.fl * cl[2] / nt);
             }
+        }
+        if (fork) {
+            KCU(cudaEventRecord(c->join_ev, c->side));
+            KCU(cudaStreamWaitEvent(c->stream, c->join_ev, 0));
         }
         cudaEvent_t es = prof_start(c);
         KCU(launch_lag_sum((const LagSum*)(dbase + oS), nit, part, dout, c->stream));
@@ -3326,6 +3352,9 @@ int kdefft_destroy(kdefft_ctx c) {
     for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
     c->gcache.clear();
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
     if (c->staging_ev) cudaEventDestroy(c->staging_ev);
     if (c->acjobs_ev) cudaEventDestroy(c->acjobs_ev);
     if (c->specjobs_ev) cudaEventDestroy(c->specjobs_ev);
