@@ -101,8 +101,12 @@ typedef struct kdefft_ds_s*  kdefft_ds;
 int kdefft_opts_default(kdefft_opts* opts);
 
 /* Create a context on CUDA device `device`, ordering all work on `stream`
- * (a cudaStream_t; NULL = the legacy default stream).  The context owns its
- * device buffers (twiddle tables, scratch, work lists) until kdefft_destroy.
+ * (a cudaStream_t; NULL = the legacy default stream).  Inside a call some
+ * launches may run on a second stream of the context's own, forked from
+ * `stream` after the work before them and joined back into it before the
+ * call's later work: the ordering on `stream` is unchanged.  The context
+ * owns its device buffers (twiddle tables, scratch, work lists) until
+ * kdefft_destroy.
  * Fails with KDEFFT_ERR_CUDA when no usable GPU is present: there is no CPU
  * fallback. */
 int kdefft_create(kdefft_ctx* ctx, int device, void* stream);
