@@ -557,6 +557,37 @@ def _ise_exact_scaled(X, H, w, mu, S_, pair_scale, cross_H):
 
 # ---------------------------------------------------------------- the mutants
 
+def _autocorr_fft(pad=0, power=2):
+    """oracle.functionals.autocorr_fft with the padding 2 M_k - pad or the
+    spectrum's modulus to another power."""
+    def ac(c):
+        import scipy.fft as sf
+        c = np.asarray(c, dtype=np.float64)
+        P = [2 * m - pad for m in c.shape]
+        czp = np.zeros(P)
+        czp[tuple(slice(0, m) for m in c.shape)] = c
+        return sf.irfftn(np.abs(sf.rfftn(czp)) ** power, s=P)
+    return ac
+
+
+def _lag_sums(shrink=0, flip0=False, norm_pow=2, absolute=True):
+    """oracle.functionals.lag_sums with one change: the lag box one short on
+    every axis, the first axis' lag read with the wrong sign, n^-1 for n^-2,
+    or the magnitude summed without |k|."""
+    def ls(a, n, terms, delta, L):
+        Ls = [max(0, l - shrink) for l in L]
+        k = F.lag_kernel(terms, delta, Ls)
+        ax = [np.arange(-Ls[i], Ls[i] + 1) for i in range(len(Ls))]
+        if flip0:
+            ax[0] = -ax[0][::-1] if len(ax) == 1 else ax[0][::-1]
+        idx = np.ix_(*[ax[i] % a.shape[i] for i in range(len(Ls))])
+        aj = a[idx]
+        nn = float(n) ** norm_pow
+        mag = np.abs(k) if absolute else k
+        return float(np.sum(k * aj)) / nn, float(np.sum(mag * aj)) / nn
+    return ls
+
+
 MUTANTS = {
     # gauss: Hermite partials and the density (Sec. 5)
     "He recurrence: contraction term added": lambda mp: _patch(mp, _he_table(sign=+1.0), (gauss, "hermite_table")),
@@ -596,6 +627,12 @@ MUTANTS = {
     "autocorrelation: lag axes mismatched": lambda mp: _patch(mp, _autocorr_axes_shifted, (F, "autocorr")),
     "half box: weight 1 on the positive half": lambda mp: _patch(mp, _half_box_weights(pos=1.0), (F, "half_box_weights")),
     "half box: sign of the last nonzero lag": lambda mp: _patch(mp, _half_box_weights(first=False), (F, "half_box_weights")),
+    "FFT autocorrelation: padding 2M - 2 (the largest lags wrap)": lambda mp: _patch(mp, _autocorr_fft(pad=2), (F, "autocorr_fft")),
+    "FFT autocorrelation: |C| for |C|^2": lambda mp: _patch(mp, _autocorr_fft(power=1), (F, "autocorr_fft")),
+    "lag sums: box one short on every axis": lambda mp: _patch(mp, _lag_sums(shrink=1), (F, "lag_sums")),
+    "lag sums: first-axis lag read with the wrong sign": lambda mp: _patch(mp, _lag_sums(flip0=True), (F, "lag_sums")),
+    "lag sums: n^-1 for n^-2": lambda mp: _patch(mp, _lag_sums(norm_pow=1), (F, "lag_sums")),
+    "lag sums: magnitude without |k|": lambda mp: _patch(mp, _lag_sums(absolute=False), (F, "lag_sums")),
     # selectors (Eqs. 8, 10-11, 29-36; SCV and PI readings)
     "gradients: one diagonal entry left out": lambda mp: _patch(mp, _vech_pairs_offdiag, (S, "vech_pairs")),
     "gradients: factor 2 on the diagonal, not off it": lambda mp: _patch(mp, _tie_swapped, (S, "_tie")),
