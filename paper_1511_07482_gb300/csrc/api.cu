@@ -2901,8 +2901,8 @@ static int run_requests(kdefft_ctx c, ReqSet& rs, const std::vector<int>& sel, s
                     }
                     const TermVec& tl = rs.grids[gi[h]].terms;
                     if ((int)tl.size() > MAXTERM) return fail(KDEFFT_ERR_UNSUPPORTED, "too many kernel terms");
-                    it.nterm[h] = (int)tl.size();
-                    for (size_t m = 0; m < tl.size(); ++m) {
+                    it.nterm[h] = tl.size();
+                    for (int m = 0; m < tl.size(); ++m) {
                         int o = 0;
                         for (int k = 0; k < d; ++k) o += tl[m].alpha[k];
                         if (o > kRmax[d]) return fail(KDEFFT_ERR_UNSUPPORTED, "derivative order too high for d");

@@ -138,13 +138,15 @@ bool smooth(long long x) {
 
 bool radix(int P, AxisPlan& ap) {
     if (P < 2 || P > MAXP) return false;
+    // at most 7 stages for P <= 4096 (3^7 = 2187); the bound only keeps
+    // every write visibly inside the stage array
     int x = P, n = 0;
-    while (x % 8 == 0) { ap.radix[n++] = 8; x /= 8; }
-    if (x % 4 == 0) { ap.radix[n++] = 4; x /= 4; }
-    if (x % 2 == 0) { ap.radix[n++] = 2; x /= 2; }
-    while (x % 5 == 0) { ap.radix[n++] = 5; x /= 5; }
-    while (x % 3 == 0) { ap.radix[n++] = 3; x /= 3; }
-    if (x != 1 || n > MAXST) return false;
+    while (x % 8 == 0 && n < MAXST) { ap.radix[n++] = 8; x /= 8; }
+    if (x % 4 == 0 && n < MAXST) { ap.radix[n++] = 4; x /= 4; }
+    if (x % 2 == 0 && n < MAXST) { ap.radix[n++] = 2; x /= 2; }
+    while (x % 5 == 0 && n < MAXST) { ap.radix[n++] = 5; x /= 5; }
+    while (x % 3 == 0 && n < MAXST) { ap.radix[n++] = 3; x /= 3; }
+    if (x != 1) return false;
     ap.P = P;
     ap.nst = n;
     return true;
